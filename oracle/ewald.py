@@ -1,0 +1,209 @@
+"""Independent reference sums for the Laplace kernel (oracle; test infrastructure only).
+
+These do not use the DMK machinery, the PSWF window or truncated kernels: they
+evaluate Eq. periodic_sum for K = 1/(4 pi r) through the classical Gaussian (Ewald)
+split of Eq. ewald-split, H = erf(r/nu)/(4 pi r) + erfc(r/nu)/(4 pi r), with
+H_M-hat = exp(-k^2 nu^2/4)/k^2 (Eq. Hhat_k):
+
+  real space   sum over images within the erfc cutoff, excluding p = 0 when x_t = x_s;
+  Fourier      D=3: Eq. ewald_far_3P_es with the Gaussian window (k = 0 dropped: neutral
+               or neutralising background, Sec. 1 footnote);
+               D=2: Eq. ewald_far_2P_es: for (k1,k2) != 0 the kappa_3 integral in closed
+               form (checked against scipy quadrature in the tests); for (k1,k2) = 0 the
+               neutral-regularised integral  int (e^{-k^2 nu^2/4} cos(kz) - 1)/k^2 dk
+               up to its z-independent value at z = 0 (cancels for neutral charges);
+               D=1: Eq. ewald_far_1P_es: the (kappa_2, kappa_3) integral in polar form,
+               2 pi int_0^inf J0(kappa rho) e^{-(k1^2+kappa^2) nu^2/4}/(k1^2+kappa^2) kappa dkappa,
+               by Gauss-Legendre quadrature for k1 != 0, and the neutral-regularised
+               closed form for k1 = 0;
+  self         - rho_t lim_{r->0} erf(r/nu)/(4 pi r) = - rho_t/(2 pi^{3/2} nu).
+D = 0 is the plain O(N^2) sum.  Gradients (the field) are returned as well.
+"""
+import numpy as np
+import scipy.special as sp
+
+SQPI = np.sqrt(np.pi)
+
+
+def direct_free(x, q, grad=False):
+    """u_t = sum_{s != t} q_s/(4 pi |x_t - x_s|) (D = 0, Eq. periodic_sum)."""
+    dx = x[:, None, :] - x[None, :, :]
+    r = np.sqrt(np.sum(dx * dx, axis=2))
+    np.fill_diagonal(r, np.inf)
+    u = (q[None, :] / (4 * np.pi * r)).sum(axis=1)
+    if not grad:
+        return u
+    g = -(dx * (q[None, :] / (4 * np.pi * r ** 3))[:, :, None]).sum(axis=1)
+    return u, g
+
+
+def _real_space(x, q, L, periodic, nu, grad):
+    N = x.shape[0]
+    rc = 6.5 * nu
+    ranges = []
+    for i in range(3):
+        if periodic[i]:
+            n = int(np.ceil(rc / L[i])) + 1
+            ranges.append(np.arange(-n, n + 1))
+        else:
+            ranges.append(np.array([0]))
+    u = np.zeros(N)
+    g = np.zeros((N, 3))
+    for a in ranges[0]:
+        for b in ranges[1]:
+            for c in ranges[2]:
+                p = np.array([a * L[0], b * L[1], c * L[2]])
+                dx = x[:, None, :] - x[None, :, :] + p
+                r = np.sqrt(np.sum(dx * dx, axis=2))
+                if a == 0 and b == 0 and c == 0:
+                    np.fill_diagonal(r, np.inf)
+                with np.errstate(divide="ignore", invalid="ignore"):
+                    f = sp.erfc(r / nu) / (4 * np.pi * r)
+                    f = np.where(np.isfinite(r), f, 0.0)
+                u += (f * q[None, :]).sum(axis=1)
+                if grad:
+                    with np.errstate(divide="ignore", invalid="ignore"):
+                        df = -(sp.erfc(r / nu) / r ** 2 + 2 / (SQPI * nu) * np.exp(-(r / nu) ** 2) / r) / (4 * np.pi)
+                        df = np.where(np.isfinite(r), df / r, 0.0)
+                    g += (dx * (df * q[None, :])[:, :, None]).sum(axis=1)
+    return u, g
+
+
+def _kmax(nu):
+    # exp(-k^2 nu^2/4) < 1e-19
+    return 2 * np.sqrt(44.0) / nu
+
+
+def ewald_3p(x, q, L, nu, grad=False):
+    u, g = _real_space(x, q, L, (True, True, True), nu, grad)
+    km = _kmax(nu)
+    n = [int(np.ceil(km * L[i] / (2 * np.pi))) for i in range(3)]
+    ax = [2 * np.pi * np.arange(-n[i], n[i] + 1) / L[i] for i in range(3)]
+    kk = np.stack(np.meshgrid(*ax, indexing="ij"), -1).reshape(-1, 3)
+    k2 = np.sum(kk * kk, axis=1)
+    kk, k2 = kk[k2 > 0], k2[k2 > 0]
+    w = np.exp(-k2 * nu * nu / 4) / k2 / (L[0] * L[1] * L[2])
+    S = np.exp(-1j * x @ kk.T).T @ q              # sum_s q_s e^{-ik x_s}
+    E = np.exp(1j * x @ kk.T)                     # (N, nk)
+    u += (E @ (w * S)).real
+    if grad:
+        g += ((E * (1j * (w * S))[None, :]) @ kk).real
+    u -= q / (2 * np.pi ** 1.5 * nu)
+    return (u, g) if grad else u
+
+
+def _int_2p(alpha, z, nu):
+    """int e^{-(alpha^2+k^2) nu^2/4}/(alpha^2+k^2) e^{ikz} dk, alpha > 0 (closed form)."""
+    e = np.exp(-alpha ** 2 * nu ** 2 / 4 - z ** 2 / nu ** 2)
+    w1 = alpha * nu / 2 + z / nu
+    w2 = alpha * nu / 2 - z / nu
+    return np.pi / (2 * alpha) * e * (sp.erfcx(w1) + sp.erfcx(w2))
+
+
+def _dint_2p(alpha, z, nu):
+    """d/dz of _int_2p: the two Gaussian terms from differentiating erfc cancel, leaving
+    (pi/2) (e^{az} erfc(a nu/2 + z/nu) - e^{-az} erfc(a nu/2 - z/nu))."""
+    e = np.exp(-alpha ** 2 * nu ** 2 / 4 - z ** 2 / nu ** 2)
+    w1 = alpha * nu / 2 + z / nu
+    w2 = alpha * nu / 2 - z / nu
+    return np.pi / 2 * e * (sp.erfcx(w1) - sp.erfcx(w2))
+
+
+def ewald_2p(x, q, L, nu, grad=False):
+    u, g = _real_space(x, q, L, (True, True, False), nu, grad)
+    km = _kmax(nu)
+    n = [int(np.ceil(km * L[i] / (2 * np.pi))) for i in range(2)]
+    A = 1.0 / (L[0] * L[1] * 2 * np.pi)
+    dz = x[:, None, 2] - x[None, :, 2]
+    for a in range(-n[0], n[0] + 1):
+        for b in range(-n[1], n[1] + 1):
+            k1, k2 = 2 * np.pi * a / L[0], 2 * np.pi * b / L[1]
+            if a == 0 and b == 0:
+                # int (e^{-k^2nu^2/4} cos kz - 1)/k^2 dk = -pi (z erf(z/nu) + nu/sqrt(pi)(e^{-z^2/nu^2} - 1))
+                I0 = -np.pi * (dz * sp.erf(dz / nu) + nu / SQPI * (np.exp(-(dz / nu) ** 2) - 1))
+                u += A * (I0 * q[None, :]).sum(axis=1)
+                if grad:
+                    dI0 = -np.pi * sp.erf(dz / nu)
+                    g[:, 2] += A * (dI0 * q[None, :]).sum(axis=1)
+                continue
+            al = np.hypot(k1, k2)
+            if al * nu / 2 > np.sqrt(44.0):
+                continue
+            I = _int_2p(al, dz, nu)
+            ph = np.exp(1j * (k1 * (x[:, None, 0] - x[None, :, 0]) + k2 * (x[:, None, 1] - x[None, :, 1])))
+            u += A * (ph * I * q[None, :]).sum(axis=1).real
+            if grad:
+                g[:, 0] += A * (1j * k1 * ph * I * q[None, :]).sum(axis=1).real
+                g[:, 1] += A * (1j * k2 * ph * I * q[None, :]).sum(axis=1).real
+                g[:, 2] += A * (ph * _dint_2p(al, dz, nu) * q[None, :]).sum(axis=1).real
+    u -= q / (2 * np.pi ** 1.5 * nu)
+    return (u, g) if grad else u
+
+
+def _polar_1p(k1, rr, nu, nq=600):
+    """2 pi int_0^inf J0(kappa rho) e^{-(k1^2+kappa^2)nu^2/4}/(k1^2+kappa^2) kappa dkappa and d/drho."""
+    kmx = _kmax(nu)
+    t, wt = np.polynomial.legendre.leggauss(nq)
+    kap = 0.5 * kmx * (t + 1)
+    wt = 0.5 * kmx * wt
+    f = np.exp(-(k1 ** 2 + kap ** 2) * nu ** 2 / 4) / (k1 ** 2 + kap ** 2) * kap * wt
+    J0 = sp.j0(np.multiply.outer(rr, kap))
+    J1 = sp.j1(np.multiply.outer(rr, kap))
+    val = 2 * np.pi * (J0 @ f)
+    dval = 2 * np.pi * ((-J1 * kap) @ f)
+    return val, dval
+
+
+def ewald_1p(x, q, L, nu, grad=False):
+    u, g = _real_space(x, q, L, (True, False, False), nu, grad)
+    km = _kmax(nu)
+    n = int(np.ceil(km * L[0] / (2 * np.pi)))
+    A = 1.0 / (L[0] * (2 * np.pi) ** 2)
+    dy = x[:, None, 1] - x[None, :, 1]
+    dzz = x[:, None, 2] - x[None, :, 2]
+    rr = np.sqrt(dy ** 2 + dzz ** 2)
+    dx1 = x[:, None, 0] - x[None, :, 0]
+    for a in range(-n, n + 1):
+        k1 = 2 * np.pi * a / L[0]
+        if a == 0:
+            # 2 pi int_0^inf (J0(kappa rho) - 1) e^{-kappa^2 nu^2/4}/kappa dkappa
+            #   = -pi (E1(rho^2/nu^2) + ln(rho^2/nu^2) + gamma)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                xx = (rr / nu) ** 2
+                I0 = -np.pi * (sp.exp1(xx) + np.log(xx) + np.euler_gamma)
+                I0 = np.where(rr > 0, I0, 0.0)
+            u += A * (I0 * q[None, :]).sum(axis=1)
+            if grad:
+                with np.errstate(divide="ignore", invalid="ignore"):
+                    dI0 = -2 * np.pi * (1 - np.exp(-(rr / nu) ** 2)) / rr
+                    dI0 = np.where(rr > 0, dI0, 0.0)
+                    cy = np.where(rr > 0, dy / rr, 0.0)
+                    cz = np.where(rr > 0, dzz / rr, 0.0)
+                g[:, 1] += A * (dI0 * cy * q[None, :]).sum(axis=1)
+                g[:, 2] += A * (dI0 * cz * q[None, :]).sum(axis=1)
+            continue
+        if abs(k1) * nu / 2 > np.sqrt(44.0):
+            continue
+        I, dI = _polar_1p(k1, rr, nu)
+        ph = np.exp(1j * k1 * dx1)
+        u += A * (ph * I * q[None, :]).sum(axis=1).real
+        if grad:
+            with np.errstate(divide="ignore", invalid="ignore"):
+                cy = np.where(rr > 0, dy / rr, 0.0)
+                cz = np.where(rr > 0, dzz / rr, 0.0)
+            g[:, 0] += A * (1j * k1 * ph * I * q[None, :]).sum(axis=1).real
+            g[:, 1] += A * (ph * dI * cy * q[None, :]).sum(axis=1).real
+            g[:, 2] += A * (ph * dI * cz * q[None, :]).sum(axis=1).real
+    u -= q / (2 * np.pi ** 1.5 * nu)
+    return (u, g) if grad else u
+
+
+def laplace_reference(D, L, x, q, nu=None, grad=False):
+    """Reference u (and field gradient) for the Laplace kernel with D periodic directions."""
+    x = np.asarray(x, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64).ravel()
+    if D == 0:
+        return direct_free(x, q, grad)
+    if nu is None:
+        nu = min(L[:D]) / 4
+    return {3: ewald_3p, 2: ewald_2p, 1: ewald_1p}[D](x, q, list(L), nu, grad)

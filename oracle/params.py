@@ -1,0 +1,163 @@
+"""Plan parameters (oracle; test infrastructure only).
+
+Sec. 6.1 and Tables 1 (Laplace) and 5 (Stokes kernels) fix, per tolerance row,
+the PSWF band limit c and the Chebyshev order p.  Readings taken here:
+
+* tol in between rows maps to the next stricter row (1e-3, 1e-6, 1e-9, 1e-12).
+* c is taken as printed in Tables 1 and 5, with one exception: the rotlet
+  1e-3 row prints 6.28, and only c = 2 pi (which 6.28 rounds) reproduces its
+  N_per = 3; with the printed values every other N_F and N_per of both tables
+  follows from the rules below.
+* n_f = ceil(3c/pi) - 1 and N_F = 2 n_f + 1 (Sec. 6.1; the text of Sec. 2.3
+  omits the -1, the tables use it).  The ceiling is taken after removing a
+  relative 1e-12 so that 3c/pi landing on an integer does not round up.
+* nu_0 = s, the root cube side (Sec. 4: supp D_l = r_l = box side, and Table 1
+  gives R = L_3 + nu_0 = 2 on the unit cube).
+* Root modes: the periodic integer range of Eq. kintmax (ceil), keeping only
+  |k| nu_0 <= c (phi-hat is zero beyond the band, Eq. wfunchat), with ties kept
+  up to a relative 1e-12.  This reproduces every N_per of Tables 1 and 5 except
+  where c/(2 pi) is itself an integer (a tie whose mode carries phi-hat(c)).
+* Free directions (Sec. 5.3, Eq. k1set-1p, k1k2set-2p): step dk = pi/R (the
+  Nyquist limit for a kernel truncated at R, Sec. 5.3), N = ceil(c/(nu_0 dk)),
+  n = -N..N; R = L_3 + nu_0 (D=2), sqrt((L_2+nu_0)^2+(L_3+nu_0)^2) (D=1), with
+  the free lengths rounded up to multiples of s (Sec. 5).  The truncated symbol
+  is used for every mode (Remark alpha_switch allows "truncated for all").
+* D = 0: one cube of side max L_i (Sec. 3.1.1 "box of equal sides"); the root
+  far field is the free-space Fourier integral of the kernel truncated at
+  R = sqrt(sum (L_i+nu_0)^2) (Sec. 3.1.3), on the same trapezoidal grid rule.
+"""
+import math
+import numpy as np
+
+KERNELS = ("laplace", "stokeslet", "stresslet", "rotlet")
+TOL_ROWS = (1e-3, 1e-6, 1e-9, 1e-12)
+
+# (c, p) per tolerance row: Table 1 (Laplace) and Table 5 (Stokes kernels).
+TABLE = {
+    "laplace":   [(7.00, 12), (14.50, 20), (21.50, 30), (29.00, 38)],
+    "stokeslet": [(10.47, 13), (17.80, 23), (25.13, 34), (32.46, 44)],
+    "stresslet": [(10.47, 12), (17.80, 23), (25.13, 33), (33.51, 45)],
+    "rotlet":    [(2 * math.pi, 8), (13.61, 18), (20.94, 29), (28.27, 39)],
+}
+
+# source/target component counts (App. B): Laplace scalar; Stokeslet force -> velocity;
+# stresslet Q_lm = q_l n_m (9) -> velocity; rotlet torque -> velocity.
+D_RHO = {"laplace": 1, "stokeslet": 3, "stresslet": 9, "rotlet": 3}
+D_U = {"laplace": 1, "stokeslet": 3, "stresslet": 3, "rotlet": 3}
+
+
+def table_row(tol):
+    """Index of the tolerance row used for tol (next stricter row)."""
+    if not (1e-12 * (1 - 1e-9) <= tol <= 1e-3 * (1 + 1e-9)):
+        raise ValueError("tol outside [1e-12, 1e-3]")
+    for i, t in enumerate(TOL_ROWS):
+        if tol >= t * (1 - 1e-9):
+            return i
+    return len(TOL_ROWS) - 1
+
+
+def c_and_p(kernel, tol):
+    return TABLE[kernel][table_row(tol)]
+
+
+def n_f(c):
+    """n_f = ceil(3c/pi) - 1 (Sec. 6.1)."""
+    return int(math.ceil(3.0 * c / math.pi * (1.0 - 1e-12))) - 1
+
+
+class Geometry:
+    """Cube tiling of the primary cell (Sec. 4.1.1, Sec. 5; exact tilings only)."""
+
+    def __init__(self, D, L):
+        L = [float(v) for v in L]
+        if D not in (0, 1, 2, 3):
+            raise ValueError("D must be 0..3")
+        if any(not (v > 0 and math.isfinite(v)) for v in L):
+            raise ValueError("lengths must be positive")
+        self.D = D
+        self.L = L
+        self.s = min(L[:D]) if D > 0 else max(L)
+        M = []
+        Lext = []
+        for i in range(3):
+            ratio = L[i] / self.s
+            if i < D:
+                m = int(round(ratio))
+                if abs(ratio - m) > 1e-12 * max(1.0, ratio):
+                    raise NotImplementedError("periodic length not an integer multiple of the cube side")
+                M.append(m)
+                Lext.append(L[i])
+            else:
+                m = int(math.ceil(ratio * (1 - 1e-12)))
+                M.append(max(m, 1))
+                Lext.append(M[-1] * self.s)
+        self.M = tuple(M)
+        self.Lext = Lext
+        self.nu0 = self.s
+        self.periodic = tuple(i < D for i in range(3))
+
+
+def root_modes(kernel, geom, c, return_axes=False):
+    """Root Fourier discretisation: list of wave vectors and the constant C^{DP}.
+
+    Returns (k (n,3), C, R, dk); with return_axes, the three 1-D wavenumber axes of the
+    enclosing rectangle and the boolean mask of retained modes on it instead of k.  Sec. 4.3 (Eq. wavenumbers-3p-trunc, kintmax) for the
+    periodic directions and Sec. 5.3 (Eqs. k1set-1p, k1k2set-2p, ewald_far_allP_discr)
+    for the free ones; D=0 by the same rule in all three directions.
+    """
+    D, nu0 = geom.D, geom.nu0
+    K = c / nu0
+    axes = []
+    R = None
+    dk = None
+    Lx = geom.Lext
+    if D == 3:
+        pass
+    elif D == 2:
+        R = Lx[2] + nu0
+    elif D == 1:
+        R = math.sqrt((Lx[1] + nu0) ** 2 + (Lx[2] + nu0) ** 2)
+    else:
+        R = math.sqrt(sum((Lx[i] + nu0) ** 2 for i in range(3)))
+    if D < 3:
+        dk = math.pi / R
+        Nfree = int(math.ceil(K / dk * (1 - 1e-12)))
+    for i in range(3):
+        if i < D:
+            kmax = int(math.ceil(geom.L[i] * K / (2 * math.pi) * (1 - 1e-12)))
+            axes.append(2 * math.pi * np.arange(-kmax, kmax + 1) / geom.L[i])
+        else:
+            axes.append(dk * np.arange(-Nfree, Nfree + 1))
+    kk = np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1).reshape(-1, 3)
+    kn = np.sqrt(np.sum(kk * kk, axis=1))
+    keep = kn * nu0 <= c * (1 + 1e-12)
+    if D == 3:
+        keep &= kn > 0
+    keepr = keep.reshape(len(axes[0]), len(axes[1]), len(axes[2]))
+    kk = kk[keep]
+    if D == 3:
+        C = 1.0 / (geom.L[0] * geom.L[1] * geom.L[2])
+    elif D == 2:
+        C = dk / (geom.L[0] * geom.L[1] * 2 * math.pi)
+    elif D == 1:
+        C = dk * dk / (geom.L[0] * (2 * math.pi) ** 2)
+    else:
+        C = dk ** 3 / (2 * math.pi) ** 3
+    if return_axes:
+        return axes, keepr, C, R, dk
+    return kk, C, R, dk
+
+
+def mode_counts(kernel, D, L, tol):
+    """(N_per_i, N_free_i, R) in the layout of Tables 1 and 5 (Sec. 6.1)."""
+    c, p = c_and_p(kernel, tol)
+    g = Geometry(D, L)
+    kk, C, R, dk = root_modes(kernel, g, c)
+    counts = []
+    for i in range(3):
+        if i < D:       # N_per_i = number of distinct periodic integers kept
+            vals = np.unique(np.round(kk[:, i] / (2 * math.pi / g.L[i])).astype(int))
+            counts.append(len(vals))
+        else:           # N_free_i = 2N+1 trapezoidal nodes of Eq. k1set-1p / k1k2set-2p
+            counts.append(2 * int(math.ceil(c / g.nu0 / dk * (1 - 1e-12))) + 1)
+    return counts, R

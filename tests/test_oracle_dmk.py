@@ -1,0 +1,225 @@
+"""Whole-pipeline pins of the oracle DMK (Sec. 3-5) against independent references.
+
+* Laplace, every D: the Ewald-type reference of oracle/ewald.py (Gaussian split, no DMK
+  machinery), to within the tolerance row (Table 2 reports errors below eps).
+* D = 3: the NaCl Madelung constant (tests/golden/madelung_nacl.txt).
+* Stokes kernels, D = 0: the O(N^2) free-space sum of App. B's kernels.
+* Rotlet, D = 3: -1/2 curl of three Laplace potentials (Eq. rotlet_def_deriv).
+* Invariants: permutation, linearity, symmetry, periodic translation; 2:1 balance.
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+from scipy.integrate import quad
+import scipy.special as sp
+
+from oracle.dmk import evaluate
+from oracle import ewald
+from oracle.kernels import Kernel
+from oracle.params import Geometry
+from oracle.tree import Forest, wrap_and_quantize, BITS
+
+from paper_2606_27134_b300 import workloads
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b))
+
+
+CASES = [(3, [1, 1, 1]), (3, [2, 1, 1]), (2, [1, 1, 0.5]), (2, [1, 2, 1]), (1, [1, 1, 1]), (1, [2, 1, 1]),
+         (0, [1, 1, 1])]
+
+
+@pytest.mark.parametrize("D,L", CASES, ids=lambda v: str(v))
+def test_laplace_vs_ewald(D, L):
+    x, q = workloads.mixed_points(100, L, seed=11 + D), None
+    q = workloads.neutral_charges(100, seed=5 + D)
+    r = evaluate("laplace", D, L, 1e-6, x, q, n_s=12, grad=True)
+    ue, ge = ewald.laplace_reference(D, L, x, q, grad=True)
+    assert rel(r.u[:, 0], ue) < 1e-6
+    assert rel(r.grad[:, :, 0], ge) < 3e-6
+
+
+def test_laplace_vs_ewald_tight():
+    L = [1, 1, 1]
+    x = workloads.uniform_points(80, L, seed=3)
+    q = workloads.neutral_charges(80, seed=4)
+    r = evaluate("laplace", 3, L, 1e-9, x, q, n_s=10)
+    assert rel(r.u[:, 0], ewald.laplace_reference(3, L, x, q)) < 1e-9
+
+
+def _nacl(reps):
+    a = 0.5
+    pts, qs = [], []
+    for i, j, k in itertools.product(range(2 * reps), repeat=3):
+        pts.append([(i + 0.25) * a, (j + 0.25) * a, (k + 0.25) * a])
+        qs.append((-1.0) ** (i + j + k))
+    return np.array(pts), np.array(qs), [reps * 1.0] * 3, a
+
+
+@pytest.mark.parametrize("reps", [1, 2])
+def test_madelung(reps):
+    M = float(open(os.path.join(os.path.dirname(__file__), "golden", "madelung_nacl.txt")).read().split()[-1])
+    x, q, L, a = _nacl(reps)
+    want = -q * M / (4 * np.pi * a)
+    r = evaluate("laplace", 3, L, 1e-9, x, q, n_s=4)
+    assert np.max(np.abs(r.u[:, 0] - want)) < 1e-9 * np.max(np.abs(want))
+    assert np.max(np.abs(ewald.laplace_reference(3, L, x, q) - want)) < 1e-12
+
+
+def test_ewald_2p_integral_closed_form():
+    """The closed form used for the kappa_3 integral of Eq. ewald_far_2P_es (alpha > 0)."""
+    nu = 0.3
+    for alpha, z in [(2 * np.pi, 0.0), (2 * np.pi, 0.4), (8.9, -0.7), (20.0, 0.15)]:
+        f = lambda k: np.exp(-(alpha ** 2 + k * k) * nu * nu / 4) / (alpha ** 2 + k * k) * np.cos(k * z)
+        ref = 2 * quad(f, 0, np.inf, limit=400, epsabs=1e-15)[0]
+        assert ewald._int_2p(alpha, z, nu) == pytest.approx(ref, rel=1e-10)
+        h = 1e-6
+        fd = (ewald._int_2p(alpha, z + h, nu) - ewald._int_2p(alpha, z - h, nu)) / (2 * h)
+        assert ewald._dint_2p(alpha, z, nu) == pytest.approx(fd, rel=1e-6, abs=1e-10)
+    # zero mode: int (e^{-k^2 nu^2/4} cos kz - 1)/k^2 dk
+    for z in [0.1, 0.5, 1.3]:
+        f = lambda k: (np.exp(-k * k * nu * nu / 4) * np.cos(k * z) - 1) / (k * k)
+        K = 40.0 / nu                 # beyond K the Gaussian is < 1e-170; the -1/k^2 tail is -1/K
+        ref = 2 * (quad(f, 0, K, limit=2000, epsabs=1e-14)[0] - 1.0 / K)
+        # the reference drops the z-independent constant I(0) = -sqrt(pi) nu, which cancels
+        # in sum_s q_s I(z_t - z_s) for neutral charges (the only case Sec. 5.2 admits)
+        val = -np.pi * (z * sp.erf(z / nu) + nu / np.sqrt(np.pi) * (np.exp(-(z / nu) ** 2) - 1))
+        assert val - np.sqrt(np.pi) * nu == pytest.approx(ref, rel=1e-8)
+
+
+def test_ewald_1p_integrals():
+    """Polar kappa integrals of Eq. ewald_far_1P_es: quadrature rule and the k1 = 0 closed form."""
+    nu = 0.25
+    rr = np.array([0.05, 0.3, 0.9])
+    for k1 in [2 * np.pi, 4 * np.pi]:
+        val, _ = ewald._polar_1p(k1, rr, nu)
+        for i, r in enumerate(rr):
+            f = lambda k: sp.j0(k * r) * np.exp(-(k1 ** 2 + k * k) * nu * nu / 4) / (k1 ** 2 + k * k) * k
+            assert val[i] == pytest.approx(2 * np.pi * quad(f, 0, np.inf, limit=400)[0], rel=1e-9)
+    for r in rr:
+        f = lambda k: (sp.j0(k * r) - 1) * np.exp(-k * k * nu * nu / 4) / k
+        ref = 2 * np.pi * quad(f, 0, np.inf, limit=400)[0]
+        x = (r / nu) ** 2
+        assert -np.pi * (sp.exp1(x) + np.log(x) + np.euler_gamma) == pytest.approx(ref, rel=1e-9)
+
+
+@pytest.mark.parametrize("kernel", ["stokeslet", "stresslet", "rotlet"])
+def test_stokes_free_space_direct(kernel):
+    """D = 0: oracle vs the O(N^2) sum of the kernels of App. B."""
+    L = [1, 1, 1]
+    N = 90
+    x = workloads.mixed_points(N, L, seed=21)
+    K = Kernel(kernel)
+    rho = workloads.stokes_strengths(kernel, N, seed=22)
+    r = evaluate(kernel, 0, L, 1e-6, x, rho, n_s=12, grad=True)
+    dx = x[:, None, :] - x[None, :, :]
+    ii, jj = np.nonzero(~np.eye(N, dtype=bool))
+    Kv = K.full(dx[ii, jj])
+    u = np.zeros((N, K.d_u))
+    np.add.at(u, ii, np.einsum("nab,nb->na", Kv, rho[jj]))
+    assert rel(r.u, u) < 2e-6
+    # gradient by complex step of the direct sum
+    g = np.zeros((N, 3, K.d_u))
+    for i in range(3):
+        d = dx[ii, jj].astype(complex)
+        d[:, i] += 1e-30j
+        gi = np.zeros((N, K.d_u), dtype=complex)
+        np.add.at(gi, ii, np.einsum("nab,nb->na", K.full(d), rho[jj]))
+        g[:, i, :] = gi.imag / 1e-30
+    assert rel(r.grad, g) < 1e-5
+
+
+@pytest.mark.parametrize("D,L", [(3, [1, 1, 1]), (2, [1, 1, 1])])
+def test_rotlet_is_curl_of_laplace(D, L):
+    """Eq. rotlet_def_deriv: Omega_jl tau_l = -1/2 eps_jlm d_m H tau_l, so the rotlet sum equals
+    -1/2 curl of three Laplace potentials (one per torque component) -- to within eps."""
+    N = 90
+    x = workloads.mixed_points(N, L, seed=31)
+    tau = workloads.stokes_strengths("rotlet", N, seed=32)
+    tau -= tau.mean(axis=0)           # neutral components for the D < 3 Laplace sums
+    r = evaluate("rotlet", D, L, 1e-9, x, tau, n_s=12)
+    gl = np.stack([evaluate("laplace", D, L, 1e-9, x, tau[:, l], n_s=12, grad=True).grad[:, :, 0]
+                   for l in range(3)], axis=1)          # gl[t, l, m] = d_m phi_l
+    eps = np.zeros((3, 3, 3))
+    eps[0, 1, 2] = eps[1, 2, 0] = eps[2, 0, 1] = 1
+    eps[0, 2, 1] = eps[2, 1, 0] = eps[1, 0, 2] = -1
+    want = -0.5 * np.einsum("jlm,tlm->tj", eps, gl)
+    assert rel(r.u, want) < 1e-8
+
+
+def test_invariants():
+    L = [1, 1, 1]
+    N = 120
+    x = workloads.uniform_points(N, L, seed=41)
+    q = workloads.neutral_charges(N, seed=42)
+    q2 = workloads.neutral_charges(N, seed=43)
+    base = evaluate("laplace", 3, L, 1e-6, x, q, n_s=15).u[:, 0]
+    perm = np.random.default_rng(0).permutation(N)
+    up = evaluate("laplace", 3, L, 1e-6, x[perm], q[perm], n_s=15).u[:, 0]
+    assert np.max(np.abs(up - base[perm])) < 1e-12 * np.max(np.abs(base))
+    lin = evaluate("laplace", 3, L, 1e-6, x, 2 * q - 3 * q2, n_s=15).u[:, 0]
+    b2 = evaluate("laplace", 3, L, 1e-6, x, q2, n_s=15).u[:, 0]
+    assert np.max(np.abs(lin - (2 * base - 3 * b2))) < 1e-12 * np.max(np.abs(lin))
+    # symmetry of the (symmetric) operator: q2 . u(q) = q . u(q2), to within eps
+    assert abs(q2 @ base - q @ b2) < 1e-6 * np.sqrt(np.sum(base ** 2) * np.sum(q2 ** 2))
+    # translation by a vector in the periodic directions (the tree changes; result within eps)
+    shift = np.array([0.3137, -0.271, 0.5])
+    ut = evaluate("laplace", 3, L, 1e-6, x + shift, q, n_s=15).u[:, 0]
+    assert rel(ut, base) < 2e-6
+    # a point moved by a whole period is the same point
+    x3 = x.copy()
+    x3[7, 0] += 1.0
+    x3[9, 2] -= 1.0
+    u3 = evaluate("laplace", 3, L, 1e-6, x3, q, n_s=15).u[:, 0]
+    assert np.max(np.abs(u3 - base)) < 1e-12 * np.max(np.abs(base))
+
+
+def test_tree_is_balanced():
+    """Sec. 3.1.1: leaves hold <= n_s points and touching leaves differ by at most one level."""
+    geom = Geometry(3, [1, 1, 1])
+    x = workloads.clustered_points(600, [1, 1, 1], seed=51, n_centers=3, sigma=0.02)
+    w, G = wrap_and_quantize(x, geom)
+    f = Forest(geom, G, 10)
+    leaves = f.leaves()
+    assert all(len(b.pts) <= 10 for b in leaves)
+    assert sum(len(b.pts) for b in leaves) == len(x)
+    n = 2 ** BITS
+    for a in leaves:
+        for b in leaves:
+            if b.level < a.level + 2:
+                continue
+            for sh in itertools.product((-1, 0, 1), repeat=3):
+                ok = True
+                for i in range(3):
+                    alo, ahi = a.ix[i] << (BITS - a.level), (a.ix[i] + 1) << (BITS - a.level)
+                    blo, bhi = (b.ix[i] << (BITS - b.level)) + sh[i] * n, ((b.ix[i] + 1) << (BITS - b.level)) + sh[i] * n
+                    ok &= blo <= ahi and alo <= bhi
+                assert not ok
+
+
+def test_gradient_is_derivative():
+    """Complex-step gradient == central difference of the oracle's own u(x_t).
+
+    The moved point carries zero strength, so u_t depends on x_t only as a target, and
+    it stays far from every integer grid line (the tree does not change).
+    """
+    L = [1, 1, 1]
+    N = 60
+    x = workloads.uniform_points(N, L, seed=61)
+    q = workloads.neutral_charges(N, seed=62)
+    h = 1e-7
+    frac = np.abs(x * 2 ** BITS - np.round(x * 2 ** BITS))
+    t = int(np.argmax(np.min(frac, axis=1)))
+    assert np.min(frac[t]) > 4 * h * 2 ** BITS
+    q[t] = 0.0
+    r = evaluate("laplace", 3, L, 1e-6, x, q, n_s=10, grad=True)
+    for i in range(3):
+        xp, xm = x.copy(), x.copy()
+        xp[t, i] += h
+        xm[t, i] -= h
+        up = evaluate("laplace", 3, L, 1e-6, xp, q, n_s=10).u[t, 0]
+        um = evaluate("laplace", 3, L, 1e-6, xm, q, n_s=10).u[t, 0]
+        assert (up - um) / (2 * h) == pytest.approx(r.grad[t, i, 0], rel=1e-6, abs=1e-8)
