@@ -1,0 +1,281 @@
+"""Benchmark of the periodized DMK hot path on B300.
+
+Workload (the configuration the headline metric is quoted on): Laplace kernel, D = 2 (x, y
+periodic), cell L = (1, 1, 0.25), N = 1e5 uniform points, neutral charges uniform in [-1, 1]
+minus their mean, tol 1e-6 (p = 20, N_F = 27), n_s = 250.  One step = one full dmk_eval of
+potentials and forces (tree build, upward pass, root far field, plane waves, shifts, leaf
+stage) on inputs already resident in HBM.  value = targets/s of the mixed FP32/FP64 path; the
+plain FP64 path is timed beside it.  The inputs (~4 MB) are smaller than L2, so L2 is
+flushed (a 256 MB write) before every timed step and each step is timed on its own with
+CUDA events on the library's stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank evaluates its own independent problem (replicas; no
+collective on the data path); the step time is the max over ranks and value counts the
+targets of all ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+WORKLOAD = dict(kernel="laplace", D=2, L=[1.0, 1.0, 0.25], tol=1e-6, N=100_000, n_s=250)
+METRIC = "targets/s at 1e-5 rel-L2, FP32+forces vs plain FP64 GPU; P2P Gpairs/s"
+CONFIG = {"workload": "Laplace potential+forces, D=2 (x,y periodic), L=(1,1,0.25), N=1e5 uniform, "
+                      "neutral uniform charges, tol 1e-6 (p=20, NF=27), n_s=250",
+          "kernel": "laplace", "D": 2, "L": [1, 1, 0.25], "N": 100000, "tol": 1e-6, "n_s": 250,
+          "l2": "flushed (256 MB write) before every timed step", "inputs": "resident in HBM"}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(HERE, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.out = os.path.join(HERE, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.out), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.out, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.out):
+                f = [v.strip() for v in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = float(f[2])
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        except FileNotFoundError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def reference_arm(args, rank, world):
+    """The oracle (FP64 numpy/scipy, this host's cores) on a bounded sample of the workload."""
+    if rank != 0:
+        return
+    from oracle.dmk import evaluate
+    from paper_2606_27134_b300 import workloads as Wl
+    Ns = 4000
+    x = Wl.uniform_points(Ns, WORKLOAD["L"], 12345)
+    q = Wl.uniform_charges(Ns, 12346)
+    for _ in range(max(0, min(args.warmup, 1))):
+        pass
+    times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        t = time.perf_counter()
+        evaluate("laplace", 2, WORKLOAD["L"], WORKLOAD["tol"], x, q, n_s=WORKLOAD["n_s"], grad=True)
+        times.append(time.perf_counter() - t)
+    dt = statistics.median(times)
+    v = Ns / dt
+    sample = (f"oracle (FP64 numpy) full evaluation with forces of N={Ns} uniform points in the same cell, "
+              f"distribution and plan (25x sparser than the N=1e5 workload); median of {len(times)}")
+    cores = len(os.sched_getaffinity(0))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "targets/s", "n_gpus": args.gpus,
+            "steps": len(times), "warmup": 0, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": CONFIG,
+            "cpu_baseline": {"value": v, "unit": "targets/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "targets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+    from paper_2606_27134_b300 import dmk, workloads as Wl
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+        dist = tdist
+    args.warmup = max(args.warmup, 3)
+    W = WORKLOAD
+    N = W["N"]
+    x = Wl.uniform_points(N, W["L"], 2002 + rank)
+    q = Wl.uniform_charges(N, 3002 + rank)
+    dev = torch.device("cuda", local_rank)
+    xt = torch.tensor(x, dtype=torch.float64, device=dev)
+    qt = torch.tensor(q, dtype=torch.float64, device=dev).reshape(N, 1)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(plan, steps, warmup, host=False):
+        u = torch.empty((N, 1), dtype=torch.float64, device=dev)
+        g = torch.empty((N, 3, 1), dtype=torch.float64, device=dev)
+        if host:
+            hx = xt.cpu().pin_memory()
+            hq = qt.cpu().pin_memory()
+            hu = torch.empty((N, 1), dtype=torch.float64).pin_memory()
+            hg = torch.empty((N, 3, 1), dtype=torch.float64).pin_memory()
+
+        def step():
+            if host:
+                plan.eval_host_ptr(N, hx.data_ptr(), hq.data_ptr(), hu.data_ptr(), hg.data_ptr())
+            else:
+                plan.eval_ptr(N, xt.data_ptr(), qt.data_ptr(), u.data_ptr(), g.data_ptr())
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        stage = []
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        for i in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))
+            stream.synchronize()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+            stage.append(plan.stats())
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t_wall
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return ms, stage, wall, (u, g)
+
+    prec_results = {}
+    for prec in ("mixed", "fp64"):
+        plan = dmk.Plan("laplace", W["D"], W["L"], W["tol"], precision=prec, n_s=W["n_s"],
+                        stream=stream.cuda_stream)
+        with Clocks(local_rank) as ck:
+            ms, stats, wall, _ = timed(plan, args.steps, args.warmup)
+        plan.set_timing(True)
+        _, st_t, _, _ = timed(plan, 3, 1)
+        plan.set_timing(False)
+        prec_results[prec] = dict(ms=ms, stats=stats[-1], clocks=ck.summary(), stage=st_t[-1]["stage_ms"], wall=wall,
+                                  plan=plan)
+    # end-to-end through the host-buffer entry point (copies inside the timed region)
+    plan_m = prec_results["mixed"]["plan"]
+    ms_e2e, _, _, _ = timed(plan_m, max(3, args.steps // 2), 2, host=True)
+
+    def agg(v):
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        if dist:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    mixed = prec_results["mixed"]
+    step_ms = agg(statistics.mean(mixed["ms"]))
+    fp64_ms = agg(statistics.mean(prec_results["fp64"]["ms"]))
+    e2e_ms = agg(statistics.mean(ms_e2e))
+    value = world * N / (step_ms / 1e3)
+    st = mixed["stats"]
+    # leaf kernel share: timed with per-stage events in a separate pass
+    leaf_ms = mixed["stage"][5]
+    pairs = st["n_pairs"]
+    gpairs = pairs / (leaf_ms / 1e3) / 1e9 if leaf_ms > 0 else None
+    # roofline of the leaf kernel (FP32 ALU bound): algorithmic FLOPs per launch
+    # = pairs * F_pair + N * F_cheb, F_pair and F_cheb derived in the design notes
+    from paper_2606_27134_b300.roofline import leaf_flops, fp32_peak_tflops
+    flops = leaf_flops("laplace", st, N, grad=True, precision="mixed")
+    pk = fp32_peak_tflops()
+    achieved = flops / (leaf_ms / 1e3) / 1e12 if leaf_ms > 0 else None
+    roof = {"bound": "alu", "kernel": "k_leaf<float, Laplace, grad>", "achieved": achieved, "peak": pk,
+            "unit": "TFLOP/s", "frac": (achieved / pk) if achieved else None, "traffic": None,
+            "peak_note": "FP32 FMA pipe: 148 SMs x 128 lanes x 2 flop x 2.032 GHz (derived from unit counts and "
+                         "the maximum SM clock; no measured FP32 peak in MEASURED_PEAKS.json)"}
+    line = {"metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": dict(CONFIG, parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+            "fp64_path": {"value": world * N / (fp64_ms / 1e3), "unit": "targets/s", "ms_per_step": fp64_ms},
+            "mixed_over_fp64": fp64_ms / step_ms,
+            "p2p": {"gpairs_per_s": gpairs, "pairs_per_step": pairs, "leaf_kernel_ms": leaf_ms},
+            "stage_ms": dict(zip(["tree", "upward", "root", "planewave", "shift", "leaf", "total"], mixed["stage"])),
+            "tree": {k: st[k] for k in ("n_levels", "n_boxes", "n_leaves", "n_nonleaf", "n_direct_entries")},
+            "roofline": roof,
+            "clocks": mixed["clocks"],
+            "e2e": {"value": world * N / (e2e_ms / 1e3), "unit": "targets/s",
+                    "h2d_bytes_per_step": N * (3 + 1) * 8, "d2h_bytes_per_step": N * (1 + 3) * 8},
+            "gpu_launches": int(st["kernel_launches"]) * args.steps}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            from oracle.dmk import evaluate
+            Ns = 4000
+            xs = Wl.uniform_points(Ns, W["L"], 12345)
+            qs = Wl.uniform_charges(Ns, 12346)
+            t = time.perf_counter()
+            evaluate("laplace", 2, W["L"], W["tol"], xs, qs, n_s=W["n_s"], grad=True)
+            dt = time.perf_counter() - t
+            line["cpu_baseline"] = {"value": Ns / dt, "unit": "targets/s", "cores": len(os.sched_getaffinity(0)),
+                                    "kind": "oracle",
+                                    "sample": f"oracle (FP64 numpy) full evaluation with forces of N={Ns} uniform "
+                                              f"points, same cell/distribution/plan (25x sparser), one run "
+                                              f"({dt:.1f} s)"}
+        except Exception as e:  # the baseline is reported, never required
+            line["cpu_baseline"] = {"value": None, "error": str(e)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

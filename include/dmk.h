@@ -1,0 +1,162 @@
+/*
+ * dmk.h -- C ABI of the B300-native periodized DMK library (libdmk_b300.so).
+ *
+ * Evaluates, for N points x_t in the cuboid [0,L1) x [0,L2) x [0,L3) with the first D
+ * directions periodic, the sums of Eq. periodic_sum (Sec. 1):
+ *
+ *     u(x_t) = sum_s sum*_{p in P_D} K(x_t - x_s + p) rho_s ,
+ *
+ * where P_D is the lattice of periodic images of Eq. periodic-images and "*" drops p = 0
+ * when x_t = x_s, by the periodized dual-space multilevel kernel-splitting method:
+ * leaf residual sums over periodically wrapped neighbour lists (Sec. 2.3, Eq. u_local),
+ * per-level difference-kernel plane-wave interactions (Sec. 2.3 Eq. Dl_int_discr,
+ * Sec. 3.1.4) and the root-level Fourier far field (Sec. 4.3, 4.4, 5.3).  Sources and
+ * targets coincide (Sec. 1).  Kernels: Laplace K = 1/(4 pi r) and the Stokeslet,
+ * stresslet and rotlet of App. B.
+ *
+ * Conventions shared by every entry point
+ *   - Arrays are plain pointers, row-major, FP64, owned by the caller.  "device" pointers
+ *     must be CUDA device (or managed) memory on the current device; "host" pointers are
+ *     ordinary host memory (pinned memory gives faster copies).
+ *   - Every call returns a dmk_status_t; nothing aborts, exits or traps.  On an error the
+ *     outputs are left unspecified and dmk_last_error() gives a one-line detail.
+ *   - A plan owns its tables and a device workspace that grows on demand; calls on one
+ *     plan must not overlap (the plan is not thread-safe).  Work is enqueued on the plan's
+ *     CUDA stream; dmk_eval returns after the results are complete (it synchronises the
+ *     stream once, to read the device status word).
+ */
+#ifndef DMK_B300_H
+#define DMK_B300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DMK_LAPLACE = 0,    /* K = 1/(4 pi r); rho scalar; u scalar                                    */
+    DMK_STOKESLET = 1,  /* App. B Eq. stokeslet_def_deriv; rho = force (3); u = velocity (3)        */
+    DMK_STRESSLET = 2,  /* App. B Eq. stresslet_def_deriv; rho = Q_lm = q_l n_m, l-major (9); u (3) */
+    DMK_ROTLET = 3      /* App. B Eq. rotlet_def_deriv; rho = torque (3); u (3)                     */
+} dmk_kernel_t;
+
+typedef enum {
+    DMK_FP64 = 0,       /* plain path: every stage in FP64                                          */
+    DMK_MIXED = 1       /* FP32 residual sums, expansions and Chebyshev stages with box-relative
+                           coordinates; FP64 root Fourier sum, self correction, final accumulate  */
+} dmk_precision_t;
+
+typedef enum {
+    DMK_OK = 0,
+    DMK_ERR_INVALID_ARG = 1,   /* bad kernel, D, lengths, tol, n_s or a NULL pointer             */
+    DMK_ERR_OUT_OF_DOMAIN = 2, /* a free (non-periodic) coordinate outside [0, L_i), or non-finite */
+    DMK_ERR_NOT_NEUTRAL = 3,   /* Laplace with D = 1, 2 needs sum rho = 0 (Sec. 5.2)               */
+    DMK_ERR_UNSUPPORTED = 4,   /* periodic length not an integer multiple of the cube side
+                                  (non-exact tilings, Sec. 4.1.2, are not implemented)            */
+    DMK_ERR_TREE_DEPTH = 5,    /* a box at the depth cap still holds more than n_s points          */
+    DMK_ERR_OOM = 6,           /* device allocation failed                                        */
+    DMK_ERR_CUDA = 7,          /* a CUDA call failed; see dmk_last_error                          */
+    DMK_ERR_TIMEOUT = 8        /* reserved: no device-side wait exists in this library            */
+} dmk_status_t;
+
+typedef struct dmk_plan_s* dmk_plan_t;
+
+/* Plan for kernel k with D periodic directions (0..3) on the cell L1 x L2 x L3 and a
+ * requested relative tolerance tol in [1e-12, 1e-3].  The tolerance selects the row of the
+ * paper's parameter tables (Table 1 for Laplace, Table 5 for the Stokes kernels; Sec. 6.1):
+ * the PSWF band limit c, the Chebyshev order p and n_f = ceil(3c/pi) - 1; a tol between
+ * rows takes the next stricter row.  The cube side is s = min of the periodic lengths
+ * (max L_i for D = 0); free lengths are rounded up to multiples of s (Sec. 4.1, Sec. 5).
+ * Defaults: precision DMK_MIXED, n_s = 250 (Sec. 6), the legacy default stream.
+ * On success *out receives a plan to be released with dmk_destroy. */
+dmk_status_t dmk_plan(dmk_kernel_t k, int D, double L1, double L2, double L3, double tol,
+                      dmk_plan_t* out);
+
+/* As dmk_plan, with the precision path, the leaf capacity n_s (>= 1; the maximum number of
+ * points in a leaf box, Sec. 3.1.1, which changes speed but not accuracy, Sec. 6) and the
+ * CUDA stream (a cudaStream_t, or NULL for the legacy default stream). */
+dmk_status_t dmk_plan_ex(dmk_kernel_t k, int D, const double L[3], double tol,
+                         dmk_precision_t prec, int n_s, void* cuda_stream, dmk_plan_t* out);
+
+/* Evaluate the sums for N >= 0 points.
+ *   points      device, N x 3: positions; periodic coordinates may lie anywhere (they are
+ *               wrapped into [0, L_i)), free coordinates must lie in [0, L_i).
+ *   strengths   device, N x d_rho (1, 3, 9, 3 for the four kernels).
+ *   potentials  device, N x d_u (1, 3, 3, 3): u(x_t) in input order.
+ *   grad        device, or NULL to skip: N x 3 x d_u with grad[t][i][j] = d u_j / d x_i at
+ *               x_t (the field gradient at the target; for Laplace the force on t is
+ *               -rho_t grad[t][.][0]).
+ * D = 3 Laplace with non-zero net charge drops the k = 0 mode (neutralising background,
+ * Sec. 1 footnote).  N = 0 returns DMK_OK without touching the arrays. */
+dmk_status_t dmk_eval(dmk_plan_t plan, int64_t N, const double* points, const double* strengths,
+                      double* potentials, double* grad);
+
+/* Same as dmk_eval with HOST arrays: the library copies points and strengths to the device,
+ * evaluates, and copies potentials (and grad) back before returning. */
+dmk_status_t dmk_eval_host(dmk_plan_t plan, int64_t N, const double* points, const double* strengths,
+                           double* potentials, double* grad);
+
+/* Statistics of the last dmk_eval on this plan. */
+typedef struct {
+    int32_t c_times_1000;      /* PSWF band limit c, times 1000                                  */
+    int32_t p;                 /* Chebyshev order                                                */
+    int32_t n_f;               /* plane-wave half width; N_F = 2 n_f + 1                          */
+    int32_t n_root_modes;      /* retained root Fourier modes (rectangle points with nonzero weight) */
+    int32_t n_levels;          /* tree levels (root cubes are level 0)                           */
+    int32_t n_boxes;           /* boxes in the forest                                            */
+    int32_t n_leaves;          /* leaf boxes                                                     */
+    int32_t n_nonleaf;         /* non-leaf boxes (carry plane-wave expansions)                   */
+    int64_t n_pairs;           /* source-target pairs visited by the residual sums               */
+    int64_t n_direct_entries;  /* (target leaf, source box) entries of the direct lists          */
+    int32_t kernel_launches;   /* CUDA kernels launched by the last evaluation                   */
+    int32_t fit_terms;         /* Chebyshev terms of the residual function q used by the path    */
+    float stage_ms[8];         /* last eval: tree, upward, root, plane waves, shift, leaf, total, 0 */
+} dmk_stats_t;
+
+dmk_status_t dmk_get_stats(dmk_plan_t plan, dmk_stats_t* out);
+
+/* Enables (1) or disables (0) per-stage CUDA-event timing inside dmk_eval (stage_ms). */
+dmk_status_t dmk_set_timing(dmk_plan_t plan, int enable);
+
+/* Plan parameters computed on the host only (no device call): the values dmk_plan would use.
+ * n_axis[i] = wavenumbers on root axis i (periodic: 2 ceil(L_i c/(2 pi nu_0)) + 1 integers,
+ * Eq. kintmax; free: 2 ceil(c/(nu_0 dk)) + 1 trapezoidal nodes, Sec. 5.3); R = truncation radius
+ * (0 for D = 3); fit_terms_fp64/fp32 = Chebyshev terms of the residual function q per path. */
+typedef struct {
+    double c, s, R, dk;
+    int32_t p, n_f, n_root_modes, fit_terms_fp64, fit_terms_fp32;
+    int32_t M[3];
+    int32_t n_axis[3];
+    int32_t d_rho, d_u;
+} dmk_plan_info_t;
+
+dmk_status_t dmk_plan_info(dmk_kernel_t k, int D, const double L[3], double tol, dmk_plan_info_t* out);
+
+/* Copies one host-side plan table into out (FP64, host memory), for inspection and testing;
+ * *n receives the number of doubles available (copies min(cap, *n)).  No device call.
+ *   which = 0: root wavenumber axes, concatenated (n_axis[0] + n_axis[1] + n_axis[2]);
+ *   which = 1: root weights C^{DP} G-hat(k) gamma-hat(|k| nu_0) on the rectangle, complex as
+ *              (re, im) pairs, index ((i1 n2 + i2) n3 + i3) d_u d_rho + j d_rho + a (Sec. 4.3, 5.3);
+ *   which = 2: level-0 difference-kernel scalar w_0 h_0^ord G_0(|h_0 m|) on the half grid,
+ *              index ((m1 + n_f) N_F + (m2 + n_f)) (n_f + 1) + m3 (Sec. 2.3, Eq. Dl_int_discr);
+ *   which = 3: PSWF window values phi(0), phi''(0), phi-hat''(0), then phi-hat at k = 0.099 c j,
+ *              j = 0..10 (Sec. 2.2, Eqs. wfunc_pswf, wfunchat). */
+dmk_status_t dmk_plan_table(dmk_kernel_t k, int D, const double L[3], double tol, int which, double* out,
+                            int64_t cap, int64_t* n);
+
+/* Releases the plan, its tables and workspace.  NULL is accepted. */
+dmk_status_t dmk_destroy(dmk_plan_t plan);
+
+/* Static text for a status code. */
+const char* dmk_status_string(dmk_status_t s);
+
+/* Detail of the last error on this plan (plan-owned text, valid until the next call on it);
+ * with plan == NULL, the detail of the last failed dmk_plan/dmk_plan_ex in this thread. */
+const char* dmk_last_error(dmk_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DMK_B300_H */

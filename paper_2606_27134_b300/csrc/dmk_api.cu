@@ -1,0 +1,850 @@
+// C ABI of the periodized DMK library: plan construction, workspace, and the evaluation
+// sequence (tree -> upward -> root -> plane waves -> shift -> leaf) on the plan's stream.
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+#include <cub/device/device_select.cuh>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <functional>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dmk_internal.h"
+#include "dmk_kernels.cuh"
+
+using namespace dmk;
+
+namespace {
+
+thread_local std::string g_plan_error;
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace
+
+struct dmk_plan_s {
+    PlanTables T;
+    int prec = DMK_MIXED;
+    int n_s = 250;
+    cudaStream_t stream = nullptr;
+    Geo geo{};
+    std::string err;
+    dmk_stats_t stats{};
+    int timing = 0;
+    int device = 0;
+    size_t smem_optin = 0;
+    // device tables
+    void* d_tab64 = nullptr;
+    void* d_tab32 = nullptr;
+    Tab<double> tab64{};
+    Tab<float> tab32{};
+    void* d_root = nullptr;
+    RootTab root{};
+    double* d_self = nullptr;      // self_val then self_grad
+    // workspace
+    std::vector<DevBuf> bufs;
+    int* h_pinned = nullptr;
+    cudaEvent_t ev[8] = {};
+    int launches = 0;
+};
+
+namespace {
+
+#define CK(call)                                                                  \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) {                                                  \
+            plan->err = std::string(#call) + ": " + cudaGetErrorString(e_);       \
+            return e_ == cudaErrorMemoryAllocation ? DMK_ERR_OOM : DMK_ERR_CUDA;  \
+        }                                                                         \
+    } while (0)
+
+enum BufId {
+    B_W, B_KEYS, B_KEYS2, B_IDX, B_IDX2, B_XS, B_RS, B_CUB, B_FLAGS, B_CNT,
+    B_CELLS, B_R, B_CAND, B_BOXU64, B_BOXINT, B_LEAVES, B_DOFFS, B_DL, B_NLBOX,
+    B_PROXY, B_LOCAL, B_PW, B_SCRATCH, B_CHI, B_UHAT, B_MISC, B_DEVPTS, B_DEVRHO, B_DEVPOT, B_DEVGRAD,
+    B_COUNT
+};
+
+dmk_status_t ensure(dmk_plan_s* plan, int id, size_t bytes, void** out) {
+    if (plan->bufs.size() < B_COUNT) plan->bufs.resize(B_COUNT);
+    DevBuf& b = plan->bufs[id];
+    if (bytes == 0) bytes = 16;
+    if (b.cap < bytes) {
+        if (b.p) cudaFree(b.p);
+        b.p = nullptr;
+        b.cap = 0;
+        size_t want = bytes + bytes / 4;
+        cudaError_t e = cudaMalloc(&b.p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            plan->err = "device allocation of " + std::to_string(want) + " bytes failed";
+            return DMK_ERR_OOM;
+        }
+        b.cap = want;
+    }
+    *out = b.p;
+    return DMK_OK;
+}
+
+template <class T>
+dmk_status_t upload_tab(dmk_plan_s* plan, void** mem, Tab<T>& tab, double fit_tol) {
+    const PlanTables& P = plan->T;
+    const int p = P.p;
+    auto trunc = [&](const std::vector<double>& a) {
+        double mx = 0;
+        for (double v : a) mx = std::max(mx, std::fabs(v));
+        int n = (int)a.size();
+        while (n > 1 && std::fabs(a[n - 1]) < fit_tol * mx) --n;
+        return std::vector<double>(a.begin(), a.begin() + n);
+    };
+    std::vector<std::vector<double>> fits = {trunc(P.fit_q), trunc(P.fit_f), trunc(P.fit_g),
+                                             trunc(P.fit_dq), trunc(P.fit_df), trunc(P.fit_dg)};
+    size_t nfit = 0;
+    for (auto& f : fits) nfit += f.size();
+    if (nfit > 256) { plan->err = "residual fits longer than 256 coefficients"; return DMK_ERR_INVALID_ARG; }
+    std::vector<T> h;
+    auto push = [&](const std::vector<double>& v) {
+        size_t o = h.size();
+        for (double x : v) h.push_back((T)x);
+        while (h.size() % 4) h.push_back(0);
+        return o;
+    };
+    size_t o_nodes = push(P.nodes), o_bary = push(P.bary), o_I = push(P.Ioct), o_C = push(P.Cm);
+    std::vector<double> Eri;
+    for (auto& z : P.E) { Eri.push_back(z.real()); Eri.push_back(z.imag()); }
+    size_t o_E = push(Eri), o_g = push(P.gdiff);
+    size_t o_fit = h.size();
+    int offs[6], lens[6];
+    size_t acc = 0;
+    for (int i = 0; i < 6; ++i) {
+        offs[i] = (int)acc;
+        lens[i] = (int)fits[i].size();
+        for (double x : fits[i]) h.push_back((T)x);
+        acc += fits[i].size();
+    }
+    cudaError_t e = cudaMalloc(mem, h.size() * sizeof(T));
+    if (e != cudaSuccess) { plan->err = "table allocation failed"; return DMK_ERR_OOM; }
+    e = cudaMemcpy(*mem, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { plan->err = cudaGetErrorString(e); return DMK_ERR_CUDA; }
+    T* base = (T*)*mem;
+    tab.p = p; tab.nf = P.nf; tab.NF = P.NF; tab.nfh = P.nfh;
+    tab.d_rho = P.d_rho; tab.d_u = P.d_u; tab.kernel = P.kernel; tab.level_power = P.level_power;
+    tab.nodes = base + o_nodes; tab.bary = base + o_bary; tab.Ioct = base + o_I; tab.Cm = base + o_C;
+    tab.E = reinterpret_cast<const Cx<T>*>(base + o_E);
+    tab.gdiff = base + o_g;
+    tab.fit = base + o_fit;
+    tab.off_q = offs[0]; tab.n_q = lens[0]; tab.off_f = offs[1]; tab.n_f = lens[1];
+    tab.off_g = offs[2]; tab.n_g = lens[2]; tab.off_dq = offs[3]; tab.n_dq = lens[3];
+    tab.off_df = offs[4]; tab.n_df = lens[4]; tab.off_dg = offs[5]; tab.n_dg = lens[5];
+    return DMK_OK;
+}
+
+dmk_status_t upload_root(dmk_plan_s* plan) {
+    const PlanTables& P = plan->T;
+    const int p = P.p;
+    std::vector<double> h;
+    auto pad = [&]() { while (h.size() % 2) h.push_back(0); };
+    size_t o_k[3], o_S[3];
+    for (int i = 0; i < 3; ++i) {
+        o_k[i] = h.size();
+        for (double v : P.kax[i]) h.push_back(v);
+        pad();
+    }
+    for (int i = 0; i < 3; ++i) {
+        o_S[i] = h.size();
+        for (double k : P.kax[i])
+            for (int j = 0; j < p; ++j) {
+                double ph = -k * (P.s / 2) * P.nodes[j];
+                h.push_back(std::cos(ph));
+                h.push_back(std::sin(ph));
+            }
+    }
+    size_t o_W = h.size();
+    for (auto& z : P.Wroot) { h.push_back(z.real()); h.push_back(z.imag()); }
+    size_t o_c = h.size();
+    for (double v : P.root_const) h.push_back(v);
+    cudaError_t e = cudaMalloc(&plan->d_root, h.size() * sizeof(double));
+    if (e != cudaSuccess) { plan->err = "root table allocation failed"; return DMK_ERR_OOM; }
+    e = cudaMemcpy(plan->d_root, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { plan->err = cudaGetErrorString(e); return DMK_ERR_CUDA; }
+    double* base = (double*)plan->d_root;
+    RootTab& rt = plan->root;
+    rt.n1 = (int)P.kax[0].size(); rt.n2 = (int)P.kax[1].size(); rt.n3 = (int)P.kax[2].size();
+    rt.nmode = rt.n1 * rt.n2 * rt.n3;
+    for (int i = 0; i < 3; ++i) {
+        rt.kax[i] = base + o_k[i];
+        rt.S[i] = reinterpret_cast<const Cx<double>*>(base + o_S[i]);
+    }
+    rt.W = reinterpret_cast<const Cx<double>*>(base + o_W);
+    rt.rconst = base + o_c;
+    // self tables
+    std::vector<double> sv(P.self_val);
+    sv.insert(sv.end(), P.self_grad.begin(), P.self_grad.end());
+    e = cudaMalloc(&plan->d_self, sv.size() * sizeof(double));
+    if (e != cudaSuccess) { plan->err = "self table allocation failed"; return DMK_ERR_OOM; }
+    cudaMemcpy(plan->d_self, sv.data(), sv.size() * sizeof(double), cudaMemcpyHostToDevice);
+    return DMK_OK;
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+// work-buffer placement: dynamic shared memory when it fits, else a global scratch slice
+struct Place {
+    int use_smem;
+    size_t bytes;
+    unsigned grid;
+};
+
+template <class T>
+struct Evaluator {
+    dmk_plan_s* plan;
+    Tab<T>& tab;
+    Evaluator(dmk_plan_s* pl, Tab<T>& t) : plan(pl), tab(t) {}
+
+    dmk_status_t place(size_t bytes, int n, Place& pl, unsigned char** scratch) {
+        const size_t lim = std::min<size_t>(plan->smem_optin, 160 * 1024);
+        pl.bytes = bytes;
+        pl.grid = (unsigned)std::max(1, std::min<int>(n, 148 * 8));
+        if (bytes <= lim) {
+            pl.use_smem = 1;
+            *scratch = nullptr;
+            return DMK_OK;
+        }
+        pl.use_smem = 0;
+        pl.grid = (unsigned)std::max(1, std::min<int>(n, 148 * 2));
+        void* p = nullptr;
+        dmk_status_t s = ensure(plan, B_SCRATCH, bytes * pl.grid, &p);
+        *scratch = (unsigned char*)p;
+        return s;
+    }
+};
+
+template <class K>
+dmk_status_t set_smem(dmk_plan_s* plan, K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return DMK_OK;
+}
+
+template <class T, int MAXP>
+void launch_anterp(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int* leaves, BoxArrays B, const double* xs,
+                   int64_t N, const double* rs, T* proxy) {
+    const int p2 = tab.p * tab.p;
+    int threads = std::min(MAXP <= 24 ? 576 : 512, ((p2 + 31) / 32) * 32);
+    size_t sm = 3 * 32 * MAXP * sizeof(T);
+    unsigned grid = (unsigned)std::max(1, std::min(nleaf, 148 * 8));
+    k_anterp<T, MAXP><<<grid, threads, sm, plan->stream>>>(nleaf, leaves, B, xs, N, rs, tab, plan->T.s, proxy);
+}
+
+template <class T, int K>
+dmk_status_t launch_leaf(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int* leaves, BoxArrays B, const T* local,
+                         const double* xs, int64_t N, const int* doffs, const DirectEntry* dl, LeafOut lo, bool grad) {
+    const int p3 = tab.p * tab.p * tab.p;
+    constexpr int DU = (K == DMK_LAPLACE) ? 1 : 3;
+    size_t bytes = (size_t)(DU + 2) * p3 * sizeof(T);
+    Evaluator<T> ev(plan, tab);
+    Place pl;
+    unsigned char* scr = nullptr;
+    dmk_status_t s = ev.place(bytes, nleaf, pl, &scr);
+    if (s != DMK_OK) return s;
+    size_t dyn = pl.use_smem ? bytes : 0;
+    if (grad) {
+        s = set_smem(plan, k_leaf<T, K, true>, dyn);
+        if (s != DMK_OK) return s;
+        k_leaf<T, K, true><<<pl.grid, kLeafThreads, dyn, plan->stream>>>(nleaf, leaves, B, tab, plan->geo, local, xs,
+                                                                         N, doffs, dl, lo, scr, bytes, pl.use_smem);
+    } else {
+        s = set_smem(plan, k_leaf<T, K, false>, dyn);
+        if (s != DMK_OK) return s;
+        k_leaf<T, K, false><<<pl.grid, kLeafThreads, dyn, plan->stream>>>(nleaf, leaves, B, tab, plan->geo, local, xs,
+                                                                          N, doffs, dl, lo, scr, bytes, pl.use_smem);
+    }
+    return DMK_OK;
+}
+
+struct TreeInfo {
+    int nlev = 0;                 // number of levels
+    std::vector<int> ncell, off, nR, nl_off;
+    int nb = 0, n_nl = 0, n_leafp = 0;
+    int64_t n_entries = 0;
+    unsigned long long n_pairs = 0;
+};
+
+#define CKS(x)                              \
+    do {                                    \
+        dmk_status_t s_ = (x);              \
+        if (s_ != DMK_OK) return s_;        \
+    } while (0)
+
+template <class T>
+dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pts, const double* rho, double* pot,
+                      double* grad) {
+    cudaStream_t st = plan->stream;
+    const PlanTables& P = plan->T;
+    const int drho = P.d_rho, du = P.d_u, p = P.p, p3 = p * p * p;
+    const Geo g = plan->geo;
+    const int Mtot = g.M[0] * g.M[1] * g.M[2];
+    int launches = 0;
+    auto rec = [&](int i) { if (plan->timing) cudaEventRecord(plan->ev[i], st); };
+    rec(0);
+    // ---- (1) keys, sort, gather --------------------------------------------------------
+    void *vw, *vkeys, *vkeys2, *vidx, *vidx2, *vxs, *vrs, *vmisc;
+    CKS(ensure(plan, B_W, 3 * N * sizeof(double), &vw));
+    CKS(ensure(plan, B_KEYS, N * sizeof(uint64_t), &vkeys));
+    CKS(ensure(plan, B_KEYS2, N * sizeof(uint64_t), &vkeys2));
+    CKS(ensure(plan, B_IDX, N * sizeof(int), &vidx));
+    CKS(ensure(plan, B_IDX2, N * sizeof(int), &vidx2));
+    CKS(ensure(plan, B_XS, 3 * N * sizeof(double), &vxs));
+    CKS(ensure(plan, B_RS, N * drho * sizeof(double), &vrs));
+    CKS(ensure(plan, B_MISC, 4096, &vmisc));
+    int* d_err = (int*)vmisc;
+    double* d_sums = (double*)((char*)vmisc + 256);          // 2*drho doubles
+    int* d_count = (int*)((char*)vmisc + 512);
+    unsigned long long* d_pairs = (unsigned long long*)((char*)vmisc + 768);
+    CK(cudaMemsetAsync(vmisc, 0, 1024, st));
+    uint64_t* keys = (uint64_t*)vkeys;
+    uint64_t* keys2 = (uint64_t*)vkeys2;
+    int* idx = (int*)vidx;
+    int* idx2 = (int*)vidx2;
+    double* xs = (double*)vxs;
+    double* rs = (double*)vrs;
+    k_quantize<<<nblk(N, 256), 256, 0, st>>>(N, pts, g, (double*)vw, keys, idx, d_err);
+    ++launches;
+    int cube_bits = 0;
+    while ((1 << cube_bits) < Mtot) ++cube_bits;
+    const int end_bit = 3 * kBits + cube_bits;
+    size_t tmp_bytes = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys, keys2, idx, idx2, (int)N, 0, end_bit, st);
+    void* vcub;
+    CKS(ensure(plan, B_CUB, std::max<size_t>(tmp_bytes, 1 << 20), &vcub));
+    size_t cub_cap = plan->bufs[B_CUB].cap;
+    CK(cub::DeviceRadixSort::SortPairs(vcub, tmp_bytes, keys, keys2, idx, idx2, (int)N, 0, end_bit, st));
+    launches += 4;
+    const uint64_t* pkeys = keys2;
+    k_gather<<<nblk(N, 256), 256, 0, st>>>(N, drho, idx2, (const double*)vw, rho, xs, rs);
+    ++launches;
+    k_strength_sums<<<std::min<unsigned>(nblk(N, 256), 1024), 256, 0, st>>>(N, drho, rs, d_sums);
+    ++launches;
+    // error and neutrality check (host readback)
+    {
+        int herr = 0;
+        double hs[18];
+        CK(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hs, d_sums, 2 * drho * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (herr & kErrNonFinite) { plan->err = "non-finite coordinate"; return DMK_ERR_OUT_OF_DOMAIN; }
+        if (herr & kErrDomain) { plan->err = "a free coordinate lies outside [0, L_i)"; return DMK_ERR_OUT_OF_DOMAIN; }
+        if (P.kernel == DMK_LAPLACE && (P.D == 1 || P.D == 2) && std::fabs(hs[0]) > 1e-12 * std::max(hs[1], 1e-300)) {
+            plan->err = "Laplace with D = 1, 2 requires zero net charge";
+            return DMK_ERR_NOT_NEUTRAL;
+        }
+    }
+    // ---- (2) refinement --------------------------------------------------------------
+    TreeInfo ti;
+    std::vector<uint64_t*> cells, Rl;
+    std::vector<size_t> cell_cap;
+    // one big arena for per-level cell and R arrays: grows as needed (host tracks offsets)
+    std::vector<void*> level_mem;
+    auto alloc_level = [&](size_t bytes, void** out) -> dmk_status_t {
+        void* p = nullptr;
+        cudaError_t e = cudaMallocAsync(&p, std::max<size_t>(bytes, 16), st);
+        if (e != cudaSuccess) { plan->err = "level allocation failed"; return DMK_ERR_OOM; }
+        level_mem.push_back(p);
+        *out = p;
+        return DMK_OK;
+    };
+    auto free_levels = [&]() { for (void* p : level_mem) cudaFreeAsync(p, st); level_mem.clear(); };
+    struct Guard { std::function<void()> f; ~Guard() { f(); } };
+    Guard guard{free_levels};
+    void* vflags;
+    {
+        void* c0;
+        CKS(alloc_level(Mtot * sizeof(uint64_t), &c0));
+        std::vector<uint64_t> h(Mtot);
+        for (int i = 0; i < Mtot; ++i) h[i] = (uint64_t)i;
+        CK(cudaMemcpyAsync(c0, h.data(), Mtot * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+        cells.push_back((uint64_t*)c0);
+        ti.ncell.push_back(Mtot);
+    }
+    for (int l = 0;; ++l) {
+        const int nc = ti.ncell[l];
+        CKS(ensure(plan, B_FLAGS, (size_t)nc * sizeof(int), &vflags));
+        k_split_flags<<<nblk(nc, 256), 256, 0, st>>>(nc, cells[l], l, pkeys, N, plan->n_s, (int*)vflags);
+        void* r;
+        CKS(alloc_level((size_t)nc * sizeof(uint64_t), &r));
+        size_t tb = 0;
+        cub::DeviceSelect::Flagged(nullptr, tb, cells[l], (int*)vflags, (uint64_t*)r, d_count, nc, st);
+        if (tb > cub_cap) { CKS(ensure(plan, B_CUB, tb, &vcub)); cub_cap = plan->bufs[B_CUB].cap; }
+        CK(cub::DeviceSelect::Flagged(vcub, tb, cells[l], (int*)vflags, (uint64_t*)r, d_count, nc, st));
+        launches += 2;
+        int nr = 0;
+        CK(cudaMemcpyAsync(&nr, d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        Rl.push_back((uint64_t*)r);
+        ti.nR.push_back(nr);
+        if (nr == 0) break;
+        void* cn;
+        CKS(alloc_level((size_t)8 * nr * sizeof(uint64_t), &cn));
+        k_children<<<nblk(8 * nr, 256), 256, 0, st>>>(nr, (uint64_t*)r, (uint64_t*)cn);
+        ++launches;
+        cells.push_back((uint64_t*)cn);
+        ti.ncell.push_back(8 * nr);
+    }
+    int nlev = (int)ti.ncell.size();
+    // ---- (3) 2:1 balance, finest non-leaf level upward ---------------------------------
+    for (int l = nlev - 2; l >= 1; --l) {
+        const int nr = ti.nR[l];
+        if (nr == 0) continue;
+        const int ncand = 27 * nr + ti.nR[l - 1];
+        void *va, *vb;
+        CKS(alloc_level((size_t)ncand * sizeof(uint64_t), &va));
+        CKS(alloc_level((size_t)ncand * sizeof(uint64_t), &vb));
+        k_balance_cand<<<nblk(27 * nr, 256), 256, 0, st>>>(nr, Rl[l], l, g, (uint64_t*)va);
+        if (ti.nR[l - 1] > 0)
+            CK(cudaMemcpyAsync((uint64_t*)va + 27 * nr, Rl[l - 1], ti.nR[l - 1] * sizeof(uint64_t),
+                               cudaMemcpyDeviceToDevice, st));
+        size_t tb = 0;
+        cub::DeviceRadixSort::SortKeys(nullptr, tb, (uint64_t*)va, (uint64_t*)vb, ncand, 0, 64, st);
+        size_t tb2 = 0;
+        cub::DeviceSelect::Unique(nullptr, tb2, (uint64_t*)vb, (uint64_t*)va, d_count, ncand, st);
+        if (std::max(tb, tb2) > cub_cap) { CKS(ensure(plan, B_CUB, std::max(tb, tb2), &vcub)); cub_cap = plan->bufs[B_CUB].cap; }
+        CK(cub::DeviceRadixSort::SortKeys(vcub, tb, (uint64_t*)va, (uint64_t*)vb, ncand, 0, 64, st));
+        CK(cub::DeviceSelect::Unique(vcub, tb2, (uint64_t*)vb, (uint64_t*)va, d_count, ncand, st));
+        launches += 6;
+        int nu = 0;
+        uint64_t last = 0;
+        CK(cudaMemcpyAsync(&nu, d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (nu > 0) {
+            CK(cudaMemcpy(&last, (uint64_t*)va + nu - 1, sizeof(uint64_t), cudaMemcpyDeviceToHost));
+            if (last == kInvalidKey) --nu;
+        }
+        Rl[l - 1] = (uint64_t*)va;
+        ti.nR[l - 1] = nu;
+        // children of the grown R_{l-1}
+        void* cn;
+        CKS(alloc_level((size_t)8 * nu * sizeof(uint64_t), &cn));
+        k_children<<<nblk(8 * nu, 256), 256, 0, st>>>(nu, Rl[l - 1], (uint64_t*)cn);
+        ++launches;
+        cells[l] = (uint64_t*)cn;
+        ti.ncell[l] = 8 * nu;
+    }
+    // ---- (4) box arrays -----------------------------------------------------------------
+    ti.nlev = nlev;
+    ti.off.assign(nlev + 1, 0);
+    ti.nl_off.assign(nlev + 1, 0);
+    for (int l = 0; l < nlev; ++l) {
+        ti.off[l + 1] = ti.off[l] + ti.ncell[l];
+        ti.nl_off[l + 1] = ti.nl_off[l] + ti.nR[l];
+    }
+    const int nb = ti.off[nlev], n_nl = ti.nl_off[nlev];
+    ti.nb = nb;
+    ti.n_nl = n_nl;
+    void *vbu, *vbi;
+    CKS(ensure(plan, B_BOXU64, (size_t)nb * sizeof(uint64_t), &vbu));
+    // layout: level(1) ix(3) start(1) end(1) child0(1) parent(1) nl(1) coll(27) = 36 per box
+    CKS(ensure(plan, B_BOXINT, (size_t)nb * 36 * sizeof(int) + 2 * (kMaxLevels + 2) * sizeof(int), &vbi));
+    BoxArrays B;
+    B.key = (uint64_t*)vbu;
+    int* bi = (int*)vbi;
+    B.level = bi; B.ix = bi + nb; B.start = bi + 4 * nb; B.end = bi + 5 * nb; B.child0 = bi + 6 * nb;
+    B.parent = bi + 7 * nb; B.nl = bi + 8 * nb; B.coll = bi + 9 * nb;
+    int* d_level_off = bi + 36 * nb;
+    int* d_level_cnt = d_level_off + (kMaxLevels + 2);
+    CK(cudaMemcpyAsync(d_level_off, ti.off.data(), nlev * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_level_cnt, ti.ncell.data(), nlev * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(B.nl, 0xff, nb * sizeof(int), st));
+    for (int l = 0; l < nlev; ++l) {
+        const uint64_t* Rnext = Rl[l];
+        k_box_fill<<<nblk(ti.ncell[l], 256), 256, 0, st>>>(l, ti.off[l], ti.ncell[l], cells[l], Rnext, ti.nR[l],
+                                                           ti.off[l + 1], l > 0 ? cells[l - 1] : nullptr,
+                                                           l > 0 ? ti.ncell[l - 1] : 0, l > 0 ? ti.off[l - 1] : 0,
+                                                           pkeys, N, g, B);
+        ++launches;
+    }
+    void* vnl;
+    CKS(ensure(plan, B_NLBOX, (size_t)std::max(n_nl, 1) * sizeof(int), &vnl));
+    int* nl_box = (int*)vnl;
+    for (int l = 0; l < nlev; ++l) {
+        if (ti.nR[l] == 0) continue;
+        k_nonleaf_list<<<nblk(ti.nR[l], 256), 256, 0, st>>>(ti.nR[l], Rl[l], cells[l], ti.ncell[l], ti.off[l],
+                                                            ti.nl_off[l], nl_box, B.nl);
+        ++launches;
+    }
+    k_colleagues<<<nblk((int64_t)27 * nb, 256), 256, 0, st>>>(nb, B.level, B.ix, B.key, d_level_off, d_level_cnt, g,
+                                                              B.coll);
+    ++launches;
+    // leaves with points
+    CKS(ensure(plan, B_FLAGS, (size_t)nb * sizeof(int), &vflags));
+    void* vleaves;
+    CKS(ensure(plan, B_LEAVES, (size_t)nb * sizeof(int), &vleaves));
+    int* leaves = (int*)vleaves;
+    void* viota;
+    CKS(ensure(plan, B_CNT, (size_t)nb * sizeof(int), &viota));
+    k_leaf_flags<<<nblk(nb, 256), 256, 0, st>>>(nb, B.child0, B.start, B.end, (int*)vflags, (int*)viota);
+    {
+        size_t tb = 0;
+        cub::DeviceSelect::Flagged(nullptr, tb, (int*)viota, (int*)vflags, leaves, d_count, nb, st);
+        if (tb > cub_cap) { CKS(ensure(plan, B_CUB, tb, &vcub)); cub_cap = plan->bufs[B_CUB].cap; }
+        CK(cub::DeviceSelect::Flagged(vcub, tb, (int*)viota, (int*)vflags, leaves, d_count, nb, st));
+        CK(cudaMemcpyAsync(&ti.n_leafp, d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        launches += 3;
+    }
+    const int nleaf = ti.n_leafp;
+    // direct lists
+    void *vdo, *vdl;
+    CKS(ensure(plan, B_DOFFS, (size_t)(nleaf + 1) * sizeof(int), &vdo));
+    int* doffs = (int*)vdo;
+    CK(cudaMemsetAsync(doffs, 0, (nleaf + 1) * sizeof(int), st));
+    k_direct<false><<<nblk(nleaf, 128), 128, 0, st>>>(nleaf, leaves, B, g, doffs, nullptr, nullptr, d_pairs);
+    {
+        size_t tb = 0;
+        cub::DeviceScan::ExclusiveSum(nullptr, tb, doffs, doffs, nleaf + 1, st);
+        if (tb > cub_cap) { CKS(ensure(plan, B_CUB, tb, &vcub)); cub_cap = plan->bufs[B_CUB].cap; }
+        CK(cub::DeviceScan::ExclusiveSum(vcub, tb, doffs, doffs, nleaf + 1, st));
+        int tot = 0;
+        CK(cudaMemcpyAsync(&tot, doffs + nleaf, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&ti.n_pairs, d_pairs, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        ti.n_entries = tot;
+        launches += 2;
+    }
+    CKS(ensure(plan, B_DL, (size_t)std::max<int64_t>(ti.n_entries, 1) * sizeof(DirectEntry), &vdl));
+    DirectEntry* dl = (DirectEntry*)vdl;
+    k_direct<true><<<nblk(nleaf, 128), 128, 0, st>>>(nleaf, leaves, B, g, nullptr, doffs, dl, nullptr);
+    ++launches;
+    rec(1);
+    // ---- (5) upward pass ---------------------------------------------------------------
+    void *vpr, *vloc;
+    CKS(ensure(plan, B_PROXY, (size_t)nb * drho * p3 * sizeof(T), &vpr));
+    CKS(ensure(plan, B_LOCAL, (size_t)nb * du * p3 * sizeof(T), &vloc));
+    T* proxy = (T*)vpr;
+    T* local = (T*)vloc;
+    CK(cudaMemsetAsync(proxy, 0, (size_t)nb * drho * p3 * sizeof(T), st));
+    CK(cudaMemsetAsync(local, 0, (size_t)nb * du * p3 * sizeof(T), st));
+    launches += 2;
+    if (nleaf > 0) {
+        if (p <= 24) launch_anterp<T, 24>(plan, tab, nleaf, leaves, B, xs, N, rs, proxy);
+        else launch_anterp<T, 48>(plan, tab, nleaf, leaves, B, xs, N, rs, proxy);
+        ++launches;
+    }
+    Evaluator<T> ev(plan, tab);
+    for (int l = nlev - 2; l >= 0; --l) {
+        const int n = ti.nR[l];
+        if (n == 0) continue;
+        Place pl;
+        unsigned char* scr;
+        size_t bytes = 3 * (size_t)p3 * sizeof(T);
+        CKS(ev.place(bytes, n, pl, &scr));
+        CKS(set_smem(plan, k_upward<T>, pl.use_smem ? bytes : 0));
+        k_upward<T><<<pl.grid, 256, pl.use_smem ? bytes : 0, st>>>(n, nl_box + ti.nl_off[l], B, tab, proxy, scr, bytes,
+                                                                  pl.use_smem);
+        ++launches;
+    }
+    rec(2);
+    // ---- (6) root far field (FP64) ----------------------------------------------------------
+    {
+        const RootTab& rt = plan->root;
+        void *vchi, *vuh, *vrsc;
+        CKS(ensure(plan, B_CHI, (size_t)Mtot * drho * rt.nmode * sizeof(Cx<double>), &vchi));
+        CKS(ensure(plan, B_UHAT, (size_t)du * rt.nmode * sizeof(Cx<double>), &vuh));
+        const size_t b1 = (size_t)rt.n1 * p * p + (size_t)rt.n1 * rt.n2 * p;
+        const size_t b2 = (size_t)rt.n1 * rt.n2 * p + (size_t)rt.n1 * p * p + rt.nmode;
+        const size_t per = std::max(b1, b2) * sizeof(Cx<double>);
+        const int jobs = Mtot * std::max(drho, du);
+        const unsigned grid = (unsigned)std::min(jobs, 148 * 4);
+        CKS(ensure(plan, B_SCRATCH, per * grid, &vrsc));
+        k_root_chi<T><<<std::min<unsigned>(grid, Mtot * drho), 256, 0, st>>>(Mtot, drho, p, g, rt, proxy,
+                                                                            (Cx<double>*)vchi, (unsigned char*)vrsc, per);
+        k_root_apply<<<nblk(rt.nmode, 128), 128, 0, st>>>(Mtot, drho, du, rt, (const Cx<double>*)vchi, (Cx<double>*)vuh);
+        k_root_eval<T><<<std::min<unsigned>(grid, Mtot * du), 256, 0, st>>>(Mtot, du, p, g, rt, (const Cx<double>*)vuh,
+                                                                           d_sums, drho, local, (unsigned char*)vrsc, per);
+        launches += 3;
+    }
+    rec(3);
+    // ---- (7) plane waves: outgoing for all non-leaf boxes, then translation + incoming ------
+    if (n_nl > 0) {
+        const int NF = P.NF, nfh = P.nfh;
+        const size_t nW = (size_t)NF * NF * nfh;
+        void* vpw;
+        CKS(ensure(plan, B_PW, (size_t)n_nl * drho * nW * sizeof(Cx<T>), &vpw));
+        Cx<T>* W = (Cx<T>*)vpw;
+        {
+            size_t bytes = ((size_t)p * p * nfh + (size_t)p * NF * nfh) * sizeof(Cx<T>);
+            Place pl;
+            unsigned char* scr;
+            CKS(ev.place(bytes, n_nl, pl, &scr));
+            CKS(set_smem(plan, k_pwout<T>, pl.use_smem ? bytes : 0));
+            k_pwout<T><<<pl.grid, 256, pl.use_smem ? bytes : 0, st>>>(n_nl, nl_box, tab, proxy, W, scr, bytes,
+                                                                     pl.use_smem);
+            ++launches;
+        }
+        rec(4);
+        {
+            size_t bytes = ((size_t)du * nW + (size_t)p * NF * nfh + (size_t)p * p * nfh) * sizeof(Cx<T>);
+            Place pl;
+            unsigned char* scr;
+            CKS(ev.place(bytes, n_nl, pl, &scr));
+            CKS(set_smem(plan, k_pwin<T>, pl.use_smem ? bytes : 0));
+            k_pwin<T><<<pl.grid, 256, pl.use_smem ? bytes : 0, st>>>(n_nl, nl_box, B, tab, W, local, scr, bytes,
+                                                                    pl.use_smem);
+            ++launches;
+        }
+    } else {
+        rec(4);
+    }
+    rec(5);
+    // ---- (8) shift to children, level by level --------------------------------------------
+    for (int l = 0; l < nlev - 1; ++l) {
+        const int n = ti.nR[l];
+        if (n == 0) continue;
+        Place pl;
+        unsigned char* scr;
+        size_t bytes = 2 * (size_t)p3 * sizeof(T);
+        CKS(ev.place(bytes, n, pl, &scr));
+        CKS(set_smem(plan, k_shift<T>, pl.use_smem ? bytes : 0));
+        k_shift<T><<<pl.grid, 256, pl.use_smem ? bytes : 0, st>>>(n, nl_box + ti.nl_off[l], B, tab, local, scr, bytes,
+                                                                 pl.use_smem);
+        ++launches;
+    }
+    rec(6);
+    // ---- (9) leaf stage -----------------------------------------------------------------
+    if (nleaf > 0) {
+        LeafOut lo;
+        lo.pot = pot;
+        lo.grad = grad;
+        lo.perm = idx2;
+        lo.rs = rs;
+        lo.self_val = plan->d_self;
+        lo.self_grad = plan->d_self + P.d_u * P.d_rho;
+        const bool gr = grad != nullptr;
+        switch (P.kernel) {
+            case DMK_LAPLACE: CKS((launch_leaf<T, DMK_LAPLACE>(plan, tab, nleaf, leaves, B, local, xs, N, doffs, dl, lo, gr))); break;
+            case DMK_STOKESLET: CKS((launch_leaf<T, DMK_STOKESLET>(plan, tab, nleaf, leaves, B, local, xs, N, doffs, dl, lo, gr))); break;
+            case DMK_STRESSLET: CKS((launch_leaf<T, DMK_STRESSLET>(plan, tab, nleaf, leaves, B, local, xs, N, doffs, dl, lo, gr))); break;
+            default: CKS((launch_leaf<T, DMK_ROTLET>(plan, tab, nleaf, leaves, B, local, xs, N, doffs, dl, lo, gr))); break;
+        }
+        ++launches;
+    }
+    rec(7);
+    CK(cudaGetLastError());
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (herr & kErrIndex) { plan->err = "internal index check failed"; return DMK_ERR_CUDA; }
+    // stats
+    dmk_stats_t& S = plan->stats;
+    S.c_times_1000 = (int)std::lround(P.c * 1000);
+    S.p = P.p;
+    S.n_f = P.nf;
+    S.n_root_modes = P.n_root_modes;
+    S.n_levels = nlev;
+    S.n_boxes = nb;
+    S.n_nonleaf = n_nl;
+    S.n_leaves = nb - n_nl;
+    S.n_pairs = (int64_t)ti.n_pairs;
+    S.n_direct_entries = ti.n_entries;
+    S.kernel_launches = launches;
+    S.fit_terms = tab.n_q;
+    if (plan->timing) {
+        float ms;
+        const int map[7][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 5}, {5, 6}, {6, 7}, {0, 7}};
+        for (int i = 0; i < 7; ++i) {
+            cudaEventElapsedTime(&ms, plan->ev[map[i][0]], plan->ev[map[i][1]]);
+            S.stage_ms[i] = ms;
+        }
+    }
+    return DMK_OK;
+}
+
+dmk_status_t make_plan(int k, int D, const double L[3], double tol, int prec, int n_s, void* stream, dmk_plan_t* out) {
+    if (!out) { g_plan_error = "out pointer is NULL"; return DMK_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (prec != DMK_FP64 && prec != DMK_MIXED) { g_plan_error = "precision must be DMK_FP64 or DMK_MIXED"; return DMK_ERR_INVALID_ARG; }
+    if (n_s < 1) { g_plan_error = "n_s must be >= 1"; return DMK_ERR_INVALID_ARG; }
+    dmk_plan_s* plan = new (std::nothrow) dmk_plan_s();
+    if (!plan) { g_plan_error = "host allocation failed"; return DMK_ERR_OOM; }
+    std::string err;
+    dmk_status_t s = build_plan_tables(k, D, L, tol, plan->T, err);
+    if (s != DMK_OK) { g_plan_error = err; delete plan; return s; }
+    plan->prec = prec;
+    plan->n_s = n_s;
+    plan->stream = (cudaStream_t)stream;
+    for (int i = 0; i < 3; ++i) {
+        plan->geo.L[i] = plan->T.L[i];
+        plan->geo.M[i] = plan->T.M[i];
+        plan->geo.periodic[i] = plan->T.periodic[i];
+    }
+    plan->geo.s = plan->T.s;
+    plan->geo.D = D;
+    cudaError_t e = cudaGetDevice(&plan->device);
+    if (e != cudaSuccess) { g_plan_error = std::string("no CUDA device: ") + cudaGetErrorString(e); delete plan; return DMK_ERR_CUDA; }
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
+    plan->smem_optin = (size_t)optin;
+    if ((s = upload_tab<double>(plan, &plan->d_tab64, plan->tab64, 1e-17)) != DMK_OK ||
+        (s = upload_tab<float>(plan, &plan->d_tab32, plan->tab32, 1e-9)) != DMK_OK || (s = upload_root(plan)) != DMK_OK) {
+        g_plan_error = plan->err;
+        dmk_destroy(plan);
+        return s;
+    }
+    for (int i = 0; i < 8; ++i) cudaEventCreate(&plan->ev[i]);
+    *out = plan;
+    return DMK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dmk_status_t dmk_plan(dmk_kernel_t k, int D, double L1, double L2, double L3, double tol, dmk_plan_t* out) {
+    const double L[3] = {L1, L2, L3};
+    return make_plan(k, D, L, tol, DMK_MIXED, 250, nullptr, out);
+}
+
+dmk_status_t dmk_plan_ex(dmk_kernel_t k, int D, const double L[3], double tol, dmk_precision_t prec, int n_s,
+                         void* cuda_stream, dmk_plan_t* out) {
+    if (!L) { g_plan_error = "L is NULL"; return DMK_ERR_INVALID_ARG; }
+    return make_plan(k, D, L, tol, prec, n_s, cuda_stream, out);
+}
+
+dmk_status_t dmk_eval(dmk_plan_t plan, int64_t N, const double* points, const double* strengths, double* potentials,
+                      double* grad) {
+    if (!plan) return DMK_ERR_INVALID_ARG;
+    plan->err.clear();
+    if (N < 0) { plan->err = "N < 0"; return DMK_ERR_INVALID_ARG; }
+    if (N == 0) return DMK_OK;
+    if (N > (int64_t)1 << 30) { plan->err = "N above 2^30"; return DMK_ERR_INVALID_ARG; }
+    if (!points || !strengths || !potentials) { plan->err = "NULL array"; return DMK_ERR_INVALID_ARG; }
+    cudaSetDevice(plan->device);
+    if (plan->prec == DMK_FP64) return run_eval<double>(plan, plan->tab64, N, points, strengths, potentials, grad);
+    return run_eval<float>(plan, plan->tab32, N, points, strengths, potentials, grad);
+}
+
+dmk_status_t dmk_eval_host(dmk_plan_t plan, int64_t N, const double* points, const double* strengths,
+                           double* potentials, double* grad) {
+    if (!plan) return DMK_ERR_INVALID_ARG;
+    if (N == 0) return DMK_OK;
+    if (N < 0 || !points || !strengths || !potentials) { plan->err = "bad arguments"; return DMK_ERR_INVALID_ARG; }
+    const int drho = plan->T.d_rho, du = plan->T.d_u;
+    void *dp, *dr, *du_, *dg = nullptr;
+    dmk_status_t s;
+    if ((s = ensure(plan, B_DEVPTS, 3 * N * sizeof(double), &dp)) != DMK_OK) return s;
+    if ((s = ensure(plan, B_DEVRHO, N * drho * sizeof(double), &dr)) != DMK_OK) return s;
+    if ((s = ensure(plan, B_DEVPOT, N * du * sizeof(double), &du_)) != DMK_OK) return s;
+    if (grad && (s = ensure(plan, B_DEVGRAD, N * 3 * du * sizeof(double), &dg)) != DMK_OK) return s;
+    cudaStream_t st = plan->stream;
+    CK(cudaMemcpyAsync(dp, points, 3 * N * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dr, strengths, N * drho * sizeof(double), cudaMemcpyHostToDevice, st));
+    s = dmk_eval(plan, N, (const double*)dp, (const double*)dr, (double*)du_, (double*)dg);
+    if (s != DMK_OK) return s;
+    CK(cudaMemcpyAsync(potentials, du_, N * du * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (grad) CK(cudaMemcpyAsync(grad, dg, N * 3 * du * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return DMK_OK;
+}
+
+dmk_status_t dmk_get_stats(dmk_plan_t plan, dmk_stats_t* out) {
+    if (!plan || !out) return DMK_ERR_INVALID_ARG;
+    *out = plan->stats;
+    return DMK_OK;
+}
+
+dmk_status_t dmk_set_timing(dmk_plan_t plan, int enable) {
+    if (!plan) return DMK_ERR_INVALID_ARG;
+    plan->timing = enable ? 1 : 0;
+    return DMK_OK;
+}
+
+dmk_status_t dmk_destroy(dmk_plan_t plan) {
+    if (!plan) return DMK_OK;
+    for (auto& b : plan->bufs)
+        if (b.p) cudaFree(b.p);
+    if (plan->d_tab64) cudaFree(plan->d_tab64);
+    if (plan->d_tab32) cudaFree(plan->d_tab32);
+    if (plan->d_root) cudaFree(plan->d_root);
+    if (plan->d_self) cudaFree(plan->d_self);
+    for (int i = 0; i < 8; ++i)
+        if (plan->ev[i]) cudaEventDestroy(plan->ev[i]);
+    delete plan;
+    return DMK_OK;
+}
+
+dmk_status_t dmk_plan_info(dmk_kernel_t k, int D, const double L[3], double tol, dmk_plan_info_t* out) {
+    if (!L || !out) { g_plan_error = "NULL argument"; return DMK_ERR_INVALID_ARG; }
+    PlanTables T;
+    std::string err;
+    dmk_status_t s = build_plan_tables(k, D, L, tol, T, err);
+    if (s != DMK_OK) { g_plan_error = err; return s; }
+    auto nterms = [](const std::vector<double>& a, double tol_rel) {
+        double mx = 0;
+        for (double v : a) mx = std::max(mx, std::fabs(v));
+        int n = (int)a.size();
+        while (n > 1 && std::fabs(a[n - 1]) < tol_rel * mx) --n;
+        return n;
+    };
+    out->c = T.c; out->s = T.s; out->R = T.R; out->dk = T.dk;
+    out->p = T.p; out->n_f = T.nf; out->n_root_modes = T.n_root_modes;
+    out->fit_terms_fp64 = nterms(T.fit_q, 1e-17);
+    out->fit_terms_fp32 = nterms(T.fit_q, 1e-9);
+    for (int i = 0; i < 3; ++i) { out->M[i] = T.M[i]; out->n_axis[i] = (int)T.kax[i].size(); }
+    out->d_rho = T.d_rho; out->d_u = T.d_u;
+    return DMK_OK;
+}
+
+dmk_status_t dmk_plan_table(dmk_kernel_t k, int D, const double L[3], double tol, int which, double* out,
+                            int64_t cap, int64_t* n) {
+    if (!L || !n) { g_plan_error = "NULL argument"; return DMK_ERR_INVALID_ARG; }
+    PlanTables T;
+    std::string err;
+    dmk_status_t s = build_plan_tables(k, D, L, tol, T, err);
+    if (s != DMK_OK) { g_plan_error = err; return s; }
+    std::vector<double> v;
+    if (which == 0) {
+        for (int i = 0; i < 3; ++i) v.insert(v.end(), T.kax[i].begin(), T.kax[i].end());
+    } else if (which == 1) {
+        for (auto& z : T.Wroot) { v.push_back(z.real()); v.push_back(z.imag()); }
+    } else if (which == 2) {
+        v = T.gdiff;
+    } else if (which == 3) {
+        v = {T.phi0, T.d2phi0, T.d2phihat0};
+        v.insert(v.end(), T.phihat_samples.begin(), T.phihat_samples.end());
+    } else {
+        g_plan_error = "which must be 0..3";
+        return DMK_ERR_INVALID_ARG;
+    }
+    *n = (int64_t)v.size();
+    if (out) std::memcpy(out, v.data(), sizeof(double) * (size_t)std::min<int64_t>(cap, (int64_t)v.size()));
+    return DMK_OK;
+}
+
+const char* dmk_status_string(dmk_status_t s) {
+    switch (s) {
+        case DMK_OK: return "ok";
+        case DMK_ERR_INVALID_ARG: return "invalid argument";
+        case DMK_ERR_OUT_OF_DOMAIN: return "point outside the domain";
+        case DMK_ERR_NOT_NEUTRAL: return "non-neutral charges for D = 1, 2 Laplace";
+        case DMK_ERR_UNSUPPORTED: return "unsupported configuration";
+        case DMK_ERR_TREE_DEPTH: return "tree depth limit";
+        case DMK_ERR_OOM: return "out of device memory";
+        case DMK_ERR_CUDA: return "CUDA error";
+        case DMK_ERR_TIMEOUT: return "timeout";
+    }
+    return "unknown status";
+}
+
+const char* dmk_last_error(dmk_plan_t plan) {
+    if (!plan) return g_plan_error.c_str();
+    return plan->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+// Device-side helpers: complex arithmetic, Morton keys, table views, precision traits.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dmk {
+
+template <class T> struct Cx { T x, y; };
+template <class T> __host__ __device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <class T> __host__ __device__ __forceinline__ Cx<T> cadd(Cx<T> a, Cx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <class T> __host__ __device__ __forceinline__ Cx<T> cconj(Cx<T> a) { return {a.x, -a.y}; }
+// a += b * c
+template <class T> __device__ __forceinline__ void cfma(Cx<T>& a, Cx<T> b, Cx<T> c) {
+    a.x = fma(b.x, c.x, fma(-b.y, c.y, a.x));
+    a.y = fma(b.x, c.y, fma(b.y, c.x, a.y));
+}
+// a += b * real
+template <class T> __device__ __forceinline__ void cfmar(Cx<T>& a, Cx<T> b, T r) {
+    a.x = fma(b.x, r, a.x);
+    a.y = fma(b.y, r, a.y);
+}
+
+// ---- keys: cell key at level l = (cube << 3l) | interleave(px, py, pz) with x the lowest bit
+__host__ __device__ __forceinline__ uint64_t spread3(uint32_t v) {
+    uint64_t x = v & 0x1fffff;
+    x = (x | x << 32) & 0x1f00000000ffffULL;
+    x = (x | x << 16) & 0x1f0000ff0000ffULL;
+    x = (x | x << 8) & 0x100f00f00f00f00fULL;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ULL;
+    x = (x | x << 2) & 0x1249249249249249ULL;
+    return x;
+}
+__host__ __device__ __forceinline__ uint32_t compact3(uint64_t x) {
+    x &= 0x1249249249249249ULL;
+    x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ULL;
+    x = (x ^ (x >> 4)) & 0x100f00f00f00f00fULL;
+    x = (x ^ (x >> 8)) & 0x1f0000ff0000ffULL;
+    x = (x ^ (x >> 16)) & 0x1f00000000ffffULL;
+    x = (x ^ (x >> 32)) & 0x1fffffULL;
+    return (uint32_t)x;
+}
+
+struct Geo {
+    double L[3];
+    double s;
+    int M[3];
+    int periodic[3];
+    int D;
+};
+
+// global integer index of a cell -> key (valid indices only)
+__host__ __device__ __forceinline__ uint64_t cell_key(const Geo& g, int level, const int ix[3]) {
+    uint32_t m[3], p[3];
+    for (int i = 0; i < 3; ++i) {
+        m[i] = (uint32_t)ix[i] >> level;
+        p[i] = (uint32_t)ix[i] & ((1u << level) - 1u);
+    }
+    uint64_t cube = m[0] + (uint64_t)g.M[0] * (m[1] + (uint64_t)g.M[1] * m[2]);
+    uint64_t morton = spread3(p[0]) | (spread3(p[1]) << 1) | (spread3(p[2]) << 2);
+    return (cube << (3 * level)) | morton;
+}
+__host__ __device__ __forceinline__ void cell_ix(const Geo& g, int level, uint64_t key, int ix[3]) {
+    uint64_t cube = key >> (3 * level);
+    uint64_t morton = key & ((level == 0) ? 0ULL : ((1ULL << (3 * level)) - 1ULL));
+    int m0 = (int)(cube % g.M[0]);
+    int m1 = (int)((cube / g.M[0]) % g.M[1]);
+    int m2 = (int)(cube / ((uint64_t)g.M[0] * g.M[1]));
+    ix[0] = (m0 << level) | (int)compact3(morton);
+    ix[1] = (m1 << level) | (int)compact3(morton >> 1);
+    ix[2] = (m2 << level) | (int)compact3(morton >> 2);
+}
+
+// neighbour of ix at level by offset d; returns false if outside a free axis.  shift[i] counts
+// whole periods (-1, 0, 1) so that the image sits at (wrapped neighbour) + shift * L.
+__host__ __device__ __forceinline__ bool neighbour(const Geo& g, int level, const int ix[3], const int d[3],
+                                                   int out[3], int shift[3]) {
+    for (int i = 0; i < 3; ++i) {
+        int n = g.M[i] << level;
+        int v = ix[i] + d[i];
+        shift[i] = 0;
+        if (v < 0 || v >= n) {
+            if (!g.periodic[i]) return false;
+            if (v < 0) { v += n; shift[i] = -1; } else { v -= n; shift[i] = 1; }
+        }
+        out[i] = v;
+    }
+    return true;
+}
+
+// view of the per-precision tables on the device
+template <class T> struct Tab {
+    int p, nf, NF, nfh, d_rho, d_u, kernel, level_power;
+    const T* nodes;
+    const T* bary;
+    const T* Ioct;       // 2 x p x p
+    const T* Cm;         // p x p
+    const Cx<T>* E;      // NF x p
+    const T* gdiff;      // NF x NF x nfh
+    const T* fit;        // concatenated Chebyshev series
+    int off_q, n_q, off_f, n_f, off_g, n_g, off_dq, n_dq, off_df, n_df, off_dg, n_dg;
+};
+
+// Clenshaw evaluation of sum_k a_k T_k(t)
+template <class T> __device__ __forceinline__ T clenshaw(const T* a, int n, T t) {
+    T b1 = 0, b2 = 0;
+    T t2 = t + t;
+    for (int k = n - 1; k >= 1; --k) {
+        T b0 = fma(t2, b1, a[k] - b2);
+        b2 = b1;
+        b1 = b0;
+    }
+    return fma(t, b1, a[0] - b2);
+}
+
+}  // namespace dmk

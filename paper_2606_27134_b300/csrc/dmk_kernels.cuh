@@ -1,0 +1,879 @@
+// Evaluation kernels: upward pass (Sec. 3.1.2), root far field (Sec. 4.3, 5.3), plane-wave
+// difference-kernel interactions (Sec. 2.3 Eq. Dl_int_discr, Sec. 3.1.4), Chebyshev shift to
+// children (Sec. 3.1.4) and the leaf stage (Sec. 3.1.5, Sec. 2.4).
+//
+// Per-box tensors are stored x-major: t[(j1 * p + j2) * p + j3], j1 the x node index.
+// Work buffers come from dynamic shared memory when they fit, else from a per-CTA slice of a
+// global scratch array (the same code through a generic pointer).
+#pragma once
+#include "dmk_tree.cuh"
+
+namespace dmk {
+
+extern __shared__ __align__(16) unsigned char dsmem[];
+
+__device__ __forceinline__ unsigned char* work_base(unsigned char* scratch, size_t per_cta, int use_smem) {
+    return use_smem ? dsmem : scratch + (size_t)blockIdx.x * per_cta;
+}
+
+// Lagrange basis on first-kind Chebyshev nodes by the barycentric formula (nodes exact hits -> delta)
+template <class T>
+__device__ __forceinline__ void lagrange_row(T xi, const T* nodes, const T* bary, int p, T* out) {
+    T den = 0;
+    int hit = -1;
+    for (int a = 0; a < p; ++a) {
+        T d = xi - nodes[a];
+        if (d == T(0)) hit = a;
+        den += bary[a] / d;
+    }
+    if (hit >= 0) {
+        for (int a = 0; a < p; ++a) out[a] = (a == hit) ? T(1) : T(0);
+        return;
+    }
+    T inv = T(1) / den;
+    for (int a = 0; a < p; ++a) out[a] = bary[a] / (xi - nodes[a]) * inv;
+}
+
+// ------------------------------------------------------------------------------------------
+// Leaf anterpolation (Sec. 3.1.2): proxy(j1,j2,j3) = sum_s rho_s l_j1(xi_s) l_j2(eta_s) l_j3(zeta_s).
+// Thread per (j2, j3) pair holding the p values over j1 in registers.
+template <class T, int MAXP>
+__global__ void __launch_bounds__(MAXP <= 24 ? 576 : 512) k_anterp(int nleaf, const int* __restrict__ leaves, BoxArrays B,
+                                                 const double* __restrict__ xs, int64_t N,
+                                                 const double* __restrict__ rs, Tab<T> tab, double s,
+                                                 T* __restrict__ proxy) {
+    const int p = tab.p, p2 = p * p, drho = tab.d_rho;
+    constexpr int PC = 32;
+    T* lx = reinterpret_cast<T*>(dsmem);
+    T* ly = lx + PC * MAXP;
+    T* lz = ly + PC * MAXP;
+    for (int li = blockIdx.x; li < nleaf; li += gridDim.x) {
+        const int box = leaves[li];
+        const int l = B.level[box];
+        const double r = s / (double)(1 << l), half = 0.5 * r;
+        const double c[3] = {(B.ix[3 * box] + 0.5) * r, (B.ix[3 * box + 1] + 0.5) * r, (B.ix[3 * box + 2] + 0.5) * r};
+        const int st = B.start[box], en = B.end[box];
+        for (int a = 0; a < drho; ++a) {
+            for (int pair0 = 0; pair0 < p2; pair0 += blockDim.x) {
+                const int pair = pair0 + threadIdx.x;
+                const bool active = pair < p2;
+                const int jb = active ? pair / p : 0, jc = active ? pair % p : 0;
+                T acc[MAXP];
+#pragma unroll
+                for (int j = 0; j < MAXP; ++j) acc[j] = 0;
+                for (int s0 = st; s0 < en; s0 += PC) {
+                    const int ns = min(PC, en - s0);
+                    __syncthreads();
+                    for (int u = threadIdx.x; u < 3 * ns; u += blockDim.x) {
+                        const int pt = u / 3, ax = u % 3;
+                        const double xi = (xs[ax * N + s0 + pt] - c[ax]) / half;
+                        T* row = (ax == 0 ? lx : (ax == 1 ? ly : lz)) + pt * MAXP;
+                        lagrange_row<T>((T)xi, tab.nodes, tab.bary, p, row);
+                        if (ax == 0) {
+                            const T wgt = (T)rs[(int64_t)(s0 + pt) * drho + a];
+                            for (int j = 0; j < p; ++j) row[j] *= wgt;
+                        }
+                    }
+                    __syncthreads();
+                    if (active) {
+                        for (int pt = 0; pt < ns; ++pt) {
+                            const T t = ly[pt * MAXP + jb] * lz[pt * MAXP + jc];
+#pragma unroll
+                            for (int j = 0; j < MAXP; ++j)
+                                if (j < p) acc[j] = fma(lx[pt * MAXP + j], t, acc[j]);
+                        }
+                    }
+                }
+                if (active) {
+                    T* out = proxy + ((size_t)box * drho + a) * p * p2;
+#pragma unroll
+                    for (int j = 0; j < MAXP; ++j)
+                        if (j < p) out[j * p2 + pair] = acc[j];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Upward pass child -> parent (Sec. 3.1.2): parent += sum_children (I^T x I^T x I^T) child,
+// I[o][j_child][a_parent] = l_a(child node j in parent coordinates).
+template <class T>
+__global__ void k_upward(int n, const int* __restrict__ nl_box, BoxArrays B, Tab<T> tab, T* __restrict__ proxy,
+                         unsigned char* scratch, size_t per_cta, int use_smem) {
+    const int p = tab.p, p2 = p * p, p3 = p2 * p, drho = tab.d_rho;
+    T* t1 = reinterpret_cast<T*>(work_base(scratch, per_cta, use_smem));
+    T* t2 = t1 + p3;
+    T* acc = t2 + p3;
+    for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
+        const int P = nl_box[bi];
+        const int c0 = B.child0[P];
+        for (int a = 0; a < drho; ++a) {
+            for (int e = threadIdx.x; e < p3; e += blockDim.x) acc[e] = 0;
+            for (int o = 0; o < 8; ++o) {
+                const T* ch = proxy + ((size_t)(c0 + o) * drho + a) * p3;
+                const T* Iz = tab.Ioct + ((o >> 2) & 1) * p2;
+                const T* Iy = tab.Ioct + ((o >> 1) & 1) * p2;
+                const T* Ix = tab.Ioct + (o & 1) * p2;
+                __syncthreads();
+                for (int e = threadIdx.x; e < p3; e += blockDim.x) {      // contract z
+                    const int i12 = e / p, cc = e % p;
+                    T v = 0;
+                    for (int k = 0; k < p; ++k) v = fma(ch[i12 * p + k], Iz[k * p + cc], v);
+                    t1[e] = v;
+                }
+                __syncthreads();
+                for (int e = threadIdx.x; e < p3; e += blockDim.x) {      // contract y
+                    const int i1 = e / p2, bb = (e / p) % p, cc = e % p;
+                    T v = 0;
+                    for (int k = 0; k < p; ++k) v = fma(t1[(i1 * p + k) * p + cc], Iy[k * p + bb], v);
+                    t2[e] = v;
+                }
+                __syncthreads();
+                for (int e = threadIdx.x; e < p3; e += blockDim.x) {      // contract x
+                    const int aa = e / p2, r23 = e % p2;
+                    T v = acc[e];
+                    for (int k = 0; k < p; ++k) v = fma(t2[k * p2 + r23], Ix[k * p + aa], v);
+                    acc[e] = v;
+                }
+            }
+            __syncthreads();
+            T* out = proxy + ((size_t)P * drho + a) * p3;
+            for (int e = threadIdx.x; e < p3; e += blockDim.x) out[e] = acc[e];
+            __syncthreads();
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Shift to children (Sec. 3.1.4): local(child) += (I x I x I) local(parent)
+template <class T>
+__global__ void k_shift(int n, const int* __restrict__ nl_box, BoxArrays B, Tab<T> tab, T* __restrict__ local,
+                        unsigned char* scratch, size_t per_cta, int use_smem) {
+    const int p = tab.p, p2 = p * p, p3 = p2 * p, du = tab.d_u;
+    T* t1 = reinterpret_cast<T*>(work_base(scratch, per_cta, use_smem));
+    T* t2 = t1 + p3;
+    for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
+        const int P = nl_box[bi];
+        const int c0 = B.child0[P];
+        for (int j = 0; j < du; ++j) {
+            const T* par = local + ((size_t)P * du + j) * p3;
+            for (int o = 0; o < 8; ++o) {
+                const T* Iz = tab.Ioct + ((o >> 2) & 1) * p2;
+                const T* Iy = tab.Ioct + ((o >> 1) & 1) * p2;
+                const T* Ix = tab.Ioct + (o & 1) * p2;
+                __syncthreads();
+                for (int e = threadIdx.x; e < p3; e += blockDim.x) {
+                    const int i12 = e / p, cc = e % p;
+                    T v = 0;
+                    for (int k = 0; k < p; ++k) v = fma(Iz[cc * p + k], par[i12 * p + k], v);
+                    t1[e] = v;
+                }
+                __syncthreads();
+                for (int e = threadIdx.x; e < p3; e += blockDim.x) {
+                    const int i1 = e / p2, bb = (e / p) % p, cc = e % p;
+                    T v = 0;
+                    for (int k = 0; k < p; ++k) v = fma(Iy[bb * p + k], t1[(i1 * p + k) * p + cc], v);
+                    t2[e] = v;
+                }
+                __syncthreads();
+                T* ch = local + ((size_t)(c0 + o) * du + j) * p3;
+                for (int e = threadIdx.x; e < p3; e += blockDim.x) {
+                    const int aa = e / p2, r23 = e % p2;
+                    T v = 0;
+                    for (int k = 0; k < p; ++k) v = fma(Ix[aa * p + k], t2[k * p2 + r23], v);
+                    ch[e] += v;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Plane-wave outgoing expansions (Sec. 3.1.4, Eq. Dl_int_discr): for every non-leaf box,
+// W(m) = sum_j proxy(j) exp(-i h m . y_j); h y_j = (pi/3) m eta_j at every level.  Real input,
+// so only m3 >= 0 is stored: W[nl][a][(m1 * NF + m2) * nfh + m3].
+template <class T>
+__global__ void k_pwout(int n, const int* __restrict__ nl_box, Tab<T> tab, const T* __restrict__ proxy,
+                        Cx<T>* __restrict__ W, unsigned char* scratch, size_t per_cta, int use_smem) {
+    const int p = tab.p, p2 = p * p, p3 = p2 * p, drho = tab.d_rho;
+    const int nf = tab.nf, NF = tab.NF, nfh = tab.nfh;
+    const int nW = NF * NF * nfh;
+    Cx<T>* A1 = reinterpret_cast<Cx<T>*>(work_base(scratch, per_cta, use_smem));
+    Cx<T>* A2 = A1 + p2 * nfh;
+    for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
+        const int box = nl_box[bi];
+        for (int a = 0; a < drho; ++a) {
+            const T* pr = proxy + ((size_t)box * drho + a) * p3;
+            __syncthreads();
+            for (int e = threadIdx.x; e < p2 * nfh; e += blockDim.x) {   // j3 -> m3 (>= 0)
+                const int i12 = e / nfh, m3 = e % nfh;
+                const Cx<T>* Er = tab.E + (nf + m3) * p;
+                Cx<T> v = {0, 0};
+                for (int k = 0; k < p; ++k) cfmar(v, Er[k], pr[i12 * p + k]);
+                A1[e] = v;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < p * NF * nfh; e += blockDim.x) {   // j2 -> m2
+                const int i1 = e / (NF * nfh), m2 = (e / nfh) % NF, m3 = e % nfh;
+                const Cx<T>* Er = tab.E + m2 * p;
+                Cx<T> v = {0, 0};
+                for (int k = 0; k < p; ++k) cfma(v, Er[k], A1[(i1 * p + k) * nfh + m3]);
+                A2[e] = v;
+            }
+            __syncthreads();
+            Cx<T>* out = W + ((size_t)bi * drho + a) * nW;
+            for (int e = threadIdx.x; e < nW; e += blockDim.x) {           // j1 -> m1
+                const int m1 = e / (NF * nfh), r = e % (NF * nfh);
+                const Cx<T>* Er = tab.E + m1 * p;
+                Cx<T> v = {0, 0};
+                for (int k = 0; k < p; ++k) cfma(v, Er[k], A2[k * NF * nfh + r]);
+                out[e] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// operator symbol of the kernel on the integer wave vector m (App. B): out[j][a] = op_ja(m) * V_a
+template <class T>
+__device__ __forceinline__ void apply_op(int kernel, const T m[3], const Cx<T>* V, Cx<T>* out) {
+    if (kernel == DMK_LAPLACE) {
+        out[0] = V[0];
+    } else if (kernel == DMK_STOKESLET) {
+        const T m2 = m[0] * m[0] + m[1] * m[1] + m[2] * m[2];
+        Cx<T> md = {0, 0};
+        for (int l = 0; l < 3; ++l) cfmar(md, V[l], m[l]);
+        for (int j = 0; j < 3; ++j) out[j] = {m2 * V[j].x - m[j] * md.x, m2 * V[j].y - m[j] * md.y};
+    } else if (kernel == DMK_STRESSLET) {
+        // i [ (m_m d_jl + m_l d_mj + m_j d_lm) |m|^2 - 2 m_j m_l m_m ] Q_lm
+        const T m2 = m[0] * m[0] + m[1] * m[1] + m[2] * m[2];
+        Cx<T> Qm[3], QTm[3], tr = {V[0].x + V[4].x + V[8].x, V[0].y + V[4].y + V[8].y}, mQm = {0, 0};
+        for (int j = 0; j < 3; ++j) {
+            Qm[j] = {0, 0};
+            QTm[j] = {0, 0};
+            for (int k = 0; k < 3; ++k) {
+                cfmar(Qm[j], V[j * 3 + k], m[k]);
+                cfmar(QTm[j], V[k * 3 + j], m[k]);
+            }
+        }
+        for (int j = 0; j < 3; ++j) cfmar(mQm, Qm[j], m[j]);
+        for (int j = 0; j < 3; ++j) {
+            Cx<T> v = {m2 * (Qm[j].x + QTm[j].x + m[j] * tr.x) - 2 * m[j] * mQm.x,
+                       m2 * (Qm[j].y + QTm[j].y + m[j] * tr.y) - 2 * m[j] * mQm.y};
+            out[j] = {-v.y, v.x};     // times i
+        }
+    } else {
+        // rotlet: -1/2 i eps_jlm m_m tau_l = -1/2 i (tau x m)_j
+        Cx<T> c[3];
+        c[0] = {V[1].x * m[2] - V[2].x * m[1], V[1].y * m[2] - V[2].y * m[1]};
+        c[1] = {V[2].x * m[0] - V[0].x * m[2], V[2].y * m[0] - V[0].y * m[2]};
+        c[2] = {V[0].x * m[1] - V[1].x * m[0], V[0].y * m[1] - V[1].y * m[0]};
+        for (int j = 0; j < 3; ++j) out[j] = {T(0.5) * c[j].y, T(-0.5) * c[j].x};
+    }
+}
+
+// Translation over colleagues, symbol, incoming transform (Sec. 3.1.4): for non-leaf B,
+//   V(m) = sum_{non-leaf colleague C at offset d} exp(-i (2 pi/3) m.d) W_C(m),
+//   u_B(j) += Re sum_m 2^(a l) g(m) op(m) V(m) exp(+i (pi/3) m . eta_j).
+template <class T>
+__global__ void k_pwin(int n, const int* __restrict__ nl_box, BoxArrays B, Tab<T> tab, const Cx<T>* __restrict__ W,
+                       T* __restrict__ local, unsigned char* scratch, size_t per_cta, int use_smem) {
+    const int p = tab.p, p2 = p * p, p3 = p2 * p, drho = tab.d_rho, du = tab.d_u;
+    const int nf = tab.nf, NF = tab.NF, nfh = tab.nfh;
+    const int nW = NF * NF * nfh;
+    Cx<T>* Vp = reinterpret_cast<Cx<T>*>(work_base(scratch, per_cta, use_smem));
+    Cx<T>* B2 = Vp + du * nW;
+    Cx<T>* B1 = B2 + p * NF * nfh;
+    __shared__ int ncol;
+    __shared__ int col_nl[27];
+    __shared__ int col_d[27];
+    const T c3 = T(-0.5), s3 = T(-0.86602540378443864676);   // exp(-i 2 pi/3)
+    for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
+        const int box = nl_box[bi];
+        const int l = B.level[box];
+        const T scale = (T)ldexp(1.0, tab.level_power * l);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int k = 0;
+            for (int d = 0; d < 27; ++d) {
+                const int C = B.coll[box * 27 + d];
+                if (C >= 0 && B.nl[C] >= 0) { col_nl[k] = B.nl[C]; col_d[k] = d; ++k; }
+            }
+            ncol = k;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < nW; e += blockDim.x) {
+            const int i1 = e / (NF * nfh), i2 = (e / nfh) % NF, m3 = e % nfh;
+            const int m1 = i1 - nf, m2 = i2 - nf;
+            Cx<T> V[9];
+            for (int a = 0; a < drho; ++a) V[a] = {0, 0};
+            for (int k = 0; k < ncol; ++k) {
+                const int d = col_d[k];
+                const int dot = m1 * (d % 3 - 1) + m2 * ((d / 3) % 3 - 1) + m3 * (d / 9 - 1);
+                const int r = ((dot % 3) + 3) % 3;
+                const Cx<T> ph = (r == 0) ? Cx<T>{1, 0} : (r == 1 ? Cx<T>{c3, s3} : Cx<T>{c3, -s3});
+                const Cx<T>* Wc = W + (size_t)col_nl[k] * drho * nW + e;
+                for (int a = 0; a < drho; ++a) cfma(V[a], ph, Wc[(size_t)a * nW]);
+            }
+            const T g = scale * tab.gdiff[e];
+            const T mv[3] = {(T)m1, (T)m2, (T)m3};
+            Cx<T> out[3];
+            apply_op<T>(tab.kernel, mv, V, out);
+            for (int j = 0; j < du; ++j) Vp[(size_t)j * nW + e] = {g * out[j].x, g * out[j].y};
+        }
+        for (int j = 0; j < du; ++j) {
+            __syncthreads();
+            const Cx<T>* Vj = Vp + (size_t)j * nW;
+            for (int e = threadIdx.x; e < p * NF * nfh; e += blockDim.x) {   // m1 -> j1
+                const int i1 = e / (NF * nfh), r = e % (NF * nfh);
+                Cx<T> v = {0, 0};
+                for (int k = 0; k < NF; ++k) cfma(v, cconj(tab.E[k * p + i1]), Vj[k * NF * nfh + r]);
+                B2[e] = v;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < p2 * nfh; e += blockDim.x) {       // m2 -> j2
+                const int i1 = e / (p * nfh), i2 = (e / nfh) % p, m3 = e % nfh;
+                Cx<T> v = {0, 0};
+                for (int k = 0; k < NF; ++k) cfma(v, cconj(tab.E[k * p + i2]), B2[(i1 * NF + k) * nfh + m3]);
+                B1[e] = v;
+            }
+            __syncthreads();
+            T* u = local + ((size_t)box * du + j) * p3;
+            for (int e = threadIdx.x; e < p3; e += blockDim.x) {             // m3 -> j3, real part
+                const int i12 = e / p, i3 = e % p;
+                T v = 0;
+                for (int m3 = 0; m3 < nfh; ++m3) {
+                    const Cx<T> f = cconj(tab.E[(nf + m3) * p + i3]);
+                    const Cx<T> b = B1[i12 * nfh + m3];
+                    const T re = f.x * b.x - f.y * b.y;
+                    v += (m3 == 0 ? T(1) : T(2)) * re;
+                }
+                u[e] += v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Root far field (Sec. 4.3 Eqs. structurefac and eval_tensor; Sec. 5.3 Eq. ewald_far_allP_discr), FP64.
+struct RootTab {
+    int n1, n2, n3, nmode;
+    const double* kax[3];
+    const Cx<double>* S[3];      // S_i[k * p + j] = exp(-i k (s/2) eta_j)
+    const Cx<double>* W;         // nmode x du x drho
+    const double* rconst;        // du x drho
+};
+
+// chi_m(k) for cube m, component a (tensor form), including exp(-i k . c_m)
+template <class T>
+__global__ void k_root_chi(int M, int drho, int p, Geo g, RootTab rt, const T* __restrict__ proxy,
+                           Cx<double>* __restrict__ chi_part, unsigned char* scratch, size_t per_cta) {
+    const int p2 = p * p, p3 = p2 * p;
+    const int n1 = rt.n1, n2 = rt.n2, n3 = rt.n3;
+    Cx<double>* B1 = reinterpret_cast<Cx<double>*>(scratch + (size_t)blockIdx.x * per_cta);
+    Cx<double>* B2 = B1 + (size_t)n1 * p2;
+    for (int job = blockIdx.x; job < M * drho; job += gridDim.x) {
+        const int m = job / drho, a = job % drho;   // cube m is box m (level 0, cube order)
+        const T* pr = proxy + ((size_t)m * drho + a) * p3;
+        int mc[3] = {m % g.M[0], (m / g.M[0]) % g.M[1], m / (g.M[0] * g.M[1])};
+        const double cm[3] = {(mc[0] + 0.5) * g.s, (mc[1] + 0.5) * g.s, (mc[2] + 0.5) * g.s};
+        __syncthreads();
+        for (int e = threadIdx.x; e < n1 * p2; e += blockDim.x) {
+            const int i1 = e / p2, r = e % p2;
+            Cx<double> v = {0, 0};
+            for (int k = 0; k < p; ++k) cfmar(v, rt.S[0][i1 * p + k], (double)pr[k * p2 + r]);
+            B1[e] = v;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < n1 * n2 * p; e += blockDim.x) {
+            const int i1 = e / (n2 * p), i2 = (e / p) % n2, j3 = e % p;
+            Cx<double> v = {0, 0};
+            for (int k = 0; k < p; ++k) cfma(v, rt.S[1][i2 * p + k], B1[((size_t)i1 * p + k) * p + j3]);
+            B2[e] = v;
+        }
+        __syncthreads();
+        Cx<double>* out = chi_part + (size_t)job * rt.nmode;
+        for (int e = threadIdx.x; e < rt.nmode; e += blockDim.x) {
+            const int i1 = e / (n2 * n3), i2 = (e / n3) % n2, i3 = e % n3;
+            Cx<double> v = {0, 0};
+            for (int k = 0; k < p; ++k) cfma(v, rt.S[2][i3 * p + k], B2[((size_t)i1 * n2 + i2) * p + k]);
+            const double ph = -(rt.kax[0][i1] * cm[0] + rt.kax[1][i2] * cm[1] + rt.kax[2][i3] * cm[2]);
+            double sn, cs;
+            sincos(ph, &sn, &cs);
+            out[e] = cmul(v, Cx<double>{cs, sn});
+        }
+    }
+}
+
+// sum over cubes and apply the symbol: uhat[j][k] = sum_a W[k][j][a] sum_m chi_m,a(k)
+__global__ void k_root_apply(int M, int drho, int du, RootTab rt, const Cx<double>* __restrict__ chi_part,
+                             Cx<double>* __restrict__ uhat) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= rt.nmode) return;
+    Cx<double> chi[9];
+    for (int a = 0; a < drho; ++a) {
+        Cx<double> v = {0, 0};
+        for (int m = 0; m < M; ++m) v = cadd(v, chi_part[((size_t)m * drho + a) * rt.nmode + k]);
+        chi[a] = v;
+    }
+    for (int j = 0; j < du; ++j) {
+        Cx<double> v = {0, 0};
+        for (int a = 0; a < drho; ++a) cfma(v, rt.W[((size_t)k * du + j) * drho + a], chi[a]);
+        uhat[(size_t)j * rt.nmode + k] = v;
+    }
+}
+
+// u_m(j) = Re sum_k uhat(k) exp(i k . (c_m + y_j)) + constant, written to the cube's local grid
+template <class T>
+__global__ void k_root_eval(int M, int du, int p, Geo g, RootTab rt, const Cx<double>* __restrict__ uhat,
+                            const double* __restrict__ rho_sum, int drho, T* __restrict__ local,
+                            unsigned char* scratch, size_t per_cta) {
+    const int p2 = p * p, p3 = p2 * p;
+    const int n1 = rt.n1, n2 = rt.n2, n3 = rt.n3;
+    Cx<double>* C2 = reinterpret_cast<Cx<double>*>(scratch + (size_t)blockIdx.x * per_cta);
+    Cx<double>* C1 = C2 + (size_t)n1 * n2 * p;
+    Cx<double>* G = C1 + (size_t)n1 * p2;
+    for (int job = blockIdx.x; job < M * du; job += gridDim.x) {
+        const int m = job / du, j = job % du;
+        int mc[3] = {m % g.M[0], (m / g.M[0]) % g.M[1], m / (g.M[0] * g.M[1])};
+        const double cm[3] = {(mc[0] + 0.5) * g.s, (mc[1] + 0.5) * g.s, (mc[2] + 0.5) * g.s};
+        __syncthreads();
+        for (int e = threadIdx.x; e < rt.nmode; e += blockDim.x) {
+            const int i1 = e / (n2 * n3), i2 = (e / n3) % n2, i3 = e % n3;
+            const double ph = rt.kax[0][i1] * cm[0] + rt.kax[1][i2] * cm[1] + rt.kax[2][i3] * cm[2];
+            double sn, cs;
+            sincos(ph, &sn, &cs);
+            G[e] = cmul(uhat[(size_t)j * rt.nmode + e], Cx<double>{cs, sn});
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < n1 * n2 * p; e += blockDim.x) {      // k3 -> j3
+            const int i12 = e / p, j3 = e % p;
+            Cx<double> v = {0, 0};
+            for (int k = 0; k < n3; ++k) cfma(v, cconj(rt.S[2][k * p + j3]), G[(size_t)i12 * n3 + k]);
+            C2[e] = v;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < n1 * p2; e += blockDim.x) {          // k2 -> j2
+            const int i1 = e / p2, j2 = (e / p) % p, j3 = e % p;
+            Cx<double> v = {0, 0};
+            for (int k = 0; k < n2; ++k) cfma(v, cconj(rt.S[1][k * p + j2]), C2[((size_t)i1 * n2 + k) * p + j3]);
+            C1[e] = v;
+        }
+        __syncthreads();
+        double cst = 0;
+        for (int a = 0; a < drho; ++a) cst += rt.rconst[j * drho + a] * rho_sum[a];
+        T* u = local + ((size_t)m * du + j) * p3;
+        for (int e = threadIdx.x; e < p3; e += blockDim.x) {                // k1 -> j1, real part
+            const int j1 = e / p2, r = e % p2;
+            double v = 0;
+            for (int k = 0; k < n1; ++k) {
+                const Cx<double> f = cconj(rt.S[0][k * p + j1]);
+                const Cx<double> b = C1[(size_t)k * p2 + r];
+                v += f.x * b.x - f.y * b.y;
+            }
+            u[e] = (T)(v + cst);
+        }
+    }
+}
+
+__global__ void k_strength_sums(int64_t N, int drho, const double* __restrict__ rho, double* __restrict__ out) {
+    // out[a] = sum rho_a, out[drho + a] = sum |rho_a|
+    double s[9], sa[9];
+    for (int a = 0; a < drho; ++a) { s[a] = 0; sa[a] = 0; }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        for (int a = 0; a < drho; ++a) {
+            const double v = rho[i * drho + a];
+            s[a] += v;
+            sa[a] += fabs(v);
+        }
+    for (int a = 0; a < drho; ++a) {
+        for (int o = 16; o > 0; o >>= 1) {
+            s[a] += __shfl_down_sync(0xffffffffu, s[a], o);
+            sa[a] += __shfl_down_sync(0xffffffffu, sa[a], o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(out + a, s[a]);
+            atomicAdd(out + drho + a, sa[a]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Residual kernels K_R(x; nu) (App. B, Remark scaling_stokes_split) and their gradients for one
+// source-target pair; the 1/(4 pi) or 1/(8 pi) factor is applied once per target.  q, f, g are
+// Chebyshev series in t = 2 r^2/nu^2 - 1 for (int_0^rho phi)/rho, phi(rho), phi'(rho)/rho.
+template <class T, int K, bool GRAD>
+struct Pair;
+
+template <class T, bool GRAD>
+struct Pair<T, DMK_LAPLACE, GRAD> {
+    static constexpr int DR = 1, DU = 1;
+    __device__ __forceinline__ static void eval(const Tab<T>& tb, const T* fq, const T* ff, T dx, T dy, T dz,
+                                                T r2, T inv_nu, const T* rho, T* u, T* gr) {
+        const T rinv = rsqrt_t(r2);
+        const T t = fma(T(2) * r2, inv_nu * inv_nu, T(-1));
+        const T q = clenshaw(fq, tb.n_q, t);
+        u[0] = fma(rho[0], rinv - T(2) * inv_nu * q, u[0]);
+        if (GRAD) {
+            const T f = clenshaw(ff, tb.n_f, t);
+            const T ri2 = rinv * rinv;
+            const T gfac = rho[0] * (ri2 * rinv + T(2) * inv_nu * (f - q) * ri2);
+            gr[0] = fma(-dx, gfac, gr[0]);
+            gr[1] = fma(-dy, gfac, gr[1]);
+            gr[2] = fma(-dz, gfac, gr[2]);
+        }
+    }
+    __device__ __forceinline__ static float rsqrt_t(float v) { return rsqrtf(v); }
+    __device__ __forceinline__ static double rsqrt_t(double v) { return rsqrt(v); }
+};
+
+template <class T>
+__device__ __forceinline__ T rsqrt_any(T v);
+template <> __device__ __forceinline__ float rsqrt_any<float>(float v) { return rsqrtf(v); }
+template <> __device__ __forceinline__ double rsqrt_any<double>(double v) { return rsqrt(v); }
+
+template <class T, bool GRAD>
+struct Pair<T, DMK_STOKESLET, GRAD> {
+    static constexpr int DR = 3, DU = 3;
+    __device__ __forceinline__ static void eval(const Tab<T>& tb, const T* fit, const T*, T dx, T dy, T dz,
+                                                T r2, T inv_nu, const T* rho, T* u, T* gr) {
+        const T rinv = rsqrt_any(r2), ri2 = rinv * rinv;
+        const T t = fma(T(2) * r2, inv_nu * inv_nu, T(-1));
+        const T q = clenshaw(fit + tb.off_q, tb.n_q, t);
+        const T f = clenshaw(fit + tb.off_f, tb.n_f, t);
+        const T A = rinv - T(2) * inv_nu * (q + f);
+        const T Bc = ri2 * rinv - T(2) * inv_nu * (q - f) * ri2;
+        const T x[3] = {dx, dy, dz};
+        const T xr = dx * rho[0] + dy * rho[1] + dz * rho[2];
+        for (int j = 0; j < 3; ++j) u[j] += A * rho[j] + Bc * xr * x[j];
+        if (GRAD) {
+            const T dq = clenshaw(fit + tb.off_dq, tb.n_dq, t);
+            const T df = clenshaw(fit + tb.off_df, tb.n_df, t);
+            const T r = r2 * rinv;
+            const T dsdr = T(2) * r * inv_nu * inv_nu;
+            const T Ap = -ri2 - T(2) * inv_nu * (dq + df) * dsdr;
+            const T Bp = T(-3) * ri2 * ri2 - T(2) * inv_nu * ((dq - df) * dsdr * ri2 - T(2) * (q - f) * ri2 * rinv);
+            for (int i = 0; i < 3; ++i) {
+                const T xi_r = x[i] * rinv;
+                for (int j = 0; j < 3; ++j)
+                    gr[i * 3 + j] += Ap * xi_r * rho[j] + Bp * xi_r * xr * x[j]
+                                     + Bc * (rho[i] * x[j] + (i == j ? xr : T(0)));
+            }
+        }
+    }
+};
+
+template <class T, bool GRAD>
+struct Pair<T, DMK_STRESSLET, GRAD> {
+    static constexpr int DR = 9, DU = 3;
+    // u_j = Pd v_j/(8 pi) - (3/(4 pi)) Po x_j w, v = Qx + Q^T x + x tr Q, w = x^T Q x,
+    // Pd = T_diag/r^3 = -2 g/nu^3, Po = T_offd/r^5.  Stored as 8 pi * u: Pd v_j - 6 Po x_j w.
+    __device__ __forceinline__ static void eval(const Tab<T>& tb, const T* fit, const T*, T dx, T dy, T dz,
+                                                T r2, T inv_nu, const T* Q, T* u, T* gr) {
+        const T rinv = rsqrt_any(r2), ri2 = rinv * rinv;
+        const T t = fma(T(2) * r2, inv_nu * inv_nu, T(-1));
+        const T q = clenshaw(fit + tb.off_q, tb.n_q, t);
+        const T f = clenshaw(fit + tb.off_f, tb.n_f, t);
+        const T g = clenshaw(fit + tb.off_g, tb.n_g, t);
+        const T in3 = inv_nu * inv_nu * inv_nu;
+        const T Pd = T(-2) * g * in3;
+        const T Po = ri2 * ri2 * rinv - T(2) * inv_nu * (q - f) * ri2 * ri2 - T(2.0 / 3.0) * g * in3 * ri2;
+        const T x[3] = {dx, dy, dz};
+        T Qx[3], QTx[3];
+        for (int j = 0; j < 3; ++j) {
+            Qx[j] = Q[j * 3] * x[0] + Q[j * 3 + 1] * x[1] + Q[j * 3 + 2] * x[2];
+            QTx[j] = Q[j] * x[0] + Q[3 + j] * x[1] + Q[6 + j] * x[2];
+        }
+        const T tr = Q[0] + Q[4] + Q[8];
+        const T w = x[0] * Qx[0] + x[1] * Qx[1] + x[2] * Qx[2];
+        T v[3];
+        for (int j = 0; j < 3; ++j) {
+            v[j] = Qx[j] + QTx[j] + x[j] * tr;
+            u[j] += Pd * v[j] - T(6) * Po * x[j] * w;
+        }
+        if (GRAD) {
+            const T dq = clenshaw(fit + tb.off_dq, tb.n_dq, t);
+            const T df = clenshaw(fit + tb.off_df, tb.n_df, t);
+            const T dg = clenshaw(fit + tb.off_dg, tb.n_dg, t);
+            const T r = r2 * rinv;
+            const T dsdr = T(2) * r * inv_nu * inv_nu;
+            const T Pdp = T(-2) * dg * dsdr * in3;
+            const T Pop = T(-5) * ri2 * ri2 * ri2
+                          - T(2) * inv_nu * ((dq - df) * dsdr * ri2 * ri2 - T(4) * (q - f) * ri2 * ri2 * rinv)
+                          - T(2.0 / 3.0) * in3 * (dg * dsdr * ri2 - T(2) * g * ri2 * rinv);
+            for (int i = 0; i < 3; ++i) {
+                const T xi_r = x[i] * rinv;
+                const T dw = Qx[i] + QTx[i];
+                for (int j = 0; j < 3; ++j) {
+                    const T dv = Q[j * 3 + i] + Q[i * 3 + j] + (i == j ? tr : T(0));
+                    gr[i * 3 + j] += Pdp * xi_r * v[j] + Pd * dv
+                                     - T(6) * (Pop * xi_r * x[j] * w + Po * ((i == j ? w : T(0)) + x[j] * dw));
+                }
+            }
+        }
+    }
+};
+
+template <class T, bool GRAD>
+struct Pair<T, DMK_ROTLET, GRAD> {
+    static constexpr int DR = 3, DU = 3;
+    // u = (tau x x) Oc/(8 pi), Oc = Omega_offd / r^3
+    __device__ __forceinline__ static void eval(const Tab<T>& tb, const T* fit, const T*, T dx, T dy, T dz,
+                                                T r2, T inv_nu, const T* tau, T* u, T* gr) {
+        const T rinv = rsqrt_any(r2), ri2 = rinv * rinv;
+        const T t = fma(T(2) * r2, inv_nu * inv_nu, T(-1));
+        const T q = clenshaw(fit + tb.off_q, tb.n_q, t);
+        const T f = clenshaw(fit + tb.off_f, tb.n_f, t);
+        const T Oc = ri2 * rinv - T(2) * inv_nu * (q - f) * ri2;
+        const T x[3] = {dx, dy, dz};
+        const T c[3] = {tau[1] * dz - tau[2] * dy, tau[2] * dx - tau[0] * dz, tau[0] * dy - tau[1] * dx};
+        for (int j = 0; j < 3; ++j) u[j] += Oc * c[j];
+        if (GRAD) {
+            const T dq = clenshaw(fit + tb.off_dq, tb.n_dq, t);
+            const T df = clenshaw(fit + tb.off_df, tb.n_df, t);
+            const T r = r2 * rinv;
+            const T dsdr = T(2) * r * inv_nu * inv_nu;
+            const T Op = T(-3) * ri2 * ri2 - T(2) * inv_nu * ((dq - df) * dsdr * ri2 - T(2) * (q - f) * ri2 * rinv);
+            for (int i = 0; i < 3; ++i) {
+                const T xi_r = x[i] * rinv;
+                for (int j = 0; j < 3; ++j) {
+                    // d_i (tau x x)_j = eps_jli tau_l
+                    T dc = 0;
+                    const int l = 3 - i - j;
+                    if (i != j) dc = (((j + 1) % 3) == l ? T(1) : T(-1)) * tau[l];
+                    gr[i * 3 + j] += Op * xi_r * c[j] + Oc * dc;
+                }
+            }
+        }
+    }
+};
+
+template <int K> struct KScale { static constexpr double v = (K == DMK_LAPLACE) ? 0.07957747154594767 : 0.039788735772973836; };
+
+// ------------------------------------------------------------------------------------------
+// Leaf stage (Sec. 3.1.5): per target leaf,
+//  (1) Chebyshev coefficients of the local expansion (grid -> coefficients, 3 contractions);
+//  (2) evaluation of the expansion and its gradient at the targets (warp per target, lane = n3);
+//  (3) residual sums over the direct list (thread per target, sources staged in shared memory);
+//  (4) self correction (Sec. 2.4) and the FP64 write-back in input order.
+struct LeafOut {
+    double* pot;
+    double* grad;      // may be null
+    const int* perm;
+    const double* rs;  // sorted strengths (FP64)
+    const double* self_val;   // du x drho at nu = 1
+    const double* self_grad;  // 3 x du x drho at nu = 1
+};
+
+constexpr int kLeafThreads = 128;
+constexpr int kLeafChunk = 128;
+
+template <class T, int K, bool GRAD>
+__global__ void __launch_bounds__(kLeafThreads) k_leaf(int nleaf, const int* __restrict__ leaves, BoxArrays B,
+                                                      Tab<T> tab, Geo g, const T* __restrict__ local,
+                                                      const double* __restrict__ xs, int64_t N,
+                                                      const int* __restrict__ doffs, const DirectEntry* __restrict__ dl,
+                                                      LeafOut out, unsigned char* scratch, size_t per_cta, int use_smem) {
+    using P = Pair<T, K, GRAD>;
+    constexpr int DR = P::DR, DU = P::DU, NR = DU * 4;
+    const int p = tab.p, p2 = p * p, p3 = p2 * p;
+    T* coef = reinterpret_cast<T*>(work_base(scratch, per_cta, use_smem));
+    T* t1 = coef + DU * p3;
+    T* t2 = t1 + p3;
+    __shared__ double res[kLeafChunk][NR];
+    __shared__ T srcx[kLeafThreads][3];
+    __shared__ T srcr[kLeafThreads][DR];
+    __shared__ T tv[kLeafThreads / 32][4][64];
+    __shared__ T fits[256];
+    for (int e = threadIdx.x; e < min(256, tab.n_q + tab.n_f + tab.n_g + tab.n_dq + tab.n_df + tab.n_dg); e += blockDim.x)
+        fits[e] = tab.fit[e];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int li = blockIdx.x; li < nleaf; li += gridDim.x) {
+        const int box = leaves[li];
+        const int l = B.level[box];
+        const double r = g.s / (double)(1 << l), half = 0.5 * r;
+        const double c[3] = {(B.ix[3 * box] + 0.5) * r, (B.ix[3 * box + 1] + 0.5) * r, (B.ix[3 * box + 2] + 0.5) * r};
+        const int st = B.start[box], en = B.end[box];
+        // (1) coefficients
+        for (int j = 0; j < DU; ++j) {
+            const T* u = local + ((size_t)box * DU + j) * p3;
+            __syncthreads();
+            for (int e = threadIdx.x; e < p3; e += blockDim.x) {
+                const int i12 = e / p, n3 = e % p;
+                T v = 0;
+                for (int k = 0; k < p; ++k) v = fma(tab.Cm[n3 * p + k], u[i12 * p + k], v);
+                t1[e] = v;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < p3; e += blockDim.x) {
+                const int i1 = e / p2, n2 = (e / p) % p, n3 = e % p;
+                T v = 0;
+                for (int k = 0; k < p; ++k) v = fma(tab.Cm[n2 * p + k], t1[(i1 * p + k) * p + n3], v);
+                t2[e] = v;
+            }
+            __syncthreads();
+            T* cj = coef + (size_t)j * p3;
+            for (int e = threadIdx.x; e < p3; e += blockDim.x) {
+                const int n1 = e / p2, rr = e % p2;
+                T v = 0;
+                for (int k = 0; k < p; ++k) v = fma(tab.Cm[n1 * p + k], t2[k * p2 + rr], v);
+                cj[e] = v;
+            }
+        }
+        __syncthreads();
+        for (int t0 = st; t0 < en; t0 += kLeafChunk) {
+            const int nt = min(kLeafChunk, en - t0);
+            // (2) Chebyshev evaluation, warp per target
+            for (int tt = warp; tt < nt; tt += nwarp) {
+                const int tg = t0 + tt;
+                T xi[3];
+                for (int a = 0; a < 3; ++a) {
+                    T v = (T)((xs[a * N + tg] - c[a]) / half);
+                    xi[a] = v > T(1) ? T(1) : (v < T(-1) ? T(-1) : v);
+                }
+                // T_n and T_n' for the x and y axes into shared memory (lane n), z kept in registers
+                T Tz0 = 0, Tz1 = 0, dTz0 = 0, dTz1 = 0;
+                {
+                    T Ta[3] = {1, 1, 1}, Tb[3] = {xi[0], xi[1], xi[2]};
+                    T Ua[3] = {1, 1, 1}, Ub[3] = {2 * xi[0], 2 * xi[1], 2 * xi[2]};
+                    for (int n = 0; n < p; ++n) {
+                        T Tn[3], dTn[3];
+                        for (int a = 0; a < 3; ++a) {
+                            if (n == 0) { Tn[a] = 1; dTn[a] = 0; }
+                            else if (n == 1) { Tn[a] = xi[a]; dTn[a] = 1; }
+                            else {
+                                const T Tnew = 2 * xi[a] * Tb[a] - Ta[a];
+                                Ta[a] = Tb[a]; Tb[a] = Tnew;
+                                Tn[a] = Tnew;
+                                // T_n' = n U_{n-1}; U advanced to index n-1
+                                const T Unew = (n - 1 >= 2) ? (2 * xi[a] * Ub[a] - Ua[a]) : Ub[a];
+                                if (n - 1 >= 2) { Ua[a] = Ub[a]; Ub[a] = Unew; }
+                                dTn[a] = (T)n * Unew;
+                            }
+                        }
+                        if (lane == (n & 31)) {
+                            if (n < 32) { Tz0 = Tn[2]; dTz0 = dTn[2]; } else { Tz1 = Tn[2]; dTz1 = dTn[2]; }
+                        }
+                        if (lane == 0) {
+                            tv[warp][0][n] = Tn[0]; tv[warp][1][n] = dTn[0];
+                            tv[warp][2][n] = Tn[1]; tv[warp][3][n] = dTn[1];
+                        }
+                    }
+                }
+                __syncwarp();
+                for (int j = 0; j < DU; ++j) {
+                    const T* cj = coef + (size_t)j * p3;
+                    T S[2] = {0, 0}, Sx[2] = {0, 0}, Sy[2] = {0, 0};
+                    for (int h = 0; h < 2; ++h) {
+                        const int n3 = lane + 32 * h;
+                        if (n3 >= p) continue;
+                        for (int n1 = 0; n1 < p; ++n1) {
+                            T a0 = 0, a1 = 0;
+                            const T* row = cj + (size_t)n1 * p2 + n3;
+                            for (int n2 = 0; n2 < p; ++n2) {
+                                const T cv = row[n2 * p];
+                                a0 = fma(tv[warp][2][n2], cv, a0);
+                                a1 = fma(tv[warp][3][n2], cv, a1);
+                            }
+                            S[h] = fma(tv[warp][0][n1], a0, S[h]);
+                            Sx[h] = fma(tv[warp][1][n1], a0, Sx[h]);
+                            Sy[h] = fma(tv[warp][0][n1], a1, Sy[h]);
+                        }
+                    }
+                    T v = S[0] * Tz0 + S[1] * Tz1;
+                    T gx = Sx[0] * Tz0 + Sx[1] * Tz1;
+                    T gy = Sy[0] * Tz0 + Sy[1] * Tz1;
+                    T gz = S[0] * dTz0 + S[1] * dTz1;
+                    for (int o = 16; o > 0; o >>= 1) {
+                        v += __shfl_xor_sync(0xffffffffu, v, o);
+                        gx += __shfl_xor_sync(0xffffffffu, gx, o);
+                        gy += __shfl_xor_sync(0xffffffffu, gy, o);
+                        gz += __shfl_xor_sync(0xffffffffu, gz, o);
+                    }
+                    if (lane == 0) {
+                        const double sc = 1.0 / half;
+                        res[tt][j] = (double)v;
+                        res[tt][DU + 0 * DU + j] = (double)gx * sc;
+                        res[tt][DU + 1 * DU + j] = (double)gy * sc;
+                        res[tt][DU + 2 * DU + j] = (double)gz * sc;
+                    }
+                }
+                __syncwarp();
+            }
+            __syncthreads();
+            // (3) residual sums: thread per target
+            const int tt = threadIdx.x;
+            const bool act = tt < nt;
+            T xt[3] = {0, 0, 0};
+            if (act)
+                for (int a = 0; a < 3; ++a) xt[a] = (T)(xs[a * N + t0 + tt] - c[a]);
+            T acc[DU], gacc[3 * DU];
+            for (int j = 0; j < DU; ++j) acc[j] = 0;
+            for (int j = 0; j < 3 * DU; ++j) gacc[j] = 0;
+            const int e0 = doffs[li], e1 = doffs[li + 1];
+            for (int e = e0; e < e1; ++e) {
+                const DirectEntry de = dl[e];
+                const int lev = de.code >> 6;
+                const double sh[3] = {(double)(((de.code) & 3) - 1) * g.L[0], (double)(((de.code >> 2) & 3) - 1) * g.L[1],
+                                      (double)(((de.code >> 4) & 3) - 1) * g.L[2]};
+                const T inv_nu = (T)((double)(1 << lev) / g.s);
+                const T nu2 = T(1) / (inv_nu * inv_nu);
+                T pacc[DU], pg[3 * DU];
+                for (int j = 0; j < DU; ++j) pacc[j] = 0;
+                for (int j = 0; j < 3 * DU; ++j) pg[j] = 0;
+                for (int s0 = de.start; s0 < de.end; s0 += kLeafThreads) {
+                    const int ns = min(kLeafThreads, de.end - s0);
+                    __syncthreads();
+                    if (threadIdx.x < ns) {
+                        const int si = s0 + threadIdx.x;
+                        for (int a = 0; a < 3; ++a) srcx[threadIdx.x][a] = (T)(xs[a * N + si] + sh[a] - c[a]);
+                        for (int a = 0; a < DR; ++a) srcr[threadIdx.x][a] = (T)out.rs[(int64_t)si * DR + a];
+                    }
+                    __syncthreads();
+                    if (act) {
+                        for (int k = 0; k < ns; ++k) {
+                            const T dx = xt[0] - srcx[k][0], dy = xt[1] - srcx[k][1], dz = xt[2] - srcx[k][2];
+                            const T r2 = dx * dx + dy * dy + dz * dz;
+                            if (r2 < nu2 && r2 > T(0)) {
+                                P::eval(tab, K == DMK_LAPLACE ? fits + tab.off_q : fits,
+                                        K == DMK_LAPLACE ? fits + tab.off_f : fits, dx, dy, dz, r2, inv_nu,
+                                        srcr[k], pacc, pg);
+                            }
+                        }
+                    }
+                }
+                for (int j = 0; j < DU; ++j) acc[j] += pacc[j];
+                for (int j = 0; j < 3 * DU; ++j) gacc[j] += pg[j];
+            }
+            // (4) self correction and write-back (FP64)
+            if (act) {
+                const int tg = t0 + tt;
+                const int oi = out.perm[tg];
+                const double inv_nuT = 1.0 / r;       // nu at the leaf level = box side
+                const double ks = KScale<K>::v;
+                const double* rt = out.rs + (int64_t)tg * DR;
+                for (int j = 0; j < DU; ++j) {
+                    double v = res[tt][j] + ks * (double)acc[j];
+                    for (int a = 0; a < DR; ++a) v -= out.self_val[j * DR + a] * inv_nuT * rt[a];
+                    out.pot[(int64_t)oi * DU + j] = v;
+                }
+                if (GRAD && out.grad) {
+                    const double in3 = inv_nuT * inv_nuT * inv_nuT;
+                    for (int i = 0; i < 3; ++i)
+                        for (int j = 0; j < DU; ++j) {
+                            double v = res[tt][DU + i * DU + j] + ks * (double)gacc[i * DU + j];
+                            for (int a = 0; a < DR; ++a) v -= out.self_grad[(i * DU + j) * DR + a] * in3 * rt[a];
+                            out.grad[((int64_t)oi * 3 + i) * DU + j] = v;
+                        }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace dmk

@@ -1,0 +1,98 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
+
+Bars (stated for the method's outputs, potentials and target gradients, relative l2 over
+all targets and components): plain FP64 path <= 1e-10, mixed FP32/FP64 path <= 1e-5.  The
+forest must be identical (same box, leaf and level counts) because membership is decided
+on the same integer coordinates.
+"""
+import zlib
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.dmk import evaluate
+from paper_2606_27134_b300 import dmk, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+# id, kernel, D, L, tol, N, n_s, point generator, strength generator
+CASES = [
+    ("cfg1-laplace-3P-1e-12", "laplace", 3, [1, 1, 1], 1e-12, 2000, 250, "uniform", "neutral"),
+    ("laplace-2P-slab", "laplace", 2, [1, 1, 0.25], 1e-6, 3000, 40, "uniform", "uniform"),
+    ("laplace-1P", "laplace", 1, [2, 1, 1], 1e-6, 1200, 30, "mixed", "neutral"),
+    ("laplace-0P", "laplace", 0, [1, 1, 1], 1e-6, 1200, 30, "mixed", "neutral"),
+    ("laplace-3P-two-cubes", "laplace", 3, [1, 1, 2], 1e-9, 1200, 50, "mixed", "neutral"),
+    ("laplace-3P-clustered", "laplace", 3, [1, 1, 1], 1e-6, 3000, 25, "clustered", "balanced"),
+    ("stokeslet-1P", "stokeslet", 1, [4, 1, 1], 1e-6, 1200, 30, "uniform", "stokes"),
+    ("stokeslet-2P", "stokeslet", 2, [1, 1, 1], 1e-6, 1000, 30, "mixed", "stokes"),
+    ("stokeslet-0P", "stokeslet", 0, [1, 1, 1], 1e-6, 800, 30, "mixed", "stokes"),
+    ("stresslet-3P-four-cubes", "stresslet", 3, [1, 1, 4], 1e-6, 1200, 30, "uniform", "stokes"),
+    ("stresslet-2P", "stresslet", 2, [1, 1, 1], 1e-6, 800, 30, "mixed", "stokes"),
+    ("rotlet-3P-four-cubes", "rotlet", 3, [1, 1, 4], 1e-6, 1200, 30, "uniform", "stokes"),
+    ("rotlet-1P", "rotlet", 1, [2, 1, 1], 1e-6, 800, 30, "mixed", "stokes"),
+]
+
+_oracle_cache = {}
+
+
+def make_inputs(case):
+    cid, kernel, D, L, tol, N, n_s, pg, sg = case
+    seed = 1000 + zlib.crc32(cid.encode()) % 1000
+    if pg == "uniform":
+        x = W.uniform_points(N, L, seed)
+    elif pg == "mixed":
+        x = W.mixed_points(N, L, seed, D=D)
+    else:
+        x = W.clustered_points(N, L, seed, n_centers=8, sigma=0.03)
+    if sg == "neutral":
+        rho = W.neutral_charges(N, seed + 1).reshape(N, 1)
+    elif sg == "uniform":
+        rho = W.uniform_charges(N, seed + 1).reshape(N, 1)
+    elif sg == "balanced":
+        rho = W.balanced_charges(N, seed + 1).reshape(N, 1)
+    else:
+        rho = W.stokes_strengths(kernel, N, seed + 1)
+    return x, rho
+
+
+def oracle_result(case):
+    if case[0] not in _oracle_cache:
+        cid, kernel, D, L, tol, N, n_s, pg, sg = case
+        x, rho = make_inputs(case)
+        _oracle_cache[case[0]] = (x, rho, evaluate(kernel, D, L, tol, x, rho, n_s=n_s, grad=True))
+    return _oracle_cache[case[0]]
+
+
+def rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def gpu_eval(case, precision, x, rho):
+    cid, kernel, D, L, tol, N, n_s, pg, sg = case
+    plan = dmk.Plan(kernel, D, L, tol, precision=precision, n_s=n_s)
+    xt = torch.tensor(x, dtype=torch.float64, device="cuda")
+    rt = torch.tensor(rho, dtype=torch.float64, device="cuda")
+    u, g = plan.eval(xt, rt, grad=True)
+    torch.cuda.synchronize()
+    return u.cpu().numpy(), g.cpu().numpy(), plan.stats()
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_fp64_parity(case):
+    x, rho, ref = oracle_result(case)
+    u, g, st = gpu_eval(case, "fp64", x, rho)
+    assert st["n_boxes"] == len(ref.forest.by_id)
+    assert st["n_levels"] == ref.forest.nlevels
+    assert st["n_leaves"] == len(ref.forest.leaves())
+    assert rel(u, ref.u) <= 1e-10, rel(u, ref.u)
+    assert rel(g, ref.grad) <= 1e-10, rel(g, ref.grad)
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_mixed_parity(case):
+    x, rho, ref = oracle_result(case)
+    u, g, st = gpu_eval(case, "mixed", x, rho)
+    assert rel(u, ref.u) <= 1e-5, rel(u, ref.u)
+    assert rel(g, ref.grad) <= 1e-5, rel(g, ref.grad)

@@ -1,0 +1,84 @@
+"""The library's host-side plan tables (C++, dmk_plan_info / dmk_plan_table) against the oracle.
+
+Both sides are FP64 and written independently from the paper (C++ std:: Bessel functions and
+Sturm-bisection PSWF vs scipy and a dense eigensolver), so agreement is at roundoff.
+No device is used.
+"""
+import numpy as np
+import pytest
+
+from oracle.dmk import root_symbol
+from oracle.kernels import Kernel
+from oracle.params import Geometry, c_and_p, n_f, root_modes, TOL_ROWS
+from oracle.pswf import PSWFWindow
+from paper_2606_27134_b300 import dmk
+
+GEOMS = [(3, [1, 1, 1]), (3, [1, 1, 16]), (2, [1, 1, 0.25]), (2, [1, 2, 1]), (1, [8, 1, 1]), (1, [1, 1, 1]),
+         (0, [1, 1, 1]), (0, [0.5, 2, 1])]
+
+
+@pytest.mark.parametrize("kernel", ["laplace", "stokeslet", "stresslet", "rotlet"])
+@pytest.mark.parametrize("tol", TOL_ROWS)
+def test_parameters(kernel, tol):
+    for D, L in GEOMS:
+        info = dmk.plan_info(kernel, D, L, tol)
+        c, p = c_and_p(kernel, tol)
+        g = Geometry(D, L)
+        assert info["c"] == pytest.approx(c, rel=1e-15) and info["p"] == p and info["n_f"] == n_f(c)
+        assert info["M"] == list(g.M) and info["s"] == g.s
+        kk, C, R, dk = root_modes(kernel, g, c)
+        assert info["n_root_modes"] == kk.shape[0]
+        if D < 3:
+            assert info["R"] == pytest.approx(R, rel=1e-15)
+
+
+@pytest.mark.parametrize("kernel", ["laplace", "stokeslet", "stresslet", "rotlet"])
+@pytest.mark.parametrize("D,L", GEOMS, ids=[f"{d}P-{l}" for d, l in GEOMS])
+def test_root_weights(kernel, D, L):
+    tol = 1e-6
+    c, p = c_and_p(kernel, tol)
+    g = Geometry(D, L)
+    K = Kernel(kernel)
+    axes, keep, W, R = root_symbol(K, g, c, PSWFWindow(c))
+    ax = dmk.plan_table(kernel, D, L, tol, 0)
+    n = [len(a) for a in axes]
+    assert len(ax) == sum(n)
+    assert np.allclose(ax, np.concatenate(axes), rtol=1e-15, atol=1e-15)
+    w = dmk.plan_table(kernel, D, L, tol, 1)
+    w = (w[0::2] + 1j * w[1::2]).reshape(n[0], n[1], n[2], K.d_u, K.d_rho)
+    scale = np.max(np.abs(W))
+    assert np.max(np.abs(w - W)) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("kernel", ["laplace", "stokeslet", "stresslet", "rotlet"])
+def test_difference_kernel_table(kernel):
+    """Level-0 plane-wave symbol w_0 D_0-hat(h_0 m) (Eq. Dl_int_discr) on the half grid."""
+    tol = 1e-6
+    c, p = c_and_p(kernel, tol)
+    nf = n_f(c)
+    NF = 2 * nf + 1
+    s = 1.0
+    K = Kernel(kernel)
+    win = PSWFWindow(c)
+    h = 2 * np.pi / (3 * s)
+    m = np.arange(-nf, nf + 1)
+    mm = np.stack(np.meshgrid(m, m, np.arange(0, nf + 1), indexing="ij"), -1).reshape(-1, 3).astype(float)
+    full = (h ** 3 / (2 * np.pi) ** 3) * K.diff_symbol(h * mm, s / 2, s, win)      # (n, du, drho)
+    g = dmk.plan_table(kernel, 3, [1, 1, 1], tol, 2)
+    assert len(g) == NF * NF * (nf + 1)
+    lib = g[:, None, None] * K.op_symbol(mm)          # the library applies op(m) on integer m
+    scale = np.max(np.abs(full))
+    assert np.max(np.abs(lib - full)) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("c_kernel", ["laplace", "stokeslet", "stresslet", "rotlet"])
+@pytest.mark.parametrize("tol", TOL_ROWS)
+def test_window_values(c_kernel, tol):
+    c, p = c_and_p(c_kernel, tol)
+    w = PSWFWindow(c)
+    v = dmk.plan_table(c_kernel, 3, [1, 1, 1], tol, 3)
+    d2phi = np.polynomial.legendre.legval(0.0, np.polynomial.legendre.legder(w.phi_coef, 2))
+    assert v[0] == pytest.approx(w.phi0(), rel=1e-13)
+    assert v[1] == pytest.approx(d2phi, rel=1e-11)
+    assert v[2] == pytest.approx(w.d2phihat0(), rel=1e-11)
+    assert np.allclose(v[3:], w.phihat(0.099 * c * np.arange(11)), rtol=1e-12, atol=1e-15)
