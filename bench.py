@@ -134,6 +134,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--paths", default="mixed,fp64", help="precision paths to time (profiling: mixed)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -201,7 +203,8 @@ def main():
         return ms, stage, wall, (u, g)
 
     prec_results = {}
-    for prec in ("mixed", "fp64"):
+    paths = [p for p in args.paths.split(",") if p]
+    for prec in paths:
         plan = dmk.Plan("laplace", W["D"], W["L"], W["tol"], precision=prec, n_s=W["n_s"],
                         stream=stream.cuda_stream)
         with Clocks(local_rank) as ck:
@@ -213,7 +216,7 @@ def main():
                                   plan=plan)
     # end-to-end through the host-buffer entry point (copies inside the timed region)
     plan_m = prec_results["mixed"]["plan"]
-    ms_e2e, _, _, _ = timed(plan_m, max(3, args.steps // 2), 2, host=True)
+    ms_e2e = [float("nan")] if args.no_e2e else timed(plan_m, max(3, args.steps // 2), 2, host=True)[0]
 
     def agg(v):
         t = torch.tensor([v], dtype=torch.float64, device=dev)
@@ -223,7 +226,7 @@ def main():
 
     mixed = prec_results["mixed"]
     step_ms = agg(statistics.mean(mixed["ms"]))
-    fp64_ms = agg(statistics.mean(prec_results["fp64"]["ms"]))
+    fp64_ms = agg(statistics.mean(prec_results["fp64"]["ms"])) if "fp64" in prec_results else float("nan")
     e2e_ms = agg(statistics.mean(ms_e2e))
     value = world * N / (step_ms / 1e3)
     st = mixed["stats"]

@@ -15,13 +15,14 @@
 #include <vector>
 
 #include "dmk_internal.h"
-#include "dmk_kernels.cuh"
+#include "dmk_fast.cuh"
 
 using namespace dmk;
 
 namespace {
 
 thread_local std::string g_plan_error;
+
 
 struct DevBuf {
     void* p = nullptr;
@@ -65,6 +66,12 @@ namespace {
             plan->err = std::string(#call) + ": " + cudaGetErrorString(e_);       \
             return e_ == cudaErrorMemoryAllocation ? DMK_ERR_OOM : DMK_ERR_CUDA;  \
         }                                                                         \
+    } while (0)
+
+#define CKS(x)                              \
+    do {                                    \
+        dmk_status_t s_ = (x);              \
+        if (s_ != DMK_OK) return s_;        \
     } while (0)
 
 enum BufId {
@@ -119,6 +126,7 @@ dmk_status_t upload_tab(dmk_plan_s* plan, void** mem, Tab<T>& tab, double fit_to
         return o;
     };
     size_t o_nodes = push(P.nodes), o_bary = push(P.bary), o_I = push(P.Ioct), o_C = push(P.Cm);
+    size_t o_A = push(P.Aoct);
     std::vector<double> Eri;
     for (auto& z : P.E) { Eri.push_back(z.real()); Eri.push_back(z.imag()); }
     size_t o_E = push(Eri), o_g = push(P.gdiff);
@@ -139,6 +147,7 @@ dmk_status_t upload_tab(dmk_plan_s* plan, void** mem, Tab<T>& tab, double fit_to
     tab.p = p; tab.nf = P.nf; tab.NF = P.NF; tab.nfh = P.nfh;
     tab.d_rho = P.d_rho; tab.d_u = P.d_u; tab.kernel = P.kernel; tab.level_power = P.level_power;
     tab.nodes = base + o_nodes; tab.bary = base + o_bary; tab.Ioct = base + o_I; tab.Cm = base + o_C;
+    tab.Aoct = base + o_A;
     tab.E = reinterpret_cast<const Cx<T>*>(base + o_E);
     tab.gdiff = base + o_g;
     tab.fit = base + o_fit;
@@ -211,7 +220,8 @@ struct Evaluator {
     Evaluator(dmk_plan_s* pl, Tab<T>& t) : plan(pl), tab(t) {}
 
     dmk_status_t place(size_t bytes, int n, Place& pl, unsigned char** scratch) {
-        const size_t lim = std::min<size_t>(plan->smem_optin, 160 * 1024);
+        // kernels using place() have at most a few hundred bytes of static shared memory
+        const size_t lim = plan->smem_optin > 4096 ? plan->smem_optin - 4096 : 0;
         pl.bytes = bytes;
         pl.grid = (unsigned)std::max(1, std::min<int>(n, 148 * 8));
         if (bytes <= lim) {
@@ -228,9 +238,10 @@ struct Evaluator {
     }
 };
 
+// opt in to `bytes` of dynamic shared memory (without it the limit is 48 KB minus the static part)
 template <class K>
 dmk_status_t set_smem(dmk_plan_s* plan, K kernel, size_t bytes) {
-    if (bytes > 48 * 1024) CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    if (bytes > 0) CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     return DMK_OK;
 }
 
@@ -247,6 +258,25 @@ void launch_anterp(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int* leaves, 
 template <class T, int K>
 dmk_status_t launch_leaf(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int* leaves, BoxArrays B, const T* local,
                          const double* xs, int64_t N, const int* doffs, const DirectEntry* dl, LeafOut lo, bool grad) {
+    constexpr int DR = (K == DMK_LAPLACE) ? 1 : (K == DMK_STRESSLET ? 9 : 3);
+    const size_t dyn = (size_t)kSrcChunk * kLeaf2Threads + (size_t)kSrcChunk * DR * sizeof(T);
+    const unsigned grid = (unsigned)std::max(1, std::min(nleaf, 148 * 16));
+    if (grad) {
+        CKS(set_smem(plan, k_leaf2<T, K, true>, dyn));
+        k_leaf2<T, K, true><<<grid, kLeaf2Threads, dyn, plan->stream>>>(nleaf, leaves, B, tab, plan->geo, local, xs, N,
+                                                                        doffs, dl, lo);
+    } else {
+        CKS(set_smem(plan, k_leaf2<T, K, false>, dyn));
+        k_leaf2<T, K, false><<<grid, kLeaf2Threads, dyn, plan->stream>>>(nleaf, leaves, B, tab, plan->geo, local, xs,
+                                                                         N, doffs, dl, lo);
+    }
+    return DMK_OK;
+}
+
+template <class T, int K>
+dmk_status_t launch_leaf_generic(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int* leaves, BoxArrays B,
+                                 const T* local, const double* xs, int64_t N, const int* doffs, const DirectEntry* dl,
+                                 LeafOut lo, bool grad) {
     const int p3 = tab.p * tab.p * tab.p;
     constexpr int DU = (K == DMK_LAPLACE) ? 1 : 3;
     size_t bytes = (size_t)(DU + 2) * p3 * sizeof(T);
@@ -278,11 +308,6 @@ struct TreeInfo {
     unsigned long long n_pairs = 0;
 };
 
-#define CKS(x)                              \
-    do {                                    \
-        dmk_status_t s_ = (x);              \
-        if (s_ != DMK_OK) return s_;        \
-    } while (0)
 
 template <class T>
 dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pts, const double* rho, double* pot,
@@ -351,7 +376,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     TreeInfo ti;
     std::vector<uint64_t*> cells, Rl;
     std::vector<size_t> cell_cap;
-    // one big arena for per-level cell and R arrays: grows as needed (host tracks offsets)
+    // per-level cell and non-leaf key arrays: stream-ordered allocations released on return
     std::vector<void*> level_mem;
     auto alloc_level = [&](size_t bytes, void** out) -> dmk_status_t {
         void* p = nullptr;
@@ -538,16 +563,36 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         ++launches;
     }
     Evaluator<T> ev(plan, tab);
+    const int pitch = odd_pitch(p);
+    const int fast_threads = ((p * p + 31) / 32) * 32;
+    const int mp = (p <= 20) ? 20 : kMaxPFast;     // register width of the fiber kernels
+    const size_t up2_bytes = (2 * (size_t)mp * mp + 2 * (size_t)p * p * pitch) * sizeof(T);
+    const size_t sh2_bytes = (4 * (size_t)mp * mp + 3 * (size_t)p * p * pitch) * sizeof(T);
+    const bool fast_up = p <= kMaxPFast && up2_bytes <= plan->smem_optin;
+    const bool fast_shift = p <= kMaxPFast && sh2_bytes <= plan->smem_optin;
+    if (fast_up) {
+        if (mp == 20) CKS(set_smem(plan, k_upward2<T, 20>, up2_bytes));
+        else CKS(set_smem(plan, k_upward2<T, kMaxPFast>, up2_bytes));
+    }
     for (int l = nlev - 2; l >= 0; --l) {
         const int n = ti.nR[l];
         if (n == 0) continue;
-        Place pl;
-        unsigned char* scr;
-        size_t bytes = 3 * (size_t)p3 * sizeof(T);
-        CKS(ev.place(bytes, n, pl, &scr));
-        CKS(set_smem(plan, k_upward<T>, pl.use_smem ? bytes : 0));
-        k_upward<T><<<pl.grid, 256, pl.use_smem ? bytes : 0, st>>>(n, nl_box + ti.nl_off[l], B, tab, proxy, scr, bytes,
-                                                                  pl.use_smem);
+        if (fast_up) {
+            if (mp == 20)
+                k_upward2<T, 20><<<std::min(n, 148 * 4), fast_threads, up2_bytes, st>>>(n, nl_box + ti.nl_off[l], B, tab,
+                                                                                         proxy);
+            else
+                k_upward2<T, kMaxPFast><<<std::min(n, 148 * 4), fast_threads, up2_bytes, st>>>(n, nl_box + ti.nl_off[l],
+                                                                                                B, tab, proxy);
+        } else {
+            Place pl;
+            unsigned char* scr;
+            size_t bytes = 3 * (size_t)p3 * sizeof(T);
+            CKS(ev.place(bytes, n, pl, &scr));
+            CKS(set_smem(plan, k_upward<T>, pl.use_smem ? bytes : 0));
+            k_upward<T><<<pl.grid, 256, pl.use_smem ? bytes : 0, st>>>(n, nl_box + ti.nl_off[l], B, tab, proxy, scr,
+                                                                      bytes, pl.use_smem);
+        }
         ++launches;
     }
     rec(2);
@@ -604,16 +649,42 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     }
     rec(5);
     // ---- (8) shift to children, level by level --------------------------------------------
+    if (fast_shift) {
+        if (mp == 20) CKS(set_smem(plan, k_shift2<T, 20>, sh2_bytes));
+        else CKS(set_smem(plan, k_shift2<T, kMaxPFast>, sh2_bytes));
+    }
     for (int l = 0; l < nlev - 1; ++l) {
         const int n = ti.nR[l];
         if (n == 0) continue;
+        if (fast_shift) {
+            if (mp == 20)
+                k_shift2<T, 20><<<std::min(n, 148 * 4), fast_threads, sh2_bytes, st>>>(n, nl_box + ti.nl_off[l], B, tab,
+                                                                                        local);
+            else
+                k_shift2<T, kMaxPFast><<<std::min(n, 148 * 4), fast_threads, sh2_bytes, st>>>(n, nl_box + ti.nl_off[l],
+                                                                                               B, tab, local);
+        } else {
+            Place pl;
+            unsigned char* scr;
+            size_t bytes = 2 * (size_t)p3 * sizeof(T);
+            CKS(ev.place(bytes, n, pl, &scr));
+            CKS(set_smem(plan, k_shift<T>, pl.use_smem ? bytes : 0));
+            k_shift<T><<<pl.grid, 256, pl.use_smem ? bytes : 0, st>>>(n, nl_box + ti.nl_off[l], B, tab, local, scr,
+                                                                     bytes, pl.use_smem);
+        }
+        ++launches;
+    }
+    // leaf grids that did not pass through k_shift2 become Chebyshev coefficients here
+    if (nleaf > 0) {
+        const int root_only = fast_shift ? 1 : 0;
+        const int n = root_only ? std::min(nleaf, Mtot) : nleaf;
         Place pl;
         unsigned char* scr;
         size_t bytes = 2 * (size_t)p3 * sizeof(T);
         CKS(ev.place(bytes, n, pl, &scr));
-        CKS(set_smem(plan, k_shift<T>, pl.use_smem ? bytes : 0));
-        k_shift<T><<<pl.grid, 256, pl.use_smem ? bytes : 0, st>>>(n, nl_box + ti.nl_off[l], B, tab, local, scr, bytes,
-                                                                 pl.use_smem);
+        CKS(set_smem(plan, k_grid2coef<T>, pl.use_smem ? bytes : 0));
+        k_grid2coef<T><<<pl.grid, 256, pl.use_smem ? bytes : 0, st>>>(n, leaves, B.level, root_only, tab, local, scr,
+                                                                      bytes, pl.use_smem);
         ++launches;
     }
     rec(6);

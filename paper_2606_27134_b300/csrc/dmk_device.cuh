@@ -95,6 +95,7 @@ template <class T> struct Tab {
     const T* nodes;
     const T* bary;
     const T* Ioct;       // 2 x p x p
+    const T* Aoct;       // 2 x p x p: parent grid -> child Chebyshev coefficients
     const T* Cm;         // p x p
     const Cx<T>* E;      // NF x p
     const T* gdiff;      // NF x NF x nfh

@@ -27,6 +27,8 @@ struct PlanTables {
     std::vector<double> nodes, bary;
     // child grid from parent grid: Ioct[o][j_child * p + a_parent], o = 0 (lower), 1 (upper)
     std::vector<double> Ioct;
+    // parent grid -> Chebyshev coefficients of a child: Aoct[o][n * p + a] = sum_j Cm[n][j] Ioct[o][j][a]
+    std::vector<double> Aoct;
     // grid values -> Chebyshev coefficients: Cm[n * p + j]
     std::vector<double> Cm;
     // plane waves: E[(m + nf) * p + j] = exp(-i pi/3 m eta_j), m = -nf..nf

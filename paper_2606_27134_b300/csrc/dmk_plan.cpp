@@ -378,6 +378,15 @@ dmk_status_t build_plan_tables(int kernel, int D, const double Lin[3], double to
         for (int j = 0; j < p; ++j)
             T.Cm[n * p + j] = (n == 0 ? 1.0 : 2.0) / p * std::cos(n * (2.0 * j + 1.0) * kPi / (2.0 * p));
 
+    T.Aoct.assign(2 * p * p, 0.0);
+    for (int o = 0; o < 2; ++o)
+        for (int n = 0; n < p; ++n)
+            for (int a = 0; a < p; ++a) {
+                double v = 0;
+                for (int j = 0; j < p; ++j) v += T.Cm[n * p + j] * T.Ioct[(o * p + j) * p + a];
+                T.Aoct[(o * p + n) * p + a] = v;
+            }
+
     // ---- plane waves (Sec. 2.3 Eq. Dl_int_discr): h_l y = (pi/3) m eta at every level ----
     T.E.resize(T.NF * p);
     for (int m = -T.nf; m <= T.nf; ++m)
