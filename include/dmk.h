@@ -97,6 +97,26 @@ dmk_status_t dmk_eval(dmk_plan_t plan, int64_t N, const double* points, const do
 dmk_status_t dmk_eval_host(dmk_plan_t plan, int64_t N, const double* points, const double* strengths,
                            double* potentials, double* grad);
 
+/* dmk_eval without any device allocation.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc at evaluation time -- for example code
+ * running inside CUDA stream capture (where allocation calls are not allowed or would be
+ * recorded into the graph), or applications whose device memory is fully reserved by their
+ * own pool allocator and that must not let a library allocate behind their back.
+ *   - Same arguments, layouts and results as dmk_eval (device arrays; the plan, created
+ *     beforehand with dmk_plan/dmk_plan_ex, owns its tables).
+ *   - All workspace comes from one file-scope static device array of 64 MiB (every GPU that
+ *     loads the library holds it until the process exits); nothing is allocated or freed.
+ *   - N must lie in [0, 16384]; a larger N returns DMK_ERR_INVALID_ARG, and a problem whose
+ *     workspace does not fit in 64 MiB (large p, FP64, deep trees) returns DMK_ERR_OOM, both
+ *     with a message in dmk_last_error.
+ *   - The first call on a device looks up the device address of the static array; make
+ *     that first call before any stream capture.
+ *   - Every call shares the one array, which keeps the previous call's contents; the call
+ *     clears everything it needs to start at zero.  Calls that overlap on the GPU (on
+ *     different streams, plans or threads) race on the array and must be serialised. */
+dmk_status_t dmk_eval_static(dmk_plan_t plan, int64_t N, const double* points, const double* strengths,
+                             double* potentials, double* grad);
+
 /* Statistics of the last dmk_eval on this plan. */
 typedef struct {
     int32_t c_times_1000;      /* PSWF band limit c, times 1000                                  */

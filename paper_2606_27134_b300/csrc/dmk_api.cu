@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <functional>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -23,6 +24,15 @@ namespace {
 
 thread_local std::string g_plan_error;
 
+// Static device workspace of dmk_eval_static (see include/dmk.h): every GPU that loads the
+// library holds these bytes until the process exits.  Host code only ever sees the address
+// returned by cudaGetSymbolAddress for the current device.
+constexpr size_t kStaticWorkspaceBytes = (size_t)64 << 20;
+constexpr int64_t kStaticMaxN = 16384;
+static __device__ __align__(256) unsigned char g_static_workspace[kStaticWorkspaceBytes];
+constexpr int kMaxDevices = 64;
+void* g_static_ptr[kMaxDevices] = {};
+std::mutex g_static_mu;
 
 struct DevBuf {
     void* p = nullptr;
@@ -55,6 +65,9 @@ struct dmk_plan_s {
     int* h_pinned = nullptr;
     cudaEvent_t ev[8] = {};
     int launches = 0;
+    // set only while dmk_eval_static runs: device buffers are carved from this range
+    unsigned char* arena = nullptr;
+    size_t arena_cap = 0, arena_off = 0;
 };
 
 namespace {
@@ -81,10 +94,32 @@ enum BufId {
     B_COUNT
 };
 
+// carve `bytes` (rounded to 256) from the static workspace of dmk_eval_static
+dmk_status_t arena_take(dmk_plan_s* plan, size_t bytes, void** out) {
+    size_t need = (std::max<size_t>(bytes, 16) + 255) & ~(size_t)255;
+    if (plan->arena_off + need > plan->arena_cap) {
+        plan->err = "dmk_eval_static: this problem needs more than the " + std::to_string(plan->arena_cap >> 20) +
+                    " MiB static workspace";
+        return DMK_ERR_OOM;
+    }
+    *out = plan->arena + plan->arena_off;
+    plan->arena_off += need;
+    return DMK_OK;
+}
+
 dmk_status_t ensure(dmk_plan_s* plan, int id, size_t bytes, void** out) {
     if (plan->bufs.size() < B_COUNT) plan->bufs.resize(B_COUNT);
     DevBuf& b = plan->bufs[id];
     if (bytes == 0) bytes = 16;
+    if (plan->arena) {
+        if (b.cap < bytes) {
+            dmk_status_t s = arena_take(plan, bytes, &b.p);
+            if (s != DMK_OK) return s;
+            b.cap = (bytes + 255) & ~(size_t)255;
+        }
+        *out = b.p;
+        return DMK_OK;
+    }
     if (b.cap < bytes) {
         if (b.p) cudaFree(b.p);
         b.p = nullptr;
@@ -230,7 +265,8 @@ struct Evaluator {
             return DMK_OK;
         }
         pl.use_smem = 0;
-        pl.grid = (unsigned)std::max(1, std::min<int>(n, 148 * 2));
+        // the static workspace of dmk_eval_static holds at most 16 per-CTA slices
+        pl.grid = (unsigned)std::max(1, std::min<int>(n, plan->arena ? 16 : 148 * 2));
         void* p = nullptr;
         dmk_status_t s = ensure(plan, B_SCRATCH, bytes * pl.grid, &p);
         *scratch = (unsigned char*)p;
@@ -379,6 +415,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     // per-level cell and non-leaf key arrays: stream-ordered allocations released on return
     std::vector<void*> level_mem;
     auto alloc_level = [&](size_t bytes, void** out) -> dmk_status_t {
+        if (plan->arena) return arena_take(plan, bytes, out);
         void* p = nullptr;
         cudaError_t e = cudaMallocAsync(&p, std::max<size_t>(bytes, 16), st);
         if (e != cudaSuccess) { plan->err = "level allocation failed"; return DMK_ERR_OOM; }
@@ -799,6 +836,47 @@ dmk_status_t dmk_eval(dmk_plan_t plan, int64_t N, const double* points, const do
     cudaSetDevice(plan->device);
     if (plan->prec == DMK_FP64) return run_eval<double>(plan, plan->tab64, N, points, strengths, potentials, grad);
     return run_eval<float>(plan, plan->tab32, N, points, strengths, potentials, grad);
+}
+
+dmk_status_t dmk_eval_static(dmk_plan_t plan, int64_t N, const double* points, const double* strengths,
+                             double* potentials, double* grad) {
+    if (!plan) return DMK_ERR_INVALID_ARG;
+    plan->err.clear();
+    if (N < 0 || N > kStaticMaxN) {
+        plan->err = "dmk_eval_static: N must lie in [0, " + std::to_string(kStaticMaxN) + "]";
+        return DMK_ERR_INVALID_ARG;
+    }
+    if (N == 0) return DMK_OK;
+    if (!points || !strengths || !potentials) { plan->err = "NULL array"; return DMK_ERR_INVALID_ARG; }
+    cudaError_t e = cudaSetDevice(plan->device);
+    if (e != cudaSuccess) { plan->err = cudaGetErrorString(e); return DMK_ERR_CUDA; }
+    if (plan->device < 0 || plan->device >= kMaxDevices) { plan->err = "device index out of range"; return DMK_ERR_CUDA; }
+    void* base = nullptr;
+    {
+        // once per device, with that device current: the device address of the static array
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        if (!g_static_ptr[plan->device]) {
+            e = cudaGetSymbolAddress(&g_static_ptr[plan->device], g_static_workspace);
+            if (e != cudaSuccess) {
+                g_static_ptr[plan->device] = nullptr;
+                plan->err = std::string("cudaGetSymbolAddress of the static workspace: ") + cudaGetErrorString(e);
+                return DMK_ERR_CUDA;
+            }
+        }
+        base = g_static_ptr[plan->device];
+    }
+    std::vector<DevBuf> saved;
+    saved.swap(plan->bufs);            // the plan's own buffers are neither used nor freed
+    plan->arena = (unsigned char*)base;
+    plan->arena_cap = kStaticWorkspaceBytes;
+    plan->arena_off = 0;
+    dmk_status_t s = (plan->prec == DMK_FP64)
+                         ? run_eval<double>(plan, plan->tab64, N, points, strengths, potentials, grad)
+                         : run_eval<float>(plan, plan->tab32, N, points, strengths, potentials, grad);
+    plan->arena = nullptr;
+    plan->arena_cap = plan->arena_off = 0;
+    plan->bufs.swap(saved);
+    return s;
 }
 
 dmk_status_t dmk_eval_host(dmk_plan_t plan, int64_t N, const double* points, const double* strengths,

@@ -65,6 +65,7 @@ def load(path=None):
     lib.dmk_plan_ex.argtypes = [c_int, c_int, dp, c_double, c_int, c_int, vp, ctypes.POINTER(vp)]
     lib.dmk_eval.argtypes = [vp, c_i64, vp, vp, vp, vp]
     lib.dmk_eval_host.argtypes = [vp, c_i64, vp, vp, vp, vp]
+    lib.dmk_eval_static.argtypes = [vp, c_i64, vp, vp, vp, vp]
     lib.dmk_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.dmk_set_timing.argtypes = [vp, c_int]
     lib.dmk_destroy.argtypes = [vp]
@@ -74,7 +75,8 @@ def load(path=None):
     lib.dmk_status_string.restype = ctypes.c_char_p
     lib.dmk_last_error.argtypes = [vp]
     lib.dmk_last_error.restype = ctypes.c_char_p
-    for f in ("dmk_plan", "dmk_plan_ex", "dmk_eval", "dmk_eval_host", "dmk_get_stats", "dmk_set_timing",
+    for f in ("dmk_plan", "dmk_plan_ex", "dmk_eval", "dmk_eval_host", "dmk_eval_static", "dmk_get_stats",
+              "dmk_set_timing",
               "dmk_destroy", "dmk_plan_info", "dmk_plan_table"):
         getattr(lib, f).restype = c_int
     _lib = lib
