@@ -370,7 +370,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     double* d_sums = (double*)((char*)vmisc + 256);          // 2*drho doubles
     int* d_count = (int*)((char*)vmisc + 512);
     unsigned long long* d_pairs = (unsigned long long*)((char*)vmisc + 768);
-    CK(cudaMemsetAsync(vmisc, 0, 1024, st));
+    CK(cudaMemsetAsync(vmisc, 0, 2048, st));
     uint64_t* keys = (uint64_t*)vkeys;
     uint64_t* keys2 = (uint64_t*)vkeys2;
     int* idx = (int*)vidx;
@@ -394,24 +394,12 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     ++launches;
     k_strength_sums<<<std::min<unsigned>(nblk(N, 256), 1024), 256, 0, st>>>(N, drho, rs, d_sums);
     ++launches;
-    // error and neutrality check (host readback)
-    {
-        int herr = 0;
-        double hs[18];
-        CK(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(hs, d_sums, 2 * drho * sizeof(double), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (herr & kErrNonFinite) { plan->err = "non-finite coordinate"; return DMK_ERR_OUT_OF_DOMAIN; }
-        if (herr & kErrDomain) { plan->err = "a free coordinate lies outside [0, L_i)"; return DMK_ERR_OUT_OF_DOMAIN; }
-        if (P.kernel == DMK_LAPLACE && (P.D == 1 || P.D == 2) && std::fabs(hs[0]) > 1e-12 * std::max(hs[1], 1e-300)) {
-            plan->err = "Laplace with D = 1, 2 requires zero net charge";
-            return DMK_ERR_NOT_NEUTRAL;
-        }
-    }
-    // ---- (2) refinement --------------------------------------------------------------
+    // ---- (2) refinement on device counters (one readback per batch of 4 levels) ---------
+    int* d_nR = (int*)((char*)vmisc + 1024);       // non-leaf count per level
+    int* d_nleaf = (int*)((char*)vmisc + 1536);
     TreeInfo ti;
-    std::vector<uint64_t*> cells, Rl;
-    std::vector<size_t> cell_cap;
+    std::vector<uint64_t*> cells(kMaxLevels + 1, nullptr), Rl(kMaxLevels + 1, nullptr);
+    std::vector<int64_t> capC(kMaxLevels + 2, 0), capR(kMaxLevels + 2, 0);
     // per-level cell and non-leaf key arrays: stream-ordered allocations released on return
     std::vector<void*> level_mem;
     auto alloc_level = [&](size_t bytes, void** out) -> dmk_status_t {
@@ -427,77 +415,81 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     struct Guard { std::function<void()> f; ~Guard() { f(); } };
     Guard guard{free_levels};
     void* vflags;
+    // cells with more than n_s points are disjoint: at most N/(n_s+1) split per level
+    const int64_t maxsplit = std::max<int64_t>(1, N / ((int64_t)plan->n_s + 1));
     {
         void* c0;
-        CKS(alloc_level(Mtot * sizeof(uint64_t), &c0));
-        std::vector<uint64_t> h(Mtot);
-        for (int i = 0; i < Mtot; ++i) h[i] = (uint64_t)i;
-        CK(cudaMemcpyAsync(c0, h.data(), Mtot * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
-        cells.push_back((uint64_t*)c0);
-        ti.ncell.push_back(Mtot);
-    }
-    for (int l = 0;; ++l) {
-        const int nc = ti.ncell[l];
-        CKS(ensure(plan, B_FLAGS, (size_t)nc * sizeof(int), &vflags));
-        k_split_flags<<<nblk(nc, 256), 256, 0, st>>>(nc, cells[l], l, pkeys, N, plan->n_s, (int*)vflags);
-        void* r;
-        CKS(alloc_level((size_t)nc * sizeof(uint64_t), &r));
-        size_t tb = 0;
-        cub::DeviceSelect::Flagged(nullptr, tb, cells[l], (int*)vflags, (uint64_t*)r, d_count, nc, st);
-        if (tb > cub_cap) { CKS(ensure(plan, B_CUB, tb, &vcub)); cub_cap = plan->bufs[B_CUB].cap; }
-        CK(cub::DeviceSelect::Flagged(vcub, tb, cells[l], (int*)vflags, (uint64_t*)r, d_count, nc, st));
-        launches += 2;
-        int nr = 0;
-        CK(cudaMemcpyAsync(&nr, d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        Rl.push_back((uint64_t*)r);
-        ti.nR.push_back(nr);
-        if (nr == 0) break;
-        void* cn;
-        CKS(alloc_level((size_t)8 * nr * sizeof(uint64_t), &cn));
-        k_children<<<nblk(8 * nr, 256), 256, 0, st>>>(nr, (uint64_t*)r, (uint64_t*)cn);
+        CKS(alloc_level((size_t)Mtot * sizeof(uint64_t), &c0));
+        k_iota_u64<<<nblk(Mtot, 256), 256, 0, st>>>(Mtot, (uint64_t*)c0);
         ++launches;
-        cells.push_back((uint64_t*)cn);
-        ti.ncell.push_back(8 * nr);
+        cells[0] = (uint64_t*)c0;
+        capC[0] = Mtot;
     }
-    int nlev = (int)ti.ncell.size();
-    // ---- (3) 2:1 balance, finest non-leaf level upward ---------------------------------
-    for (int l = nlev - 2; l >= 1; --l) {
-        const int nr = ti.nR[l];
-        if (nr == 0) continue;
-        const int ncand = 27 * nr + ti.nR[l - 1];
-        void *va, *vb;
-        CKS(alloc_level((size_t)ncand * sizeof(uint64_t), &va));
-        CKS(alloc_level((size_t)ncand * sizeof(uint64_t), &vb));
-        k_balance_cand<<<nblk(27 * nr, 256), 256, 0, st>>>(nr, Rl[l], l, g, (uint64_t*)va);
-        if (ti.nR[l - 1] > 0)
-            CK(cudaMemcpyAsync((uint64_t*)va + 27 * nr, Rl[l - 1], ti.nR[l - 1] * sizeof(uint64_t),
-                               cudaMemcpyDeviceToDevice, st));
-        size_t tb = 0;
-        cub::DeviceRadixSort::SortKeys(nullptr, tb, (uint64_t*)va, (uint64_t*)vb, ncand, 0, 64, st);
-        size_t tb2 = 0;
-        cub::DeviceSelect::Unique(nullptr, tb2, (uint64_t*)vb, (uint64_t*)va, d_count, ncand, st);
-        if (std::max(tb, tb2) > cub_cap) { CKS(ensure(plan, B_CUB, std::max(tb, tb2), &vcub)); cub_cap = plan->bufs[B_CUB].cap; }
-        CK(cub::DeviceRadixSort::SortKeys(vcub, tb, (uint64_t*)va, (uint64_t*)vb, ncand, 0, 64, st));
-        CK(cub::DeviceSelect::Unique(vcub, tb2, (uint64_t*)vb, (uint64_t*)va, d_count, ncand, st));
-        launches += 6;
-        int nu = 0;
-        uint64_t last = 0;
-        CK(cudaMemcpyAsync(&nu, d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (nu > 0) {
-            CK(cudaMemcpy(&last, (uint64_t*)va + nu - 1, sizeof(uint64_t), cudaMemcpyDeviceToHost));
-            if (last == kInvalidKey) --nu;
+    std::vector<int> hnR(kMaxLevels + 1, 0);
+    int nlev = 0;
+    for (int l = 0; nlev == 0;) {
+        const int lend = std::min(l + 4, kBits + 1);
+        for (; l < lend; ++l) {
+            capR[l] = std::min<int64_t>(capC[l], maxsplit);
+            CKS(ensure(plan, B_FLAGS, (size_t)capC[l] * sizeof(int), &vflags));
+            k_split_flags<<<nblk(capC[l], 256), 256, 0, st>>>((int)capC[l], cells[l], l, Mtot,
+                                                            l > 0 ? d_nR + l - 1 : d_nR, pkeys, N, plan->n_s,
+                                                            (int*)vflags);
+            void* r;
+            CKS(alloc_level((size_t)capR[l] * sizeof(uint64_t), &r));
+            size_t tb = 0;
+            cub::DeviceSelect::Flagged(nullptr, tb, cells[l], (int*)vflags, (uint64_t*)r, d_nR + l, (int)capC[l], st);
+            if (tb > cub_cap) { CKS(ensure(plan, B_CUB, tb, &vcub)); cub_cap = plan->bufs[B_CUB].cap; }
+            CK(cub::DeviceSelect::Flagged(vcub, tb, cells[l], (int*)vflags, (uint64_t*)r, d_nR + l, (int)capC[l], st));
+            Rl[l] = (uint64_t*)r;
+            capC[l + 1] = 8 * capR[l];
+            void* cn;
+            CKS(alloc_level((size_t)capC[l + 1] * sizeof(uint64_t), &cn));
+            k_children<<<nblk(capC[l + 1], 256), 256, 0, st>>>((int)capC[l + 1], Rl[l], d_nR + l, (uint64_t*)cn);
+            cells[l + 1] = (uint64_t*)cn;
+            launches += 4;
         }
-        Rl[l - 1] = (uint64_t*)va;
-        ti.nR[l - 1] = nu;
-        // children of the grown R_{l-1}
-        void* cn;
-        CKS(alloc_level((size_t)8 * nu * sizeof(uint64_t), &cn));
-        k_children<<<nblk(8 * nu, 256), 256, 0, st>>>(nu, Rl[l - 1], (uint64_t*)cn);
-        ++launches;
-        cells[l] = (uint64_t*)cn;
-        ti.ncell[l] = 8 * nu;
+        CK(cudaMemcpyAsync(hnR.data(), d_nR, l * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int k = 0; k < l; ++k)
+            if (hnR[k] == 0) { nlev = k + 1; break; }
+        if (nlev == 0 && l > kBits) nlev = kBits + 1;      // level kBits never splits
+    }
+    // ---- (3) 2:1 balance, finest non-leaf level upward, on device counters ----------------
+    {
+        std::vector<int64_t> cR(nlev);
+        for (int k = 0; k < nlev; ++k) cR[k] = hnR[k];
+        for (int l = nlev - 2; l >= 1; --l) {
+            const int64_t capP = cR[l - 1];
+            const int64_t ncand = 27 * cR[l] + capP;
+            void *va, *vb;
+            CKS(alloc_level((size_t)ncand * sizeof(uint64_t), &va));
+            CKS(alloc_level((size_t)ncand * sizeof(uint64_t), &vb));
+            k_balance_cand<<<nblk(ncand, 256), 256, 0, st>>>((int)cR[l], Rl[l], d_nR + l, (int)capP, Rl[l - 1],
+                                                             d_nR + l - 1, l, g, (uint64_t*)va);
+            size_t tb = 0, tb2 = 0;
+            cub::DeviceRadixSort::SortKeys(nullptr, tb, (uint64_t*)va, (uint64_t*)vb, (int)ncand, 0, 64, st);
+            cub::DeviceSelect::Unique(nullptr, tb2, (uint64_t*)vb, (uint64_t*)va, d_nR + l - 1, (int)ncand, st);
+            if (std::max(tb, tb2) > cub_cap) { CKS(ensure(plan, B_CUB, std::max(tb, tb2), &vcub)); cub_cap = plan->bufs[B_CUB].cap; }
+            CK(cub::DeviceRadixSort::SortKeys(vcub, tb, (uint64_t*)va, (uint64_t*)vb, (int)ncand, 0, 64, st));
+            CK(cub::DeviceSelect::Unique(vcub, tb2, (uint64_t*)vb, (uint64_t*)va, d_nR + l - 1, (int)ncand, st));
+            k_trim_invalid<<<1, 1, 0, st>>>((uint64_t*)va, d_nR + l - 1);
+            Rl[l - 1] = (uint64_t*)va;
+            const int64_t maxcells = (3 * (l - 1) < 40) ? ((int64_t)Mtot << (3 * (l - 1))) : ncand;
+            cR[l - 1] = std::min(ncand, maxcells);
+            void* cn;
+            CKS(alloc_level((size_t)8 * cR[l - 1] * sizeof(uint64_t), &cn));
+            k_children<<<nblk(8 * cR[l - 1], 256), 256, 0, st>>>((int)(8 * cR[l - 1]), Rl[l - 1], d_nR + l - 1,
+                                                                 (uint64_t*)cn);
+            cells[l] = (uint64_t*)cn;
+            launches += 9;
+        }
+        CK(cudaMemcpyAsync(hnR.data(), d_nR, nlev * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int k = 0; k < nlev; ++k) {
+            ti.nR.push_back(hnR[k]);
+            ti.ncell.push_back(k == 0 ? Mtot : 8 * hnR[k - 1]);
+        }
     }
     // ---- (4) box arrays -----------------------------------------------------------------
     ti.nlev = nlev;
@@ -554,35 +546,35 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     k_leaf_flags<<<nblk(nb, 256), 256, 0, st>>>(nb, B.child0, B.start, B.end, (int*)vflags, (int*)viota);
     {
         size_t tb = 0;
-        cub::DeviceSelect::Flagged(nullptr, tb, (int*)viota, (int*)vflags, leaves, d_count, nb, st);
+        cub::DeviceSelect::Flagged(nullptr, tb, (int*)viota, (int*)vflags, leaves, d_nleaf, nb, st);
         if (tb > cub_cap) { CKS(ensure(plan, B_CUB, tb, &vcub)); cub_cap = plan->bufs[B_CUB].cap; }
-        CK(cub::DeviceSelect::Flagged(vcub, tb, (int*)viota, (int*)vflags, leaves, d_count, nb, st));
-        CK(cudaMemcpyAsync(&ti.n_leafp, d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cub::DeviceSelect::Flagged(vcub, tb, (int*)viota, (int*)vflags, leaves, d_nleaf, nb, st));
+        launches += 3;
+    }
+    // direct lists: counts for every possible leaf slot, scan, one readback of the totals
+    void *vdo, *vdl;
+    CKS(ensure(plan, B_DOFFS, (size_t)(nb + 1) * sizeof(int), &vdo));
+    int* doffs = (int*)vdo;
+    CK(cudaMemsetAsync(doffs, 0, (nb + 1) * sizeof(int), st));
+    k_direct<false><<<nblk(nb, 128), 128, 0, st>>>(nb, d_nleaf, leaves, B, g, doffs, nullptr, nullptr, d_pairs);
+    {
+        size_t tb = 0;
+        cub::DeviceScan::ExclusiveSum(nullptr, tb, doffs, doffs, nb + 1, st);
+        if (tb > cub_cap) { CKS(ensure(plan, B_CUB, tb, &vcub)); cub_cap = plan->bufs[B_CUB].cap; }
+        CK(cub::DeviceScan::ExclusiveSum(vcub, tb, doffs, doffs, nb + 1, st));
+        int hv[2] = {0, 0};
+        CK(cudaMemcpyAsync(&hv[0], d_nleaf, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&hv[1], doffs + nb, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&ti.n_pairs, d_pairs, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        ti.n_leafp = hv[0];
+        ti.n_entries = hv[1];
         launches += 3;
     }
     const int nleaf = ti.n_leafp;
-    // direct lists
-    void *vdo, *vdl;
-    CKS(ensure(plan, B_DOFFS, (size_t)(nleaf + 1) * sizeof(int), &vdo));
-    int* doffs = (int*)vdo;
-    CK(cudaMemsetAsync(doffs, 0, (nleaf + 1) * sizeof(int), st));
-    k_direct<false><<<nblk(nleaf, 128), 128, 0, st>>>(nleaf, leaves, B, g, doffs, nullptr, nullptr, d_pairs);
-    {
-        size_t tb = 0;
-        cub::DeviceScan::ExclusiveSum(nullptr, tb, doffs, doffs, nleaf + 1, st);
-        if (tb > cub_cap) { CKS(ensure(plan, B_CUB, tb, &vcub)); cub_cap = plan->bufs[B_CUB].cap; }
-        CK(cub::DeviceScan::ExclusiveSum(vcub, tb, doffs, doffs, nleaf + 1, st));
-        int tot = 0;
-        CK(cudaMemcpyAsync(&tot, doffs + nleaf, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(&ti.n_pairs, d_pairs, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        ti.n_entries = tot;
-        launches += 2;
-    }
     CKS(ensure(plan, B_DL, (size_t)std::max<int64_t>(ti.n_entries, 1) * sizeof(DirectEntry), &vdl));
     DirectEntry* dl = (DirectEntry*)vdl;
-    k_direct<true><<<nblk(nleaf, 128), 128, 0, st>>>(nleaf, leaves, B, g, nullptr, doffs, dl, nullptr);
+    k_direct<true><<<nblk(nleaf, 128), 128, 0, st>>>(nleaf, d_nleaf, leaves, B, g, nullptr, doffs, dl, nullptr);
     ++launches;
     rec(1);
     // ---- (5) upward pass ---------------------------------------------------------------
@@ -672,14 +664,14 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         }
         rec(4);
         {
-            size_t bytes = ((size_t)du * nW + (size_t)p * NF * nfh + (size_t)p * p * nfh) * sizeof(Cx<T>);
-            Place pl;
-            unsigned char* scr;
-            CKS(ev.place(bytes, n_nl, pl, &scr));
-            CKS(set_smem(plan, k_pwin<T>, pl.use_smem ? bytes : 0));
-            k_pwin<T><<<pl.grid, 256, pl.use_smem ? bytes : 0, st>>>(n_nl, nl_box, B, tab, W, local, scr, bytes,
-                                                                    pl.use_smem);
-            ++launches;
+        size_t bytes = ((size_t)du * nW + (size_t)p * NF * nfh + (size_t)p * p * nfh) * sizeof(Cx<T>);
+        Place pl;
+        unsigned char* scr;
+        CKS(ev.place(bytes, n_nl, pl, &scr));
+        CKS(set_smem(plan, k_pwin<T>, pl.use_smem ? bytes : 0));
+        k_pwin<T><<<pl.grid, 256, pl.use_smem ? bytes : 0, st>>>(n_nl, nl_box, B, tab, W, local, scr, bytes,
+                                                                pl.use_smem);
+        ++launches;
         }
     } else {
         rec(4);
@@ -746,8 +738,16 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     rec(7);
     CK(cudaGetLastError());
     int herr = 0;
+    double hs[18];
     CK(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hs, d_sums, 2 * drho * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (herr & kErrNonFinite) { plan->err = "non-finite coordinate"; return DMK_ERR_OUT_OF_DOMAIN; }
+    if (herr & kErrDomain) { plan->err = "a free coordinate lies outside [0, L_i)"; return DMK_ERR_OUT_OF_DOMAIN; }
+    if (P.kernel == DMK_LAPLACE && (P.D == 1 || P.D == 2) && std::fabs(hs[0]) > 1e-12 * std::max(hs[1], 1e-300)) {
+        plan->err = "Laplace with D = 1, 2 requires zero net charge";
+        return DMK_ERR_NOT_NEUTRAL;
+    }
     if (herr & kErrIndex) { plan->err = "internal index check failed"; return DMK_ERR_CUDA; }
     // stats
     dmk_stats_t& S = plan->stats;

@@ -87,34 +87,67 @@ __device__ __forceinline__ void cell_range(const uint64_t* pkeys, int64_t N, int
     hi = upper_bound_u64(pkeys, N, last);
 }
 
-// refinement rule (Sec. 3.1.1): split iff the cell holds more than n_s points (and level < cap)
-__global__ void k_split_flags(int ncell, const uint64_t* __restrict__ cells, int level,
-                              const uint64_t* __restrict__ pkeys, int64_t N, int n_s, int* __restrict__ flags) {
+// Refinement and balance run on device-side counters: the host sizes every array by an upper
+// bound and the kernels read the actual counts, so no host round trip is needed per level.
+
+// refinement rule (Sec. 3.1.1): split iff the cell holds more than n_s points (and level < cap).
+// Cells of `level`: ncell = ncell0 at level 0, else 8 * (non-leaf count of level - 1).
+__global__ void k_split_flags(int cap, const uint64_t* __restrict__ cells, int level, int ncell0,
+                              const int* __restrict__ nR_prev, const uint64_t* __restrict__ pkeys, int64_t N,
+                              int n_s, int* __restrict__ flags) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ncell) return;
+    if (i >= cap) return;
+    const int ncell = (level == 0) ? ncell0 : 8 * nR_prev[0];
+    if (i >= ncell) { flags[i] = 0; return; }
     int64_t lo, hi;
     cell_range(pkeys, N, level, cells[i], lo, hi);
     flags[i] = (hi - lo > n_s && level < kBits) ? 1 : 0;
 }
 
-__global__ void k_children(int n, const uint64_t* __restrict__ R, uint64_t* __restrict__ out) {
+// children of the first nR[0] cells of R (8 each, in key order)
+__global__ void k_children(int cap8, const uint64_t* __restrict__ R, const int* __restrict__ nR,
+                           uint64_t* __restrict__ out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 8 * n) return;
+    if (i >= cap8 || (i >> 3) >= nR[0]) return;
     out[i] = (R[i >> 3] << 3) | (uint64_t)(i & 7);
 }
 
 // 2:1 balance, bottom-up: every non-leaf cell at level l needs all its neighbour cells at
-// level l to exist, i.e. their parents (level l-1) must be non-leaf.  Emits those parents.
-__global__ void k_balance_cand(int n, const uint64_t* __restrict__ R, int level, Geo g, uint64_t* __restrict__ out) {
+// level l to exist, i.e. their parents (level l-1) must be non-leaf.  Writes the parents of
+// the 27 neighbours of the first nR[0] cells of R (a neighbour outside a free axis stands in
+// its own cell's parent, already required), then the current non-leaf cells of level l-1,
+// then kInvalidKey padding up to 27 capR + capP entries.
+__global__ void k_balance_cand(int capR, const uint64_t* __restrict__ R, const int* __restrict__ nR, int capP,
+                               const uint64_t* __restrict__ Rp, const int* __restrict__ nRp, int level, Geo g,
+                               uint64_t* __restrict__ out) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 27 * n) return;
-    int i = t / 27, d = t % 27;
-    int dd[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
-    int ix[3], nb[3], sh[3];
-    cell_ix(g, level, R[i], ix);
-    if (!neighbour(g, level, ix, dd, nb, sh)) { out[t] = kInvalidKey; return; }
-    int par[3] = {nb[0] >> 1, nb[1] >> 1, nb[2] >> 1};
-    out[t] = cell_key(g, level - 1, par);
+    if (t >= 27 * capR + capP) return;
+    if (t < 27 * capR) {
+        const int i = t / 27, d = t % 27;
+        if (i >= nR[0]) { out[t] = kInvalidKey; return; }
+        int dd[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+        int ix[3], nb[3], sh[3];
+        cell_ix(g, level, R[i], ix);
+        if (!neighbour(g, level, ix, dd, nb, sh))
+            for (int a = 0; a < 3; ++a) nb[a] = ix[a];
+        int par[3] = {nb[0] >> 1, nb[1] >> 1, nb[2] >> 1};
+        out[t] = cell_key(g, level - 1, par);
+    } else {
+        const int j = t - 27 * capR;
+        out[t] = (j < nRp[0]) ? Rp[j] : kInvalidKey;
+    }
+}
+
+// after sort + unique the padding key (largest) may remain once at the end: drop it
+__global__ void k_trim_invalid(const uint64_t* __restrict__ sorted_unique, int* __restrict__ count) {
+    const int n = count[0];
+    if (n > 0 && sorted_unique[n - 1] == kInvalidKey) count[0] = n - 1;
+}
+
+// level-0 cells: every cube of the tiling, in key (= cube) order
+__global__ void k_iota_u64(int n, uint64_t* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (uint64_t)i;
 }
 
 struct BoxArrays {
@@ -211,11 +244,15 @@ __device__ __forceinline__ int pack_code(const int sh[3], int level) {
 }
 
 template <bool FILL>
-__global__ void k_direct(int nleaf, const int* __restrict__ leaves, BoxArrays B, Geo g,
-                         int* __restrict__ counts, const int* __restrict__ offs, DirectEntry* __restrict__ out,
+__global__ void k_direct(int cap, const int* __restrict__ nleaf_dev, const int* __restrict__ leaves, BoxArrays B,
+                         Geo g, int* __restrict__ counts, const int* __restrict__ offs, DirectEntry* __restrict__ out,
                          unsigned long long* __restrict__ npairs) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nleaf) return;
+    if (i >= cap) return;
+    if (i >= nleaf_dev[0]) {
+        if (!FILL) counts[i] = 0;
+        return;
+    }
     int T = leaves[i];
     int lT = B.level[T];
     int cnt = 0;
