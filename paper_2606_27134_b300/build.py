@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libdmk_b300.so")
 SOURCES = ["dmk_plan.cpp", "dmk_api.cu"]
-HEADERS = ["dmk_internal.h", "dmk_device.cuh", "dmk_tree.cuh", "dmk_kernels.cuh"]
+HEADERS = ["dmk_internal.h", "dmk_device.cuh", "dmk_tree.cuh", "dmk_kernels.cuh", "dmk_fast.cuh"]
 
 
 def nvcc():

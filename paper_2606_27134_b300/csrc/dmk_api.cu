@@ -282,21 +282,36 @@ dmk_status_t set_smem(dmk_plan_s* plan, K kernel, size_t bytes) {
 }
 
 template <class T, int MAXP>
-void launch_anterp(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int* leaves, BoxArrays B, const double* xs,
+dmk_status_t launch_anterp(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int* leaves, BoxArrays B, const double* xs,
                    int64_t N, const double* rs, T* proxy) {
     const int p2 = tab.p * tab.p;
     int threads = std::min(MAXP <= 24 ? 576 : 512, ((p2 + 31) / 32) * 32);
-    size_t sm = 3 * 32 * MAXP * sizeof(T);
+    size_t sm = 3 * (size_t)kAnterpChunk * MAXP * sizeof(T);
+    CKS(set_smem(plan, k_anterp<T, MAXP>, sm));
     unsigned grid = (unsigned)std::max(1, std::min(nleaf, 148 * 8));
     k_anterp<T, MAXP><<<grid, threads, sm, plan->stream>>>(nleaf, leaves, B, xs, N, rs, tab, plan->T.s, proxy);
+    return DMK_OK;
 }
 
 template <class T, int K>
 dmk_status_t launch_leaf(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int* leaves, BoxArrays B, const T* local,
                          const double* xs, int64_t N, const int* doffs, const DirectEntry* dl, LeafOut lo, bool grad) {
     constexpr int DR = (K == DMK_LAPLACE) ? 1 : (K == DMK_STRESSLET ? 9 : 3);
-    const size_t dyn = (size_t)kSrcChunk * kLeaf2Threads + (size_t)kSrcChunk * DR * sizeof(T);
     const unsigned grid = (unsigned)std::max(1, std::min(nleaf, 148 * 16));
+    if (tab.p <= kMaxPFast) {
+        const size_t dyn3 = leaf3_smem<T, DR>(tab.p);
+        if (grad) {
+            CKS(set_smem(plan, k_leaf3<T, K, true>, dyn3));
+            k_leaf3<T, K, true><<<grid, kLeaf3Threads, dyn3, plan->stream>>>(nleaf, leaves, B, tab, plan->geo, local,
+                                                                            xs, N, doffs, dl, lo);
+        } else {
+            CKS(set_smem(plan, k_leaf3<T, K, false>, dyn3));
+            k_leaf3<T, K, false><<<grid, kLeaf3Threads, dyn3, plan->stream>>>(nleaf, leaves, B, tab, plan->geo, local,
+                                                                             xs, N, doffs, dl, lo);
+        }
+        return DMK_OK;
+    }
+    const size_t dyn = (size_t)kSrcChunk * kLeaf2Threads + (size_t)kSrcChunk * DR * sizeof(T);
     if (grad) {
         CKS(set_smem(plan, k_leaf2<T, K, true>, dyn));
         k_leaf2<T, K, true><<<grid, kLeaf2Threads, dyn, plan->stream>>>(nleaf, leaves, B, tab, plan->geo, local, xs, N,
@@ -587,32 +602,31 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     CK(cudaMemsetAsync(local, 0, (size_t)nb * du * p3 * sizeof(T), st));
     launches += 2;
     if (nleaf > 0) {
-        if (p <= 24) launch_anterp<T, 24>(plan, tab, nleaf, leaves, B, xs, N, rs, proxy);
-        else launch_anterp<T, 48>(plan, tab, nleaf, leaves, B, xs, N, rs, proxy);
+        if (p <= 20) CKS((launch_anterp<T, 20>(plan, tab, nleaf, leaves, B, xs, N, rs, proxy)));
+        else if (p <= 24) CKS((launch_anterp<T, 24>(plan, tab, nleaf, leaves, B, xs, N, rs, proxy)));
+        else CKS((launch_anterp<T, 48>(plan, tab, nleaf, leaves, B, xs, N, rs, proxy)));
         ++launches;
     }
     Evaluator<T> ev(plan, tab);
     const int pitch = odd_pitch(p);
     const int fast_threads = ((p * p + 31) / 32) * 32;
     const int mp = (p <= 20) ? 20 : kMaxPFast;     // register width of the fiber kernels
-    const size_t up2_bytes = (2 * (size_t)mp * mp + 2 * (size_t)p * p * pitch) * sizeof(T);
-    const size_t sh2_bytes = (4 * (size_t)mp * mp + 3 * (size_t)p * p * pitch) * sizeof(T);
-    const bool fast_up = p <= kMaxPFast && up2_bytes <= plan->smem_optin;
-    const bool fast_shift = p <= kMaxPFast && sh2_bytes <= plan->smem_optin;
+    // per-child tensor kernels: three operators and two padded p^3 buffers per CTA
+    const size_t ch_bytes = (3 * (size_t)mp * mp + 2 * (size_t)p * p * pitch) * sizeof(T);
+    const bool fast_up = p <= kMaxPFast && ch_bytes <= plan->smem_optin;
+    const bool fast_shift = fast_up;
     if (fast_up) {
-        if (mp == 20) CKS(set_smem(plan, k_upward2<T, 20>, up2_bytes));
-        else CKS(set_smem(plan, k_upward2<T, kMaxPFast>, up2_bytes));
+        if (mp == 20) CKS(set_smem(plan, k_up_cluster<T, 20>, ch_bytes));
+        else CKS(set_smem(plan, k_up_cluster<T, kMaxPFast>, ch_bytes));
     }
     for (int l = nlev - 2; l >= 0; --l) {
         const int n = ti.nR[l];
         if (n == 0) continue;
         if (fast_up) {
             if (mp == 20)
-                k_upward2<T, 20><<<std::min(n, 148 * 4), fast_threads, up2_bytes, st>>>(n, nl_box + ti.nl_off[l], B, tab,
-                                                                                         proxy);
+                k_up_cluster<T, 20><<<8 * n, fast_threads, ch_bytes, st>>>(nl_box + ti.nl_off[l], B, tab, proxy);
             else
-                k_upward2<T, kMaxPFast><<<std::min(n, 148 * 4), fast_threads, up2_bytes, st>>>(n, nl_box + ti.nl_off[l],
-                                                                                                B, tab, proxy);
+                k_up_cluster<T, kMaxPFast><<<8 * n, fast_threads, ch_bytes, st>>>(nl_box + ti.nl_off[l], B, tab, proxy);
         } else {
             Place pl;
             unsigned char* scr;
@@ -663,15 +677,28 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
             ++launches;
         }
         rec(4);
-        {
-        size_t bytes = ((size_t)du * nW + (size_t)p * NF * nfh + (size_t)p * p * nfh) * sizeof(Cx<T>);
-        Place pl;
-        unsigned char* scr;
-        CKS(ev.place(bytes, n_nl, pl, &scr));
-        CKS(set_smem(plan, k_pwin<T>, pl.use_smem ? bytes : 0));
-        k_pwin<T><<<pl.grid, 256, pl.use_smem ? bytes : 0, st>>>(n_nl, nl_box, B, tab, W, local, scr, bytes,
-                                                                pl.use_smem);
-        ++launches;
+        const int mpw = (p <= 20) ? 20 : kMaxPFast;
+        const size_t pw2_bytes =
+            ((size_t)NF * mpw + (size_t)p * NF * nfh + (size_t)p * p * (nfh | 1)) * sizeof(Cx<T>);
+        if (p <= kMaxPFast && pw2_bytes + 512 <= plan->smem_optin) {
+            const unsigned grid = (unsigned)std::min(n_nl, 148 * 4);
+            if (mpw == 20) {
+                CKS(set_smem(plan, k_pwin2<T, 20>, pw2_bytes));
+                k_pwin2<T, 20><<<grid, 384, pw2_bytes, st>>>(n_nl, nl_box, B, tab, W, local);
+            } else {
+                CKS(set_smem(plan, k_pwin2<T, kMaxPFast>, pw2_bytes));
+                k_pwin2<T, kMaxPFast><<<grid, 384, pw2_bytes, st>>>(n_nl, nl_box, B, tab, W, local);
+            }
+            ++launches;
+        } else {
+            size_t bytes = ((size_t)du * nW + (size_t)p * NF * nfh + (size_t)p * p * nfh) * sizeof(Cx<T>);
+            Place pl;
+            unsigned char* scr;
+            CKS(ev.place(bytes, n_nl, pl, &scr));
+            CKS(set_smem(plan, k_pwin<T>, pl.use_smem ? bytes : 0));
+            k_pwin<T><<<pl.grid, 256, pl.use_smem ? bytes : 0, st>>>(n_nl, nl_box, B, tab, W, local, scr, bytes,
+                                                                    pl.use_smem);
+            ++launches;
         }
     } else {
         rec(4);
@@ -679,19 +706,18 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     rec(5);
     // ---- (8) shift to children, level by level --------------------------------------------
     if (fast_shift) {
-        if (mp == 20) CKS(set_smem(plan, k_shift2<T, 20>, sh2_bytes));
-        else CKS(set_smem(plan, k_shift2<T, kMaxPFast>, sh2_bytes));
+        if (mp == 20) CKS(set_smem(plan, k_shift_child<T, 20>, ch_bytes));
+        else CKS(set_smem(plan, k_shift_child<T, kMaxPFast>, ch_bytes));
     }
     for (int l = 0; l < nlev - 1; ++l) {
         const int n = ti.nR[l];
         if (n == 0) continue;
         if (fast_shift) {
             if (mp == 20)
-                k_shift2<T, 20><<<std::min(n, 148 * 4), fast_threads, sh2_bytes, st>>>(n, nl_box + ti.nl_off[l], B, tab,
-                                                                                        local);
+                k_shift_child<T, 20><<<8 * n, fast_threads, ch_bytes, st>>>(nl_box + ti.nl_off[l], B, tab, local);
             else
-                k_shift2<T, kMaxPFast><<<std::min(n, 148 * 4), fast_threads, sh2_bytes, st>>>(n, nl_box + ti.nl_off[l],
-                                                                                               B, tab, local);
+                k_shift_child<T, kMaxPFast><<<8 * n, fast_threads, ch_bytes, st>>>(nl_box + ti.nl_off[l], B, tab,
+                                                                                   local);
         } else {
             Place pl;
             unsigned char* scr;
@@ -703,7 +729,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         }
         ++launches;
     }
-    // leaf grids that did not pass through k_shift2 become Chebyshev coefficients here
+    // leaf grids that did not pass through k_shift_child become Chebyshev coefficients here
     if (nleaf > 0) {
         const int root_only = fast_shift ? 1 : 0;
         const int n = root_only ? std::min(nleaf, Mtot) : nleaf;

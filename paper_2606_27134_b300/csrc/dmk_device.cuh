@@ -104,6 +104,12 @@ template <class T> struct Tab {
 };
 
 // Clenshaw evaluation of sum_k a_k T_k(t)
+// four values loaded as one vector from shared memory
+template <class T>
+struct alignas(4 * sizeof(T)) Quad {
+    T x, y, z, w;
+};
+
 template <class T> __device__ __forceinline__ T clenshaw(const T* a, int n, T t) {
     T b1 = 0, b2 = 0;
     T t2 = t + t;

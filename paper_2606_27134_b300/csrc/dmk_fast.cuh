@@ -1,6 +1,9 @@
-// Register-blocked tensor contractions for the upward pass and the shift to children, and the
-// leaf stage with in-support pair compaction.  These replace the generic versions in
-// dmk_kernels.cuh when p <= kMaxPFast.
+// Kernels for p <= kMaxPFast that replace the generic versions in dmk_kernels.cuh:
+//  * upward pass on 8-CTA thread-block clusters (one CTA per child octant, reduction of the
+//    eight contributions through distributed shared memory) and the shift to children with one
+//    CTA per (parent, child);
+//  * translation + incoming plane-wave transform without materialising the weighted spectrum;
+//  * the leaf stage, one thread per target, with in-support pair compaction.
 //
 // A p x p x p tensor sits in shared memory x-major with an odd row pitch P = p | 1, so that
 // p-long fibers along any axis, one per thread, are read without bank conflicts.  Contracting
@@ -8,6 +11,8 @@
 // and accumulates p outputs in registers, with the operator rows loaded as shared-memory
 // broadcasts.  Operator rows are zero-padded to MAXP so the unrolled loops need no guards.
 #pragma once
+#include <cooperative_groups.h>
+
 #include "dmk_kernels.cuh"
 
 namespace dmk {
@@ -25,19 +30,6 @@ __device__ __forceinline__ void fiber_contract(const T* in, int p, int P, int ax
                                                T (&acc)[MAXP]) {
 #pragma unroll
     for (int j = 0; j < MAXP; ++j) acc[j] = 0;
-    for (int k = 0; k < p; ++k) {
-        const int e = (ax == 2) ? pidx(fa, fb, k, p, P) : (ax == 1) ? pidx(fa, k, fb, p, P) : pidx(k, fa, fb, p, P);
-        const T x = in[e];
-        const T* row = M + k * MAXP;
-#pragma unroll
-        for (int j = 0; j < MAXP; ++j) acc[j] = fma(row[j], x, acc[j]);
-    }
-}
-
-// acc[j] += sum_k M[k][j] * in(fiber, k)
-template <class T, int MAXP>
-__device__ __forceinline__ void fiber_accum(const T* in, int p, int P, int ax, int fa, int fb, const T* M,
-                                            T (&acc)[MAXP]) {
     for (int k = 0; k < p; ++k) {
         const int e = (ax == 2) ? pidx(fa, fb, k, p, P) : (ax == 1) ? pidx(fa, k, fb, p, P) : pidx(k, fa, fb, p, P);
         const T x = in[e];
@@ -67,115 +59,9 @@ __device__ __forceinline__ void load_op(T* Ms, int p, F src) {
     }
 }
 
-template <class T>
-__device__ __forceinline__ void load_padded(T* dst, const T* src, int p, int P) {
-    const int p3 = p * p * p;
-    for (int e = threadIdx.x; e < p3; e += blockDim.x) dst[(e / p) * P + (e % p)] = src[e];
-}
-
-// Upward pass child -> parent (Sec. 3.1.2): parent = sum_o (I_o^T x I_o^T x I_o^T) child_o.
-// Thread f < p^2 owns the x-fiber (i1, i2) of the parent across all eight children.
-template <class T, int MAXP>
-__global__ void __launch_bounds__(576) k_upward2(int n, const int* __restrict__ nl_box, BoxArrays B, Tab<T> tab,
-                                                 T* __restrict__ proxy) {
-    const int p = tab.p, p2 = p * p, p3 = p2 * p, P = odd_pitch(p), drho = tab.d_rho;
-    T* Mo = reinterpret_cast<T*>(dsmem);                 // 2 x MAXP x MAXP
-    T* bufA = Mo + 2 * MAXP * MAXP;
-    T* bufB = bufA + p * p * P;
-    // rows k = child node, columns = parent index: I[o][k][c]
-    for (int o = 0; o < 2; ++o)
-        load_op<T, MAXP>(Mo + o * MAXP * MAXP, p, [&](int k, int j) { return tab.Ioct[(o * p + k) * p + j]; });
-    const int f = threadIdx.x;
-    const bool own = f < p2;
-    const int fa = own ? f / p : 0, fb = own ? f % p : 0;
-    for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
-        const int Pb = nl_box[bi];
-        const int c0 = B.child0[Pb];
-        for (int a = 0; a < drho; ++a) {
-            T acc[MAXP];
-#pragma unroll
-            for (int j = 0; j < MAXP; ++j) acc[j] = 0;
-            for (int o = 0; o < 8; ++o) {
-                __syncthreads();
-                load_padded(bufA, proxy + ((size_t)(c0 + o) * drho + a) * p3, p, P);
-                __syncthreads();
-                T t[MAXP];
-                if (own) {
-                    fiber_contract<T, MAXP>(bufA, p, P, 2, fa, fb, Mo + ((o >> 2) & 1) * MAXP * MAXP, t);
-                    fiber_store<T, MAXP>(bufB, p, P, 2, fa, fb, t);
-                }
-                __syncthreads();
-                if (own) {
-                    fiber_contract<T, MAXP>(bufB, p, P, 1, fa, fb, Mo + ((o >> 1) & 1) * MAXP * MAXP, t);
-                    fiber_store<T, MAXP>(bufA, p, P, 1, fa, fb, t);
-                }
-                __syncthreads();
-                if (own) fiber_accum<T, MAXP>(bufA, p, P, 0, fa, fb, Mo + (o & 1) * MAXP * MAXP, acc);
-            }
-            if (own) {
-                T* out = proxy + ((size_t)Pb * drho + a) * p3;
-#pragma unroll
-                for (int j = 0; j < MAXP; ++j)
-                    if (j < p) out[(j * p + fa) * p + fb] = acc[j];
-            }
-        }
-    }
-}
-
-// Shift to children (Sec. 3.1.4).  Non-leaf child: local += (I_o x I_o x I_o) parent.  Leaf child:
-// local += (A_o x A_o x A_o) parent, A_o = C I_o, i.e. the Chebyshev coefficients of the child's
-// interpolant, which is what the leaf stage evaluates.
-template <class T, int MAXP>
-__global__ void __launch_bounds__(576) k_shift2(int n, const int* __restrict__ nl_box, BoxArrays B, Tab<T> tab,
-                                                T* __restrict__ local) {
-    const int p = tab.p, p2 = p * p, p3 = p2 * p, P = odd_pitch(p), du = tab.d_u;
-    T* MI = reinterpret_cast<T*>(dsmem);                 // 2 x MAXP x MAXP, rows k = parent index
-    T* MA = MI + 2 * MAXP * MAXP;
-    T* bufP = MA + 2 * MAXP * MAXP;
-    T* t1 = bufP + p * p * P;
-    T* t2 = t1 + p * p * P;
-    for (int o = 0; o < 2; ++o) {
-        load_op<T, MAXP>(MI + o * MAXP * MAXP, p, [&](int k, int j) { return tab.Ioct[(o * p + j) * p + k]; });
-        load_op<T, MAXP>(MA + o * MAXP * MAXP, p, [&](int k, int j) { return tab.Aoct[(o * p + j) * p + k]; });
-    }
-    const int f = threadIdx.x;
-    const bool own = f < p2;
-    const int fa = own ? f / p : 0, fb = own ? f % p : 0;
-    for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
-        const int Pb = nl_box[bi];
-        const int c0 = B.child0[Pb];
-        for (int j = 0; j < du; ++j) {
-            __syncthreads();
-            load_padded(bufP, local + ((size_t)Pb * du + j) * p3, p, P);
-            for (int o = 0; o < 8; ++o) {
-                const int C = c0 + o;
-                const T* Mbase = (B.child0[C] < 0) ? MA : MI;
-                __syncthreads();
-                T t[MAXP];
-                if (own) {
-                    fiber_contract<T, MAXP>(bufP, p, P, 2, fa, fb, Mbase + ((o >> 2) & 1) * MAXP * MAXP, t);
-                    fiber_store<T, MAXP>(t1, p, P, 2, fa, fb, t);
-                }
-                __syncthreads();
-                if (own) {
-                    fiber_contract<T, MAXP>(t1, p, P, 1, fa, fb, Mbase + ((o >> 1) & 1) * MAXP * MAXP, t);
-                    fiber_store<T, MAXP>(t2, p, P, 1, fa, fb, t);
-                }
-                __syncthreads();
-                if (own) {
-                    fiber_contract<T, MAXP>(t2, p, P, 0, fa, fb, Mbase + (o & 1) * MAXP * MAXP, t);
-                    T* out = local + ((size_t)C * du + j) * p3;
-#pragma unroll
-                    for (int jj = 0; jj < MAXP; ++jj)
-                        if (jj < p) out[(jj * p + fa) * p + fb] += t[jj];
-                }
-            }
-        }
-    }
-}
 
 // Grid values -> Chebyshev coefficients in place, for leaves whose grid did not come through
-// k_shift2 (root-level leaves, and every leaf when p > kMaxPFast).
+// k_shift_child (root-level leaves, and every leaf when p > kMaxPFast).
 template <class T>
 __global__ void k_grid2coef(int n, const int* __restrict__ boxes, const int* __restrict__ level, int root_only,
                             Tab<T> tab, T* __restrict__ local, unsigned char* scratch, size_t per_cta, int use_smem) {
@@ -442,6 +328,557 @@ __global__ void __launch_bounds__(kLeaf2Threads) k_leaf2(int nleaf, const int* _
                         }
                 }
             }
+        }
+    }
+}
+
+}  // namespace dmk
+
+namespace dmk {
+
+// V(m) = sum over non-leaf colleagues C at offset d of exp(-i (2 pi/3) m.d) W_C(m), then
+// component j of op(m) V (App. B symbols on the integer wave vector; see apply_op).  DR is the
+// strength dimension, a template argument so that V stays in registers.
+template <class T, int DR>
+__device__ __forceinline__ Cx<T> pw_gather_op(int kernel, int j, int m1, int m2, int m3, size_t e, size_t nW,
+                                             int ncol, const int* col_nl, const int* col_d,
+                                             const Cx<T>* __restrict__ W) {
+    const T c3 = T(-0.5), s3 = T(-0.86602540378443864676);   // exp(-i 2 pi/3)
+    // colleagues in batches of KB with all loads of a batch issued before the first FMA, so
+    // that each thread keeps several L2 requests in flight
+    constexpr int KB = DR == 1 ? 9 : (DR == 3 ? 3 : 1);
+    Cx<T> V[DR == 1 ? 1 : 9];
+#pragma unroll
+    for (int a = 0; a < DR; ++a) V[a] = {0, 0};
+    for (int k0 = 0; k0 < ncol; k0 += KB) {
+        Cx<T> w[KB][DR];
+#pragma unroll
+        for (int kk = 0; kk < KB; ++kk) {
+            const int k = k0 + kk;
+            const Cx<T>* Wc = W + (size_t)col_nl[k < ncol ? k : 0] * DR * nW + e;
+#pragma unroll
+            for (int a = 0; a < DR; ++a) w[kk][a] = (k < ncol) ? Wc[(size_t)a * nW] : Cx<T>{0, 0};
+        }
+#pragma unroll
+        for (int kk = 0; kk < KB; ++kk) {
+            const int d = col_d[k0 + kk < ncol ? k0 + kk : 0];
+            const int dot = m1 * (d % 3 - 1) + m2 * ((d / 3) % 3 - 1) + m3 * (d / 9 - 1);
+            const int r = ((dot % 3) + 3) % 3;
+            const Cx<T> ph = (r == 0) ? Cx<T>{1, 0} : (r == 1 ? Cx<T>{c3, s3} : Cx<T>{c3, -s3});
+#pragma unroll
+            for (int a = 0; a < DR; ++a) cfma(V[a], ph, w[kk][a]);
+        }
+    }
+    if (DR == 1) return V[0];
+    const T mv[3] = {(T)m1, (T)m2, (T)m3};
+    Cx<T> out[3];
+    apply_op<T>(kernel, mv, V, out);
+    return j == 0 ? out[0] : (j == 1 ? out[1] : out[2]);
+}
+
+// Translation + difference-kernel symbol + incoming transform (Sec. 3.1.4, Eq. Dl_int_discr)
+// without materialising the weighted spectrum.  Stage A: thread per spectral column (m2, m3)
+// gathers V(m1, m2, m3) from the non-leaf colleagues, applies 2^(a l) g(m) op(m), and contracts
+// m1 -> j1 into p register accumulators.  Stage B: thread per (j1, m3), m2 -> j2.  Stage C:
+// thread per (j1, j2), m3 -> j3 with the half-spectrum weights (1 for m3 = 0, 2 otherwise).
+template <class T, int MAXP>
+__global__ void __launch_bounds__(384) k_pwin2(int n, const int* __restrict__ nl_box, BoxArrays B, Tab<T> tab,
+                                               const Cx<T>* __restrict__ W, T* __restrict__ local) {
+    const int p = tab.p, p2 = p * p, p3 = p2 * p, drho = tab.d_rho, du = tab.d_u;
+    const int nf = tab.nf, NF = tab.NF, nfh = tab.nfh, nW = NF * NF * nfh;
+    const int pm3 = nfh | 1;                                   // odd pitch of the m3 axis in B1
+    Cx<T>* F = reinterpret_cast<Cx<T>*>(dsmem);                // NF x MAXP: conj(E), zero-padded
+    Cx<T>* B2 = F + NF * MAXP;                                 // p x NF x nfh
+    Cx<T>* B1 = B2 + p * NF * nfh;                             // p x p x pm3
+    __shared__ int ncol;
+    __shared__ int col_nl[27];
+    __shared__ int col_d[27];
+    for (int e = threadIdx.x; e < NF * MAXP; e += blockDim.x) {
+        const int m = e / MAXP, j = e % MAXP;
+        F[e] = (j < p) ? cconj(tab.E[m * p + j]) : Cx<T>{0, 0};
+    }
+    for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
+        const int box = nl_box[bi];
+        const int l = B.level[box];
+        const T scale = (T)ldexp(1.0, tab.level_power * l);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int k = 0;
+            for (int d = 0; d < 27; ++d) {
+                const int C = B.coll[box * 27 + d];
+                if (C >= 0 && B.nl[C] >= 0) { col_nl[k] = B.nl[C]; col_d[k] = d; ++k; }
+            }
+            ncol = k;
+        }
+        __syncthreads();
+        for (int j = 0; j < du; ++j) {
+            // stage A
+            for (int c = threadIdx.x; c < NF * nfh; c += blockDim.x) {
+                const int i2 = c / nfh, m3 = c % nfh;
+                Cx<T> acc[MAXP];
+#pragma unroll
+                for (int q = 0; q < MAXP; ++q) acc[q] = {0, 0};
+                for (int i1 = 0; i1 < NF; ++i1) {
+                    const int e = (i1 * NF + i2) * nfh + m3;
+                    const int m1 = i1 - nf, m2 = i2 - nf;
+                    Cx<T> o;
+                    if (drho == 1)
+                        o = pw_gather_op<T, 1>(tab.kernel, j, m1, m2, m3, e, nW, ncol, col_nl, col_d, W);
+                    else if (drho == 3)
+                        o = pw_gather_op<T, 3>(tab.kernel, j, m1, m2, m3, e, nW, ncol, col_nl, col_d, W);
+                    else
+                        o = pw_gather_op<T, 9>(tab.kernel, j, m1, m2, m3, e, nW, ncol, col_nl, col_d, W);
+                    const T gs = scale * tab.gdiff[e];
+                    o = {gs * o.x, gs * o.y};
+                    const Cx<T>* Fr = F + i1 * MAXP;
+#pragma unroll
+                    for (int q = 0; q < MAXP; ++q) cfma(acc[q], Fr[q], o);
+                }
+#pragma unroll
+                for (int q = 0; q < MAXP; ++q)
+                    if (q < p) B2[(q * NF + i2) * nfh + m3] = acc[q];
+            }
+            __syncthreads();
+            // stage B
+            for (int c = threadIdx.x; c < p * nfh; c += blockDim.x) {
+                const int j1 = c / nfh, m3 = c % nfh;
+                Cx<T> acc[MAXP];
+#pragma unroll
+                for (int q = 0; q < MAXP; ++q) acc[q] = {0, 0};
+                for (int i2 = 0; i2 < NF; ++i2) {
+                    const Cx<T> b = B2[(j1 * NF + i2) * nfh + m3];
+                    const Cx<T>* Fr = F + i2 * MAXP;
+#pragma unroll
+                    for (int q = 0; q < MAXP; ++q) cfma(acc[q], Fr[q], b);
+                }
+#pragma unroll
+                for (int q = 0; q < MAXP; ++q)
+                    if (q < p) B1[(j1 * p + q) * pm3 + m3] = acc[q];
+            }
+            __syncthreads();
+            // stage C
+            T* u = local + ((size_t)box * du + j) * p3;
+            for (int c = threadIdx.x; c < p2; c += blockDim.x) {
+                T acc[MAXP];
+#pragma unroll
+                for (int q = 0; q < MAXP; ++q) acc[q] = 0;
+                for (int m3 = 0; m3 < nfh; ++m3) {
+                    const Cx<T> b = B1[c * pm3 + m3];
+                    const T wgt = (m3 == 0) ? T(1) : T(2);
+                    const Cx<T> bw = {wgt * b.x, wgt * b.y};
+                    const Cx<T>* Fr = F + (nf + m3) * MAXP;
+#pragma unroll
+                    for (int q = 0; q < MAXP; ++q) acc[q] = fma(Fr[q].x, bw.x, fma(-Fr[q].y, bw.y, acc[q]));
+                }
+#pragma unroll
+                for (int q = 0; q < MAXP; ++q)
+                    if (q < p) u[c * p + q] += acc[q];
+            }
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace dmk
+
+namespace dmk {
+
+// ------------------------------------------------------------------------------------------
+// Leaf stage for p <= kMaxPFast (Sec. 3.1.5, Sec. 2.4), one thread per target throughout.
+// (2) the leaf's Chebyshev coefficients c[n1][n2][n3] (x, y, z) are staged in shared memory with
+//     the n3 rows padded to a multiple of four; each thread keeps T_n3(z), T'_n3(z) in registers,
+//     runs the y and x recurrences on the fly, and reads coefficient rows as broadcast vectors;
+// (3) residual sums: sources stream through shared memory in chunks of kSrcChunk as
+//     (x, y, z, nu^2) and (x_lo, y_lo, z_lo, 1/nu) vectors; the support test r^2 < nu^2 on the
+//     leading parts fills a per-thread byte queue, and only queued sources are evaluated, with
+//     two-float differences in the FP32 path and r > 0 excluding the target itself;
+// (4) self correction and the FP64 write-back in input order.
+constexpr int kLeaf3Threads = 128;
+
+template <class T, int K, bool GRAD>
+__global__ void __launch_bounds__(kLeaf3Threads) k_leaf3(int nleaf, const int* __restrict__ leaves, BoxArrays B,
+                                                        Tab<T> tab, Geo g, const T* __restrict__ coef,
+                                                        const double* __restrict__ xs, int64_t N,
+                                                        const int* __restrict__ doffs,
+                                                        const DirectEntry* __restrict__ dl, LeafOut out) {
+    using Pr = Pair<T, K, GRAD>;
+    using Q4 = Quad<T>;
+    constexpr int DR = Pr::DR, DU = Pr::DU, MQ = kMaxPFast / 4;
+    constexpr bool kTwo = sizeof(T) == 4;
+    const int p = tab.p, p2 = p * p, p3 = p2 * p, PQ = (p + 3) & ~3, ng = PQ >> 2;
+    __shared__ Q4 sA[kSrcChunk];   // source offset from the leaf centre (leading part), nu^2
+    __shared__ Q4 sB[kSrcChunk];   // trailing parts (FP32 path), 1/nu
+    __shared__ T fits[256];
+    // dynamic: the byte queue q[kSrcChunk][threads], aliased by the coefficient block during
+    // step (2); then the staged strengths
+    extern __shared__ __align__(32) unsigned char dsm3[];
+    const size_t qbytes = max((size_t)kSrcChunk * kLeaf3Threads, (size_t)p2 * PQ * sizeof(T));
+    unsigned char (*q)[kLeaf3Threads] = reinterpret_cast<unsigned char (*)[kLeaf3Threads]>(dsm3);
+    T* cs = reinterpret_cast<T*>(dsm3);
+    T (*sr)[DR] = reinterpret_cast<T (*)[DR]>(dsm3 + ((qbytes + 15) & ~(size_t)15));
+    for (int e = threadIdx.x; e < min(256, tab.n_q + tab.n_f + tab.n_g + tab.n_dq + tab.n_df + tab.n_dg);
+         e += blockDim.x)
+        fits[e] = tab.fit[e];
+    const int tt = threadIdx.x;
+    for (int li = blockIdx.x; li < nleaf; li += gridDim.x) {
+        const int box = leaves[li];
+        const int l = B.level[box];
+        const double r = g.s / (double)(1 << l), half = 0.5 * r;
+        const double c[3] = {(B.ix[3 * box] + 0.5) * r, (B.ix[3 * box + 1] + 0.5) * r, (B.ix[3 * box + 2] + 0.5) * r};
+        const int st = B.start[box], en = B.end[box];
+        for (int t0 = st; t0 < en; t0 += kLeaf3Threads) {
+            const int nt = min(kLeaf3Threads, en - t0);
+            const bool act = tt < nt;
+            // target offsets from the leaf centre
+            double xd[3] = {0, 0, 0};
+            if (act)
+                for (int a = 0; a < 3; ++a) xd[a] = xs[a * N + t0 + tt] - c[a];
+            // (2) Chebyshev evaluation
+            T ev[DU], eg[3 * DU];
+            {
+                T xi[3];
+                for (int a = 0; a < 3; ++a) {
+                    const T v = (T)(xd[a] / half);
+                    xi[a] = v > T(1) ? T(1) : (v < T(-1) ? T(-1) : v);
+                }
+                T Tz[kMaxPFast], dTz[kMaxPFast];
+                {
+                    T tm2 = 0, tm1 = 1, um2 = 0, um1 = 1;   // T_{n-2}, T_{n-1}, U_{n-2}, U_{n-1}
+#pragma unroll
+                    for (int n = 0; n < kMaxPFast; ++n) {
+                        T tn, dn;
+                        if (n == 0) { tn = 1; dn = 0; }
+                        else if (n == 1) { tn = xi[2]; dn = 1; tm2 = 1; tm1 = xi[2]; um2 = 1; um1 = 2 * xi[2]; }
+                        else {
+                            tn = 2 * xi[2] * tm1 - tm2;
+                            dn = (T)n * um1;
+                            const T un = 2 * xi[2] * um1 - um2;
+                            tm2 = tm1; tm1 = tn; um2 = um1; um1 = un;
+                        }
+                        Tz[n] = n < p ? tn : T(0);
+                        dTz[n] = n < p ? dn : T(0);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < DU; ++j) {
+                    __syncthreads();
+                    const T* cj = coef + ((size_t)box * DU + j) * p3;
+                    for (int e = tt; e < p2 * PQ; e += kLeaf3Threads) {
+                        const int n12 = e / PQ, n3 = e - n12 * PQ;
+                        cs[e] = n3 < p ? cj[n12 * p + n3] : T(0);
+                    }
+                    __syncthreads();
+                    T S = 0, Sx = 0, Sy = 0, Sz = 0;
+                    if (act) {
+                        T xm2 = 0, xm1 = 1, xu2 = 0, xu1 = 1;
+                        for (int n1 = 0; n1 < p; ++n1) {
+                            T tx, dtx;
+                            if (n1 == 0) { tx = 1; dtx = 0; }
+                            else if (n1 == 1) { tx = xi[0]; dtx = 1; xm2 = 1; xm1 = xi[0]; xu2 = 1; xu1 = 2 * xi[0]; }
+                            else {
+                                tx = 2 * xi[0] * xm1 - xm2;
+                                dtx = (T)n1 * xu1;
+                                const T un = 2 * xi[0] * xu1 - xu2;
+                                xm2 = xm1; xm1 = tx; xu2 = xu1; xu1 = un;
+                            }
+                            T b0 = 0, b1 = 0, b2 = 0;
+                            T ym2 = 0, ym1 = 1, yu2 = 0, yu1 = 1;
+                            const Q4* rows = reinterpret_cast<const Q4*>(cs + (size_t)n1 * p * PQ);
+                            for (int n2 = 0; n2 < p; ++n2) {
+                                T ty, dty;
+                                if (n2 == 0) { ty = 1; dty = 0; }
+                                else if (n2 == 1) { ty = xi[1]; dty = 1; ym2 = 1; ym1 = xi[1]; yu2 = 1; yu1 = 2 * xi[1]; }
+                                else {
+                                    ty = 2 * xi[1] * ym1 - ym2;
+                                    dty = (T)n2 * yu1;
+                                    const T un = 2 * xi[1] * yu1 - yu2;
+                                    ym2 = ym1; ym1 = ty; yu2 = yu1; yu1 = un;
+                                }
+                                const Q4* row = rows + n2 * ng;
+                                T a0 = 0, a1 = 0, a0b = 0, a1b = 0;
+#pragma unroll
+                                for (int gq = 0; gq < MQ; ++gq) {
+                                    if (gq < ng) {
+                                        const Q4 cv = row[gq];
+                                        a0 = fma(cv.x, Tz[4 * gq], a0);
+                                        a0b = fma(cv.y, Tz[4 * gq + 1], a0b);
+                                        a0 = fma(cv.z, Tz[4 * gq + 2], a0);
+                                        a0b = fma(cv.w, Tz[4 * gq + 3], a0b);
+                                        if (GRAD) {
+                                            a1 = fma(cv.x, dTz[4 * gq], a1);
+                                            a1b = fma(cv.y, dTz[4 * gq + 1], a1b);
+                                            a1 = fma(cv.z, dTz[4 * gq + 2], a1);
+                                            a1b = fma(cv.w, dTz[4 * gq + 3], a1b);
+                                        }
+                                    }
+                                }
+                                a0 += a0b;
+                                b0 = fma(ty, a0, b0);
+                                if (GRAD) {
+                                    a1 += a1b;
+                                    b1 = fma(dty, a0, b1);
+                                    b2 = fma(ty, a1, b2);
+                                }
+                            }
+                            S = fma(tx, b0, S);
+                            if (GRAD) {
+                                Sx = fma(dtx, b0, Sx);
+                                Sy = fma(tx, b1, Sy);
+                                Sz = fma(tx, b2, Sz);
+                            }
+                        }
+                    }
+                    const T sc = (T)(1.0 / half);
+                    ev[j] = S;
+                    eg[0 * DU + j] = Sx * sc;
+                    eg[1 * DU + j] = Sy * sc;
+                    eg[2 * DU + j] = Sz * sc;
+                }
+            }
+            // (3) residual sums with in-support compaction
+            T xt[3], xtl[3] = {0, 0, 0};
+            for (int a = 0; a < 3; ++a) {
+                xt[a] = (T)xd[a];
+                if (kTwo) xtl[a] = (T)(xd[a] - (double)xt[a]);
+            }
+            double accd[DU], gaccd[3 * DU];
+#pragma unroll
+            for (int j = 0; j < DU; ++j) accd[j] = 0;
+#pragma unroll
+            for (int j = 0; j < 3 * DU; ++j) gaccd[j] = 0;
+            int e = doffs[li];
+            const int e1 = doffs[li + 1];
+            int eo = 0;
+            while (e < e1) {
+                __syncthreads();
+                int filled = 0;
+                while (filled < kSrcChunk && e < e1) {
+                    const DirectEntry de = dl[e];
+                    const int take = min(de.end - de.start - eo, kSrcChunk - filled);
+                    const int lev = de.code >> 6;
+                    const double sh0 = (double)(((de.code) & 3) - 1) * g.L[0];
+                    const double sh1 = (double)(((de.code >> 2) & 3) - 1) * g.L[1];
+                    const double sh2 = (double)(((de.code >> 4) & 3) - 1) * g.L[2];
+                    const double inv = (double)(1 << lev) / g.s;
+                    const T nu2 = (T)(1.0 / (inv * inv));
+                    for (int k = tt; k < take; k += kLeaf3Threads) {
+                        const int si = de.start + eo + k, slot = filled + k;
+                        const double vx = xs[si] + sh0 - c[0], vy = xs[N + si] + sh1 - c[1],
+                                     vz = xs[2 * N + si] + sh2 - c[2];
+                        Q4 a, b;
+                        a.x = (T)vx; a.y = (T)vy; a.z = (T)vz; a.w = nu2;
+                        b.x = kTwo ? (T)(vx - (double)a.x) : T(0);
+                        b.y = kTwo ? (T)(vy - (double)a.y) : T(0);
+                        b.z = kTwo ? (T)(vz - (double)a.z) : T(0);
+                        b.w = (T)inv;
+                        sA[slot] = a;
+                        sB[slot] = b;
+                        for (int a2 = 0; a2 < DR; ++a2) sr[slot][a2] = (T)out.rs[(int64_t)si * DR + a2];
+                    }
+                    filled += take;
+                    eo += take;
+                    if (eo == de.end - de.start) { ++e; eo = 0; }
+                }
+                __syncthreads();
+                if (act) {
+                    int cnt = 0;
+                    for (int k = 0; k < filled; ++k) {
+                        const Q4 a = sA[k];
+                        const T dx = xt[0] - a.x, dy = xt[1] - a.y, dz = xt[2] - a.z;
+                        const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                        if (r2 < a.w) q[cnt++][tt] = (unsigned char)k;
+                    }
+                    T acc[DU], gacc[3 * DU];
+#pragma unroll
+                    for (int j = 0; j < DU; ++j) acc[j] = 0;
+#pragma unroll
+                    for (int j = 0; j < 3 * DU; ++j) gacc[j] = 0;
+                    for (int i = 0; i < cnt; ++i) {
+                        const int k = q[i][tt];
+                        const Q4 a = sA[k], b = sB[k];
+                        T dx = xt[0] - a.x, dy = xt[1] - a.y, dz = xt[2] - a.z;
+                        if (kTwo) {
+                            dx += xtl[0] - b.x;
+                            dy += xtl[1] - b.y;
+                            dz += xtl[2] - b.z;
+                        }
+                        const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                        if (r2 > T(0))
+                            Pr::eval(tab, K == DMK_LAPLACE ? fits + tab.off_q : fits,
+                                     K == DMK_LAPLACE ? fits + tab.off_f : fits, dx, dy, dz, r2, b.w, sr[k], acc,
+                                     gacc);
+                    }
+#pragma unroll
+                    for (int j = 0; j < DU; ++j) accd[j] += (double)acc[j];
+#pragma unroll
+                    for (int j = 0; j < 3 * DU; ++j) gaccd[j] += (double)gacc[j];
+                }
+            }
+            __syncthreads();
+            // (4) self correction and write-back (FP64)
+            if (act) {
+                const int tg = t0 + tt;
+                const int oi = out.perm[tg];
+                const double inv_nuT = 1.0 / r;
+                const double ks = KScale<K>::v;
+                const double* rt = out.rs + (int64_t)tg * DR;
+#pragma unroll
+                for (int j = 0; j < DU; ++j) {
+                    double v = (double)ev[j] + ks * accd[j];
+                    for (int a = 0; a < DR; ++a) v -= out.self_val[j * DR + a] * inv_nuT * rt[a];
+                    out.pot[(int64_t)oi * DU + j] = v;
+                }
+                if (GRAD && out.grad) {
+                    const double in3 = inv_nuT * inv_nuT * inv_nuT;
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+#pragma unroll
+                        for (int j = 0; j < DU; ++j) {
+                            double v = (double)eg[i * DU + j] + ks * gaccd[i * DU + j];
+                            for (int a = 0; a < DR; ++a) v -= out.self_grad[(i * DU + j) * DR + a] * in3 * rt[a];
+                            out.grad[((int64_t)oi * 3 + i) * DU + j] = v;
+                        }
+                }
+            }
+        }
+    }
+}
+
+// dynamic shared memory of k_leaf3
+template <class T, int DR>
+inline size_t leaf3_smem(int p) {
+    const int PQ = (p + 3) & ~3;
+    const size_t qbytes = std::max((size_t)kSrcChunk * kLeaf3Threads, (size_t)p * p * PQ * sizeof(T));
+    return ((qbytes + 15) & ~(size_t)15) + (size_t)kSrcChunk * DR * sizeof(T);
+}
+
+}  // namespace dmk
+
+namespace dmk {
+
+// p^3 tensor from global memory into the padded shared layout, KB independent loads in flight
+// per thread
+template <class T, int KB = 8>
+__device__ __forceinline__ void load_padded_batched(T* dst, const T* __restrict__ src, int p, int P) {
+    const int p3 = p * p * p;
+    for (int e0 = threadIdx.x; e0 < p3; e0 += KB * blockDim.x) {
+        T v[KB];
+#pragma unroll
+        for (int u = 0; u < KB; ++u) {
+            const int e = e0 + u * blockDim.x;
+            v[u] = e < p3 ? src[e] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < KB; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < p3) dst[(e / p) * P + (e % p)] = v[u];
+        }
+    }
+}
+
+// Upward pass child -> parent (Sec. 3.1.2) on thread-block clusters: cluster = parent box,
+// CTA rank o = child octant.  Each CTA applies (I_o^T x I_o^T x I_o^T) to its child's proxy
+// charges (three fiber contractions in shared memory), then the eight CTAs reduce the eight
+// contributions through distributed shared memory in the fixed order o = 0..7, each CTA
+// writing one eighth of the parent's tensor.
+template <class T, int MAXP>
+__global__ void __cluster_dims__(8, 1, 1) __launch_bounds__((MAXP * MAXP + 31) / 32 * 32)
+    k_up_cluster(const int* __restrict__ nl_box, BoxArrays B, Tab<T> tab, T* __restrict__ proxy) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int o = (int)cl.block_rank();
+    const int bi = blockIdx.x >> 3;
+    const int p = tab.p, p2 = p * p, p3 = p2 * p, P = odd_pitch(p), drho = tab.d_rho;
+    T* Mo = reinterpret_cast<T*>(dsmem);                 // 3 x MAXP x MAXP, one per axis
+    T* bufA = Mo + 3 * MAXP * MAXP;
+    T* bufB = bufA + p * p * P;
+    for (int ax = 0; ax < 3; ++ax) {
+        const int bit = (o >> ax) & 1;
+        load_op<T, MAXP>(Mo + ax * MAXP * MAXP, p, [&](int k, int j) { return tab.Ioct[(bit * p + k) * p + j]; });
+    }
+    const int f = threadIdx.x;
+    const bool own = f < p2;
+    const int fa = own ? f / p : 0, fb = own ? f % p : 0;
+    const int Pb = nl_box[bi];
+    const int C = B.child0[Pb] + o;
+    const int lo = (o * p3) >> 3, hi = ((o + 1) * p3) >> 3;
+    for (int a = 0; a < drho; ++a) {
+        __syncthreads();
+        load_padded_batched<T>(bufA, proxy + ((size_t)C * drho + a) * p3, p, P);
+        __syncthreads();
+        T t[MAXP];
+        if (own) {
+            fiber_contract<T, MAXP>(bufA, p, P, 2, fa, fb, Mo + 2 * MAXP * MAXP, t);
+            fiber_store<T, MAXP>(bufB, p, P, 2, fa, fb, t);
+        }
+        __syncthreads();
+        if (own) {
+            fiber_contract<T, MAXP>(bufB, p, P, 1, fa, fb, Mo + 1 * MAXP * MAXP, t);
+            fiber_store<T, MAXP>(bufA, p, P, 1, fa, fb, t);
+        }
+        __syncthreads();
+        if (own) fiber_contract<T, MAXP>(bufA, p, P, 0, fa, fb, Mo, t);
+        // this child's contribution, unpadded, in bufB (free since the second contraction)
+        if (own) {
+#pragma unroll
+            for (int j = 0; j < MAXP; ++j)
+                if (j < p) bufB[(j * p + fa) * p + fb] = t[j];
+        }
+        cl.sync();
+        T* out = proxy + ((size_t)Pb * drho + a) * p3;
+        for (int e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+            T sum = 0;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) sum += cl.map_shared_rank(bufB, r)[e];
+            out[e] = sum;
+        }
+        cl.sync();
+    }
+}
+
+// Shift to children (Sec. 3.1.4), one CTA per (parent, child octant): non-leaf child
+// local += (I_o x I_o x I_o) parent; leaf child local += (A_o x A_o x A_o) parent, A_o = C I_o,
+// the Chebyshev coefficients of the child's interpolant.
+template <class T, int MAXP>
+__global__ void __launch_bounds__((MAXP * MAXP + 31) / 32 * 32) k_shift_child(const int* __restrict__ nl_box, BoxArrays B, Tab<T> tab,
+                                                     T* __restrict__ local) {
+    const int o = blockIdx.x & 7;
+    const int bi = blockIdx.x >> 3;
+    const int p = tab.p, p2 = p * p, p3 = p2 * p, P = odd_pitch(p), du = tab.d_u;
+    T* Mo = reinterpret_cast<T*>(dsmem);                 // 3 x MAXP x MAXP, rows k = parent index
+    T* bufA = Mo + 3 * MAXP * MAXP;
+    T* bufB = bufA + p * p * P;
+    const int Pb = nl_box[bi];
+    const int C = B.child0[Pb] + o;
+    const T* src = (B.child0[C] < 0) ? tab.Aoct : tab.Ioct;
+    for (int ax = 0; ax < 3; ++ax) {
+        const int bit = (o >> ax) & 1;
+        load_op<T, MAXP>(Mo + ax * MAXP * MAXP, p, [&](int k, int j) { return src[(bit * p + j) * p + k]; });
+    }
+    const int f = threadIdx.x;
+    const bool own = f < p2;
+    const int fa = own ? f / p : 0, fb = own ? f % p : 0;
+    for (int j = 0; j < du; ++j) {
+        __syncthreads();
+        load_padded_batched<T>(bufA, local + ((size_t)Pb * du + j) * p3, p, P);
+        __syncthreads();
+        T t[MAXP];
+        if (own) {
+            fiber_contract<T, MAXP>(bufA, p, P, 2, fa, fb, Mo + 2 * MAXP * MAXP, t);
+            fiber_store<T, MAXP>(bufB, p, P, 2, fa, fb, t);
+        }
+        __syncthreads();
+        if (own) {
+            fiber_contract<T, MAXP>(bufB, p, P, 1, fa, fb, Mo + 1 * MAXP * MAXP, t);
+            fiber_store<T, MAXP>(bufA, p, P, 1, fa, fb, t);
+        }
+        __syncthreads();
+        if (own) {
+            fiber_contract<T, MAXP>(bufA, p, P, 0, fa, fb, Mo, t);
+            T* out = local + ((size_t)C * du + j) * p3;
+#pragma unroll
+            for (int jj = 0; jj < MAXP; ++jj)
+                if (jj < p) out[(jj * p + fa) * p + fb] += t[jj];
         }
     }
 }

@@ -36,14 +36,40 @@ __device__ __forceinline__ void lagrange_row(T xi, const T* nodes, const T* bary
 
 // ------------------------------------------------------------------------------------------
 // Leaf anterpolation (Sec. 3.1.2): proxy(j1,j2,j3) = sum_s rho_s l_j1(xi_s) l_j2(eta_s) l_j3(zeta_s).
-// Thread per (j2, j3) pair holding the p values over j1 in registers.
+// Sources in chunks of kAnterpChunk: one thread per (source, axis) builds the Lagrange row
+// (barycentric form, zero-padded to MAXP, the x row scaled by the strength); then one thread per
+// (j2, j3) accumulates the p values over j1 in registers, reading the x rows as vectors.
+constexpr int kAnterpChunk = 128;
+
+template <class T>
+__device__ __forceinline__ void lagrange_row_padded(T xi, const T* nodes, const T* bary, int p, int maxp, T scale,
+                                                    T* out) {
+    T den = 0;
+    int hit = -1;
+    for (int a = 0; a < p; ++a) {
+        const T d = xi - nodes[a];
+        if (d == T(0)) hit = a;
+        const T w = bary[a] / d;
+        out[a] = w;
+        den += w;
+    }
+    if (hit >= 0) {
+        for (int a = 0; a < p; ++a) out[a] = (a == hit) ? scale : T(0);
+    } else {
+        const T f = scale / den;
+        for (int a = 0; a < p; ++a) out[a] *= f;
+    }
+    for (int a = p; a < maxp; ++a) out[a] = T(0);
+}
+
 template <class T, int MAXP>
 __global__ void __launch_bounds__(MAXP <= 24 ? 576 : 512) k_anterp(int nleaf, const int* __restrict__ leaves, BoxArrays B,
                                                  const double* __restrict__ xs, int64_t N,
                                                  const double* __restrict__ rs, Tab<T> tab, double s,
                                                  T* __restrict__ proxy) {
+    static_assert(MAXP % 4 == 0, "rows are read as four-vectors");
     const int p = tab.p, p2 = p * p, drho = tab.d_rho;
-    constexpr int PC = 32;
+    constexpr int PC = kAnterpChunk;
     T* lx = reinterpret_cast<T*>(dsmem);
     T* ly = lx + PC * MAXP;
     T* lz = ly + PC * MAXP;
@@ -65,22 +91,25 @@ __global__ void __launch_bounds__(MAXP <= 24 ? 576 : 512) k_anterp(int nleaf, co
                     const int ns = min(PC, en - s0);
                     __syncthreads();
                     for (int u = threadIdx.x; u < 3 * ns; u += blockDim.x) {
-                        const int pt = u / 3, ax = u % 3;
+                        const int ax = u / ns, pt = u - ax * ns;
                         const double xi = (xs[ax * N + s0 + pt] - c[ax]) / half;
                         T* row = (ax == 0 ? lx : (ax == 1 ? ly : lz)) + pt * MAXP;
-                        lagrange_row<T>((T)xi, tab.nodes, tab.bary, p, row);
-                        if (ax == 0) {
-                            const T wgt = (T)rs[(int64_t)(s0 + pt) * drho + a];
-                            for (int j = 0; j < p; ++j) row[j] *= wgt;
-                        }
+                        const T wgt = (ax == 0) ? (T)rs[(int64_t)(s0 + pt) * drho + a] : T(1);
+                        lagrange_row_padded<T>((T)xi, tab.nodes, tab.bary, p, MAXP, wgt, row);
                     }
                     __syncthreads();
                     if (active) {
                         for (int pt = 0; pt < ns; ++pt) {
                             const T t = ly[pt * MAXP + jb] * lz[pt * MAXP + jc];
+                            const Quad<T>* rx = reinterpret_cast<const Quad<T>*>(lx + pt * MAXP);
 #pragma unroll
-                            for (int j = 0; j < MAXP; ++j)
-                                if (j < p) acc[j] = fma(lx[pt * MAXP + j], t, acc[j]);
+                            for (int q = 0; q < MAXP / 4; ++q) {
+                                const Quad<T> v = rx[q];
+                                acc[4 * q] = fma(v.x, t, acc[4 * q]);
+                                acc[4 * q + 1] = fma(v.y, t, acc[4 * q + 1]);
+                                acc[4 * q + 2] = fma(v.z, t, acc[4 * q + 2]);
+                                acc[4 * q + 3] = fma(v.w, t, acc[4 * q + 3]);
+                            }
                         }
                     }
                 }
