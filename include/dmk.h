@@ -161,7 +161,12 @@ dmk_status_t dmk_plan_info(dmk_kernel_t k, int D, const double L[3], double tol,
  *   which = 2: level-0 difference-kernel scalar w_0 h_0^ord G_0(|h_0 m|) on the half grid,
  *              index ((m1 + n_f) N_F + (m2 + n_f)) (n_f + 1) + m3 (Sec. 2.3, Eq. Dl_int_discr);
  *   which = 3: PSWF window values phi(0), phi''(0), phi-hat''(0), then phi-hat at k = 0.099 c j,
- *              j = 0..10 (Sec. 2.2, Eqs. wfunc_pswf, wfunchat). */
+ *              j = 0..10 (Sec. 2.2, Eqs. wfunc_pswf, wfunchat);
+ *   which = 4: the FP32 path's piecewise cubic residual tables (App. B residual functions, the
+ *              "precomputed polynomial approximations"): series q, f, g, dq/ds, df/ds, dg/ds of
+ *              s = r^2/nu^2, with q(s) = int_0^r phi / r, f(s) = phi(r), g(s) = phi'(r)/r; 256
+ *              intervals each, 4 coefficients per interval, index ((series 256 + i) 4 + c);
+ *              X(s) = c0 + u (c1 + u (c2 + u c3)) with u = 256 s - i. */
 dmk_status_t dmk_plan_table(dmk_kernel_t k, int D, const double L[3], double tol, int which, double* out,
                             int64_t cap, int64_t* n);
 

@@ -90,7 +90,7 @@ namespace {
 enum BufId {
     B_W, B_KEYS, B_KEYS2, B_IDX, B_IDX2, B_XS, B_RS, B_CUB, B_FLAGS, B_CNT,
     B_CELLS, B_R, B_CAND, B_BOXU64, B_BOXINT, B_LEAVES, B_DOFFS, B_DL, B_NLBOX,
-    B_PROXY, B_LOCAL, B_PW, B_SCRATCH, B_CHI, B_UHAT, B_MISC, B_DEVPTS, B_DEVRHO, B_DEVPOT, B_DEVGRAD,
+    B_PROXY, B_LOCAL, B_PW, B_SCRATCH, B_CHI, B_UHAT, B_MISC, B_DEVPTS, B_DEVRHO, B_DEVPOT, B_DEVGRAD, B_XF, B_VW,
     B_COUNT
 };
 
@@ -137,6 +137,49 @@ dmk_status_t ensure(dmk_plan_s* plan, int id, size_t bytes, void** out) {
     return DMK_OK;
 }
 
+// value and t-derivative of sum_n a_n T_n(t) (T_n' = n U_{n-1})
+void cheb_value_deriv(const std::vector<double>& a, double t, double& v, double& d) {
+    double tm1 = 1, tm2 = 0, um1 = 1, um2 = 0;   // T_{n-1}, T_{n-2}, U_{n-1}, U_{n-2}
+    v = 0;
+    d = 0;
+    for (size_t n = 0; n < a.size(); ++n) {
+        double tn, un;
+        if (n == 0) { tn = 1; un = 1; }
+        else if (n == 1) { tn = t; un = 2 * t; tm2 = 1; um2 = 1; }
+        else { tn = 2 * t * tm1 - tm2; un = 2 * t * um1 - um2; tm2 = tm1; um2 = um1; }
+        v += a[n] * tn;
+        if (n > 0) d += a[n] * (double)n * (n == 1 ? 1.0 : um1);
+        tm1 = tn;
+        um1 = un;
+    }
+}
+
+// Piecewise cubic Hermite tables of the six residual series q, f, g, q', f', g' on s in [0, 1]
+// (App. B residual functions as precomputed polynomial approximations): kHermNT intervals, the
+// interval i holding (c0, c1, c2, c3) with X = c0 + u (c1 + u (c2 + u c3)), u = s kHermNT - i,
+// matching the FP64 series value and s-derivative at both interval ends.
+std::vector<double> herm_tables(const PlanTables& P) {
+    const std::vector<double>* ser[6] = {&P.fit_q, &P.fit_f, &P.fit_g, &P.fit_dq, &P.fit_df, &P.fit_dg};
+    std::vector<double> out((size_t)6 * kHermNT * 4, 0.0);
+    std::vector<double> v(kHermNT + 1), d(kHermNT + 1);
+    for (int k = 0; k < 6; ++k) {
+        if (ser[k]->empty()) continue;
+        for (int j = 0; j <= kHermNT; ++j) {
+            const double sj = (double)j / kHermNT;
+            cheb_value_deriv(*ser[k], 2 * sj - 1, v[j], d[j]);
+            d[j] *= 2.0 / kHermNT;      // d/du = (d/ds) / kHermNT, d/ds = 2 d/dt
+        }
+        for (int i = 0; i < kHermNT; ++i) {
+            double* c = &out[((size_t)k * kHermNT + i) * 4];
+            c[0] = v[i];
+            c[1] = d[i];
+            c[2] = 3 * (v[i + 1] - v[i]) - 2 * d[i] - d[i + 1];
+            c[3] = 2 * (v[i] - v[i + 1]) + d[i] + d[i + 1];
+        }
+    }
+    return out;
+}
+
 template <class T>
 dmk_status_t upload_tab(dmk_plan_s* plan, void** mem, Tab<T>& tab, double fit_tol) {
     const PlanTables& P = plan->T;
@@ -174,6 +217,13 @@ dmk_status_t upload_tab(dmk_plan_s* plan, void** mem, Tab<T>& tab, double fit_to
         for (double x : fits[i]) h.push_back((T)x);
         acc += fits[i].size();
     }
+    while (h.size() % 4) h.push_back(0);
+    // FP32 path: cubic tables, 16-byte aligned
+    size_t o_herm = h.size();
+    if (sizeof(T) == 4) {
+        std::vector<double> ht = herm_tables(P);
+        for (double x : ht) h.push_back((T)x);
+    }
     cudaError_t e = cudaMalloc(mem, h.size() * sizeof(T));
     if (e != cudaSuccess) { plan->err = "table allocation failed"; return DMK_ERR_OOM; }
     e = cudaMemcpy(*mem, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
@@ -186,6 +236,7 @@ dmk_status_t upload_tab(dmk_plan_s* plan, void** mem, Tab<T>& tab, double fit_to
     tab.E = reinterpret_cast<const Cx<T>*>(base + o_E);
     tab.gdiff = base + o_g;
     tab.fit = base + o_fit;
+    tab.herm = (sizeof(T) == 4) ? reinterpret_cast<const float*>(base + o_herm) : nullptr;
     tab.off_q = offs[0]; tab.n_q = lens[0]; tab.off_f = offs[1]; tab.n_f = lens[1];
     tab.off_g = offs[2]; tab.n_g = lens[2]; tab.off_dq = offs[3]; tab.n_dq = lens[3];
     tab.off_df = offs[4]; tab.n_df = lens[4]; tab.off_dg = offs[5]; tab.n_dg = lens[5];
@@ -383,7 +434,6 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     CKS(ensure(plan, B_MISC, 4096, &vmisc));
     int* d_err = (int*)vmisc;
     double* d_sums = (double*)((char*)vmisc + 256);          // 2*drho doubles
-    int* d_count = (int*)((char*)vmisc + 512);
     unsigned long long* d_pairs = (unsigned long long*)((char*)vmisc + 768);
     CK(cudaMemsetAsync(vmisc, 0, 2048, st));
     uint64_t* keys = (uint64_t*)vkeys;
@@ -405,7 +455,17 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     CK(cub::DeviceRadixSort::SortPairs(vcub, tmp_bytes, keys, keys2, idx, idx2, (int)N, 0, end_bit, st));
     launches += 4;
     const uint64_t* pkeys = keys2;
-    k_gather<<<nblk(N, 256), 256, 0, st>>>(N, drho, idx2, (const double*)vw, rho, xs, rs);
+    // FP32 path: leading/trailing FP32 parts of the sorted coordinates and FP32 strengths, so
+    // that the leaf stage forms source offsets without FP64 arithmetic
+    float *xh = nullptr, *xl = nullptr, *rsf = nullptr;
+    if (sizeof(T) == 4) {
+        void* vxf;
+        CKS(ensure(plan, B_XF, (size_t)N * (6 + drho) * sizeof(float), &vxf));
+        xh = (float*)vxf;
+        xl = xh + 3 * N;
+        rsf = xl + 3 * N;
+    }
+    k_gather<<<nblk(N, 256), 256, 0, st>>>(N, drho, idx2, (const double*)vw, rho, xs, rs, xh, xl, rsf);
     ++launches;
     k_strength_sums<<<std::min<unsigned>(nblk(N, 256), 1024), 256, 0, st>>>(N, drho, rs, d_sums);
     ++launches;
@@ -442,8 +502,13 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     }
     std::vector<int> hnR(kMaxLevels + 1, 0);
     int nlev = 0;
+    // first batch: the depth of a uniform distribution plus two levels, so that uniform inputs
+    // need a single readback; then batches of four
+    int batch = 2;
+    for (double cap = (double)Mtot * plan->n_s; cap < (double)N; cap *= 8) ++batch;
     for (int l = 0; nlev == 0;) {
-        const int lend = std::min(l + 4, kBits + 1);
+        const int lend = std::min(l + batch, kBits + 1);
+        batch = 4;
         for (; l < lend; ++l) {
             capR[l] = std::min<int64_t>(capC[l], maxsplit);
             CKS(ensure(plan, B_FLAGS, (size_t)capC[l] * sizeof(int), &vflags));
@@ -482,11 +547,13 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
             CKS(alloc_level((size_t)ncand * sizeof(uint64_t), &vb));
             k_balance_cand<<<nblk(ncand, 256), 256, 0, st>>>((int)cR[l], Rl[l], d_nR + l, (int)capP, Rl[l - 1],
                                                              d_nR + l - 1, l, g, (uint64_t*)va);
+            // keys of level l-1 are below Mtot 8^(l-1); one more bit keeps the all-ones padding last
+            const int kbits = std::min(64, cube_bits + 3 * (l - 1) + 1);
             size_t tb = 0, tb2 = 0;
-            cub::DeviceRadixSort::SortKeys(nullptr, tb, (uint64_t*)va, (uint64_t*)vb, (int)ncand, 0, 64, st);
+            cub::DeviceRadixSort::SortKeys(nullptr, tb, (uint64_t*)va, (uint64_t*)vb, (int)ncand, 0, kbits, st);
             cub::DeviceSelect::Unique(nullptr, tb2, (uint64_t*)vb, (uint64_t*)va, d_nR + l - 1, (int)ncand, st);
             if (std::max(tb, tb2) > cub_cap) { CKS(ensure(plan, B_CUB, std::max(tb, tb2), &vcub)); cub_cap = plan->bufs[B_CUB].cap; }
-            CK(cub::DeviceRadixSort::SortKeys(vcub, tb, (uint64_t*)va, (uint64_t*)vb, (int)ncand, 0, 64, st));
+            CK(cub::DeviceRadixSort::SortKeys(vcub, tb, (uint64_t*)va, (uint64_t*)vb, (int)ncand, 0, kbits, st));
             CK(cub::DeviceSelect::Unique(vcub, tb2, (uint64_t*)vb, (uint64_t*)va, d_nR + l - 1, (int)ncand, st));
             k_trim_invalid<<<1, 1, 0, st>>>((uint64_t*)va, d_nR + l - 1);
             Rl[l - 1] = (uint64_t*)va;
@@ -530,22 +597,25 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     int* d_level_cnt = d_level_off + (kMaxLevels + 2);
     CK(cudaMemcpyAsync(d_level_off, ti.off.data(), nlev * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(d_level_cnt, ti.ncell.data(), nlev * sizeof(int), cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(B.nl, 0xff, nb * sizeof(int), st));
-    for (int l = 0; l < nlev; ++l) {
-        const uint64_t* Rnext = Rl[l];
-        k_box_fill<<<nblk(ti.ncell[l], 256), 256, 0, st>>>(l, ti.off[l], ti.ncell[l], cells[l], Rnext, ti.nR[l],
-                                                           ti.off[l + 1], l > 0 ? cells[l - 1] : nullptr,
-                                                           l > 0 ? ti.ncell[l - 1] : 0, l > 0 ? ti.off[l - 1] : 0,
-                                                           pkeys, N, g, B);
-        ++launches;
+    LevelSet ls;
+    std::memset(&ls, 0, sizeof(ls));
+    ls.nlev = nlev;
+    for (int l = 0; l <= nlev; ++l) {
+        ls.off[l] = ti.off[l];
+        ls.nl_off[l] = ti.nl_off[l];
     }
+    for (int l = 0; l < nlev; ++l) {
+        ls.cells[l] = cells[l];
+        ls.R[l] = Rl[l];
+        ls.nR[l] = ti.nR[l];
+    }
+    k_box_fill_all<<<nblk(nb, 256), 256, 0, st>>>(ls, nb, pkeys, N, g, B);
+    ++launches;
     void* vnl;
     CKS(ensure(plan, B_NLBOX, (size_t)std::max(n_nl, 1) * sizeof(int), &vnl));
     int* nl_box = (int*)vnl;
-    for (int l = 0; l < nlev; ++l) {
-        if (ti.nR[l] == 0) continue;
-        k_nonleaf_list<<<nblk(ti.nR[l], 256), 256, 0, st>>>(ti.nR[l], Rl[l], cells[l], ti.ncell[l], ti.off[l],
-                                                            ti.nl_off[l], nl_box, B.nl);
+    if (n_nl > 0) {
+        k_nonleaf_all<<<nblk(n_nl, 256), 256, 0, st>>>(ls, n_nl, nl_box);
         ++launches;
     }
     k_colleagues<<<nblk((int64_t)27 * nb, 256), 256, 0, st>>>(nb, B.level, B.ix, B.key, d_level_off, d_level_cnt, g,
@@ -645,18 +715,28 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         void *vchi, *vuh, *vrsc;
         CKS(ensure(plan, B_CHI, (size_t)Mtot * drho * rt.nmode * sizeof(Cx<double>), &vchi));
         CKS(ensure(plan, B_UHAT, (size_t)du * rt.nmode * sizeof(Cx<double>), &vuh));
-        const size_t b1 = (size_t)rt.n1 * p * p + (size_t)rt.n1 * rt.n2 * p;
-        const size_t b2 = (size_t)rt.n1 * rt.n2 * p + (size_t)rt.n1 * p * p + rt.nmode;
-        const size_t per = std::max(b1, b2) * sizeof(Cx<double>);
-        const int jobs = Mtot * std::max(drho, du);
-        const unsigned grid = (unsigned)std::min(jobs, 148 * 4);
-        CKS(ensure(plan, B_SCRATCH, per * grid, &vrsc));
-        k_root_chi<T><<<std::min<unsigned>(grid, Mtot * drho), 256, 0, st>>>(Mtot, drho, p, g, rt, proxy,
-                                                                            (Cx<double>*)vchi, (unsigned char*)vrsc, per);
-        k_root_apply<<<nblk(rt.nmode, 128), 128, 0, st>>>(Mtot, drho, du, rt, (const Cx<double>*)vchi, (Cx<double>*)vuh);
-        k_root_eval<T><<<std::min<unsigned>(grid, Mtot * du), 256, 0, st>>>(Mtot, du, p, g, rt, (const Cx<double>*)vuh,
-                                                                           d_sums, drho, local, (unsigned char*)vrsc, per);
-        launches += 3;
+        // scratch: forward B1 (n1 p^2) + B2 (n1 n2 p) per (cube, strength component); backward
+        // G (nmode) + C2 (n1 n2 p) + C1 (n1 p^2) per (cube, potential component)
+        const size_t f1 = (size_t)rt.n1 * p * p, f2 = (size_t)rt.n1 * rt.n2 * p;
+        const int jf = Mtot * drho, jb = Mtot * du;
+        const size_t nfwd = (size_t)jf * (f1 + f2), nbwd = (size_t)jb * (rt.nmode + f2 + f1);
+        CKS(ensure(plan, B_SCRATCH, std::max(nfwd, nbwd) * sizeof(Cx<double>), &vrsc));
+        Cx<double>* r0 = (Cx<double>*)vrsc;
+        Cx<double>* chi = (Cx<double>*)vchi;
+        Cx<double>* uh = (Cx<double>*)vuh;
+        auto blocks = [](int64_t n) { return (unsigned)((n + 127) / 128); };
+        k_root_fwd1<T><<<blocks((int64_t)jf * f1), 128, 0, st>>>(jf, p, rt, proxy, r0);
+        k_root_fwd2<<<blocks((int64_t)jf * f2), 128, 0, st>>>(jf, p, rt, r0, r0 + (size_t)jf * f1);
+        k_root_fwd3<<<blocks((int64_t)jf * rt.nmode), 128, 0, st>>>(jf, drho, p, g, rt, r0 + (size_t)jf * f1, chi);
+        k_root_apply<<<nblk(rt.nmode, 128), 128, 0, st>>>(Mtot, drho, du, rt, chi, uh);
+        Cx<double>* G = r0;
+        Cx<double>* C2 = G + (size_t)jb * rt.nmode;
+        Cx<double>* C1 = C2 + (size_t)jb * f2;
+        k_root_bwd0<<<blocks((int64_t)jb * rt.nmode), 128, 0, st>>>(jb, du, g, rt, uh, G);
+        k_root_bwd1<<<blocks((int64_t)jb * f2), 128, 0, st>>>(jb, p, rt, G, C2);
+        k_root_bwd2<<<blocks((int64_t)jb * f1), 128, 0, st>>>(jb, p, rt, C2, C1);
+        k_root_bwd3<T><<<blocks((int64_t)jb * p * p * p), 128, 0, st>>>(jb, du, p, rt, C1, d_sums, drho, local);
+        launches += 8;
     }
     rec(3);
     // ---- (7) plane waves: outgoing for all non-leaf boxes, then translation + incoming ------
@@ -681,15 +761,20 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         const size_t pw2_bytes =
             ((size_t)NF * mpw + (size_t)p * NF * nfh + (size_t)p * p * (nfh | 1)) * sizeof(Cx<T>);
         if (p <= kMaxPFast && pw2_bytes + 512 <= plan->smem_optin) {
+            void* vvw;
+            CKS(ensure(plan, B_VW, (size_t)n_nl * du * nW * sizeof(Cx<T>), &vvw));
+            Cx<T>* Vw = (Cx<T>*)vvw;
+            const int nchunk = (int)((nW + kTransModes - 1) / kTransModes);
+            k_pw_trans<T><<<(unsigned)n_nl * nchunk, kTransThreads, 0, st>>>(n_nl, nl_box, B, tab, W, Vw);
             const unsigned grid = (unsigned)std::min(n_nl, 148 * 4);
             if (mpw == 20) {
-                CKS(set_smem(plan, k_pwin2<T, 20>, pw2_bytes));
-                k_pwin2<T, 20><<<grid, 384, pw2_bytes, st>>>(n_nl, nl_box, B, tab, W, local);
+                CKS(set_smem(plan, k_pwin3<T, 20>, pw2_bytes));
+                k_pwin3<T, 20><<<grid, 384, pw2_bytes, st>>>(n_nl, nl_box, tab, Vw, local);
             } else {
-                CKS(set_smem(plan, k_pwin2<T, kMaxPFast>, pw2_bytes));
-                k_pwin2<T, kMaxPFast><<<grid, 384, pw2_bytes, st>>>(n_nl, nl_box, B, tab, W, local);
+                CKS(set_smem(plan, k_pwin3<T, kMaxPFast>, pw2_bytes));
+                k_pwin3<T, kMaxPFast><<<grid, 384, pw2_bytes, st>>>(n_nl, nl_box, tab, Vw, local);
             }
-            ++launches;
+            launches += 2;
         } else {
             size_t bytes = ((size_t)du * nW + (size_t)p * NF * nfh + (size_t)p * p * nfh) * sizeof(Cx<T>);
             Place pl;
@@ -752,6 +837,9 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         lo.rs = rs;
         lo.self_val = plan->d_self;
         lo.self_grad = plan->d_self + P.d_u * P.d_rho;
+        lo.xh = xh;
+        lo.xl = xl;
+        lo.rsf = rsf;
         const bool gr = grad != nullptr;
         switch (P.kernel) {
             case DMK_LAPLACE: CKS((launch_leaf<T, DMK_LAPLACE>(plan, tab, nleaf, leaves, B, local, xs, N, doffs, dl, lo, gr))); break;
@@ -993,8 +1081,10 @@ dmk_status_t dmk_plan_table(dmk_kernel_t k, int D, const double L[3], double tol
     } else if (which == 3) {
         v = {T.phi0, T.d2phi0, T.d2phihat0};
         v.insert(v.end(), T.phihat_samples.begin(), T.phihat_samples.end());
+    } else if (which == 4) {
+        v = herm_tables(T);
     } else {
-        g_plan_error = "which must be 0..3";
+        g_plan_error = "which must be 0..4";
         return DMK_ERR_INVALID_ARG;
     }
     *n = (int64_t)v.size();

@@ -101,15 +101,16 @@ template <class T> struct Tab {
     const T* gdiff;      // NF x NF x nfh
     const T* fit;        // concatenated Chebyshev series
     int off_q, n_q, off_f, n_f, off_g, n_g, off_dq, n_dq, off_df, n_df, off_dg, n_dg;
+    const float* herm;   // FP32 path: piecewise cubic tables of the six series (see HermSeries)
 };
 
-// Clenshaw evaluation of sum_k a_k T_k(t)
 // four values loaded as one vector from shared memory
 template <class T>
 struct alignas(4 * sizeof(T)) Quad {
     T x, y, z, w;
 };
 
+// Clenshaw evaluation of sum_k a_k T_k(t)
 template <class T> __device__ __forceinline__ T clenshaw(const T* a, int n, T t) {
     T b1 = 0, b2 = 0;
     T t2 = t + t;
@@ -120,5 +121,51 @@ template <class T> __device__ __forceinline__ T clenshaw(const T* a, int n, T t)
     }
     return fma(t, b1, a[0] - b2);
 }
+
+// ---- residual series (App. B, "precomputed polynomial approximations"): q, f, g and their
+// s-derivatives as functions of s = r^2 / nu^2 in [0, 1] ------------------------------------
+enum { kSerQ = 0, kSerF, kSerG, kSerDQ, kSerDF, kSerDG };
+
+// Chebyshev series in t = 2 s - 1, coefficients at the offsets of Tab (FP64 path and p > kMaxPFast)
+template <class T>
+struct ChebSeries {
+    const Tab<T>& tb;
+    const T* fit;
+    T t;
+    __device__ __forceinline__ ChebSeries(const Tab<T>& tb_, const T* fit_, T r2, T inv_nu)
+        : tb(tb_), fit(fit_), t(fma(T(2) * r2, inv_nu * inv_nu, T(-1))) {}
+    __device__ __forceinline__ T operator()(int k) const {
+        switch (k) {
+            case kSerQ: return clenshaw(fit + tb.off_q, tb.n_q, t);
+            case kSerF: return clenshaw(fit + tb.off_f, tb.n_f, t);
+            case kSerG: return clenshaw(fit + tb.off_g, tb.n_g, t);
+            case kSerDQ: return clenshaw(fit + tb.off_dq, tb.n_dq, t);
+            case kSerDF: return clenshaw(fit + tb.off_df, tb.n_df, t);
+            default: return clenshaw(fit + tb.off_dg, tb.n_dg, t);
+        }
+    }
+};
+
+// Piecewise cubic Hermite form of the same series for the FP32 path: kHermNT intervals of s, the
+// interval i holding (c0, c1, c2, c3) with X = c0 + u (c1 + u (c2 + u c3)), u = s kHermNT - i,
+// built on the host from the FP64 series values and derivatives at the interval ends.  Table
+// k (series order above) starts at tbl + k kHermNT.
+constexpr int kHermNT = 256;
+
+struct HermSeries {
+    const Quad<float>* tbl;
+    int i;
+    float u;
+    __device__ __forceinline__ HermSeries(const Quad<float>* tbl_, float r2, float inv_nu) : tbl(tbl_) {
+        const float x = r2 * (inv_nu * inv_nu) * (float)kHermNT;
+        const int ii = min((int)x, kHermNT - 1);
+        i = ii;
+        u = x - (float)ii;
+    }
+    __device__ __forceinline__ float operator()(int k) const {
+        const Quad<float> c = tbl[k * kHermNT + i];
+        return fmaf(u, fmaf(u, fmaf(u, c.w, c.z), c.y), c.x);
+    }
+};
 
 }  // namespace dmk

@@ -297,9 +297,7 @@ __global__ void __launch_bounds__(kLeaf2Threads) k_leaf2(int nleaf, const int* _
                             dz += xtl[2] - szl[k];
                         }
                         const T r2 = dx * dx + dy * dy + dz * dz;
-                        Pr::eval(tab, K == DMK_LAPLACE ? fits + tab.off_q : fits,
-                                 K == DMK_LAPLACE ? fits + tab.off_f : fits, dx, dy, dz, r2, sinv[k], sr[k], acc,
-                                 gacc);
+                        Pr::eval(ChebSeries<T>(tab, fits, r2, sinv[k]), dx, dy, dz, r2, sinv[k], sr[k], acc, gacc);
                     }
                     for (int j = 0; j < DU; ++j) accd[j] += (double)acc[j];
                     for (int j = 0; j < 3 * DU; ++j) gaccd[j] += (double)gacc[j];
@@ -374,6 +372,139 @@ __device__ __forceinline__ Cx<T> pw_gather_op(int kernel, int j, int m1, int m2,
     Cx<T> out[3];
     apply_op<T>(kernel, mv, V, out);
     return j == 0 ? out[0] : (j == 1 ? out[1] : out[2]);
+}
+
+// Translation + difference-kernel symbol (Sec. 3.1.4), one thread per (non-leaf box, mode):
+//   V_j(m) = 2^(a l) g(m) [op(m) sum_C exp(-i (2 pi/3) m.d_C) W_C(m)]_j
+// over the non-leaf colleagues C (offset d_C), written per box as du x nW complex values for the
+// incoming transform.  CTA = (box, block of kTransModes modes).
+constexpr int kTransThreads = 256;
+constexpr int kTransModes = 512;
+
+template <class T>
+__global__ void __launch_bounds__(kTransThreads) k_pw_trans(int n, const int* __restrict__ nl_box, BoxArrays B,
+                                                            Tab<T> tab, const Cx<T>* __restrict__ W,
+                                                            Cx<T>* __restrict__ Vw) {
+    const int drho = tab.d_rho, du = tab.d_u, nf = tab.nf, NF = tab.NF, nfh = tab.nfh;
+    const int nW = NF * NF * nfh;
+    const int nchunk = (nW + kTransModes - 1) / kTransModes;
+    const int bi = blockIdx.x / nchunk, e0 = (blockIdx.x % nchunk) * kTransModes;
+    __shared__ int ncol;
+    __shared__ int col_nl[27];
+    __shared__ int col_d[27];
+    const int box = nl_box[bi];
+    if (threadIdx.x == 0) {
+        int k = 0;
+        for (int d = 0; d < 27; ++d) {
+            const int C = B.coll[box * 27 + d];
+            if (C >= 0 && B.nl[C] >= 0) { col_nl[k] = B.nl[C]; col_d[k] = d; ++k; }
+        }
+        ncol = k;
+    }
+    __syncthreads();
+    const T scale = (T)ldexp(1.0, tab.level_power * B.level[box]);
+    const int e1 = min(nW, e0 + kTransModes);
+    for (int e = e0 + threadIdx.x; e < e1; e += kTransThreads) {
+        const int i1 = e / (NF * nfh), i2 = (e / nfh) % NF, m3 = e % nfh;
+        const int m1 = i1 - nf, m2 = i2 - nf;
+        const T gs = scale * tab.gdiff[e];
+        for (int j = 0; j < du; ++j) {
+            Cx<T> o;
+            if (drho == 1)
+                o = pw_gather_op<T, 1>(tab.kernel, j, m1, m2, m3, e, nW, ncol, col_nl, col_d, W);
+            else if (drho == 3)
+                o = pw_gather_op<T, 3>(tab.kernel, j, m1, m2, m3, e, nW, ncol, col_nl, col_d, W);
+            else
+                o = pw_gather_op<T, 9>(tab.kernel, j, m1, m2, m3, e, nW, ncol, col_nl, col_d, W);
+            Vw[((size_t)bi * du + j) * nW + e] = {gs * o.x, gs * o.y};
+        }
+    }
+}
+
+// Incoming transform (Sec. 3.1.4) from the translated spectrum Vw of k_pw_trans: stage A, thread
+// per spectral column (m2, m3), m1 -> j1 with the column read from global memory in batches;
+// stages B (m2 -> j2) and C (m3 -> j3, half-spectrum weights) as in k_pwin2.
+template <class T, int MAXP>
+__global__ void __launch_bounds__(384) k_pwin3(int n, const int* __restrict__ nl_box, Tab<T> tab,
+                                               const Cx<T>* __restrict__ Vw, T* __restrict__ local) {
+    const int p = tab.p, p2 = p * p, p3 = p2 * p, du = tab.d_u;
+    const int nf = tab.nf, NF = tab.NF, nfh = tab.nfh, nW = NF * NF * nfh;
+    const int pm3 = nfh | 1;
+    Cx<T>* F = reinterpret_cast<Cx<T>*>(dsmem);                // NF x MAXP: conj(E), zero-padded
+    Cx<T>* B2 = F + NF * MAXP;                                 // p x NF x nfh
+    Cx<T>* B1 = B2 + p * NF * nfh;                             // p x p x pm3
+    for (int e = threadIdx.x; e < NF * MAXP; e += blockDim.x) {
+        const int m = e / MAXP, j = e % MAXP;
+        F[e] = (j < p) ? cconj(tab.E[m * p + j]) : Cx<T>{0, 0};
+    }
+    constexpr int KB = 9;
+    for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
+        const int box = nl_box[bi];
+        for (int j = 0; j < du; ++j) {
+            __syncthreads();
+            const Cx<T>* V = Vw + ((size_t)bi * du + j) * nW;
+            // stage A
+            for (int c = threadIdx.x; c < NF * nfh; c += blockDim.x) {
+                Cx<T> acc[MAXP];
+#pragma unroll
+                for (int q = 0; q < MAXP; ++q) acc[q] = {0, 0};
+                for (int i0 = 0; i0 < NF; i0 += KB) {
+                    Cx<T> v[KB];
+#pragma unroll
+                    for (int u = 0; u < KB; ++u)
+                        v[u] = (i0 + u < NF) ? V[(size_t)(i0 + u) * NF * nfh + c] : Cx<T>{0, 0};
+#pragma unroll
+                    for (int u = 0; u < KB; ++u) {
+                        if (i0 + u < NF) {
+                            const Cx<T>* Fr = F + (i0 + u) * MAXP;
+#pragma unroll
+                            for (int q = 0; q < MAXP; ++q) cfma(acc[q], Fr[q], v[u]);
+                        }
+                    }
+                }
+                const int i2 = c / nfh, m3 = c % nfh;
+#pragma unroll
+                for (int q = 0; q < MAXP; ++q)
+                    if (q < p) B2[(q * NF + i2) * nfh + m3] = acc[q];
+            }
+            __syncthreads();
+            // stage B
+            for (int c = threadIdx.x; c < p * nfh; c += blockDim.x) {
+                const int j1 = c / nfh, m3 = c % nfh;
+                Cx<T> acc[MAXP];
+#pragma unroll
+                for (int q = 0; q < MAXP; ++q) acc[q] = {0, 0};
+                for (int i2 = 0; i2 < NF; ++i2) {
+                    const Cx<T> b = B2[(j1 * NF + i2) * nfh + m3];
+                    const Cx<T>* Fr = F + i2 * MAXP;
+#pragma unroll
+                    for (int q = 0; q < MAXP; ++q) cfma(acc[q], Fr[q], b);
+                }
+#pragma unroll
+                for (int q = 0; q < MAXP; ++q)
+                    if (q < p) B1[(j1 * p + q) * pm3 + m3] = acc[q];
+            }
+            __syncthreads();
+            // stage C
+            T* u = local + ((size_t)box * du + j) * p3;
+            for (int c = threadIdx.x; c < p2; c += blockDim.x) {
+                T acc[MAXP];
+#pragma unroll
+                for (int q = 0; q < MAXP; ++q) acc[q] = 0;
+                for (int m3 = 0; m3 < nfh; ++m3) {
+                    const Cx<T> b = B1[c * pm3 + m3];
+                    const T wgt = (m3 == 0) ? T(1) : T(2);
+                    const Cx<T> bw = {wgt * b.x, wgt * b.y};
+                    const Cx<T>* Fr = F + (nf + m3) * MAXP;
+#pragma unroll
+                    for (int q = 0; q < MAXP; ++q) acc[q] = fma(Fr[q].x, bw.x, fma(-Fr[q].y, bw.y, acc[q]));
+                }
+#pragma unroll
+                for (int q = 0; q < MAXP; ++q)
+                    if (q < p) u[c * p + q] += acc[q];
+            }
+        }
+    }
 }
 
 // Translation + difference-kernel symbol + incoming transform (Sec. 3.1.4, Eq. Dl_int_discr)
@@ -493,6 +624,23 @@ namespace dmk {
 //     leading parts fills a per-thread byte queue, and only queued sources are evaluated, with
 //     two-float differences in the FP32 path and r > 0 excluding the target itself;
 // (4) self correction and the FP64 write-back in input order.
+// (a_h + a_l) + (b_h + b_l) as an unnormalised FP32 pair: the leading sum with its exact
+// rounding error (Knuth's TwoSum), plus the trailing parts.  Accurate to about 2^-48 of the
+// operands' magnitude.
+__device__ __forceinline__ void two_float_add(float ah, float al, float bh, float bl, float& h, float& l) {
+    const float s = ah + bh;
+    const float bb = s - ah;
+    const float e = (ah - (s - bb)) + (bh - bb);
+    h = s;
+    l = e + (al + bl);
+}
+
+// FP64 value as leading + trailing FP32 parts
+__device__ __forceinline__ void split_double(double v, float& h, float& l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
+
 constexpr int kLeaf3Threads = 128;
 
 template <class T, int K, bool GRAD>
@@ -508,7 +656,10 @@ __global__ void __launch_bounds__(kLeaf3Threads) k_leaf3(int nleaf, const int* _
     const int p = tab.p, p2 = p * p, p3 = p2 * p, PQ = (p + 3) & ~3, ng = PQ >> 2;
     __shared__ Q4 sA[kSrcChunk];   // source offset from the leaf centre (leading part), nu^2
     __shared__ Q4 sB[kSrcChunk];   // trailing parts (FP32 path), 1/nu
-    __shared__ T fits[256];
+    __shared__ T fits[kTwo ? 1 : 256];
+    // FP32 path: the piecewise cubic series tables this kernel uses (q, f[, g][, q', f'[, g']])
+    constexpr int NSER = (K == DMK_STRESSLET) ? (GRAD ? 6 : 3) : ((GRAD && K != DMK_LAPLACE) ? 5 : 2);
+    __shared__ Quad<float> herm[kTwo ? NSER * kHermNT : 1];
     // dynamic: the byte queue q[kSrcChunk][threads], aliased by the coefficient block during
     // step (2); then the staged strengths
     extern __shared__ __align__(32) unsigned char dsm3[];
@@ -516,9 +667,14 @@ __global__ void __launch_bounds__(kLeaf3Threads) k_leaf3(int nleaf, const int* _
     unsigned char (*q)[kLeaf3Threads] = reinterpret_cast<unsigned char (*)[kLeaf3Threads]>(dsm3);
     T* cs = reinterpret_cast<T*>(dsm3);
     T (*sr)[DR] = reinterpret_cast<T (*)[DR]>(dsm3 + ((qbytes + 15) & ~(size_t)15));
-    for (int e = threadIdx.x; e < min(256, tab.n_q + tab.n_f + tab.n_g + tab.n_dq + tab.n_df + tab.n_dg);
-         e += blockDim.x)
-        fits[e] = tab.fit[e];
+    if constexpr (kTwo) {
+        const Quad<float>* hsrc = reinterpret_cast<const Quad<float>*>(tab.herm);
+        for (int e = threadIdx.x; e < NSER * kHermNT; e += blockDim.x) herm[e] = hsrc[e];
+    } else {
+        for (int e = threadIdx.x; e < min(256, tab.n_q + tab.n_f + tab.n_g + tab.n_dq + tab.n_df + tab.n_dg);
+             e += blockDim.x)
+            fits[e] = tab.fit[e];
+    }
     const int tt = threadIdx.x;
     for (int li = blockIdx.x; li < nleaf; li += gridDim.x) {
         const int box = leaves[li];
@@ -529,16 +685,28 @@ __global__ void __launch_bounds__(kLeaf3Threads) k_leaf3(int nleaf, const int* _
         for (int t0 = st; t0 < en; t0 += kLeaf3Threads) {
             const int nt = min(kLeaf3Threads, en - t0);
             const bool act = tt < nt;
-            // target offsets from the leaf centre
-            double xd[3] = {0, 0, 0};
-            if (act)
-                for (int a = 0; a < 3; ++a) xd[a] = xs[a * N + t0 + tt] - c[a];
+            // target offsets from the leaf centre: FP64 in the FP64 path; in the FP32 path the
+            // sum of the point's FP32 parts and the FP32 parts of -centre
+            T xt[3] = {0, 0, 0}, xtl[3] = {0, 0, 0};
+            if (act) {
+                const int tg = t0 + tt;
+                for (int a = 0; a < 3; ++a) {
+                    if constexpr (kTwo) {
+                        float ch, cl;
+                        split_double(-c[a], ch, cl);
+                        two_float_add(out.xh[a * N + tg], out.xl[a * N + tg], ch, cl, xt[a], xtl[a]);
+                    } else {
+                        xt[a] = (T)(xs[a * N + tg] - c[a]);
+                    }
+                }
+            }
             // (2) Chebyshev evaluation
             T ev[DU], eg[3 * DU];
             {
                 T xi[3];
+                const T ih = (T)(1.0 / half);
                 for (int a = 0; a < 3; ++a) {
-                    const T v = (T)(xd[a] / half);
+                    const T v = (xt[a] + xtl[a]) * ih;
                     xi[a] = v > T(1) ? T(1) : (v < T(-1) ? T(-1) : v);
                 }
                 T Tz[kMaxPFast], dTz[kMaxPFast];
@@ -636,11 +804,6 @@ __global__ void __launch_bounds__(kLeaf3Threads) k_leaf3(int nleaf, const int* _
                 }
             }
             // (3) residual sums with in-support compaction
-            T xt[3], xtl[3] = {0, 0, 0};
-            for (int a = 0; a < 3; ++a) {
-                xt[a] = (T)xd[a];
-                if (kTwo) xtl[a] = (T)(xd[a] - (double)xt[a]);
-            }
             double accd[DU], gaccd[3 * DU];
 #pragma unroll
             for (int j = 0; j < DU; ++j) accd[j] = 0;
@@ -661,19 +824,31 @@ __global__ void __launch_bounds__(kLeaf3Threads) k_leaf3(int nleaf, const int* _
                     const double sh2 = (double)(((de.code >> 4) & 3) - 1) * g.L[2];
                     const double inv = (double)(1 << lev) / g.s;
                     const T nu2 = (T)(1.0 / (inv * inv));
+                    const T tinv = (T)inv;
+                    // image shift minus the target leaf's centre, per entry
+                    const double E[3] = {sh0 - c[0], sh1 - c[1], sh2 - c[2]};
+                    float Eh[3] = {0, 0, 0}, El[3] = {0, 0, 0};
+                    if constexpr (kTwo)
+                        for (int a = 0; a < 3; ++a) split_double(E[a], Eh[a], El[a]);
                     for (int k = tt; k < take; k += kLeaf3Threads) {
                         const int si = de.start + eo + k, slot = filled + k;
-                        const double vx = xs[si] + sh0 - c[0], vy = xs[N + si] + sh1 - c[1],
-                                     vz = xs[2 * N + si] + sh2 - c[2];
                         Q4 a, b;
-                        a.x = (T)vx; a.y = (T)vy; a.z = (T)vz; a.w = nu2;
-                        b.x = kTwo ? (T)(vx - (double)a.x) : T(0);
-                        b.y = kTwo ? (T)(vy - (double)a.y) : T(0);
-                        b.z = kTwo ? (T)(vz - (double)a.z) : T(0);
-                        b.w = (T)inv;
+                        if constexpr (kTwo) {
+                            two_float_add(out.xh[si], out.xl[si], Eh[0], El[0], a.x, b.x);
+                            two_float_add(out.xh[N + si], out.xl[N + si], Eh[1], El[1], a.y, b.y);
+                            two_float_add(out.xh[2 * N + si], out.xl[2 * N + si], Eh[2], El[2], a.z, b.z);
+                            for (int a2 = 0; a2 < DR; ++a2) sr[slot][a2] = out.rsf[(int64_t)si * DR + a2];
+                        } else {
+                            a.x = (T)(xs[si] + E[0]);
+                            a.y = (T)(xs[N + si] + E[1]);
+                            a.z = (T)(xs[2 * N + si] + E[2]);
+                            b.x = b.y = b.z = T(0);
+                            for (int a2 = 0; a2 < DR; ++a2) sr[slot][a2] = (T)out.rs[(int64_t)si * DR + a2];
+                        }
+                        a.w = nu2;
+                        b.w = tinv;
                         sA[slot] = a;
                         sB[slot] = b;
-                        for (int a2 = 0; a2 < DR; ++a2) sr[slot][a2] = (T)out.rs[(int64_t)si * DR + a2];
                     }
                     filled += take;
                     eo += take;
@@ -682,6 +857,7 @@ __global__ void __launch_bounds__(kLeaf3Threads) k_leaf3(int nleaf, const int* _
                 __syncthreads();
                 if (act) {
                     int cnt = 0;
+#pragma unroll 4
                     for (int k = 0; k < filled; ++k) {
                         const Q4 a = sA[k];
                         const T dx = xt[0] - a.x, dy = xt[1] - a.y, dz = xt[2] - a.z;
@@ -703,10 +879,12 @@ __global__ void __launch_bounds__(kLeaf3Threads) k_leaf3(int nleaf, const int* _
                             dz += xtl[2] - b.z;
                         }
                         const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                        if (r2 > T(0))
-                            Pr::eval(tab, K == DMK_LAPLACE ? fits + tab.off_q : fits,
-                                     K == DMK_LAPLACE ? fits + tab.off_f : fits, dx, dy, dz, r2, b.w, sr[k], acc,
-                                     gacc);
+                        if (r2 > T(0)) {
+                            if constexpr (kTwo)
+                                Pr::eval(HermSeries(herm, r2, b.w), dx, dy, dz, r2, b.w, sr[k], acc, gacc);
+                            else
+                                Pr::eval(ChebSeries<T>(tab, fits, r2, b.w), dx, dy, dz, r2, b.w, sr[k], acc, gacc);
+                        }
                     }
 #pragma unroll
                     for (int j = 0; j < DU; ++j) accd[j] += (double)acc[j];

@@ -509,6 +509,119 @@ __global__ void k_root_eval(int M, int du, int p, Geo g, RootTab rt, const Cx<do
     }
 }
 
+// Root far field spread over the whole GPU: every stage of the tensor-form sums (the same
+// contractions as k_root_chi / k_root_eval) is its own launch with one thread per output
+// element of all cubes and components, so that the FP64 work is not confined to one CTA per
+// cube.  Scratch layout per job (cube m, component): B1 n1 x p^2, B2 n1 x n2 x p (forward);
+// G nmode, C2 n1 x n2 x p, C1 n1 x p^2 (backward).
+template <class T>
+__global__ void k_root_fwd1(int jobs, int p, RootTab rt, const T* __restrict__ proxy, Cx<double>* __restrict__ B1) {
+    const int p2 = p * p, p3 = p2 * p, per = rt.n1 * p2;
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= (int64_t)jobs * per) return;
+    const int job = (int)(id / per), e = (int)(id % per);
+    const int i1 = e / p2, r = e % p2;
+    const T* pr = proxy + (size_t)job * p3;
+    Cx<double> v = {0, 0};
+    for (int k = 0; k < p; ++k) cfmar(v, rt.S[0][i1 * p + k], (double)pr[k * p2 + r]);
+    B1[id] = v;
+}
+
+__global__ void k_root_fwd2(int jobs, int p, RootTab rt, const Cx<double>* __restrict__ B1,
+                            Cx<double>* __restrict__ B2) {
+    const int p2 = p * p, n2 = rt.n2, per = rt.n1 * n2 * p;
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= (int64_t)jobs * per) return;
+    const int job = (int)(id / per), e = (int)(id % per);
+    const int i1 = e / (n2 * p), i2 = (e / p) % n2, j3 = e % p;
+    const Cx<double>* b = B1 + (size_t)job * rt.n1 * p2 + (size_t)i1 * p2 + j3;
+    Cx<double> v = {0, 0};
+    for (int k = 0; k < p; ++k) cfma(v, rt.S[1][i2 * p + k], b[k * p]);
+    B2[id] = v;
+}
+
+__global__ void k_root_fwd3(int jobs, int drho, int p, Geo g, RootTab rt, const Cx<double>* __restrict__ B2,
+                            Cx<double>* __restrict__ chi_part) {
+    const int n2 = rt.n2, n3 = rt.n3, per = rt.nmode;
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= (int64_t)jobs * per) return;
+    const int job = (int)(id / per), e = (int)(id % per);
+    const int m = job / drho;
+    const int mc[3] = {m % g.M[0], (m / g.M[0]) % g.M[1], m / (g.M[0] * g.M[1])};
+    const int i1 = e / (n2 * n3), i2 = (e / n3) % n2, i3 = e % n3;
+    const Cx<double>* b = B2 + (size_t)job * rt.n1 * n2 * p + ((size_t)i1 * n2 + i2) * p;
+    Cx<double> v = {0, 0};
+    for (int k = 0; k < p; ++k) cfma(v, rt.S[2][i3 * p + k], b[k]);
+    const double ph = -(rt.kax[0][i1] * (mc[0] + 0.5) * g.s + rt.kax[1][i2] * (mc[1] + 0.5) * g.s +
+                        rt.kax[2][i3] * (mc[2] + 0.5) * g.s);
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    chi_part[id] = cmul(v, Cx<double>{cs, sn});
+}
+
+__global__ void k_root_bwd0(int jobs, int du, Geo g, RootTab rt, const Cx<double>* __restrict__ uhat,
+                            Cx<double>* __restrict__ G) {
+    const int n2 = rt.n2, n3 = rt.n3, per = rt.nmode;
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= (int64_t)jobs * per) return;
+    const int job = (int)(id / per), e = (int)(id % per);
+    const int m = job / du, j = job % du;
+    const int mc[3] = {m % g.M[0], (m / g.M[0]) % g.M[1], m / (g.M[0] * g.M[1])};
+    const int i1 = e / (n2 * n3), i2 = (e / n3) % n2, i3 = e % n3;
+    const double ph = rt.kax[0][i1] * (mc[0] + 0.5) * g.s + rt.kax[1][i2] * (mc[1] + 0.5) * g.s +
+                      rt.kax[2][i3] * (mc[2] + 0.5) * g.s;
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    G[id] = cmul(uhat[(size_t)j * rt.nmode + e], Cx<double>{cs, sn});
+}
+
+__global__ void k_root_bwd1(int jobs, int p, RootTab rt, const Cx<double>* __restrict__ G,
+                            Cx<double>* __restrict__ C2) {
+    const int n3 = rt.n3, per = rt.n1 * rt.n2 * p;
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= (int64_t)jobs * per) return;
+    const int job = (int)(id / per), e = (int)(id % per);
+    const int i12 = e / p, j3 = e % p;
+    const Cx<double>* gg = G + (size_t)job * rt.nmode + (size_t)i12 * n3;
+    Cx<double> v = {0, 0};
+    for (int k = 0; k < n3; ++k) cfma(v, cconj(rt.S[2][k * p + j3]), gg[k]);
+    C2[id] = v;
+}
+
+__global__ void k_root_bwd2(int jobs, int p, RootTab rt, const Cx<double>* __restrict__ C2,
+                            Cx<double>* __restrict__ C1) {
+    const int p2 = p * p, n2 = rt.n2, per = rt.n1 * p2;
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= (int64_t)jobs * per) return;
+    const int job = (int)(id / per), e = (int)(id % per);
+    const int i1 = e / p2, j2 = (e / p) % p, j3 = e % p;
+    const Cx<double>* c = C2 + (size_t)job * rt.n1 * n2 * p + (size_t)i1 * n2 * p + j3;
+    Cx<double> v = {0, 0};
+    for (int k = 0; k < n2; ++k) cfma(v, cconj(rt.S[1][k * p + j2]), c[k * p]);
+    C1[id] = v;
+}
+
+template <class T>
+__global__ void k_root_bwd3(int jobs, int du, int p, RootTab rt, const Cx<double>* __restrict__ C1,
+                            const double* __restrict__ rho_sum, int drho, T* __restrict__ local) {
+    const int p2 = p * p, p3 = p2 * p;
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= (int64_t)jobs * p3) return;
+    const int job = (int)(id / p3), e = (int)(id % p3);
+    const int j = job % du;
+    const int j1 = e / p2, r = e % p2;
+    const Cx<double>* c = C1 + (size_t)job * rt.n1 * p2 + r;
+    double v = 0;
+    for (int k = 0; k < rt.n1; ++k) {
+        const Cx<double> f = cconj(rt.S[0][k * p + j1]);
+        const Cx<double> b = c[(size_t)k * p2];
+        v += f.x * b.x - f.y * b.y;
+    }
+    double cst = 0;
+    for (int a = 0; a < drho; ++a) cst += rt.rconst[j * drho + a] * rho_sum[a];
+    local[(size_t)job * p3 + e] = (T)(v + cst);
+}
+
 __global__ void k_strength_sums(int64_t N, int drho, const double* __restrict__ rho, double* __restrict__ out) {
     // out[a] = sum rho_a, out[drho + a] = sum |rho_a|
     double s[9], sa[9];
@@ -541,14 +654,14 @@ struct Pair;
 template <class T, bool GRAD>
 struct Pair<T, DMK_LAPLACE, GRAD> {
     static constexpr int DR = 1, DU = 1;
-    __device__ __forceinline__ static void eval(const Tab<T>& tb, const T* fq, const T* ff, T dx, T dy, T dz,
-                                                T r2, T inv_nu, const T* rho, T* u, T* gr) {
+    template <class SE>
+    __device__ __forceinline__ static void eval(const SE& se, T dx, T dy, T dz, T r2, T inv_nu, const T* rho, T* u,
+                                                T* gr) {
         const T rinv = rsqrt_t(r2);
-        const T t = fma(T(2) * r2, inv_nu * inv_nu, T(-1));
-        const T q = clenshaw(fq, tb.n_q, t);
+        const T q = se(kSerQ);
         u[0] = fma(rho[0], rinv - T(2) * inv_nu * q, u[0]);
         if (GRAD) {
-            const T f = clenshaw(ff, tb.n_f, t);
+            const T f = se(kSerF);
             const T ri2 = rinv * rinv;
             const T gfac = rho[0] * (ri2 * rinv + T(2) * inv_nu * (f - q) * ri2);
             gr[0] = fma(-dx, gfac, gr[0]);
@@ -568,20 +681,20 @@ template <> __device__ __forceinline__ double rsqrt_any<double>(double v) { retu
 template <class T, bool GRAD>
 struct Pair<T, DMK_STOKESLET, GRAD> {
     static constexpr int DR = 3, DU = 3;
-    __device__ __forceinline__ static void eval(const Tab<T>& tb, const T* fit, const T*, T dx, T dy, T dz,
-                                                T r2, T inv_nu, const T* rho, T* u, T* gr) {
+    template <class SE>
+    __device__ __forceinline__ static void eval(const SE& se, T dx, T dy, T dz, T r2, T inv_nu, const T* rho, T* u,
+                                                T* gr) {
         const T rinv = rsqrt_any(r2), ri2 = rinv * rinv;
-        const T t = fma(T(2) * r2, inv_nu * inv_nu, T(-1));
-        const T q = clenshaw(fit + tb.off_q, tb.n_q, t);
-        const T f = clenshaw(fit + tb.off_f, tb.n_f, t);
+        const T q = se(kSerQ);
+        const T f = se(kSerF);
         const T A = rinv - T(2) * inv_nu * (q + f);
         const T Bc = ri2 * rinv - T(2) * inv_nu * (q - f) * ri2;
         const T x[3] = {dx, dy, dz};
         const T xr = dx * rho[0] + dy * rho[1] + dz * rho[2];
         for (int j = 0; j < 3; ++j) u[j] += A * rho[j] + Bc * xr * x[j];
         if (GRAD) {
-            const T dq = clenshaw(fit + tb.off_dq, tb.n_dq, t);
-            const T df = clenshaw(fit + tb.off_df, tb.n_df, t);
+            const T dq = se(kSerDQ);
+            const T df = se(kSerDF);
             const T r = r2 * rinv;
             const T dsdr = T(2) * r * inv_nu * inv_nu;
             const T Ap = -ri2 - T(2) * inv_nu * (dq + df) * dsdr;
@@ -601,13 +714,13 @@ struct Pair<T, DMK_STRESSLET, GRAD> {
     static constexpr int DR = 9, DU = 3;
     // u_j = Pd v_j/(8 pi) - (3/(4 pi)) Po x_j w, v = Qx + Q^T x + x tr Q, w = x^T Q x,
     // Pd = T_diag/r^3 = -2 g/nu^3, Po = T_offd/r^5.  Stored as 8 pi * u: Pd v_j - 6 Po x_j w.
-    __device__ __forceinline__ static void eval(const Tab<T>& tb, const T* fit, const T*, T dx, T dy, T dz,
-                                                T r2, T inv_nu, const T* Q, T* u, T* gr) {
+    template <class SE>
+    __device__ __forceinline__ static void eval(const SE& se, T dx, T dy, T dz, T r2, T inv_nu, const T* Q, T* u,
+                                                T* gr) {
         const T rinv = rsqrt_any(r2), ri2 = rinv * rinv;
-        const T t = fma(T(2) * r2, inv_nu * inv_nu, T(-1));
-        const T q = clenshaw(fit + tb.off_q, tb.n_q, t);
-        const T f = clenshaw(fit + tb.off_f, tb.n_f, t);
-        const T g = clenshaw(fit + tb.off_g, tb.n_g, t);
+        const T q = se(kSerQ);
+        const T f = se(kSerF);
+        const T g = se(kSerG);
         const T in3 = inv_nu * inv_nu * inv_nu;
         const T Pd = T(-2) * g * in3;
         const T Po = ri2 * ri2 * rinv - T(2) * inv_nu * (q - f) * ri2 * ri2 - T(2.0 / 3.0) * g * in3 * ri2;
@@ -625,9 +738,9 @@ struct Pair<T, DMK_STRESSLET, GRAD> {
             u[j] += Pd * v[j] - T(6) * Po * x[j] * w;
         }
         if (GRAD) {
-            const T dq = clenshaw(fit + tb.off_dq, tb.n_dq, t);
-            const T df = clenshaw(fit + tb.off_df, tb.n_df, t);
-            const T dg = clenshaw(fit + tb.off_dg, tb.n_dg, t);
+            const T dq = se(kSerDQ);
+            const T df = se(kSerDF);
+            const T dg = se(kSerDG);
             const T r = r2 * rinv;
             const T dsdr = T(2) * r * inv_nu * inv_nu;
             const T Pdp = T(-2) * dg * dsdr * in3;
@@ -651,19 +764,19 @@ template <class T, bool GRAD>
 struct Pair<T, DMK_ROTLET, GRAD> {
     static constexpr int DR = 3, DU = 3;
     // u = (tau x x) Oc/(8 pi), Oc = Omega_offd / r^3
-    __device__ __forceinline__ static void eval(const Tab<T>& tb, const T* fit, const T*, T dx, T dy, T dz,
-                                                T r2, T inv_nu, const T* tau, T* u, T* gr) {
+    template <class SE>
+    __device__ __forceinline__ static void eval(const SE& se, T dx, T dy, T dz, T r2, T inv_nu, const T* tau, T* u,
+                                                T* gr) {
         const T rinv = rsqrt_any(r2), ri2 = rinv * rinv;
-        const T t = fma(T(2) * r2, inv_nu * inv_nu, T(-1));
-        const T q = clenshaw(fit + tb.off_q, tb.n_q, t);
-        const T f = clenshaw(fit + tb.off_f, tb.n_f, t);
+        const T q = se(kSerQ);
+        const T f = se(kSerF);
         const T Oc = ri2 * rinv - T(2) * inv_nu * (q - f) * ri2;
         const T x[3] = {dx, dy, dz};
         const T c[3] = {tau[1] * dz - tau[2] * dy, tau[2] * dx - tau[0] * dz, tau[0] * dy - tau[1] * dx};
         for (int j = 0; j < 3; ++j) u[j] += Oc * c[j];
         if (GRAD) {
-            const T dq = clenshaw(fit + tb.off_dq, tb.n_dq, t);
-            const T df = clenshaw(fit + tb.off_df, tb.n_df, t);
+            const T dq = se(kSerDQ);
+            const T df = se(kSerDF);
             const T r = r2 * rinv;
             const T dsdr = T(2) * r * inv_nu * inv_nu;
             const T Op = T(-3) * ri2 * ri2 - T(2) * inv_nu * ((dq - df) * dsdr * ri2 - T(2) * (q - f) * ri2 * rinv);
@@ -696,6 +809,9 @@ struct LeafOut {
     const double* rs;  // sorted strengths (FP64)
     const double* self_val;   // du x drho at nu = 1
     const double* self_grad;  // 3 x du x drho at nu = 1
+    const float* xh;          // FP32 path: leading FP32 parts of the sorted coordinates (3 x N)
+    const float* xl;          //            trailing parts
+    const float* rsf;         //            sorted strengths in FP32
 };
 
 constexpr int kLeafThreads = 128;
@@ -868,9 +984,8 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(int nleaf, const int* __r
                             const T dx = xt[0] - srcx[k][0], dy = xt[1] - srcx[k][1], dz = xt[2] - srcx[k][2];
                             const T r2 = dx * dx + dy * dy + dz * dz;
                             if (r2 < nu2 && r2 > T(0)) {
-                                P::eval(tab, K == DMK_LAPLACE ? fits + tab.off_q : fits,
-                                        K == DMK_LAPLACE ? fits + tab.off_f : fits, dx, dy, dz, r2, inv_nu,
-                                        srcr[k], pacc, pg);
+                                P::eval(ChebSeries<T>(tab, fits, r2, inv_nu), dx, dy, dz, r2, inv_nu, srcr[k], pacc,
+                                        pg);
                             }
                         }
                     }

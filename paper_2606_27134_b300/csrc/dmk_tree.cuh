@@ -47,12 +47,25 @@ __global__ void k_quantize(int64_t N, const double* __restrict__ pts, Geo g, dou
 
 // sorted order -> sorted SoA coordinates and strengths
 __global__ void k_gather(int64_t N, int drho, const int* __restrict__ idx, const double* __restrict__ w,
-                         const double* __restrict__ rho, double* __restrict__ xs, double* __restrict__ rs) {
+                         const double* __restrict__ rho, double* __restrict__ xs, double* __restrict__ rs,
+                         float* __restrict__ xh, float* __restrict__ xl, float* __restrict__ rsf) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= N) return;
     int i = idx[k];
-    for (int a = 0; a < 3; ++a) xs[a * N + k] = w[a * N + i];
-    for (int a = 0; a < drho; ++a) rs[k * drho + a] = rho[(int64_t)i * drho + a];
+    for (int a = 0; a < 3; ++a) {
+        const double v = w[a * N + i];
+        xs[a * N + k] = v;
+        if (xh) {   // leading + trailing FP32 parts (exact split of the FP64 value to 48 bits)
+            const float h = (float)v;
+            xh[a * N + k] = h;
+            xl[a * N + k] = (float)(v - (double)h);
+        }
+    }
+    for (int a = 0; a < drho; ++a) {
+        const double r = rho[(int64_t)i * drho + a];
+        rs[k * drho + a] = r;
+        if (rsf) rsf[k * drho + a] = (float)r;
+    }
 }
 
 __device__ __forceinline__ int64_t lower_bound_u64(const uint64_t* a, int64_t n, uint64_t v) {
@@ -201,6 +214,64 @@ __global__ void k_nonleaf_list(int nRl, const uint64_t* __restrict__ Rl, const u
     int b = off + (int)pos;
     nl_box[nl_off + k] = b;
     nl_of_box[b] = nl_off + k;
+}
+
+// per-level arrays of the forest, passed by value to the all-level kernels below
+struct LevelSet {
+    const uint64_t* cells[kMaxLevels + 1];   // sorted cell keys of each level
+    const uint64_t* R[kMaxLevels + 1];       // sorted non-leaf subset of each level
+    int off[kMaxLevels + 2];                 // first box of each level
+    int nl_off[kMaxLevels + 2];              // first non-leaf index of each level
+    int nR[kMaxLevels + 1];
+    int nlev;
+};
+
+__device__ __forceinline__ int level_of(const int* off, int nlev, int b) {
+    int l = 0;
+    while (l + 1 < nlev && off[l + 1] <= b) ++l;
+    return l;
+}
+
+// k_box_fill for every level in one launch
+__global__ void k_box_fill_all(LevelSet ls, int nb, const uint64_t* __restrict__ pkeys, int64_t N, Geo g,
+                               BoxArrays B) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const int level = level_of(ls.off, ls.nlev, b);
+    const int i = b - ls.off[level];
+    const uint64_t key = ls.cells[level][i];
+    B.key[b] = key;
+    B.level[b] = level;
+    int ix[3];
+    cell_ix(g, level, key, ix);
+    B.ix[3 * b] = ix[0];
+    B.ix[3 * b + 1] = ix[1];
+    B.ix[3 * b + 2] = ix[2];
+    int64_t lo, hi;
+    cell_range(pkeys, N, level, key, lo, hi);
+    B.start[b] = (int)lo;
+    B.end[b] = (int)hi;
+    const int nRl = ls.nR[level];
+    const int64_t r = (nRl > 0) ? find_u64(ls.R[level], nRl, key) : -1;
+    B.child0[b] = (r >= 0) ? ls.off[level + 1] + 8 * (int)r : -1;
+    B.nl[b] = (r >= 0) ? ls.nl_off[level] + (int)r : -1;
+    if (level == 0) {
+        B.parent[b] = -1;
+    } else {
+        const int np = ls.off[level] - ls.off[level - 1];
+        const int64_t pi = find_u64(ls.cells[level - 1], np, key >> 3);
+        B.parent[b] = (pi >= 0) ? ls.off[level - 1] + (int)pi : -1;
+    }
+}
+
+// non-leaf list of every level in one launch: nl_box[nl_off_l + k] = box of R_l[k]
+__global__ void k_nonleaf_all(LevelSet ls, int n_nl, int* __restrict__ nl_box) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_nl) return;
+    const int l = level_of(ls.nl_off, ls.nlev, t);
+    const int k = t - ls.nl_off[l];
+    const int ncell = ls.off[l + 1] - ls.off[l];
+    nl_box[t] = ls.off[l] + (int)find_u64(ls.cells[l], ncell, ls.R[l][k]);
 }
 
 // colleague table: coll[b * 27 + d] = box at the same level with offset d, or -1

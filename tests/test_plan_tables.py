@@ -82,3 +82,39 @@ def test_window_values(c_kernel, tol):
     assert v[1] == pytest.approx(d2phi, rel=1e-11)
     assert v[2] == pytest.approx(w.d2phihat0(), rel=1e-11)
     assert np.allclose(v[3:], w.phihat(0.099 * c * np.arange(11)), rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("kernel,tol", [("laplace", 1e-3), ("laplace", 1e-6), ("stokeslet", 1e-6),
+                                        ("stresslet", 1e-6), ("rotlet", 1e-3), ("laplace", 1e-9)])
+def test_residual_cubic_tables(kernel, tol):
+    """FP32-path piecewise cubic tables of the residual series (App. B polynomial approximations)
+    against the oracle's window: q = int_0^r phi / r, f = phi(r), g = phi'(r)/r in s = r^2, and
+    their s-derivatives from the identities dq/ds = (f - q)/(2s), df/ds = g/2,
+    dg/ds = (phi''(r) - g)/(2s).  The FP64 coefficients interpolate to 2e-8 of each series'
+    scale (well below FP32 rounding); rounded to FP32 and evaluated in FP32 they stay within 4e-7."""
+    from numpy.polynomial import legendre as npleg
+    info = dmk.plan_info(kernel, 3, [1, 1, 1], tol)
+    W = PSWFWindow(info["c"])
+    NT = 256
+    tab = dmk.plan_table(kernel, 3, [1, 1, 1], tol, 4).reshape(6, NT, 4)
+    rng = np.random.default_rng(11)
+    s = np.concatenate([rng.uniform(0.02, 1.0, 4000), [0.02, 0.5, 1.0 - 1e-12]])
+    r = np.sqrt(s)
+    I = 0.5 * (1.0 - W.Phi(r))                              # int_0^r phi
+    q = I / r
+    f = W.phi(r)
+    g = W.dphi(r) / r
+    d2 = npleg.legval(r, npleg.legder(W.phi_coef, 2))
+    ref = [q, f, g, (f - q) / (2 * s), g / 2, (d2 - g) / (2 * s)]
+    x = s * NT
+    i = np.minimum(x.astype(int), NT - 1)
+    u = x - i
+    for k in range(6):
+        c = tab[k, i]
+        val = c[:, 0] + u * (c[:, 1] + u * (c[:, 2] + u * c[:, 3]))
+        scale = np.max(np.abs(ref[k]))
+        assert np.max(np.abs(val - ref[k])) <= 2e-8 * scale, k
+        c32 = c.astype(np.float32)
+        u32 = u.astype(np.float32)
+        v32 = c32[:, 0] + u32 * (c32[:, 1] + u32 * (c32[:, 2] + u32 * c32[:, 3]))
+        assert np.max(np.abs(v32.astype(np.float64) - ref[k])) <= 4e-7 * scale, k
