@@ -13,6 +13,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "dmk_internal.h"
@@ -62,12 +63,14 @@ struct dmk_plan_s {
     double* d_self = nullptr;      // self_val then self_grad
     // workspace
     std::vector<DevBuf> bufs;
-    int* h_pinned = nullptr;
+    unsigned char* h_meta = nullptr;   // pinned host staging for the small per-evaluation readbacks
     cudaEvent_t ev[8] = {};
     int launches = 0;
     // set only while dmk_eval_static runs: device buffers are carved from this range
     unsigned char* arena = nullptr;
     size_t arena_cap = 0, arena_off = 0;
+    // dynamic shared memory already opted in per kernel (the attribute persists on the device)
+    std::unordered_map<const void*, size_t> smem_set;
 };
 
 namespace {
@@ -328,7 +331,11 @@ struct Evaluator {
 // opt in to `bytes` of dynamic shared memory (without it the limit is 48 KB minus the static part)
 template <class K>
 dmk_status_t set_smem(dmk_plan_s* plan, K kernel, size_t bytes) {
-    if (bytes > 0) CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    if (bytes == 0) return DMK_OK;
+    size_t& done = plan->smem_set[(const void*)kernel];
+    if (bytes <= done) return DMK_OK;
+    CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    done = bytes;
     return DMK_OK;
 }
 
@@ -469,13 +476,13 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     ++launches;
     k_strength_sums<<<std::min<unsigned>(nblk(N, 256), 1024), 256, 0, st>>>(N, drho, rs, d_sums);
     ++launches;
-    // ---- (2) refinement on device counters (one readback per batch of 4 levels) ---------
+    // ---- (2) refinement: one pass over the sorted keys, all levels at once ----------------
     int* d_nR = (int*)((char*)vmisc + 1024);       // non-leaf count per level
+    int* d_missing = (int*)((char*)vmisc + 1280);  // balance check, per level
     int* d_nleaf = (int*)((char*)vmisc + 1536);
     TreeInfo ti;
-    std::vector<uint64_t*> cells(kMaxLevels + 1, nullptr), Rl(kMaxLevels + 1, nullptr);
-    std::vector<int64_t> capC(kMaxLevels + 2, 0), capR(kMaxLevels + 2, 0);
-    // per-level cell and non-leaf key arrays: stream-ordered allocations released on return
+    std::vector<const uint64_t*> Rl(kMaxLevels + 1, nullptr);
+    // balance arrays that outgrow the refinement layout: stream-ordered, released on return
     std::vector<void*> level_mem;
     auto alloc_level = [&](size_t bytes, void** out) -> dmk_status_t {
         if (plan->arena) return arena_take(plan, bytes, out);
@@ -489,56 +496,72 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     auto free_levels = [&]() { for (void* p : level_mem) cudaFreeAsync(p, st); level_mem.clear(); };
     struct Guard { std::function<void()> f; ~Guard() { f(); } };
     Guard guard{free_levels};
-    void* vflags;
     // cells with more than n_s points are disjoint: at most N/(n_s+1) split per level
-    const int64_t maxsplit = std::max<int64_t>(1, N / ((int64_t)plan->n_s + 1));
+    const int64_t cap = std::max<int64_t>(1, N / ((int64_t)plan->n_s + 1));
+    const int nblkR = (int)((N + kRefineThreads - 1) / kRefineThreads);
+    void *vrblk, *vR;
+    CKS(ensure(plan, B_CNT, (size_t)2 * kBits * nblkR * sizeof(int), &vrblk));
+    CKS(ensure(plan, B_R, (size_t)kBits * cap * sizeof(uint64_t), &vR));
+    int* bcnt = (int*)vrblk;
+    int* boff = bcnt + (size_t)kBits * nblkR;
+    uint64_t* Rall = (uint64_t*)vR;
+    k_refine_count<<<nblkR, kRefineThreads, 0, st>>>(N, pkeys, plan->n_s, nblkR, bcnt);
+    k_refine_scan<<<1, 1024, 0, st>>>(nblkR, bcnt, boff, d_nR);
+    k_refine_write<<<nblkR, kRefineThreads, 0, st>>>(N, pkeys, plan->n_s, nblkR, boff, cap, Rall);
     {
-        void* c0;
-        CKS(alloc_level((size_t)Mtot * sizeof(uint64_t), &c0));
-        k_iota_u64<<<nblk(Mtot, 256), 256, 0, st>>>(Mtot, (uint64_t*)c0);
-        ++launches;
-        cells[0] = (uint64_t*)c0;
-        capC[0] = Mtot;
+        const int64_t nchk = (int64_t)(kBits - 1) * 27 * cap;
+        k_balance_check<<<(unsigned)((nchk + 255) / 256), 256, 0, st>>>(cap, Rall, d_nR, g, d_missing);
     }
-    std::vector<int> hnR(kMaxLevels + 1, 0);
-    int nlev = 0;
-    // first batch: the depth of a uniform distribution plus two levels, so that uniform inputs
-    // need a single readback; then batches of four
-    int batch = 2;
-    for (double cap = (double)Mtot * plan->n_s; cap < (double)N; cap *= 8) ++batch;
-    for (int l = 0; nlev == 0;) {
-        const int lend = std::min(l + batch, kBits + 1);
-        batch = 4;
-        for (; l < lend; ++l) {
-            capR[l] = std::min<int64_t>(capC[l], maxsplit);
-            CKS(ensure(plan, B_FLAGS, (size_t)capC[l] * sizeof(int), &vflags));
-            k_split_flags<<<nblk(capC[l], 256), 256, 0, st>>>((int)capC[l], cells[l], l, Mtot,
-                                                            l > 0 ? d_nR + l - 1 : d_nR, pkeys, N, plan->n_s,
-                                                            (int*)vflags);
-            void* r;
-            CKS(alloc_level((size_t)capR[l] * sizeof(uint64_t), &r));
-            size_t tb = 0;
-            cub::DeviceSelect::Flagged(nullptr, tb, cells[l], (int*)vflags, (uint64_t*)r, d_nR + l, (int)capC[l], st);
-            if (tb > cub_cap) { CKS(ensure(plan, B_CUB, tb, &vcub)); cub_cap = plan->bufs[B_CUB].cap; }
-            CK(cub::DeviceSelect::Flagged(vcub, tb, cells[l], (int*)vflags, (uint64_t*)r, d_nR + l, (int)capC[l], st));
-            Rl[l] = (uint64_t*)r;
-            capC[l + 1] = 8 * capR[l];
-            void* cn;
-            CKS(alloc_level((size_t)capC[l + 1] * sizeof(uint64_t), &cn));
-            k_children<<<nblk(capC[l + 1], 256), 256, 0, st>>>((int)capC[l + 1], Rl[l], d_nR + l, (uint64_t*)cn);
-            cells[l + 1] = (uint64_t*)cn;
-            launches += 4;
+    launches += 4;
+    // one pinned readback of nR[0..kBits] (misc + 1024) and missing[] (misc + 1280)
+    const int* hmeta = (const int*)plan->h_meta;
+    const int kMissing = 64;                              // int offset of missing[] in the copy
+    CK(cudaMemcpyAsync(plan->h_meta, d_nR, 512, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int nlev = kBits + 1;
+    for (int k = 0; k <= kBits; ++k)
+        if (hmeta[k] == 0) { nlev = k + 1; break; }
+    for (int l = 0; l < nlev; ++l) Rl[l] = Rall + (size_t)l * cap;
+    bool balanced = true;
+    for (int k = 0; k < kBits; ++k)
+        if (hmeta[kMissing + k] != 0) balanced = false;
+    std::vector<int64_t> cR(nlev);
+    for (int k = 0; k < nlev; ++k) cR[k] = hmeta[k];
+    // ---- (3) 2:1 balance, finest non-leaf level upward (only when the check found gaps) -----
+    // Small levels: one single-CTA kernel per level, no host round trip until the end; if one
+    // of them reports more new cells than it holds, the general path below redoes the balance
+    // from the refinement arrays.
+    bool need_general = false;
+    if (!balanced) {
+        int64_t worst = 0;
+        for (int l = 1; l < nlev; ++l) worst = std::max(worst, 27 * cR[l]);
+        if (worst <= ((int64_t)1 << 20)) {
+            int* d_overflow = (int*)((char*)vmisc + 1600);
+            std::vector<const uint64_t*> Rs(Rl);
+            std::vector<int64_t> cs(cR);
+            for (int l = nlev - 2; l >= 1; --l) {
+                void* vo;
+                CKS(alloc_level((size_t)(cs[l - 1] + kBalNew) * sizeof(uint64_t), &vo));
+                k_balance_small<<<1, kBalThreads, 0, st>>>(Rs[l], Rs[l - 1], d_nR, l, g, (uint64_t*)vo, d_overflow);
+                Rs[l - 1] = (const uint64_t*)vo;
+                cs[l - 1] += kBalNew;
+                ++launches;
+            }
+            CK(cudaMemcpyAsync(plan->h_meta, d_nR, 1024, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (hmeta[(1600 - 1024) / 4] == 0) {
+                Rl = Rs;
+            } else {
+                need_general = true;
+                // restore the refinement counts
+                for (int k = 0; k < nlev; ++k) ((int*)plan->h_meta)[k] = (int)cR[k];
+                CK(cudaMemcpyAsync(d_nR, plan->h_meta, nlev * sizeof(int), cudaMemcpyHostToDevice, st));
+            }
+        } else {
+            need_general = true;
         }
-        CK(cudaMemcpyAsync(hnR.data(), d_nR, l * sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        for (int k = 0; k < l; ++k)
-            if (hnR[k] == 0) { nlev = k + 1; break; }
-        if (nlev == 0 && l > kBits) nlev = kBits + 1;      // level kBits never splits
     }
-    // ---- (3) 2:1 balance, finest non-leaf level upward, on device counters ----------------
-    {
-        std::vector<int64_t> cR(nlev);
-        for (int k = 0; k < nlev; ++k) cR[k] = hnR[k];
+    if (need_general) {
         for (int l = nlev - 2; l >= 1; --l) {
             const int64_t capP = cR[l - 1];
             const int64_t ncand = 27 * cR[l] + capP;
@@ -556,22 +579,17 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
             CK(cub::DeviceRadixSort::SortKeys(vcub, tb, (uint64_t*)va, (uint64_t*)vb, (int)ncand, 0, kbits, st));
             CK(cub::DeviceSelect::Unique(vcub, tb2, (uint64_t*)vb, (uint64_t*)va, d_nR + l - 1, (int)ncand, st));
             k_trim_invalid<<<1, 1, 0, st>>>((uint64_t*)va, d_nR + l - 1);
-            Rl[l - 1] = (uint64_t*)va;
+            Rl[l - 1] = (const uint64_t*)va;
             const int64_t maxcells = (3 * (l - 1) < 40) ? ((int64_t)Mtot << (3 * (l - 1))) : ncand;
             cR[l - 1] = std::min(ncand, maxcells);
-            void* cn;
-            CKS(alloc_level((size_t)8 * cR[l - 1] * sizeof(uint64_t), &cn));
-            k_children<<<nblk(8 * cR[l - 1], 256), 256, 0, st>>>((int)(8 * cR[l - 1]), Rl[l - 1], d_nR + l - 1,
-                                                                 (uint64_t*)cn);
-            cells[l] = (uint64_t*)cn;
-            launches += 9;
+            launches += 6;
         }
-        CK(cudaMemcpyAsync(hnR.data(), d_nR, nlev * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(plan->h_meta, d_nR, nlev * sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        for (int k = 0; k < nlev; ++k) {
-            ti.nR.push_back(hnR[k]);
-            ti.ncell.push_back(k == 0 ? Mtot : 8 * hnR[k - 1]);
-        }
+    }
+    for (int k = 0; k < nlev; ++k) {
+        ti.nR.push_back(hmeta[k]);
+        ti.ncell.push_back(k == 0 ? Mtot : 8 * hmeta[k - 1]);
     }
     // ---- (4) box arrays -----------------------------------------------------------------
     ti.nlev = nlev;
@@ -593,10 +611,6 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     int* bi = (int*)vbi;
     B.level = bi; B.ix = bi + nb; B.start = bi + 4 * nb; B.end = bi + 5 * nb; B.child0 = bi + 6 * nb;
     B.parent = bi + 7 * nb; B.nl = bi + 8 * nb; B.coll = bi + 9 * nb;
-    int* d_level_off = bi + 36 * nb;
-    int* d_level_cnt = d_level_off + (kMaxLevels + 2);
-    CK(cudaMemcpyAsync(d_level_off, ti.off.data(), nlev * sizeof(int), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_level_cnt, ti.ncell.data(), nlev * sizeof(int), cudaMemcpyHostToDevice, st));
     LevelSet ls;
     std::memset(&ls, 0, sizeof(ls));
     ls.nlev = nlev;
@@ -605,61 +619,55 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         ls.nl_off[l] = ti.nl_off[l];
     }
     for (int l = 0; l < nlev; ++l) {
-        ls.cells[l] = cells[l];
         ls.R[l] = Rl[l];
         ls.nR[l] = ti.nR[l];
     }
-    k_box_fill_all<<<nblk(nb, 256), 256, 0, st>>>(ls, nb, pkeys, N, g, B);
-    ++launches;
-    void* vnl;
+    void *vnl, *vflags, *vleaves, *viota;
     CKS(ensure(plan, B_NLBOX, (size_t)std::max(n_nl, 1) * sizeof(int), &vnl));
-    int* nl_box = (int*)vnl;
-    if (n_nl > 0) {
-        k_nonleaf_all<<<nblk(n_nl, 256), 256, 0, st>>>(ls, n_nl, nl_box);
-        ++launches;
-    }
-    k_colleagues<<<nblk((int64_t)27 * nb, 256), 256, 0, st>>>(nb, B.level, B.ix, B.key, d_level_off, d_level_cnt, g,
-                                                              B.coll);
-    ++launches;
-    // leaves with points
     CKS(ensure(plan, B_FLAGS, (size_t)nb * sizeof(int), &vflags));
-    void* vleaves;
     CKS(ensure(plan, B_LEAVES, (size_t)nb * sizeof(int), &vleaves));
+    CKS(ensure(plan, B_CAND, (size_t)nb * sizeof(int), &viota));
+    int* nl_box = (int*)vnl;
     int* leaves = (int*)vleaves;
-    void* viota;
-    CKS(ensure(plan, B_CNT, (size_t)nb * sizeof(int), &viota));
-    k_leaf_flags<<<nblk(nb, 256), 256, 0, st>>>(nb, B.child0, B.start, B.end, (int*)vflags, (int*)viota);
+    k_box_fill_all<<<nblk(nb, 256), 256, 0, st>>>(ls, nb, pkeys, N, g, B, nl_box, (int*)vflags, (int*)viota);
+    k_colleagues<<<nblk((int64_t)27 * nb, 256), 256, 0, st>>>(nb, B.level, B.ix, B.key, ls, g, B.coll);
+    launches += 2;
+    // leaves with points, in box order
     {
         size_t tb = 0;
         cub::DeviceSelect::Flagged(nullptr, tb, (int*)viota, (int*)vflags, leaves, d_nleaf, nb, st);
         if (tb > cub_cap) { CKS(ensure(plan, B_CUB, tb, &vcub)); cub_cap = plan->bufs[B_CUB].cap; }
         CK(cub::DeviceSelect::Flagged(vcub, tb, (int*)viota, (int*)vflags, leaves, d_nleaf, nb, st));
-        launches += 3;
+        launches += 2;
     }
     // direct lists: counts for every possible leaf slot, scan, one readback of the totals
     void *vdo, *vdl;
     CKS(ensure(plan, B_DOFFS, (size_t)(nb + 1) * sizeof(int), &vdo));
     int* doffs = (int*)vdo;
     CK(cudaMemsetAsync(doffs, 0, (nb + 1) * sizeof(int), st));
-    k_direct<false><<<nblk(nb, 128), 128, 0, st>>>(nb, d_nleaf, leaves, B, g, doffs, nullptr, nullptr, d_pairs);
+    k_direct<false><<<nblk((int64_t)32 * nb, 128), 128, 0, st>>>(nb, d_nleaf, leaves, B, g, doffs, nullptr, nullptr,
+                                                                 d_pairs);
     {
         size_t tb = 0;
         cub::DeviceScan::ExclusiveSum(nullptr, tb, doffs, doffs, nb + 1, st);
         if (tb > cub_cap) { CKS(ensure(plan, B_CUB, tb, &vcub)); cub_cap = plan->bufs[B_CUB].cap; }
         CK(cub::DeviceScan::ExclusiveSum(vcub, tb, doffs, doffs, nb + 1, st));
-        int hv[2] = {0, 0};
-        CK(cudaMemcpyAsync(&hv[0], d_nleaf, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(&hv[1], doffs + nb, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(&ti.n_pairs, d_pairs, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        // pinned readback: misc + 768 .. + 1540 holds the pair count and the leaf count
+        CK(cudaMemcpyAsync(plan->h_meta, (char*)vmisc + 768, 772, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(plan->h_meta + 1024, doffs + nb, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        ti.n_leafp = hv[0];
-        ti.n_entries = hv[1];
+        int n_entries = 0;
+        std::memcpy(&ti.n_pairs, plan->h_meta, sizeof(unsigned long long));
+        std::memcpy(&ti.n_leafp, plan->h_meta + (1536 - 768), sizeof(int));
+        std::memcpy(&n_entries, plan->h_meta + 1024, sizeof(int));
+        ti.n_entries = n_entries;
         launches += 3;
     }
     const int nleaf = ti.n_leafp;
     CKS(ensure(plan, B_DL, (size_t)std::max<int64_t>(ti.n_entries, 1) * sizeof(DirectEntry), &vdl));
     DirectEntry* dl = (DirectEntry*)vdl;
-    k_direct<true><<<nblk(nleaf, 128), 128, 0, st>>>(nleaf, d_nleaf, leaves, B, g, nullptr, doffs, dl, nullptr);
+    k_direct<true><<<nblk((int64_t)32 * nleaf, 128), 128, 0, st>>>(nleaf, d_nleaf, leaves, B, g, nullptr, doffs, dl,
+                                                                   nullptr);
     ++launches;
     rec(1);
     // ---- (5) upward pass ---------------------------------------------------------------
@@ -746,7 +754,24 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         void* vpw;
         CKS(ensure(plan, B_PW, (size_t)n_nl * drho * nW * sizeof(Cx<T>), &vpw));
         Cx<T>* W = (Cx<T>*)vpw;
-        {
+        // register-blocked outgoing transform: FP32 path (the FP64 tensors do not fit in shared memory)
+        const size_t po2_bytes = pwout2_smem<T>(p, NF, nfh);
+        bool pwout_done = false;
+        if constexpr (sizeof(T) == 4) {
+            if (p <= kMaxPFast && nfh <= mp && po2_bytes <= plan->smem_optin) {
+                const unsigned grid = (unsigned)std::min(n_nl, 148 * 2);
+                if (mp == 20) {
+                    CKS(set_smem(plan, k_pwout2<T, 20>, po2_bytes));
+                    k_pwout2<T, 20><<<grid, 416, po2_bytes, st>>>(n_nl, nl_box, tab, proxy, W);
+                } else {
+                    CKS(set_smem(plan, k_pwout2<T, kMaxPFast>, po2_bytes));
+                    k_pwout2<T, kMaxPFast><<<grid, 416, po2_bytes, st>>>(n_nl, nl_box, tab, proxy, W);
+                }
+                ++launches;
+                pwout_done = true;
+            }
+        }
+        if (!pwout_done) {
             size_t bytes = ((size_t)p * p * nfh + (size_t)p * NF * nfh) * sizeof(Cx<T>);
             Place pl;
             unsigned char* scr;
@@ -853,9 +878,11 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     CK(cudaGetLastError());
     int herr = 0;
     double hs[18];
-    CK(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(hs, d_sums, 2 * drho * sizeof(double), cudaMemcpyDeviceToHost, st));
+    // pinned readback of the error flags (misc + 0) and strength sums (misc + 256)
+    CK(cudaMemcpyAsync(plan->h_meta, vmisc, 256 + 2 * drho * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    std::memcpy(&herr, plan->h_meta, sizeof(int));
+    std::memcpy(hs, plan->h_meta + 256, 2 * drho * sizeof(double));
     if (herr & kErrNonFinite) { plan->err = "non-finite coordinate"; return DMK_ERR_OUT_OF_DOMAIN; }
     if (herr & kErrDomain) { plan->err = "a free coordinate lies outside [0, L_i)"; return DMK_ERR_OUT_OF_DOMAIN; }
     if (P.kernel == DMK_LAPLACE && (P.D == 1 || P.D == 2) && std::fabs(hs[0]) > 1e-12 * std::max(hs[1], 1e-300)) {
@@ -918,6 +945,13 @@ dmk_status_t make_plan(int k, int D, const double L[3], double tol, int prec, in
         g_plan_error = plan->err;
         dmk_destroy(plan);
         return s;
+    }
+    e = cudaMallocHost((void**)&plan->h_meta, 4096);
+    if (e != cudaSuccess) {
+        plan->h_meta = nullptr;
+        g_plan_error = std::string("pinned host allocation failed: ") + cudaGetErrorString(e);
+        dmk_destroy(plan);
+        return DMK_ERR_OOM;
     }
     for (int i = 0; i < 8; ++i) cudaEventCreate(&plan->ev[i]);
     *out = plan;
@@ -1038,6 +1072,7 @@ dmk_status_t dmk_destroy(dmk_plan_t plan) {
     if (plan->d_self) cudaFree(plan->d_self);
     for (int i = 0; i < 8; ++i)
         if (plan->ev[i]) cudaEventDestroy(plan->ev[i]);
+    if (plan->h_meta) cudaFreeHost(plan->h_meta);
     delete plan;
     return DMK_OK;
 }

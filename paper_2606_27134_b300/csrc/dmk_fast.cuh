@@ -50,6 +50,26 @@ __device__ __forceinline__ void fiber_store(T* out, int p, int P, int ax, int fa
     }
 }
 
+// p^3 tensor from global memory into the padded shared layout, KB independent loads in flight
+// per thread
+template <class T, int KB = 8>
+__device__ __forceinline__ void load_padded_batched(T* dst, const T* __restrict__ src, int p, int P) {
+    const int p3 = p * p * p;
+    for (int e0 = threadIdx.x; e0 < p3; e0 += KB * blockDim.x) {
+        T v[KB];
+#pragma unroll
+        for (int u = 0; u < KB; ++u) {
+            const int e = e0 + u * blockDim.x;
+            v[u] = e < p3 ? src[e] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < KB; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < p3) dst[(e / p) * P + (e % p)] = v[u];
+        }
+    }
+}
+
 // operator rows into shared memory: Ms[k * MAXP + j] = src(k, j) (zero beyond p)
 template <class T, int MAXP, class F>
 __device__ __forceinline__ void load_op(T* Ms, int p, F src) {
@@ -421,9 +441,108 @@ __global__ void __launch_bounds__(kTransThreads) k_pw_trans(int n, const int* __
     }
 }
 
+// Plane-wave outgoing expansions (Sec. 3.1.4, Eq. Dl_int_discr), register-blocked: for every
+// non-leaf box W(m) = sum_j proxy(j) exp(-i h m . y_j), m3 >= 0 only (real input).  The proxy
+// tensor is staged in shared memory; stage 1, thread per (j1, j2) fiber: j3 -> m3 with the
+// fiber in registers; stage 2, thread per (j1, m3, half of m2): j2 -> m2; stage 3, thread per
+// (m2, m3, half of m1): j1 -> m1, written to W[nl][a][(m1 NF + m2) nfh + m3].
+template <class T, int MAXP>
+__global__ void __launch_bounds__(416) k_pwout2(int n, const int* __restrict__ nl_box, Tab<T> tab,
+                                                const T* __restrict__ proxy, Cx<T>* __restrict__ W) {
+    const int p = tab.p, p2 = p * p, p3 = p2 * p, P = odd_pitch(p), drho = tab.d_rho;
+    const int nf = tab.nf, NF = tab.NF, nfh = tab.nfh, nW = NF * NF * nfh;
+    const int NFP = NF + 1;                                    // row pitch of Et
+    const int pm3 = nfh | 1;
+    const int H = (NF + 1) / 2;                                // outputs per thread in stages 2, 3
+    constexpr int MAXH = MAXP + 2;                             // H <= MAXH, nfh <= MAXP
+    Cx<T>* Et = reinterpret_cast<Cx<T>*>(dsmem);               // p x NFP: Et[k][m] = E[m][k]
+    Cx<T>* A1 = Et + p * NFP;                                  // p^2 x pm3
+    Cx<T>* A2 = A1 + p2 * pm3;                                 // p x NF x nfh
+    T* X = reinterpret_cast<T*>(A2 + p * NF * nfh);            // p^2 x P
+    for (int e = threadIdx.x; e < p * NFP; e += blockDim.x) {
+        const int k = e / NFP, m = e % NFP;
+        Et[e] = (m < NF) ? tab.E[m * p + k] : Cx<T>{0, 0};
+    }
+    for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
+        const int box = nl_box[bi];
+        for (int a = 0; a < drho; ++a) {
+            __syncthreads();
+            load_padded_batched<T>(X, proxy + ((size_t)box * drho + a) * p3, p, P);
+            __syncthreads();
+            for (int c = threadIdx.x; c < p2; c += blockDim.x) {       // j3 -> m3
+                T x[MAXP];
+#pragma unroll
+                for (int k = 0; k < MAXP; ++k) x[k] = (k < p) ? X[c * P + k] : T(0);
+                Cx<T> acc[MAXP];
+#pragma unroll
+                for (int m = 0; m < MAXP; ++m) acc[m] = {0, 0};
+#pragma unroll
+                for (int k = 0; k < MAXP; ++k) {
+                    if (k < p) {
+                        const Cx<T>* row = Et + k * NFP + nf;
+#pragma unroll
+                        for (int m = 0; m < MAXP; ++m)
+                            if (m < nfh) cfmar(acc[m], row[m], x[k]);
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < MAXP; ++m)
+                    if (m < nfh) A1[c * pm3 + m] = acc[m];
+            }
+            __syncthreads();
+            for (int c = threadIdx.x; c < 2 * p * nfh; c += blockDim.x) {   // j2 -> m2
+                const int h = c / (p * nfh), r = c % (p * nfh);
+                const int j1 = r / nfh, m3 = r % nfh;
+                const int m0 = h * H, mc = min(H, NF - m0);
+                Cx<T> acc[MAXH];
+#pragma unroll
+                for (int m = 0; m < MAXH; ++m) acc[m] = {0, 0};
+                for (int k = 0; k < p; ++k) {
+                    const Cx<T> v = A1[(j1 * p + k) * pm3 + m3];
+                    const Cx<T>* row = Et + k * NFP + m0;
+#pragma unroll
+                    for (int m = 0; m < MAXH; ++m)
+                        if (m < mc) cfma(acc[m], row[m], v);
+                }
+#pragma unroll
+                for (int m = 0; m < MAXH; ++m)
+                    if (m < mc) A2[(j1 * NF + m0 + m) * nfh + m3] = acc[m];
+            }
+            __syncthreads();
+            Cx<T>* out = W + ((size_t)bi * drho + a) * nW;
+            for (int c = threadIdx.x; c < 2 * NF * nfh; c += blockDim.x) {  // j1 -> m1
+                const int h = c / (NF * nfh), r = c % (NF * nfh);
+                const int m0 = h * H, mc = min(H, NF - m0);
+                Cx<T> acc[MAXH];
+#pragma unroll
+                for (int m = 0; m < MAXH; ++m) acc[m] = {0, 0};
+                for (int k = 0; k < p; ++k) {
+                    const Cx<T> v = A2[k * NF * nfh + r];
+                    const Cx<T>* row = Et + k * NFP + m0;
+#pragma unroll
+                    for (int m = 0; m < MAXH; ++m)
+                        if (m < mc) cfma(acc[m], row[m], v);
+                }
+#pragma unroll
+                for (int m = 0; m < MAXH; ++m)
+                    if (m < mc) out[(size_t)(m0 + m) * NF * nfh + r] = acc[m];
+            }
+        }
+    }
+}
+
+// shared memory of k_pwout2
+template <class T>
+inline size_t pwout2_smem(int p, int NF, int nfh) {
+    const int P = p | 1, pm3 = nfh | 1;
+    return ((size_t)p * (NF + 1) + (size_t)p * p * pm3 + (size_t)p * NF * nfh) * sizeof(Cx<T>) +
+           (size_t)p * p * P * sizeof(T);
+}
+
 // Incoming transform (Sec. 3.1.4) from the translated spectrum Vw of k_pw_trans: stage A, thread
 // per spectral column (m2, m3), m1 -> j1 with the column read from global memory in batches;
-// stages B (m2 -> j2) and C (m3 -> j3, half-spectrum weights) as in k_pwin2.
+// stages B (m2 -> j2) and C (m3 -> j3, half-spectrum weights, 1 for m3 = 0 and 2 otherwise) in
+// shared memory with an odd row pitch.
 template <class T, int MAXP>
 __global__ void __launch_bounds__(384) k_pwin3(int n, const int* __restrict__ nl_box, Tab<T> tab,
                                                const Cx<T>* __restrict__ Vw, T* __restrict__ local) {
@@ -507,109 +626,6 @@ __global__ void __launch_bounds__(384) k_pwin3(int n, const int* __restrict__ nl
     }
 }
 
-// Translation + difference-kernel symbol + incoming transform (Sec. 3.1.4, Eq. Dl_int_discr)
-// without materialising the weighted spectrum.  Stage A: thread per spectral column (m2, m3)
-// gathers V(m1, m2, m3) from the non-leaf colleagues, applies 2^(a l) g(m) op(m), and contracts
-// m1 -> j1 into p register accumulators.  Stage B: thread per (j1, m3), m2 -> j2.  Stage C:
-// thread per (j1, j2), m3 -> j3 with the half-spectrum weights (1 for m3 = 0, 2 otherwise).
-template <class T, int MAXP>
-__global__ void __launch_bounds__(384) k_pwin2(int n, const int* __restrict__ nl_box, BoxArrays B, Tab<T> tab,
-                                               const Cx<T>* __restrict__ W, T* __restrict__ local) {
-    const int p = tab.p, p2 = p * p, p3 = p2 * p, drho = tab.d_rho, du = tab.d_u;
-    const int nf = tab.nf, NF = tab.NF, nfh = tab.nfh, nW = NF * NF * nfh;
-    const int pm3 = nfh | 1;                                   // odd pitch of the m3 axis in B1
-    Cx<T>* F = reinterpret_cast<Cx<T>*>(dsmem);                // NF x MAXP: conj(E), zero-padded
-    Cx<T>* B2 = F + NF * MAXP;                                 // p x NF x nfh
-    Cx<T>* B1 = B2 + p * NF * nfh;                             // p x p x pm3
-    __shared__ int ncol;
-    __shared__ int col_nl[27];
-    __shared__ int col_d[27];
-    for (int e = threadIdx.x; e < NF * MAXP; e += blockDim.x) {
-        const int m = e / MAXP, j = e % MAXP;
-        F[e] = (j < p) ? cconj(tab.E[m * p + j]) : Cx<T>{0, 0};
-    }
-    for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
-        const int box = nl_box[bi];
-        const int l = B.level[box];
-        const T scale = (T)ldexp(1.0, tab.level_power * l);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int k = 0;
-            for (int d = 0; d < 27; ++d) {
-                const int C = B.coll[box * 27 + d];
-                if (C >= 0 && B.nl[C] >= 0) { col_nl[k] = B.nl[C]; col_d[k] = d; ++k; }
-            }
-            ncol = k;
-        }
-        __syncthreads();
-        for (int j = 0; j < du; ++j) {
-            // stage A
-            for (int c = threadIdx.x; c < NF * nfh; c += blockDim.x) {
-                const int i2 = c / nfh, m3 = c % nfh;
-                Cx<T> acc[MAXP];
-#pragma unroll
-                for (int q = 0; q < MAXP; ++q) acc[q] = {0, 0};
-                for (int i1 = 0; i1 < NF; ++i1) {
-                    const int e = (i1 * NF + i2) * nfh + m3;
-                    const int m1 = i1 - nf, m2 = i2 - nf;
-                    Cx<T> o;
-                    if (drho == 1)
-                        o = pw_gather_op<T, 1>(tab.kernel, j, m1, m2, m3, e, nW, ncol, col_nl, col_d, W);
-                    else if (drho == 3)
-                        o = pw_gather_op<T, 3>(tab.kernel, j, m1, m2, m3, e, nW, ncol, col_nl, col_d, W);
-                    else
-                        o = pw_gather_op<T, 9>(tab.kernel, j, m1, m2, m3, e, nW, ncol, col_nl, col_d, W);
-                    const T gs = scale * tab.gdiff[e];
-                    o = {gs * o.x, gs * o.y};
-                    const Cx<T>* Fr = F + i1 * MAXP;
-#pragma unroll
-                    for (int q = 0; q < MAXP; ++q) cfma(acc[q], Fr[q], o);
-                }
-#pragma unroll
-                for (int q = 0; q < MAXP; ++q)
-                    if (q < p) B2[(q * NF + i2) * nfh + m3] = acc[q];
-            }
-            __syncthreads();
-            // stage B
-            for (int c = threadIdx.x; c < p * nfh; c += blockDim.x) {
-                const int j1 = c / nfh, m3 = c % nfh;
-                Cx<T> acc[MAXP];
-#pragma unroll
-                for (int q = 0; q < MAXP; ++q) acc[q] = {0, 0};
-                for (int i2 = 0; i2 < NF; ++i2) {
-                    const Cx<T> b = B2[(j1 * NF + i2) * nfh + m3];
-                    const Cx<T>* Fr = F + i2 * MAXP;
-#pragma unroll
-                    for (int q = 0; q < MAXP; ++q) cfma(acc[q], Fr[q], b);
-                }
-#pragma unroll
-                for (int q = 0; q < MAXP; ++q)
-                    if (q < p) B1[(j1 * p + q) * pm3 + m3] = acc[q];
-            }
-            __syncthreads();
-            // stage C
-            T* u = local + ((size_t)box * du + j) * p3;
-            for (int c = threadIdx.x; c < p2; c += blockDim.x) {
-                T acc[MAXP];
-#pragma unroll
-                for (int q = 0; q < MAXP; ++q) acc[q] = 0;
-                for (int m3 = 0; m3 < nfh; ++m3) {
-                    const Cx<T> b = B1[c * pm3 + m3];
-                    const T wgt = (m3 == 0) ? T(1) : T(2);
-                    const Cx<T> bw = {wgt * b.x, wgt * b.y};
-                    const Cx<T>* Fr = F + (nf + m3) * MAXP;
-#pragma unroll
-                    for (int q = 0; q < MAXP; ++q) acc[q] = fma(Fr[q].x, bw.x, fma(-Fr[q].y, bw.y, acc[q]));
-                }
-#pragma unroll
-                for (int q = 0; q < MAXP; ++q)
-                    if (q < p) u[c * p + q] += acc[q];
-            }
-            __syncthreads();
-        }
-    }
-}
-
 }  // namespace dmk
 
 namespace dmk {
@@ -676,11 +692,19 @@ __global__ void __launch_bounds__(kLeaf3Threads) k_leaf3(int nleaf, const int* _
             fits[e] = tab.fit[e];
     }
     const int tt = threadIdx.x;
+    // per-level scales by exact power-of-two scaling of per-launch constants (no FP64 division
+    // in the loops); FP32 path: leading/trailing FP32 parts of the periods
+    const double inv_s = 1.0 / g.s, s2 = g.s * g.s;
+    const float inv_s_f = (float)inv_s, s2_f = (float)s2;
+    float Lh[3], Ll[3];
+    for (int a = 0; a < 3; ++a) split_double(g.L[a], Lh[a], Ll[a]);
     for (int li = blockIdx.x; li < nleaf; li += gridDim.x) {
         const int box = leaves[li];
         const int l = B.level[box];
-        const double r = g.s / (double)(1 << l), half = 0.5 * r;
+        const double r = ldexp(g.s, -l), half = 0.5 * r;
         const double c[3] = {(B.ix[3 * box] + 0.5) * r, (B.ix[3 * box + 1] + 0.5) * r, (B.ix[3 * box + 2] + 0.5) * r};
+        float ch[3], cl[3];            // FP32 parts of -centre
+        for (int a = 0; a < 3; ++a) split_double(-c[a], ch[a], cl[a]);
         const int st = B.start[box], en = B.end[box];
         for (int t0 = st; t0 < en; t0 += kLeaf3Threads) {
             const int nt = min(kLeaf3Threads, en - t0);
@@ -692,9 +716,7 @@ __global__ void __launch_bounds__(kLeaf3Threads) k_leaf3(int nleaf, const int* _
                 const int tg = t0 + tt;
                 for (int a = 0; a < 3; ++a) {
                     if constexpr (kTwo) {
-                        float ch, cl;
-                        split_double(-c[a], ch, cl);
-                        two_float_add(out.xh[a * N + tg], out.xl[a * N + tg], ch, cl, xt[a], xtl[a]);
+                        two_float_add(out.xh[a * N + tg], out.xl[a * N + tg], ch[a], cl[a], xt[a], xtl[a]);
                     } else {
                         xt[a] = (T)(xs[a * N + tg] - c[a]);
                     }
@@ -819,17 +841,22 @@ __global__ void __launch_bounds__(kLeaf3Threads) k_leaf3(int nleaf, const int* _
                     const DirectEntry de = dl[e];
                     const int take = min(de.end - de.start - eo, kSrcChunk - filled);
                     const int lev = de.code >> 6;
-                    const double sh0 = (double)(((de.code) & 3) - 1) * g.L[0];
-                    const double sh1 = (double)(((de.code >> 2) & 3) - 1) * g.L[1];
-                    const double sh2 = (double)(((de.code >> 4) & 3) - 1) * g.L[2];
-                    const double inv = (double)(1 << lev) / g.s;
-                    const T nu2 = (T)(1.0 / (inv * inv));
-                    const T tinv = (T)inv;
-                    // image shift minus the target leaf's centre, per entry
-                    const double E[3] = {sh0 - c[0], sh1 - c[1], sh2 - c[2]};
+                    const int sb[3] = {((de.code) & 3) - 1, ((de.code >> 2) & 3) - 1, ((de.code >> 4) & 3) - 1};
+                    // 1/nu and nu^2 of the entry's level; image shift minus the target leaf's
+                    // centre (FP32 parts in the FP32 path)
+                    T nu2, tinv;
+                    double E[3] = {0, 0, 0};
                     float Eh[3] = {0, 0, 0}, El[3] = {0, 0, 0};
-                    if constexpr (kTwo)
-                        for (int a = 0; a < 3; ++a) split_double(E[a], Eh[a], El[a]);
+                    if constexpr (kTwo) {
+                        tinv = ldexpf(inv_s_f, lev);
+                        nu2 = ldexpf(s2_f, -2 * lev);
+                        for (int a = 0; a < 3; ++a)
+                            two_float_add((float)sb[a] * Lh[a], (float)sb[a] * Ll[a], ch[a], cl[a], Eh[a], El[a]);
+                    } else {
+                        tinv = (T)ldexp(inv_s, lev);
+                        nu2 = (T)ldexp(s2, -2 * lev);
+                        for (int a = 0; a < 3; ++a) E[a] = (double)sb[a] * g.L[a] - c[a];
+                    }
                     for (int k = tt; k < take; k += kLeaf3Threads) {
                         const int si = de.start + eo + k, slot = filled + k;
                         Q4 a, b;
@@ -856,21 +883,37 @@ __global__ void __launch_bounds__(kLeaf3Threads) k_leaf3(int nleaf, const int* _
                 }
                 __syncthreads();
                 if (act) {
+                    // support tests of 32 sources into a bit mask (independent iterations),
+                    // then the set bits appended to the queue; the queue column is swizzled by
+                    // row so that lanes with different queue lengths write to different banks
                     int cnt = 0;
-#pragma unroll 4
-                    for (int k = 0; k < filled; ++k) {
-                        const Q4 a = sA[k];
-                        const T dx = xt[0] - a.x, dy = xt[1] - a.y, dz = xt[2] - a.z;
-                        const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                        if (r2 < a.w) q[cnt++][tt] = (unsigned char)k;
+                    for (int k0 = 0; k0 < filled; k0 += 32) {
+                        const int kn = min(32, filled - k0);
+                        unsigned mask = 0;
+#pragma unroll 8
+                        for (int kk = 0; kk < 32; ++kk) {
+                            if (kk < kn) {
+                                const Q4 a = sA[k0 + kk];
+                                const T dx = xt[0] - a.x, dy = xt[1] - a.y, dz = xt[2] - a.z;
+                                const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                                mask |= (r2 < a.w ? 1u : 0u) << kk;
+                            }
+                        }
+                        while (mask) {
+                            const int kk = __ffs(mask) - 1;
+                            mask &= mask - 1;
+                            q[cnt][tt ^ ((cnt & 7) << 2)] = (unsigned char)(k0 + kk);
+                            ++cnt;
+                        }
                     }
                     T acc[DU], gacc[3 * DU];
 #pragma unroll
                     for (int j = 0; j < DU; ++j) acc[j] = 0;
 #pragma unroll
                     for (int j = 0; j < 3 * DU; ++j) gacc[j] = 0;
+#pragma unroll 2
                     for (int i = 0; i < cnt; ++i) {
-                        const int k = q[i][tt];
+                        const int k = q[i][tt ^ ((i & 7) << 2)];
                         const Q4 a = sA[k], b = sB[k];
                         T dx = xt[0] - a.x, dy = xt[1] - a.y, dz = xt[2] - a.z;
                         if (kTwo) {
@@ -934,33 +977,13 @@ inline size_t leaf3_smem(int p) {
 
 namespace dmk {
 
-// p^3 tensor from global memory into the padded shared layout, KB independent loads in flight
-// per thread
-template <class T, int KB = 8>
-__device__ __forceinline__ void load_padded_batched(T* dst, const T* __restrict__ src, int p, int P) {
-    const int p3 = p * p * p;
-    for (int e0 = threadIdx.x; e0 < p3; e0 += KB * blockDim.x) {
-        T v[KB];
-#pragma unroll
-        for (int u = 0; u < KB; ++u) {
-            const int e = e0 + u * blockDim.x;
-            v[u] = e < p3 ? src[e] : T(0);
-        }
-#pragma unroll
-        for (int u = 0; u < KB; ++u) {
-            const int e = e0 + u * blockDim.x;
-            if (e < p3) dst[(e / p) * P + (e % p)] = v[u];
-        }
-    }
-}
-
 // Upward pass child -> parent (Sec. 3.1.2) on thread-block clusters: cluster = parent box,
 // CTA rank o = child octant.  Each CTA applies (I_o^T x I_o^T x I_o^T) to its child's proxy
 // charges (three fiber contractions in shared memory), then the eight CTAs reduce the eight
 // contributions through distributed shared memory in the fixed order o = 0..7, each CTA
 // writing one eighth of the parent's tensor.
 template <class T, int MAXP>
-__global__ void __cluster_dims__(8, 1, 1) __launch_bounds__((MAXP * MAXP + 31) / 32 * 32)
+__global__ void __cluster_dims__(8, 1, 1) __launch_bounds__((MAXP * MAXP + 31) / 32 * 32, sizeof(T) == 4 ? 2 : 1)
     k_up_cluster(const int* __restrict__ nl_box, BoxArrays B, Tab<T> tab, T* __restrict__ proxy) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
@@ -1018,7 +1041,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__((MAXP * MAXP + 31) /
 // local += (I_o x I_o x I_o) parent; leaf child local += (A_o x A_o x A_o) parent, A_o = C I_o,
 // the Chebyshev coefficients of the child's interpolant.
 template <class T, int MAXP>
-__global__ void __launch_bounds__((MAXP * MAXP + 31) / 32 * 32) k_shift_child(const int* __restrict__ nl_box, BoxArrays B, Tab<T> tab,
+__global__ void __launch_bounds__((MAXP * MAXP + 31) / 32 * 32, sizeof(T) == 4 ? 2 : 1) k_shift_child(const int* __restrict__ nl_box, BoxArrays B, Tab<T> tab,
                                                      T* __restrict__ local) {
     const int o = blockIdx.x & 7;
     const int bi = blockIdx.x >> 3;

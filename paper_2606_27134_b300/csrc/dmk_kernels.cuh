@@ -63,7 +63,8 @@ __device__ __forceinline__ void lagrange_row_padded(T xi, const T* nodes, const 
 }
 
 template <class T, int MAXP>
-__global__ void __launch_bounds__(MAXP <= 24 ? 576 : 512) k_anterp(int nleaf, const int* __restrict__ leaves, BoxArrays B,
+__global__ void __launch_bounds__(MAXP <= 24 ? (MAXP * MAXP + 31) / 32 * 32 : 512, (MAXP <= 24 && sizeof(T) == 4) ? 2 : 1)
+    k_anterp(int nleaf, const int* __restrict__ leaves, BoxArrays B,
                                                  const double* __restrict__ xs, int64_t N,
                                                  const double* __restrict__ rs, Tab<T> tab, double s,
                                                  T* __restrict__ proxy) {

@@ -100,29 +100,147 @@ __device__ __forceinline__ void cell_range(const uint64_t* pkeys, int64_t N, int
     hi = upper_bound_u64(pkeys, N, last);
 }
 
-// Refinement and balance run on device-side counters: the host sizes every array by an upper
-// bound and the kernels read the actual counts, so no host round trip is needed per level.
+// ---- refinement (Sec. 3.1.1), one pass over the sorted points --------------------------------
+// The cells of level l are the runs of equal key >> 3(kBits - l) in the sorted point keys.  A
+// cell splits iff it holds more than n_s points (and l < kBits), i.e. its run, starting at i,
+// still covers i + n_s.  A split cell's parent holds at least as many points and splits too, so
+// the split cells of every level follow from one pass over the points; they come out in key
+// order through an order-preserving compaction: per-block counts, a one-CTA scan, a write pass.
+constexpr int kRefineThreads = 256;
 
-// refinement rule (Sec. 3.1.1): split iff the cell holds more than n_s points (and level < cap).
-// Cells of `level`: ncell = ncell0 at level 0, else 8 * (non-leaf count of level - 1).
-__global__ void k_split_flags(int cap, const uint64_t* __restrict__ cells, int level, int ncell0,
-                              const int* __restrict__ nR_prev, const uint64_t* __restrict__ pkeys, int64_t N,
-                              int n_s, int* __restrict__ flags) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= cap) return;
-    const int ncell = (level == 0) ? ncell0 : 8 * nR_prev[0];
-    if (i >= ncell) { flags[i] = 0; return; }
-    int64_t lo, hi;
-    cell_range(pkeys, N, level, cells[i], lo, hi);
-    flags[i] = (hi - lo > n_s && level < kBits) ? 1 : 0;
+struct SplitProbe {
+    uint64_t k0, km1, kns;
+    bool first, has_ns;
+    __device__ __forceinline__ SplitProbe(const uint64_t* pk, int64_t N, int64_t i, int n_s) {
+        first = (i == 0);
+        has_ns = i + n_s < N;
+        k0 = pk[i];
+        km1 = first ? 0 : pk[i - 1];
+        kns = has_ns ? pk[i + n_s] : 0;
+    }
+    // point i starts a level-l cell with more than n_s points
+    __device__ __forceinline__ bool split(int l) const {
+        const int sh = 3 * (kBits - l);
+        const uint64_t c = k0 >> sh;
+        return (first || (km1 >> sh) != c) && has_ns && (kns >> sh) == c;
+    }
+};
+
+// counts of split-cell starts per level and block: bcnt[l * nblk + block]
+__global__ void __launch_bounds__(kRefineThreads) k_refine_count(int64_t N, const uint64_t* __restrict__ pk, int n_s,
+                                                                 int nblk, int* __restrict__ bcnt) {
+    __shared__ int wc[kBits][kRefineThreads / 32];
+    const int64_t i = blockIdx.x * (int64_t)kRefineThreads + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool valid = i < N;
+    SplitProbe sp(pk, N, valid ? i : 0, n_s);
+    for (int l = 0; l < kBits; ++l) {
+        const unsigned bal = __ballot_sync(0xffffffffu, valid && sp.split(l));
+        if (lane == 0) wc[l][warp] = __popc(bal);
+    }
+    __syncthreads();
+    if (threadIdx.x < kBits) {
+        int sum = 0;
+        for (int w = 0; w < kRefineThreads / 32; ++w) sum += wc[threadIdx.x][w];
+        bcnt[threadIdx.x * nblk + blockIdx.x] = sum;
+    }
 }
 
-// children of the first nR[0] cells of R (8 each, in key order)
-__global__ void k_children(int cap8, const uint64_t* __restrict__ R, const int* __restrict__ nR,
-                           uint64_t* __restrict__ out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= cap8 || (i >> 3) >= nR[0]) return;
-    out[i] = (R[i >> 3] << 3) | (uint64_t)(i & 7);
+// one CTA: exclusive scan of the block counts of every level -> boff, totals -> nR[l].  A level
+// with no split cell has none below it, so the scan stops at the first empty level.
+__global__ void __launch_bounds__(1024) k_refine_scan(int nblk, const int* __restrict__ bcnt, int* __restrict__ boff,
+                                                      int* __restrict__ nR) {
+    __shared__ int wsum[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int per = (nblk + 1023) / 1024;
+    const int b0 = min(nblk, t * per), b1 = min(nblk, b0 + per);
+    int done = 0;
+    for (int l = 0; l < kBits; ++l) {
+        const int* c = bcnt + (size_t)l * nblk;
+        int s = 0;
+        for (int b = b0; b < b1; ++b) s += c[b];
+        int x = s;                                     // inclusive warp scan
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int v = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            wsum[lane] = v;
+        }
+        __syncthreads();
+        int run = x - s + (w > 0 ? wsum[w - 1] : 0);
+        for (int b = b0; b < b1; ++b) {
+            boff[(size_t)l * nblk + b] = run;
+            run += c[b];
+        }
+        const int total = wsum[31];
+        if (t == 0) nR[l] = total;
+        done = l + 1;
+        __syncthreads();
+        if (total == 0) break;
+    }
+    if (t == 0)
+        for (int l = done; l <= kBits; ++l) nR[l] = 0;   // level kBits never splits
+}
+
+// split cells of level l, in key order: R[l * cap + k]
+__global__ void __launch_bounds__(kRefineThreads) k_refine_write(int64_t N, const uint64_t* __restrict__ pk, int n_s,
+                                                                 int nblk, const int* __restrict__ boff, int64_t cap,
+                                                                 uint64_t* __restrict__ R) {
+    __shared__ int wc[kBits][kRefineThreads / 32];
+    const int64_t i = blockIdx.x * (int64_t)kRefineThreads + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool valid = i < N;
+    SplitProbe sp(pk, N, valid ? i : 0, n_s);
+    unsigned bals[kBits];
+    for (int l = 0; l < kBits; ++l) {
+        bals[l] = __ballot_sync(0xffffffffu, valid && sp.split(l));
+        if (lane == 0) wc[l][warp] = __popc(bals[l]);
+    }
+    __syncthreads();
+    if (threadIdx.x < kBits) {                         // exclusive prefix over the warps
+        int run = 0;
+        for (int w = 0; w < kRefineThreads / 32; ++w) {
+            const int v = wc[threadIdx.x][w];
+            wc[threadIdx.x][w] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    const unsigned below = (1u << lane) - 1u;
+    for (int l = 0; l < kBits; ++l) {
+        if (bals[l] & (1u << lane)) {
+            const int pos = boff[(size_t)l * nblk + blockIdx.x] + wc[l][warp] + __popc(bals[l] & below);
+            R[(size_t)l * cap + pos] = sp.k0 >> (3 * (kBits - l));
+        }
+    }
+}
+
+// Balance check of every level at once: counts, per level l - 1, the parents of neighbours of
+// level-l non-leaf cells that are not non-leaf (missing[l - 1]).  All zero means the refined
+// forest is already 2:1 balanced.
+__global__ void k_balance_check(int64_t cap, const uint64_t* __restrict__ R, const int* __restrict__ nR, Geo g,
+                                int* __restrict__ missing) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t per = 27 * cap;
+    if (t >= (int64_t)(kBits - 1) * per) return;
+    const int l = 1 + (int)(t / per);
+    const int64_t r = t % per;
+    const int i = (int)(r / 27), d = (int)(r % 27);
+    if (i >= nR[l]) return;
+    const int dd[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+    int ix[3], nb[3], sh[3];
+    cell_ix(g, l, R[(size_t)l * cap + i], ix);
+    if (!neighbour(g, l, ix, dd, nb, sh)) return;
+    const int par[3] = {nb[0] >> 1, nb[1] >> 1, nb[2] >> 1};
+    if (find_u64(R + (size_t)(l - 1) * cap, nR[l - 1], cell_key(g, l - 1, par)) < 0) atomicAdd(&missing[l - 1], 1);
 }
 
 // 2:1 balance, bottom-up: every non-leaf cell at level l needs all its neighbour cells at
@@ -151,17 +269,82 @@ __global__ void k_balance_cand(int capR, const uint64_t* __restrict__ R, const i
     }
 }
 
+// 2:1 balance of one level in one CTA, for levels with few non-leaf cells: the parents of the
+// neighbours of the non-leaf cells of level l that are not yet non-leaf at level l - 1 are
+// collected, deduplicated and ordered by rank, and merged with R_{l-1} into Rout (sorted), with
+// the new count in nR[l - 1].  More than kBalNew such cells sets *overflow and leaves nR
+// unchanged; the caller then balances with the general path.  A set *overflow also makes later
+// levels return at once.
+constexpr int kBalThreads = 1024;
+constexpr int kBalNew = 2048;
+
+__global__ void __launch_bounds__(kBalThreads) k_balance_small(const uint64_t* __restrict__ R,
+                                                               const uint64_t* __restrict__ Rp, int* __restrict__ nR,
+                                                               int l, Geo g, uint64_t* __restrict__ Rout,
+                                                               int* __restrict__ overflow) {
+    __shared__ uint64_t nw[kBalNew];
+    __shared__ uint64_t U[kBalNew];
+    __shared__ unsigned char fst[kBalNew];
+    __shared__ int cnt, nu;
+    if (*overflow) return;
+    const int n = nR[l], m = nR[l - 1];
+    if (threadIdx.x == 0) { cnt = 0; nu = 0; }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 27 * n; t += blockDim.x) {
+        const int i = t / 27, d = t % 27;
+        const int dd[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+        int ix[3], nb[3], sh[3];
+        cell_ix(g, l, R[i], ix);
+        if (!neighbour(g, l, ix, dd, nb, sh)) continue;
+        const int par[3] = {nb[0] >> 1, nb[1] >> 1, nb[2] >> 1};
+        const uint64_t P = cell_key(g, l - 1, par);
+        if (find_u64(Rp, m, P) < 0) {
+            const int k = atomicAdd(&cnt, 1);
+            if (k < kBalNew) nw[k] = P;
+        }
+    }
+    __syncthreads();
+    const int k = cnt;
+    if (k > kBalNew) {
+        if (threadIdx.x == 0) *overflow = 1;
+        return;
+    }
+    // distinct new cells in key order: the first occurrence of each value goes to its rank among
+    // the distinct values
+    for (int a = threadIdx.x; a < k; a += blockDim.x) {
+        const uint64_t v = nw[a];
+        bool first = true;
+        for (int b = 0; b < a && first; ++b) first = nw[b] != v;
+        fst[a] = first ? 1 : 0;
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < k; a += blockDim.x) {
+        if (!fst[a]) continue;
+        const uint64_t v = nw[a];
+        int r = 0;
+        for (int b = 0; b < k; ++b) r += (fst[b] && nw[b] < v) ? 1 : 0;
+        U[r] = v;
+        atomicAdd(&nu, 1);
+    }
+    __syncthreads();
+    const int u = nu;
+    for (int a = threadIdx.x; a < m; a += blockDim.x) {
+        const uint64_t x = Rp[a];
+        Rout[a + lower_bound_u64(U, u, x)] = x;
+    }
+    for (int b = threadIdx.x; b < u; b += blockDim.x) {
+        const uint64_t y = U[b];
+        Rout[b + lower_bound_u64(Rp, m, y)] = y;
+    }
+    if (threadIdx.x == 0) nR[l - 1] = m + u;
+}
+
 // after sort + unique the padding key (largest) may remain once at the end: drop it
 __global__ void k_trim_invalid(const uint64_t* __restrict__ sorted_unique, int* __restrict__ count) {
     const int n = count[0];
     if (n > 0 && sorted_unique[n - 1] == kInvalidKey) count[0] = n - 1;
 }
 
-// level-0 cells: every cube of the tiling, in key (= cube) order
-__global__ void k_iota_u64(int n, uint64_t* __restrict__ out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = (uint64_t)i;
-}
 
 struct BoxArrays {
     uint64_t* key;   // cell key (level-local)
@@ -175,51 +358,11 @@ struct BoxArrays {
     int* coll;       // 27 per box: colleague box or -1
 };
 
-// fills the boxes of one level: cells_l sorted; R_l sorted non-leaf subset; parents from R_{l-1}
-__global__ void k_box_fill(int level, int off, int ncell, const uint64_t* __restrict__ cells,
-                           const uint64_t* __restrict__ Rl, int nRl, int off_next,
-                           const uint64_t* __restrict__ cells_prev, int ncell_prev, int off_prev,
-                           const uint64_t* __restrict__ pkeys, int64_t N, Geo g, BoxArrays B) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ncell) return;
-    int b = off + i;
-    uint64_t key = cells[i];
-    B.key[b] = key;
-    B.level[b] = level;
-    int ix[3];
-    cell_ix(g, level, key, ix);
-    B.ix[3 * b] = ix[0];
-    B.ix[3 * b + 1] = ix[1];
-    B.ix[3 * b + 2] = ix[2];
-    int64_t lo, hi;
-    cell_range(pkeys, N, level, key, lo, hi);
-    B.start[b] = (int)lo;
-    B.end[b] = (int)hi;
-    int64_t r = (nRl > 0) ? find_u64(Rl, nRl, key) : -1;
-    B.child0[b] = (r >= 0) ? off_next + 8 * (int)r : -1;
-    if (level == 0) {
-        B.parent[b] = -1;
-    } else {
-        int64_t pi = find_u64(cells_prev, ncell_prev, key >> 3);
-        B.parent[b] = (pi >= 0) ? off_prev + (int)pi : -1;
-    }
-}
-
-// non-leaf list: boxes whose key is in R_l, in R_l order
-__global__ void k_nonleaf_list(int nRl, const uint64_t* __restrict__ Rl, const uint64_t* __restrict__ cells,
-                               int ncell, int off, int nl_off, int* __restrict__ nl_box, int* __restrict__ nl_of_box) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nRl) return;
-    int64_t pos = find_u64(cells, ncell, Rl[k]);
-    int b = off + (int)pos;
-    nl_box[nl_off + k] = b;
-    nl_of_box[b] = nl_off + k;
-}
-
-// per-level arrays of the forest, passed by value to the all-level kernels below
+// per-level arrays of the forest, passed by value to the all-level kernels below.  The cells of
+// level 0 are the cubes 0..Mtot-1; the cells of level l > 0 are the eight children of each
+// non-leaf cell of level l - 1, in key order: cell i = R_{l-1}[i / 8] * 8 + i % 8.
 struct LevelSet {
-    const uint64_t* cells[kMaxLevels + 1];   // sorted cell keys of each level
-    const uint64_t* R[kMaxLevels + 1];       // sorted non-leaf subset of each level
+    const uint64_t* R[kMaxLevels + 1];       // sorted non-leaf cells of each level
     int off[kMaxLevels + 2];                 // first box of each level
     int nl_off[kMaxLevels + 2];              // first non-leaf index of each level
     int nR[kMaxLevels + 1];
@@ -232,14 +375,20 @@ __device__ __forceinline__ int level_of(const int* off, int nlev, int b) {
     return l;
 }
 
-// k_box_fill for every level in one launch
+__device__ __forceinline__ uint64_t level_cell(const LevelSet& ls, int l, int i) {
+    return l == 0 ? (uint64_t)i : ((ls.R[l - 1][i >> 3] << 3) | (uint64_t)(i & 7));
+}
+
+// Boxes of every level in one launch: key, level, index, point range, first child, parent,
+// non-leaf index (and the non-leaf list), and the leaf flags for the leaf compaction.
 __global__ void k_box_fill_all(LevelSet ls, int nb, const uint64_t* __restrict__ pkeys, int64_t N, Geo g,
-                               BoxArrays B) {
+                               BoxArrays B, int* __restrict__ nl_box, int* __restrict__ leaf_flag,
+                               int* __restrict__ iota) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
     const int level = level_of(ls.off, ls.nlev, b);
     const int i = b - ls.off[level];
-    const uint64_t key = ls.cells[level][i];
+    const uint64_t key = level_cell(ls, level, i);
     B.key[b] = key;
     B.level[b] = level;
     int ix[3];
@@ -254,30 +403,34 @@ __global__ void k_box_fill_all(LevelSet ls, int nb, const uint64_t* __restrict__
     const int nRl = ls.nR[level];
     const int64_t r = (nRl > 0) ? find_u64(ls.R[level], nRl, key) : -1;
     B.child0[b] = (r >= 0) ? ls.off[level + 1] + 8 * (int)r : -1;
-    B.nl[b] = (r >= 0) ? ls.nl_off[level] + (int)r : -1;
+    if (r >= 0) {
+        B.nl[b] = ls.nl_off[level] + (int)r;
+        nl_box[ls.nl_off[level] + r] = b;
+    } else {
+        B.nl[b] = -1;
+    }
+    // parent: the level-(l-1) cell R_{l-1}[i / 8]; its box index there
     if (level == 0) {
         B.parent[b] = -1;
     } else {
-        const int np = ls.off[level] - ls.off[level - 1];
-        const int64_t pi = find_u64(ls.cells[level - 1], np, key >> 3);
-        B.parent[b] = (pi >= 0) ? ls.off[level - 1] + (int)pi : -1;
+        const int pl = level - 1;
+        const uint64_t pkey = key >> 3;
+        int64_t pi;
+        if (pl == 0) {
+            pi = (int64_t)pkey;
+        } else {
+            const int64_t gi = find_u64(ls.R[pl - 1], ls.nR[pl - 1], pkey >> 3);
+            pi = (gi < 0) ? -1 : gi * 8 + (int64_t)(pkey & 7);
+        }
+        B.parent[b] = (pi >= 0) ? ls.off[pl] + (int)pi : -1;
     }
-}
-
-// non-leaf list of every level in one launch: nl_box[nl_off_l + k] = box of R_l[k]
-__global__ void k_nonleaf_all(LevelSet ls, int n_nl, int* __restrict__ nl_box) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_nl) return;
-    const int l = level_of(ls.nl_off, ls.nlev, t);
-    const int k = t - ls.nl_off[l];
-    const int ncell = ls.off[l + 1] - ls.off[l];
-    nl_box[t] = ls.off[l] + (int)find_u64(ls.cells[l], ncell, ls.R[l][k]);
+    leaf_flag[b] = (r < 0 && hi > lo) ? 1 : 0;
+    iota[b] = b;
 }
 
 // colleague table: coll[b * 27 + d] = box at the same level with offset d, or -1
 __global__ void k_colleagues(int nb, const int* __restrict__ level, const int* __restrict__ ixa,
-                             const uint64_t* __restrict__ keys, const int* __restrict__ level_off,
-                             const int* __restrict__ level_cnt, Geo g, int* __restrict__ coll) {
+                             const uint64_t* __restrict__ keys, LevelSet ls, Geo g, int* __restrict__ coll) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 27 * nb) return;
     int b = t / 27, d = t % 27;
@@ -288,19 +441,10 @@ __global__ void k_colleagues(int nb, const int* __restrict__ level, const int* _
     int res = -1;
     if (neighbour(g, l, ix, dd, nbx, sh)) {
         uint64_t k = cell_key(g, l, nbx);
-        int64_t pos = find_u64(keys + level_off[l], level_cnt[l], k);
-        if (pos >= 0) res = level_off[l] + (int)pos;
+        int64_t pos = find_u64(keys + ls.off[l], ls.off[l + 1] - ls.off[l], k);
+        if (pos >= 0) res = ls.off[l] + (int)pos;
     }
     coll[t] = res;
-}
-
-// leaves holding points
-__global__ void k_leaf_flags(int nb, const int* __restrict__ child0, const int* __restrict__ start,
-                             const int* __restrict__ end, int* __restrict__ flags, int* __restrict__ iota) {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
-    flags[b] = (child0[b] < 0 && end[b] > start[b]) ? 1 : 0;
-    iota[b] = b;
 }
 
 // Direct list of target leaf T (telescoping recursion of the split, Eqs. multilevel_ks,
@@ -318,54 +462,56 @@ template <bool FILL>
 __global__ void k_direct(int cap, const int* __restrict__ nleaf_dev, const int* __restrict__ leaves, BoxArrays B,
                          Geo g, int* __restrict__ counts, const int* __restrict__ offs, DirectEntry* __restrict__ out,
                          unsigned long long* __restrict__ npairs) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // one warp per leaf, lane d < 27 = colleague offset; entries in the order (ancestor level
+    // descending, then the leaf's own colleagues), d ascending within a level
+    const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (i >= cap) return;
     if (i >= nleaf_dev[0]) {
-        if (!FILL) counts[i] = 0;
+        if (!FILL && lane == 0) counts[i] = 0;
         return;
     }
-    int T = leaves[i];
-    int lT = B.level[T];
+    const int T = leaves[i];
+    const int lT = B.level[T];
+    const int nt = B.end[T] - B.start[T];
+    const unsigned below = (1u << lane) - 1u;
+    int pos = FILL ? offs[i] : 0;
     int cnt = 0;
     long long pairs = 0;
-    int pos = FILL ? offs[i] : 0;
-    int nt = B.end[T] - B.start[T];
-    // ancestors A_j, j = lT-1 .. 0
-    int A = B.parent[T];
-    for (int j = lT - 1; j >= 0; --j) {
-        int ix[3] = {B.ix[3 * A], B.ix[3 * A + 1], B.ix[3 * A + 2]};
-        for (int d = 0; d < 27; ++d) {
-            int C = B.coll[A * 27 + d];
-            if (C < 0 || B.child0[C] >= 0 || B.end[C] <= B.start[C]) continue;
+    auto visit = [&](int box, int j, bool need_leaf) {
+        const int d = lane;
+        int C = -1;
+        if (d < 27) {
+            C = B.coll[box * 27 + d];
+            if (C >= 0 && ((need_leaf && B.child0[C] >= 0) || B.end[C] <= B.start[C])) C = -1;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, C >= 0);
+        if (C >= 0) {
             if (FILL) {
-                int dd[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1}, nbx[3], sh[3];
+                const int dd[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+                const int ix[3] = {B.ix[3 * box], B.ix[3 * box + 1], B.ix[3 * box + 2]};
+                int nbx[3], sh[3];
                 neighbour(g, j, ix, dd, nbx, sh);
-                out[pos++] = {B.start[C], B.end[C], pack_code(sh, j), 0};
+                out[pos + __popc(bal & below)] = {B.start[C], B.end[C], pack_code(sh, j), 0};
             } else {
-                ++cnt;
                 pairs += (long long)(B.end[C] - B.start[C]) * nt;
             }
         }
+        pos += __popc(bal);
+        cnt += __popc(bal);
+    };
+    int A = B.parent[T];
+    for (int j = lT - 1; j >= 0; --j) {         // (a) leaf colleagues of the ancestors
+        visit(A, j, true);
         A = B.parent[A];
     }
-    {
-        int ix[3] = {B.ix[3 * T], B.ix[3 * T + 1], B.ix[3 * T + 2]};
-        for (int d = 0; d < 27; ++d) {
-            int C = B.coll[T * 27 + d];
-            if (C < 0 || B.end[C] <= B.start[C]) continue;
-            if (FILL) {
-                int dd[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1}, nbx[3], sh[3];
-                neighbour(g, lT, ix, dd, nbx, sh);
-                out[pos++] = {B.start[C], B.end[C], pack_code(sh, lT), 0};
-            } else {
-                ++cnt;
-                pairs += (long long)(B.end[C] - B.start[C]) * nt;
-            }
-        }
-    }
+    visit(T, lT, false);                         // (b) every colleague of T
     if (!FILL) {
-        counts[i] = cnt;
-        atomicAdd(npairs, (unsigned long long)pairs);
+        for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+        if (lane == 0) {
+            counts[i] = cnt;
+            atomicAdd(npairs, (unsigned long long)pairs);
+        }
     }
 }
 
