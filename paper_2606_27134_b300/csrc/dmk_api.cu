@@ -270,6 +270,16 @@ dmk_status_t upload_root(dmk_plan_s* plan) {
     for (auto& z : P.Wroot) { h.push_back(z.real()); h.push_back(z.imag()); }
     size_t o_c = h.size();
     for (double v : P.root_const) h.push_back(v);
+    // n3 mod M3 per x3 wavenumber (used when x3 is periodic: k3 = 2 pi n3 / L3)
+    size_t o_n = h.size();
+    {
+        const int M3 = std::max(1, P.M[2]);
+        const double L3 = P.L[2];
+        for (double k : P.kax[2]) {
+            const long long n3 = std::llround(k * L3 / (2 * 3.14159265358979323846));
+            h.push_back((double)(((n3 % M3) + M3) % M3));
+        }
+    }
     cudaError_t e = cudaMalloc(&plan->d_root, h.size() * sizeof(double));
     if (e != cudaSuccess) { plan->err = "root table allocation failed"; return DMK_ERR_OOM; }
     e = cudaMemcpy(plan->d_root, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -284,6 +294,7 @@ dmk_status_t upload_root(dmk_plan_s* plan) {
     }
     rt.W = reinterpret_cast<const Cx<double>*>(base + o_W);
     rt.rconst = base + o_c;
+    rt.nmod3 = base + o_n;
     // self tables
     std::vector<double> sv(P.self_val);
     sv.insert(sv.end(), P.self_grad.begin(), P.self_grad.end());
@@ -733,6 +744,37 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         Cx<double>* chi = (Cx<double>*)vchi;
         Cx<double>* uh = (Cx<double>*)vuh;
         auto blocks = [](int64_t n) { return (unsigned)((n + 127) / 128); };
+        // cubes stacked along a periodic x3: DFT over the cube index (Sec. 3.4, Case 1)
+        const bool fft_root = P.D == 3 && g.M[0] == 1 && g.M[1] == 1 && g.M[2] >= kRootFftMin &&
+                              g.M[2] <= kRootFftMax;
+        if (fft_root) {
+            const int M3 = g.M[2];
+            const size_t E = f2;                                   // n1 n2 p per (cube, component)
+            const size_t need = std::max((size_t)jf * (f1 + 2 * f2),
+                                         (size_t)M3 * du * (f2 + f1 + (size_t)p * p * p));
+            CKS(ensure(plan, B_SCRATCH, need * sizeof(Cx<double>), &vrsc));
+            Cx<double>* q0 = (Cx<double>*)vrsc;
+            Cx<double>* chi = (Cx<double>*)vchi;
+            Cx<double>* uh = (Cx<double>*)vuh;
+            Cx<double>* B1f = q0;
+            Cx<double>* B2f = B1f + (size_t)jf * f1;
+            Cx<double>* Bh = B2f + (size_t)jf * f2;
+            k_root_fwd1<T><<<blocks((int64_t)jf * f1), 128, 0, st>>>(jf, p, rt, proxy, B1f);
+            k_root_fwd2<<<blocks((int64_t)jf * f2), 128, 0, st>>>(jf, p, rt, B1f, B2f);
+            k_rootfft_dft<<<blocks((int64_t)M3 * drho * E), 128, 0, st>>>(M3, drho, (int)E, B2f, Bh);
+            k_rootfft_chi<<<blocks((int64_t)drho * rt.nmode), 128, 0, st>>>(drho, p, g, rt, Bh, chi);
+            k_root_apply<<<nblk(rt.nmode, 128), 128, 0, st>>>(1, drho, du, rt, chi, uh);
+            const int jbb = M3 * du;
+            Cx<double>* C2 = q0;
+            Cx<double>* C1 = C2 + (size_t)jbb * f2;
+            Cx<double>* Gs = C1 + (size_t)jbb * f1;
+            k_rootfft_bwd1<<<blocks((int64_t)jbb * f2), 128, 0, st>>>(M3, du, p, g, rt, uh, C2);
+            k_root_bwd2<<<blocks((int64_t)jbb * f1), 128, 0, st>>>(jbb, p, rt, C2, C1);
+            k_rootfft_bwd3<<<blocks((int64_t)jbb * p * p * p), 128, 0, st>>>(jbb, p, rt, C1, Gs);
+            k_rootfft_idft<T><<<blocks((int64_t)M3 * du * p * p * p), 128, 0, st>>>(M3, du, p, rt, Gs, d_sums, drho,
+                                                                                     local);
+            launches += 9;
+        } else {
         k_root_fwd1<T><<<blocks((int64_t)jf * f1), 128, 0, st>>>(jf, p, rt, proxy, r0);
         k_root_fwd2<<<blocks((int64_t)jf * f2), 128, 0, st>>>(jf, p, rt, r0, r0 + (size_t)jf * f1);
         k_root_fwd3<<<blocks((int64_t)jf * rt.nmode), 128, 0, st>>>(jf, drho, p, g, rt, r0 + (size_t)jf * f1, chi);
@@ -745,6 +787,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         k_root_bwd2<<<blocks((int64_t)jb * f1), 128, 0, st>>>(jb, p, rt, C2, C1);
         k_root_bwd3<T><<<blocks((int64_t)jb * p * p * p), 128, 0, st>>>(jb, du, p, rt, C1, d_sums, drho, local);
         launches += 8;
+        }
     }
     rec(3);
     // ---- (7) plane waves: outgoing for all non-leaf boxes, then translation + incoming ------

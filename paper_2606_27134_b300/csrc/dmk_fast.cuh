@@ -12,6 +12,7 @@
 // broadcasts.  Operator rows are zero-padded to MAXP so the unrolled loops need no guards.
 #pragma once
 #include <cooperative_groups.h>
+#include <cuda_fp16.h>
 
 #include "dmk_kernels.cuh"
 
@@ -50,23 +51,19 @@ __device__ __forceinline__ void fiber_store(T* out, int p, int P, int ax, int fa
     }
 }
 
-// p^3 tensor from global memory into the padded shared layout, KB independent loads in flight
-// per thread
-template <class T, int KB = 8>
+// p^3 tensor from global memory into the padded shared layout: one p-long row per thread, all of
+// its loads in flight at once (no index division)
+template <class T, int MAXP = kMaxPFast>
 __device__ __forceinline__ void load_padded_batched(T* dst, const T* __restrict__ src, int p, int P) {
-    const int p3 = p * p * p;
-    for (int e0 = threadIdx.x; e0 < p3; e0 += KB * blockDim.x) {
-        T v[KB];
+    const int rows = p * p;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const T* s = src + (size_t)r * p;
+        T v[MAXP];
 #pragma unroll
-        for (int u = 0; u < KB; ++u) {
-            const int e = e0 + u * blockDim.x;
-            v[u] = e < p3 ? src[e] : T(0);
-        }
+        for (int j = 0; j < MAXP; ++j) v[j] = (j < p) ? s[j] : T(0);
 #pragma unroll
-        for (int u = 0; u < KB; ++u) {
-            const int e = e0 + u * blockDim.x;
-            if (e < p3) dst[(e / p) * P + (e % p)] = v[u];
-        }
+        for (int j = 0; j < MAXP; ++j)
+            if (j < p) dst[r * P + j] = v[j];
     }
 }
 
@@ -467,7 +464,7 @@ __global__ void __launch_bounds__(416) k_pwout2(int n, const int* __restrict__ n
         const int box = nl_box[bi];
         for (int a = 0; a < drho; ++a) {
             __syncthreads();
-            load_padded_batched<T>(X, proxy + ((size_t)box * drho + a) * p3, p, P);
+            load_padded_batched<T, MAXP>(X, proxy + ((size_t)box * drho + a) * p3, p, P);
             __syncthreads();
             for (int c = threadIdx.x; c < p2; c += blockDim.x) {       // j3 -> m3
                 T x[MAXP];
@@ -657,6 +654,73 @@ __device__ __forceinline__ void split_double(double v, float& h, float& l) {
     l = (float)(v - (double)h);
 }
 
+// Tensor-product Chebyshev sum at one target (Sec. 3.1.5): S = sum c[n1][n2][n3] T_n1(x) T_n2(y)
+// T_n3(z) and its three derivatives, with c staged in shared memory in rows of NG four-vectors
+// (n3 padded to 4 NG with zeros) and T_n3(z), T'_n3(z) in registers; the x and y recurrences run
+// on the fly.  GUARD: rows shorter than NG four-vectors (ng < NG).
+template <class T, int NG, bool GUARD, bool GRAD>
+__device__ __forceinline__ void cheb_eval(const T* cs, int p, int ng, const T (&Tz)[kMaxPFast],
+                                          const T (&dTz)[kMaxPFast], const T xi[3], T& S, T& Sx, T& Sy, T& Sz) {
+    using Q4 = Quad<T>;
+    T xm2 = 0, xm1 = 1, xu2 = 0, xu1 = 1;
+    for (int n1 = 0; n1 < p; ++n1) {
+        T tx, dtx;
+        if (n1 == 0) { tx = 1; dtx = 0; }
+        else if (n1 == 1) { tx = xi[0]; dtx = 1; xm2 = 1; xm1 = xi[0]; xu2 = 1; xu1 = 2 * xi[0]; }
+        else {
+            tx = 2 * xi[0] * xm1 - xm2;
+            dtx = (T)n1 * xu1;
+            const T un = 2 * xi[0] * xu1 - xu2;
+            xm2 = xm1; xm1 = tx; xu2 = xu1; xu1 = un;
+        }
+        T b0 = 0, b1 = 0, b2 = 0;
+        T ym2 = 0, ym1 = 1, yu2 = 0, yu1 = 1;
+        const Q4* rows = reinterpret_cast<const Q4*>(cs + (size_t)n1 * p * 4 * ng);
+        for (int n2 = 0; n2 < p; ++n2) {
+            T ty, dty;
+            if (n2 == 0) { ty = 1; dty = 0; }
+            else if (n2 == 1) { ty = xi[1]; dty = 1; ym2 = 1; ym1 = xi[1]; yu2 = 1; yu1 = 2 * xi[1]; }
+            else {
+                ty = 2 * xi[1] * ym1 - ym2;
+                dty = (T)n2 * yu1;
+                const T un = 2 * xi[1] * yu1 - yu2;
+                ym2 = ym1; ym1 = ty; yu2 = yu1; yu1 = un;
+            }
+            const Q4* row = rows + n2 * ng;
+            T a0 = 0, a1 = 0, a0b = 0, a1b = 0;
+#pragma unroll
+            for (int gq = 0; gq < NG; ++gq) {
+                if (!GUARD || gq < ng) {
+                    const Q4 cv = row[gq];
+                    a0 = fma(cv.x, Tz[4 * gq], a0);
+                    a0b = fma(cv.y, Tz[4 * gq + 1], a0b);
+                    a0 = fma(cv.z, Tz[4 * gq + 2], a0);
+                    a0b = fma(cv.w, Tz[4 * gq + 3], a0b);
+                    if (GRAD) {
+                        a1 = fma(cv.x, dTz[4 * gq], a1);
+                        a1b = fma(cv.y, dTz[4 * gq + 1], a1b);
+                        a1 = fma(cv.z, dTz[4 * gq + 2], a1);
+                        a1b = fma(cv.w, dTz[4 * gq + 3], a1b);
+                    }
+                }
+            }
+            a0 += a0b;
+            b0 = fma(ty, a0, b0);
+            if (GRAD) {
+                a1 += a1b;
+                b1 = fma(dty, a0, b1);
+                b2 = fma(ty, a1, b2);
+            }
+        }
+        S = fma(tx, b0, S);
+        if (GRAD) {
+            Sx = fma(dtx, b0, Sx);
+            Sy = fma(tx, b1, Sy);
+            Sz = fma(tx, b2, Sz);
+        }
+    }
+}
+
 constexpr int kLeaf3Threads = 128;
 
 template <class T, int K, bool GRAD>
@@ -672,6 +736,9 @@ __global__ void __launch_bounds__(kLeaf3Threads) k_leaf3(int nleaf, const int* _
     const int p = tab.p, p2 = p * p, p3 = p2 * p, PQ = (p + 3) & ~3, ng = PQ >> 2;
     __shared__ Q4 sA[kSrcChunk];   // source offset from the leaf centre (leading part), nu^2
     __shared__ Q4 sB[kSrcChunk];   // trailing parts (FP32 path), 1/nu
+    // FP32 path: the support test in half precision on source pairs: -offset/nu (x, y, z) and
+    // sigma = r_T/nu, so that |x_t sigma - x_s/nu|^2 < 1 (x_t in units of the leaf side r_T)
+    __shared__ Quad<__half2> sT[kTwo ? kSrcChunk / 2 : 1];
     __shared__ T fits[kTwo ? 1 : 256];
     // FP32 path: the piecewise cubic series tables this kernel uses (q, f[, g][, q', f'[, g']])
     constexpr int NSER = (K == DMK_STRESSLET) ? (GRAD ? 6 : 3) : ((GRAD && K != DMK_LAPLACE) ? 5 : 2);
@@ -722,6 +789,9 @@ __global__ void __launch_bounds__(kLeaf3Threads) k_leaf3(int nleaf, const int* _
                     }
                 }
             }
+            const float inv_rT = ldexpf(inv_s_f, l);
+            __half2 xu2[3];
+            for (int a = 0; a < 3; ++a) xu2[a] = __float2half2_rn((float)(xt[a] + xtl[a]) * inv_rT);
             // (2) Chebyshev evaluation
             T ev[DU], eg[3 * DU];
             {
@@ -760,63 +830,13 @@ __global__ void __launch_bounds__(kLeaf3Threads) k_leaf3(int nleaf, const int* _
                     __syncthreads();
                     T S = 0, Sx = 0, Sy = 0, Sz = 0;
                     if (act) {
-                        T xm2 = 0, xm1 = 1, xu2 = 0, xu1 = 1;
-                        for (int n1 = 0; n1 < p; ++n1) {
-                            T tx, dtx;
-                            if (n1 == 0) { tx = 1; dtx = 0; }
-                            else if (n1 == 1) { tx = xi[0]; dtx = 1; xm2 = 1; xm1 = xi[0]; xu2 = 1; xu1 = 2 * xi[0]; }
-                            else {
-                                tx = 2 * xi[0] * xm1 - xm2;
-                                dtx = (T)n1 * xu1;
-                                const T un = 2 * xi[0] * xu1 - xu2;
-                                xm2 = xm1; xm1 = tx; xu2 = xu1; xu1 = un;
-                            }
-                            T b0 = 0, b1 = 0, b2 = 0;
-                            T ym2 = 0, ym1 = 1, yu2 = 0, yu1 = 1;
-                            const Q4* rows = reinterpret_cast<const Q4*>(cs + (size_t)n1 * p * PQ);
-                            for (int n2 = 0; n2 < p; ++n2) {
-                                T ty, dty;
-                                if (n2 == 0) { ty = 1; dty = 0; }
-                                else if (n2 == 1) { ty = xi[1]; dty = 1; ym2 = 1; ym1 = xi[1]; yu2 = 1; yu1 = 2 * xi[1]; }
-                                else {
-                                    ty = 2 * xi[1] * ym1 - ym2;
-                                    dty = (T)n2 * yu1;
-                                    const T un = 2 * xi[1] * yu1 - yu2;
-                                    ym2 = ym1; ym1 = ty; yu2 = yu1; yu1 = un;
-                                }
-                                const Q4* row = rows + n2 * ng;
-                                T a0 = 0, a1 = 0, a0b = 0, a1b = 0;
-#pragma unroll
-                                for (int gq = 0; gq < MQ; ++gq) {
-                                    if (gq < ng) {
-                                        const Q4 cv = row[gq];
-                                        a0 = fma(cv.x, Tz[4 * gq], a0);
-                                        a0b = fma(cv.y, Tz[4 * gq + 1], a0b);
-                                        a0 = fma(cv.z, Tz[4 * gq + 2], a0);
-                                        a0b = fma(cv.w, Tz[4 * gq + 3], a0b);
-                                        if (GRAD) {
-                                            a1 = fma(cv.x, dTz[4 * gq], a1);
-                                            a1b = fma(cv.y, dTz[4 * gq + 1], a1b);
-                                            a1 = fma(cv.z, dTz[4 * gq + 2], a1);
-                                            a1b = fma(cv.w, dTz[4 * gq + 3], a1b);
-                                        }
-                                    }
-                                }
-                                a0 += a0b;
-                                b0 = fma(ty, a0, b0);
-                                if (GRAD) {
-                                    a1 += a1b;
-                                    b1 = fma(dty, a0, b1);
-                                    b2 = fma(ty, a1, b2);
-                                }
-                            }
-                            S = fma(tx, b0, S);
-                            if (GRAD) {
-                                Sx = fma(dtx, b0, Sx);
-                                Sy = fma(tx, b1, Sy);
-                                Sz = fma(tx, b2, Sz);
-                            }
-                        }
+                        // exact unrolling for the common row lengths (p = 17..20, 21..24)
+                        if (ng == 5)
+                            cheb_eval<T, 5, false, GRAD>(cs, p, ng, Tz, dTz, xi, S, Sx, Sy, Sz);
+                        else if (ng == 6)
+                            cheb_eval<T, 6, false, GRAD>(cs, p, ng, Tz, dTz, xi, S, Sx, Sy, Sz);
+                        else
+                            cheb_eval<T, MQ, true, GRAD>(cs, p, ng, Tz, dTz, xi, S, Sx, Sy, Sz);
                     }
                     const T sc = (T)(1.0 / half);
                     ev[j] = S;
@@ -876,6 +896,14 @@ __global__ void __launch_bounds__(kLeaf3Threads) k_leaf3(int nleaf, const int* _
                         b.w = tinv;
                         sA[slot] = a;
                         sB[slot] = b;
+                        if constexpr (kTwo) {
+                            __half* hp = reinterpret_cast<__half*>(&sT[slot >> 1]);
+                            const int hh = slot & 1;
+                            hp[0 + hh] = __float2half_rn(-(a.x + b.x) * tinv);
+                            hp[2 + hh] = __float2half_rn(-(a.y + b.y) * tinv);
+                            hp[4 + hh] = __float2half_rn(-(a.z + b.z) * tinv);
+                            hp[6 + hh] = __float2half_rn(ldexpf(1.0f, lev - l));
+                        }
                     }
                     filled += take;
                     eo += take;
@@ -889,21 +917,56 @@ __global__ void __launch_bounds__(kLeaf3Threads) k_leaf3(int nleaf, const int* _
                     int cnt = 0;
                     for (int k0 = 0; k0 < filled; k0 += 32) {
                         const int kn = min(32, filled - k0);
-                        unsigned mask = 0;
+                        if constexpr (kTwo) {
+                            // two sources per half2 instruction; bit m of me / mo: source
+                            // k0 + 2m / k0 + 2m + 1
+                            const __half2 one2 = __float2half2_rn(1.0f);
+                            unsigned me = 0, mo = 0;
 #pragma unroll 8
-                        for (int kk = 0; kk < 32; ++kk) {
-                            if (kk < kn) {
-                                const Q4 a = sA[k0 + kk];
-                                const T dx = xt[0] - a.x, dy = xt[1] - a.y, dz = xt[2] - a.z;
-                                const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                                mask |= (r2 < a.w ? 1u : 0u) << kk;
+                            for (int m = 0; m < 16; ++m) {
+                                if (2 * m < kn) {
+                                    const Quad<__half2> v = sT[(k0 >> 1) + m];
+                                    const __half2 dx = __hfma2(xu2[0], v.w, v.x);
+                                    const __half2 dy = __hfma2(xu2[1], v.w, v.y);
+                                    const __half2 dz = __hfma2(xu2[2], v.w, v.z);
+                                    const __half2 r2 = __hfma2(dx, dx, __hfma2(dy, dy, __hmul2(dz, dz)));
+                                    const unsigned mm = __hlt2_mask(r2, one2);
+                                    me |= (mm & 1u) << m;
+                                    mo |= ((mm >> 16) & 1u) << m;
+                                }
                             }
-                        }
-                        while (mask) {
-                            const int kk = __ffs(mask) - 1;
-                            mask &= mask - 1;
-                            q[cnt][tt ^ ((cnt & 7) << 2)] = (unsigned char)(k0 + kk);
-                            ++cnt;
+                            const int ne = (kn + 1) >> 1, no = kn >> 1;
+                            me &= (ne >= 32) ? ~0u : ((1u << ne) - 1u);
+                            mo &= (no >= 32) ? ~0u : ((1u << no) - 1u);
+                            while (me) {
+                                const int m = __ffs(me) - 1;
+                                me &= me - 1;
+                                q[cnt][tt ^ ((cnt & 7) << 2)] = (unsigned char)(k0 + 2 * m);
+                                ++cnt;
+                            }
+                            while (mo) {
+                                const int m = __ffs(mo) - 1;
+                                mo &= mo - 1;
+                                q[cnt][tt ^ ((cnt & 7) << 2)] = (unsigned char)(k0 + 2 * m + 1);
+                                ++cnt;
+                            }
+                        } else {
+                            unsigned mask = 0;
+#pragma unroll 8
+                            for (int kk = 0; kk < 32; ++kk) {
+                                if (kk < kn) {
+                                    const Q4 a = sA[k0 + kk];
+                                    const T dx = xt[0] - a.x, dy = xt[1] - a.y, dz = xt[2] - a.z;
+                                    const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                                    mask |= (r2 < a.w ? 1u : 0u) << kk;
+                                }
+                            }
+                            while (mask) {
+                                const int kk = __ffs(mask) - 1;
+                                mask &= mask - 1;
+                                q[cnt][tt ^ ((cnt & 7) << 2)] = (unsigned char)(k0 + kk);
+                                ++cnt;
+                            }
                         }
                     }
                     T acc[DU], gacc[3 * DU];
@@ -1005,7 +1068,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__((MAXP * MAXP + 31) /
     const int lo = (o * p3) >> 3, hi = ((o + 1) * p3) >> 3;
     for (int a = 0; a < drho; ++a) {
         __syncthreads();
-        load_padded_batched<T>(bufA, proxy + ((size_t)C * drho + a) * p3, p, P);
+        load_padded_batched<T, MAXP>(bufA, proxy + ((size_t)C * drho + a) * p3, p, P);
         __syncthreads();
         T t[MAXP];
         if (own) {
@@ -1051,7 +1114,8 @@ __global__ void __launch_bounds__((MAXP * MAXP + 31) / 32 * 32, sizeof(T) == 4 ?
     T* bufB = bufA + p * p * P;
     const int Pb = nl_box[bi];
     const int C = B.child0[Pb] + o;
-    const T* src = (B.child0[C] < 0) ? tab.Aoct : tab.Ioct;
+    const bool leaf_child = B.child0[C] < 0;
+    const T* src = leaf_child ? tab.Aoct : tab.Ioct;
     for (int ax = 0; ax < 3; ++ax) {
         const int bit = (o >> ax) & 1;
         load_op<T, MAXP>(Mo + ax * MAXP * MAXP, p, [&](int k, int j) { return src[(bit * p + j) * p + k]; });
@@ -1061,7 +1125,7 @@ __global__ void __launch_bounds__((MAXP * MAXP + 31) / 32 * 32, sizeof(T) == 4 ?
     const int fa = own ? f / p : 0, fb = own ? f % p : 0;
     for (int j = 0; j < du; ++j) {
         __syncthreads();
-        load_padded_batched<T>(bufA, local + ((size_t)Pb * du + j) * p3, p, P);
+        load_padded_batched<T, MAXP>(bufA, local + ((size_t)Pb * du + j) * p3, p, P);
         __syncthreads();
         T t[MAXP];
         if (own) {
@@ -1077,9 +1141,15 @@ __global__ void __launch_bounds__((MAXP * MAXP + 31) / 32 * 32, sizeof(T) == 4 ?
         if (own) {
             fiber_contract<T, MAXP>(bufA, p, P, 0, fa, fb, Mo, t);
             T* out = local + ((size_t)C * du + j) * p3;
+            if (leaf_child) {                          // only the shift writes a leaf's expansion
 #pragma unroll
-            for (int jj = 0; jj < MAXP; ++jj)
-                if (jj < p) out[(jj * p + fa) * p + fb] += t[jj];
+                for (int jj = 0; jj < MAXP; ++jj)
+                    if (jj < p) out[(jj * p + fa) * p + fb] = t[jj];
+            } else {                                   // non-leaf: add to its plane-wave part
+#pragma unroll
+                for (int jj = 0; jj < MAXP; ++jj)
+                    if (jj < p) out[(jj * p + fa) * p + fb] += t[jj];
+            }
         }
     }
 }

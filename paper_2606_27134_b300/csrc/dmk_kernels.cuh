@@ -396,6 +396,7 @@ struct RootTab {
     const Cx<double>* S[3];      // S_i[k * p + j] = exp(-i k (s/2) eta_j)
     const Cx<double>* W;         // nmode x du x drho
     const double* rconst;        // du x drho
+    const double* nmod3;         // per x3 wavenumber k3 = 2 pi n3 / L3: n3 mod M3 (periodic x3)
 };
 
 // chi_m(k) for cube m, component a (tensor form), including exp(-i k . c_m)
@@ -621,6 +622,118 @@ __global__ void k_root_bwd3(int jobs, int du, int p, RootTab rt, const Cx<double
     double cst = 0;
     for (int a = 0; a < drho; ++a) cst += rt.rconst[j * drho + a] * rho_sum[a];
     local[(size_t)job * p3 + e] = (T)(v + cst);
+}
+
+// ---- root far field for cubes stacked along a periodic x3 (Sec. 3.4 "Case 1: elongated
+// cuboid", Eqs. beta_def, 1d-DFT-beta, structfac-case1-wDFTCoeffs, ufar_inverse_fft) ----------
+// With M3 cubes of side s along x3 and k3 = 2 pi n3 / (M3 s), the cube phase exp(-i k . c_m) is
+// exp(-i k . c_0) exp(-2 pi i (n3 mod M3) m / M3): the sum over cubes becomes a length-M3 DFT
+// over the cube index of the partial sums beta_m(j3; k1, k2) (contracted over j1, j2), taken once
+// for all modes.  The evaluation is the transpose: partial sums G_s grouped by n3 mod M3, then
+// an inverse DFT over s gives every cube's grid.  The length-M3 transforms are direct sums, one
+// thread per output (M3 <= kRootFftMax); the quadratic cost is then in M3 n1 n2 p, not in the
+// number of modes.
+
+constexpr int kRootFftMin = 2;       // cubes along x3 from which the cube-index DFT path is used
+constexpr int kRootFftMax = 4096;
+
+// forward: beta_hat[(s drho + a) E + e] = sum_m exp(-2 pi i s m / M3) beta[(m drho + a) E + e],
+// one thread per output (direct length-M3 sum; M3 <= kRootFftMax)
+__global__ void k_rootfft_dft(int M, int drho, int E, const Cx<double>* __restrict__ beta,
+                              Cx<double>* __restrict__ bhat) {
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t per = (int64_t)drho * E;
+    if (id >= (int64_t)M * per) return;
+    const int sidx = (int)(id / per);
+    const int64_t t = id % per;
+    Cx<double> v = {0, 0};
+    for (int m = 0; m < M; ++m) {
+        double sn, cs;
+        sincospi(-2.0 * (double)((sidx * m) % M) / M, &sn, &cs);
+        cfma(v, Cx<double>{cs, sn}, beta[(size_t)m * per + t]);
+    }
+    bhat[id] = v;
+}
+
+// chi(k) for component a (as one cube): exp(-i k . c_0) sum_j3 S3(j3, k3) beta_hat_{n3 mod M3}
+__global__ void k_rootfft_chi(int drho, int p, Geo g, RootTab rt, const Cx<double>* __restrict__ bhat,
+                              Cx<double>* __restrict__ chi) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)drho * rt.nmode) return;
+    const int a = (int)(t / rt.nmode), e = (int)(t % rt.nmode);
+    const int n2 = rt.n2, n3 = rt.n3, E = rt.n1 * n2 * p;
+    const int i1 = e / (n2 * n3), i2 = (e / n3) % n2, i3 = e % n3;
+    const int sm = (int)rt.nmod3[i3];
+    const Cx<double>* b = bhat + ((size_t)sm * drho + a) * E + ((size_t)i1 * n2 + i2) * p;
+    Cx<double> v = {0, 0};
+    for (int k = 0; k < p; ++k) cfma(v, rt.S[2][i3 * p + k], b[k]);
+    const double h = 0.5 * g.s;
+    const double ph = -(rt.kax[0][i1] + rt.kax[1][i2] + rt.kax[2][i3]) * h;
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    chi[t] = cmul(v, Cx<double>{cs, sn});
+}
+
+// evaluation, k3 -> j3 grouped by s = n3 mod M3: C2[(s du + j)][i1][i2][j3] =
+//   sum_{i3 : n3 mod M3 = s} conj(S3(j3, k3)) exp(i k . c_0) uhat_j(k)
+__global__ void k_rootfft_bwd1(int M, int du, int p, Geo g, RootTab rt, const Cx<double>* __restrict__ uhat,
+                               Cx<double>* __restrict__ C2) {
+    const int n1 = rt.n1, n2 = rt.n2, n3 = rt.n3, per = n1 * n2 * p;
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= (int64_t)M * du * per) return;
+    const int job = (int)(id / per), e = (int)(id % per);
+    const int sm = job / du, j = job % du;
+    const int i12 = e / p, j3 = e % p;
+    const int i1 = i12 / n2, i2 = i12 % n2;
+    const double h = 0.5 * g.s;
+    Cx<double> v = {0, 0};
+    for (int i3 = 0; i3 < n3; ++i3) {
+        if ((int)rt.nmod3[i3] != sm) continue;
+        const double ph = (rt.kax[0][i1] + rt.kax[1][i2] + rt.kax[2][i3]) * h;
+        double sn, cs;
+        sincos(ph, &sn, &cs);
+        const Cx<double> gk = cmul(uhat[(size_t)j * rt.nmode + (size_t)i12 * n3 + i3], Cx<double>{cs, sn});
+        cfma(v, cconj(rt.S[2][i3 * p + j3]), gk);
+    }
+    C2[id] = v;
+}
+
+// k1 -> j1, complex: Gs[job][j1][j2][j3] = sum_i1 conj(S1(j1, k1)) C1[job][i1][j2][j3]
+__global__ void k_rootfft_bwd3(int jobs, int p, RootTab rt, const Cx<double>* __restrict__ C1,
+                               Cx<double>* __restrict__ Gs) {
+    const int p2 = p * p, p3 = p2 * p;
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= (int64_t)jobs * p3) return;
+    const int job = (int)(id / p3), e = (int)(id % p3);
+    const int j1 = e / p2, r = e % p2;
+    const Cx<double>* c = C1 + (size_t)job * rt.n1 * p2 + r;
+    Cx<double> v = {0, 0};
+    for (int k = 0; k < rt.n1; ++k) cfma(v, cconj(rt.S[0][k * p + j1]), c[(size_t)k * p2]);
+    Gs[id] = v;
+}
+
+// inverse DFT over s and the real part: local[(m du + j) p^3 + e] = Re sum_s exp(2 pi i s m / M3)
+// Gs[(s du + j) p^3 + e] + constant (cube m is box m of level 0); one thread per output
+template <class T>
+__global__ void k_rootfft_idft(int M, int du, int p, RootTab rt, const Cx<double>* __restrict__ Gs,
+                               const double* __restrict__ rho_sum, int drho, T* __restrict__ local) {
+    const int p3 = p * p * p;
+    const int64_t per = (int64_t)du * p3;
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= (int64_t)M * per) return;
+    const int m = (int)(id / per);
+    const int64_t t = id % per;
+    const int j = (int)(t / p3);
+    double v = 0;
+    for (int sidx = 0; sidx < M; ++sidx) {
+        double sn, cs;
+        sincospi(2.0 * (double)((sidx * m) % M) / M, &sn, &cs);
+        const Cx<double> gsv = Gs[(size_t)sidx * per + t];
+        v += cs * gsv.x - sn * gsv.y;
+    }
+    double cst = 0;
+    for (int b = 0; b < drho; ++b) cst += rt.rconst[j * drho + b] * rho_sum[b];
+    local[id] = (T)(v + cst);
 }
 
 __global__ void k_strength_sums(int64_t N, int drho, const double* __restrict__ rho, double* __restrict__ out) {
