@@ -127,6 +127,77 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+EXTRA = [
+    # (name, kernel, D, L, N, point generator, strengths) -- the other workload shapes, mixed path
+    ("Stokeslet velocity+gradient, D=1, L=(8,1,1), N=1e6 uniform, N(0,1) forces minus mean, tol 1e-6",
+     "stokeslet", 1, [8.0, 1.0, 1.0], 1_000_000, "uniform", "stokes"),
+    ("Stresslet potential+gradient, D=3, L=(1,1,16) (16 cubes, DFT over the cube index), N=4e6 uniform, "
+     "q (x) n strengths, tol 1e-6", "stresslet", 3, [1.0, 1.0, 16.0], 4_000_000, "uniform", "stokes"),
+    ("Rotlet potential+gradient, D=3, L=(1,1,16) (16 cubes, DFT over the cube index), N=4e6 uniform, "
+     "N(0,1) torques, tol 1e-6", "rotlet", 3, [1.0, 1.0, 16.0], 4_000_000, "uniform", "stokes"),
+    ("Laplace energy and forces through torch.autograd (two evaluations), D=3, L=(1,1,1), N=1e6 in 64 "
+     "Gaussian clusters (sigma 0.02), balanced +-1 charges, tol 1e-6", "laplace-autograd", 3, [1.0, 1.0, 1.0],
+     1_000_000, "clusters", "balanced"),
+]
+
+
+def extra_configs(dmk, Wl, dev, stream, steps=3, warmup=2):
+    """Targets/s of the other workload shapes (mixed path, potentials and gradients), a few steps each."""
+    import torch
+    from paper_2606_27134_b300 import autograd as ag
+    out = []
+    for name, kernel, D, L, N, pg, sg in EXTRA:
+        try:
+            if pg == "uniform":
+                x = Wl.uniform_points(N, L, 7001)
+            else:
+                x = Wl.clustered_points(N, L, 7001, n_centers=64, sigma=0.02)
+            if sg == "stokes":
+                rho = Wl.stokes_strengths(kernel, N, 7002)
+            else:
+                rho = Wl.balanced_charges(N, 7002).reshape(N, 1)
+            xt = torch.tensor(x, dtype=torch.float64, device=dev)
+            rt = torch.tensor(rho, dtype=torch.float64, device=dev)
+            if kernel == "laplace-autograd":
+                pot = ag.Potential("laplace", D, L, 1e-6, precision="mixed", n_s=250)
+
+                def step():
+                    xx = xt.detach().requires_grad_(True)
+                    u = pot(xx, rt)
+                    E = 0.5 * (rt * u).sum()
+                    (gx,) = torch.autograd.grad(E, xx)
+                    return gx
+                plan = pot.plan
+            else:
+                plan = dmk.Plan(kernel, D, L, 1e-6, precision="mixed", n_s=250)   # default stream
+
+                def step():
+                    return plan.eval(xt, rt, grad=True)
+            for _ in range(warmup):
+                step()
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(steps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(torch.cuda.current_stream())
+                step()
+                b.record(torch.cuda.current_stream())
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            st = plan.stats()
+            t = statistics.median(ms)
+            out.append({"workload": name, "N": N, "ms_per_step": t, "targets_per_s": N / (t / 1e3),
+                        "p": st["p"], "n_boxes": st["n_boxes"], "n_levels": st["n_levels"], "pairs": st["n_pairs"],
+                        "steps": steps, "warmup": warmup})
+            if kernel != "laplace-autograd":
+                plan.close()
+            del xt, rt
+            torch.cuda.empty_cache()
+        except Exception as e:  # reported, never fatal
+            out.append({"workload": name, "error": str(e)[:200]})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -136,6 +207,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--paths", default="mixed,fp64", help="precision paths to time (profiling: mixed)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workload configurations (profiling)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -240,7 +312,7 @@ def main():
     flops = leaf_flops("laplace", st, N, grad=True, precision="mixed")
     pk = fp32_peak_tflops()
     achieved = flops / (leaf_ms / 1e3) / 1e12 if leaf_ms > 0 else None
-    roof = {"bound": "alu", "kernel": "k_leaf<float, Laplace, grad>", "achieved": achieved, "peak": pk,
+    roof = {"bound": "alu", "kernel": "k_leaf3<float, Laplace, grad>", "achieved": achieved, "peak": pk,
             "unit": "TFLOP/s", "frac": (achieved / pk) if achieved else None, "traffic": None,
             "peak_note": "FP32 FMA pipe: 148 SMs x 128 lanes x 2 flop x 2.032 GHz (derived from unit counts and "
                          "the maximum SM clock; no measured FP32 peak in MEASURED_PEAKS.json)"}
@@ -258,6 +330,8 @@ def main():
             "e2e": {"value": world * N / (e2e_ms / 1e3), "unit": "targets/s",
                     "h2d_bytes_per_step": N * (3 + 1) * 8, "d2h_bytes_per_step": N * (1 + 3) * 8},
             "gpu_launches": int(st["kernel_launches"]) * args.steps}
+    if not args.no_extra:
+        line["other_configs"] = extra_configs(dmk, Wl, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             from oracle.dmk import evaluate
