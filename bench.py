@@ -308,12 +308,12 @@ def main():
     gpairs = pairs / (leaf_ms / 1e3) / 1e9 if leaf_ms > 0 else None
     # roofline of the leaf kernel (FP32 ALU bound): algorithmic FLOPs per launch
     # = pairs * F_pair + N * F_cheb, F_pair and F_cheb derived in the design notes
-    from paper_2606_27134_b300.roofline import leaf_flops, fp32_peak_tflops
+    from paper_2606_27134_b300.roofline import leaf_flops, fp32_peak_tflops, LEAF_TRAFFIC_BYTES
     flops = leaf_flops("laplace", st, N, grad=True, precision="mixed")
     pk = fp32_peak_tflops()
     achieved = flops / (leaf_ms / 1e3) / 1e12 if leaf_ms > 0 else None
     roof = {"bound": "alu", "kernel": "k_leaf3<float, Laplace, grad>", "achieved": achieved, "peak": pk,
-            "unit": "TFLOP/s", "frac": (achieved / pk) if achieved else None, "traffic": None,
+            "unit": "TFLOP/s", "frac": (achieved / pk) if achieved else None, "traffic": LEAF_TRAFFIC_BYTES,
             "peak_note": "FP32 FMA pipe: 148 SMs x 128 lanes x 2 flop x 2.032 GHz (derived from unit counts and "
                          "the maximum SM clock; no measured FP32 peak in MEASURED_PEAKS.json)"}
     line = {"metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,

@@ -9,6 +9,11 @@ Per-unit figures (method arithmetic, not the instructions a kernel happens to is
 One leaf-kernel launch processes every visited pair and every target once.
 """
 
+# DRAM bytes (read + write) of one k_leaf3<float, Laplace, grad> launch at the benchmark
+# workload, from one ncu capture of the kernel as it stands (profiles/k_leaf3_laplace_2P_N1e5_mixed.md);
+# set to None whenever the kernel changes until it is captured again.
+LEAF_TRAFFIC_BYTES = 37.22e6 + 0.017e6
+
 SMS = 148
 FP32_LANES_PER_SM = 128
 MAX_SM_GHZ = 2.032
