@@ -186,8 +186,16 @@ def extra_configs(dmk, Wl, dev, stream, steps=3, warmup=2):
                 ms.append(a.elapsed_time(b))
             st = plan.stats()
             t = statistics.median(ms)
+            # one more pass with per-stage events
+            plan.set_timing(True)
+            step()
+            torch.cuda.synchronize()
+            stage = plan.stats()["stage_ms"]
+            plan.set_timing(False)
             out.append({"workload": name, "N": N, "ms_per_step": t, "targets_per_s": N / (t / 1e3),
                         "p": st["p"], "n_boxes": st["n_boxes"], "n_levels": st["n_levels"], "pairs": st["n_pairs"],
+                        "stage_ms": dict(zip(["tree", "upward", "root", "planewave", "shift", "leaf", "total"],
+                                             [round(v, 3) for v in stage])),
                         "steps": steps, "warmup": warmup})
             if kernel != "laplace-autograd":
                 plan.close()

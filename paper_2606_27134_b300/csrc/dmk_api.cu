@@ -71,6 +71,9 @@ struct dmk_plan_s {
     size_t arena_cap = 0, arena_off = 0;
     // dynamic shared memory already opted in per kernel (the attribute persists on the device)
     std::unordered_map<const void*, size_t> smem_set;
+    // levels the point keys are sorted to (their leading 3 sort_levels bits): the depth of the
+    // last forest plus one, all kBits levels at first or after a deeper forest appears
+    int sort_levels = kBits;
 };
 
 namespace {
@@ -93,7 +96,7 @@ namespace {
 enum BufId {
     B_W, B_KEYS, B_KEYS2, B_IDX, B_IDX2, B_XS, B_RS, B_CUB, B_FLAGS, B_CNT,
     B_CELLS, B_R, B_CAND, B_BOXU64, B_BOXINT, B_LEAVES, B_DOFFS, B_DL, B_NLBOX,
-    B_PROXY, B_LOCAL, B_PW, B_SCRATCH, B_CHI, B_UHAT, B_MISC, B_DEVPTS, B_DEVRHO, B_DEVPOT, B_DEVGRAD, B_XF, B_VW,
+    B_PROXY, B_LOCAL, B_PW, B_SCRATCH, B_CHI, B_UHAT, B_MISC, B_DEVPTS, B_DEVRHO, B_DEVPOT, B_DEVGRAD, B_XF, B_VW, B_PART,
     B_COUNT
 };
 
@@ -465,13 +468,8 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     int cube_bits = 0;
     while ((1 << cube_bits) < Mtot) ++cube_bits;
     const int end_bit = 3 * kBits + cube_bits;
-    size_t tmp_bytes = 0;
-    cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys, keys2, idx, idx2, (int)N, 0, end_bit, st);
-    void* vcub;
-    CKS(ensure(plan, B_CUB, std::max<size_t>(tmp_bytes, 1 << 20), &vcub));
-    size_t cub_cap = plan->bufs[B_CUB].cap;
-    CK(cub::DeviceRadixSort::SortPairs(vcub, tmp_bytes, keys, keys2, idx, idx2, (int)N, 0, end_bit, st));
-    launches += 4;
+    void* vcub = nullptr;
+    size_t cub_cap = 0;
     const uint64_t* pkeys = keys2;
     // FP32 path: leading/trailing FP32 parts of the sorted coordinates and FP32 strengths, so
     // that the leaf stage forms source offsets without FP64 arithmetic
@@ -483,14 +481,51 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         xl = xh + 3 * N;
         rsf = xl + 3 * N;
     }
-    k_gather<<<nblk(N, 256), 256, 0, st>>>(N, drho, idx2, (const double*)vw, rho, xs, rs, xh, xl, rsf);
-    ++launches;
-    k_strength_sums<<<std::min<unsigned>(nblk(N, 256), 1024), 256, 0, st>>>(N, drho, rs, d_sums);
-    ++launches;
-    // ---- (2) refinement: one pass over the sorted keys, all levels at once ----------------
+    const int ngb = (int)((N + kGatherThreads - 1) / kGatherThreads);
+    void* vpart;
+    CKS(ensure(plan, B_PART, (size_t)ngb * 2 * drho * sizeof(double), &vpart));
     int* d_nR = (int*)((char*)vmisc + 1024);       // non-leaf count per level
     int* d_missing = (int*)((char*)vmisc + 1280);  // balance check, per level
     int* d_nleaf = (int*)((char*)vmisc + 1536);
+    // cells with more than n_s points are disjoint: at most N/(n_s+1) split per level
+    const int64_t cap = std::max<int64_t>(1, N / ((int64_t)plan->n_s + 1));
+    const int nblkR = (int)((N + kRefineThreads - 1) / kRefineThreads);
+    void *vrblk, *vR;
+    CKS(ensure(plan, B_CNT, (size_t)2 * kBits * nblkR * sizeof(int), &vrblk));
+    CKS(ensure(plan, B_R, (size_t)kBits * cap * sizeof(uint64_t), &vR));
+    int* bcnt = (int*)vrblk;
+    int* boff = bcnt + (size_t)kBits * nblkR;
+    uint64_t* Rall = (uint64_t*)vR;
+    // one pinned readback of nR[0..kBits] (misc + 1024) and missing[] (misc + 1280)
+    const int* hmeta = (const int*)plan->h_meta;
+    const int kMissing = 64;                              // int offset of missing[] in the copy
+    // ---- (1)+(2) sort on the leading key bits, gather, one-pass refinement; repeated with all
+    // key bits if the forest reaches the sorted depth ----------------------------------------
+    int lsort = std::max(1, std::min(kBits, plan->sort_levels));
+    for (int attempt = 0;; ++attempt) {
+        const int begin_bit = 3 * (kBits - lsort);
+        size_t tmp_bytes = 0;
+        cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys, keys2, idx, idx2, (int)N, begin_bit, end_bit, st);
+        CKS(ensure(plan, B_CUB, std::max<size_t>(tmp_bytes, 1 << 20), &vcub));
+        cub_cap = plan->bufs[B_CUB].cap;
+        CK(cub::DeviceRadixSort::SortPairs(vcub, tmp_bytes, keys, keys2, idx, idx2, (int)N, begin_bit, end_bit, st));
+        k_gather<<<ngb, kGatherThreads, 0, st>>>(N, drho, idx2, (const double*)vw, rho, xs, rs, xh, xl, rsf,
+                                                  (double*)vpart);
+        k_sum_partials<<<1, 1024, 0, st>>>(ngb, 2 * drho, (const double*)vpart, d_sums);
+        k_refine_count<<<nblkR, kRefineThreads, 0, st>>>(N, pkeys, plan->n_s, nblkR, lsort, bcnt);
+        k_refine_scan<<<1, 1024, 0, st>>>(nblkR, bcnt, boff, d_nR);
+        k_refine_write<<<nblkR, kRefineThreads, 0, st>>>(N, pkeys, plan->n_s, nblkR, lsort, boff, cap, Rall);
+        {
+            const int64_t nchk = (int64_t)(kBits - 1) * 27 * cap;
+            CK(cudaMemsetAsync(d_missing, 0, kBits * sizeof(int), st));
+            k_balance_check<<<(unsigned)((nchk + 255) / 256), 256, 0, st>>>(cap, Rall, d_nR, g, d_missing);
+        }
+        launches += 11;
+        CK(cudaMemcpyAsync(plan->h_meta, d_nR, 512, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (lsort >= kBits || hmeta[lsort - 1] == 0) break;
+        lsort = kBits;                                     // deeper than the sorted bits: resort
+    }
     TreeInfo ti;
     std::vector<const uint64_t*> Rl(kMaxLevels + 1, nullptr);
     // balance arrays that outgrow the refinement layout: stream-ordered, released on return
@@ -507,31 +542,10 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     auto free_levels = [&]() { for (void* p : level_mem) cudaFreeAsync(p, st); level_mem.clear(); };
     struct Guard { std::function<void()> f; ~Guard() { f(); } };
     Guard guard{free_levels};
-    // cells with more than n_s points are disjoint: at most N/(n_s+1) split per level
-    const int64_t cap = std::max<int64_t>(1, N / ((int64_t)plan->n_s + 1));
-    const int nblkR = (int)((N + kRefineThreads - 1) / kRefineThreads);
-    void *vrblk, *vR;
-    CKS(ensure(plan, B_CNT, (size_t)2 * kBits * nblkR * sizeof(int), &vrblk));
-    CKS(ensure(plan, B_R, (size_t)kBits * cap * sizeof(uint64_t), &vR));
-    int* bcnt = (int*)vrblk;
-    int* boff = bcnt + (size_t)kBits * nblkR;
-    uint64_t* Rall = (uint64_t*)vR;
-    k_refine_count<<<nblkR, kRefineThreads, 0, st>>>(N, pkeys, plan->n_s, nblkR, bcnt);
-    k_refine_scan<<<1, 1024, 0, st>>>(nblkR, bcnt, boff, d_nR);
-    k_refine_write<<<nblkR, kRefineThreads, 0, st>>>(N, pkeys, plan->n_s, nblkR, boff, cap, Rall);
-    {
-        const int64_t nchk = (int64_t)(kBits - 1) * 27 * cap;
-        k_balance_check<<<(unsigned)((nchk + 255) / 256), 256, 0, st>>>(cap, Rall, d_nR, g, d_missing);
-    }
-    launches += 4;
-    // one pinned readback of nR[0..kBits] (misc + 1024) and missing[] (misc + 1280)
-    const int* hmeta = (const int*)plan->h_meta;
-    const int kMissing = 64;                              // int offset of missing[] in the copy
-    CK(cudaMemcpyAsync(plan->h_meta, d_nR, 512, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
     int nlev = kBits + 1;
     for (int k = 0; k <= kBits; ++k)
         if (hmeta[k] == 0) { nlev = k + 1; break; }
+    plan->sort_levels = std::min(kBits, nlev + 1);
     for (int l = 0; l < nlev; ++l) Rl[l] = Rall + (size_t)l * cap;
     bool balanced = true;
     for (int k = 0; k < kBits; ++k)
@@ -802,7 +816,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         bool pwout_done = false;
         if constexpr (sizeof(T) == 4) {
             if (p <= kMaxPFast && nfh <= mp && po2_bytes <= plan->smem_optin) {
-                const unsigned grid = (unsigned)std::min(n_nl, 148 * 2);
+                const unsigned grid = (unsigned)std::min(2 * n_nl, 148 * 4);
                 if (mp == 20) {
                     CKS(set_smem(plan, k_pwout2<T, 20>, po2_bytes));
                     k_pwout2<T, 20><<<grid, 416, po2_bytes, st>>>(n_nl, nl_box, tab, proxy, W);

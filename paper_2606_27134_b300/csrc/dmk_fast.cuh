@@ -439,29 +439,32 @@ __global__ void __launch_bounds__(kTransThreads) k_pw_trans(int n, const int* __
 }
 
 // Plane-wave outgoing expansions (Sec. 3.1.4, Eq. Dl_int_discr), register-blocked: for every
-// non-leaf box W(m) = sum_j proxy(j) exp(-i h m . y_j), m3 >= 0 only (real input).  The proxy
-// tensor is staged in shared memory; stage 1, thread per (j1, j2) fiber: j3 -> m3 with the
-// fiber in registers; stage 2, thread per (j1, m3, half of m2): j2 -> m2; stage 3, thread per
-// (m2, m3, half of m1): j1 -> m1, written to W[nl][a][(m1 NF + m2) nfh + m3].
+// non-leaf box W(m) = sum_j proxy(j) exp(-i h m . y_j), m3 >= 0 only (real input).  Work item =
+// (box, half of the m2 range).  The proxy tensor is staged in shared memory; stage 1, thread per
+// (j1, j2) fiber: j3 -> m3 with the fiber in registers; stage 2, thread per (j1, m3): j2 -> m2
+// for the item's m2 half; stage 3, thread per (m2 of the half, m3, half of m1): j1 -> m1,
+// written to W[nl][a][(m1 NF + m2) nfh + m3].  The proxy buffer is reused for stage 2's output.
 template <class T, int MAXP>
-__global__ void __launch_bounds__(416) k_pwout2(int n, const int* __restrict__ nl_box, Tab<T> tab,
+__global__ void __launch_bounds__(416, MAXP <= 20 ? 2 : 1) k_pwout2(int n, const int* __restrict__ nl_box, Tab<T> tab,
                                                 const T* __restrict__ proxy, Cx<T>* __restrict__ W) {
     const int p = tab.p, p2 = p * p, p3 = p2 * p, P = odd_pitch(p), drho = tab.d_rho;
     const int nf = tab.nf, NF = tab.NF, nfh = tab.nfh, nW = NF * NF * nfh;
     const int NFP = NF + 1;                                    // row pitch of Et
     const int pm3 = nfh | 1;
-    const int H = (NF + 1) / 2;                                // outputs per thread in stages 2, 3
+    const int H = (NF + 1) / 2;                                // m values per half
     constexpr int MAXH = MAXP + 2;                             // H <= MAXH, nfh <= MAXP
     Cx<T>* Et = reinterpret_cast<Cx<T>*>(dsmem);               // p x NFP: Et[k][m] = E[m][k]
     Cx<T>* A1 = Et + p * NFP;                                  // p^2 x pm3
-    Cx<T>* A2 = A1 + p2 * pm3;                                 // p x NF x nfh
-    T* X = reinterpret_cast<T*>(A2 + p * NF * nfh);            // p^2 x P
+    T* X = reinterpret_cast<T*>(A1 + p2 * pm3);                // p^2 x P (stage 1 input)
+    Cx<T>* A2 = reinterpret_cast<Cx<T>*>(X);                   // p x H x nfh (stage 2 output)
     for (int e = threadIdx.x; e < p * NFP; e += blockDim.x) {
         const int k = e / NFP, m = e % NFP;
         Et[e] = (m < NF) ? tab.E[m * p + k] : Cx<T>{0, 0};
     }
-    for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
+    for (int w = blockIdx.x; w < 2 * n; w += gridDim.x) {
+        const int bi = w >> 1, half = w & 1;
         const int box = nl_box[bi];
+        const int m20 = half * H, m2c = min(H, NF - m20);
         for (int a = 0; a < drho; ++a) {
             __syncthreads();
             load_padded_batched<T, MAXP>(X, proxy + ((size_t)box * drho + a) * p3, p, P);
@@ -487,34 +490,33 @@ __global__ void __launch_bounds__(416) k_pwout2(int n, const int* __restrict__ n
                     if (m < nfh) A1[c * pm3 + m] = acc[m];
             }
             __syncthreads();
-            for (int c = threadIdx.x; c < 2 * p * nfh; c += blockDim.x) {   // j2 -> m2
-                const int h = c / (p * nfh), r = c % (p * nfh);
-                const int j1 = r / nfh, m3 = r % nfh;
-                const int m0 = h * H, mc = min(H, NF - m0);
+            for (int c = threadIdx.x; c < p * nfh; c += blockDim.x) {   // j2 -> m2 (this half)
+                const int j1 = c / nfh, m3 = c % nfh;
                 Cx<T> acc[MAXH];
 #pragma unroll
                 for (int m = 0; m < MAXH; ++m) acc[m] = {0, 0};
                 for (int k = 0; k < p; ++k) {
                     const Cx<T> v = A1[(j1 * p + k) * pm3 + m3];
-                    const Cx<T>* row = Et + k * NFP + m0;
+                    const Cx<T>* row = Et + k * NFP + m20;
 #pragma unroll
                     for (int m = 0; m < MAXH; ++m)
-                        if (m < mc) cfma(acc[m], row[m], v);
+                        if (m < m2c) cfma(acc[m], row[m], v);
                 }
 #pragma unroll
                 for (int m = 0; m < MAXH; ++m)
-                    if (m < mc) A2[(j1 * NF + m0 + m) * nfh + m3] = acc[m];
+                    if (m < m2c) A2[(j1 * H + m) * nfh + m3] = acc[m];
             }
             __syncthreads();
             Cx<T>* out = W + ((size_t)bi * drho + a) * nW;
-            for (int c = threadIdx.x; c < 2 * NF * nfh; c += blockDim.x) {  // j1 -> m1
-                const int h = c / (NF * nfh), r = c % (NF * nfh);
-                const int m0 = h * H, mc = min(H, NF - m0);
+            for (int c = threadIdx.x; c < 2 * m2c * nfh; c += blockDim.x) {  // j1 -> m1
+                const int h1 = c / (m2c * nfh), r = c % (m2c * nfh);
+                const int mm = r / nfh, m3 = r % nfh;
+                const int m0 = h1 * H, mc = min(H, NF - m0);
                 Cx<T> acc[MAXH];
 #pragma unroll
                 for (int m = 0; m < MAXH; ++m) acc[m] = {0, 0};
                 for (int k = 0; k < p; ++k) {
-                    const Cx<T> v = A2[k * NF * nfh + r];
+                    const Cx<T> v = A2[(k * H + mm) * nfh + m3];
                     const Cx<T>* row = Et + k * NFP + m0;
 #pragma unroll
                     for (int m = 0; m < MAXH; ++m)
@@ -522,7 +524,7 @@ __global__ void __launch_bounds__(416) k_pwout2(int n, const int* __restrict__ n
                 }
 #pragma unroll
                 for (int m = 0; m < MAXH; ++m)
-                    if (m < mc) out[(size_t)(m0 + m) * NF * nfh + r] = acc[m];
+                    if (m < mc) out[(size_t)(m0 + m) * NF * nfh + (m20 + mm) * nfh + m3] = acc[m];
             }
         }
     }
@@ -531,9 +533,9 @@ __global__ void __launch_bounds__(416) k_pwout2(int n, const int* __restrict__ n
 // shared memory of k_pwout2
 template <class T>
 inline size_t pwout2_smem(int p, int NF, int nfh) {
-    const int P = p | 1, pm3 = nfh | 1;
-    return ((size_t)p * (NF + 1) + (size_t)p * p * pm3 + (size_t)p * NF * nfh) * sizeof(Cx<T>) +
-           (size_t)p * p * P * sizeof(T);
+    const int P = p | 1, pm3 = nfh | 1, H = (NF + 1) / 2;
+    const size_t xbytes = std::max((size_t)p * p * P * sizeof(T), (size_t)p * H * nfh * sizeof(Cx<T>));
+    return ((size_t)p * (NF + 1) + (size_t)p * p * pm3) * sizeof(Cx<T>) + xbytes;
 }
 
 // Incoming transform (Sec. 3.1.4) from the translated spectrum Vw of k_pw_trans: stage A, thread

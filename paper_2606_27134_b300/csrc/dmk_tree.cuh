@@ -46,25 +46,64 @@ __global__ void k_quantize(int64_t N, const double* __restrict__ pts, Geo g, dou
 }
 
 // sorted order -> sorted SoA coordinates and strengths
-__global__ void k_gather(int64_t N, int drho, const int* __restrict__ idx, const double* __restrict__ w,
-                         const double* __restrict__ rho, double* __restrict__ xs, double* __restrict__ rs,
-                         float* __restrict__ xh, float* __restrict__ xl, float* __restrict__ rsf) {
-    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= N) return;
-    int i = idx[k];
-    for (int a = 0; a < 3; ++a) {
-        const double v = w[a * N + i];
-        xs[a * N + k] = v;
-        if (xh) {   // leading + trailing FP32 parts (exact split of the FP64 value to 48 bits)
-            const float h = (float)v;
-            xh[a * N + k] = h;
-            xl[a * N + k] = (float)(v - (double)h);
+// Gather into key order (FP64 coordinates and strengths; FP32 two-part copies for the mixed
+// path) and per-block sums of the strengths and of their absolute values (block b writes
+// partial[b * 2 d_rho + v], v < d_rho: sum rho_v, v >= d_rho: sum |rho_v|).
+constexpr int kGatherThreads = 256;
+
+__global__ void __launch_bounds__(kGatherThreads) k_gather(int64_t N, int drho, const int* __restrict__ idx,
+                                                           const double* __restrict__ w,
+                                                           const double* __restrict__ rho, double* __restrict__ xs,
+                                                           double* __restrict__ rs, float* __restrict__ xh,
+                                                           float* __restrict__ xl, float* __restrict__ rsf,
+                                                           double* __restrict__ partial) {
+    __shared__ double red[18][kGatherThreads / 32];
+    const int64_t k = blockIdx.x * (int64_t)kGatherThreads + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double s[9], sa[9];
+    for (int a = 0; a < drho; ++a) { s[a] = 0; sa[a] = 0; }
+    if (k < N) {
+        const int i = idx[k];
+        for (int a = 0; a < 3; ++a) {
+            const double v = w[a * N + i];
+            xs[a * N + k] = v;
+            if (xh) {   // leading + trailing FP32 parts (exact split of the FP64 value to 48 bits)
+                const float h = (float)v;
+                xh[a * N + k] = h;
+                xl[a * N + k] = (float)(v - (double)h);
+            }
+        }
+        for (int a = 0; a < drho; ++a) {
+            const double r = rho[(int64_t)i * drho + a];
+            rs[k * drho + a] = r;
+            if (rsf) rsf[k * drho + a] = (float)r;
+            s[a] = r;
+            sa[a] = fabs(r);
         }
     }
     for (int a = 0; a < drho; ++a) {
-        const double r = rho[(int64_t)i * drho + a];
-        rs[k * drho + a] = r;
-        if (rsf) rsf[k * drho + a] = (float)r;
+        for (int o = 16; o > 0; o >>= 1) {
+            s[a] += __shfl_down_sync(0xffffffffu, s[a], o);
+            sa[a] += __shfl_down_sync(0xffffffffu, sa[a], o);
+        }
+        if (lane == 0) { red[a][warp] = s[a]; red[drho + a][warp] = sa[a]; }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * drho) {
+        double t = 0;
+        for (int q = 0; q < kGatherThreads / 32; ++q) t += red[threadIdx.x][q];
+        partial[(size_t)blockIdx.x * 2 * drho + threadIdx.x] = t;
+    }
+}
+
+// one CTA: out[v] = sum over blocks of partial[b * nv + v], in a fixed order (warp per value)
+__global__ void k_sum_partials(int nb, int nv, const double* __restrict__ partial, double* __restrict__ out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int v = warp; v < nv; v += nwarp) {
+        double t = 0;
+        for (int b = lane; b < nb; b += 32) t += partial[(size_t)b * nv + v];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) out[v] = t;
     }
 }
 
@@ -106,6 +145,8 @@ __device__ __forceinline__ void cell_range(const uint64_t* pkeys, int64_t N, int
 // still covers i + n_s.  A split cell's parent holds at least as many points and splits too, so
 // the split cells of every level follow from one pass over the points; they come out in key
 // order through an order-preserving compaction: per-block counts, a one-CTA scan, a write pass.
+// Only levels l < lmax are examined: the keys may be sorted on their leading 3 lmax bits only
+// (plus the cube index), which orders every cell of those levels.
 constexpr int kRefineThreads = 256;
 
 struct SplitProbe {
@@ -128,14 +169,14 @@ struct SplitProbe {
 
 // counts of split-cell starts per level and block: bcnt[l * nblk + block]
 __global__ void __launch_bounds__(kRefineThreads) k_refine_count(int64_t N, const uint64_t* __restrict__ pk, int n_s,
-                                                                 int nblk, int* __restrict__ bcnt) {
+                                                                 int nblk, int lmax, int* __restrict__ bcnt) {
     __shared__ int wc[kBits][kRefineThreads / 32];
     const int64_t i = blockIdx.x * (int64_t)kRefineThreads + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool valid = i < N;
     SplitProbe sp(pk, N, valid ? i : 0, n_s);
     for (int l = 0; l < kBits; ++l) {
-        const unsigned bal = __ballot_sync(0xffffffffu, valid && sp.split(l));
+        const unsigned bal = __ballot_sync(0xffffffffu, valid && l < lmax && sp.split(l));
         if (lane == 0) wc[l][warp] = __popc(bal);
     }
     __syncthreads();
@@ -192,8 +233,8 @@ __global__ void __launch_bounds__(1024) k_refine_scan(int nblk, const int* __res
 
 // split cells of level l, in key order: R[l * cap + k]
 __global__ void __launch_bounds__(kRefineThreads) k_refine_write(int64_t N, const uint64_t* __restrict__ pk, int n_s,
-                                                                 int nblk, const int* __restrict__ boff, int64_t cap,
-                                                                 uint64_t* __restrict__ R) {
+                                                                 int nblk, int lmax, const int* __restrict__ boff,
+                                                                 int64_t cap, uint64_t* __restrict__ R) {
     __shared__ int wc[kBits][kRefineThreads / 32];
     const int64_t i = blockIdx.x * (int64_t)kRefineThreads + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -201,7 +242,7 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine_write(int64_t N, cons
     SplitProbe sp(pk, N, valid ? i : 0, n_s);
     unsigned bals[kBits];
     for (int l = 0; l < kBits; ++l) {
-        bals[l] = __ballot_sync(0xffffffffu, valid && sp.split(l));
+        bals[l] = __ballot_sync(0xffffffffu, valid && l < lmax && sp.split(l));
         if (lane == 0) wc[l][warp] = __popc(bals[l]);
     }
     __syncthreads();
@@ -276,7 +317,8 @@ __global__ void k_balance_cand(int capR, const uint64_t* __restrict__ R, const i
 // unchanged; the caller then balances with the general path.  A set *overflow also makes later
 // levels return at once.
 constexpr int kBalThreads = 1024;
-constexpr int kBalNew = 2048;
+constexpr int kBalNew = 1024;
+constexpr int kBalCache = 2048;     // R_{l-1} searched in shared memory up to this size
 
 __global__ void __launch_bounds__(kBalThreads) k_balance_small(const uint64_t* __restrict__ R,
                                                                const uint64_t* __restrict__ Rp, int* __restrict__ nR,
@@ -284,11 +326,15 @@ __global__ void __launch_bounds__(kBalThreads) k_balance_small(const uint64_t* _
                                                                int* __restrict__ overflow) {
     __shared__ uint64_t nw[kBalNew];
     __shared__ uint64_t U[kBalNew];
+    __shared__ uint64_t Rc[kBalCache];
     __shared__ unsigned char fst[kBalNew];
     __shared__ int cnt, nu;
     if (*overflow) return;
     const int n = nR[l], m = nR[l - 1];
     if (threadIdx.x == 0) { cnt = 0; nu = 0; }
+    if (m <= kBalCache)
+        for (int a = threadIdx.x; a < m; a += blockDim.x) Rc[a] = Rp[a];
+    const uint64_t* Rs = (m <= kBalCache) ? Rc : Rp;
     __syncthreads();
     for (int t = threadIdx.x; t < 27 * n; t += blockDim.x) {
         const int i = t / 27, d = t % 27;
@@ -298,7 +344,7 @@ __global__ void __launch_bounds__(kBalThreads) k_balance_small(const uint64_t* _
         if (!neighbour(g, l, ix, dd, nb, sh)) continue;
         const int par[3] = {nb[0] >> 1, nb[1] >> 1, nb[2] >> 1};
         const uint64_t P = cell_key(g, l - 1, par);
-        if (find_u64(Rp, m, P) < 0) {
+        if (find_u64(Rs, m, P) < 0) {
             const int k = atomicAdd(&cnt, 1);
             if (k < kBalNew) nw[k] = P;
         }
@@ -334,7 +380,7 @@ __global__ void __launch_bounds__(kBalThreads) k_balance_small(const uint64_t* _
     }
     for (int b = threadIdx.x; b < u; b += blockDim.x) {
         const uint64_t y = U[b];
-        Rout[b + lower_bound_u64(Rp, m, y)] = y;
+        Rout[b + lower_bound_u64(Rs, m, y)] = y;
     }
     if (threadIdx.x == 0) nR[l - 1] = m + u;
 }
