@@ -298,11 +298,10 @@ def main():
     plan_m = prec_results["mixed"]["plan"]
     ms_e2e = [float("nan")] if args.no_e2e else timed(plan_m, max(3, args.steps // 2), 2, host=True)[0]
 
+    from paper_2606_27134_b300.replicas import max_over_ranks
+
     def agg(v):
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        if dist:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(v, dist, dev)
 
     mixed = prec_results["mixed"]
     step_ms = agg(statistics.mean(mixed["ms"]))
