@@ -365,6 +365,17 @@ dmk_status_t launch_anterp(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int* 
     return DMK_OK;
 }
 
+template <class T, int MAXP>
+dmk_status_t launch_anterp2(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int* leaves, BoxArrays B,
+                            const double* xs, int64_t N, const double* rs, T* proxy) {
+    const int threads = (((tab.p + 1) / 2) * tab.p + 31) / 32 * 32;
+    const size_t sm = 3 * (size_t)kAnterpChunk * MAXP * sizeof(T);
+    CKS(set_smem(plan, k_anterp2<T, MAXP>, sm));
+    const unsigned grid = (unsigned)std::max(1, std::min(nleaf, 148 * 8));
+    k_anterp2<T, MAXP><<<grid, threads, sm, plan->stream>>>(nleaf, leaves, B, xs, N, rs, tab, plan->T.s, proxy);
+    return DMK_OK;
+}
+
 template <class T, int K>
 dmk_status_t launch_leaf(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int* leaves, BoxArrays B, const T* local,
                          const double* xs, int64_t N, const int* doffs, const DirectEntry* dl, LeafOut lo, bool grad) {
@@ -705,14 +716,15 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     CK(cudaMemsetAsync(local, 0, (size_t)nb * du * p3 * sizeof(T), st));
     launches += 2;
     if (nleaf > 0) {
-        if (p <= 20) CKS((launch_anterp<T, 20>(plan, tab, nleaf, leaves, B, xs, N, rs, proxy)));
-        else if (p <= 24) CKS((launch_anterp<T, 24>(plan, tab, nleaf, leaves, B, xs, N, rs, proxy)));
+        if (p <= 20) CKS((launch_anterp2<T, 20>(plan, tab, nleaf, leaves, B, xs, N, rs, proxy)));
+        else if (p <= 24) CKS((launch_anterp2<T, 24>(plan, tab, nleaf, leaves, B, xs, N, rs, proxy)));
         else CKS((launch_anterp<T, 48>(plan, tab, nleaf, leaves, B, xs, N, rs, proxy)));
         ++launches;
     }
     Evaluator<T> ev(plan, tab);
     const int pitch = odd_pitch(p);
-    const int fast_threads = ((p * p + 31) / 32) * 32;
+    const int up_threads = (((p * p + 1) / 2 + 31) / 32) * 32;     // k_up_cluster: two fibers per thread
+    const int shift_threads = ((p * p + 31) / 32) * 32;            // k_shift_child: one fiber per thread
     const int mp = (p <= 20) ? 20 : kMaxPFast;     // register width of the fiber kernels
     // per-child tensor kernels: three operators and two padded p^3 buffers per CTA
     const size_t ch_bytes = (3 * (size_t)mp * mp + 2 * (size_t)p * p * pitch) * sizeof(T);
@@ -727,9 +739,9 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         if (n == 0) continue;
         if (fast_up) {
             if (mp == 20)
-                k_up_cluster<T, 20><<<8 * n, fast_threads, ch_bytes, st>>>(nl_box + ti.nl_off[l], B, tab, proxy);
+                k_up_cluster<T, 20><<<8 * n, up_threads, ch_bytes, st>>>(nl_box + ti.nl_off[l], B, tab, proxy);
             else
-                k_up_cluster<T, kMaxPFast><<<8 * n, fast_threads, ch_bytes, st>>>(nl_box + ti.nl_off[l], B, tab, proxy);
+                k_up_cluster<T, kMaxPFast><<<8 * n, up_threads, ch_bytes, st>>>(nl_box + ti.nl_off[l], B, tab, proxy);
         } else {
             Place pl;
             unsigned char* scr;
@@ -881,9 +893,9 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         if (n == 0) continue;
         if (fast_shift) {
             if (mp == 20)
-                k_shift_child<T, 20><<<8 * n, fast_threads, ch_bytes, st>>>(nl_box + ti.nl_off[l], B, tab, local);
+                k_shift_child<T, 20><<<8 * n, shift_threads, ch_bytes, st>>>(nl_box + ti.nl_off[l], B, tab, local);
             else
-                k_shift_child<T, kMaxPFast><<<8 * n, fast_threads, ch_bytes, st>>>(nl_box + ti.nl_off[l], B, tab,
+                k_shift_child<T, kMaxPFast><<<8 * n, shift_threads, ch_bytes, st>>>(nl_box + ti.nl_off[l], B, tab,
                                                                                    local);
         } else {
             Place pl;

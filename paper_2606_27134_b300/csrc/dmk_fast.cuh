@@ -40,6 +40,36 @@ __device__ __forceinline__ void fiber_contract(const T* in, int p, int P, int ax
     }
 }
 
+// two fibers per thread: out0/out1[j] = sum_k M[k][j] in(fiber0/1, k); each operator row
+// (read as four-vectors) serves both fibers
+template <class T, int MAXP>
+__device__ __forceinline__ void fiber_contract2(const T* in, int p, int P, int ax, int fa0, int fb0, int fa1,
+                                                int fb1, bool two, const T* M, T (&acc0)[MAXP],
+                                                T (&acc1)[MAXP]) {
+    static_assert(MAXP % 4 == 0, "operator rows are read as four-vectors");
+#pragma unroll
+    for (int j = 0; j < MAXP; ++j) { acc0[j] = 0; acc1[j] = 0; }
+    for (int k = 0; k < p; ++k) {
+        const int e0 = (ax == 2) ? pidx(fa0, fb0, k, p, P) : (ax == 1) ? pidx(fa0, k, fb0, p, P) : pidx(k, fa0, fb0, p, P);
+        const int e1 = (ax == 2) ? pidx(fa1, fb1, k, p, P) : (ax == 1) ? pidx(fa1, k, fb1, p, P) : pidx(k, fa1, fb1, p, P);
+        const T x0 = in[e0];
+        const T x1 = two ? in[e1] : T(0);
+        const Quad<T>* row = reinterpret_cast<const Quad<T>*>(M + k * MAXP);
+#pragma unroll
+        for (int q = 0; q < MAXP / 4; ++q) {
+            const Quad<T> m = row[q];
+            acc0[4 * q] = fma(m.x, x0, acc0[4 * q]);
+            acc0[4 * q + 1] = fma(m.y, x0, acc0[4 * q + 1]);
+            acc0[4 * q + 2] = fma(m.z, x0, acc0[4 * q + 2]);
+            acc0[4 * q + 3] = fma(m.w, x0, acc0[4 * q + 3]);
+            acc1[4 * q] = fma(m.x, x1, acc1[4 * q]);
+            acc1[4 * q + 1] = fma(m.y, x1, acc1[4 * q + 1]);
+            acc1[4 * q + 2] = fma(m.z, x1, acc1[4 * q + 2]);
+            acc1[4 * q + 3] = fma(m.w, x1, acc1[4 * q + 3]);
+        }
+    }
+}
+
 template <class T, int MAXP>
 __device__ __forceinline__ void fiber_store(T* out, int p, int P, int ax, int fa, int fb, const T (&acc)[MAXP]) {
 #pragma unroll
@@ -1048,7 +1078,7 @@ namespace dmk {
 // contributions through distributed shared memory in the fixed order o = 0..7, each CTA
 // writing one eighth of the parent's tensor.
 template <class T, int MAXP>
-__global__ void __cluster_dims__(8, 1, 1) __launch_bounds__((MAXP * MAXP + 31) / 32 * 32, sizeof(T) == 4 ? 2 : 1)
+__global__ void __cluster_dims__(8, 1, 1) __launch_bounds__((MAXP * MAXP / 2 + 31) / 32 * 32, sizeof(T) == 4 ? 2 : 1)
     k_up_cluster(const int* __restrict__ nl_box, BoxArrays B, Tab<T> tab, T* __restrict__ proxy) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
@@ -1062,9 +1092,12 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__((MAXP * MAXP + 31) /
         const int bit = (o >> ax) & 1;
         load_op<T, MAXP>(Mo + ax * MAXP * MAXP, p, [&](int k, int j) { return tab.Ioct[(bit * p + k) * p + j]; });
     }
+    // fibers f and f + H of the p^2 fibers per thread
+    const int H = (p2 + 1) / 2;
     const int f = threadIdx.x;
-    const bool own = f < p2;
-    const int fa = own ? f / p : 0, fb = own ? f % p : 0;
+    const bool own = f < H, two = own && f + H < p2;
+    const int fa0 = own ? f / p : 0, fb0 = own ? f % p : 0;
+    const int fa1 = two ? (f + H) / p : 0, fb1 = two ? (f + H) % p : 0;
     const int Pb = nl_box[bi];
     const int C = B.child0[Pb] + o;
     const int lo = (o * p3) >> 3, hi = ((o + 1) * p3) >> 3;
@@ -1072,23 +1105,28 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__((MAXP * MAXP + 31) /
         __syncthreads();
         load_padded_batched<T, MAXP>(bufA, proxy + ((size_t)C * drho + a) * p3, p, P);
         __syncthreads();
-        T t[MAXP];
+        T t0[MAXP], t1[MAXP];
         if (own) {
-            fiber_contract<T, MAXP>(bufA, p, P, 2, fa, fb, Mo + 2 * MAXP * MAXP, t);
-            fiber_store<T, MAXP>(bufB, p, P, 2, fa, fb, t);
+            fiber_contract2<T, MAXP>(bufA, p, P, 2, fa0, fb0, fa1, fb1, two, Mo + 2 * MAXP * MAXP, t0, t1);
+            fiber_store<T, MAXP>(bufB, p, P, 2, fa0, fb0, t0);
+            if (two) fiber_store<T, MAXP>(bufB, p, P, 2, fa1, fb1, t1);
         }
         __syncthreads();
         if (own) {
-            fiber_contract<T, MAXP>(bufB, p, P, 1, fa, fb, Mo + 1 * MAXP * MAXP, t);
-            fiber_store<T, MAXP>(bufA, p, P, 1, fa, fb, t);
+            fiber_contract2<T, MAXP>(bufB, p, P, 1, fa0, fb0, fa1, fb1, two, Mo + 1 * MAXP * MAXP, t0, t1);
+            fiber_store<T, MAXP>(bufA, p, P, 1, fa0, fb0, t0);
+            if (two) fiber_store<T, MAXP>(bufA, p, P, 1, fa1, fb1, t1);
         }
         __syncthreads();
-        if (own) fiber_contract<T, MAXP>(bufA, p, P, 0, fa, fb, Mo, t);
+        if (own) fiber_contract2<T, MAXP>(bufA, p, P, 0, fa0, fb0, fa1, fb1, two, Mo, t0, t1);
         // this child's contribution, unpadded, in bufB (free since the second contraction)
         if (own) {
 #pragma unroll
             for (int j = 0; j < MAXP; ++j)
-                if (j < p) bufB[(j * p + fa) * p + fb] = t[j];
+                if (j < p) {
+                    bufB[(j * p + fa0) * p + fb0] = t0[j];
+                    if (two) bufB[(j * p + fa1) * p + fb1] = t1[j];
+                }
         }
         cl.sync();
         T* out = proxy + ((size_t)Pb * drho + a) * p3;

@@ -126,6 +126,80 @@ __global__ void __launch_bounds__(MAXP <= 24 ? (MAXP * MAXP + 31) / 32 * 32 : 51
     }
 }
 
+// Anterpolation with two (j2, j3) pairs per thread, (j2, j3) and (j2 + ceil(p/2), j3), which
+// share the z row value and every x row load: 40 FMA per source for 3 + MAXP/4 shared-memory
+// loads.  Threads: ceil(p/2) p.
+template <class T, int MAXP>
+__global__ void __launch_bounds__((MAXP / 2 * MAXP + 31) / 32 * 32, sizeof(T) == 4 ? 2 : 1)
+    k_anterp2(int nleaf, const int* __restrict__ leaves, BoxArrays B, const double* __restrict__ xs, int64_t N,
+              const double* __restrict__ rs, Tab<T> tab, double s, T* __restrict__ proxy) {
+    static_assert(MAXP % 4 == 0, "rows are read as four-vectors");
+    const int p = tab.p, p2 = p * p, drho = tab.d_rho, hq = (p + 1) / 2;
+    constexpr int PC = kAnterpChunk;
+    T* lx = reinterpret_cast<T*>(dsmem);
+    T* ly = lx + PC * MAXP;
+    T* lz = ly + PC * MAXP;
+    const int q = threadIdx.x;
+    const bool active = q < hq * p;
+    const int jb = active ? q / p : 0, jc = active ? q % p : 0;
+    const bool second = active && jb + hq < p;
+    for (int li = blockIdx.x; li < nleaf; li += gridDim.x) {
+        const int box = leaves[li];
+        const int l = B.level[box];
+        const double r = s / (double)(1 << l), half = 0.5 * r;
+        const double c[3] = {(B.ix[3 * box] + 0.5) * r, (B.ix[3 * box + 1] + 0.5) * r, (B.ix[3 * box + 2] + 0.5) * r};
+        const int st = B.start[box], en = B.end[box];
+        for (int a = 0; a < drho; ++a) {
+            T acc[MAXP], acc2[MAXP];
+#pragma unroll
+            for (int j = 0; j < MAXP; ++j) { acc[j] = 0; acc2[j] = 0; }
+            for (int s0 = st; s0 < en; s0 += PC) {
+                const int ns = min(PC, en - s0);
+                __syncthreads();
+                for (int u = threadIdx.x; u < 3 * ns; u += blockDim.x) {
+                    const int ax = u / ns, pt = u - ax * ns;
+                    const double xi = (xs[ax * N + s0 + pt] - c[ax]) / half;
+                    T* row = (ax == 0 ? lx : (ax == 1 ? ly : lz)) + pt * MAXP;
+                    const T wgt = (ax == 0) ? (T)rs[(int64_t)(s0 + pt) * drho + a] : T(1);
+                    lagrange_row_padded<T>((T)xi, tab.nodes, tab.bary, p, MAXP, wgt, row);
+                }
+                __syncthreads();
+                if (active) {
+                    for (int pt = 0; pt < ns; ++pt) {
+                        const T z = lz[pt * MAXP + jc];
+                        const T t = ly[pt * MAXP + jb] * z;
+                        const T t2 = second ? ly[pt * MAXP + jb + hq] * z : T(0);
+                        const Quad<T>* rx = reinterpret_cast<const Quad<T>*>(lx + pt * MAXP);
+#pragma unroll
+                        for (int k = 0; k < MAXP / 4; ++k) {
+                            const Quad<T> v = rx[k];
+                            acc[4 * k] = fma(v.x, t, acc[4 * k]);
+                            acc[4 * k + 1] = fma(v.y, t, acc[4 * k + 1]);
+                            acc[4 * k + 2] = fma(v.z, t, acc[4 * k + 2]);
+                            acc[4 * k + 3] = fma(v.w, t, acc[4 * k + 3]);
+                            acc2[4 * k] = fma(v.x, t2, acc2[4 * k]);
+                            acc2[4 * k + 1] = fma(v.y, t2, acc2[4 * k + 1]);
+                            acc2[4 * k + 2] = fma(v.z, t2, acc2[4 * k + 2]);
+                            acc2[4 * k + 3] = fma(v.w, t2, acc2[4 * k + 3]);
+                        }
+                    }
+                }
+            }
+            if (active) {
+                T* out = proxy + ((size_t)box * drho + a) * p * p2;
+                const int pair = jb * p + jc, pair2 = (jb + hq) * p + jc;
+#pragma unroll
+                for (int j = 0; j < MAXP; ++j)
+                    if (j < p) {
+                        out[j * p2 + pair] = acc[j];
+                        if (second) out[j * p2 + pair2] = acc2[j];
+                    }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // Upward pass child -> parent (Sec. 3.1.2): parent += sum_children (I^T x I^T x I^T) child,
 // I[o][j_child][a_parent] = l_a(child node j in parent coordinates).
