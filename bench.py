@@ -30,6 +30,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, HERE)
 
 WORKLOAD = dict(kernel="laplace", D=2, L=[1.0, 1.0, 0.25], tol=1e-6, N=100_000, n_s=250)
+STAGES = ["tree", "upward", "root", "planewave", "shift", "leaf", "total", "leaf_pair"]
 METRIC = "targets/s at 1e-5 rel-L2, FP32+forces vs plain FP64 GPU; P2P Gpairs/s"
 CONFIG = {"workload": "Laplace potential+forces, D=2 (x,y periodic), L=(1,1,0.25), N=1e5 uniform, "
                       "neutral uniform charges, tol 1e-6 (p=20, NF=27), n_s=250",
@@ -194,7 +195,7 @@ def extra_configs(dmk, Wl, dev, stream, steps=3, warmup=2):
             plan.set_timing(False)
             out.append({"workload": name, "N": N, "ms_per_step": t, "targets_per_s": N / (t / 1e3),
                         "p": st["p"], "n_boxes": st["n_boxes"], "n_levels": st["n_levels"], "pairs": st["n_pairs"],
-                        "stage_ms": dict(zip(["tree", "upward", "root", "planewave", "shift", "leaf", "total"],
+                        "stage_ms": dict(zip(STAGES,
                                              [round(v, 3) for v in stage])),
                         "steps": steps, "warmup": warmup})
             if kernel != "laplace-autograd":
@@ -309,28 +310,34 @@ def main():
     e2e_ms = agg(statistics.mean(ms_e2e))
     value = world * N / (step_ms / 1e3)
     st = mixed["stats"]
-    # leaf kernel share: timed with per-stage events in a separate pass
+    # leaf kernels: timed with per-stage events in a separate pass (stage 7 = the residual
+    # kernel k_pair, stage 5 = k_pair + k_leafexp)
     leaf_ms = mixed["stage"][5]
+    pair_ms = mixed["stage"][7]
     pairs = st["n_pairs"]
-    gpairs = pairs / (leaf_ms / 1e3) / 1e9 if leaf_ms > 0 else None
-    # roofline of the leaf kernel (FP32 ALU bound): algorithmic FLOPs per launch
-    # = pairs * F_pair + N * F_cheb, F_pair and F_cheb derived in the design notes
-    from paper_2606_27134_b300.roofline import leaf_flops, fp32_peak_tflops, LEAF_TRAFFIC_BYTES
-    flops = leaf_flops("laplace", st, N, grad=True, precision="mixed")
+    gpairs = pairs / (pair_ms / 1e3) / 1e9 if pair_ms > 0 else None
+    # roofline of the dominant kernel, k_pair (FP32 ALU bound): algorithmic FLOPs per launch
+    # = visited pairs * F_pair, F_pair derived in the design notes
+    from paper_2606_27134_b300.roofline import pair_flops, leafexp_flops, fp32_peak_tflops, PAIR_TRAFFIC_BYTES
+    flops = pair_flops("laplace", st, grad=True)
     pk = fp32_peak_tflops()
-    achieved = flops / (leaf_ms / 1e3) / 1e12 if leaf_ms > 0 else None
-    roof = {"bound": "alu", "kernel": "k_leaf3<float, Laplace, grad>", "achieved": achieved, "peak": pk,
-            "unit": "TFLOP/s", "frac": (achieved / pk) if achieved else None, "traffic": LEAF_TRAFFIC_BYTES,
+    achieved = flops / (pair_ms / 1e3) / 1e12 if pair_ms > 0 else None
+    exp_ms = leaf_ms - pair_ms
+    exp_tf = leafexp_flops(st, N, grad=True) / (exp_ms / 1e3) / 1e12 if exp_ms > 0 else None
+    roof = {"bound": "alu", "kernel": "k_pair<float, Laplace, grad>", "achieved": achieved, "peak": pk,
+            "unit": "TFLOP/s", "frac": (achieved / pk) if achieved else None, "traffic": PAIR_TRAFFIC_BYTES,
             "peak_note": "FP32 FMA pipe: 148 SMs x 128 lanes x 2 flop x 2.032 GHz (derived from unit counts and "
-                         "the maximum SM clock; no measured FP32 peak in MEASURED_PEAKS.json)"}
+                         "the maximum SM clock; no measured FP32 peak in MEASURED_PEAKS.json)",
+            "second_kernel": {"kernel": "k_leafexp<float, Laplace, grad>", "ms": exp_ms, "achieved": exp_tf,
+                              "frac": (exp_tf / pk) if exp_tf else None}}
     line = {"metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": dict(CONFIG, parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
             "fp64_path": {"value": world * N / (fp64_ms / 1e3), "unit": "targets/s", "ms_per_step": fp64_ms},
             "mixed_over_fp64": fp64_ms / step_ms,
-            "p2p": {"gpairs_per_s": gpairs, "pairs_per_step": pairs, "leaf_kernel_ms": leaf_ms},
-            "stage_ms": dict(zip(["tree", "upward", "root", "planewave", "shift", "leaf", "total"], mixed["stage"])),
+            "p2p": {"gpairs_per_s": gpairs, "pairs_per_step": pairs, "pair_kernel_ms": pair_ms, "leaf_stage_ms": leaf_ms},
+            "stage_ms": dict(zip(STAGES, mixed["stage"])),
             "tree": {k: st[k] for k in ("n_levels", "n_boxes", "n_leaves", "n_nonleaf", "n_direct_entries")},
             "roofline": roof,
             "clocks": mixed["clocks"],

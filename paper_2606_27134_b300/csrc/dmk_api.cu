@@ -9,6 +9,7 @@
 #include <functional>
 #include <mutex>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -64,7 +65,16 @@ struct dmk_plan_s {
     // workspace
     std::vector<DevBuf> bufs;
     unsigned char* h_meta = nullptr;   // pinned host staging for the small per-evaluation readbacks
-    cudaEvent_t ev[8] = {};
+    cudaEvent_t ev[10] = {};
+    // residual sums (k_pair) run on their own stream beside the far field when pair_overlap is
+    // set, at most pair_blocks resident blocks per SM (0: as many as fit)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int pair_overlap = 1;
+    int pair_blocks = 2;
+    int n_sm = 148;
+    // resident blocks per SM of the persistent kernels, by kernel
+    std::unordered_map<const void*, int> occ;
     int launches = 0;
     // set only while dmk_eval_static runs: device buffers are carved from this range
     unsigned char* arena = nullptr;
@@ -95,7 +105,7 @@ namespace {
 
 enum BufId {
     B_W, B_KEYS, B_KEYS2, B_IDX, B_IDX2, B_XS, B_RS, B_CUB, B_FLAGS, B_CNT,
-    B_CELLS, B_R, B_CAND, B_BOXU64, B_BOXINT, B_LEAVES, B_DOFFS, B_DL, B_NLBOX,
+    B_CELLS, B_R, B_CAND, B_BOXU64, B_BOXINT, B_LEAVES, B_DOFFS, B_DL, B_NLBOX, B_TASKS,
     B_PROXY, B_LOCAL, B_PW, B_SCRATCH, B_CHI, B_UHAT, B_MISC, B_DEVPTS, B_DEVRHO, B_DEVPOT, B_DEVGRAD, B_XF, B_VW, B_PART,
     B_COUNT
 };
@@ -376,24 +386,50 @@ dmk_status_t launch_anterp2(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int*
     return DMK_OK;
 }
 
+// resident blocks per SM of a kernel at a block size and dynamic shared memory (cached per plan)
+template <class Kern>
+dmk_status_t resident_blocks(dmk_plan_s* plan, Kern kernel, int threads, size_t smem, int* out) {
+    auto it = plan->occ.find((const void*)kernel);
+    if (it != plan->occ.end()) { *out = it->second; return DMK_OK; }
+    int n = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem));
+    plan->occ[(const void*)kernel] = *out = std::max(1, n);
+    return DMK_OK;
+}
+
+// residual sums (k_pair, persistent: every resident block takes tasks from the counter) on
+// stream sp
+template <class T, int K, bool G>
+dmk_status_t launch_pair(dmk_plan_s* plan, Tab<T>& tab, const int* leaves, BoxArrays B, const double* xs, int64_t N,
+                         const int* doffs, const DirectEntry* dl, LeafOut lo, const int* toffs, int tcap,
+                         const int4* tasks, int* next, cudaStream_t sp) {
+    constexpr int DR = Pair<T, K, G>::DR;
+    const size_t sm = pair_smem<T, DR>();
+    CKS(set_smem(plan, k_pair<T, K, G>, sm));
+    int per_sm = 1;
+    CKS(resident_blocks(plan, k_pair<T, K, G>, kPairWarps * 32, sm, &per_sm));
+    if (plan->pair_overlap && plan->pair_blocks > 0) per_sm = std::min(per_sm, plan->pair_blocks);
+    k_pair<T, K, G><<<per_sm * plan->n_sm, kPairWarps * 32, sm, sp>>>(leaves, B, tab, plan->geo, xs, N, doffs, toffs,
+                                                                      tcap, tasks, next, dl, lo);
+    return DMK_OK;
+}
+
+// leaf expansions + residual sums + self terms (k_leafexp)
+template <class T, int K, bool G>
+dmk_status_t launch_leafexp(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int* leaves, BoxArrays B, const T* local,
+                            const double* xs, int64_t N, LeafOut lo) {
+    const size_t se = leafexp_smem<T>(tab.p);
+    CKS(set_smem(plan, k_leafexp<T, K, G>, se));
+    const unsigned grid = (unsigned)std::max(1, std::min(nleaf, 148 * 16));
+    k_leafexp<T, K, G><<<grid, kLeafExpThreads, se, plan->stream>>>(nleaf, leaves, B, tab, plan->geo, local, xs, N, lo);
+    return DMK_OK;
+}
+
 template <class T, int K>
 dmk_status_t launch_leaf(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int* leaves, BoxArrays B, const T* local,
                          const double* xs, int64_t N, const int* doffs, const DirectEntry* dl, LeafOut lo, bool grad) {
     constexpr int DR = (K == DMK_LAPLACE) ? 1 : (K == DMK_STRESSLET ? 9 : 3);
     const unsigned grid = (unsigned)std::max(1, std::min(nleaf, 148 * 16));
-    if (tab.p <= kMaxPFast) {
-        const size_t dyn3 = leaf3_smem<T, DR>(tab.p);
-        if (grad) {
-            CKS(set_smem(plan, k_leaf3<T, K, true>, dyn3));
-            k_leaf3<T, K, true><<<grid, kLeaf3Threads, dyn3, plan->stream>>>(nleaf, leaves, B, tab, plan->geo, local,
-                                                                            xs, N, doffs, dl, lo);
-        } else {
-            CKS(set_smem(plan, k_leaf3<T, K, false>, dyn3));
-            k_leaf3<T, K, false><<<grid, kLeaf3Threads, dyn3, plan->stream>>>(nleaf, leaves, B, tab, plan->geo, local,
-                                                                             xs, N, doffs, dl, lo);
-        }
-        return DMK_OK;
-    }
     const size_t dyn = (size_t)kSrcChunk * kLeaf2Threads + (size_t)kSrcChunk * DR * sizeof(T);
     if (grad) {
         CKS(set_smem(plan, k_leaf2<T, K, true>, dyn));
@@ -467,6 +503,8 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     int* d_err = (int*)vmisc;
     double* d_sums = (double*)((char*)vmisc + 256);          // 2*drho doubles
     unsigned long long* d_pairs = (unsigned long long*)((char*)vmisc + 768);
+    // the previous evaluation's residual kernel (side stream) is done with the workspace
+    CK(cudaStreamWaitEvent(st, plan->ev_join, 0));
     CK(cudaMemsetAsync(vmisc, 0, 2048, st));
     uint64_t* keys = (uint64_t*)vkeys;
     uint64_t* keys2 = (uint64_t*)vkeys2;
@@ -498,6 +536,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     int* d_nR = (int*)((char*)vmisc + 1024);       // non-leaf count per level
     int* d_missing = (int*)((char*)vmisc + 1280);  // balance check, per level
     int* d_nleaf = (int*)((char*)vmisc + 1536);
+    int* d_next = (int*)((char*)vmisc + 2040);     // residual-task counter of k_pair
     // cells with more than n_s points are disjoint: at most N/(n_s+1) split per level
     const int64_t cap = std::max<int64_t>(1, N / ((int64_t)plan->n_s + 1));
     const int nblkR = (int)((N + kRefineThreads - 1) / kRefineThreads);
@@ -676,18 +715,20 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         CK(cub::DeviceSelect::Flagged(vcub, tb, (int*)viota, (int*)vflags, leaves, d_nleaf, nb, st));
         launches += 2;
     }
-    // direct lists: counts for every possible leaf slot, scan, one readback of the totals
-    void *vdo, *vdl;
-    CKS(ensure(plan, B_DOFFS, (size_t)(nb + 1) * sizeof(int), &vdo));
+    // direct lists and residual tasks: counts for every possible leaf slot (entries in the
+    // first nb + 1 ints, tasks in the next nb + 1), one scan over both, one readback of the totals
+    void *vdo, *vdl, *vtk;
+    CKS(ensure(plan, B_DOFFS, 2 * (size_t)(nb + 1) * sizeof(int), &vdo));
     int* doffs = (int*)vdo;
-    CK(cudaMemsetAsync(doffs, 0, (nb + 1) * sizeof(int), st));
+    int* toffs = doffs + nb + 1;
+    CK(cudaMemsetAsync(doffs, 0, 2 * (size_t)(nb + 1) * sizeof(int), st));
     k_direct<false><<<nblk((int64_t)32 * nb, 128), 128, 0, st>>>(nb, d_nleaf, leaves, B, g, doffs, nullptr, nullptr,
-                                                                 d_pairs);
+                                                                 d_pairs, nb + 1, nullptr);
     {
         size_t tb = 0;
-        cub::DeviceScan::ExclusiveSum(nullptr, tb, doffs, doffs, nb + 1, st);
+        cub::DeviceScan::ExclusiveSum(nullptr, tb, doffs, doffs, 2 * (nb + 1), st);
         if (tb > cub_cap) { CKS(ensure(plan, B_CUB, tb, &vcub)); cub_cap = plan->bufs[B_CUB].cap; }
-        CK(cub::DeviceScan::ExclusiveSum(vcub, tb, doffs, doffs, nb + 1, st));
+        CK(cub::DeviceScan::ExclusiveSum(vcub, tb, doffs, doffs, 2 * (nb + 1), st));
         // pinned readback: misc + 768 .. + 1540 holds the pair count and the leaf count
         CK(cudaMemcpyAsync(plan->h_meta, (char*)vmisc + 768, 772, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(plan->h_meta + 1024, doffs + nb, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -702,10 +743,46 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     const int nleaf = ti.n_leafp;
     CKS(ensure(plan, B_DL, (size_t)std::max<int64_t>(ti.n_entries, 1) * sizeof(DirectEntry), &vdl));
     DirectEntry* dl = (DirectEntry*)vdl;
+    // at most nt/32 + 5 tasks per leaf
+    CKS(ensure(plan, B_TASKS, ((size_t)N / 32 + 5 * (size_t)nleaf + 1) * sizeof(int4), &vtk));
+    int4* tasks = (int4*)vtk;
     k_direct<true><<<nblk((int64_t)32 * nleaf, 128), 128, 0, st>>>(nleaf, d_nleaf, leaves, B, g, nullptr, doffs, dl,
-                                                                   nullptr);
+                                                                   nullptr, nb + 1, tasks);
     ++launches;
     rec(1);
+    // ---- leaf residual sums: they need only the tree, so with pair_overlap they run on the
+    // side stream beside the far field (steps 5-8) and are joined before the leaf expansions
+    LeafOut lo;
+    lo.pot = pot;
+    lo.grad = grad;
+    lo.perm = idx2;
+    lo.rs = rs;
+    lo.self_val = plan->d_self;
+    lo.self_grad = plan->d_self + P.d_u * P.d_rho;
+    lo.xh = xh;
+    lo.xl = xl;
+    lo.rsf = rsf;
+    const bool gr = grad != nullptr;
+    const bool fast_leaf = nleaf > 0 && p <= kMaxPFast;
+    auto run_pair = [&](cudaStream_t sp) -> dmk_status_t {
+        if (plan->timing) cudaEventRecord(plan->ev[8], sp);
+        switch (P.kernel) {
+            case DMK_LAPLACE: CKS((gr ? launch_pair<T, DMK_LAPLACE, true> : launch_pair<T, DMK_LAPLACE, false>)(plan, tab, leaves, B, xs, N, doffs, dl, lo, toffs, nb, tasks, d_next, sp)); break;
+            case DMK_STOKESLET: CKS((gr ? launch_pair<T, DMK_STOKESLET, true> : launch_pair<T, DMK_STOKESLET, false>)(plan, tab, leaves, B, xs, N, doffs, dl, lo, toffs, nb, tasks, d_next, sp)); break;
+            case DMK_STRESSLET: CKS((gr ? launch_pair<T, DMK_STRESSLET, true> : launch_pair<T, DMK_STRESSLET, false>)(plan, tab, leaves, B, xs, N, doffs, dl, lo, toffs, nb, tasks, d_next, sp)); break;
+            default: CKS((gr ? launch_pair<T, DMK_ROTLET, true> : launch_pair<T, DMK_ROTLET, false>)(plan, tab, leaves, B, xs, N, doffs, dl, lo, toffs, nb, tasks, d_next, sp)); break;
+        }
+        if (plan->timing) cudaEventRecord(plan->ev[9], sp);
+        ++launches;
+        return DMK_OK;
+    };
+    const bool overlap = fast_leaf && plan->pair_overlap;
+    if (overlap) {
+        CK(cudaEventRecord(plan->ev_fork, st));
+        CK(cudaStreamWaitEvent(plan->side, plan->ev_fork, 0));
+        CKS(run_pair(plan->side));
+        CK(cudaEventRecord(plan->ev_join, plan->side));
+    }
     // ---- (5) upward pass ---------------------------------------------------------------
     void *vpr, *vloc;
     CKS(ensure(plan, B_PROXY, (size_t)nb * drho * p3 * sizeof(T), &vpr));
@@ -923,18 +1000,17 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     }
     rec(6);
     // ---- (9) leaf stage -----------------------------------------------------------------
-    if (nleaf > 0) {
-        LeafOut lo;
-        lo.pot = pot;
-        lo.grad = grad;
-        lo.perm = idx2;
-        lo.rs = rs;
-        lo.self_val = plan->d_self;
-        lo.self_grad = plan->d_self + P.d_u * P.d_rho;
-        lo.xh = xh;
-        lo.xl = xl;
-        lo.rsf = rsf;
-        const bool gr = grad != nullptr;
+    if (fast_leaf) {
+        if (overlap) CK(cudaStreamWaitEvent(st, plan->ev_join, 0));
+        else CKS(run_pair(st));
+        switch (P.kernel) {
+            case DMK_LAPLACE: CKS((gr ? launch_leafexp<T, DMK_LAPLACE, true> : launch_leafexp<T, DMK_LAPLACE, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo)); break;
+            case DMK_STOKESLET: CKS((gr ? launch_leafexp<T, DMK_STOKESLET, true> : launch_leafexp<T, DMK_STOKESLET, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo)); break;
+            case DMK_STRESSLET: CKS((gr ? launch_leafexp<T, DMK_STRESSLET, true> : launch_leafexp<T, DMK_STRESSLET, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo)); break;
+            default: CKS((gr ? launch_leafexp<T, DMK_ROTLET, true> : launch_leafexp<T, DMK_ROTLET, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo)); break;
+        }
+        ++launches;
+    } else if (nleaf > 0) {
         switch (P.kernel) {
             case DMK_LAPLACE: CKS((launch_leaf<T, DMK_LAPLACE>(plan, tab, nleaf, leaves, B, local, xs, N, doffs, dl, lo, gr))); break;
             case DMK_STOKESLET: CKS((launch_leaf<T, DMK_STOKESLET>(plan, tab, nleaf, leaves, B, local, xs, N, doffs, dl, lo, gr))); break;
@@ -975,9 +1051,11 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     S.fit_terms = tab.n_q;
     if (plan->timing) {
         float ms;
-        const int map[7][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 5}, {5, 6}, {6, 7}, {0, 7}};
-        for (int i = 0; i < 7; ++i) {
-            cudaEventElapsedTime(&ms, plan->ev[map[i][0]], plan->ev[map[i][1]]);
+        // stage 7: the residual kernel alone (on the side stream when it overlaps the far field)
+        const int map[8][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 5}, {5, 6}, {6, 7}, {0, 7}, {8, 9}};
+        for (int i = 0; i < 8; ++i) {
+            ms = 0;
+            if (i < 7 || fast_leaf) cudaEventElapsedTime(&ms, plan->ev[map[i][0]], plan->ev[map[i][1]]);
             S.stage_ms[i] = ms;
         }
     }
@@ -1009,6 +1087,7 @@ dmk_status_t make_plan(int k, int D, const double L[3], double tol, int prec, in
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
     plan->smem_optin = (size_t)optin;
+    cudaDeviceGetAttribute(&plan->n_sm, cudaDevAttrMultiProcessorCount, plan->device);
     if ((s = upload_tab<double>(plan, &plan->d_tab64, plan->tab64, 1e-17)) != DMK_OK ||
         (s = upload_tab<float>(plan, &plan->d_tab32, plan->tab32, 1e-9)) != DMK_OK || (s = upload_root(plan)) != DMK_OK) {
         g_plan_error = plan->err;
@@ -1022,7 +1101,16 @@ dmk_status_t make_plan(int k, int D, const double L[3], double tol, int prec, in
         dmk_destroy(plan);
         return DMK_ERR_OOM;
     }
-    for (int i = 0; i < 8; ++i) cudaEventCreate(&plan->ev[i]);
+    for (int i = 0; i < 10; ++i) cudaEventCreate(&plan->ev[i]);
+    if (cudaStreamCreateWithFlags(&plan->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        g_plan_error = "stream or event creation failed";
+        dmk_destroy(plan);
+        return DMK_ERR_CUDA;
+    }
+    if (const char* v = std::getenv("DMK_PAIR_OVERLAP")) plan->pair_overlap = std::atoi(v) != 0;
+    if (const char* v = std::getenv("DMK_PAIR_BLOCKS")) plan->pair_blocks = std::max(0, std::atoi(v));
     *out = plan;
     return DMK_OK;
 }
@@ -1139,7 +1227,13 @@ dmk_status_t dmk_destroy(dmk_plan_t plan) {
     if (plan->d_tab32) cudaFree(plan->d_tab32);
     if (plan->d_root) cudaFree(plan->d_root);
     if (plan->d_self) cudaFree(plan->d_self);
-    for (int i = 0; i < 8; ++i)
+    if (plan->side) {
+        cudaStreamSynchronize(plan->side);
+        cudaStreamDestroy(plan->side);
+    }
+    if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
+    if (plan->ev_join) cudaEventDestroy(plan->ev_join);
+    for (int i = 0; i < 10; ++i)
         if (plan->ev[i]) cudaEventDestroy(plan->ev[i]);
     if (plan->h_meta) cudaFreeHost(plan->h_meta);
     delete plan;

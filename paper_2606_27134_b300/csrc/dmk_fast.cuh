@@ -660,15 +660,7 @@ __global__ void __launch_bounds__(384) k_pwin3(int n, const int* __restrict__ nl
 namespace dmk {
 
 // ------------------------------------------------------------------------------------------
-// Leaf stage for p <= kMaxPFast (Sec. 3.1.5, Sec. 2.4), one thread per target throughout.
-// (2) the leaf's Chebyshev coefficients c[n1][n2][n3] (x, y, z) are staged in shared memory with
-//     the n3 rows padded to a multiple of four; each thread keeps T_n3(z), T'_n3(z) in registers,
-//     runs the y and x recurrences on the fly, and reads coefficient rows as broadcast vectors;
-// (3) residual sums: sources stream through shared memory in chunks of kSrcChunk as
-//     (x, y, z, nu^2) and (x_lo, y_lo, z_lo, 1/nu) vectors; the support test r^2 < nu^2 on the
-//     leading parts fills a per-thread byte queue, and only queued sources are evaluated, with
-//     two-float differences in the FP32 path and r > 0 excluding the target itself;
-// (4) self correction and the FP64 write-back in input order.
+// Helpers of the leaf stage for p <= kMaxPFast (k_pair, k_leafexp below).
 // (a_h + a_l) + (b_h + b_l) as an unnormalised FP32 pair: the leading sum with its exact
 // rounding error (Knuth's TwoSum), plus the trailing parts.  Accurate to about 2^-48 of the
 // operands' magnitude.
@@ -753,35 +745,68 @@ __device__ __forceinline__ void cheb_eval(const T* cs, int p, int ng, const T (&
     }
 }
 
-constexpr int kLeaf3Threads = 128;
+// ------------------------------------------------------------------------------------------
+// Leaf stage for p <= kMaxPFast in two launches.
+//
+// k_pair: the residual sums (Sec. 2.4 and the direct interactions of Sec. 3.1.5) as
+// independent warp tasks.  A task is a tile of m consecutive targets of one leaf: m = 32 for
+// the full tiles and, for the nt mod 32 remaining targets, one tile per set bit of that
+// remainder (m = 16, 8, 4, 2, 1), so that every lane of every task has a target.  In a tile of
+// m < 32 targets lane = s m + i holds target i and takes every S-th source pair (S = 32/m,
+// split s) of each chunk; the S partial sums are combined by a fixed xor-shuffle tree.  Warps
+// take tasks from a device counter and stage their own chunks of kPairChunk sources, so no
+// barrier couples the warps of a block.  A chunk holds (x, y, z, nu^2) and (x_lo, y_lo, z_lo,
+// 1/nu) per source (source offsets from the target leaf's centre, FP32 leading and trailing
+// parts in the FP32 path).  Per chunk: support test |x_t sigma - x_s/nu| < 1 (half precision on
+// source pairs in the FP32 path, FP64 r^2 < nu^2 in the FP64 path) into bit masks, in-support
+// sources appended to a per-lane byte queue, queued pairs evaluated with two-float differences
+// and the cubic residual tables (r > 0 excludes the target itself), FP32 sums folded into FP64
+// per chunk.  The result K * sum is written to the output in input order.  The kernel needs
+// only the tree, so it may run beside the far field on another stream.
+//
+// k_leafexp: thread per target.  The leaf's Chebyshev coefficients c[n1][n2][n3] (x, y, z) are
+// staged in shared memory with the n3 rows padded to a multiple of four; each thread keeps
+// T_n3(z), T'_n3(z) in registers, runs the y and x recurrences on the fly and reads coefficient
+// rows as broadcast vectors (Sec. 3.1.5).  The expansion is added to the residual sums written
+// by k_pair, the self term (Sec. 2.4) subtracted, and the result written in FP64.
+constexpr int kPairWarps = 4;
+constexpr int kPairChunk = 128;
+
+// byte offsets within one warp's shared-memory region of k_pair
+template <class T, int DR>
+struct PairSmem {
+    static constexpr bool kTwo = sizeof(T) == 4;
+    static constexpr size_t a = 0;                                                    // Quad<T> [C]
+    static constexpr size_t b = a + kPairChunk * sizeof(Quad<T>);                     // Quad<T> [C]
+    static constexpr size_t t = b + kPairChunk * sizeof(Quad<T>);                     // Quad<half2> [C/2]
+    static constexpr size_t r = t + (kTwo ? kPairChunk / 2 * sizeof(Quad<__half2>) : 0);   // T [C][DR]
+    static constexpr size_t q = (r + kPairChunk * DR * sizeof(T) + 15) & ~(size_t)15;     // u8 [C][32]
+    static constexpr size_t bytes = q + kPairChunk * 32;
+};
 
 template <class T, int K, bool GRAD>
-__global__ void __launch_bounds__(kLeaf3Threads) k_leaf3(int nleaf, const int* __restrict__ leaves, BoxArrays B,
-                                                        Tab<T> tab, Geo g, const T* __restrict__ coef,
-                                                        const double* __restrict__ xs, int64_t N,
-                                                        const int* __restrict__ doffs,
-                                                        const DirectEntry* __restrict__ dl, LeafOut out) {
+__global__ void __launch_bounds__(kPairWarps * 32, 4) k_pair(const int* __restrict__ leaves, BoxArrays B, Tab<T> tab,
+                                                            Geo g, const double* __restrict__ xs, int64_t N,
+                                                            const int* __restrict__ doffs,
+                                                            const int* __restrict__ toffs, int tcap,
+                                                            const int4* __restrict__ tasks, int* __restrict__ next,
+                                                            const DirectEntry* __restrict__ dl, LeafOut out) {
     using Pr = Pair<T, K, GRAD>;
     using Q4 = Quad<T>;
-    constexpr int DR = Pr::DR, DU = Pr::DU, MQ = kMaxPFast / 4;
+    constexpr int DR = Pr::DR, DU = Pr::DU, C = kPairChunk;
     constexpr bool kTwo = sizeof(T) == 4;
-    const int p = tab.p, p2 = p * p, p3 = p2 * p, PQ = (p + 3) & ~3, ng = PQ >> 2;
-    __shared__ Q4 sA[kSrcChunk];   // source offset from the leaf centre (leading part), nu^2
-    __shared__ Q4 sB[kSrcChunk];   // trailing parts (FP32 path), 1/nu
-    // FP32 path: the support test in half precision on source pairs: -offset/nu (x, y, z) and
-    // sigma = r_T/nu, so that |x_t sigma - x_s/nu|^2 < 1 (x_t in units of the leaf side r_T)
-    __shared__ Quad<__half2> sT[kTwo ? kSrcChunk / 2 : 1];
-    __shared__ T fits[kTwo ? 1 : 256];
-    // FP32 path: the piecewise cubic series tables this kernel uses (q, f[, g][, q', f'[, g']])
+    using WS = PairSmem<T, DR>;
     constexpr int NSER = (K == DMK_STRESSLET) ? (GRAD ? 6 : 3) : ((GRAD && K != DMK_LAPLACE) ? 5 : 2);
     __shared__ Quad<float> herm[kTwo ? NSER * kHermNT : 1];
-    // dynamic: the byte queue q[kSrcChunk][threads], aliased by the coefficient block during
-    // step (2); then the staged strengths
-    extern __shared__ __align__(32) unsigned char dsm3[];
-    const size_t qbytes = max((size_t)kSrcChunk * kLeaf3Threads, (size_t)p2 * PQ * sizeof(T));
-    unsigned char (*q)[kLeaf3Threads] = reinterpret_cast<unsigned char (*)[kLeaf3Threads]>(dsm3);
-    T* cs = reinterpret_cast<T*>(dsm3);
-    T (*sr)[DR] = reinterpret_cast<T (*)[DR]>(dsm3 + ((qbytes + 15) & ~(size_t)15));
+    __shared__ T fits[kTwo ? 1 : 256];
+    extern __shared__ __align__(16) unsigned char dsmp[];
+    const int lane = threadIdx.x & 31;
+    unsigned char* wsm = dsmp + (threadIdx.x >> 5) * WS::bytes;
+    Q4* sA = reinterpret_cast<Q4*>(wsm + WS::a);
+    Q4* sB = reinterpret_cast<Q4*>(wsm + WS::b);
+    Quad<__half2>* sT = reinterpret_cast<Quad<__half2>*>(wsm + WS::t);
+    T (*sr)[DR] = reinterpret_cast<T (*)[DR]>(wsm + WS::r);
+    unsigned char (*q)[32] = reinterpret_cast<unsigned char (*)[32]>(wsm + WS::q);
     if constexpr (kTwo) {
         const Quad<float>* hsrc = reinterpret_cast<const Quad<float>*>(tab.herm);
         for (int e = threadIdx.x; e < NSER * kHermNT; e += blockDim.x) herm[e] = hsrc[e];
@@ -790,257 +815,305 @@ __global__ void __launch_bounds__(kLeaf3Threads) k_leaf3(int nleaf, const int* _
              e += blockDim.x)
             fits[e] = tab.fit[e];
     }
-    const int tt = threadIdx.x;
-    // per-level scales by exact power-of-two scaling of per-launch constants (no FP64 division
-    // in the loops); FP32 path: leading/trailing FP32 parts of the periods
+    __syncthreads();
+    const int ntask = toffs[tcap] - toffs[0];
     const double inv_s = 1.0 / g.s, s2 = g.s * g.s;
     const float inv_s_f = (float)inv_s, s2_f = (float)s2;
     float Lh[3], Ll[3];
     for (int a = 0; a < 3; ++a) split_double(g.L[a], Lh[a], Ll[a]);
+    while (true) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(next, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= ntask) break;
+        const int4 tk = tasks[t];
+        const int li = tk.x, m = tk.z;
+        const int lgm = __ffs(m) - 1;
+        const int ti = lane & (m - 1), s = lane >> lgm, S = 32 >> lgm;
+        const int box = leaves[li];
+        const int l = B.level[box];
+        const double r = ldexp(g.s, -l);
+        const double c[3] = {(B.ix[3 * box] + 0.5) * r, (B.ix[3 * box + 1] + 0.5) * r, (B.ix[3 * box + 2] + 0.5) * r};
+        float ch[3], cl[3];
+        for (int a = 0; a < 3; ++a) split_double(-c[a], ch[a], cl[a]);
+        const int tg = B.start[box] + tk.y + ti;
+        T xt[3], xtl[3] = {0, 0, 0};
+        for (int a = 0; a < 3; ++a) {
+            if constexpr (kTwo) two_float_add(out.xh[a * N + tg], out.xl[a * N + tg], ch[a], cl[a], xt[a], xtl[a]);
+            else xt[a] = (T)(xs[a * N + tg] - c[a]);
+        }
+        const float inv_rT = ldexpf(inv_s_f, l);
+        __half2 xu2[3];
+        for (int a = 0; a < 3; ++a) xu2[a] = __float2half2_rn((float)(xt[a] + xtl[a]) * inv_rT);
+        double accd[DU], gaccd[3 * DU];
+#pragma unroll
+        for (int j = 0; j < DU; ++j) accd[j] = 0;
+#pragma unroll
+        for (int j = 0; j < 3 * DU; ++j) gaccd[j] = 0;
+        int e = doffs[li];
+        const int e1 = doffs[li + 1];
+        int eo = 0;
+        while (e < e1) {
+            __syncwarp();
+            int filled = 0;
+            while (filled < C && e < e1) {
+                const DirectEntry de = dl[e];
+                const int take = min(de.end - de.start - eo, C - filled);
+                const int lev = de.code >> 6;
+                const int sb[3] = {((de.code) & 3) - 1, ((de.code >> 2) & 3) - 1, ((de.code >> 4) & 3) - 1};
+                T nu2, tinv;
+                double E[3] = {0, 0, 0};
+                float Eh[3] = {0, 0, 0}, El[3] = {0, 0, 0};
+                if constexpr (kTwo) {
+                    tinv = ldexpf(inv_s_f, lev);
+                    nu2 = ldexpf(s2_f, -2 * lev);
+                    for (int a = 0; a < 3; ++a)
+                        two_float_add((float)sb[a] * Lh[a], (float)sb[a] * Ll[a], ch[a], cl[a], Eh[a], El[a]);
+                } else {
+                    tinv = (T)ldexp(inv_s, lev);
+                    nu2 = (T)ldexp(s2, -2 * lev);
+                    for (int a = 0; a < 3; ++a) E[a] = (double)sb[a] * g.L[a] - c[a];
+                }
+                for (int k = lane; k < take; k += 32) {
+                    const int si = de.start + eo + k, slot = filled + k;
+                    Q4 a, b;
+                    if constexpr (kTwo) {
+                        two_float_add(out.xh[si], out.xl[si], Eh[0], El[0], a.x, b.x);
+                        two_float_add(out.xh[N + si], out.xl[N + si], Eh[1], El[1], a.y, b.y);
+                        two_float_add(out.xh[2 * N + si], out.xl[2 * N + si], Eh[2], El[2], a.z, b.z);
+                        for (int a2 = 0; a2 < DR; ++a2) sr[slot][a2] = out.rsf[(int64_t)si * DR + a2];
+                    } else {
+                        a.x = (T)(xs[si] + E[0]);
+                        a.y = (T)(xs[N + si] + E[1]);
+                        a.z = (T)(xs[2 * N + si] + E[2]);
+                        b.x = b.y = b.z = T(0);
+                        for (int a2 = 0; a2 < DR; ++a2) sr[slot][a2] = (T)out.rs[(int64_t)si * DR + a2];
+                    }
+                    a.w = nu2;
+                    b.w = tinv;
+                    sA[slot] = a;
+                    sB[slot] = b;
+                    if constexpr (kTwo) {
+                        __half* hp = reinterpret_cast<__half*>(&sT[slot >> 1]);
+                        const int hh = slot & 1;
+                        hp[0 + hh] = __float2half_rn(-(a.x + b.x) * tinv);
+                        hp[2 + hh] = __float2half_rn(-(a.y + b.y) * tinv);
+                        hp[4 + hh] = __float2half_rn(-(a.z + b.z) * tinv);
+                        hp[6 + hh] = __float2half_rn(ldexpf(1.0f, lev - l));
+                    }
+                }
+                filled += take;
+                eo += take;
+                if (eo == de.end - de.start) { ++e; eo = 0; }
+            }
+            if constexpr (kTwo) {
+                // an odd chunk: the unused half of the last pair fails every support test
+                if ((filled & 1) && lane == 0) {
+                    __half* hp = reinterpret_cast<__half*>(&sT[filled >> 1]);
+                    hp[1] = hp[3] = hp[5] = __float2half_rn(30000.0f);
+                    hp[7] = __float2half_rn(0.0f);
+                }
+            }
+            __syncwarp();
+            // support tests into bit masks, set bits appended to the queue (column swizzled by
+            // row so that lanes with different queue lengths write to different banks)
+            int cnt = 0;
+            if constexpr (kTwo) {
+                const __half2 one2 = __float2half2_rn(1.0f);
+                const int npair = (filled + 1) >> 1;
+                const int nu = (npair - s + S - 1) / S;     // this split's pair slots s + S u
+                for (int u0 = 0; u0 < nu; u0 += 16) {
+                    const int un = min(16, nu - u0);
+                    unsigned me = 0, mo = 0;
+#pragma unroll 8
+                    for (int mm = 0; mm < 16; ++mm) {
+                        if (mm < un) {
+                            const Quad<__half2> v = sT[s + S * (u0 + mm)];
+                            const __half2 dx = __hfma2(xu2[0], v.w, v.x);
+                            const __half2 dy = __hfma2(xu2[1], v.w, v.y);
+                            const __half2 dz = __hfma2(xu2[2], v.w, v.z);
+                            const __half2 r2 = __hfma2(dx, dx, __hfma2(dy, dy, __hmul2(dz, dz)));
+                            const unsigned mk = __hlt2_mask(r2, one2);
+                            me |= (mk & 1u) << mm;
+                            mo |= ((mk >> 16) & 1u) << mm;
+                        }
+                    }
+                    while (me) {
+                        const int mm = __ffs(me) - 1;
+                        me &= me - 1;
+                        q[cnt][lane ^ ((cnt & 7) << 2)] = (unsigned char)(2 * (s + S * (u0 + mm)));
+                        ++cnt;
+                    }
+                    while (mo) {
+                        const int mm = __ffs(mo) - 1;
+                        mo &= mo - 1;
+                        q[cnt][lane ^ ((cnt & 7) << 2)] = (unsigned char)(2 * (s + S * (u0 + mm)) + 1);
+                        ++cnt;
+                    }
+                }
+            } else {
+                const int nu = (filled - s + S - 1) / S;    // this split's sources s + S u
+                for (int u0 = 0; u0 < nu; u0 += 32) {
+                    const int un = min(32, nu - u0);
+                    unsigned mask = 0;
+#pragma unroll 8
+                    for (int kk = 0; kk < 32; ++kk) {
+                        if (kk < un) {
+                            const Q4 a = sA[s + S * (u0 + kk)];
+                            const T dx = xt[0] - a.x, dy = xt[1] - a.y, dz = xt[2] - a.z;
+                            const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                            mask |= (r2 < a.w ? 1u : 0u) << kk;
+                        }
+                    }
+                    while (mask) {
+                        const int kk = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        q[cnt][lane ^ ((cnt & 7) << 2)] = (unsigned char)(s + S * (u0 + kk));
+                        ++cnt;
+                    }
+                }
+            }
+            T acc[DU], gacc[3 * DU];
+#pragma unroll
+            for (int j = 0; j < DU; ++j) acc[j] = 0;
+#pragma unroll
+            for (int j = 0; j < 3 * DU; ++j) gacc[j] = 0;
+#pragma unroll 2
+            for (int i = 0; i < cnt; ++i) {
+                const int k = q[i][lane ^ ((i & 7) << 2)];
+                const Q4 a = sA[k], b = sB[k];
+                T dx = xt[0] - a.x, dy = xt[1] - a.y, dz = xt[2] - a.z;
+                if (kTwo) {
+                    dx += xtl[0] - b.x;
+                    dy += xtl[1] - b.y;
+                    dz += xtl[2] - b.z;
+                }
+                const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                if (r2 > T(0)) {
+                    if constexpr (kTwo)
+                        Pr::eval(HermSeries(herm, r2, b.w), dx, dy, dz, r2, b.w, sr[k], acc, gacc);
+                    else
+                        Pr::eval(ChebSeries<T>(tab, fits, r2, b.w), dx, dy, dz, r2, b.w, sr[k], acc, gacc);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < DU; ++j) accd[j] += (double)acc[j];
+#pragma unroll
+            for (int j = 0; j < 3 * DU; ++j) gaccd[j] += (double)gacc[j];
+        }
+        // the S splits of a target, combined in a fixed order (every lane gets the same sum)
+        for (int o = m; o < 32; o <<= 1) {
+#pragma unroll
+            for (int j = 0; j < DU; ++j) accd[j] += __shfl_xor_sync(0xffffffffu, accd[j], o);
+#pragma unroll
+            for (int j = 0; j < 3 * DU; ++j) gaccd[j] += __shfl_xor_sync(0xffffffffu, gaccd[j], o);
+        }
+        if (s == 0) {
+            const int oi = out.perm[tg];
+            const double ks = KScale<K>::v;
+#pragma unroll
+            for (int j = 0; j < DU; ++j) out.pot[(int64_t)oi * DU + j] = ks * accd[j];
+            if (GRAD && out.grad) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < DU; ++j) out.grad[((int64_t)oi * 3 + i) * DU + j] = ks * gaccd[i * DU + j];
+            }
+        }
+    }
+}
+
+template <class T, int DR>
+inline size_t pair_smem() {
+    return (size_t)kPairWarps * PairSmem<T, DR>::bytes;
+}
+
+constexpr int kLeafExpThreads = 128;
+
+template <class T, int K, bool GRAD>
+__global__ void __launch_bounds__(kLeafExpThreads) k_leafexp(int nleaf, const int* __restrict__ leaves, BoxArrays B,
+                                                            Tab<T> tab, Geo g, const T* __restrict__ coef,
+                                                            const double* __restrict__ xs, int64_t N, LeafOut out) {
+    using Pr = Pair<T, K, GRAD>;
+    constexpr int DR = Pr::DR, DU = Pr::DU, MQ = kMaxPFast / 4;
+    constexpr bool kTwo = sizeof(T) == 4;
+    const int p = tab.p, p2 = p * p, p3 = p2 * p, PQ = (p + 3) & ~3, ng = PQ >> 2;
+    extern __shared__ __align__(16) unsigned char dsme[];
+    T* cs = reinterpret_cast<T*>(dsme);   // one output component's coefficients, rows padded to PQ
+    const int tt = threadIdx.x;
     for (int li = blockIdx.x; li < nleaf; li += gridDim.x) {
         const int box = leaves[li];
         const int l = B.level[box];
         const double r = ldexp(g.s, -l), half = 0.5 * r;
         const double c[3] = {(B.ix[3 * box] + 0.5) * r, (B.ix[3 * box + 1] + 0.5) * r, (B.ix[3 * box + 2] + 0.5) * r};
-        float ch[3], cl[3];            // FP32 parts of -centre
+        float ch[3], cl[3];
         for (int a = 0; a < 3; ++a) split_double(-c[a], ch[a], cl[a]);
         const int st = B.start[box], en = B.end[box];
-        for (int t0 = st; t0 < en; t0 += kLeaf3Threads) {
-            const int nt = min(kLeaf3Threads, en - t0);
-            const bool act = tt < nt;
-            // target offsets from the leaf centre: FP64 in the FP64 path; in the FP32 path the
-            // sum of the point's FP32 parts and the FP32 parts of -centre
-            T xt[3] = {0, 0, 0}, xtl[3] = {0, 0, 0};
+        for (int t0 = st; t0 < en; t0 += kLeafExpThreads) {
+            const bool act = tt < en - t0;
+            const int tg = t0 + tt;
+            T xi[3] = {0, 0, 0};
             if (act) {
-                const int tg = t0 + tt;
-                for (int a = 0; a < 3; ++a) {
-                    if constexpr (kTwo) {
-                        two_float_add(out.xh[a * N + tg], out.xl[a * N + tg], ch[a], cl[a], xt[a], xtl[a]);
-                    } else {
-                        xt[a] = (T)(xs[a * N + tg] - c[a]);
-                    }
-                }
-            }
-            const float inv_rT = ldexpf(inv_s_f, l);
-            __half2 xu2[3];
-            for (int a = 0; a < 3; ++a) xu2[a] = __float2half2_rn((float)(xt[a] + xtl[a]) * inv_rT);
-            // (2) Chebyshev evaluation
-            T ev[DU], eg[3 * DU];
-            {
-                T xi[3];
                 const T ih = (T)(1.0 / half);
                 for (int a = 0; a < 3; ++a) {
-                    const T v = (xt[a] + xtl[a]) * ih;
+                    T x0, x1 = 0;
+                    if constexpr (kTwo) two_float_add(out.xh[a * N + tg], out.xl[a * N + tg], ch[a], cl[a], x0, x1);
+                    else x0 = (T)(xs[a * N + tg] - c[a]);
+                    const T v = (x0 + x1) * ih;
                     xi[a] = v > T(1) ? T(1) : (v < T(-1) ? T(-1) : v);
                 }
-                T Tz[kMaxPFast], dTz[kMaxPFast];
-                {
-                    T tm2 = 0, tm1 = 1, um2 = 0, um1 = 1;   // T_{n-2}, T_{n-1}, U_{n-2}, U_{n-1}
+            }
+            T Tz[kMaxPFast], dTz[kMaxPFast];
+            {
+                T tm2 = 0, tm1 = 1, um2 = 0, um1 = 1;
 #pragma unroll
-                    for (int n = 0; n < kMaxPFast; ++n) {
-                        T tn, dn;
-                        if (n == 0) { tn = 1; dn = 0; }
-                        else if (n == 1) { tn = xi[2]; dn = 1; tm2 = 1; tm1 = xi[2]; um2 = 1; um1 = 2 * xi[2]; }
-                        else {
-                            tn = 2 * xi[2] * tm1 - tm2;
-                            dn = (T)n * um1;
-                            const T un = 2 * xi[2] * um1 - um2;
-                            tm2 = tm1; tm1 = tn; um2 = um1; um1 = un;
-                        }
-                        Tz[n] = n < p ? tn : T(0);
-                        dTz[n] = n < p ? dn : T(0);
+                for (int n = 0; n < kMaxPFast; ++n) {
+                    T tn, dn;
+                    if (n == 0) { tn = 1; dn = 0; }
+                    else if (n == 1) { tn = xi[2]; dn = 1; tm2 = 1; tm1 = xi[2]; um2 = 1; um1 = 2 * xi[2]; }
+                    else {
+                        tn = 2 * xi[2] * tm1 - tm2;
+                        dn = (T)n * um1;
+                        const T un = 2 * xi[2] * um1 - um2;
+                        tm2 = tm1; tm1 = tn; um2 = um1; um1 = un;
                     }
-                }
-#pragma unroll
-                for (int j = 0; j < DU; ++j) {
-                    __syncthreads();
-                    const T* cj = coef + ((size_t)box * DU + j) * p3;
-                    for (int e = tt; e < p2 * PQ; e += kLeaf3Threads) {
-                        const int n12 = e / PQ, n3 = e - n12 * PQ;
-                        cs[e] = n3 < p ? cj[n12 * p + n3] : T(0);
-                    }
-                    __syncthreads();
-                    T S = 0, Sx = 0, Sy = 0, Sz = 0;
-                    if (act) {
-                        // exact unrolling for the common row lengths (p = 17..20, 21..24)
-                        if (ng == 5)
-                            cheb_eval<T, 5, false, GRAD>(cs, p, ng, Tz, dTz, xi, S, Sx, Sy, Sz);
-                        else if (ng == 6)
-                            cheb_eval<T, 6, false, GRAD>(cs, p, ng, Tz, dTz, xi, S, Sx, Sy, Sz);
-                        else
-                            cheb_eval<T, MQ, true, GRAD>(cs, p, ng, Tz, dTz, xi, S, Sx, Sy, Sz);
-                    }
-                    const T sc = (T)(1.0 / half);
-                    ev[j] = S;
-                    eg[0 * DU + j] = Sx * sc;
-                    eg[1 * DU + j] = Sy * sc;
-                    eg[2 * DU + j] = Sz * sc;
+                    Tz[n] = n < p ? tn : T(0);
+                    dTz[n] = n < p ? dn : T(0);
                 }
             }
-            // (3) residual sums with in-support compaction
-            double accd[DU], gaccd[3 * DU];
+            T ev[DU], eg[3 * DU];
 #pragma unroll
-            for (int j = 0; j < DU; ++j) accd[j] = 0;
-#pragma unroll
-            for (int j = 0; j < 3 * DU; ++j) gaccd[j] = 0;
-            int e = doffs[li];
-            const int e1 = doffs[li + 1];
-            int eo = 0;
-            while (e < e1) {
+            for (int j = 0; j < DU; ++j) {
                 __syncthreads();
-                int filled = 0;
-                while (filled < kSrcChunk && e < e1) {
-                    const DirectEntry de = dl[e];
-                    const int take = min(de.end - de.start - eo, kSrcChunk - filled);
-                    const int lev = de.code >> 6;
-                    const int sb[3] = {((de.code) & 3) - 1, ((de.code >> 2) & 3) - 1, ((de.code >> 4) & 3) - 1};
-                    // 1/nu and nu^2 of the entry's level; image shift minus the target leaf's
-                    // centre (FP32 parts in the FP32 path)
-                    T nu2, tinv;
-                    double E[3] = {0, 0, 0};
-                    float Eh[3] = {0, 0, 0}, El[3] = {0, 0, 0};
-                    if constexpr (kTwo) {
-                        tinv = ldexpf(inv_s_f, lev);
-                        nu2 = ldexpf(s2_f, -2 * lev);
-                        for (int a = 0; a < 3; ++a)
-                            two_float_add((float)sb[a] * Lh[a], (float)sb[a] * Ll[a], ch[a], cl[a], Eh[a], El[a]);
-                    } else {
-                        tinv = (T)ldexp(inv_s, lev);
-                        nu2 = (T)ldexp(s2, -2 * lev);
-                        for (int a = 0; a < 3; ++a) E[a] = (double)sb[a] * g.L[a] - c[a];
-                    }
-                    for (int k = tt; k < take; k += kLeaf3Threads) {
-                        const int si = de.start + eo + k, slot = filled + k;
-                        Q4 a, b;
-                        if constexpr (kTwo) {
-                            two_float_add(out.xh[si], out.xl[si], Eh[0], El[0], a.x, b.x);
-                            two_float_add(out.xh[N + si], out.xl[N + si], Eh[1], El[1], a.y, b.y);
-                            two_float_add(out.xh[2 * N + si], out.xl[2 * N + si], Eh[2], El[2], a.z, b.z);
-                            for (int a2 = 0; a2 < DR; ++a2) sr[slot][a2] = out.rsf[(int64_t)si * DR + a2];
-                        } else {
-                            a.x = (T)(xs[si] + E[0]);
-                            a.y = (T)(xs[N + si] + E[1]);
-                            a.z = (T)(xs[2 * N + si] + E[2]);
-                            b.x = b.y = b.z = T(0);
-                            for (int a2 = 0; a2 < DR; ++a2) sr[slot][a2] = (T)out.rs[(int64_t)si * DR + a2];
-                        }
-                        a.w = nu2;
-                        b.w = tinv;
-                        sA[slot] = a;
-                        sB[slot] = b;
-                        if constexpr (kTwo) {
-                            __half* hp = reinterpret_cast<__half*>(&sT[slot >> 1]);
-                            const int hh = slot & 1;
-                            hp[0 + hh] = __float2half_rn(-(a.x + b.x) * tinv);
-                            hp[2 + hh] = __float2half_rn(-(a.y + b.y) * tinv);
-                            hp[4 + hh] = __float2half_rn(-(a.z + b.z) * tinv);
-                            hp[6 + hh] = __float2half_rn(ldexpf(1.0f, lev - l));
-                        }
-                    }
-                    filled += take;
-                    eo += take;
-                    if (eo == de.end - de.start) { ++e; eo = 0; }
+                const T* cj = coef + ((size_t)box * DU + j) * p3;
+                for (int e = tt; e < p2 * PQ; e += kLeafExpThreads) {
+                    const int n12 = e / PQ, n3 = e - n12 * PQ;
+                    cs[e] = n3 < p ? cj[n12 * p + n3] : T(0);
                 }
                 __syncthreads();
+                T S = 0, Sx = 0, Sy = 0, Sz = 0;
                 if (act) {
-                    // support tests of 32 sources into a bit mask (independent iterations),
-                    // then the set bits appended to the queue; the queue column is swizzled by
-                    // row so that lanes with different queue lengths write to different banks
-                    int cnt = 0;
-                    for (int k0 = 0; k0 < filled; k0 += 32) {
-                        const int kn = min(32, filled - k0);
-                        if constexpr (kTwo) {
-                            // two sources per half2 instruction; bit m of me / mo: source
-                            // k0 + 2m / k0 + 2m + 1
-                            const __half2 one2 = __float2half2_rn(1.0f);
-                            unsigned me = 0, mo = 0;
-#pragma unroll 8
-                            for (int m = 0; m < 16; ++m) {
-                                if (2 * m < kn) {
-                                    const Quad<__half2> v = sT[(k0 >> 1) + m];
-                                    const __half2 dx = __hfma2(xu2[0], v.w, v.x);
-                                    const __half2 dy = __hfma2(xu2[1], v.w, v.y);
-                                    const __half2 dz = __hfma2(xu2[2], v.w, v.z);
-                                    const __half2 r2 = __hfma2(dx, dx, __hfma2(dy, dy, __hmul2(dz, dz)));
-                                    const unsigned mm = __hlt2_mask(r2, one2);
-                                    me |= (mm & 1u) << m;
-                                    mo |= ((mm >> 16) & 1u) << m;
-                                }
-                            }
-                            const int ne = (kn + 1) >> 1, no = kn >> 1;
-                            me &= (ne >= 32) ? ~0u : ((1u << ne) - 1u);
-                            mo &= (no >= 32) ? ~0u : ((1u << no) - 1u);
-                            while (me) {
-                                const int m = __ffs(me) - 1;
-                                me &= me - 1;
-                                q[cnt][tt ^ ((cnt & 7) << 2)] = (unsigned char)(k0 + 2 * m);
-                                ++cnt;
-                            }
-                            while (mo) {
-                                const int m = __ffs(mo) - 1;
-                                mo &= mo - 1;
-                                q[cnt][tt ^ ((cnt & 7) << 2)] = (unsigned char)(k0 + 2 * m + 1);
-                                ++cnt;
-                            }
-                        } else {
-                            unsigned mask = 0;
-#pragma unroll 8
-                            for (int kk = 0; kk < 32; ++kk) {
-                                if (kk < kn) {
-                                    const Q4 a = sA[k0 + kk];
-                                    const T dx = xt[0] - a.x, dy = xt[1] - a.y, dz = xt[2] - a.z;
-                                    const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                                    mask |= (r2 < a.w ? 1u : 0u) << kk;
-                                }
-                            }
-                            while (mask) {
-                                const int kk = __ffs(mask) - 1;
-                                mask &= mask - 1;
-                                q[cnt][tt ^ ((cnt & 7) << 2)] = (unsigned char)(k0 + kk);
-                                ++cnt;
-                            }
-                        }
-                    }
-                    T acc[DU], gacc[3 * DU];
-#pragma unroll
-                    for (int j = 0; j < DU; ++j) acc[j] = 0;
-#pragma unroll
-                    for (int j = 0; j < 3 * DU; ++j) gacc[j] = 0;
-#pragma unroll 2
-                    for (int i = 0; i < cnt; ++i) {
-                        const int k = q[i][tt ^ ((i & 7) << 2)];
-                        const Q4 a = sA[k], b = sB[k];
-                        T dx = xt[0] - a.x, dy = xt[1] - a.y, dz = xt[2] - a.z;
-                        if (kTwo) {
-                            dx += xtl[0] - b.x;
-                            dy += xtl[1] - b.y;
-                            dz += xtl[2] - b.z;
-                        }
-                        const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                        if (r2 > T(0)) {
-                            if constexpr (kTwo)
-                                Pr::eval(HermSeries(herm, r2, b.w), dx, dy, dz, r2, b.w, sr[k], acc, gacc);
-                            else
-                                Pr::eval(ChebSeries<T>(tab, fits, r2, b.w), dx, dy, dz, r2, b.w, sr[k], acc, gacc);
-                        }
-                    }
-#pragma unroll
-                    for (int j = 0; j < DU; ++j) accd[j] += (double)acc[j];
-#pragma unroll
-                    for (int j = 0; j < 3 * DU; ++j) gaccd[j] += (double)gacc[j];
+                    if (ng == 5)
+                        cheb_eval<T, 5, false, GRAD>(cs, p, ng, Tz, dTz, xi, S, Sx, Sy, Sz);
+                    else if (ng == 6)
+                        cheb_eval<T, 6, false, GRAD>(cs, p, ng, Tz, dTz, xi, S, Sx, Sy, Sz);
+                    else
+                        cheb_eval<T, MQ, true, GRAD>(cs, p, ng, Tz, dTz, xi, S, Sx, Sy, Sz);
                 }
+                const T sc = (T)(1.0 / half);
+                ev[j] = S;
+                eg[0 * DU + j] = Sx * sc;
+                eg[1 * DU + j] = Sy * sc;
+                eg[2 * DU + j] = Sz * sc;
             }
-            __syncthreads();
-            // (4) self correction and write-back (FP64)
+            // expansion + residual sums (written by k_pair), minus the self term
             if (act) {
-                const int tg = t0 + tt;
                 const int oi = out.perm[tg];
                 const double inv_nuT = 1.0 / r;
-                const double ks = KScale<K>::v;
                 const double* rt = out.rs + (int64_t)tg * DR;
 #pragma unroll
                 for (int j = 0; j < DU; ++j) {
-                    double v = (double)ev[j] + ks * accd[j];
+                    double v = (double)ev[j] + out.pot[(int64_t)oi * DU + j];
                     for (int a = 0; a < DR; ++a) v -= out.self_val[j * DR + a] * inv_nuT * rt[a];
                     out.pot[(int64_t)oi * DU + j] = v;
                 }
@@ -1050,9 +1123,10 @@ __global__ void __launch_bounds__(kLeaf3Threads) k_leaf3(int nleaf, const int* _
                     for (int i = 0; i < 3; ++i)
 #pragma unroll
                         for (int j = 0; j < DU; ++j) {
-                            double v = (double)eg[i * DU + j] + ks * gaccd[i * DU + j];
+                            const int64_t o = ((int64_t)oi * 3 + i) * DU + j;
+                            double v = (double)eg[i * DU + j] + out.grad[o];
                             for (int a = 0; a < DR; ++a) v -= out.self_grad[(i * DU + j) * DR + a] * in3 * rt[a];
-                            out.grad[((int64_t)oi * 3 + i) * DU + j] = v;
+                            out.grad[o] = v;
                         }
                 }
             }
@@ -1060,13 +1134,12 @@ __global__ void __launch_bounds__(kLeaf3Threads) k_leaf3(int nleaf, const int* _
     }
 }
 
-// dynamic shared memory of k_leaf3
-template <class T, int DR>
-inline size_t leaf3_smem(int p) {
+template <class T>
+inline size_t leafexp_smem(int p) {
     const int PQ = (p + 3) & ~3;
-    const size_t qbytes = std::max((size_t)kSrcChunk * kLeaf3Threads, (size_t)p * p * PQ * sizeof(T));
-    return ((qbytes + 15) & ~(size_t)15) + (size_t)kSrcChunk * DR * sizeof(T);
+    return (size_t)p * p * PQ * sizeof(T);
 }
+
 
 }  // namespace dmk
 

@@ -500,26 +500,54 @@ __global__ void k_colleagues(int nb, const int* __restrict__ level, const int* _
 // Entry = {start, end, packed shifts and level, unused}.
 struct DirectEntry { int start, end, code, pad; };
 
+// Residual-sum tasks of the leaf stage: a tile of m consecutive targets of one leaf, m = 32
+// for the full tiles and one tile per set bit of nt mod 32 for the rest; as (leaf index, first
+// target offset within the leaf, m, 0).
+// task k of a leaf with nt targets: full tiles first, then the remainder's set bits high to low
+__device__ __forceinline__ int4 pair_task(int li, int nt, int k) {
+    const int a = nt >> 5;
+    if (k < a) return make_int4(li, 32 * k, 32, 0);
+    int rem = nt & 31, t0 = 32 * a, j = k - a;
+    while (true) {
+        const int bit = 31 - __clz(rem);
+        if (j == 0) return make_int4(li, t0, 1 << bit, 0);
+        t0 += 1 << bit;
+        rem &= ~(1 << bit);
+        --j;
+    }
+}
+
+// number of such tasks
+__device__ __forceinline__ int pair_task_count(int nt) { return (nt >> 5) + __popc(nt & 31); }
+
+
 __device__ __forceinline__ int pack_code(const int sh[3], int level) {
     return (sh[0] + 1) | ((sh[1] + 1) << 2) | ((sh[2] + 1) << 4) | (level << 6);
 }
 
+// Per leaf: the direct-list entry count and the residual-task count (pair_task_count) at
+// counts[i] and counts[tbase + i] (FILL = false); after one exclusive scan over both halves,
+// the entries and the leaf's tasks (pair_task) at offs[i] and offs[tbase + i] - offs[tbase].
 template <bool FILL>
 __global__ void k_direct(int cap, const int* __restrict__ nleaf_dev, const int* __restrict__ leaves, BoxArrays B,
                          Geo g, int* __restrict__ counts, const int* __restrict__ offs, DirectEntry* __restrict__ out,
-                         unsigned long long* __restrict__ npairs) {
+                         unsigned long long* __restrict__ npairs, int tbase, int4* __restrict__ tasks) {
     // one warp per leaf, lane d < 27 = colleague offset; entries in the order (ancestor level
     // descending, then the leaf's own colleagues), d ascending within a level
     const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= cap) return;
     if (i >= nleaf_dev[0]) {
-        if (!FILL && lane == 0) counts[i] = 0;
+        if (!FILL && lane == 0) counts[i] = counts[tbase + i] = 0;
         return;
     }
     const int T = leaves[i];
     const int lT = B.level[T];
     const int nt = B.end[T] - B.start[T];
+    if (FILL) {
+        const int t0 = offs[tbase + i] - offs[tbase], ntask = pair_task_count(nt);
+        for (int k = lane; k < ntask; k += 32) tasks[t0 + k] = pair_task(i, nt, k);
+    }
     const unsigned below = (1u << lane) - 1u;
     int pos = FILL ? offs[i] : 0;
     int cnt = 0;
@@ -556,6 +584,7 @@ __global__ void k_direct(int cap, const int* __restrict__ nleaf_dev, const int* 
         for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
         if (lane == 0) {
             counts[i] = cnt;
+            counts[tbase + i] = pair_task_count(nt);
             atomicAdd(npairs, (unsigned long long)pairs);
         }
     }

@@ -35,7 +35,7 @@ class Stats(ctypes.Structure):
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "stage_ms"}
-        d["stage_ms"] = list(self.stage_ms)[:7]
+        d["stage_ms"] = list(self.stage_ms)[:8]
         return d
 
 

@@ -6,13 +6,15 @@ Per-unit figures (method arithmetic, not the instructions a kernel happens to is
       r^2, the reciprocal square root, the polynomial, the potential and force updates);
   Chebyshev evaluation of the leaf expansion with its gradient: 2 p^3 FMA = 4 p^3 FLOP
       per target (sum-factorised contraction of the p^3 coefficients).
-One leaf-kernel launch processes every visited pair and every target once.
+One launch of the residual kernel (k_pair) processes every visited pair once; one launch of
+the expansion kernel (k_leafexp) every target once.
 """
 
-# DRAM bytes (read + write) of one k_leaf3<float, Laplace, grad> launch at the benchmark
-# workload, from one ncu capture of the kernel as it stands (profiles/k_leaf3_laplace_2P_N1e5_mixed.md);
-# set to None whenever the kernel changes until it is captured again.
-LEAF_TRAFFIC_BYTES = 37.22e6 + 0.017e6
+# DRAM bytes (read + write) of one k_pair<float, Laplace, grad> launch at the benchmark
+# workload, from one ncu capture of the kernel as it stands
+# (profiles/k_pair_laplace_2P_N1e5_mixed.md); None whenever the kernel has changed since the
+# capture.
+PAIR_TRAFFIC_BYTES = 3.713e6 + 0.0
 
 SMS = 148
 FP32_LANES_PER_SM = 128
@@ -24,11 +26,21 @@ def fp32_peak_tflops():
     return SMS * FP32_LANES_PER_SM * 2 * MAX_SM_GHZ / 1e3
 
 
-def leaf_flops(kernel, stats, n_targets, grad=True, precision="mixed"):
+def pair_flops(kernel, stats, grad=True):
+    """Residual kernel: visited pairs x (22 + d_q) for Laplace with the gradient."""
     if kernel != "laplace":
         raise NotImplementedError("per-pair figure stated for the Laplace kernel")
     d_q = max(int(stats.get("fit_terms", 1)) - 1, 0)
     per_pair = (12 + d_q) + (10 if grad else 0)
+    return float(stats["n_pairs"]) * per_pair
+
+
+def leafexp_flops(stats, n_targets, grad=True):
+    """Expansion kernel: targets x 4 p^3 (value and gradient)."""
     p = int(stats["p"])
-    per_target = (4 if grad else 2) * p ** 3
-    return float(stats["n_pairs"]) * per_pair + float(n_targets) * per_target
+    return float(n_targets) * (4 if grad else 2) * p ** 3
+
+
+def leaf_flops(kernel, stats, n_targets, grad=True, precision="mixed"):
+    """Both leaf kernels together."""
+    return pair_flops(kernel, stats, grad) + leafexp_flops(stats, n_targets, grad)
