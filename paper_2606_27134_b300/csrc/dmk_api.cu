@@ -520,15 +520,14 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     void* vcub = nullptr;
     size_t cub_cap = 0;
     const uint64_t* pkeys = keys2;
-    // FP32 path: leading/trailing FP32 parts of the sorted coordinates and FP32 strengths, so
-    // that the leaf stage forms source offsets without FP64 arithmetic
-    float *xh = nullptr, *xl = nullptr, *rsf = nullptr;
+    // FP32 path: per sorted point a record of the leading/trailing FP32 parts of the
+    // coordinates and the FP32 strengths, so that the leaf stage forms source offsets without
+    // FP64 arithmetic and reads a source in one piece
+    float* pk = nullptr;
     if (sizeof(T) == 4) {
         void* vxf;
-        CKS(ensure(plan, B_XF, (size_t)N * (6 + drho) * sizeof(float), &vxf));
-        xh = (float*)vxf;
-        xl = xh + 3 * N;
-        rsf = xl + 3 * N;
+        CKS(ensure(plan, B_XF, (size_t)N * point_record_floats(drho) * sizeof(float), &vxf));
+        pk = (float*)vxf;
     }
     const int ngb = (int)((N + kGatherThreads - 1) / kGatherThreads);
     void* vpart;
@@ -559,7 +558,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         CKS(ensure(plan, B_CUB, std::max<size_t>(tmp_bytes, 1 << 20), &vcub));
         cub_cap = plan->bufs[B_CUB].cap;
         CK(cub::DeviceRadixSort::SortPairs(vcub, tmp_bytes, keys, keys2, idx, idx2, (int)N, begin_bit, end_bit, st));
-        k_gather<<<ngb, kGatherThreads, 0, st>>>(N, drho, idx2, (const double*)vw, rho, xs, rs, xh, xl, rsf,
+        k_gather<<<ngb, kGatherThreads, 0, st>>>(N, drho, idx2, (const double*)vw, rho, xs, rs, pk,
                                                   (double*)vpart);
         k_sum_partials<<<1, 1024, 0, st>>>(ngb, 2 * drho, (const double*)vpart, d_sums);
         k_refine_count<<<nblkR, kRefineThreads, 0, st>>>(N, pkeys, plan->n_s, nblkR, lsort, bcnt);
@@ -759,9 +758,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     lo.rs = rs;
     lo.self_val = plan->d_self;
     lo.self_grad = plan->d_self + P.d_u * P.d_rho;
-    lo.xh = xh;
-    lo.xl = xl;
-    lo.rsf = rsf;
+    lo.pk = reinterpret_cast<const float4*>(pk);
     const bool gr = grad != nullptr;
     const bool fast_leaf = nleaf > 0 && p <= kMaxPFast;
     auto run_pair = [&](cudaStream_t sp) -> dmk_status_t {

@@ -785,7 +785,7 @@ struct PairSmem {
 };
 
 template <class T, int K, bool GRAD>
-__global__ void __launch_bounds__(kPairWarps * 32, 4) k_pair(const int* __restrict__ leaves, BoxArrays B, Tab<T> tab,
+__global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? 4 : 2) k_pair(const int* __restrict__ leaves, BoxArrays B, Tab<T> tab,
                                                             Geo g, const double* __restrict__ xs, int64_t N,
                                                             const int* __restrict__ doffs,
                                                             const int* __restrict__ toffs, int tcap,
@@ -795,12 +795,14 @@ __global__ void __launch_bounds__(kPairWarps * 32, 4) k_pair(const int* __restri
     using Q4 = Quad<T>;
     constexpr int DR = Pr::DR, DU = Pr::DU, C = kPairChunk;
     constexpr bool kTwo = sizeof(T) == 4;
+    constexpr int RQ = point_record_floats(DR) / 4;     // float4s per point record
     using WS = PairSmem<T, DR>;
     constexpr int NSER = (K == DMK_STRESSLET) ? (GRAD ? 6 : 3) : ((GRAD && K != DMK_LAPLACE) ? 5 : 2);
     __shared__ Quad<float> herm[kTwo ? NSER * kHermNT : 1];
     __shared__ T fits[kTwo ? 1 : 256];
     extern __shared__ __align__(16) unsigned char dsmp[];
     const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
     unsigned char* wsm = dsmp + (threadIdx.x >> 5) * WS::bytes;
     Q4* sA = reinterpret_cast<Q4*>(wsm + WS::a);
     Q4* sB = reinterpret_cast<Q4*>(wsm + WS::b);
@@ -824,7 +826,7 @@ __global__ void __launch_bounds__(kPairWarps * 32, 4) k_pair(const int* __restri
     while (true) {
         int t = 0;
         if (lane == 0) t = atomicAdd(next, 1);
-        t = __shfl_sync(0xffffffffu, t, 0);
+        t = __shfl_sync(full, t, 0);
         if (t >= ntask) break;
         const int4 tk = tasks[t];
         const int li = tk.x, m = tk.z;
@@ -838,9 +840,13 @@ __global__ void __launch_bounds__(kPairWarps * 32, 4) k_pair(const int* __restri
         for (int a = 0; a < 3; ++a) split_double(-c[a], ch[a], cl[a]);
         const int tg = B.start[box] + tk.y + ti;
         T xt[3], xtl[3] = {0, 0, 0};
-        for (int a = 0; a < 3; ++a) {
-            if constexpr (kTwo) two_float_add(out.xh[a * N + tg], out.xl[a * N + tg], ch[a], cl[a], xt[a], xtl[a]);
-            else xt[a] = (T)(xs[a * N + tg] - c[a]);
+        if constexpr (kTwo) {
+            const float4 p0 = out.pk[(int64_t)tg * RQ], p1 = out.pk[(int64_t)tg * RQ + 1];
+            two_float_add(p0.x, p1.x, ch[0], cl[0], xt[0], xtl[0]);
+            two_float_add(p0.y, p1.y, ch[1], cl[1], xt[1], xtl[1]);
+            two_float_add(p0.z, p1.z, ch[2], cl[2], xt[2], xtl[2]);
+        } else {
+            for (int a = 0; a < 3; ++a) xt[a] = (T)(xs[a * N + tg] - c[a]);
         }
         const float inv_rT = ldexpf(inv_s_f, l);
         __half2 xu2[3];
@@ -850,62 +856,63 @@ __global__ void __launch_bounds__(kPairWarps * 32, 4) k_pair(const int* __restri
         for (int j = 0; j < DU; ++j) accd[j] = 0;
 #pragma unroll
         for (int j = 0; j < 3 * DU; ++j) gaccd[j] = 0;
-        int e = doffs[li];
-        const int e1 = doffs[li + 1];
-        int eo = 0;
-        while (e < e1) {
-            __syncwarp();
-            int filled = 0;
-            while (filled < C && e < e1) {
-                const DirectEntry de = dl[e];
-                const int take = min(de.end - de.start - eo, C - filled);
-                const int lev = de.code >> 6;
-                const int sb[3] = {((de.code) & 3) - 1, ((de.code >> 2) & 3) - 1, ((de.code >> 4) & 3) - 1};
-                T nu2, tinv;
-                double E[3] = {0, 0, 0};
-                float Eh[3] = {0, 0, 0}, El[3] = {0, 0, 0};
-                if constexpr (kTwo) {
-                    tinv = ldexpf(inv_s_f, lev);
-                    nu2 = ldexpf(s2_f, -2 * lev);
-                    for (int a = 0; a < 3; ++a)
-                        two_float_add((float)sb[a] * Lh[a], (float)sb[a] * Ll[a], ch[a], cl[a], Eh[a], El[a]);
-                } else {
-                    tinv = (T)ldexp(inv_s, lev);
-                    nu2 = (T)ldexp(s2, -2 * lev);
-                    for (int a = 0; a < 3; ++a) E[a] = (double)sb[a] * g.L[a] - c[a];
-                }
-                for (int k = lane; k < take; k += 32) {
-                    const int si = de.start + eo + k, slot = filled + k;
-                    Q4 a, b;
-                    if constexpr (kTwo) {
-                        two_float_add(out.xh[si], out.xl[si], Eh[0], El[0], a.x, b.x);
-                        two_float_add(out.xh[N + si], out.xl[N + si], Eh[1], El[1], a.y, b.y);
-                        two_float_add(out.xh[2 * N + si], out.xl[2 * N + si], Eh[2], El[2], a.z, b.z);
-                        for (int a2 = 0; a2 < DR; ++a2) sr[slot][a2] = out.rsf[(int64_t)si * DR + a2];
-                    } else {
-                        a.x = (T)(xs[si] + E[0]);
-                        a.y = (T)(xs[N + si] + E[1]);
-                        a.z = (T)(xs[2 * N + si] + E[2]);
-                        b.x = b.y = b.z = T(0);
-                        for (int a2 = 0; a2 < DR; ++a2) sr[slot][a2] = (T)out.rs[(int64_t)si * DR + a2];
-                    }
-                    a.w = nu2;
-                    b.w = tinv;
-                    sA[slot] = a;
-                    sB[slot] = b;
-                    if constexpr (kTwo) {
-                        __half* hp = reinterpret_cast<__half*>(&sT[slot >> 1]);
-                        const int hh = slot & 1;
-                        hp[0 + hh] = __float2half_rn(-(a.x + b.x) * tinv);
-                        hp[2 + hh] = __float2half_rn(-(a.y + b.y) * tinv);
-                        hp[4 + hh] = __float2half_rn(-(a.z + b.z) * tinv);
-                        hp[6 + hh] = __float2half_rn(ldexpf(1.0f, lev - l));
-                    }
-                }
-                filled += take;
-                eo += take;
-                if (eo == de.end - de.start) { ++e; eo = 0; }
+
+        // the per-entry constants: 1/nu and nu^2 of the entry's level, the image shift minus
+        // the target leaf's centre (FP32 parts in the FP32 path), the level ratio for the
+        // half-precision test
+        struct EntryC { T nu2, tinv; float Eh[3], El[3], hs; double E[3]; };
+        auto entry_consts = [&](const DirectEntry& de, EntryC& ec) {
+            const int lev = de.code >> 6;
+            const int sb[3] = {((de.code) & 3) - 1, ((de.code >> 2) & 3) - 1, ((de.code >> 4) & 3) - 1};
+            if constexpr (kTwo) {
+                ec.tinv = ldexpf(inv_s_f, lev);
+                ec.nu2 = ldexpf(s2_f, -2 * lev);
+                for (int a = 0; a < 3; ++a)
+                    two_float_add((float)sb[a] * Lh[a], (float)sb[a] * Ll[a], ch[a], cl[a], ec.Eh[a], ec.El[a]);
+            } else {
+                ec.tinv = (T)ldexp(inv_s, lev);
+                ec.nu2 = (T)ldexp(s2, -2 * lev);
+                for (int a = 0; a < 3; ++a) ec.E[a] = (double)sb[a] * g.L[a] - c[a];
             }
+            ec.hs = ldexpf(1.0f, lev - l);
+        };
+        // one source (sorted index si) into chunk slot `slot`
+        auto stage = [&](int64_t si, int slot, const EntryC& ec) {
+            Q4 a, b;
+            if constexpr (kTwo) {
+                const float4* rp = out.pk + si * RQ;
+                const float4 p0 = rp[0], p1 = rp[1];
+                two_float_add(p0.x, p1.x, ec.Eh[0], ec.El[0], a.x, b.x);
+                two_float_add(p0.y, p1.y, ec.Eh[1], ec.El[1], a.y, b.y);
+                two_float_add(p0.z, p1.z, ec.Eh[2], ec.El[2], a.z, b.z);
+                sr[slot][0] = p0.w;
+                if constexpr (DR > 1) {
+                    sr[slot][1] = p1.w;
+                    const float* rf = reinterpret_cast<const float*>(rp);
+                    for (int a2 = 2; a2 < DR; ++a2) sr[slot][a2] = rf[point_record_rho(a2)];
+                }
+            } else {
+                a.x = (T)(xs[si] + ec.E[0]);
+                a.y = (T)(xs[N + si] + ec.E[1]);
+                a.z = (T)(xs[2 * N + si] + ec.E[2]);
+                b.x = b.y = b.z = T(0);
+                for (int a2 = 0; a2 < DR; ++a2) sr[slot][a2] = (T)out.rs[si * DR + a2];
+            }
+            a.w = ec.nu2;
+            b.w = ec.tinv;
+            sA[slot] = a;
+            sB[slot] = b;
+            if constexpr (kTwo) {
+                __half* hp = reinterpret_cast<__half*>(&sT[slot >> 1]);
+                const int hh = slot & 1;
+                hp[0 + hh] = __float2half_rn(-(a.x + b.x) * ec.tinv);
+                hp[2 + hh] = __float2half_rn(-(a.y + b.y) * ec.tinv);
+                hp[4 + hh] = __float2half_rn(-(a.z + b.z) * ec.tinv);
+                hp[6 + hh] = __float2half_rn(ec.hs);
+            }
+        };
+        // support tests, queue and pair evaluation of one staged chunk of `filled` sources
+        auto run_chunk = [&](int filled) {
             if constexpr (kTwo) {
                 // an odd chunk: the unused half of the last pair fails every support test
                 if ((filled & 1) && lane == 0) {
@@ -915,8 +922,8 @@ __global__ void __launch_bounds__(kPairWarps * 32, 4) k_pair(const int* __restri
                 }
             }
             __syncwarp();
-            // support tests into bit masks, set bits appended to the queue (column swizzled by
-            // row so that lanes with different queue lengths write to different banks)
+            // support tests into bit masks, set bits appended to the queue (column swizzled
+            // by row so that lanes with different queue lengths write to different banks)
             int cnt = 0;
             if constexpr (kTwo) {
                 const __half2 one2 = __float2half2_rn(1.0f);
@@ -1000,13 +1007,63 @@ __global__ void __launch_bounds__(kPairWarps * 32, 4) k_pair(const int* __restri
             for (int j = 0; j < DU; ++j) accd[j] += (double)acc[j];
 #pragma unroll
             for (int j = 0; j < 3 * DU; ++j) gaccd[j] += (double)gacc[j];
+        };
+
+        const int e0 = doffs[li], e1 = doffs[li + 1], ne = e1 - e0;
+        if (ne <= 32) {
+            // Interleaved chunks: lane j holds entry e0 + j; chunk k takes positions
+            // k, k + nchunk, k + 2 nchunk, ... of every entry, so that each chunk samples the
+            // whole neighbourhood and the in-support counts of a tile's targets stay close
+            // (the warp runs to the longest queue).  With nchunk >= Ns / (C - ne) a chunk
+            // holds at most Ns / nchunk + ne <= C sources.
+            DirectEntry de = {0, 0, 0, 0};
+            EntryC ec;
+            if (lane < ne) {
+                de = dl[e0 + lane];
+                entry_consts(de, ec);
+            }
+            const int len = de.end - de.start;
+            const int Ns = __reduce_add_sync(full, len);
+            const int nchunk = (Ns + (C - ne) - 1) / (C - ne);
+            for (int k = 0; k < nchunk; ++k) {
+                __syncwarp();
+                const int cnt = len > k ? (len - k + nchunk - 1) / nchunk : 0;
+                int incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(full, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                const int filled = __shfl_sync(full, incl, 31);
+                const int off = incl - cnt;
+                for (int i = 0; i < cnt; ++i) stage((int64_t)de.start + k + (int64_t)nchunk * i, off + i, ec);
+                run_chunk(filled);
+            }
+        } else {
+            // contiguous chunks over the entries in order
+            int e = e0, eo = 0;
+            while (e < e1) {
+                __syncwarp();
+                int filled = 0;
+                while (filled < C && e < e1) {
+                    const DirectEntry de = dl[e];
+                    const int take = min(de.end - de.start - eo, C - filled);
+                    EntryC ec;
+                    entry_consts(de, ec);
+                    for (int k = lane; k < take; k += 32) stage((int64_t)de.start + eo + k, filled + k, ec);
+                    filled += take;
+                    eo += take;
+                    if (eo == de.end - de.start) { ++e; eo = 0; }
+                }
+                run_chunk(filled);
+            }
         }
         // the S splits of a target, combined in a fixed order (every lane gets the same sum)
         for (int o = m; o < 32; o <<= 1) {
 #pragma unroll
-            for (int j = 0; j < DU; ++j) accd[j] += __shfl_xor_sync(0xffffffffu, accd[j], o);
+            for (int j = 0; j < DU; ++j) accd[j] += __shfl_xor_sync(full, accd[j], o);
 #pragma unroll
-            for (int j = 0; j < 3 * DU; ++j) gaccd[j] += __shfl_xor_sync(0xffffffffu, gaccd[j], o);
+            for (int j = 0; j < 3 * DU; ++j) gaccd[j] += __shfl_xor_sync(full, gaccd[j], o);
         }
         if (s == 0) {
             const int oi = out.perm[tg];
@@ -1055,9 +1112,16 @@ __global__ void __launch_bounds__(kLeafExpThreads) k_leafexp(int nleaf, const in
             T xi[3] = {0, 0, 0};
             if (act) {
                 const T ih = (T)(1.0 / half);
+                constexpr int RQ = point_record_floats(DR) / 4;
+                float4 p0 = make_float4(0, 0, 0, 0), p1 = p0;
+                if constexpr (kTwo) {
+                    p0 = out.pk[(int64_t)tg * RQ];
+                    p1 = out.pk[(int64_t)tg * RQ + 1];
+                }
+                const float ph[3] = {p0.x, p0.y, p0.z}, pl[3] = {p1.x, p1.y, p1.z};
                 for (int a = 0; a < 3; ++a) {
                     T x0, x1 = 0;
-                    if constexpr (kTwo) two_float_add(out.xh[a * N + tg], out.xl[a * N + tg], ch[a], cl[a], x0, x1);
+                    if constexpr (kTwo) two_float_add(ph[a], pl[a], ch[a], cl[a], x0, x1);
                     else x0 = (T)(xs[a * N + tg] - c[a]);
                     const T v = (x0 + x1) * ih;
                     xi[a] = v > T(1) ? T(1) : (v < T(-1) ? T(-1) : v);

@@ -997,9 +997,7 @@ struct LeafOut {
     const double* rs;  // sorted strengths (FP64)
     const double* self_val;   // du x drho at nu = 1
     const double* self_grad;  // 3 x du x drho at nu = 1
-    const float* xh;          // FP32 path: leading FP32 parts of the sorted coordinates (3 x N)
-    const float* xl;          //            trailing parts
-    const float* rsf;         //            sorted strengths in FP32
+    const float4* pk;         // FP32 path: one record per sorted point (point_record layout)
 };
 
 constexpr int kLeafThreads = 128;

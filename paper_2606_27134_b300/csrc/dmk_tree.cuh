@@ -51,11 +51,17 @@ __global__ void k_quantize(int64_t N, const double* __restrict__ pts, Geo g, dou
 // partial[b * 2 d_rho + v], v < d_rho: sum rho_v, v >= d_rho: sum |rho_v|).
 constexpr int kGatherThreads = 256;
 
+// FP32 path: one record per sorted point, read whole by the leaf kernels (one 32-byte sector
+// for d_rho = 1): floats 0-2 the leading FP32 parts of the coordinates, 4-6 the trailing
+// parts (exact split of the FP64 value to 48 bits), the strengths in FP32 at 3, 7, 8, 9, ...
+// Records of 8 floats for d_rho = 1, else 16.
+__host__ __device__ constexpr int point_record_floats(int drho) { return drho <= 1 ? 8 : 16; }
+__host__ __device__ constexpr int point_record_rho(int a) { return a == 0 ? 3 : (a == 1 ? 7 : 6 + a); }
+
 __global__ void __launch_bounds__(kGatherThreads) k_gather(int64_t N, int drho, const int* __restrict__ idx,
                                                            const double* __restrict__ w,
                                                            const double* __restrict__ rho, double* __restrict__ xs,
-                                                           double* __restrict__ rs, float* __restrict__ xh,
-                                                           float* __restrict__ xl, float* __restrict__ rsf,
+                                                           double* __restrict__ rs, float* __restrict__ pk,
                                                            double* __restrict__ partial) {
     __shared__ double red[18][kGatherThreads / 32];
     const int64_t k = blockIdx.x * (int64_t)kGatherThreads + threadIdx.x;
@@ -64,21 +70,26 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(int64_t N, int drho, 
     for (int a = 0; a < drho; ++a) { s[a] = 0; sa[a] = 0; }
     if (k < N) {
         const int i = idx[k];
+        float rec[16];
+        const int nf = point_record_floats(drho);
+        for (int f = 0; f < 16; ++f) rec[f] = 0.0f;
         for (int a = 0; a < 3; ++a) {
             const double v = w[a * N + i];
             xs[a * N + k] = v;
-            if (xh) {   // leading + trailing FP32 parts (exact split of the FP64 value to 48 bits)
-                const float h = (float)v;
-                xh[a * N + k] = h;
-                xl[a * N + k] = (float)(v - (double)h);
-            }
+            const float h = (float)v;
+            rec[a] = h;
+            rec[4 + a] = (float)(v - (double)h);
         }
         for (int a = 0; a < drho; ++a) {
             const double r = rho[(int64_t)i * drho + a];
             rs[k * drho + a] = r;
-            if (rsf) rsf[k * drho + a] = (float)r;
+            rec[point_record_rho(a)] = (float)r;
             s[a] = r;
             sa[a] = fabs(r);
+        }
+        if (pk) {
+            float4* dst = reinterpret_cast<float4*>(pk + k * nf);
+            for (int f = 0; f < nf / 4; ++f) dst[f] = make_float4(rec[4 * f], rec[4 * f + 1], rec[4 * f + 2], rec[4 * f + 3]);
         }
     }
     for (int a = 0; a < drho; ++a) {
