@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <functional>
 #include <mutex>
 #include <cmath>
@@ -105,7 +106,7 @@ namespace {
 
 enum BufId {
     B_W, B_KEYS, B_KEYS2, B_IDX, B_IDX2, B_XS, B_RS, B_CUB, B_FLAGS, B_CNT,
-    B_CELLS, B_R, B_CAND, B_BOXU64, B_BOXINT, B_LEAVES, B_DOFFS, B_DL, B_NLBOX, B_TASKS,
+    B_CELLS, B_R, B_CAND, B_BOXU64, B_BOXINT, B_LEAVES, B_DOFFS, B_DL, B_NLBOX, B_TASKS, B_BAL,
     B_PROXY, B_LOCAL, B_PW, B_SCRATCH, B_CHI, B_UHAT, B_MISC, B_DEVPTS, B_DEVRHO, B_DEVPOT, B_DEVGRAD, B_XF, B_VW, B_PART,
     B_COUNT
 };
@@ -120,6 +121,21 @@ dmk_status_t arena_take(dmk_plan_s* plan, size_t bytes, void** out) {
     }
     *out = plan->arena + plan->arena_off;
     plan->arena_off += need;
+    return DMK_OK;
+}
+
+// Waits for the small readback just queued on st.  These complete within tens of
+// microseconds, and a blocking wait was measured to return up to ~70 us after the copy had
+// finished, so the host polls first (at most 2 ms) and only then blocks.
+dmk_status_t host_wait(dmk_plan_s* plan, cudaStream_t st) {
+    const auto t0 = std::chrono::steady_clock::now();
+    while (true) {
+        const cudaError_t e = cudaStreamQuery(st);
+        if (e == cudaSuccess) return DMK_OK;
+        if (e != cudaErrorNotReady) CK(e);
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(2000)) break;
+    }
+    CK(cudaStreamSynchronize(st));
     return DMK_OK;
 }
 
@@ -571,7 +587,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         }
         launches += 11;
         CK(cudaMemcpyAsync(plan->h_meta, d_nR, 512, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+        CKS(host_wait(plan, st));
         if (lsort >= kBits || hmeta[lsort - 1] == 0) break;
         lsort = kBits;                                     // deeper than the sorted bits: resort
     }
@@ -613,16 +629,23 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
             int* d_overflow = (int*)((char*)vmisc + 1600);
             std::vector<const uint64_t*> Rs(Rl);
             std::vector<int64_t> cs(cR);
+            // every level's output from one plan buffer (no allocation per level)
+            auto bal_bytes = [&](int l) { return ((size_t)(cR[l - 1] + kBalNew) * sizeof(uint64_t) + 255) & ~(size_t)255; };
+            size_t bal_total = 0;
+            for (int l = nlev - 2; l >= 1; --l) bal_total += bal_bytes(l);
+            void* vbal;
+            CKS(ensure(plan, B_BAL, bal_total, &vbal));
+            size_t bal_off = 0;
             for (int l = nlev - 2; l >= 1; --l) {
-                void* vo;
-                CKS(alloc_level((size_t)(cs[l - 1] + kBalNew) * sizeof(uint64_t), &vo));
+                void* vo = (char*)vbal + bal_off;
+                bal_off += bal_bytes(l);
                 k_balance_small<<<1, kBalThreads, 0, st>>>(Rs[l], Rs[l - 1], d_nR, l, g, (uint64_t*)vo, d_overflow);
                 Rs[l - 1] = (const uint64_t*)vo;
                 cs[l - 1] += kBalNew;
                 ++launches;
             }
             CK(cudaMemcpyAsync(plan->h_meta, d_nR, 1024, cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
+            CKS(host_wait(plan, st));
             if (hmeta[(1600 - 1024) / 4] == 0) {
                 Rl = Rs;
             } else {
@@ -659,7 +682,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
             launches += 6;
         }
         CK(cudaMemcpyAsync(plan->h_meta, d_nR, nlev * sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+        CKS(host_wait(plan, st));
     }
     for (int k = 0; k < nlev; ++k) {
         ti.nR.push_back(hmeta[k]);
@@ -731,7 +754,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         // pinned readback: misc + 768 .. + 1540 holds the pair count and the leaf count
         CK(cudaMemcpyAsync(plan->h_meta, (char*)vmisc + 768, 772, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(plan->h_meta + 1024, doffs + nb, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+        CKS(host_wait(plan, st));
         int n_entries = 0;
         std::memcpy(&ti.n_pairs, plan->h_meta, sizeof(unsigned long long));
         std::memcpy(&ti.n_leafp, plan->h_meta + (1536 - 768), sizeof(int));
@@ -1022,7 +1045,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     double hs[18];
     // pinned readback of the error flags (misc + 0) and strength sums (misc + 256)
     CK(cudaMemcpyAsync(plan->h_meta, vmisc, 256 + 2 * drho * sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    CKS(host_wait(plan, st));
     std::memcpy(&herr, plan->h_meta, sizeof(int));
     std::memcpy(hs, plan->h_meta + 256, 2 * drho * sizeof(double));
     if (herr & kErrNonFinite) { plan->err = "non-finite coordinate"; return DMK_ERR_OUT_OF_DOMAIN; }
