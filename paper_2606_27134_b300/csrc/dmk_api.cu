@@ -70,7 +70,7 @@ struct dmk_plan_s {
     // residual sums (k_pair) run on their own stream beside the far field when pair_overlap is
     // set, at most pair_blocks resident blocks per SM (0: as many as fit)
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_cnt = nullptr;
     int pair_overlap = 1;
     int pair_blocks = 2;
     int n_sm = 148;
@@ -136,6 +136,19 @@ dmk_status_t host_wait(dmk_plan_s* plan, cudaStream_t st) {
         if (std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(2000)) break;
     }
     CK(cudaStreamSynchronize(st));
+    return DMK_OK;
+}
+
+// the same for an event
+dmk_status_t host_wait_event(dmk_plan_s* plan, cudaEvent_t ev) {
+    const auto t0 = std::chrono::steady_clock::now();
+    while (true) {
+        const cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return DMK_OK;
+        if (e != cudaErrorNotReady) CK(e);
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(2000)) break;
+    }
+    CK(cudaEventSynchronize(ev));
     return DMK_OK;
 }
 
@@ -380,25 +393,25 @@ dmk_status_t set_smem(dmk_plan_s* plan, K kernel, size_t bytes) {
 }
 
 template <class T, int MAXP>
-dmk_status_t launch_anterp(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int* leaves, BoxArrays B, const double* xs,
-                   int64_t N, const double* rs, T* proxy) {
+dmk_status_t launch_anterp(dmk_plan_s* plan, Tab<T>& tab, int nleaf_cap, const int* nleaf_dev, const int* leaves,
+                           BoxArrays B, const double* xs, int64_t N, const double* rs, T* proxy) {
     const int p2 = tab.p * tab.p;
     int threads = std::min(MAXP <= 24 ? 576 : 512, ((p2 + 31) / 32) * 32);
     size_t sm = 3 * (size_t)kAnterpChunk * MAXP * sizeof(T);
     CKS(set_smem(plan, k_anterp<T, MAXP>, sm));
-    unsigned grid = (unsigned)std::max(1, std::min(nleaf, 148 * 8));
-    k_anterp<T, MAXP><<<grid, threads, sm, plan->stream>>>(nleaf, leaves, B, xs, N, rs, tab, plan->T.s, proxy);
+    unsigned grid = (unsigned)std::max(1, std::min(nleaf_cap, 148 * 8));
+    k_anterp<T, MAXP><<<grid, threads, sm, plan->stream>>>(nleaf_dev, leaves, B, xs, N, rs, tab, plan->T.s, proxy);
     return DMK_OK;
 }
 
 template <class T, int MAXP>
-dmk_status_t launch_anterp2(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int* leaves, BoxArrays B,
-                            const double* xs, int64_t N, const double* rs, T* proxy) {
+dmk_status_t launch_anterp2(dmk_plan_s* plan, Tab<T>& tab, int nleaf_cap, const int* nleaf_dev, const int* leaves,
+                            BoxArrays B, const double* xs, int64_t N, const double* rs, T* proxy) {
     const int threads = (((tab.p + 1) / 2) * tab.p + 31) / 32 * 32;
     const size_t sm = 3 * (size_t)kAnterpChunk * MAXP * sizeof(T);
     CKS(set_smem(plan, k_anterp2<T, MAXP>, sm));
-    const unsigned grid = (unsigned)std::max(1, std::min(nleaf, 148 * 8));
-    k_anterp2<T, MAXP><<<grid, threads, sm, plan->stream>>>(nleaf, leaves, B, xs, N, rs, tab, plan->T.s, proxy);
+    const unsigned grid = (unsigned)std::max(1, std::min(nleaf_cap, 148 * 8));
+    k_anterp2<T, MAXP><<<grid, threads, sm, plan->stream>>>(nleaf_dev, leaves, B, xs, N, rs, tab, plan->T.s, proxy);
     return DMK_OK;
 }
 
@@ -415,19 +428,29 @@ dmk_status_t resident_blocks(dmk_plan_s* plan, Kern kernel, int threads, size_t 
 
 // residual sums (k_pair, persistent: every resident block takes tasks from the counter) on
 // stream sp
+template <class T, int K, bool G, int C>
+dmk_status_t launch_pair_c(dmk_plan_s* plan, Tab<T>& tab, const int* leaves, BoxArrays B, const double* xs, int64_t N,
+                           const int* doffs, const DirectEntry* dl, LeafOut lo, const int* toffs, int tcap,
+                           const int4* tasks, int* next, cudaStream_t sp) {
+    constexpr int DR = Pair<T, K, G>::DR;
+    const size_t sm = pair_smem<T, DR, C>();
+    CKS(set_smem(plan, k_pair<T, K, G, C>, sm));
+    int per_sm = 1;
+    CKS(resident_blocks(plan, k_pair<T, K, G, C>, kPairWarps * 32, sm, &per_sm));
+    if (plan->pair_overlap && plan->pair_blocks > 0) per_sm = std::min(per_sm, plan->pair_blocks);
+    k_pair<T, K, G, C><<<per_sm * plan->n_sm, kPairWarps * 32, sm, sp>>>(leaves, B, tab, plan->geo, xs, N, doffs,
+                                                                         toffs, tcap, tasks, next, dl, lo);
+    return DMK_OK;
+}
+
+// 128-source chunks: 47 KB of shared memory per block (FP32 Laplace), so that two resident
+// blocks per SM leave room for the far-field kernels running beside them (256-source chunks
+// crowded out the upward clusters: 1.56 -> 1.72 ms per step)
 template <class T, int K, bool G>
 dmk_status_t launch_pair(dmk_plan_s* plan, Tab<T>& tab, const int* leaves, BoxArrays B, const double* xs, int64_t N,
                          const int* doffs, const DirectEntry* dl, LeafOut lo, const int* toffs, int tcap,
                          const int4* tasks, int* next, cudaStream_t sp) {
-    constexpr int DR = Pair<T, K, G>::DR;
-    const size_t sm = pair_smem<T, DR>();
-    CKS(set_smem(plan, k_pair<T, K, G>, sm));
-    int per_sm = 1;
-    CKS(resident_blocks(plan, k_pair<T, K, G>, kPairWarps * 32, sm, &per_sm));
-    if (plan->pair_overlap && plan->pair_blocks > 0) per_sm = std::min(per_sm, plan->pair_blocks);
-    k_pair<T, K, G><<<per_sm * plan->n_sm, kPairWarps * 32, sm, sp>>>(leaves, B, tab, plan->geo, xs, N, doffs, toffs,
-                                                                      tcap, tasks, next, dl, lo);
-    return DMK_OK;
+    return launch_pair_c<T, K, G, 128>(plan, tab, leaves, B, xs, N, doffs, dl, lo, toffs, tcap, tasks, next, sp);
 }
 
 // leaf expansions + residual sums + self terms (k_leafexp)
@@ -751,26 +774,18 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         cub::DeviceScan::ExclusiveSum(nullptr, tb, doffs, doffs, 2 * (nb + 1), st);
         if (tb > cub_cap) { CKS(ensure(plan, B_CUB, tb, &vcub)); cub_cap = plan->bufs[B_CUB].cap; }
         CK(cub::DeviceScan::ExclusiveSum(vcub, tb, doffs, doffs, 2 * (nb + 1), st));
-        // pinned readback: misc + 768 .. + 1540 holds the pair count and the leaf count
+        // pinned readback: misc + 768 .. + 1540 holds the pair count and the leaf count; read by
+        // the host only after the upward pass is queued (ev_cnt), so the GPU does not wait for it
         CK(cudaMemcpyAsync(plan->h_meta, (char*)vmisc + 768, 772, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(plan->h_meta + 1024, doffs + nb, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CKS(host_wait(plan, st));
-        int n_entries = 0;
-        std::memcpy(&ti.n_pairs, plan->h_meta, sizeof(unsigned long long));
-        std::memcpy(&ti.n_leafp, plan->h_meta + (1536 - 768), sizeof(int));
-        std::memcpy(&n_entries, plan->h_meta + 1024, sizeof(int));
-        ti.n_entries = n_entries;
+        CK(cudaEventRecord(plan->ev_cnt, st));
         launches += 3;
     }
-    const int nleaf = ti.n_leafp;
-    CKS(ensure(plan, B_DL, (size_t)std::max<int64_t>(ti.n_entries, 1) * sizeof(DirectEntry), &vdl));
-    DirectEntry* dl = (DirectEntry*)vdl;
-    // at most nt/32 + 5 tasks per leaf
-    CKS(ensure(plan, B_TASKS, ((size_t)N / 32 + 5 * (size_t)nleaf + 1) * sizeof(int4), &vtk));
-    int4* tasks = (int4*)vtk;
-    k_direct<true><<<nblk((int64_t)32 * nleaf, 128), 128, 0, st>>>(nleaf, d_nleaf, leaves, B, g, nullptr, doffs, dl,
-                                                                   nullptr, nb + 1, tasks);
-    ++launches;
+    // leaf boxes (with or without points): the bound used before the leaf count is read back
+    const int nleaf_cap = nb - n_nl;
+    int nleaf = 0;
+    DirectEntry* dl = nullptr;
+    int4* tasks = nullptr;
     rec(1);
     // ---- leaf residual sums: they need only the tree, so with pair_overlap they run on the
     // side stream beside the far field (steps 5-8) and are joined before the leaf expansions
@@ -783,7 +798,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     lo.self_grad = plan->d_self + P.d_u * P.d_rho;
     lo.pk = reinterpret_cast<const float4*>(pk);
     const bool gr = grad != nullptr;
-    const bool fast_leaf = nleaf > 0 && p <= kMaxPFast;
+    bool fast_leaf = false, overlap = false;
     auto run_pair = [&](cudaStream_t sp) -> dmk_status_t {
         if (plan->timing) cudaEventRecord(plan->ev[8], sp);
         switch (P.kernel) {
@@ -796,13 +811,35 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         ++launches;
         return DMK_OK;
     };
-    const bool overlap = fast_leaf && plan->pair_overlap;
-    if (overlap) {
-        CK(cudaEventRecord(plan->ev_fork, st));
-        CK(cudaStreamWaitEvent(plan->side, plan->ev_fork, 0));
-        CKS(run_pair(plan->side));
-        CK(cudaEventRecord(plan->ev_join, plan->side));
-    }
+    // the direct lists' counts (queued before the upward pass), the filled lists and tasks, and
+    // with pair_overlap the residual sums on the side stream, which waits for the counts only
+    auto finish_direct = [&]() -> dmk_status_t {
+        CKS(host_wait_event(plan, plan->ev_cnt));
+        int n_entries = 0;
+        std::memcpy(&ti.n_pairs, plan->h_meta, sizeof(unsigned long long));
+        std::memcpy(&ti.n_leafp, plan->h_meta + (1536 - 768), sizeof(int));
+        std::memcpy(&n_entries, plan->h_meta + 1024, sizeof(int));
+        ti.n_entries = n_entries;
+        nleaf = ti.n_leafp;
+        fast_leaf = nleaf > 0 && p <= kMaxPFast;
+        overlap = fast_leaf && plan->pair_overlap;
+        CKS(ensure(plan, B_DL, (size_t)std::max<int64_t>(ti.n_entries, 1) * sizeof(DirectEntry), &vdl));
+        dl = (DirectEntry*)vdl;
+        // at most nt/32 + 5 tasks per leaf
+        CKS(ensure(plan, B_TASKS, ((size_t)N / 32 + 5 * (size_t)nleaf + 1) * sizeof(int4), &vtk));
+        tasks = (int4*)vtk;
+        const cudaStream_t sd = overlap ? plan->side : st;
+        if (overlap) CK(cudaStreamWaitEvent(plan->side, plan->ev_cnt, 0));
+        if (nleaf > 0)
+            k_direct<true><<<nblk((int64_t)32 * nleaf, 128), 128, 0, sd>>>(nleaf, d_nleaf, leaves, B, g, nullptr,
+                                                                           doffs, dl, nullptr, nb + 1, tasks);
+        ++launches;
+        if (overlap) {
+            CKS(run_pair(plan->side));
+            CK(cudaEventRecord(plan->ev_join, plan->side));
+        }
+        return DMK_OK;
+    };
     // ---- (5) upward pass ---------------------------------------------------------------
     void *vpr, *vloc;
     CKS(ensure(plan, B_PROXY, (size_t)nb * drho * p3 * sizeof(T), &vpr));
@@ -812,10 +849,10 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     CK(cudaMemsetAsync(proxy, 0, (size_t)nb * drho * p3 * sizeof(T), st));
     CK(cudaMemsetAsync(local, 0, (size_t)nb * du * p3 * sizeof(T), st));
     launches += 2;
-    if (nleaf > 0) {
-        if (p <= 20) CKS((launch_anterp2<T, 20>(plan, tab, nleaf, leaves, B, xs, N, rs, proxy)));
-        else if (p <= 24) CKS((launch_anterp2<T, 24>(plan, tab, nleaf, leaves, B, xs, N, rs, proxy)));
-        else CKS((launch_anterp<T, 48>(plan, tab, nleaf, leaves, B, xs, N, rs, proxy)));
+    if (nleaf_cap > 0) {
+        if (p <= 20) CKS((launch_anterp2<T, 20>(plan, tab, nleaf_cap, d_nleaf, leaves, B, xs, N, rs, proxy)));
+        else if (p <= 24) CKS((launch_anterp2<T, 24>(plan, tab, nleaf_cap, d_nleaf, leaves, B, xs, N, rs, proxy)));
+        else CKS((launch_anterp<T, 48>(plan, tab, nleaf_cap, d_nleaf, leaves, B, xs, N, rs, proxy)));
         ++launches;
     }
     Evaluator<T> ev(plan, tab);
@@ -851,6 +888,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         ++launches;
     }
     rec(2);
+    CKS(finish_direct());
     // ---- (6) root far field (FP64) ----------------------------------------------------------
     {
         const RootTab& rt = plan->root;
@@ -1014,7 +1052,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         size_t bytes = 2 * (size_t)p3 * sizeof(T);
         CKS(ev.place(bytes, n, pl, &scr));
         CKS(set_smem(plan, k_grid2coef<T>, pl.use_smem ? bytes : 0));
-        k_grid2coef<T><<<pl.grid, 256, pl.use_smem ? bytes : 0, st>>>(n, leaves, B.level, root_only, tab, local, scr,
+        k_grid2coef<T><<<pl.grid, 256, pl.use_smem ? bytes : 0, st>>>(n, d_nleaf, leaves, B.level, root_only, tab, local, scr,
                                                                       bytes, pl.use_smem);
         ++launches;
     }
@@ -1124,7 +1162,8 @@ dmk_status_t make_plan(int k, int D, const double L[3], double tol, int prec, in
     for (int i = 0; i < 10; ++i) cudaEventCreate(&plan->ev[i]);
     if (cudaStreamCreateWithFlags(&plan->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&plan->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&plan->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&plan->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->ev_cnt, cudaEventDisableTiming) != cudaSuccess) {
         g_plan_error = "stream or event creation failed";
         dmk_destroy(plan);
         return DMK_ERR_CUDA;
@@ -1253,6 +1292,7 @@ dmk_status_t dmk_destroy(dmk_plan_t plan) {
     }
     if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
     if (plan->ev_join) cudaEventDestroy(plan->ev_join);
+    if (plan->ev_cnt) cudaEventDestroy(plan->ev_cnt);
     for (int i = 0; i < 10; ++i)
         if (plan->ev[i]) cudaEventDestroy(plan->ev[i]);
     if (plan->h_meta) cudaFreeHost(plan->h_meta);

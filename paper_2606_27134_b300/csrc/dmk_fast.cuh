@@ -110,9 +110,11 @@ __device__ __forceinline__ void load_op(T* Ms, int p, F src) {
 // Grid values -> Chebyshev coefficients in place, for leaves whose grid did not come through
 // k_shift_child (root-level leaves, and every leaf when p > kMaxPFast).
 template <class T>
-__global__ void k_grid2coef(int n, const int* __restrict__ boxes, const int* __restrict__ level, int root_only,
-                            Tab<T> tab, T* __restrict__ local, unsigned char* scratch, size_t per_cta, int use_smem) {
+__global__ void k_grid2coef(int ncap, const int* __restrict__ nleaf_dev, const int* __restrict__ boxes,
+                            const int* __restrict__ level, int root_only, Tab<T> tab, T* __restrict__ local,
+                            unsigned char* scratch, size_t per_cta, int use_smem) {
     const int p = tab.p, p2 = p * p, p3 = p2 * p, du = tab.d_u;
+    const int n = min(ncap, *nleaf_dev);   // the first ncap entries of the leaf list at most
     T* t1 = reinterpret_cast<T*>(work_base(scratch, per_cta, use_smem));
     T* t2 = t1 + p3;
     for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
@@ -754,7 +756,7 @@ __device__ __forceinline__ void cheb_eval(const T* cs, int p, int ng, const T (&
 // remainder (m = 16, 8, 4, 2, 1), so that every lane of every task has a target.  In a tile of
 // m < 32 targets lane = s m + i holds target i and takes every S-th source pair (S = 32/m,
 // split s) of each chunk; the S partial sums are combined by a fixed xor-shuffle tree.  Warps
-// take tasks from a device counter and stage their own chunks of kPairChunk sources, so no
+// take tasks from a device counter and stage their own chunks of C sources, so no
 // barrier couples the warps of a block.  A chunk holds (x, y, z, nu^2) and (x_lo, y_lo, z_lo,
 // 1/nu) per source (source offsets from the target leaf's centre, FP32 leading and trailing
 // parts in the FP32 path).  Per chunk: support test |x_t sigma - x_s/nu| < 1 (half precision on
@@ -770,21 +772,22 @@ __device__ __forceinline__ void cheb_eval(const T* cs, int p, int ng, const T (&
 // rows as broadcast vectors (Sec. 3.1.5).  The expansion is added to the residual sums written
 // by k_pair, the self term (Sec. 2.4) subtracted, and the result written in FP64.
 constexpr int kPairWarps = 4;
-constexpr int kPairChunk = 128;
 
-// byte offsets within one warp's shared-memory region of k_pair
-template <class T, int DR>
+// byte offsets within one warp's shared-memory region of k_pair for chunks of C sources
+// (C <= 256: the queue holds byte indices)
+template <class T, int DR, int C>
 struct PairSmem {
+    static_assert(C <= 256 && C % 32 == 0, "chunk of at most 256 sources");
     static constexpr bool kTwo = sizeof(T) == 4;
     static constexpr size_t a = 0;                                                    // Quad<T> [C]
-    static constexpr size_t b = a + kPairChunk * sizeof(Quad<T>);                     // Quad<T> [C]
-    static constexpr size_t t = b + kPairChunk * sizeof(Quad<T>);                     // Quad<half2> [C/2]
-    static constexpr size_t r = t + (kTwo ? kPairChunk / 2 * sizeof(Quad<__half2>) : 0);   // T [C][DR]
-    static constexpr size_t q = (r + kPairChunk * DR * sizeof(T) + 15) & ~(size_t)15;     // u8 [C][32]
-    static constexpr size_t bytes = q + kPairChunk * 32;
+    static constexpr size_t b = a + C * sizeof(Quad<T>);                              // Quad<T> [C]
+    static constexpr size_t t = b + C * sizeof(Quad<T>);                              // Quad<half2> [C/2]
+    static constexpr size_t r = t + (kTwo ? C / 2 * sizeof(Quad<__half2>) : 0);      // T [C][DR]
+    static constexpr size_t q = (r + C * DR * sizeof(T) + 15) & ~(size_t)15;          // u8 [C][32]
+    static constexpr size_t bytes = q + C * 32;
 };
 
-template <class T, int K, bool GRAD>
+template <class T, int K, bool GRAD, int C>
 __global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? 4 : 2) k_pair(const int* __restrict__ leaves, BoxArrays B, Tab<T> tab,
                                                             Geo g, const double* __restrict__ xs, int64_t N,
                                                             const int* __restrict__ doffs,
@@ -793,10 +796,10 @@ __global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? 4 : 2) k_pai
                                                             const DirectEntry* __restrict__ dl, LeafOut out) {
     using Pr = Pair<T, K, GRAD>;
     using Q4 = Quad<T>;
-    constexpr int DR = Pr::DR, DU = Pr::DU, C = kPairChunk;
+    constexpr int DR = Pr::DR, DU = Pr::DU;
     constexpr bool kTwo = sizeof(T) == 4;
     constexpr int RQ = point_record_floats(DR) / 4;     // float4s per point record
-    using WS = PairSmem<T, DR>;
+    using WS = PairSmem<T, DR, C>;
     constexpr int NSER = (K == DMK_STRESSLET) ? (GRAD ? 6 : 3) : ((GRAD && K != DMK_LAPLACE) ? 5 : 2);
     __shared__ Quad<float> herm[kTwo ? NSER * kHermNT : 1];
     __shared__ T fits[kTwo ? 1 : 256];
@@ -1080,9 +1083,9 @@ __global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? 4 : 2) k_pai
     }
 }
 
-template <class T, int DR>
+template <class T, int DR, int C>
 inline size_t pair_smem() {
-    return (size_t)kPairWarps * PairSmem<T, DR>::bytes;
+    return (size_t)kPairWarps * PairSmem<T, DR, C>::bytes;
 }
 
 constexpr int kLeafExpThreads = 128;

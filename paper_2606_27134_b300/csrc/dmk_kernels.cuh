@@ -64,7 +64,7 @@ __device__ __forceinline__ void lagrange_row_padded(T xi, const T* nodes, const 
 
 template <class T, int MAXP>
 __global__ void __launch_bounds__(MAXP <= 24 ? (MAXP * MAXP + 31) / 32 * 32 : 512, (MAXP <= 24 && sizeof(T) == 4) ? 2 : 1)
-    k_anterp(int nleaf, const int* __restrict__ leaves, BoxArrays B,
+    k_anterp(const int* __restrict__ nleaf_dev, const int* __restrict__ leaves, BoxArrays B,
                                                  const double* __restrict__ xs, int64_t N,
                                                  const double* __restrict__ rs, Tab<T> tab, double s,
                                                  T* __restrict__ proxy) {
@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(MAXP <= 24 ? (MAXP * MAXP + 31) / 32 * 32 : 51
     T* lx = reinterpret_cast<T*>(dsmem);
     T* ly = lx + PC * MAXP;
     T* lz = ly + PC * MAXP;
+    const int nleaf = *nleaf_dev;
     for (int li = blockIdx.x; li < nleaf; li += gridDim.x) {
         const int box = leaves[li];
         const int l = B.level[box];
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(MAXP <= 24 ? (MAXP * MAXP + 31) / 32 * 32 : 51
 // loads.  Threads: ceil(p/2) p.
 template <class T, int MAXP>
 __global__ void __launch_bounds__((MAXP / 2 * MAXP + 31) / 32 * 32, sizeof(T) == 4 ? 2 : 1)
-    k_anterp2(int nleaf, const int* __restrict__ leaves, BoxArrays B, const double* __restrict__ xs, int64_t N,
+    k_anterp2(const int* __restrict__ nleaf_dev, const int* __restrict__ leaves, BoxArrays B, const double* __restrict__ xs, int64_t N,
               const double* __restrict__ rs, Tab<T> tab, double s, T* __restrict__ proxy) {
     static_assert(MAXP % 4 == 0, "rows are read as four-vectors");
     const int p = tab.p, p2 = p * p, drho = tab.d_rho, hq = (p + 1) / 2;
@@ -143,6 +144,7 @@ __global__ void __launch_bounds__((MAXP / 2 * MAXP + 31) / 32 * 32, sizeof(T) ==
     const bool active = q < hq * p;
     const int jb = active ? q / p : 0, jc = active ? q % p : 0;
     const bool second = active && jb + hq < p;
+    const int nleaf = *nleaf_dev;
     for (int li = blockIdx.x; li < nleaf; li += gridDim.x) {
         const int box = leaves[li];
         const int l = B.level[box];
