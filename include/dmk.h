@@ -131,7 +131,8 @@ typedef struct {
     int64_t n_direct_entries;  /* (target leaf, source box) entries of the direct lists          */
     int32_t kernel_launches;   /* CUDA kernels launched by the last evaluation                   */
     int32_t fit_terms;         /* Chebyshev terms of the residual function q used by the path    */
-    float stage_ms[8];         /* last eval: tree, upward, root, plane waves, shift, leaf, total, 0 */
+    float stage_ms[10];        /* last eval: tree, upward, root, plane waves, shift, leaf, total,
+                                  residual kernel, expansion kernel, 0 (stages 7 and 8: p <= 24) */
 } dmk_stats_t;
 
 dmk_status_t dmk_get_stats(dmk_plan_t plan, dmk_stats_t* out);

@@ -66,7 +66,7 @@ struct dmk_plan_s {
     // workspace
     std::vector<DevBuf> bufs;
     unsigned char* h_meta = nullptr;   // pinned host staging for the small per-evaluation readbacks
-    cudaEvent_t ev[10] = {};
+    cudaEvent_t ev[11] = {};
     // residual sums (k_pair) run on their own stream beside the far field when pair_overlap is
     // set, at most pair_blocks resident blocks per SM (0: as many as fit)
     cudaStream_t side = nullptr;
@@ -1061,6 +1061,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     if (fast_leaf) {
         if (overlap) CK(cudaStreamWaitEvent(st, plan->ev_join, 0));
         else CKS(run_pair(st));
+        if (plan->timing) cudaEventRecord(plan->ev[10], st);
         switch (P.kernel) {
             case DMK_LAPLACE: CKS((gr ? launch_leafexp<T, DMK_LAPLACE, true> : launch_leafexp<T, DMK_LAPLACE, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo)); break;
             case DMK_STOKESLET: CKS((gr ? launch_leafexp<T, DMK_STOKESLET, true> : launch_leafexp<T, DMK_STOKESLET, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo)); break;
@@ -1109,9 +1110,10 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     S.fit_terms = tab.n_q;
     if (plan->timing) {
         float ms;
-        // stage 7: the residual kernel alone (on the side stream when it overlaps the far field)
-        const int map[8][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 5}, {5, 6}, {6, 7}, {0, 7}, {8, 9}};
-        for (int i = 0; i < 8; ++i) {
+        // stage 7: the residual kernel alone (on the side stream when it overlaps the far
+        // field); stage 8: the expansion kernel alone
+        const int map[9][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 5}, {5, 6}, {6, 7}, {0, 7}, {8, 9}, {10, 7}};
+        for (int i = 0; i < 9; ++i) {
             ms = 0;
             if (i < 7 || fast_leaf) cudaEventElapsedTime(&ms, plan->ev[map[i][0]], plan->ev[map[i][1]]);
             S.stage_ms[i] = ms;
@@ -1159,7 +1161,7 @@ dmk_status_t make_plan(int k, int D, const double L[3], double tol, int prec, in
         dmk_destroy(plan);
         return DMK_ERR_OOM;
     }
-    for (int i = 0; i < 10; ++i) cudaEventCreate(&plan->ev[i]);
+    for (int i = 0; i < 11; ++i) cudaEventCreate(&plan->ev[i]);
     if (cudaStreamCreateWithFlags(&plan->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&plan->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&plan->ev_join, cudaEventDisableTiming) != cudaSuccess ||
@@ -1293,7 +1295,7 @@ dmk_status_t dmk_destroy(dmk_plan_t plan) {
     if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
     if (plan->ev_join) cudaEventDestroy(plan->ev_join);
     if (plan->ev_cnt) cudaEventDestroy(plan->ev_cnt);
-    for (int i = 0; i < 10; ++i)
+    for (int i = 0; i < 11; ++i)
         if (plan->ev[i]) cudaEventDestroy(plan->ev[i]);
     if (plan->h_meta) cudaFreeHost(plan->h_meta);
     delete plan;

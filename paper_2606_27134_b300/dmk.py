@@ -31,11 +31,11 @@ class Stats(ctypes.Structure):
                 ("n_root_modes", ctypes.c_int32), ("n_levels", ctypes.c_int32), ("n_boxes", ctypes.c_int32),
                 ("n_leaves", ctypes.c_int32), ("n_nonleaf", ctypes.c_int32), ("n_pairs", ctypes.c_int64),
                 ("n_direct_entries", ctypes.c_int64), ("kernel_launches", ctypes.c_int32),
-                ("fit_terms", ctypes.c_int32), ("stage_ms", ctypes.c_float * 8)]
+                ("fit_terms", ctypes.c_int32), ("stage_ms", ctypes.c_float * 10)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "stage_ms"}
-        d["stage_ms"] = list(self.stage_ms)[:8]
+        d["stage_ms"] = list(self.stage_ms)[:9]
         return d
 
 

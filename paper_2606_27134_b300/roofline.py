@@ -14,7 +14,7 @@ the expansion kernel (k_leafexp) every target once.
 # workload, from one ncu capture of the kernel as it stands
 # (profiles/k_pair_laplace_2P_N1e5_mixed.md); None whenever the kernel has changed since the
 # capture.
-PAIR_TRAFFIC_BYTES = None
+PAIR_TRAFFIC_BYTES = 4.128e6 + 0.0
 
 SMS = 148
 FP32_LANES_PER_SM = 128
