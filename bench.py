@@ -291,9 +291,12 @@ def main():
         with Clocks(local_rank) as ck:
             ms, stats, wall, _ = timed(plan, args.steps, args.warmup)
         plan.set_timing(True)
-        _, st_t, _, _ = timed(plan, 3, 1)
+        _, st_t, _, _ = timed(plan, 5, 1)
         plan.set_timing(False)
-        prec_results[prec] = dict(ms=ms, stats=stats[-1], clocks=ck.summary(), stage=st_t[-1]["stage_ms"], wall=wall,
+        # per-stage median over the timing steps (the tree stage holds host round trips and
+        # varies from step to step)
+        stage_med = [statistics.median(st["stage_ms"][i] for st in st_t) for i in range(len(st_t[0]["stage_ms"]))]
+        prec_results[prec] = dict(ms=ms, stats=stats[-1], clocks=ck.summary(), stage=stage_med, wall=wall,
                                   plan=plan)
     # end-to-end through the host-buffer entry point (copies inside the timed region)
     plan_m = prec_results["mixed"]["plan"]
