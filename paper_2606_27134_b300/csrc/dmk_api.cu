@@ -482,33 +482,6 @@ dmk_status_t launch_leaf(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int* le
     return DMK_OK;
 }
 
-template <class T, int K>
-dmk_status_t launch_leaf_generic(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int* leaves, BoxArrays B,
-                                 const T* local, const double* xs, int64_t N, const int* doffs, const DirectEntry* dl,
-                                 LeafOut lo, bool grad) {
-    const int p3 = tab.p * tab.p * tab.p;
-    constexpr int DU = (K == DMK_LAPLACE) ? 1 : 3;
-    size_t bytes = (size_t)(DU + 2) * p3 * sizeof(T);
-    Evaluator<T> ev(plan, tab);
-    Place pl;
-    unsigned char* scr = nullptr;
-    dmk_status_t s = ev.place(bytes, nleaf, pl, &scr);
-    if (s != DMK_OK) return s;
-    size_t dyn = pl.use_smem ? bytes : 0;
-    if (grad) {
-        s = set_smem(plan, k_leaf<T, K, true>, dyn);
-        if (s != DMK_OK) return s;
-        k_leaf<T, K, true><<<pl.grid, kLeafThreads, dyn, plan->stream>>>(nleaf, leaves, B, tab, plan->geo, local, xs,
-                                                                         N, doffs, dl, lo, scr, bytes, pl.use_smem);
-    } else {
-        s = set_smem(plan, k_leaf<T, K, false>, dyn);
-        if (s != DMK_OK) return s;
-        k_leaf<T, K, false><<<pl.grid, kLeafThreads, dyn, plan->stream>>>(nleaf, leaves, B, tab, plan->geo, local, xs,
-                                                                          N, doffs, dl, lo, scr, bytes, pl.use_smem);
-    }
-    return DMK_OK;
-}
-
 struct TreeInfo {
     int nlev = 0;                 // number of levels
     std::vector<int> ncell, off, nR, nl_off;

@@ -987,11 +987,8 @@ struct Pair<T, DMK_ROTLET, GRAD> {
 template <int K> struct KScale { static constexpr double v = (K == DMK_LAPLACE) ? 0.07957747154594767 : 0.039788735772973836; };
 
 // ------------------------------------------------------------------------------------------
-// Leaf stage (Sec. 3.1.5): per target leaf,
-//  (1) Chebyshev coefficients of the local expansion (grid -> coefficients, 3 contractions);
-//  (2) evaluation of the expansion and its gradient at the targets (warp per target, lane = n3);
-//  (3) residual sums over the direct list (thread per target, sources staged in shared memory);
-//  (4) self correction (Sec. 2.4) and the FP64 write-back in input order.
+// Outputs and per-point inputs of the leaf stage (Sec. 3.1.5, Sec. 2.4): potentials and
+// gradients in input order, the sort permutation, strengths, self terms, FP32 point records.
 struct LeafOut {
     double* pot;
     double* grad;      // may be null
@@ -1002,210 +999,5 @@ struct LeafOut {
     const float4* pk;         // FP32 path: one record per sorted point (point_record layout)
 };
 
-constexpr int kLeafThreads = 128;
-constexpr int kLeafChunk = 128;
-
-template <class T, int K, bool GRAD>
-__global__ void __launch_bounds__(kLeafThreads) k_leaf(int nleaf, const int* __restrict__ leaves, BoxArrays B,
-                                                      Tab<T> tab, Geo g, const T* __restrict__ local,
-                                                      const double* __restrict__ xs, int64_t N,
-                                                      const int* __restrict__ doffs, const DirectEntry* __restrict__ dl,
-                                                      LeafOut out, unsigned char* scratch, size_t per_cta, int use_smem) {
-    using P = Pair<T, K, GRAD>;
-    constexpr int DR = P::DR, DU = P::DU, NR = DU * 4;
-    const int p = tab.p, p2 = p * p, p3 = p2 * p;
-    T* coef = reinterpret_cast<T*>(work_base(scratch, per_cta, use_smem));
-    T* t1 = coef + DU * p3;
-    T* t2 = t1 + p3;
-    __shared__ double res[kLeafChunk][NR];
-    __shared__ T srcx[kLeafThreads][3];
-    __shared__ T srcr[kLeafThreads][DR];
-    __shared__ T tv[kLeafThreads / 32][4][64];
-    __shared__ T fits[256];
-    for (int e = threadIdx.x; e < min(256, tab.n_q + tab.n_f + tab.n_g + tab.n_dq + tab.n_df + tab.n_dg); e += blockDim.x)
-        fits[e] = tab.fit[e];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int li = blockIdx.x; li < nleaf; li += gridDim.x) {
-        const int box = leaves[li];
-        const int l = B.level[box];
-        const double r = g.s / (double)(1 << l), half = 0.5 * r;
-        const double c[3] = {(B.ix[3 * box] + 0.5) * r, (B.ix[3 * box + 1] + 0.5) * r, (B.ix[3 * box + 2] + 0.5) * r};
-        const int st = B.start[box], en = B.end[box];
-        // (1) coefficients
-        for (int j = 0; j < DU; ++j) {
-            const T* u = local + ((size_t)box * DU + j) * p3;
-            __syncthreads();
-            for (int e = threadIdx.x; e < p3; e += blockDim.x) {
-                const int i12 = e / p, n3 = e % p;
-                T v = 0;
-                for (int k = 0; k < p; ++k) v = fma(tab.Cm[n3 * p + k], u[i12 * p + k], v);
-                t1[e] = v;
-            }
-            __syncthreads();
-            for (int e = threadIdx.x; e < p3; e += blockDim.x) {
-                const int i1 = e / p2, n2 = (e / p) % p, n3 = e % p;
-                T v = 0;
-                for (int k = 0; k < p; ++k) v = fma(tab.Cm[n2 * p + k], t1[(i1 * p + k) * p + n3], v);
-                t2[e] = v;
-            }
-            __syncthreads();
-            T* cj = coef + (size_t)j * p3;
-            for (int e = threadIdx.x; e < p3; e += blockDim.x) {
-                const int n1 = e / p2, rr = e % p2;
-                T v = 0;
-                for (int k = 0; k < p; ++k) v = fma(tab.Cm[n1 * p + k], t2[k * p2 + rr], v);
-                cj[e] = v;
-            }
-        }
-        __syncthreads();
-        for (int t0 = st; t0 < en; t0 += kLeafChunk) {
-            const int nt = min(kLeafChunk, en - t0);
-            // (2) Chebyshev evaluation, warp per target
-            for (int tt = warp; tt < nt; tt += nwarp) {
-                const int tg = t0 + tt;
-                T xi[3];
-                for (int a = 0; a < 3; ++a) {
-                    T v = (T)((xs[a * N + tg] - c[a]) / half);
-                    xi[a] = v > T(1) ? T(1) : (v < T(-1) ? T(-1) : v);
-                }
-                // T_n and T_n' for the x and y axes into shared memory (lane n), z kept in registers
-                T Tz0 = 0, Tz1 = 0, dTz0 = 0, dTz1 = 0;
-                {
-                    T Ta[3] = {1, 1, 1}, Tb[3] = {xi[0], xi[1], xi[2]};
-                    T Ua[3] = {1, 1, 1}, Ub[3] = {2 * xi[0], 2 * xi[1], 2 * xi[2]};
-                    for (int n = 0; n < p; ++n) {
-                        T Tn[3], dTn[3];
-                        for (int a = 0; a < 3; ++a) {
-                            if (n == 0) { Tn[a] = 1; dTn[a] = 0; }
-                            else if (n == 1) { Tn[a] = xi[a]; dTn[a] = 1; }
-                            else {
-                                const T Tnew = 2 * xi[a] * Tb[a] - Ta[a];
-                                Ta[a] = Tb[a]; Tb[a] = Tnew;
-                                Tn[a] = Tnew;
-                                // T_n' = n U_{n-1}; U advanced to index n-1
-                                const T Unew = (n - 1 >= 2) ? (2 * xi[a] * Ub[a] - Ua[a]) : Ub[a];
-                                if (n - 1 >= 2) { Ua[a] = Ub[a]; Ub[a] = Unew; }
-                                dTn[a] = (T)n * Unew;
-                            }
-                        }
-                        if (lane == (n & 31)) {
-                            if (n < 32) { Tz0 = Tn[2]; dTz0 = dTn[2]; } else { Tz1 = Tn[2]; dTz1 = dTn[2]; }
-                        }
-                        if (lane == 0) {
-                            tv[warp][0][n] = Tn[0]; tv[warp][1][n] = dTn[0];
-                            tv[warp][2][n] = Tn[1]; tv[warp][3][n] = dTn[1];
-                        }
-                    }
-                }
-                __syncwarp();
-                for (int j = 0; j < DU; ++j) {
-                    const T* cj = coef + (size_t)j * p3;
-                    T S[2] = {0, 0}, Sx[2] = {0, 0}, Sy[2] = {0, 0};
-                    for (int h = 0; h < 2; ++h) {
-                        const int n3 = lane + 32 * h;
-                        if (n3 >= p) continue;
-                        for (int n1 = 0; n1 < p; ++n1) {
-                            T a0 = 0, a1 = 0;
-                            const T* row = cj + (size_t)n1 * p2 + n3;
-                            for (int n2 = 0; n2 < p; ++n2) {
-                                const T cv = row[n2 * p];
-                                a0 = fma(tv[warp][2][n2], cv, a0);
-                                a1 = fma(tv[warp][3][n2], cv, a1);
-                            }
-                            S[h] = fma(tv[warp][0][n1], a0, S[h]);
-                            Sx[h] = fma(tv[warp][1][n1], a0, Sx[h]);
-                            Sy[h] = fma(tv[warp][0][n1], a1, Sy[h]);
-                        }
-                    }
-                    T v = S[0] * Tz0 + S[1] * Tz1;
-                    T gx = Sx[0] * Tz0 + Sx[1] * Tz1;
-                    T gy = Sy[0] * Tz0 + Sy[1] * Tz1;
-                    T gz = S[0] * dTz0 + S[1] * dTz1;
-                    for (int o = 16; o > 0; o >>= 1) {
-                        v += __shfl_xor_sync(0xffffffffu, v, o);
-                        gx += __shfl_xor_sync(0xffffffffu, gx, o);
-                        gy += __shfl_xor_sync(0xffffffffu, gy, o);
-                        gz += __shfl_xor_sync(0xffffffffu, gz, o);
-                    }
-                    if (lane == 0) {
-                        const double sc = 1.0 / half;
-                        res[tt][j] = (double)v;
-                        res[tt][DU + 0 * DU + j] = (double)gx * sc;
-                        res[tt][DU + 1 * DU + j] = (double)gy * sc;
-                        res[tt][DU + 2 * DU + j] = (double)gz * sc;
-                    }
-                }
-                __syncwarp();
-            }
-            __syncthreads();
-            // (3) residual sums: thread per target
-            const int tt = threadIdx.x;
-            const bool act = tt < nt;
-            T xt[3] = {0, 0, 0};
-            if (act)
-                for (int a = 0; a < 3; ++a) xt[a] = (T)(xs[a * N + t0 + tt] - c[a]);
-            T acc[DU], gacc[3 * DU];
-            for (int j = 0; j < DU; ++j) acc[j] = 0;
-            for (int j = 0; j < 3 * DU; ++j) gacc[j] = 0;
-            const int e0 = doffs[li], e1 = doffs[li + 1];
-            for (int e = e0; e < e1; ++e) {
-                const DirectEntry de = dl[e];
-                const int lev = de.code >> 6;
-                const double sh[3] = {(double)(((de.code) & 3) - 1) * g.L[0], (double)(((de.code >> 2) & 3) - 1) * g.L[1],
-                                      (double)(((de.code >> 4) & 3) - 1) * g.L[2]};
-                const T inv_nu = (T)((double)(1 << lev) / g.s);
-                const T nu2 = T(1) / (inv_nu * inv_nu);
-                T pacc[DU], pg[3 * DU];
-                for (int j = 0; j < DU; ++j) pacc[j] = 0;
-                for (int j = 0; j < 3 * DU; ++j) pg[j] = 0;
-                for (int s0 = de.start; s0 < de.end; s0 += kLeafThreads) {
-                    const int ns = min(kLeafThreads, de.end - s0);
-                    __syncthreads();
-                    if (threadIdx.x < ns) {
-                        const int si = s0 + threadIdx.x;
-                        for (int a = 0; a < 3; ++a) srcx[threadIdx.x][a] = (T)(xs[a * N + si] + sh[a] - c[a]);
-                        for (int a = 0; a < DR; ++a) srcr[threadIdx.x][a] = (T)out.rs[(int64_t)si * DR + a];
-                    }
-                    __syncthreads();
-                    if (act) {
-                        for (int k = 0; k < ns; ++k) {
-                            const T dx = xt[0] - srcx[k][0], dy = xt[1] - srcx[k][1], dz = xt[2] - srcx[k][2];
-                            const T r2 = dx * dx + dy * dy + dz * dz;
-                            if (r2 < nu2 && r2 > T(0)) {
-                                P::eval(ChebSeries<T>(tab, fits, r2, inv_nu), dx, dy, dz, r2, inv_nu, srcr[k], pacc,
-                                        pg);
-                            }
-                        }
-                    }
-                }
-                for (int j = 0; j < DU; ++j) acc[j] += pacc[j];
-                for (int j = 0; j < 3 * DU; ++j) gacc[j] += pg[j];
-            }
-            // (4) self correction and write-back (FP64)
-            if (act) {
-                const int tg = t0 + tt;
-                const int oi = out.perm[tg];
-                const double inv_nuT = 1.0 / r;       // nu at the leaf level = box side
-                const double ks = KScale<K>::v;
-                const double* rt = out.rs + (int64_t)tg * DR;
-                for (int j = 0; j < DU; ++j) {
-                    double v = res[tt][j] + ks * (double)acc[j];
-                    for (int a = 0; a < DR; ++a) v -= out.self_val[j * DR + a] * inv_nuT * rt[a];
-                    out.pot[(int64_t)oi * DU + j] = v;
-                }
-                if (GRAD && out.grad) {
-                    const double in3 = inv_nuT * inv_nuT * inv_nuT;
-                    for (int i = 0; i < 3; ++i)
-                        for (int j = 0; j < DU; ++j) {
-                            double v = res[tt][DU + i * DU + j] + ks * (double)gacc[i * DU + j];
-                            for (int a = 0; a < DR; ++a) v -= out.self_grad[(i * DU + j) * DR + a] * in3 * rt[a];
-                            out.grad[((int64_t)oi * 3 + i) * DU + j] = v;
-                        }
-                }
-            }
-            __syncthreads();
-        }
-    }
-}
 
 }  // namespace dmk
