@@ -1,4 +1,5 @@
-"""Independent reference sums for the Laplace kernel (oracle; test infrastructure only).
+"""Independent reference sums for the Laplace kernel and, D = 3, the Stokeslet (oracle; test
+infrastructure only).
 
 These do not use the DMK machinery, the PSWF window or truncated kernels: they
 evaluate Eq. periodic_sum for K = 1/(4 pi r) through the classical Gaussian (Ewald)
@@ -18,6 +19,9 @@ H_M-hat = exp(-k^2 nu^2/4)/k^2 (Eq. Hhat_k):
                closed form for k1 = 0;
   self         - rho_t lim_{r->0} erf(r/nu)/(4 pi r) = - rho_t/(2 pi^{3/2} nu).
 D = 0 is the plain O(N^2) sum.  Gradients (the field) are returned as well.
+
+Stokeslet, D = 3: Hasimoto's split of the Oseen tensor (below), real-space images within the
+cutoff plus the Fourier sum over k != 0, minus the target's own smooth part.
 """
 import numpy as np
 import scipy.special as sp
@@ -207,3 +211,90 @@ def laplace_reference(D, L, x, q, nu=None, grad=False):
     if nu is None:
         nu = min(L[:D]) / 4
     return {3: ewald_3p, 2: ewald_2p, 1: ewald_1p}[D](x, q, list(L), nu, grad)
+
+
+# ---- Stokeslet, triply periodic: Hasimoto's split of the Oseen tensor ----------------------
+#
+# G(x) = (delta/r + x x^T/r^3)/(8 pi), G-hat(k) = (I - k k^T/k^2)/k^2 (unit viscosity), split as
+# G-hat = G-hat (1 - phi) + G-hat phi with phi(k) = (1 + k^2 nu^2/4) e^{-k^2 nu^2/4} (Hasimoto,
+# J. Fluid Mech. 5 (1959)).  The smooth part in real space, written with the Laplace Gaussian
+# split H_M = erf(r/nu)/(4 pi r) (H_M-hat = e^{-k^2 nu^2/4}/k^2), the Gaussian
+# g = e^{-r^2/nu^2}/(pi^{3/2} nu^3) (g-hat = e^{-k^2 nu^2/4}) and the radial V with
+# laplacian(V) = H_M (V-hat = -e^{-k^2 nu^2/4}/k^4):
+#
+#   G^F = I (H_M + nu^2/4 g) - grad grad V + nu^2/4 grad grad H_M,
+#   r^2 V'(r) = [(r^2/2 - nu^2/4) erf(r/nu) + nu r/(2 sqrt(pi)) e^{-r^2/nu^2}]/(4 pi),
+#
+# and G^R = G - G^F decays like e^{-r^2/nu^2}.  grad grad f = f'' xx^T/r^2 + f'/r (I - xx^T/r^2)
+# for radial f.  G^F(0) = I/(2 pi^{3/2} nu) (the smooth self term).  The tests check G^F against
+# the inverse Fourier transform of G-hat phi by radial quadrature.
+
+def _stokes_smooth_radial(r, nu):
+    """(a, b) with G^F(x) = a(r) I + b(r) x x^T/r^2 (r > 0; complex r allowed)."""
+    E = sp.erf(r / nu)
+    e = np.exp(-(r / nu) ** 2)
+    H = E / (4 * np.pi * r)
+    Hp = (2 * r / (SQPI * nu) * e - E) / (4 * np.pi * r ** 2)
+    Hpp = (-4 * e / (SQPI * nu ** 3) - 4 * e / (SQPI * nu * r ** 2) + 2 * E / r ** 3) / (4 * np.pi)
+    g = e / (np.pi ** 1.5 * nu ** 3)
+    Nr = (r * r / 2 - nu * nu / 4) * E + nu * r / (2 * SQPI) * e
+    Vp = Nr / (4 * np.pi * r ** 2)
+    Vpp = (r * r * E - 2 * Nr) / (4 * np.pi * r ** 3)
+    q = nu * nu / 4
+    # I part: H + q g - V'/r + q H'/r ; xx part: -(V'' - V'/r) + q (H'' - H'/r)
+    a = H + q * g - Vp / r + q * Hp / r
+    b = -(Vpp - Vp / r) + q * (Hpp - Hp / r)
+    return a, b
+
+
+def stokes_smooth(x, nu):
+    """G^F at displacements x (n, 3), r > 0: (n, 3, 3)."""
+    r = np.sqrt(np.sum(x * x, axis=-1))
+    a, b = _stokes_smooth_radial(r, nu)
+    xx = x[:, :, None] * x[:, None, :] / (r * r)[:, None, None]
+    return a[:, None, None] * np.eye(3) + b[:, None, None] * xx
+
+
+def stokeslet_ewald_3p(xt, xs, f, L, nu):
+    """Velocities u_t = sum_s sum*_p G(x_t - x_s + p) f_s for D = 3 (k = 0 excluded), at the
+    targets xt (n, 3; may be complex for complex-step derivatives) from sources xs (N, 3)
+    with forces f (N, 3); target t and source t are the same point (p = 0 skipped)."""
+    N = xs.shape[0]
+    rc = 6.5 * nu
+    n = [int(np.ceil(rc / L[i])) + 1 for i in range(3)]
+    u = np.zeros((xt.shape[0], 3), dtype=np.result_type(xt, 1.0))
+    same = np.eye(xt.shape[0], N, dtype=bool)
+    for a in range(-n[0], n[0] + 1):
+        for b in range(-n[1], n[1] + 1):
+            for c in range(-n[2], n[2] + 1):
+                p = np.array([a * L[0], b * L[1], c * L[2]])
+                dx = xt[:, None, :] - xs[None, :, :] + p
+                keep = ~same if (a == 0 and b == 0 and c == 0) else np.ones_like(same)
+                d = dx[keep]
+                r = np.sqrt(np.sum(d * d, axis=-1))
+                aa, bb = _stokes_smooth_radial(r, nu)
+                # G^R = G - G^F = (1/(8 pi r) - a) I + (1/(8 pi r) - b) x x^T/r^2
+                ci = 1 / (8 * np.pi * r) - aa
+                cx = 1 / (8 * np.pi * r) - bb
+                fs = np.broadcast_to(f[None, :, :], dx.shape)[keep]
+                v = ci[:, None] * fs + (cx * np.sum(d * fs, axis=-1) / (r * r))[:, None] * d
+                tt = np.nonzero(keep)[0]
+                np.add.at(u, tt, v)
+    # Fourier part, real form (analytic in xt)
+    km = _kmax(nu)
+    m = [int(np.ceil(km * L[i] / (2 * np.pi))) for i in range(3)]
+    ax = [2 * np.pi * np.arange(-m[i], m[i] + 1) / L[i] for i in range(3)]
+    kk = np.stack(np.meshgrid(*ax, indexing="ij"), -1).reshape(-1, 3)
+    k2 = np.sum(kk * kk, axis=1)
+    kk, k2 = kk[k2 > 0], k2[k2 > 0]
+    phi = (1 + k2 * nu * nu / 4) * np.exp(-k2 * nu * nu / 4) / k2 / (L[0] * L[1] * L[2])
+    ks = xs @ kk.T                                     # (N, nk)
+    C = np.cos(ks).T @ f                               # (nk, 3) sum_s f_s cos(k x_s)
+    S = np.sin(ks).T @ f
+    kt = xt @ kk.T                                     # (n, nk)
+    for A, trig in ((C, np.cos(kt)), (S, np.sin(kt))):
+        Ap = A - kk * (np.sum(kk * A, axis=1) / k2)[:, None]     # (I - k k^T/k^2) A
+        u = u + trig @ (phi[:, None] * Ap)
+    # the target's own smooth part
+    u = u - f[: xt.shape[0]] / (2 * np.pi ** 1.5 * nu)
+    return u

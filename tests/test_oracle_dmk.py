@@ -5,6 +5,11 @@
 * D = 3: the NaCl Madelung constant (tests/golden/madelung_nacl.txt).
 * Stokes kernels, D = 0: the O(N^2) free-space sum of App. B's kernels.
 * Rotlet, D = 3: -1/2 curl of three Laplace potentials (Eq. rotlet_def_deriv).
+* Stokeslet, D = 3: Hasimoto's Ewald split of the Oseen tensor (oracle/ewald.py; its smooth
+  part checked against the inverse Fourier transform by quadrature), velocities and gradients.
+* Stresslet, D = 3: the stress of the Stokeslet flow, T_jlm = -delta_jm P_l + d_m G_jl + d_j G_ml
+  with the Stokeslet pressure P_l = -d_l (1/(4 pi r)), mode by mode for k != 0, so the periodic
+  stresslet sum equals Stokeslet and Laplace gradient sums.
 * Invariants: permutation, linearity, symmetry, periodic translation; 2:1 balance.
 """
 import itertools
@@ -148,6 +153,80 @@ def test_rotlet_is_curl_of_laplace(D, L):
     eps[0, 2, 1] = eps[2, 1, 0] = eps[1, 0, 2] = -1
     want = -0.5 * np.einsum("jlm,tlm->tj", eps, gl)
     assert rel(r.u, want) < 1e-8
+
+
+@pytest.mark.parametrize("r", [0.05, 0.3, 0.7, 1.5])
+def test_hasimoto_smooth_part_is_inverse_transform(r):
+    """G^F(x) of oracle/ewald.py equals (2 pi)^-3 int (I - k k^T/k^2) phi(k)/k^2 e^{ikx} d^3k,
+    phi = (1 + k^2 nu^2/4) e^{-k^2 nu^2/4}, by radial quadrature: the angular mean of
+    k_j k_l/k^2 e^{ikx} is j1(kr)/(kr) delta_jl - j2(kr) x_j x_l/r^2; and G^F(0) = I/(2 pi^1.5 nu)."""
+    nu = 0.3
+    xh = np.array([0.48, -0.6, 0.64])
+    xh /= np.linalg.norm(xh)
+    h = lambda k: (1 + k * k * nu * nu / 4) * np.exp(-k * k * nu * nu / 4)
+    a = quad(lambda k: h(k) * (sp.spherical_jn(0, k * r) - sp.spherical_jn(1, k * r) / (k * r)), 0, 60 / nu,
+             limit=500)[0] / (2 * np.pi ** 2)
+    b = quad(lambda k: h(k) * sp.spherical_jn(2, k * r), 0, 60 / nu, limit=500)[0] / (2 * np.pi ** 2)
+    want = a * np.eye(3) + b * np.outer(xh, xh)
+    got = ewald.stokes_smooth((r * xh)[None], nu)[0]
+    assert np.abs(got - want).max() < 1e-12 * np.abs(want).max()
+    self_q = quad(lambda k: h(k) * 2 / 3, 0, 60 / nu)[0] / (2 * np.pi ** 2)
+    assert self_q == pytest.approx(1 / (2 * np.pi ** 1.5 * nu), rel=1e-12)
+    small = ewald.stokes_smooth((1e-3 * xh)[None], nu)[0]
+    assert np.abs(small - np.eye(3) / (2 * np.pi ** 1.5 * nu)).max() < 1e-5 / nu
+
+
+@pytest.mark.parametrize("L", [[1, 1, 1], [1, 1, 2]])
+def test_stokeslet_3p_vs_ewald(L):
+    """D = 3 Stokeslet: oracle vs Hasimoto's Ewald sum (two split parameters agree to roundoff),
+    velocities and target gradients (complex step of the Ewald sum)."""
+    N = 50
+    x = workloads.mixed_points(N, L, seed=61)
+    f = workloads.stokes_strengths("stokeslet", N, seed=62)
+    r = evaluate("stokeslet", 3, L, 1e-9, x, f, n_s=12, grad=True)
+    e1 = ewald.stokeslet_ewald_3p(x, x, f, L, 0.2 * min(L))
+    e2 = ewald.stokeslet_ewald_3p(x, x, f, L, 0.3 * min(L))
+    assert rel(e1, e2) < 1e-13
+    assert rel(r.u, e1) < 1e-8
+    h = 1e-20
+    g = np.zeros((N, 3, 3))
+    for i in range(3):
+        xt = x.astype(complex)
+        xt[:, i] += 1j * h
+        g[:, i, :] = ewald.stokeslet_ewald_3p(xt, x, f, L, 0.25 * min(L)).imag / h
+    assert rel(r.grad, g) < 1e-8
+
+
+def test_stresslet_3p_is_stokeslet_stress():
+    """D = 3 stresslet (rho[s, 3l+m] = Q_lm) = sum_m [d_m u^(m)_j + d_j u^(m)_m] + sum_l d_l phi^(lj),
+    u^(m) the Stokeslet velocity of the forces Q_lm (l = 0..2), phi^(lj) the Laplace potential of
+    the charges Q_lj; every sum without its k = 0 mode.  Checked first in free space on the
+    kernels themselves."""
+    KL, KG, KT = Kernel("laplace"), Kernel("stokeslet"), Kernel("stresslet")
+    x0 = np.array([0.31, -0.52, 0.17])
+    hh = 1e-6
+    dG = np.zeros((3, 3, 3))
+    P = np.zeros(3)
+    for m in range(3):
+        e = np.zeros(3)
+        e[m] = hh
+        dG[m] = (KG.full((x0 + e)[None])[0] - KG.full((x0 - e)[None])[0]) / (2 * hh)
+        P[m] = -(KL.full((x0 + e)[None])[0, 0, 0] - KL.full((x0 - e)[None])[0, 0, 0]) / (2 * hh)
+    Tc = np.zeros((3, 3, 3))
+    for j, l, m in itertools.product(range(3), repeat=3):
+        Tc[j, l, m] = -(j == m) * P[l] + dG[m, j, l] + dG[j, m, l]
+    assert np.abs(KT.full(x0[None])[0] - Tc.reshape(3, 9)).max() < 1e-8 * np.abs(Tc).max()
+    N, L, tol = 60, [1, 1, 1], 1e-8
+    x = workloads.mixed_points(N, L, seed=51)
+    Q = workloads.stokes_strengths("stresslet", N, seed=52)
+    uT = evaluate("stresslet", 3, L, tol, x, Q, n_s=12).u
+    want = np.zeros((N, 3))
+    for m in range(3):
+        g = evaluate("stokeslet", 3, L, tol, x, Q[:, [3 * l + m for l in range(3)]], n_s=12, grad=True).grad
+        want += g[:, m, :] + g[:, :, m]
+    for l, j in itertools.product(range(3), repeat=2):
+        want[:, j] += evaluate("laplace", 3, L, tol, x, Q[:, 3 * l + j], n_s=12, grad=True).grad[:, l, 0]
+    assert rel(uT, want) < 1e-8
 
 
 def test_invariants():
