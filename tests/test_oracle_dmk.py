@@ -7,9 +7,10 @@
 * Rotlet, D = 3: -1/2 curl of three Laplace potentials (Eq. rotlet_def_deriv).
 * Stokeslet, D = 3: Hasimoto's Ewald split of the Oseen tensor (oracle/ewald.py; its smooth
   part checked against the inverse Fourier transform by quadrature), velocities and gradients.
-* Stresslet, D = 3: the stress of the Stokeslet flow, T_jlm = -delta_jm P_l + d_m G_jl + d_j G_ml
-  with the Stokeslet pressure P_l = -d_l (1/(4 pi r)), mode by mode for k != 0, so the periodic
-  stresslet sum equals Stokeslet and Laplace gradient sums.
+* Stresslet, D = 3, 2, 1: the stress of the Stokeslet flow, T_jlm = -delta_jm P_l + d_m G_jl +
+  d_j G_ml with the Stokeslet pressure P_l = -d_l (1/(4 pi r)), mode by mode for k != 0, so the
+  periodic stresslet sum equals Stokeslet and Laplace gradient sums; the Stokeslet flows are
+  divergence-free.
 * Invariants: permutation, linearity, symmetry, periodic translation; 2:1 balance.
 """
 import itertools
@@ -197,11 +198,13 @@ def test_stokeslet_3p_vs_ewald(L):
     assert rel(r.grad, g) < 1e-8
 
 
-def test_stresslet_3p_is_stokeslet_stress():
-    """D = 3 stresslet (rho[s, 3l+m] = Q_lm) = sum_m [d_m u^(m)_j + d_j u^(m)_m] + sum_l d_l phi^(lj),
+@pytest.mark.parametrize("D,L", [(3, [1, 1, 1]), (2, [1, 1, 0.5]), (1, [1, 1, 1])])
+def test_stresslet_is_stokeslet_stress(D, L):
+    """Stresslet (rho[s, 3l+m] = Q_lm) = sum_m [d_m u^(m)_j + d_j u^(m)_m] + sum_l d_l phi^(lj),
     u^(m) the Stokeslet velocity of the forces Q_lm (l = 0..2), phi^(lj) the Laplace potential of
-    the charges Q_lj; every sum without its k = 0 mode.  Checked first in free space on the
-    kernels themselves."""
+    the charges Q_lj; every sum without its k = 0 mode.  For D < 3 every component of Q has zero
+    sum, so that each Laplace and Stokeslet sum is defined.  Checked first in free space on the
+    kernels themselves.  The Stokeslet flows are divergence-free: sum_j d_j u^(m)_j = 0."""
     KL, KG, KT = Kernel("laplace"), Kernel("stokeslet"), Kernel("stresslet")
     x0 = np.array([0.31, -0.52, 0.17])
     hh = 1e-6
@@ -216,16 +219,19 @@ def test_stresslet_3p_is_stokeslet_stress():
     for j, l, m in itertools.product(range(3), repeat=3):
         Tc[j, l, m] = -(j == m) * P[l] + dG[m, j, l] + dG[j, m, l]
     assert np.abs(KT.full(x0[None])[0] - Tc.reshape(3, 9)).max() < 1e-8 * np.abs(Tc).max()
-    N, L, tol = 60, [1, 1, 1], 1e-8
-    x = workloads.mixed_points(N, L, seed=51)
+    N, tol = 60, 1e-8
+    x = workloads.mixed_points(N, L, seed=51, D=D)
     Q = workloads.stokes_strengths("stresslet", N, seed=52)
-    uT = evaluate("stresslet", 3, L, tol, x, Q, n_s=12).u
+    if D < 3:
+        Q = Q - Q.mean(axis=0)
+    uT = evaluate("stresslet", D, L, tol, x, Q, n_s=12).u
     want = np.zeros((N, 3))
     for m in range(3):
-        g = evaluate("stokeslet", 3, L, tol, x, Q[:, [3 * l + m for l in range(3)]], n_s=12, grad=True).grad
+        g = evaluate("stokeslet", D, L, tol, x, Q[:, [3 * l + m for l in range(3)]], n_s=12, grad=True).grad
         want += g[:, m, :] + g[:, :, m]
+        assert np.linalg.norm(np.einsum("tjj->t", g)) < 1e-8 * np.linalg.norm(g)
     for l, j in itertools.product(range(3), repeat=2):
-        want[:, j] += evaluate("laplace", 3, L, tol, x, Q[:, 3 * l + j], n_s=12, grad=True).grad[:, l, 0]
+        want[:, j] += evaluate("laplace", D, L, tol, x, Q[:, 3 * l + j], n_s=12, grad=True).grad[:, l, 0]
     assert rel(uT, want) < 1e-8
 
 
