@@ -22,13 +22,14 @@
  *     outputs are left unspecified and dmk_last_error() gives a one-line detail.
  *   - A plan owns its tables and a device workspace that grows on demand; calls on one
  *     plan must not overlap (the plan is not thread-safe).  Work is enqueued on the plan's
- *     CUDA stream and, for the residual sums of the leaf stage (p <= 24), on a second
- *     stream the plan owns, ordered against the first by events: those sums need only the
- *     tree and run beside the far field.  dmk_eval returns after all of it is complete (the
- *     host waits for the small readbacks of the tree build and for the device status word).
- *   - Environment, read when a plan is created: DMK_PAIR_OVERLAP=0 keeps the residual sums
- *     on the plan's stream, after the far field; DMK_PAIR_BLOCKS=n caps their resident
- *     blocks per SM while they run beside the far field (default 2; 0 = no cap).
+ *     CUDA stream (with DMK_PAIR_OVERLAP=1, below, the residual sums of the leaf stage go to
+ *     a second stream the plan owns, ordered against the first by events).  dmk_eval
+ *     returns after all of it is complete (the host waits for the small readbacks of the
+ *     tree build and for the device status word).
+ *   - Environment, read when a plan is created: DMK_PAIR_OVERLAP=1 runs the residual sums
+ *     (p <= 24; they need only the tree) beside the far field on the second stream;
+ *     DMK_PAIR_BLOCKS=n caps their resident blocks per SM while they do (default 2;
+ *     0 = no cap).  The default order is serial.
  */
 #ifndef DMK_B300_H
 #define DMK_B300_H

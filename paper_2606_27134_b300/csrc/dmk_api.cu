@@ -68,10 +68,12 @@ struct dmk_plan_s {
     unsigned char* h_meta = nullptr;   // pinned host staging for the small per-evaluation readbacks
     cudaEvent_t ev[11] = {};
     // residual sums (k_pair) run on their own stream beside the far field when pair_overlap is
-    // set, at most pair_blocks resident blocks per SM (0: as many as fit)
+    // set, at most pair_blocks resident blocks per SM (0: as many as fit).  Off by default: on
+    // the larger and adaptive workloads the far-field kernels beside it slowed down more than
+    // the overlap saved
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_cnt = nullptr;
-    int pair_overlap = 1;
+    int pair_overlap = 0;
     int pair_blocks = 2;
     int n_sm = 148;
     // resident blocks per SM of the persistent kernels, by kernel
