@@ -106,8 +106,7 @@ dmk_status_t dmk_eval_host(dmk_plan_t plan, int64_t N, const double* points, con
 /* dmk_eval without any device allocation.  The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc at evaluation time -- applications whose
  * device memory is fully reserved by their own pool allocator and that must not let a
- * library allocate behind their back.  It cannot itself be captured into a CUDA graph: like
- * dmk_eval it waits on the host for the small readbacks of the tree build.
+ * library allocate behind their back.
  *   - Same arguments, layouts and results as dmk_eval (device arrays; the plan, created
  *     beforehand with dmk_plan/dmk_plan_ex, owns its tables).
  *   - All workspace comes from one file-scope static device array of 64 MiB (every GPU that

@@ -1,5 +1,5 @@
 """dmk_eval_static: the evaluation without device allocation, for callers that cannot call
-cudaMalloc while they evaluate (inside CUDA stream capture, or under an application's own
+cudaMalloc while they evaluate (applications whose device memory is held by their own
 memory pool).  It must return what dmk_eval returns, on consecutive calls that share its
 static workspace, and reject problems beyond its stated limits.
 
