@@ -1,5 +1,5 @@
-"""Independent reference sums for the Laplace kernel and, D = 3, the Stokeslet (oracle; test
-infrastructure only).
+"""Independent reference sums for the Laplace kernel and, D = 3 and 2, the Stokeslet (oracle;
+test infrastructure only).
 
 These do not use the DMK machinery, the PSWF window or truncated kernels: they
 evaluate Eq. periodic_sum for K = 1/(4 pi r) through the classical Gaussian (Ewald)
@@ -20,8 +20,10 @@ H_M-hat = exp(-k^2 nu^2/4)/k^2 (Eq. Hhat_k):
   self         - rho_t lim_{r->0} erf(r/nu)/(4 pi r) = - rho_t/(2 pi^{3/2} nu).
 D = 0 is the plain O(N^2) sum.  Gradients (the field) are returned as well.
 
-Stokeslet, D = 3: Hasimoto's split of the Oseen tensor (below), real-space images within the
-cutoff plus the Fourier sum over k != 0, minus the target's own smooth part.
+Stokeslet, D = 3 and D = 2: Hasimoto's split of the Oseen tensor (below), real-space images
+within the cutoff plus the Fourier sum over k != 0 (D = 2: the kappa_3 integrals in closed
+form, and the in-plane mode (0, 0) regularised for in-plane forces that sum to zero), minus the
+target's own smooth part.
 """
 import numpy as np
 import scipy.special as sp
@@ -255,13 +257,11 @@ def stokes_smooth(x, nu):
     return a[:, None, None] * np.eye(3) + b[:, None, None] * xx
 
 
-def stokeslet_ewald_3p(xt, xs, f, L, nu):
-    """Velocities u_t = sum_s sum*_p G(x_t - x_s + p) f_s for D = 3 (k = 0 excluded), at the
-    targets xt (n, 3; may be complex for complex-step derivatives) from sources xs (N, 3)
-    with forces f (N, 3); target t and source t are the same point (p = 0 skipped)."""
+def _stokes_real(xt, xs, f, L, periodic, nu):
+    """Real-space part: sum over the images within the cutoff of G^R(x_t - x_s + p) f_s."""
     N = xs.shape[0]
     rc = 6.5 * nu
-    n = [int(np.ceil(rc / L[i])) + 1 for i in range(3)]
+    n = [int(np.ceil(rc / L[i])) + 1 if periodic[i] else 0 for i in range(3)]
     u = np.zeros((xt.shape[0], 3), dtype=np.result_type(xt, 1.0))
     same = np.eye(xt.shape[0], N, dtype=bool)
     for a in range(-n[0], n[0] + 1):
@@ -280,6 +280,14 @@ def stokeslet_ewald_3p(xt, xs, f, L, nu):
                 v = ci[:, None] * fs + (cx * np.sum(d * fs, axis=-1) / (r * r))[:, None] * d
                 tt = np.nonzero(keep)[0]
                 np.add.at(u, tt, v)
+    return u
+
+
+def stokeslet_ewald_3p(xt, xs, f, L, nu):
+    """Velocities u_t = sum_s sum*_p G(x_t - x_s + p) f_s for D = 3 (k = 0 excluded), at the
+    targets xt (n, 3; may be complex for complex-step derivatives) from sources xs (N, 3)
+    with forces f (N, 3); target t and source t are the same point (p = 0 skipped)."""
+    u = _stokes_real(xt, xs, f, L, (True, True, True), nu)
     # Fourier part, real form (analytic in xt)
     km = _kmax(nu)
     m = [int(np.ceil(km * L[i] / (2 * np.pi))) for i in range(3)]
@@ -296,5 +304,72 @@ def stokeslet_ewald_3p(xt, xs, f, L, nu):
         Ap = A - kk * (np.sum(kk * A, axis=1) / k2)[:, None]     # (I - k k^T/k^2) A
         u = u + trig @ (phi[:, None] * Ap)
     # the target's own smooth part
+    u = u - f[: xt.shape[0]] / (2 * np.pi ** 1.5 * nu)
+    return u
+
+
+# ---- Stokeslet, doubly periodic (D = 2, x3 free) -----------------------------------------
+#
+# Same split; the Fourier part integrates G-hat phi over kappa_3 in closed form.  With
+# I_L(alpha, z) = int e^{-(alpha^2+k^2) nu^2/4}/(alpha^2+k^2) e^{ikz} dk (_int_2p) and
+# k^2 = alpha^2 + kappa_3^2, k = (k1, k2, kappa_3):
+#   I0 = int phi/k^2 e^{ikz}  = I_L + (sqrt(pi) nu/2) e^{-alpha^2 nu^2/4 - z^2/nu^2},
+#   I2 = int phi/k^4 e^{ikz}  = -d I_L/d(alpha^2),
+#   dI2/dz                    = -(z/2) I_L.
+# Per in-plane mode (k1, k2) != 0, M = int (I - k k^T/k^2) phi/k^2 e^{ikz} dk has the entries
+#   M_ab = I0 delta_ab - k_a k_b I2 (a, b in-plane),  M_a3 = M_3a = -k_a int kappa_3 phi/k^4 e^{ikz}
+#        = i k_a dI2/dz = -i k_a (z/2) I_L,  M_33 = I0 - (I0 - alpha^2 I2) = alpha^2 I2.
+# The mode (0, 0) projects out x3 and leaves, for in-plane forces that sum to zero,
+#   M_aa = int (e^{-k^2 nu^2/4} cos kz - 1)/k^2 dk + (sqrt(pi) nu/2) e^{-z^2/nu^2}.
+
+def _stokes_2p_modes(alpha, z, nu):
+    """(I0, I2, I_L) of the comment above, alpha > 0 (arrays; complex z allowed)."""
+    IL = _int_2p(alpha, z, nu)
+    E = np.exp(-alpha ** 2 * nu ** 2 / 4 - z ** 2 / nu ** 2)
+    w1 = alpha * nu / 2 + z / nu
+    w2 = alpha * nu / 2 - z / nu
+    dIL = -IL / alpha + np.pi / (2 * alpha) * E * (z * (sp.erfcx(w1) - sp.erfcx(w2)) - 2 * nu / SQPI)
+    I0 = IL + SQPI * nu / 2 * E
+    I2 = -dIL / (2 * alpha)
+    return I0, I2, IL
+
+
+def stokeslet_ewald_2p(xt, xs, f, L, nu):
+    """As stokeslet_ewald_3p for D = 2 (x1, x2 periodic, x3 free); the in-plane force
+    components must sum to zero (the (0, 0) mode drops their divergent constant)."""
+    u = _stokes_real(xt, xs, f, L, (True, True, False), nu)
+    km = _kmax(nu)
+    n = [int(np.ceil(km * L[i] / (2 * np.pi))) for i in range(2)]
+    A = 1.0 / (L[0] * L[1] * 2 * np.pi)
+    dx = xt[:, None, :] - xs[None, :, :]
+    z = dx[:, :, 2]
+    for a in range(-n[0], n[0] + 1):
+        for b in range(-n[1], n[1] + 1):
+            k1, k2 = 2 * np.pi * a / L[0], 2 * np.pi * b / L[1]
+            if a == 0 and b == 0:
+                I00 = -np.pi * (z * sp.erf(z / nu) + nu / SQPI * (np.exp(-(z / nu) ** 2) - 1))
+                w = A * (I00 + SQPI * nu / 2 * np.exp(-(z / nu) ** 2))
+                u[:, 0] = u[:, 0] + w @ f[:, 0]
+                u[:, 1] = u[:, 1] + w @ f[:, 1]
+                continue
+            al = np.hypot(k1, k2)
+            if al * nu / 2 > np.sqrt(44.0):
+                continue
+            I0, I2, IL = _stokes_2p_modes(al, z, nu)
+            th = k1 * dx[:, :, 0] + k2 * dx[:, :, 1]
+            c, sn = np.cos(th), np.sin(th)
+            kv = (k1, k2)
+            # real part of M e^{i th}: real entries times cos(th); the (a, 3) entries
+            # -i k_a (z/2) I_L give +k_a (z/2) I_L sin(th)
+            for j in range(3):
+                for l in range(3):
+                    if j < 2 and l < 2:
+                        term = ((I0 if j == l else 0.0) - kv[j] * kv[l] * I2) * c
+                    elif j == 2 and l == 2:
+                        term = (al * al * I2) * c
+                    else:
+                        ka = kv[j] if j < 2 else kv[l]
+                        term = ka * z / 2 * IL * sn
+                    u[:, j] = u[:, j] + A * (term @ f[:, l])
     u = u - f[: xt.shape[0]] / (2 * np.pi ** 1.5 * nu)
     return u

@@ -5,8 +5,9 @@
 * D = 3: the NaCl Madelung constant (tests/golden/madelung_nacl.txt).
 * Stokes kernels, D = 0: the O(N^2) free-space sum of App. B's kernels.
 * Rotlet, D = 3: -1/2 curl of three Laplace potentials (Eq. rotlet_def_deriv).
-* Stokeslet, D = 3: Hasimoto's Ewald split of the Oseen tensor (oracle/ewald.py; its smooth
-  part checked against the inverse Fourier transform by quadrature), velocities and gradients.
+* Stokeslet, D = 3 and D = 2: Hasimoto's Ewald split of the Oseen tensor (oracle/ewald.py; its
+  smooth part checked against the inverse Fourier transform by quadrature, the slab's kappa_3
+  integrals against quadrature), velocities and gradients.
 * Stresslet, D = 3, 2, 1: the stress of the Stokeslet flow, T_jlm = -delta_jm P_l + d_m G_jl +
   d_j G_ml with the Stokeslet pressure P_l = -d_l (1/(4 pi r)), mode by mode for k != 0, so the
   periodic stresslet sum equals Stokeslet and Laplace gradient sums; the Stokeslet flows are
@@ -195,6 +196,43 @@ def test_stokeslet_3p_vs_ewald(L):
         xt = x.astype(complex)
         xt[:, i] += 1j * h
         g[:, i, :] = ewald.stokeslet_ewald_3p(xt, x, f, L, 0.25 * min(L)).imag / h
+    assert rel(r.grad, g) < 1e-8
+
+
+@pytest.mark.parametrize("alpha,z", [(2.0, 0.1), (5.0, -0.4), (9.0, 0.7), (0.8, 0.0)])
+def test_stokes_slab_integrals(alpha, z):
+    """The closed forms of the D = 2 Stokeslet reference: I0 = int phi/k^2 e^{ikz}, I2 =
+    int phi/k^4 e^{ikz} and dI2/dz = -(z/2) I_L (k^2 = alpha^2 + kappa^2), by quadrature."""
+    nu = 0.3
+    phi = lambda k: (1 + (alpha ** 2 + k * k) * nu * nu / 4) * np.exp(-(alpha ** 2 + k * k) * nu * nu / 4)
+    I0q = 2 * quad(lambda k: phi(k) / (alpha ** 2 + k * k) * np.cos(k * z), 0, 80 / nu, limit=400)[0]
+    I2q = 2 * quad(lambda k: phi(k) / (alpha ** 2 + k * k) ** 2 * np.cos(k * z), 0, 80 / nu, limit=400)[0]
+    dI2q = -2 * quad(lambda k: k * phi(k) / (alpha ** 2 + k * k) ** 2 * np.sin(k * z), 0, 80 / nu, limit=400)[0]
+    I0, I2, IL = ewald._stokes_2p_modes(alpha, z, nu)
+    assert I0 == pytest.approx(I0q, rel=1e-11)
+    assert I2 == pytest.approx(I2q, rel=1e-11)
+    assert -z / 2 * IL == pytest.approx(dI2q, rel=1e-10, abs=1e-14)
+
+
+@pytest.mark.parametrize("L", [[1, 1, 1], [2, 1, 0.5]])
+def test_stokeslet_2p_vs_ewald(L):
+    """D = 2 Stokeslet (forces summing to zero): oracle vs the Ewald sum of oracle/ewald.py
+    (two split parameters agree to roundoff), velocities and target gradients."""
+    N = 50
+    x = workloads.mixed_points(N, L, seed=71, D=2)
+    f = workloads.stokes_strengths("stokeslet", N, seed=72)
+    r = evaluate("stokeslet", 2, L, 1e-9, x, f, n_s=12, grad=True)
+    s0 = 0.2 * min(L[:2])
+    e1 = ewald.stokeslet_ewald_2p(x, x, f, L, s0)
+    e2 = ewald.stokeslet_ewald_2p(x, x, f, L, 1.5 * s0)
+    assert rel(e1, e2) < 1e-13
+    assert rel(r.u, e1) < 1e-8
+    h = 1e-20
+    g = np.zeros((N, 3, 3))
+    for i in range(3):
+        xt = x.astype(complex)
+        xt[:, i] += 1j * h
+        g[:, i, :] = ewald.stokeslet_ewald_2p(xt, x, f, L, 1.25 * s0).imag / h
     assert rel(r.grad, g) < 1e-8
 
 
