@@ -1,5 +1,5 @@
-"""Independent reference sums for the Laplace kernel and, D = 3 and 2, the Stokeslet (oracle;
-test infrastructure only).
+"""Independent reference sums for the Laplace kernel and the periodic Stokeslet (oracle; test
+infrastructure only).
 
 These do not use the DMK machinery, the PSWF window or truncated kernels: they
 evaluate Eq. periodic_sum for K = 1/(4 pi r) through the classical Gaussian (Ewald)
@@ -20,10 +20,11 @@ H_M-hat = exp(-k^2 nu^2/4)/k^2 (Eq. Hhat_k):
   self         - rho_t lim_{r->0} erf(r/nu)/(4 pi r) = - rho_t/(2 pi^{3/2} nu).
 D = 0 is the plain O(N^2) sum.  Gradients (the field) are returned as well.
 
-Stokeslet, D = 3 and D = 2: Hasimoto's split of the Oseen tensor (below), real-space images
+Stokeslet, D = 3, 2, 1: Hasimoto's split of the Oseen tensor (below), real-space images
 within the cutoff plus the Fourier sum over k != 0 (D = 2: the kappa_3 integrals in closed
-form, and the in-plane mode (0, 0) regularised for in-plane forces that sum to zero), minus the
-target's own smooth part.
+form; D = 1: the transverse integrals in polar form by Gauss-Legendre quadrature; the
+non-periodic mode regularised for forces that sum to zero), minus the target's own smooth
+part.
 """
 import numpy as np
 import scipy.special as sp
@@ -371,5 +372,76 @@ def stokeslet_ewald_2p(xt, xs, f, L, nu):
                         ka = kv[j] if j < 2 else kv[l]
                         term = ka * z / 2 * IL * sn
                     u[:, j] = u[:, j] + A * (term @ f[:, l])
+    u = u - f[: xt.shape[0]] / (2 * np.pi ** 1.5 * nu)
+    return u
+
+
+# ---- Stokeslet, singly periodic (D = 1, x1 periodic) -------------------------------------
+#
+# Same split; the transverse wavevector q = (kappa_2, kappa_3), |q| = kappa, is integrated in
+# polar form about rho = (x2, x3) differences, r = |rho|, with the angular means
+#   <e^{iq.rho}> = J0(kappa r),  <q_a e^{iq.rho}> = i kappa J1(kappa r) rhohat_a,
+#   <q_a q_b e^{iq.rho}> = kappa^2/2 [(J0 + J2) delta_ab - 2 J2 rhohat_a rhohat_b].
+# With h0 = phi/k^2, h2 = phi/k^4 (k^2 = k1^2 + kappa^2) and the radial integrals (Gauss-Legendre
+# on [0, kmax]) P0 = 2 pi int h0 J0 kappa, Q0 = 2 pi int h2 J0 kappa, P1 = 2 pi int h2 J1 kappa^2,
+# R0 = pi int h2 (J0 + J2) kappa^3, R2 = 2 pi int h2 J2 kappa^3, a mode k1 != 0 contributes
+#   M_11 = P0 - k1^2 Q0,  M_1a = M_a1 = -i k1 P1 rhohat_a,  M_ab = (P0 - R0) delta_ab + R2 rhohat rhohat.
+# The mode k1 = 0 (q only) keeps, for forces that sum to zero, M_11 = the Laplace regularised
+# integral -pi (E1(r^2/nu^2) + ln(r^2/nu^2) + gamma) + pi e^{-r^2/nu^2} and
+#   M_ab = pi int [phi (J0 - J2) - e^{-kappa^2 nu^2/4}]/kappa delta_ab + 2 pi int phi J2/kappa rhohat rhohat.
+
+def stokeslet_ewald_1p(xt, xs, f, L, nu, nq=800):
+    """As stokeslet_ewald_3p for D = 1 (x1 periodic; x2, x3 free); the force components must
+    sum to zero (the k1 = 0 mode drops their divergent constant)."""
+    u = _stokes_real(xt, xs, f, L, (True, False, False), nu)
+    km = _kmax(nu)
+    t, wt = np.polynomial.legendre.leggauss(nq)
+    kap = 0.5 * km * (t + 1)
+    wt = 0.5 * km * wt
+    dx = xt[:, None, :] - xs[None, :, :]
+    # a target's own term is even in the displacement: taken at displacement 0 (constant in xt)
+    same = np.eye(xt.shape[0], xs.shape[0], dtype=bool)
+    dx = np.where(same[..., None], 0.0, dx)
+    r = np.sqrt(dx[:, :, 1] ** 2 + dx[:, :, 2] ** 2)
+    zero = same
+    rz = np.where(zero, 1.0, r)
+    rh = [np.where(zero, 0.0, dx[:, :, 1 + i] / rz) for i in range(2)]
+    kr = r[:, :, None] * kap
+    J0, J1, J2 = sp.jv(0, kr), sp.jv(1, kr), sp.jv(2, kr)
+    n = int(np.ceil(km * L[0] / (2 * np.pi)))
+    A = 1.0 / (L[0] * (2 * np.pi) ** 2)
+    for a in range(-n, n + 1):
+        k1 = 2 * np.pi * a / L[0]
+        if a == 0:
+            e = np.exp(-kap ** 2 * nu ** 2 / 4)
+            phi = (1 + kap ** 2 * nu ** 2 / 4) * e
+            xx = np.where(zero, 1.0, r * r / (nu * nu))
+            m11 = -np.pi * (sp.exp1(xx) + np.log(xx) + np.euler_gamma) + np.pi * np.exp(-xx)
+            M11 = np.where(zero, np.pi, m11)           # its limit at r = 0
+            T0 = np.pi * (((phi * (J0 - J2) - e) / kap) @ wt)
+            T2 = 2 * np.pi * ((phi * J2 / kap) @ wt)
+            C1 = 0.0 * M11
+        else:
+            if abs(k1) * nu / 2 > np.sqrt(44.0):
+                continue
+            k2 = k1 * k1 + kap ** 2
+            phi = (1 + k2 * nu * nu / 4) * np.exp(-k2 * nu * nu / 4)
+            h0, h2 = phi / k2 * wt, phi / k2 ** 2 * wt
+            P0 = 2 * np.pi * (J0 @ (h0 * kap))
+            M11 = P0 - k1 * k1 * 2 * np.pi * (J0 @ (h2 * kap))
+            C1 = k1 * 2 * np.pi * (J1 @ (h2 * kap ** 2))      # M_1a = -i C1 rhohat_a
+            T0 = P0 - np.pi * ((J0 + J2) @ (h2 * kap ** 3))
+            T2 = 2 * np.pi * (J2 @ (h2 * kap ** 3))
+        # real part of M e^{i k1 d1}: the real entries times cos; -i C1 rhohat_a gives
+        # +C1 rhohat_a sin (written without real parts, so that it is analytic in xt)
+        c, sn = np.cos(k1 * dx[:, :, 0]), np.sin(k1 * dx[:, :, 0])
+        u[:, 0] = u[:, 0] + A * ((M11 * c) @ f[:, 0])
+        for i in range(2):
+            cross = C1 * rh[i] * sn
+            u[:, 0] = u[:, 0] + A * (cross @ f[:, 1 + i])
+            u[:, 1 + i] = u[:, 1 + i] + A * (cross @ f[:, 0])
+            for j in range(2):
+                Mij = (T0 if i == j else 0.0) + T2 * rh[i] * rh[j]
+                u[:, 1 + i] = u[:, 1 + i] + A * ((Mij * c) @ f[:, 1 + j])
     u = u - f[: xt.shape[0]] / (2 * np.pi ** 1.5 * nu)
     return u

@@ -5,9 +5,9 @@
 * D = 3: the NaCl Madelung constant (tests/golden/madelung_nacl.txt).
 * Stokes kernels, D = 0: the O(N^2) free-space sum of App. B's kernels.
 * Rotlet, D = 3: -1/2 curl of three Laplace potentials (Eq. rotlet_def_deriv).
-* Stokeslet, D = 3 and D = 2: Hasimoto's Ewald split of the Oseen tensor (oracle/ewald.py; its
+* Stokeslet, D = 3, 2, 1: Hasimoto's Ewald split of the Oseen tensor (oracle/ewald.py; its
   smooth part checked against the inverse Fourier transform by quadrature, the slab's kappa_3
-  integrals against quadrature), velocities and gradients.
+  integrals and the 2D angular means of D = 1 against quadrature), velocities and gradients.
 * Stresslet, D = 3, 2, 1: the stress of the Stokeslet flow, T_jlm = -delta_jm P_l + d_m G_jl +
   d_j G_ml with the Stokeslet pressure P_l = -d_l (1/(4 pi r)), mode by mode for k != 0, so the
   periodic stresslet sum equals Stokeslet and Laplace gradient sums; the Stokeslet flows are
@@ -233,6 +233,47 @@ def test_stokeslet_2p_vs_ewald(L):
         xt = x.astype(complex)
         xt[:, i] += 1j * h
         g[:, i, :] = ewald.stokeslet_ewald_2p(xt, x, f, L, 1.25 * s0).imag / h
+    assert rel(r.grad, g) < 1e-8
+
+
+def test_polar_angular_means():
+    """The 2D angular means the D = 1 Stokeslet reference uses, by quadrature over the angle:
+    <q_a e^{iq.rho}> = i kappa J1 rhohat_a and <q_a q_b e^{iq.rho}> = kappa^2/2 [(J0 + J2) delta_ab
+    - 2 J2 rhohat_a rhohat_b]."""
+    kappa, rho = 3.7, np.array([0.21, -0.35])
+    r = np.linalg.norm(rho)
+    rh = rho / r
+    th = np.linspace(0, 2 * np.pi, 4001)[:-1]
+    q = kappa * np.stack([np.cos(th), np.sin(th)], -1)
+    e = np.exp(1j * q @ rho)
+    m1 = (q * e[:, None]).mean(axis=0)
+    m2 = np.einsum("na,nb,n->ab", q, q, e) / len(th)
+    J0, J1, J2 = (sp.jv(v, kappa * r) for v in (0, 1, 2))
+    assert np.abs(m1 - 1j * kappa * J1 * rh).max() < 1e-12
+    want = kappa ** 2 / 2 * ((J0 + J2) * np.eye(2) - 2 * J2 * np.outer(rh, rh))
+    assert np.abs(m2 - want).max() < 1e-12
+
+
+@pytest.mark.parametrize("L", [[1, 1, 1], [2, 1, 1]])
+def test_stokeslet_1p_vs_ewald(L):
+    """D = 1 Stokeslet (forces summing to zero): oracle vs the Ewald sum of oracle/ewald.py
+    (two split parameters agree to roundoff), velocities and target gradients (complex step of
+    1e-6: the complex Bessel routines are accurate relative to the function's size only)."""
+    N = 40
+    x = workloads.mixed_points(N, L, seed=81, D=1)
+    f = workloads.stokes_strengths("stokeslet", N, seed=82)
+    r = evaluate("stokeslet", 1, L, 1e-9, x, f, n_s=12, grad=True)
+    s0 = 0.2 * L[0]
+    e1 = ewald.stokeslet_ewald_1p(x, x, f, L, s0)
+    e2 = ewald.stokeslet_ewald_1p(x, x, f, L, 1.5 * s0)
+    assert rel(e1, e2) < 1e-13
+    assert rel(r.u, e1) < 1e-8
+    h = 1e-6
+    g = np.zeros((N, 3, 3))
+    for i in range(3):
+        xt = x.astype(complex)
+        xt[:, i] += 1j * h
+        g[:, i, :] = ewald.stokeslet_ewald_1p(xt, x, f, L, 1.25 * s0).imag / h
     assert rel(r.grad, g) < 1e-8
 
 
