@@ -4,7 +4,7 @@
   machinery), to within the tolerance row (Table 2 reports errors below eps).
 * D = 3: the NaCl Madelung constant (tests/golden/madelung_nacl.txt).
 * Stokes kernels, D = 0: the O(N^2) free-space sum of App. B's kernels.
-* Rotlet, D = 3: -1/2 curl of three Laplace potentials (Eq. rotlet_def_deriv).
+* Rotlet, D = 3, 2, 1: -1/2 curl of three Laplace potentials (Eq. rotlet_def_deriv).
 * Stokeslet, D = 3, 2, 1: Hasimoto's Ewald split of the Oseen tensor (oracle/ewald.py; its
   smooth part checked against the inverse Fourier transform by quadrature, the slab's kappa_3
   integrals and the 2D angular means of D = 1 against quadrature), velocities and gradients.
@@ -139,7 +139,7 @@ def test_stokes_free_space_direct(kernel):
     assert rel(r.grad, g) < 1e-5
 
 
-@pytest.mark.parametrize("D,L", [(3, [1, 1, 1]), (2, [1, 1, 1])])
+@pytest.mark.parametrize("D,L", [(3, [1, 1, 1]), (2, [1, 1, 1]), (1, [1, 1, 1])])
 def test_rotlet_is_curl_of_laplace(D, L):
     """Eq. rotlet_def_deriv: Omega_jl tau_l = -1/2 eps_jlm d_m H tau_l, so the rotlet sum equals
     -1/2 curl of three Laplace potentials (one per torque component) -- to within eps."""
