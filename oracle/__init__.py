@@ -17,7 +17,8 @@ symbols   truncated Green's-function symbols and kernel symbols (Sec. 5.2, App. 
 kernels   residual kernels, difference-kernel symbols, self terms (Sec. 2, App. B)
 tree      forest of octrees, 2:1 balance, interaction recursion (Sec. 3.1.1, 4.1)
 dmk       the evaluation: upward, root far field, downward, leaf (Sec. 3.1, 4.2-4.3, 5.3)
-ewald     independent Ewald-type reference on tiny inputs (Sec. 1, Eq. ewald-split)
+ewald     independent Ewald-type references on tiny inputs (Sec. 1, Eq. ewald-split): Laplace,
+          every D; the Stokeslet, D = 1-3, by Hasimoto's split of the Oseen tensor
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test against
 values fixed by the paper or by mathematics; none is "parity unpinned" except

@@ -39,8 +39,3 @@ def leafexp_flops(stats, n_targets, grad=True):
     """Expansion kernel: targets x 4 p^3 (value and gradient)."""
     p = int(stats["p"])
     return float(n_targets) * (4 if grad else 2) * p ** 3
-
-
-def leaf_flops(kernel, stats, n_targets, grad=True, precision="mixed"):
-    """Both leaf kernels together."""
-    return pair_flops(kernel, stats, grad) + leafexp_flops(stats, n_targets, grad)
