@@ -133,7 +133,8 @@ EXTRA = [
     ("Stokeslet velocity+gradient, D=1, L=(8,1,1), N=1e6 uniform, N(0,1) forces minus mean, tol 1e-6",
      "stokeslet", 1, [8.0, 1.0, 1.0], 1_000_000, "uniform", "stokes"),
     ("Stresslet potential+gradient, D=3, L=(1,1,16) (16 cubes, DFT over the cube index), N=4e6 uniform, "
-     "q (x) n strengths, tol 1e-6", "stresslet", 3, [1.0, 1.0, 16.0], 4_000_000, "uniform", "stokes"),
+     "q (x) n strengths, tol 1e-6; k = 0 excluded, the 3P compensation term of the literature not applied",
+     "stresslet", 3, [1.0, 1.0, 16.0], 4_000_000, "uniform", "stokes"),
     ("Rotlet potential+gradient, D=3, L=(1,1,16) (16 cubes, DFT over the cube index), N=4e6 uniform, "
      "N(0,1) torques, tol 1e-6", "rotlet", 3, [1.0, 1.0, 16.0], 4_000_000, "uniform", "stokes"),
     ("Laplace energy and forces through torch.autograd (two evaluations), D=3, L=(1,1,1), N=1e6 in 64 "
