@@ -60,7 +60,10 @@ typedef enum {
     DMK_ERR_NOT_NEUTRAL = 3,   /* Laplace with D = 1, 2 needs sum rho = 0 (Sec. 5.2)               */
     DMK_ERR_UNSUPPORTED = 4,   /* periodic length not an integer multiple of the cube side
                                   (non-exact tilings, Sec. 4.1.2, are not implemented)            */
-    DMK_ERR_TREE_DEPTH = 5,    /* a box at the depth cap still holds more than n_s points          */
+    DMK_ERR_TREE_DEPTH = 5,    /* reserved, never returned: a box at the depth cap (18 levels below
+                                  a cube) that holds more than n_s points (coincident or nearly
+                                  coincident points) stays a leaf, the result is still the
+                                  method's, and dmk_stats_t.n_capped_leaves counts such boxes     */
     DMK_ERR_OOM = 6,           /* device allocation failed                                        */
     DMK_ERR_CUDA = 7,          /* a CUDA call failed; see dmk_last_error                          */
     DMK_ERR_TIMEOUT = 8        /* reserved: no device-side wait exists in this library            */
@@ -103,6 +106,30 @@ dmk_status_t dmk_eval(dmk_plan_t plan, int64_t N, const double* points, const do
 dmk_status_t dmk_eval_host(dmk_plan_t plan, int64_t N, const double* points, const double* strengths,
                            double* potentials, double* grad);
 
+/* Vector-Jacobian product of dmk_eval, the reverse-mode derivative used for training-style
+ * differentiation (not in the paper).  For a scalar L(u) with upstream gradient g = dL/du
+ * (N x d_u), u = dmk_eval(points, strengths):
+ *   d_strengths[s][l] = dL/drho_s,l = sum_t sum_j K_jl(x_t - x_s) g_t,j = v_l(x_s),
+ *   d_points[a][i]    = dL/dx_a,i  = sum_j grad_u[a][i][j] g_a,j + sum_l grad_v[a][i][l] rho_a,l,
+ * where v is the sum of Eq. periodic_sum with strengths g.  This holds for the kernels with
+ * K(-x) = K(x)^T -- Laplace, Stokeslet, rotlet -- so one more evaluation of the whole method
+ * (residual sums, plane waves, root far field) with strengths g and target gradients gives
+ * both; the assembly of d_points runs on the GPU too.
+ *   points, strengths  device, as passed to dmk_eval (N x 3, N x d_rho).
+ *   grad_u             device, N x 3 x d_u: the grad output of that dmk_eval.
+ *   g                  device, N x d_u: upstream gradient; need not sum to zero.  For Laplace
+ *                      with D = 1, 2 a net sum is allowed here: the free-direction zero mode is
+ *                      then the truncated Green's function of Sec. 5.2, which differs from any
+ *                      other regularisation by a constant, so d_points is exact and
+ *                      d_strengths is exact up to an additive constant (which no neutral
+ *                      change of the strengths sees).
+ *   d_strengths        device, N x d_rho, or NULL to skip.
+ *   d_points           device, N x 3, or NULL to skip.
+ * The stresslet (d_rho = 9 != d_u) returns DMK_ERR_UNSUPPORTED.  Workspace as dmk_eval; the
+ * call returns after the results are complete. */
+dmk_status_t dmk_vjp(dmk_plan_t plan, int64_t N, const double* points, const double* strengths,
+                     const double* grad_u, const double* g, double* d_strengths, double* d_points);
+
 /* dmk_eval without any device allocation.  The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc at evaluation time -- applications whose
  * device memory is fully reserved by their own pool allocator and that must not let a
@@ -114,15 +141,15 @@ dmk_status_t dmk_eval_host(dmk_plan_t plan, int64_t N, const double* points, con
  *   - N must lie in [0, 16384]; a larger N returns DMK_ERR_INVALID_ARG, and a problem whose
  *     workspace does not fit in 64 MiB (large p, FP64, deep trees) returns DMK_ERR_OOM, both
  *     with a message in dmk_last_error.
- *   - The first call on a device looks up the device address of the static array; make
- *     that first call before any stream capture.
+ *   - The first call on a device looks up the device address of the static array (a CUDA
+ *     runtime query that must not run while a stream is being captured), so make that first
+ *     call on each device before any stream capture begins.
  *   - Every call shares the one array, which keeps the previous call's contents; the call
  *     clears everything it needs to start at zero.  Calls that overlap on the GPU (on
  *     different streams, plans or threads) race on the array and must be serialised. */
 dmk_status_t dmk_eval_static(dmk_plan_t plan, int64_t N, const double* points, const double* strengths,
                              double* potentials, double* grad);
 
-/* Statistics of the last dmk_eval on this plan. */
 typedef struct {
     int32_t c_times_1000;      /* PSWF band limit c, times 1000                                  */
     int32_t p;                 /* Chebyshev order                                                */
@@ -138,8 +165,13 @@ typedef struct {
     int32_t fit_terms;         /* Chebyshev terms of the residual function q used by the path    */
     float stage_ms[10];        /* last eval: tree, upward, root, plane waves, shift, leaf, total,
                                   residual kernel, expansion kernel, 0 (stages 7 and 8: p <= 24) */
+    int32_t n_capped_leaves;   /* boxes at the depth cap holding more than n_s points (kept as leaves) */
+    int32_t reserved;
+    int64_t n_device_allocs;   /* device allocations (cudaMalloc, cudaMallocAsync) made by this plan
+                                  since it was created, tables included; current at every call   */
 } dmk_stats_t;
 
+/* Statistics of the last evaluation on this plan (n_device_allocs: as of this call). */
 dmk_status_t dmk_get_stats(dmk_plan_t plan, dmk_stats_t* out);
 
 /* Enables (1) or disables (0) per-stage CUDA-event timing inside dmk_eval (stage_ms). */

@@ -166,11 +166,17 @@ class Result:
     pass
 
 
-def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_parts=False):
+def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_parts=False, targets=None):
     """Evaluate u(x_t) = sum_s sum*_p K(x_t - x_s + p) rho_s (Eq. periodic_sum) by periodized DMK.
 
     points (N,3), strengths (N, d_rho); returns potentials (N, d_u) in input order and, if
     grad, the target gradients g[t, i, j] = d u_j / d x_i (N, 3, d_u).
+
+    targets: None (every point is a target) or an array of point indices.  The method is the
+    same -- every point is a source, the forest, upward pass, root far field and downward pass
+    are those of the whole problem -- but the leaf step (Sec. 3.1.5) runs only for the listed
+    targets, so each of their values is the one the full evaluation gives; the other rows of
+    the outputs are NaN.
     """
     kern = Kernel(kernel)
     c, p = c_and_p(kernel, tol)
@@ -279,6 +285,13 @@ def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_p
     # ---- step 5: leaf evaluation, residual sums, self correction (Sec. 3.1.5, 2.4) --
     u = np.zeros((N, kern.d_u))
     gu = np.zeros((N, 3, kern.d_u)) if grad else None
+    want = None
+    if targets is not None:
+        want = np.zeros(N, dtype=bool)
+        want[np.asarray(targets, dtype=np.int64)] = True
+        u[:] = np.nan
+        if grad:
+            gu[:] = np.nan
     per_leaf = {}
     for (A, S, sh, l) in direct:
         for T in forest.leaves_below(A):
@@ -286,9 +299,9 @@ def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_p
                 per_leaf.setdefault(T.id, []).append((S, sh, l))
     Lvec = np.array(geom.L)
     for T in forest.leaves():
-        if not len(T.pts):
+        t = T.pts if want is None else T.pts[want[T.pts]]
+        if not len(t):
             continue
-        t = T.pts
         cT = center(T)
         half = s / 2 ** T.level / 2
 
@@ -334,7 +347,7 @@ def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_p
         Rr = R
         corr = -np.diag([(1 + math.log(Rr)) / (2 * np.pi), (math.log(Rr) + 0.5) / (4 * np.pi),
                          (math.log(Rr) + 0.5) / (4 * np.pi)]) / geom.L[0]
-        u += (corr @ rho.sum(axis=0))[None, :]
+        u += (corr @ rho.sum(axis=0))[None, :]      # NaN rows (targets not evaluated) stay NaN
     res = Result()
     res.u = u
     res.grad = gu

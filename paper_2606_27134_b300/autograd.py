@@ -1,18 +1,21 @@
-"""torch.autograd.Function around dmk_eval.
+"""torch.autograd.Function around dmk_eval and dmk_vjp.
 
-u_t = sum_s sum*_p K(x_t - x_s + p) rho_s.  For L = sum_t g_t . u_t and an even kernel whose
-matrix is symmetric (Laplace, Stokeslet: K(-x) = K(x), K_jl = K_lj), the sum is self-adjoint:
+u_t = sum_s sum*_p K(x_t - x_s + p) rho_s.  For L = sum_t g_t . u_t and a kernel with
+K(-x) = K(x)^T (Laplace, Stokeslet: even and symmetric; rotlet: odd and antisymmetric), the
+sum is self-adjoint:
     dL/drho_s = sum_t K(x_t - x_s)^T g_t = v(x_s),         v = the same sum with strengths g;
     dL/dx_a   = sum_j g_a,j grad u_j(x_a) + sum_l rho_a,l grad v_l(x_a),
 so the backward pass is one more evaluation of the same hot path (every stage: leaf residual
-sums, plane waves, root Fourier sum) with strengths g and target gradients.  The forward saves
-the field gradient of u.  Both passes run in the CUDA library.
+sums, plane waves, root Fourier sum) with strengths g and target gradients, followed by the
+assembly of dL/dx; dmk_vjp does all of it in the CUDA library.  The forward saves the field
+gradient of u.  The stresslet (9 strength components, 3 outputs) is not self-adjoint and is
+not covered.
 """
 import torch
 
 from . import dmk
 
-SELF_ADJOINT = ("laplace", "stokeslet")
+SELF_ADJOINT = ("laplace", "stokeslet", "rotlet")
 
 
 class _DMKFunction(torch.autograd.Function):
@@ -29,21 +32,22 @@ class _DMKFunction(torch.autograd.Function):
         points, strengths, gu = ctx.saved_tensors
         plan = ctx.plan
         N = points.shape[0]
-        g = g.contiguous().reshape(N, plan.d_u)
-        v, gv = plan.eval(points.detach(), g.to(torch.float64), grad=True)
-        d_rho = v.reshape(strengths.shape) if ctx.needs_input_grad[1] else None
-        d_x = None
-        if ctx.needs_input_grad[0]:
-            rho = strengths.reshape(N, plan.d_rho)
-            d_x = torch.einsum("tij,tj->ti", gu, g) + torch.einsum("tij,tj->ti", gv, rho)
+        want_x, want_rho = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        d_rho, d_x = plan.vjp(points.detach(), strengths.detach(), gu, g.to(torch.float64),
+                              want_strengths=want_rho, want_points=want_x)
+        if d_rho is not None:
+            d_rho = d_rho.reshape(strengths.shape)
         return d_x, d_rho, None
 
 
 class Potential(torch.nn.Module):
     """u = Potential(kernel, D, L, tol)(points, strengths), differentiable in both arguments.
 
-    Supported for the self-adjoint kernels (Laplace, Stokeslet).  Points and strengths are CUDA
-    float64 tensors of shapes (N, 3) and (N, d_rho).
+    Supported for the self-adjoint kernels (Laplace, Stokeslet, rotlet).  Points and strengths
+    are CUDA float64 tensors of shapes (N, 3) and (N, d_rho).  Laplace with D = 1 or 2 needs
+    neutral strengths in the forward pass (Sec. 5.2); the upstream gradient of the backward pass
+    need not be neutral: dL/dpoints is exact and dL/dstrengths is exact up to an additive
+    constant, which no neutral change of the strengths sees.
     """
 
     def __init__(self, kernel, D, L, tol, precision="mixed", n_s=250, stream=None):

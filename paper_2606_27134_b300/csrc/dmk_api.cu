@@ -75,10 +75,15 @@ struct dmk_plan_s {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_cnt = nullptr;
     int pair_overlap = 0;
     int pair_blocks = 2;
-    int n_sm = 148;
+    int n_sm = 148;                 // replaced by the device's SM count at plan creation
     // resident blocks per SM of the persistent kernels, by kernel
     std::unordered_map<const void*, int> occ;
     int launches = 0;
+    // device allocations made by this plan so far (cudaMalloc, cudaMallocAsync)
+    int64_t n_allocs = 0;
+    // set by dmk_vjp while it evaluates with the upstream gradient as strengths: the net
+    // charge of Laplace D = 1, 2 is then allowed (only gradients of the result are used)
+    int allow_charged = 0;
     // set only while dmk_eval_static runs: device buffers are carved from this range
     unsigned char* arena = nullptr;
     size_t arena_cap = 0, arena_off = 0;
@@ -110,6 +115,7 @@ enum BufId {
     B_W, B_KEYS, B_KEYS2, B_IDX, B_IDX2, B_XS, B_RS, B_CUB, B_FLAGS, B_CNT,
     B_CELLS, B_R, B_CAND, B_BOXU64, B_BOXINT, B_LEAVES, B_DOFFS, B_DL, B_NLBOX, B_TASKS, B_BAL,
     B_PROXY, B_LOCAL, B_PW, B_SCRATCH, B_CHI, B_UHAT, B_MISC, B_DEVPTS, B_DEVRHO, B_DEVPOT, B_DEVGRAD, B_XF, B_VW, B_PART,
+    B_VJPV, B_VJPG,
     B_COUNT
 };
 
@@ -178,6 +184,7 @@ dmk_status_t ensure(dmk_plan_s* plan, int id, size_t bytes, void** out) {
             plan->err = "device allocation of " + std::to_string(want) + " bytes failed";
             return DMK_ERR_OOM;
         }
+        ++plan->n_allocs;
         b.cap = want;
     }
     *out = b.p;
@@ -273,6 +280,7 @@ dmk_status_t upload_tab(dmk_plan_s* plan, void** mem, Tab<T>& tab, double fit_to
     }
     cudaError_t e = cudaMalloc(mem, h.size() * sizeof(T));
     if (e != cudaSuccess) { plan->err = "table allocation failed"; return DMK_ERR_OOM; }
+    ++plan->n_allocs;
     e = cudaMemcpy(*mem, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { plan->err = cudaGetErrorString(e); return DMK_ERR_CUDA; }
     T* base = (T*)*mem;
@@ -326,6 +334,7 @@ dmk_status_t upload_root(dmk_plan_s* plan) {
     }
     cudaError_t e = cudaMalloc(&plan->d_root, h.size() * sizeof(double));
     if (e != cudaSuccess) { plan->err = "root table allocation failed"; return DMK_ERR_OOM; }
+    ++plan->n_allocs;
     e = cudaMemcpy(plan->d_root, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { plan->err = cudaGetErrorString(e); return DMK_ERR_CUDA; }
     double* base = (double*)plan->d_root;
@@ -344,6 +353,7 @@ dmk_status_t upload_root(dmk_plan_s* plan) {
     sv.insert(sv.end(), P.self_grad.begin(), P.self_grad.end());
     e = cudaMalloc(&plan->d_self, sv.size() * sizeof(double));
     if (e != cudaSuccess) { plan->err = "self table allocation failed"; return DMK_ERR_OOM; }
+    ++plan->n_allocs;
     cudaMemcpy(plan->d_self, sv.data(), sv.size() * sizeof(double), cudaMemcpyHostToDevice);
     return DMK_OK;
 }
@@ -367,7 +377,7 @@ struct Evaluator {
         // kernels using place() have at most a few hundred bytes of static shared memory
         const size_t lim = plan->smem_optin > 4096 ? plan->smem_optin - 4096 : 0;
         pl.bytes = bytes;
-        pl.grid = (unsigned)std::max(1, std::min<int>(n, 148 * 8));
+        pl.grid = (unsigned)std::max(1, std::min<int>(n, plan->n_sm * 8));
         if (bytes <= lim) {
             pl.use_smem = 1;
             *scratch = nullptr;
@@ -375,7 +385,7 @@ struct Evaluator {
         }
         pl.use_smem = 0;
         // the static workspace of dmk_eval_static holds at most 16 per-CTA slices
-        pl.grid = (unsigned)std::max(1, std::min<int>(n, plan->arena ? 16 : 148 * 2));
+        pl.grid = (unsigned)std::max(1, std::min<int>(n, plan->arena ? 16 : plan->n_sm * 2));
         void* p = nullptr;
         dmk_status_t s = ensure(plan, B_SCRATCH, bytes * pl.grid, &p);
         *scratch = (unsigned char*)p;
@@ -401,7 +411,7 @@ dmk_status_t launch_anterp(dmk_plan_s* plan, Tab<T>& tab, int nleaf_cap, const i
     int threads = std::min(MAXP <= 24 ? 576 : 512, ((p2 + 31) / 32) * 32);
     size_t sm = 3 * (size_t)kAnterpChunk * MAXP * sizeof(T);
     CKS(set_smem(plan, k_anterp<T, MAXP>, sm));
-    unsigned grid = (unsigned)std::max(1, std::min(nleaf_cap, 148 * 8));
+    unsigned grid = (unsigned)std::max(1, std::min(nleaf_cap, plan->n_sm * 8));
     k_anterp<T, MAXP><<<grid, threads, sm, plan->stream>>>(nleaf_dev, leaves, B, xs, N, rs, tab, plan->T.s, proxy);
     return DMK_OK;
 }
@@ -412,7 +422,7 @@ dmk_status_t launch_anterp2(dmk_plan_s* plan, Tab<T>& tab, int nleaf_cap, const 
     const int threads = (((tab.p + 1) / 2) * tab.p + 31) / 32 * 32;
     const size_t sm = 3 * (size_t)kAnterpChunk * MAXP * sizeof(T);
     CKS(set_smem(plan, k_anterp2<T, MAXP>, sm));
-    const unsigned grid = (unsigned)std::max(1, std::min(nleaf_cap, 148 * 8));
+    const unsigned grid = (unsigned)std::max(1, std::min(nleaf_cap, plan->n_sm * 8));
     k_anterp2<T, MAXP><<<grid, threads, sm, plan->stream>>>(nleaf_dev, leaves, B, xs, N, rs, tab, plan->T.s, proxy);
     return DMK_OK;
 }
@@ -461,7 +471,7 @@ dmk_status_t launch_leafexp(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int*
                             const double* xs, int64_t N, LeafOut lo) {
     const size_t se = leafexp_smem<T>(tab.p);
     CKS(set_smem(plan, k_leafexp<T, K, G>, se));
-    const unsigned grid = (unsigned)std::max(1, std::min(nleaf, 148 * 16));
+    const unsigned grid = (unsigned)std::max(1, std::min(nleaf, plan->n_sm * 16));
     k_leafexp<T, K, G><<<grid, kLeafExpThreads, se, plan->stream>>>(nleaf, leaves, B, tab, plan->geo, local, xs, N, lo);
     return DMK_OK;
 }
@@ -470,7 +480,7 @@ template <class T, int K>
 dmk_status_t launch_leaf(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int* leaves, BoxArrays B, const T* local,
                          const double* xs, int64_t N, const int* doffs, const DirectEntry* dl, LeafOut lo, bool grad) {
     constexpr int DR = (K == DMK_LAPLACE) ? 1 : (K == DMK_STRESSLET ? 9 : 3);
-    const unsigned grid = (unsigned)std::max(1, std::min(nleaf, 148 * 16));
+    const unsigned grid = (unsigned)std::max(1, std::min(nleaf, plan->n_sm * 16));
     const size_t dyn = (size_t)kSrcChunk * kLeaf2Threads + (size_t)kSrcChunk * DR * sizeof(T);
     if (grad) {
         CKS(set_smem(plan, k_leaf2<T, K, true>, dyn));
@@ -550,6 +560,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     int* d_missing = (int*)((char*)vmisc + 1280);  // balance check, per level
     int* d_nleaf = (int*)((char*)vmisc + 1536);
     int* d_next = (int*)((char*)vmisc + 2040);     // residual-task counter of k_pair
+    int* d_capped = (int*)((char*)vmisc + 1352);   // depth-cap cells over n_s (after missing[])
     // cells with more than n_s points are disjoint: at most N/(n_s+1) split per level
     const int64_t cap = std::max<int64_t>(1, N / ((int64_t)plan->n_s + 1));
     const int nblkR = (int)((N + kRefineThreads - 1) / kRefineThreads);
@@ -575,12 +586,12 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         k_gather<<<ngb, kGatherThreads, 0, st>>>(N, drho, idx2, (const double*)vw, rho, xs, rs, pk,
                                                   (double*)vpart);
         k_sum_partials<<<1, 1024, 0, st>>>(ngb, 2 * drho, (const double*)vpart, d_sums);
-        k_refine_count<<<nblkR, kRefineThreads, 0, st>>>(N, pkeys, plan->n_s, nblkR, lsort, bcnt);
+        CK(cudaMemsetAsync(d_missing, 0, (kBits + 1) * sizeof(int), st));      // missing[] and capped
+        k_refine_count<<<nblkR, kRefineThreads, 0, st>>>(N, pkeys, plan->n_s, nblkR, lsort, bcnt, d_capped);
         k_refine_scan<<<1, 1024, 0, st>>>(nblkR, bcnt, boff, d_nR);
         k_refine_write<<<nblkR, kRefineThreads, 0, st>>>(N, pkeys, plan->n_s, nblkR, lsort, boff, cap, Rall);
         {
             const int64_t nchk = (int64_t)(kBits - 1) * 27 * cap;
-            CK(cudaMemsetAsync(d_missing, 0, kBits * sizeof(int), st));
             k_balance_check<<<(unsigned)((nchk + 255) / 256), 256, 0, st>>>(cap, Rall, d_nR, g, d_missing);
         }
         launches += 11;
@@ -589,6 +600,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         if (lsort >= kBits || hmeta[lsort - 1] == 0) break;
         lsort = kBits;                                     // deeper than the sorted bits: resort
     }
+    const int n_capped = hmeta[(1352 - 1024) / 4];
     TreeInfo ti;
     std::vector<const uint64_t*> Rl(kMaxLevels + 1, nullptr);
     // balance arrays that outgrow the refinement layout: stream-ordered, released on return
@@ -598,6 +610,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         void* p = nullptr;
         cudaError_t e = cudaMallocAsync(&p, std::max<size_t>(bytes, 16), st);
         if (e != cudaSuccess) { plan->err = "level allocation failed"; return DMK_ERR_OOM; }
+        ++plan->n_allocs;
         level_mem.push_back(p);
         *out = p;
         return DMK_OK;
@@ -938,7 +951,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         bool pwout_done = false;
         if constexpr (sizeof(T) == 4) {
             if (p <= kMaxPFast && nfh <= mp && po2_bytes <= plan->smem_optin) {
-                const unsigned grid = (unsigned)std::min(2 * n_nl, 148 * 4);
+                const unsigned grid = (unsigned)std::min(2 * n_nl, plan->n_sm * 4);
                 if (mp == 20) {
                     CKS(set_smem(plan, k_pwout2<T, 20>, po2_bytes));
                     k_pwout2<T, 20><<<grid, 416, po2_bytes, st>>>(n_nl, nl_box, tab, proxy, W);
@@ -970,7 +983,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
             Cx<T>* Vw = (Cx<T>*)vvw;
             const int nchunk = (int)((nW + kTransModes - 1) / kTransModes);
             k_pw_trans<T><<<(unsigned)n_nl * nchunk, kTransThreads, 0, st>>>(n_nl, nl_box, B, tab, W, Vw);
-            const unsigned grid = (unsigned)std::min(n_nl, 148 * 4);
+            const unsigned grid = (unsigned)std::min(n_nl, plan->n_sm * 4);
             if (mpw == 20) {
                 CKS(set_smem(plan, k_pwin3<T, 20>, pw2_bytes));
                 k_pwin3<T, 20><<<grid, 384, pw2_bytes, st>>>(n_nl, nl_box, tab, Vw, local);
@@ -1064,7 +1077,8 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     std::memcpy(hs, plan->h_meta + 256, 2 * drho * sizeof(double));
     if (herr & kErrNonFinite) { plan->err = "non-finite coordinate"; return DMK_ERR_OUT_OF_DOMAIN; }
     if (herr & kErrDomain) { plan->err = "a free coordinate lies outside [0, L_i)"; return DMK_ERR_OUT_OF_DOMAIN; }
-    if (P.kernel == DMK_LAPLACE && (P.D == 1 || P.D == 2) && std::fabs(hs[0]) > 1e-12 * std::max(hs[1], 1e-300)) {
+    if (!plan->allow_charged && P.kernel == DMK_LAPLACE && (P.D == 1 || P.D == 2) &&
+        std::fabs(hs[0]) > 1e-12 * std::max(hs[1], 1e-300)) {
         plan->err = "Laplace with D = 1, 2 requires zero net charge";
         return DMK_ERR_NOT_NEUTRAL;
     }
@@ -1083,6 +1097,8 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     S.n_direct_entries = ti.n_entries;
     S.kernel_launches = launches;
     S.fit_terms = tab.n_q;
+    S.n_capped_leaves = n_capped;
+    S.n_device_allocs = plan->n_allocs;
     if (plan->timing) {
         float ms;
         // stage 7: the residual kernel alone (on the side stream when it overlaps the far
@@ -1220,6 +1236,39 @@ dmk_status_t dmk_eval_static(dmk_plan_t plan, int64_t N, const double* points, c
     return s;
 }
 
+dmk_status_t dmk_vjp(dmk_plan_t plan, int64_t N, const double* points, const double* strengths,
+                     const double* grad_u, const double* g, double* d_strengths, double* d_points) {
+    if (!plan) return DMK_ERR_INVALID_ARG;
+    plan->err.clear();
+    if (plan->T.kernel == DMK_STRESSLET) {
+        plan->err = "dmk_vjp: the stresslet is not self-adjoint (d_rho = 9, d_u = 3)";
+        return DMK_ERR_UNSUPPORTED;
+    }
+    if (N < 0) { plan->err = "N < 0"; return DMK_ERR_INVALID_ARG; }
+    if (N == 0) return DMK_OK;
+    if (N > (int64_t)1 << 30) { plan->err = "N above 2^30"; return DMK_ERR_INVALID_ARG; }
+    if (!points || !strengths || !g || (d_points && !grad_u)) { plan->err = "NULL array"; return DMK_ERR_INVALID_ARG; }
+    if (!d_strengths && !d_points) return DMK_OK;
+    cudaSetDevice(plan->device);
+    const int du = plan->T.d_u;
+    void *vv = d_strengths, *vg = nullptr;
+    if (!vv) CKS(ensure(plan, B_VJPV, (size_t)N * du * sizeof(double), &vv));
+    if (d_points) CKS(ensure(plan, B_VJPG, (size_t)N * 3 * du * sizeof(double), &vg));
+    plan->allow_charged = 1;
+    const dmk_status_t s = (plan->prec == DMK_FP64)
+                               ? run_eval<double>(plan, plan->tab64, N, points, g, (double*)vv, (double*)vg)
+                               : run_eval<float>(plan, plan->tab32, N, points, g, (double*)vv, (double*)vg);
+    plan->allow_charged = 0;
+    if (s != DMK_OK) return s;
+    if (d_points) {
+        k_vjp_points<<<nblk(3 * N, 256), 256, 0, plan->stream>>>(N, du, grad_u, g, (const double*)vg, strengths,
+                                                                d_points);
+        CK(cudaGetLastError());
+        CKS(host_wait(plan, plan->stream));
+    }
+    return DMK_OK;
+}
+
 dmk_status_t dmk_eval_host(dmk_plan_t plan, int64_t N, const double* points, const double* strengths,
                            double* potentials, double* grad) {
     if (!plan) return DMK_ERR_INVALID_ARG;
@@ -1246,6 +1295,7 @@ dmk_status_t dmk_eval_host(dmk_plan_t plan, int64_t N, const double* points, con
 dmk_status_t dmk_get_stats(dmk_plan_t plan, dmk_stats_t* out) {
     if (!plan || !out) return DMK_ERR_INVALID_ARG;
     *out = plan->stats;
+    out->n_device_allocs = plan->n_allocs;
     return DMK_OK;
 }
 

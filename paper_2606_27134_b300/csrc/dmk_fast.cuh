@@ -760,7 +760,8 @@ __device__ __forceinline__ void cheb_eval(const T* cs, int p, int ng, const T (&
 // barrier couples the warps of a block.  A chunk holds (x, y, z, nu^2) and (x_lo, y_lo, z_lo,
 // 1/nu) per source (source offsets from the target leaf's centre, FP32 leading and trailing
 // parts in the FP32 path).  Per chunk: support test |x_t sigma - x_s/nu| < 1 (half precision on
-// source pairs in the FP32 path, FP64 r^2 < nu^2 in the FP64 path) into bit masks, in-support
+// source pairs with a margin for its rounding in the FP32 path, FP64 r^2 < nu^2 in the FP64
+// path) into bit masks, in-support
 // sources appended to a per-lane byte queue, queued pairs evaluated with two-float differences
 // and the cubic residual tables (r > 0 excludes the target itself), FP32 sums folded into FP64
 // per chunk.  The result K * sum is written to the output in input order.  The kernel needs
@@ -929,7 +930,11 @@ __global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? 4 : 2) k_pai
             // by row so that lanes with different queue lengths write to different banks)
             int cnt = 0;
             if constexpr (kTwo) {
-                const __half2 one2 = __float2half2_rn(1.0f);
+                // the half-precision test passes every pair with r^2 / nu^2 < 1: its rounding
+                // error stays below 5e-3 for |dx / nu| < 1 (operands below 2 in magnitude), so
+                // the bound 1.02 keeps every in-support pair; the exact test r^2 < nu^2 is
+                // repeated in FP32 before a pair is evaluated
+                const __half2 one2 = __float2half2_rn(1.02f);
                 const int npair = (filled + 1) >> 1;
                 const int nu = (npair - s + S - 1) / S;     // this split's pair slots s + S u
                 for (int u0 = 0; u0 < nu; u0 += 16) {
@@ -999,7 +1004,9 @@ __global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? 4 : 2) k_pai
                     dz += xtl[2] - b.z;
                 }
                 const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                if (r2 > T(0)) {
+                // r = 0: the target itself (Eq. periodic_sum drops it); r >= nu: outside the
+                // residual kernel's support (the queue of the FP32 path holds a few such pairs)
+                if (r2 > T(0) && r2 < a.w) {
                     if constexpr (kTwo)
                         Pr::eval(HermSeries(herm, r2, b.w), dx, dy, dz, r2, b.w, sr[k], acc, gacc);
                     else

@@ -812,6 +812,21 @@ __global__ void k_rootfft_idft(int M, int du, int p, RootTab rt, const Cx<double
     local[id] = (T)(v + cst);
 }
 
+// Position part of the vector-Jacobian product (reverse-mode derivative of the sums for a
+// kernel with K(-x) = K(x)^T): d[a][i] = sum_j gu[a][i][j] g[a][j] + sum_l gv[a][i][l] rho[a][l],
+// gu the field gradient of the forward sum, gv that of the sum with strengths g (d_u = d_rho).
+__global__ void k_vjp_points(int64_t N, int du, const double* __restrict__ gu, const double* __restrict__ g,
+                             const double* __restrict__ gv, const double* __restrict__ rho, double* __restrict__ d) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= 3 * N) return;
+    const int64_t a = t / 3;
+    const int i = (int)(t - 3 * a);
+    double v = 0;
+    for (int j = 0; j < du; ++j)
+        v = fma(gu[(a * 3 + i) * du + j], g[a * du + j], fma(gv[(a * 3 + i) * du + j], rho[a * du + j], v));
+    d[t] = v;
+}
+
 __global__ void k_strength_sums(int64_t N, int drho, const double* __restrict__ rho, double* __restrict__ out) {
     // out[a] = sum rho_a, out[drho + a] = sum |rho_a|
     double s[9], sa[9];

@@ -178,9 +178,12 @@ struct SplitProbe {
     }
 };
 
-// counts of split-cell starts per level and block: bcnt[l * nblk + block]
+// counts of split-cell starts per level and block: bcnt[l * nblk + block].  With the keys sorted
+// on all their bits (lmax = kBits), also counts into *capped the cells at the depth cap (level
+// kBits, never split) that hold more than n_s points: they stay leaves.
 __global__ void __launch_bounds__(kRefineThreads) k_refine_count(int64_t N, const uint64_t* __restrict__ pk, int n_s,
-                                                                 int nblk, int lmax, int* __restrict__ bcnt) {
+                                                                 int nblk, int lmax, int* __restrict__ bcnt,
+                                                                 int* __restrict__ capped) {
     __shared__ int wc[kBits][kRefineThreads / 32];
     const int64_t i = blockIdx.x * (int64_t)kRefineThreads + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -190,6 +193,8 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine_count(int64_t N, cons
         const unsigned bal = __ballot_sync(0xffffffffu, valid && l < lmax && sp.split(l));
         if (lane == 0) wc[l][warp] = __popc(bal);
     }
+    const unsigned cap_bal = __ballot_sync(0xffffffffu, valid && lmax >= kBits && sp.split(kBits));
+    if (lane == 0 && cap_bal) atomicAdd(capped, __popc(cap_bal));
     __syncthreads();
     if (threadIdx.x < kBits) {
         int sum = 0;

@@ -31,10 +31,12 @@ class Stats(ctypes.Structure):
                 ("n_root_modes", ctypes.c_int32), ("n_levels", ctypes.c_int32), ("n_boxes", ctypes.c_int32),
                 ("n_leaves", ctypes.c_int32), ("n_nonleaf", ctypes.c_int32), ("n_pairs", ctypes.c_int64),
                 ("n_direct_entries", ctypes.c_int64), ("kernel_launches", ctypes.c_int32),
-                ("fit_terms", ctypes.c_int32), ("stage_ms", ctypes.c_float * 10)]
+                ("fit_terms", ctypes.c_int32), ("stage_ms", ctypes.c_float * 10),
+                ("n_capped_leaves", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_device_allocs", ctypes.c_int64)]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "stage_ms"}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("stage_ms", "reserved")}
         d["stage_ms"] = list(self.stage_ms)[:9]
         return d
 
@@ -66,6 +68,7 @@ def load(path=None):
     lib.dmk_eval.argtypes = [vp, c_i64, vp, vp, vp, vp]
     lib.dmk_eval_host.argtypes = [vp, c_i64, vp, vp, vp, vp]
     lib.dmk_eval_static.argtypes = [vp, c_i64, vp, vp, vp, vp]
+    lib.dmk_vjp.argtypes = [vp, c_i64, vp, vp, vp, vp, vp, vp]
     lib.dmk_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.dmk_set_timing.argtypes = [vp, c_int]
     lib.dmk_destroy.argtypes = [vp]
@@ -75,7 +78,7 @@ def load(path=None):
     lib.dmk_status_string.restype = ctypes.c_char_p
     lib.dmk_last_error.argtypes = [vp]
     lib.dmk_last_error.restype = ctypes.c_char_p
-    for f in ("dmk_plan", "dmk_plan_ex", "dmk_eval", "dmk_eval_host", "dmk_eval_static", "dmk_get_stats",
+    for f in ("dmk_plan", "dmk_plan_ex", "dmk_eval", "dmk_eval_host", "dmk_eval_static", "dmk_vjp", "dmk_get_stats",
               "dmk_set_timing",
               "dmk_destroy", "dmk_plan_info", "dmk_plan_table"):
         getattr(lib, f).restype = c_int
@@ -142,6 +145,30 @@ class Plan:
         g = torch.empty((N, 3, self.d_u), dtype=torch.float64, device=pts.device) if grad else None
         self.eval_ptr(N, pts.data_ptr(), rho.data_ptr(), u.data_ptr(), g.data_ptr() if grad else 0)
         return u, g
+
+    def vjp(self, points, strengths, grad_u, g, want_strengths=True, want_points=True):
+        """dmk_vjp: (dL/dstrengths (N, d_rho) or None, dL/dpoints (N, 3) or None) for the upstream
+        gradient g = dL/du (N, d_u); grad_u is the field gradient returned by the forward eval.
+        CUDA float64 tensors."""
+        import torch
+        N = points.shape[0]
+        pts = points.contiguous()
+        rho = strengths.reshape(N, self.d_rho).contiguous()
+        gg = g.reshape(N, self.d_u).contiguous()
+        for t in (pts, rho, gg):
+            if not (t.is_cuda and t.dtype == torch.float64):
+                raise TypeError("points, strengths and g must be CUDA float64 tensors")
+        gu = grad_u.contiguous() if want_points else None
+        if want_points and not (gu.is_cuda and gu.dtype == torch.float64 and gu.numel() == N * 3 * self.d_u):
+            raise TypeError("grad_u must be the (N, 3, d_u) CUDA float64 field gradient of the forward eval")
+        ds = torch.empty((N, self.d_rho), dtype=torch.float64, device=pts.device) if want_strengths else None
+        dx = torch.empty((N, 3), dtype=torch.float64, device=pts.device) if want_points else None
+        vp = ctypes.c_void_p
+        _check(load().dmk_vjp(self._h, N, vp(pts.data_ptr()), vp(rho.data_ptr()),
+                              vp(gu.data_ptr()) if want_points else None, vp(gg.data_ptr()),
+                              vp(ds.data_ptr()) if want_strengths else None,
+                              vp(dx.data_ptr()) if want_points else None), self._h)
+        return ds, dx
 
     def eval_host(self, points, strengths, grad=False):
         """Host numpy arrays in, host numpy arrays out (copies inside the library)."""

@@ -55,3 +55,18 @@ def test_bad_precision_and_leaf_size():
     assert lib.dmk_plan_ex(0, 3, L, 1e-6, 1, 0, None, ctypes.byref(h)) == 1
     assert lib.dmk_plan_ex(0, 3, None, 1e-6, 1, 250, None, ctypes.byref(h)) == 1
     assert lib.dmk_destroy(None) == 0
+
+
+def test_peaks_library_exports_its_entry_point():
+    path = build.build_peaks()
+    lib = ctypes.CDLL(path)
+    assert hasattr(lib, "dmk_peak_measure")
+
+
+def test_stats_struct_matches_header():
+    """dmk_stats_t as ctypes lays it out (the binding) against the header's field list."""
+    txt = open(HDR).read()
+    body = txt[txt.index("typedef struct {", txt.index("DMK_ERR_TIMEOUT")):txt.index("} dmk_stats_t;")]
+    names = re.findall(r"^\s*(?:int32_t|int64_t|float)\s+(\w+)", body, re.M)
+    assert names == [f for f, _ in dmk.Stats._fields_]
+    assert ctypes.sizeof(dmk.Stats) == 112

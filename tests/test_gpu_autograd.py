@@ -71,3 +71,103 @@ def test_forces_finite_difference():
             xm[t, i] -= h
             fd = -(energy(xp) - energy(xm)) / (2 * h)
             assert abs(fd - Fs[t, i]) <= 10 * tol * scale + 1e-6 * abs(fd)
+
+
+def test_forces_finite_difference_fullsize_clusters():
+    """The adaptive workload at full size (N = 1e6 points in 64 Gaussian clusters, sigma 0.02,
+    balanced +-1 charges, D = 3, tol 1e-6), plain FP64 path, fixed tree: forces through autograd
+    (dmk_vjp) on a 1000-point subset (seed 2005) against central differences of the energy.
+    Moving the whole subset at once along random directions v gives the directional derivative
+    sum_a F_a . v_a from two evaluations; a few dozen single-coordinate differences follow.
+    Only points farther than 4h from every line of the finest integer grid are moved, so every
+    point keeps its integer coordinates and the forest is the same for all evaluations."""
+    N, L, D, tol, h = 1_000_000, [1.0, 1.0, 1.0], 3, 1e-6, 1e-7
+    x = W.clustered_points(N, L, 2005, n_centers=64, sigma=0.02)
+    q = W.balanced_charges(N, 2006)
+    frac = np.abs(x * 2 ** BITS - np.round(x * 2 ** BITS))
+    cand = np.nonzero(np.min(frac, axis=1) > 4 * h * 2 ** BITS)[0]
+    rng = np.random.default_rng(2005)
+    sub = rng.choice(cand, 1000, replace=False)
+    dev = torch.device("cuda", 0)
+    xt = torch.tensor(x, dtype=torch.float64, device=dev)
+    qt = torch.tensor(q, dtype=torch.float64, device=dev).reshape(N, 1)
+    pot = ag.Potential("laplace", D, L, tol, precision="fp64", n_s=250)
+    xg = xt.clone().requires_grad_(True)
+    u = pot(xg, qt)
+    E = 0.5 * (qt * u).sum()
+    (gx,) = torch.autograd.grad(E, xg)
+    F = -gx[torch.tensor(sub, device=dev)].cpu().numpy()
+    nb0 = pot.plan.stats()["n_boxes"]
+
+    def energy(dx):
+        xx = xt.clone()
+        xx[torch.tensor(sub, device=dev)] += torch.tensor(dx, dtype=torch.float64, device=dev)
+        with torch.no_grad():
+            uu = pot(xx, qt)
+        assert pot.plan.stats()["n_boxes"] == nb0
+        return 0.5 * float((qt * uu).sum())
+
+    scale = np.linalg.norm(F)
+    for k in range(4):
+        v = rng.standard_normal((1000, 3))
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        fd = -(energy(h * v) - energy(-h * v)) / (2 * h)
+        an = float(np.sum(F * v))
+        assert abs(fd - an) <= 10 * tol * scale, (k, fd, an)
+    fscale = np.sqrt(np.mean(np.sum(F ** 2, axis=1)))
+    for a in rng.choice(1000, 8, replace=False):
+        for i in range(3):
+            e = np.zeros((1000, 3))
+            e[a, i] = h
+            fd = -(energy(e) - energy(-e)) / (2 * h)
+            assert abs(fd - F[a, i]) <= 10 * tol * fscale + 1e-6 * abs(fd), (a, i, fd, F[a, i])
+
+
+@pytest.mark.parametrize("kernel,D,L", [("laplace", 2, [1.0, 1.0, 0.5]), ("laplace", 1, [1.0, 1.0, 1.0]),
+                                        ("rotlet", 3, [1.0, 1.0, 1.0]), ("stokeslet", 2, [1.0, 1.0, 1.0])])
+def test_vjp_nonneutral_upstream_gradient(kernel, D, L):
+    """L = sum_t |u_t|^2 / 2: its upstream gradient g = u does not sum to zero.  dmk_vjp's
+    position gradient against central differences of L (fixed tree), and its strength gradient
+    against the change of L under a neutral change of the strengths (exact up to the constant
+    that no neutral change sees)."""
+    N, tol, h = 1200, 1e-6, 1e-7
+    x = W.mixed_points(N, L, 95, D=D)
+    rho = W.stokes_strengths(kernel, N, 96)
+    dev = torch.device("cuda", 0)
+    xt = torch.tensor(x, dtype=torch.float64, device=dev)
+    rt = torch.tensor(rho, dtype=torch.float64, device=dev)
+    pot = ag.Potential(kernel, D, L, tol, precision="fp64", n_s=40)
+
+    def loss(xx, rr):
+        uu = pot(xx, rr)
+        return 0.5 * (uu * uu).sum()
+
+    xg = xt.clone().requires_grad_(True)
+    rg = rt.clone().requires_grad_(True)
+    Lv = loss(xg, rg)
+    gx, gr = torch.autograd.grad(Lv, (xg, rg))
+    u0 = pot(xt, rt)
+    assert abs(float(u0.sum(0).abs().max())) > 1e-3 * float(u0.abs().sum())   # g really is non-neutral
+    gx, gr = gx.cpu().numpy(), gr.cpu().numpy()
+    frac = np.abs(x * 2 ** BITS - np.round(x * 2 ** BITS))
+    cand = np.nonzero(np.min(frac, axis=1) > 4 * h * 2 ** BITS)[0]
+    rng = np.random.default_rng(97)
+    fscale = np.sqrt(np.mean(np.sum(gx ** 2, axis=1)))
+    with torch.no_grad():
+        for a in rng.choice(cand, 4, replace=False):
+            for i in range(3):
+                xp, xm = xt.clone(), xt.clone()
+                xp[a, i] += h
+                xm[a, i] -= h
+                fd = (float(loss(xp, rt)) - float(loss(xm, rt))) / (2 * h)
+                assert abs(fd - gx[a, i]) <= 10 * tol * fscale + 1e-6 * abs(fd), (a, i, fd, gx[a, i])
+        # neutral change of the strengths: +e at one point, -e at another
+        d = np.zeros_like(rho)
+        d[3] = 1.0
+        d[11] = -1.0
+        dt = torch.tensor(d, dtype=torch.float64, device=dev)
+        eps = 1e-4
+        fd = (float(loss(xt, rt + eps * dt)) - float(loss(xt, rt - eps * dt))) / (2 * eps)
+        an = float(np.sum(gr * d))
+        # the adjoint is one more evaluation of the eps-approximate sum: agreement to 10 tol
+        assert abs(fd - an) <= 10 * tol * (np.abs(gr[3]).sum() + np.abs(gr[11]).sum()), (fd, an)

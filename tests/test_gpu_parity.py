@@ -32,6 +32,9 @@ CASES = [
     ("stresslet-2P", "stresslet", 2, [1, 1, 1], 1e-6, 800, 30, "mixed", "stokes"),
     ("rotlet-3P-four-cubes", "rotlet", 3, [1, 1, 4], 1e-6, 1200, 30, "uniform", "stokes"),
     ("rotlet-1P", "rotlet", 1, [2, 1, 1], 1e-6, 800, 30, "mixed", "stokes"),
+    # the 16 cubes stacked along x3 of the stresslet/rotlet workload (cube-index DFT root)
+    ("stresslet-3P-16-cubes", "stresslet", 3, [1, 1, 16], 1e-6, 1600, 50, "uniform", "stokes"),
+    ("rotlet-3P-16-cubes", "rotlet", 3, [1, 1, 16], 1e-6, 1600, 50, "uniform", "stokes"),
 ]
 
 _oracle_cache = {}

@@ -387,3 +387,22 @@ def test_gradient_is_derivative():
         up = evaluate("laplace", 3, L, 1e-6, xp, q, n_s=10).u[t, 0]
         um = evaluate("laplace", 3, L, 1e-6, xm, q, n_s=10).u[t, 0]
         assert (up - um) / (2 * h) == pytest.approx(r.grad[t, i, 0], rel=1e-6, abs=1e-8)
+
+
+@pytest.mark.parametrize("kernel,D,L", [("laplace", 2, [1, 1, 0.5]), ("stokeslet", 1, [2, 1, 1])])
+def test_target_subset_equals_full(kernel, D, L):
+    """Restricting the leaf step to a subset of targets returns, for those targets, the values
+    of the full evaluation (same forest, far field and residual sums; only the order in which
+    numpy contracts the Chebyshev sums may differ, hence 1e-14 and not bitwise), and NaN
+    elsewhere."""
+    N = 500
+    x = workloads.mixed_points(N, L, seed=31, D=D)
+    rho = workloads.stokes_strengths(kernel, N, seed=32) if kernel != "laplace" else \
+        workloads.neutral_charges(N, seed=32).reshape(N, 1)
+    full = evaluate(kernel, D, L, 1e-6, x, rho, n_s=20, grad=True)
+    idx = np.random.default_rng(33).choice(N, 60, replace=False)
+    sub = evaluate(kernel, D, L, 1e-6, x, rho, n_s=20, grad=True, targets=idx)
+    assert rel(sub.u[idx], full.u[idx]) < 1e-14
+    assert rel(sub.grad[idx], full.grad[idx]) < 1e-14
+    rest = np.setdiff1d(np.arange(N), idx)
+    assert np.all(np.isnan(sub.u[rest])) and np.all(np.isnan(sub.grad[rest]))

@@ -37,25 +37,44 @@ def rel(a, b):
 def test_static_matches_allocating_entry_point(case):
     kernel, D, L, prec, N, n_s, bar = case
     lib = dmk.load()
+    # a fresh plan whose first evaluations go through dmk_eval_static: the plan's allocation
+    # count (tables only) must not move, and a second plan gives the allocating reference
     plan = dmk.Plan(kernel, D, L, 1e-6, precision=prec, n_s=n_s)
+    ref = dmk.Plan(kernel, D, L, 1e-6, precision=prec, n_s=n_s)
     dev = torch.device("cuda", 0)
+    allocs = plan.stats()["n_device_allocs"]
+    assert allocs > 0                     # the plan's tables
+    inputs = []
+    for seed in (11, 12):
+        inputs.append((torch.tensor(W.mixed_points(N, L, seed, D=D), dtype=torch.float64, device=dev),
+                       torch.tensor(W.stokes_strengths(kernel, N, seed + 1), dtype=torch.float64, device=dev)))
     out = []
-    for seed in (11, 12):      # two calls in a row: the shared array keeps the previous contents
-        x = torch.tensor(W.mixed_points(N, L, seed, D=D), dtype=torch.float64, device=dev)
-        rho = torch.tensor(W.stokes_strengths(kernel, N, seed + 1), dtype=torch.float64, device=dev)
-        u0 = torch.empty((N, plan.d_u), dtype=torch.float64, device=dev)
-        g0 = torch.empty((N, 3, plan.d_u), dtype=torch.float64, device=dev)
-        u1 = torch.full_like(u0, float("nan"))
-        g1 = torch.full_like(g0, float("nan"))
-        assert call(lib, "dmk_eval", plan, N, x, rho, u0, g0) == 0, lib.dmk_last_error(plan._h)
+    for x, rho in inputs:      # two calls in a row: the shared array keeps the previous contents
+        u1 = torch.full((N, plan.d_u), float("nan"), dtype=torch.float64, device=dev)
+        g1 = torch.full((N, 3, plan.d_u), float("nan"), dtype=torch.float64, device=dev)
         st = call(lib, "dmk_eval_static", plan, N, x, rho, u1, g1)
         assert st == 0, lib.dmk_last_error(plan._h).decode()
         torch.cuda.synchronize()
+        assert plan.stats()["n_device_allocs"] == allocs
+        out.append((u1, g1))
+    for (x, rho), (u1, g1) in zip(inputs, out):
+        u0 = torch.empty((N, plan.d_u), dtype=torch.float64, device=dev)
+        g0 = torch.empty((N, 3, plan.d_u), dtype=torch.float64, device=dev)
+        assert call(lib, "dmk_eval", ref, N, x, rho, u0, g0) == 0, lib.dmk_last_error(ref._h)
+        torch.cuda.synchronize()
         assert torch.isfinite(u1).all() and torch.isfinite(g1).all()
-        assert rel(u1, u0) <= bar and rel(g1, g0) <= bar
-        out.append(u1.clone())
-    assert not torch.equal(out[0], out[1])
+        # the same kernels in the same order on the same inputs: identical results
+        assert torch.equal(u1, u0) and torch.equal(g1, g0), (rel(u1, u0), rel(g1, g0), bar)
+    assert not torch.equal(out[0][0], out[1][0])
+    # after the allocating plan has run, the static entry point still matches it
+    x, rho = inputs[0]
+    u1 = torch.full((N, plan.d_u), float("nan"), dtype=torch.float64, device=dev)
+    g1 = torch.full((N, 3, plan.d_u), float("nan"), dtype=torch.float64, device=dev)
+    assert call(lib, "dmk_eval_static", ref, N, x, rho, u1, g1) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(u1, out[0][0]) and torch.equal(g1, out[0][1])
     plan.close()
+    ref.close()
 
 
 def test_static_rejects_oversize_problems():
