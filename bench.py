@@ -21,7 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
-import threading
+import tempfile
 import time
 
 import numpy as np
@@ -46,15 +46,14 @@ def peaks():
 
 
 class Clocks:
-    """Samples SM clocks and throttle reasons during the timed region."""
+    """Samples SM clocks and throttle reasons during the timed region (into a temporary file)."""
 
     def __init__(self, index=0):
         self.index = index
         self.proc = None
-        self.out = os.path.join(HERE, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.out = os.path.join(tempfile.gettempdir(), f"dmk_bench_clocks_{os.getpid()}_{index}.csv")
 
     def __enter__(self):
-        os.makedirs(os.path.dirname(self.out), exist_ok=True)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -234,6 +233,8 @@ def main():
     from paper_2606_27134_b300 import dmk, workloads as Wl
 
     torch.cuda.set_device(local_rank)
+    from paper_2606_27134_b300 import peaks as pkmod
+    measured_peaks = pkmod.measure(local_rank)
     dist = None
     if world > 1:
         import torch.distributed as tdist
@@ -324,25 +325,42 @@ def main():
     pair_ms = mixed["stage"][7]
     pairs = st["n_pairs"]
     gpairs = pairs / (pair_ms / 1e3) / 1e9 if pair_ms > 0 else None
-    # roofline of the dominant kernel, k_pair (FP32 ALU bound): algorithmic FLOPs per launch
-    # = visited pairs * F_pair, F_pair derived in the design notes
-    from paper_2606_27134_b300.roofline import pair_flops, leafexp_flops, fp32_peak_tflops, PAIR_TRAFFIC_BYTES
-    flops = pair_flops("laplace", st, grad=True)
-    pk = fp32_peak_tflops()
+    # roofline of the dominant kernel, k_pair (FP32 ALU bound): algorithmic FLOPs per launch =
+    # visited pairs x F_pair (roofline.pair_flops), over its CUDA-event duration; the peaks are
+    # the pipe throughputs measured on this GPU in this run (paper_2606_27134_b300.peaks)
+    from paper_2606_27134_b300 import roofline as rf
+    pk_meas = measured_peaks
+    pk = pk_meas["fp32_tflops"]
+    flops = rf.pair_flops("laplace", st, grad=True)
     achieved = flops / (pair_ms / 1e3) / 1e12 if pair_ms > 0 else None
     exp_ms = mixed["stage"][8]
-    exp_tf = leafexp_flops(st, N, grad=True) / (exp_ms / 1e3) / 1e12 if exp_ms > 0 else None
+    exp_tf = rf.leafexp_flops(st, N, grad=True) / (exp_ms / 1e3) / 1e12 if exp_ms > 0 else None
     roof = {"bound": "alu", "kernel": "k_pair<float, Laplace, grad>", "achieved": achieved, "peak": pk,
-            "unit": "TFLOP/s", "frac": (achieved / pk) if achieved else None, "traffic": PAIR_TRAFFIC_BYTES,
-            "peak_note": "FP32 FMA pipe: 148 SMs x 128 lanes x 2 flop x 2.032 GHz (derived from unit counts and "
-                         "the maximum SM clock; no measured FP32 peak in MEASURED_PEAKS.json)",
+            "unit": "TFLOP/s", "frac": (achieved / pk) if achieved else None, "traffic": rf.PAIR_TRAFFIC_BYTES,
+            "peak_note": "of measured: FP32 FFMA throughput of this GPU, dmk_peak_measure in this run "
+                         "(derived 148 SMs x 128 lanes x 2 x %.3f GHz = %.1f TFLOP/s)" % (
+                             rf.MAX_SM_GHZ, rf.fp32_peak_tflops()),
+            "per_unit": "%d FLOP per visited pair (22 + d_q, d_q = %d)" % (rf.pair_flops("laplace", {"n_pairs": 1,
+                        "fit_terms": st["fit_terms"]}, grad=True), max(int(st["fit_terms"]) - 1, 0)),
             "second_kernel": {"kernel": "k_leafexp<float, Laplace, grad>", "ms": exp_ms, "achieved": exp_tf,
                               "frac": (exp_tf / pk) if exp_tf else None}}
+    fp64_line = {"value": world * N / (fp64_ms / 1e3), "unit": "targets/s", "ms_per_step": fp64_ms}
+    if "fp64" in prec_results:
+        st64 = prec_results["fp64"]["stats"]
+        pair64 = prec_results["fp64"]["stage"][7]
+        if pair64 > 0:
+            a64 = rf.pair_flops("laplace", st64, grad=True) / (pair64 / 1e3) / 1e12
+            fp64_line["roofline"] = {"bound": "alu", "kernel": "k_pair<double, Laplace, grad>", "achieved": a64,
+                                     "peak": pk_meas["fp64_tflops"], "unit": "TFLOP/s",
+                                     "frac": a64 / pk_meas["fp64_tflops"],
+                                     "peak_note": "of measured: FP64 DFMA throughput, dmk_peak_measure in this run"}
+        fp64_line["stage_ms"] = dict(zip(STAGES, prec_results["fp64"]["stage"]))
     line = {"metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": dict(CONFIG, parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
-            "fp64_path": {"value": world * N / (fp64_ms / 1e3), "unit": "targets/s", "ms_per_step": fp64_ms},
+            "fp64_path": fp64_line,
+            "peaks": {k: pk_meas[k] for k in ("fp32_tflops", "fp64_tflops", "mufu_rsqrt_tops", "clocks")},
             "mixed_over_fp64": fp64_ms / step_ms,
             "p2p": {"gpairs_per_s": gpairs, "pairs_per_step": pairs, "pair_kernel_ms": pair_ms, "leaf_stage_ms": leaf_ms},
             "stage_ms": dict(zip(STAGES, mixed["stage"])),
@@ -357,17 +375,25 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             from oracle.dmk import evaluate
+            from threadpoolctl import threadpool_limits
             Ns = 4000
             xs = Wl.uniform_points(Ns, W["L"], 12345)
             qs = Wl.uniform_charges(Ns, 12346)
             t = time.perf_counter()
             evaluate("laplace", 2, W["L"], W["tol"], xs, qs, n_s=W["n_s"], grad=True)
             dt = time.perf_counter() - t
+            # the oracle is Python loops over boxes with numpy contractions: only the BLAS calls
+            # inside numpy use more than one thread; timed again with BLAS on one thread
+            with threadpool_limits(limits=1):
+                t = time.perf_counter()
+                evaluate("laplace", 2, W["L"], W["tol"], xs, qs, n_s=W["n_s"], grad=True)
+                dt1 = time.perf_counter() - t
             line["cpu_baseline"] = {"value": Ns / dt, "unit": "targets/s", "cores": len(os.sched_getaffinity(0)),
-                                    "kind": "oracle",
-                                    "sample": f"oracle (FP64 numpy) full evaluation with forces of N={Ns} uniform "
-                                              f"points, same cell/distribution/plan (25x sparser), one run "
-                                              f"({dt:.1f} s)"}
+                                    "kind": "oracle", "value_1_thread": Ns / dt1,
+                                    "sample": f"oracle (FP64 numpy, single-threaded Python with numpy's BLAS "
+                                              f"threads) full evaluation with forces of N={Ns} uniform points, same "
+                                              f"cell/distribution/plan (25x sparser), one run ({dt:.1f} s; "
+                                              f"{dt1:.1f} s with BLAS on one thread)"}
         except Exception as e:  # the baseline is reported, never required
             line["cpu_baseline"] = {"value": None, "error": str(e)}
     if rank == 0:

@@ -320,7 +320,10 @@ def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_p
                 img = w[srcs] + np.array(sh) * Lvec
                 dx = xt[:, None, :] - img[None, :, :]              # (nt, ns, 3)
                 r2 = np.sum(dx.real ** 2, axis=2)
-                ok = (r2 < nul * nul) & (r2 > 0)       # excluded: p=0 with x_t = x_s (Eq. periodic_sum)
+                # excluded: r = 0 (p = 0 with x_t = x_s, Eq. periodic_sum) and the target's own
+                # periodic images, which lie at |p| >= min periodic L_i = nu_0 >= nu, outside the
+                # support of K_R whatever the rounding of r^2 (Remark comp_supp)
+                ok = (r2 < nul * nul) & (r2 > 0) & (srcs[None, :] != t[:, None])
                 ti, si = np.nonzero(ok)
                 if len(ti) == 0:
                     continue

@@ -89,9 +89,7 @@ struct dmk_plan_s {
     size_t arena_cap = 0, arena_off = 0;
     // dynamic shared memory already opted in per kernel (the attribute persists on the device)
     std::unordered_map<const void*, size_t> smem_set;
-    // levels the point keys are sorted to (their leading 3 sort_levels bits): the depth of the
-    // last forest plus one, all kBits levels at first or after a deeper forest appears
-    int sort_levels = kBits;
+
 };
 
 namespace {
@@ -440,29 +438,19 @@ dmk_status_t resident_blocks(dmk_plan_s* plan, Kern kernel, int threads, size_t 
 
 // residual sums (k_pair, persistent: every resident block takes tasks from the counter) on
 // stream sp
-template <class T, int K, bool G, int C>
-dmk_status_t launch_pair_c(dmk_plan_s* plan, Tab<T>& tab, const int* leaves, BoxArrays B, const double* xs, int64_t N,
-                           const int* doffs, const DirectEntry* dl, LeafOut lo, const int* toffs, int tcap,
-                           const int4* tasks, int* next, cudaStream_t sp) {
-    constexpr int DR = Pair<T, K, G>::DR;
-    const size_t sm = pair_smem<T, DR, C>();
-    CKS(set_smem(plan, k_pair<T, K, G, C>, sm));
-    int per_sm = 1;
-    CKS(resident_blocks(plan, k_pair<T, K, G, C>, kPairWarps * 32, sm, &per_sm));
-    if (plan->pair_overlap && plan->pair_blocks > 0) per_sm = std::min(per_sm, plan->pair_blocks);
-    k_pair<T, K, G, C><<<per_sm * plan->n_sm, kPairWarps * 32, sm, sp>>>(leaves, B, tab, plan->geo, xs, N, doffs,
-                                                                         toffs, tcap, tasks, next, dl, lo);
-    return DMK_OK;
-}
-
-// 128-source chunks: 47 KB of shared memory per block (FP32 Laplace), so that two resident
-// blocks per SM leave room for the far-field kernels running beside them (256-source chunks
-// crowded out the upward clusters: 1.56 -> 1.72 ms per step)
 template <class T, int K, bool G>
 dmk_status_t launch_pair(dmk_plan_s* plan, Tab<T>& tab, const int* leaves, BoxArrays B, const double* xs, int64_t N,
                          const int* doffs, const DirectEntry* dl, LeafOut lo, const int* toffs, int tcap,
                          const int4* tasks, int* next, cudaStream_t sp) {
-    return launch_pair_c<T, K, G, 128>(plan, tab, leaves, B, xs, N, doffs, dl, lo, toffs, tcap, tasks, next, sp);
+    constexpr int DR = Pair<T, K, G>::DR;
+    const size_t sm = pair_smem<T, DR>();
+    CKS(set_smem(plan, k_pair<T, K, G>, sm));
+    int per_sm = 1;
+    CKS(resident_blocks(plan, k_pair<T, K, G>, kPairWarps * 32, sm, &per_sm));
+    if (plan->pair_overlap && plan->pair_blocks > 0) per_sm = std::min(per_sm, plan->pair_blocks);
+    k_pair<T, K, G><<<per_sm * plan->n_sm, kPairWarps * 32, sm, sp>>>(leaves, B, tab, plan->geo, xs, N, doffs, toffs,
+                                                                      tcap, tasks, next, dl, lo);
+    return DMK_OK;
 }
 
 // leaf expansions + residual sums + self terms (k_leafexp)
@@ -575,7 +563,13 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     const int kMissing = 64;                              // int offset of missing[] in the copy
     // ---- (1)+(2) sort on the leading key bits, gather, one-pass refinement; repeated with all
     // key bits if the forest reaches the sorted depth ----------------------------------------
-    int lsort = std::max(1, std::min(kBits, plan->sort_levels));
+    // Levels the keys are sorted to first (their leading 3 lsort bits): the depth a forest of
+    // N points with n_s per leaf reaches when they are uniform, plus four levels.  Deeper
+    // forests (clustered points) sort again on all bits.  The choice depends on N and n_s only,
+    // so the point order within a leaf -- and with it the rounding of every sum -- is the same
+    // for the same input, whatever the plan evaluated before.
+    int lsort = 4;
+    for (double cells = (double)N / plan->n_s; cells > 1.0 && lsort < kBits; cells /= 8.0) ++lsort;
     for (int attempt = 0;; ++attempt) {
         const int begin_bit = 3 * (kBits - lsort);
         size_t tmp_bytes = 0;
@@ -621,7 +615,6 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     int nlev = kBits + 1;
     for (int k = 0; k <= kBits; ++k)
         if (hmeta[k] == 0) { nlev = k + 1; break; }
-    plan->sort_levels = std::min(kBits, nlev + 1);
     for (int l = 0; l < nlev; ++l) Rl[l] = Rall + (size_t)l * cap;
     bool balanced = true;
     for (int k = 0; k < kBits; ++k)
@@ -813,8 +806,8 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         overlap = fast_leaf && plan->pair_overlap;
         CKS(ensure(plan, B_DL, (size_t)std::max<int64_t>(ti.n_entries, 1) * sizeof(DirectEntry), &vdl));
         dl = (DirectEntry*)vdl;
-        // at most nt/32 + 5 tasks per leaf
-        CKS(ensure(plan, B_TASKS, ((size_t)N / 32 + 5 * (size_t)nleaf + 1) * sizeof(int4), &vtk));
+        // at most nt / kPairTile + kPairTileLog tasks per leaf
+        CKS(ensure(plan, B_TASKS, ((size_t)N / kPairTile + (size_t)kPairTileLog * nleaf + 1) * sizeof(int4), &vtk));
         tasks = (int4*)vtk;
         const cudaStream_t sd = overlap ? plan->side : st;
         if (overlap) CK(cudaStreamWaitEvent(plan->side, plan->ev_cnt, 0));
@@ -837,7 +830,27 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     CK(cudaMemsetAsync(proxy, 0, (size_t)nb * drho * p3 * sizeof(T), st));
     CK(cudaMemsetAsync(local, 0, (size_t)nb * du * p3 * sizeof(T), st));
     launches += 2;
-    if (nleaf_cap > 0) {
+    bool anterp_done = false;
+    if constexpr (sizeof(T) == 4) {
+        if (nleaf_cap > 0 && p <= 24) {
+            const int XM = 4 * ((drho * p + 3) / 4);
+            const unsigned grid = (unsigned)std::max(1, std::min(nleaf_cap, plan->n_sm * 8));
+            if (p <= 20) {
+                const size_t sm = anterp3_smem<20, 10>(XM);
+                CKS(set_smem(plan, k_anterp3<20, 10>, sm));
+                k_anterp3<20, 10><<<grid, kAntThreads, sm, st>>>(d_nleaf, leaves, B, xs, N, rs, tab, plan->T.s,
+                                                                 (float*)proxy, XM);
+            } else {
+                const size_t sm = anterp3_smem<24, 12>(XM);
+                CKS(set_smem(plan, k_anterp3<24, 12>, sm));
+                k_anterp3<24, 12><<<grid, kAntThreads, sm, st>>>(d_nleaf, leaves, B, xs, N, rs, tab, plan->T.s,
+                                                                 (float*)proxy, XM);
+            }
+            ++launches;
+            anterp_done = true;
+        }
+    }
+    if (nleaf_cap > 0 && !anterp_done) {
         if (p <= 20) CKS((launch_anterp2<T, 20>(plan, tab, nleaf_cap, d_nleaf, leaves, B, xs, N, rs, proxy)));
         else if (p <= 24) CKS((launch_anterp2<T, 24>(plan, tab, nleaf_cap, d_nleaf, leaves, B, xs, N, rs, proxy)));
         else CKS((launch_anterp<T, 48>(plan, tab, nleaf_cap, d_nleaf, leaves, B, xs, N, rs, proxy)));
@@ -946,18 +959,22 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         void* vpw;
         CKS(ensure(plan, B_PW, (size_t)n_nl * drho * nW * sizeof(Cx<T>), &vpw));
         Cx<T>* W = (Cx<T>*)vpw;
-        // register-blocked outgoing transform: FP32 path (the FP64 tensors do not fit in shared memory)
-        const size_t po2_bytes = pwout2_smem<T>(p, NF, nfh);
+        // outgoing transform with the node and mode symmetries (k_pwout3) when its arrays fit in
+        // shared memory (the range of |m2| split in parts if needed), else the generic kernel
+        const int MH = nfh <= 16 ? 16 : (nfh <= 20 ? 20 : 0);
         bool pwout_done = false;
-        if constexpr (sizeof(T) == 4) {
-            if (p <= kMaxPFast && nfh <= mp && po2_bytes <= plan->smem_optin) {
-                const unsigned grid = (unsigned)std::min(2 * n_nl, plan->n_sm * 4);
-                if (mp == 20) {
-                    CKS(set_smem(plan, k_pwout2<T, 20>, po2_bytes));
-                    k_pwout2<T, 20><<<grid, 416, po2_bytes, st>>>(n_nl, nl_box, tab, proxy, W);
+        if (p <= kMaxPFast && MH > 0) {
+            int nsplit = 1;
+            while (nsplit < nfh && pwout3_smem<T>(p, nfh, MH, nsplit) > plan->smem_optin) ++nsplit;
+            const size_t po3 = pwout3_smem<T>(p, nfh, MH, nsplit);
+            if (po3 <= plan->smem_optin) {
+                const unsigned grid = (unsigned)std::min<int64_t>((int64_t)nsplit * n_nl, (int64_t)plan->n_sm * 2);
+                if (MH == 16) {
+                    CKS(set_smem(plan, k_pwout3<T, 16>, po3));
+                    k_pwout3<T, 16><<<grid, pw_sym_threads<T>(), po3, st>>>(n_nl, nl_box, tab, proxy, W, nsplit);
                 } else {
-                    CKS(set_smem(plan, k_pwout2<T, kMaxPFast>, po2_bytes));
-                    k_pwout2<T, kMaxPFast><<<grid, 416, po2_bytes, st>>>(n_nl, nl_box, tab, proxy, W);
+                    CKS(set_smem(plan, k_pwout3<T, 20>, po3));
+                    k_pwout3<T, 20><<<grid, pw_sym_threads<T>(), po3, st>>>(n_nl, nl_box, tab, proxy, W, nsplit);
                 }
                 ++launches;
                 pwout_done = true;
@@ -974,22 +991,30 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
             ++launches;
         }
         rec(4);
-        const int mpw = (p <= 20) ? 20 : kMaxPFast;
-        const size_t pw2_bytes =
-            ((size_t)NF * mpw + (size_t)p * NF * nfh + (size_t)p * p * (nfh | 1)) * sizeof(Cx<T>);
-        if (p <= kMaxPFast && pw2_bytes + 512 <= plan->smem_optin) {
+        const size_t pw4_bytes = MH > 0 ? pwin4_smem<T>(p, NF, nfh, MH) : 0;
+        if (p <= kMaxPFast && MH > 0 && pw4_bytes <= plan->smem_optin) {
             void* vvw;
             CKS(ensure(plan, B_VW, (size_t)n_nl * du * nW * sizeof(Cx<T>), &vvw));
             Cx<T>* Vw = (Cx<T>*)vvw;
-            const int nchunk = (int)((nW + kTransModes - 1) / kTransModes);
-            k_pw_trans<T><<<(unsigned)n_nl * nchunk, kTransThreads, 0, st>>>(n_nl, nl_box, B, tab, W, Vw);
-            const unsigned grid = (unsigned)std::min(n_nl, plan->n_sm * 4);
-            if (mpw == 20) {
-                CKS(set_smem(plan, k_pwin3<T, 20>, pw2_bytes));
-                k_pwin3<T, 20><<<grid, 384, pw2_bytes, st>>>(n_nl, nl_box, tab, Vw, local);
+            const int nchunk = (int)((nW + kTransThreads - 1) / kTransThreads);
+            const unsigned tgrid = (unsigned)(((nchunk + kTransGroup - 1) / kTransGroup) * (int64_t)n_nl * kTransGroup);
+            if (drho == 1) {
+                k_pw_trans<T, 1, true><<<tgrid, kTransThreads, 0, st>>>(n_nl, nl_box, B, tab, W, 1, Vw);
+            } else if (drho == 3) {
+                k_pw_trans<T, 3, true><<<tgrid, kTransThreads, 0, st>>>(n_nl, nl_box, B, tab, W, 3, Vw);
             } else {
-                CKS(set_smem(plan, k_pwin3<T, kMaxPFast>, pw2_bytes));
-                k_pwin3<T, kMaxPFast><<<grid, 384, pw2_bytes, st>>>(n_nl, nl_box, tab, Vw, local);
+                k_pw_symbol<T, 9><<<nblk((int64_t)n_nl * nW, kTransThreads), kTransThreads, 0, st>>>(n_nl, nl_box, B,
+                                                                                                   tab, W);
+                k_pw_trans<T, 3, false><<<tgrid, kTransThreads, 0, st>>>(n_nl, nl_box, B, tab, W, drho, Vw);
+                ++launches;
+            }
+            const unsigned grid = (unsigned)std::min<int64_t>(n_nl, (int64_t)plan->n_sm * 2);
+            if (MH == 16) {
+                CKS(set_smem(plan, k_pwin4<T, 16>, pw4_bytes));
+                k_pwin4<T, 16><<<grid, pw_sym_threads<T>(), pw4_bytes, st>>>(n_nl, nl_box, tab, Vw, local);
+            } else {
+                CKS(set_smem(plan, k_pwin4<T, 20>, pw4_bytes));
+                k_pwin4<T, 20><<<grid, pw_sym_threads<T>(), pw4_bytes, st>>>(n_nl, nl_box, tab, Vw, local);
             }
             launches += 2;
         } else {

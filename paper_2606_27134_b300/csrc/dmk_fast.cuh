@@ -175,6 +175,7 @@ __global__ void __launch_bounds__(kLeaf2Threads) k_leaf2(int nleaf, const int* _
     constexpr bool kTwo = sizeof(T) == 4;
     constexpr int kLo = kTwo ? kSrcChunk : 1;
     __shared__ T sx[kSrcChunk], sy[kSrcChunk], sz[kSrcChunk], sinv[kSrcChunk], snu2[kSrcChunk];
+    __shared__ int sidx[kSrcChunk];
     __shared__ T sxl[kLo], syl[kLo], szl[kLo];
     __shared__ T tv[kLeaf2Threads / 32][4][64];
     // dynamic: the in-support queue (source slot per (position, thread)) and staged strengths
@@ -315,6 +316,7 @@ __global__ void __launch_bounds__(kLeaf2Threads) k_leaf2(int nleaf, const int* _
                         }
                         sinv[slot] = (T)inv;
                         snu2[slot] = (T)(1.0 / (inv * inv));
+                        sidx[slot] = si;
                         for (int a = 0; a < DR; ++a) sr[slot][a] = (T)out.rs[(int64_t)si * DR + a];
                     }
                     filled += take;
@@ -332,7 +334,8 @@ __global__ void __launch_bounds__(kLeaf2Threads) k_leaf2(int nleaf, const int* _
                             dz += xtl[2] - szl[k];
                         }
                         const T r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 < snu2[k] && r2 > T(0)) q[cnt++][tt] = (unsigned char)k;
+                        // r = 0 and the target's own periodic images (|p| >= nu_0) are dropped
+                        if (r2 < snu2[k] && r2 > T(0) && sidx[k] != t0 + tt) q[cnt++][tt] = (unsigned char)k;
                     }
                     T acc[DU], gacc[3 * DU];
                     for (int j = 0; j < DU; ++j) acc[j] = 0;
@@ -386,58 +389,37 @@ namespace dmk {
 // V(m) = sum over non-leaf colleagues C at offset d of exp(-i (2 pi/3) m.d) W_C(m), then
 // component j of op(m) V (App. B symbols on the integer wave vector; see apply_op).  DR is the
 // strength dimension, a template argument so that V stays in registers.
-template <class T, int DR>
-__device__ __forceinline__ Cx<T> pw_gather_op(int kernel, int j, int m1, int m2, int m3, size_t e, size_t nW,
-                                             int ncol, const int* col_nl, const int* col_d,
-                                             const Cx<T>* __restrict__ W) {
-    const T c3 = T(-0.5), s3 = T(-0.86602540378443864676);   // exp(-i 2 pi/3)
-    // colleagues in batches of KB with all loads of a batch issued before the first FMA, so
-    // that each thread keeps several L2 requests in flight
-    constexpr int KB = DR == 1 ? 9 : (DR == 3 ? 3 : 1);
-    Cx<T> V[DR == 1 ? 1 : 9];
-#pragma unroll
-    for (int a = 0; a < DR; ++a) V[a] = {0, 0};
-    for (int k0 = 0; k0 < ncol; k0 += KB) {
-        Cx<T> w[KB][DR];
-#pragma unroll
-        for (int kk = 0; kk < KB; ++kk) {
-            const int k = k0 + kk;
-            const Cx<T>* Wc = W + (size_t)col_nl[k < ncol ? k : 0] * DR * nW + e;
-#pragma unroll
-            for (int a = 0; a < DR; ++a) w[kk][a] = (k < ncol) ? Wc[(size_t)a * nW] : Cx<T>{0, 0};
-        }
-#pragma unroll
-        for (int kk = 0; kk < KB; ++kk) {
-            const int d = col_d[k0 + kk < ncol ? k0 + kk : 0];
-            const int dot = m1 * (d % 3 - 1) + m2 * ((d / 3) % 3 - 1) + m3 * (d / 9 - 1);
-            const int r = ((dot % 3) + 3) % 3;
-            const Cx<T> ph = (r == 0) ? Cx<T>{1, 0} : (r == 1 ? Cx<T>{c3, s3} : Cx<T>{c3, -s3});
-#pragma unroll
-            for (int a = 0; a < DR; ++a) cfma(V[a], ph, w[kk][a]);
-        }
-    }
-    if (DR == 1) return V[0];
-    const T mv[3] = {(T)m1, (T)m2, (T)m3};
-    Cx<T> out[3];
-    apply_op<T>(kernel, mv, V, out);
-    return j == 0 ? out[0] : (j == 1 ? out[1] : out[2]);
+// Translation + difference-kernel symbol (Sec. 3.1.4), one thread per (non-leaf box, mode):
+//   V(m) = 2^(a l) g(m) op(m) sum_C exp(-i (2 pi/3) m.d_C) W_C(m)
+// over the non-leaf colleagues C (offset d_C).  The symbol -- the scalar 2^(a l) g(m) and the
+// tensor op(m) of App. B mapping d_rho strength components to d_u -- depends on the mode only,
+// so it commutes with the sum over colleagues.  For d_rho <= 3 it is applied after the sum
+// (OP = true, NC = d_rho gathered components); for the stresslet (d_rho = 9, d_u = 3),
+// k_pw_symbol applies it to every box's spectrum first, in place, so that the translation
+// gathers 3 components instead of 9 (OP = false, NC = 3).  Each thread gathers its mode once
+// for all output components.  Blocks are ordered (group of kTransGroup mode blocks, box, mode
+// block) so that the boxes running together share their colleagues' spectra in L2.
+constexpr int kTransThreads = 256;
+constexpr int kTransGroup = 8;
+
+// exp(-i (2 pi/3) r) for r = 0, 1, 2
+template <class T>
+__device__ __forceinline__ Cx<T> third_root(int r) {
+    const T c3 = T(-0.5), s3 = T(-0.86602540378443864676);
+    return (r == 0) ? Cx<T>{1, 0} : (r == 1 ? Cx<T>{c3, s3} : Cx<T>{c3, -s3});
 }
 
-// Translation + difference-kernel symbol (Sec. 3.1.4), one thread per (non-leaf box, mode):
-//   V_j(m) = 2^(a l) g(m) [op(m) sum_C exp(-i (2 pi/3) m.d_C) W_C(m)]_j
-// over the non-leaf colleagues C (offset d_C), written per box as du x nW complex values for the
-// incoming transform.  CTA = (box, block of kTransModes modes).
-constexpr int kTransThreads = 256;
-constexpr int kTransModes = 512;
-
-template <class T>
+template <class T, int NC, bool OP>
 __global__ void __launch_bounds__(kTransThreads) k_pw_trans(int n, const int* __restrict__ nl_box, BoxArrays B,
-                                                            Tab<T> tab, const Cx<T>* __restrict__ W,
+                                                            Tab<T> tab, const Cx<T>* __restrict__ W, int wstride,
                                                             Cx<T>* __restrict__ Vw) {
-    const int drho = tab.d_rho, du = tab.d_u, nf = tab.nf, NF = tab.NF, nfh = tab.nfh;
+    const int du = tab.d_u, nf = tab.nf, NF = tab.NF, nfh = tab.nfh;
     const int nW = NF * NF * nfh;
-    const int nchunk = (nW + kTransModes - 1) / kTransModes;
-    const int bi = blockIdx.x / nchunk, e0 = (blockIdx.x % nchunk) * kTransModes;
+    const int nchunk = (nW + kTransThreads - 1) / kTransThreads;
+    const int gsz = n * kTransGroup;
+    const int grp = blockIdx.x / gsz, rem = blockIdx.x - grp * gsz;
+    const int bi = rem / kTransGroup, chunk = grp * kTransGroup + rem % kTransGroup;
+    if (chunk >= nchunk) return;
     __shared__ int ncol;
     __shared__ int col_nl[27];
     __shared__ int col_d[27];
@@ -451,23 +433,73 @@ __global__ void __launch_bounds__(kTransThreads) k_pw_trans(int n, const int* __
         ncol = k;
     }
     __syncthreads();
-    const T scale = (T)ldexp(1.0, tab.level_power * B.level[box]);
-    const int e1 = min(nW, e0 + kTransModes);
-    for (int e = e0 + threadIdx.x; e < e1; e += kTransThreads) {
-        const int i1 = e / (NF * nfh), i2 = (e / nfh) % NF, m3 = e % nfh;
-        const int m1 = i1 - nf, m2 = i2 - nf;
-        const T gs = scale * tab.gdiff[e];
-        for (int j = 0; j < du; ++j) {
-            Cx<T> o;
-            if (drho == 1)
-                o = pw_gather_op<T, 1>(tab.kernel, j, m1, m2, m3, e, nW, ncol, col_nl, col_d, W);
-            else if (drho == 3)
-                o = pw_gather_op<T, 3>(tab.kernel, j, m1, m2, m3, e, nW, ncol, col_nl, col_d, W);
-            else
-                o = pw_gather_op<T, 9>(tab.kernel, j, m1, m2, m3, e, nW, ncol, col_nl, col_d, W);
-            Vw[((size_t)bi * du + j) * nW + e] = {gs * o.x, gs * o.y};
+    const int e = chunk * kTransThreads + threadIdx.x;
+    if (e >= nW) return;
+    const int i1 = e / (NF * nfh), i2 = (e / nfh) % NF, m3 = e % nfh;
+    const int m1 = i1 - nf, m2 = i2 - nf;
+    // m mod 3 per axis, in 0..2
+    const int r1 = ((m1 % 3) + 3) % 3, r2 = ((m2 % 3) + 3) % 3, r3 = m3 % 3;
+    // colleagues in batches of KB, all loads of a batch issued before the first FMA
+    constexpr int KB = NC == 1 ? 9 : 3;
+    Cx<T> V[NC];
+#pragma unroll
+    for (int a = 0; a < NC; ++a) V[a] = {0, 0};
+    const int nc = ncol;
+    for (int k0 = 0; k0 < nc; k0 += KB) {
+        Cx<T> w[KB][NC];
+#pragma unroll
+        for (int kk = 0; kk < KB; ++kk) {
+            const int k = k0 + kk;
+            const Cx<T>* Wc = W + (size_t)col_nl[k < nc ? k : 0] * wstride * nW + e;
+#pragma unroll
+            for (int a = 0; a < NC; ++a) w[kk][a] = (k < nc) ? Wc[(size_t)a * nW] : Cx<T>{0, 0};
+        }
+#pragma unroll
+        for (int kk = 0; kk < KB; ++kk) {
+            const int d = col_d[k0 + kk < nc ? k0 + kk : 0];
+            const int t = r1 * (d % 3 - 1) + r2 * ((d / 3) % 3 - 1) + r3 * (d / 9 - 1) + 6;   // 0..12
+            const Cx<T> ph = third_root<T>(t % 3);
+#pragma unroll
+            for (int a = 0; a < NC; ++a) cfma(V[a], ph, w[kk][a]);
         }
     }
+    if constexpr (OP) {
+        const T gs = (T)ldexp(1.0, tab.level_power * B.level[box]) * tab.gdiff[e];
+        Cx<T> out[3];
+        if constexpr (NC == 1) {
+            out[0] = V[0];
+        } else {
+            const T mv[3] = {(T)m1, (T)m2, (T)m3};
+            apply_op<T>(tab.kernel, mv, V, out);
+        }
+        for (int j = 0; j < du; ++j) Vw[((size_t)bi * du + j) * nW + e] = {gs * out[j].x, gs * out[j].y};
+    } else {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) Vw[((size_t)bi * NC + j) * nW + e] = V[j];
+    }
+}
+
+// The symbol 2^(a l) g(m) op(m) applied to every non-leaf box's outgoing spectrum in place: the
+// d_u results overwrite the first d_u of the d_rho component slots (thread per (box, mode); each
+// thread reads its own d_rho values before it writes).  Used for the stresslet (d_rho = 9).
+template <class T, int DR>
+__global__ void __launch_bounds__(kTransThreads) k_pw_symbol(int n, const int* __restrict__ nl_box, BoxArrays B,
+                                                             Tab<T> tab, Cx<T>* __restrict__ W) {
+    const int nf = tab.nf, NF = tab.NF, nfh = tab.nfh, du = tab.d_u;
+    const int nW = NF * NF * nfh;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * nW) return;
+    const int bi = (int)(t / nW), e = (int)(t - (int64_t)bi * nW);
+    const int i1 = e / (NF * nfh), i2 = (e / nfh) % NF, m3 = e % nfh;
+    const T mv[3] = {(T)(i1 - nf), (T)(i2 - nf), (T)m3};
+    Cx<T>* Wb = W + (size_t)bi * DR * nW + e;
+    Cx<T> V[DR];
+#pragma unroll
+    for (int a = 0; a < DR; ++a) V[a] = Wb[(size_t)a * nW];
+    Cx<T> out[3];
+    apply_op<T>(tab.kernel, mv, V, out);
+    const T gs = (T)ldexp(1.0, tab.level_power * B.level[nl_box[bi]]) * tab.gdiff[e];
+    for (int j = 0; j < du; ++j) Wb[(size_t)j * nW] = {gs * out[j].x, gs * out[j].y};
 }
 
 // Plane-wave outgoing expansions (Sec. 3.1.4, Eq. Dl_int_discr), register-blocked: for every
@@ -560,6 +592,182 @@ __global__ void __launch_bounds__(416, MAXP <= 20 ? 2 : 1) k_pwout2(int n, const
             }
         }
     }
+}
+
+// Plane-wave outgoing expansions with the symmetries of the nodes and of the modes (Sec.
+// 3.1.4, Eq. Dl_int_discr): W(m) = sum_j proxy(j) exp(-i theta m . eta_j), theta = pi / 3,
+// m3 >= 0 only (real input).  With C(m, k) = cos(theta m eta_k) and S(m, k) = sin(theta m eta_k),
+// the first-kind nodes satisfy eta_{p-1-k} = -eta_k, so along one axis C is even and S odd
+// about the middle node, and in m C is even and S odd.  One 1-D stage on a complex column
+// A = R - i I (I = 0 for the first, real, stage) then reads, with the even and odd parts
+// Re_k = R_k + R_{p-1-k}, Ro_k = R_k - R_{p-1-k} (Ie, Io likewise; k < p/2, plus the middle
+// node eta = 0 for odd p):
+//   P = sum Re C, Q = sum Io S, U = sum Ro S, V = sum Ie C,
+//   A'(+m) = (P - Q) - i (U + V),   A'(-m) = (P + Q) - i (V - U),
+// i.e. p real FMA per complex output instead of 4 p.  Stage 1 (j3 -> m3 >= 0, thread per (j1,
+// j2) fiber), stage 2 (j2 -> m2, thread per (j1, m3) column, the range of |m2| split in nsplit
+// parts when shared memory is short), stage 3 (j1 -> m1, thread per (m2, m3) column), real
+// parts in separate arrays.  Work item = (box, part of |m2|); stage 1 is repeated per part.
+template <class T>
+constexpr int pw_sym_threads() { return sizeof(T) == 4 ? 512 : 256; }
+
+template <class T, int MH>
+__global__ void __launch_bounds__(pw_sym_threads<T>(), 1) k_pwout3(int n, const int* __restrict__ nl_box, Tab<T> tab,
+                                                   const T* __restrict__ proxy, Cx<T>* __restrict__ W, int nsplit) {
+    const int p = tab.p, p2 = p * p, p3 = p2 * p, P = odd_pitch(p), drho = tab.d_rho;
+    const int nf = tab.nf, NF = tab.NF, nfh = tab.nfh, nW = NF * NF * nfh;
+    const int hp = p >> 1, odd = p & 1, pm3 = nfh | 1;
+    const int hcn = (nfh + nsplit - 1) / nsplit;            // |m2| values per part
+    T* Ct = reinterpret_cast<T*>(dsmem);                     // hp x MH: C(m, k) at [k][m]
+    T* St = Ct + hp * MH;                                    // hp x MH: S(m, k)
+    T* R1 = St + hp * MH;                                    // p^2 x pm3
+    T* I1 = R1 + p2 * pm3;
+    T* R2 = I1 + p2 * pm3;                                   // p x (2 hcn) x nfh, slot = 2 i + (m2 < 0)
+    T* I2 = R2 + p * 2 * hcn * nfh;
+    T* X = R2;                                               // p^2 x P (stage 1 input), aliases R2/I2
+    for (int e = threadIdx.x; e < hp * MH; e += blockDim.x) {
+        const int k = e / MH, m = e % MH;
+        const Cx<T> v = (m < nfh) ? tab.E[(m + nf) * p + k] : Cx<T>{0, 0};   // exp(-i theta m eta_k)
+        Ct[e] = v.x;
+        St[e] = -v.y;
+    }
+    for (int w = blockIdx.x; w < nsplit * n; w += gridDim.x) {
+        const int bi = w / nsplit, part = w % nsplit;
+        const int a0 = part * hcn, hc = min(hcn, nfh - a0);
+        if (hc <= 0) continue;
+        const int box = nl_box[bi];
+        for (int a = 0; a < drho; ++a) {
+            __syncthreads();
+            load_padded_batched<T, kMaxPFast>(X, proxy + ((size_t)box * drho + a) * p3, p, P);
+            __syncthreads();
+            // stage 1: j3 -> m3, real input
+            for (int c = threadIdx.x; c < p2; c += blockDim.x) {
+                T ev[kMaxPFast / 2], od[kMaxPFast / 2];
+#pragma unroll
+                for (int k = 0; k < kMaxPFast / 2; ++k) {
+                    const T x0 = (k < hp) ? X[c * P + k] : T(0), x1 = (k < hp) ? X[c * P + p - 1 - k] : T(0);
+                    ev[k] = x0 + x1;
+                    od[k] = x0 - x1;
+                }
+                const T mid = odd ? X[c * P + hp] : T(0);
+                T r[MH], im[MH];
+#pragma unroll
+                for (int m = 0; m < MH; ++m) { r[m] = mid; im[m] = 0; }
+#pragma unroll
+                for (int k = 0; k < kMaxPFast / 2; ++k) {
+                    if (k < hp) {
+                        const Quad<T>* cr = reinterpret_cast<const Quad<T>*>(Ct + k * MH);
+                        const Quad<T>* sr = reinterpret_cast<const Quad<T>*>(St + k * MH);
+#pragma unroll
+                        for (int q = 0; q < MH / 4; ++q) {
+                            const Quad<T> cv = cr[q], sv = sr[q];
+                            r[4 * q] = fma(ev[k], cv.x, r[4 * q]);
+                            r[4 * q + 1] = fma(ev[k], cv.y, r[4 * q + 1]);
+                            r[4 * q + 2] = fma(ev[k], cv.z, r[4 * q + 2]);
+                            r[4 * q + 3] = fma(ev[k], cv.w, r[4 * q + 3]);
+                            im[4 * q] = fma(od[k], sv.x, im[4 * q]);
+                            im[4 * q + 1] = fma(od[k], sv.y, im[4 * q + 1]);
+                            im[4 * q + 2] = fma(od[k], sv.z, im[4 * q + 2]);
+                            im[4 * q + 3] = fma(od[k], sv.w, im[4 * q + 3]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < MH; ++m)
+                    if (m < nfh) { R1[c * pm3 + m] = r[m]; I1[c * pm3 + m] = im[m]; }
+            }
+            __syncthreads();
+            // stage 2: j2 -> m2 for |m2| in [a0, a0 + hc), both signs
+            for (int c = threadIdx.x; c < p * nfh; c += blockDim.x) {
+                const int j1 = c / nfh, m3 = c % nfh;
+                const T* r1 = R1 + (size_t)j1 * p * pm3 + m3;
+                const T* i1 = I1 + (size_t)j1 * p * pm3 + m3;
+                T Pa[MH], Qa[MH], Ua[MH], Va[MH];
+                const T rm = odd ? r1[hp * pm3] : T(0), im_ = odd ? i1[hp * pm3] : T(0);
+#pragma unroll
+                for (int m = 0; m < MH; ++m) { Pa[m] = rm; Va[m] = im_; Qa[m] = 0; Ua[m] = 0; }
+                for (int k = 0; k < hp; ++k) {
+                    const T ra = r1[k * pm3], rb = r1[(p - 1 - k) * pm3];
+                    const T ia = i1[k * pm3], ib = i1[(p - 1 - k) * pm3];
+                    const T re = ra + rb, ro = ra - rb, ie = ia + ib, io = ia - ib;
+                    const T* cr = Ct + k * MH + a0;
+                    const T* sr = St + k * MH + a0;
+#pragma unroll
+                    for (int m = 0; m < MH; ++m) {
+                        if (m < hc) {
+                            const T cv = cr[m], sv = sr[m];
+                            Pa[m] = fma(re, cv, Pa[m]);
+                            Va[m] = fma(ie, cv, Va[m]);
+                            Qa[m] = fma(io, sv, Qa[m]);
+                            Ua[m] = fma(ro, sv, Ua[m]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < MH; ++m) {
+                    if (m < hc) {
+                        const int sp = ((j1 * 2 * hcn) + 2 * m) * nfh + m3, sm = sp + nfh;
+                        R2[sp] = Pa[m] - Qa[m];
+                        I2[sp] = Ua[m] + Va[m];
+                        R2[sm] = Pa[m] + Qa[m];
+                        I2[sm] = Va[m] - Ua[m];
+                    }
+                }
+            }
+            __syncthreads();
+            // stage 3: j1 -> m1, all m1, written to W[nl][a][(m1 NF + m2) nfh + m3]
+            Cx<T>* out = W + ((size_t)bi * drho + a) * nW;
+            for (int c = threadIdx.x; c < 2 * hc * nfh; c += blockDim.x) {
+                const int slot = c / nfh, m3 = c % nfh;
+                const int mi = slot >> 1, neg = slot & 1;
+                const int m2 = neg ? -(a0 + mi) : (a0 + mi);
+                if (neg && m2 == 0) continue;
+                const T* r2 = R2 + (size_t)slot * nfh + m3;
+                const T* i2 = I2 + (size_t)slot * nfh + m3;
+                const int cs = 2 * hcn * nfh;                    // stride of j1
+                T Pa[MH], Qa[MH], Ua[MH], Va[MH];
+                const T rm = odd ? r2[hp * cs] : T(0), im_ = odd ? i2[hp * cs] : T(0);
+#pragma unroll
+                for (int m = 0; m < MH; ++m) { Pa[m] = rm; Va[m] = im_; Qa[m] = 0; Ua[m] = 0; }
+                for (int k = 0; k < hp; ++k) {
+                    const T ra = r2[k * cs], rb = r2[(p - 1 - k) * cs];
+                    const T ia = i2[k * cs], ib = i2[(p - 1 - k) * cs];
+                    const T re = ra + rb, ro = ra - rb, ie = ia + ib, io = ia - ib;
+                    const Quad<T>* cr = reinterpret_cast<const Quad<T>*>(Ct + k * MH);
+                    const Quad<T>* sr = reinterpret_cast<const Quad<T>*>(St + k * MH);
+#pragma unroll
+                    for (int q = 0; q < MH / 4; ++q) {
+                        const Quad<T> cv = cr[q], sv = sr[q];
+                        const T cc[4] = {cv.x, cv.y, cv.z, cv.w}, ss[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            Pa[4 * q + u] = fma(re, cc[u], Pa[4 * q + u]);
+                            Va[4 * q + u] = fma(ie, cc[u], Va[4 * q + u]);
+                            Qa[4 * q + u] = fma(io, ss[u], Qa[4 * q + u]);
+                            Ua[4 * q + u] = fma(ro, ss[u], Ua[4 * q + u]);
+                        }
+                    }
+                }
+                const size_t col = (size_t)(m2 + nf) * nfh + m3;
+#pragma unroll
+                for (int m = 0; m < MH; ++m) {
+                    if (m < nfh) {
+                        // W = R - i I with R, I the real and (minus) imaginary parts
+                        out[(size_t)(m + nf) * NF * nfh + col] = {Pa[m] - Qa[m], -(Ua[m] + Va[m])};
+                        if (m > 0) out[(size_t)(nf - m) * NF * nfh + col] = {Pa[m] + Qa[m], -(Va[m] - Ua[m])};
+                    }
+                }
+            }
+        }
+    }
+}
+
+// shared memory of k_pwout3 for nsplit parts of |m2|
+template <class T>
+inline size_t pwout3_smem(int p, int nfh, int MH, int nsplit) {
+    const int hp = p / 2, pm3 = nfh | 1, P = p | 1, hcn = (nfh + nsplit - 1) / nsplit;
+    const size_t r2 = (size_t)2 * p * 2 * hcn * nfh, x = (size_t)p * p * P;
+    return ((size_t)2 * hp * MH + (size_t)2 * p * p * pm3 + std::max(r2, x)) * sizeof(T);
 }
 
 // shared memory of k_pwout2
@@ -657,6 +865,167 @@ __global__ void __launch_bounds__(384) k_pwin3(int n, const int* __restrict__ nl
     }
 }
 
+// Incoming transform with the same symmetries (Sec. 3.1.4): u(j) += Re sum_m w(m3) V(m)
+// exp(+i theta m . eta_j) over the half spectrum m3 >= 0 (w = 1 for m3 = 0, else 2).  Along
+// one axis, for a complex column V(m) = a_m + i b_m, V(-m) = c_m + i d_m and the mirrored node
+// pair (k, p-1-k):
+//   Ap = sum (a+c) C, Bp = sum (b+d) C, As = sum (a-c) S, Bs = sum (b-d) S   (m >= 0; V(0) once)
+//   B(k) = (Ap - Bs) + i (Bp + As),   B(p-1-k) = (Ap + Bs) + i (Bp - As),
+// the middle node (odd p) taking sum (a+c) + i sum (b+d).  Stage A (m1 -> j1, thread per (m2,
+// m3) column read from global memory), stage B (m2 -> j2, thread per (j1, m3)), stage C (m3 ->
+// j3, real part with the weights, thread per (j1, j2) fiber), real parts in separate arrays.
+template <class T, int MH>
+__global__ void __launch_bounds__(pw_sym_threads<T>(), 1) k_pwin4(int n, const int* __restrict__ nl_box, Tab<T> tab,
+                                                  const Cx<T>* __restrict__ Vw, T* __restrict__ local) {
+    const int p = tab.p, p2 = p * p, p3 = p2 * p, du = tab.d_u;
+    const int nf = tab.nf, NF = tab.NF, nfh = tab.nfh, nW = NF * NF * nfh;
+    const int hp = p >> 1, odd = p & 1, pm3 = nfh | 1;
+    constexpr int HPM = kMaxPFast / 2;
+    T* Ct = reinterpret_cast<T*>(dsmem);                     // MH x HPM: C(m, k) at [m][k]
+    T* St = Ct + MH * HPM;
+    T* Ar = St + MH * HPM;                                   // p x NF x nfh: stage A output
+    T* Ai = Ar + (size_t)p * NF * nfh;
+    T* Br = Ai + (size_t)p * NF * nfh;                       // p^2 x pm3: stage B output
+    T* Bi = Br + (size_t)p2 * pm3;
+    for (int e = threadIdx.x; e < MH * HPM; e += blockDim.x) {
+        const int m = e / HPM, k = e % HPM;
+        const Cx<T> v = (m < nfh && k < hp) ? tab.E[(m + nf) * p + k] : Cx<T>{0, 0};
+        Ct[e] = v.x;
+        St[e] = -v.y;
+    }
+    for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
+        const int box = nl_box[bi];
+        for (int j = 0; j < du; ++j) {
+            __syncthreads();
+            const Cx<T>* V = Vw + ((size_t)bi * du + j) * nW;
+            // stage A: m1 -> j1 for every (m2, m3) column
+            for (int c = threadIdx.x; c < NF * nfh; c += blockDim.x) {
+                T Ap[HPM + 1], Bp[HPM + 1], As[HPM], Bs[HPM];
+#pragma unroll
+                for (int k = 0; k <= HPM; ++k) { Ap[k] = 0; Bp[k] = 0; }
+#pragma unroll
+                for (int k = 0; k < HPM; ++k) { As[k] = 0; Bs[k] = 0; }
+                for (int m = 0; m < nfh; ++m) {
+                    const Cx<T> vp = V[(size_t)(nf + m) * NF * nfh + c];
+                    const Cx<T> vm = (m > 0) ? V[(size_t)(nf - m) * NF * nfh + c] : Cx<T>{0, 0};
+                    const T sa = vp.x + vm.x, sb = vp.y + vm.y, da = vp.x - vm.x, db = vp.y - vm.y;
+                    const T* cr = Ct + m * HPM;
+                    const T* sr = St + m * HPM;
+#pragma unroll
+                    for (int k = 0; k < HPM; ++k) {
+                        const T cv = cr[k], sv = sr[k];
+                        Ap[k] = fma(sa, cv, Ap[k]);
+                        Bp[k] = fma(sb, cv, Bp[k]);
+                        As[k] = fma(da, sv, As[k]);
+                        Bs[k] = fma(db, sv, Bs[k]);
+                    }
+                    Ap[HPM] += sa;                             // middle node (odd p)
+                    Bp[HPM] += sb;
+                }
+                const int i2 = c / nfh, m3 = c % nfh;
+#pragma unroll
+                for (int k = 0; k < HPM; ++k) {
+                    if (k < hp) {
+                        const size_t o0 = ((size_t)k * NF + i2) * nfh + m3, o1 = ((size_t)(p - 1 - k) * NF + i2) * nfh + m3;
+                        Ar[o0] = Ap[k] - Bs[k];
+                        Ai[o0] = Bp[k] + As[k];
+                        Ar[o1] = Ap[k] + Bs[k];
+                        Ai[o1] = Bp[k] - As[k];
+                    }
+                }
+                if (odd) {
+                    const size_t om = ((size_t)hp * NF + i2) * nfh + m3;
+                    Ar[om] = Ap[HPM];
+                    Ai[om] = Bp[HPM];
+                }
+            }
+            __syncthreads();
+            // stage B: m2 -> j2 for every (j1, m3)
+            for (int c = threadIdx.x; c < p * nfh; c += blockDim.x) {
+                const int j1 = c / nfh, m3 = c % nfh;
+                const T* ar = Ar + (size_t)j1 * NF * nfh + m3;
+                const T* ai = Ai + (size_t)j1 * NF * nfh + m3;
+                T Ap[HPM + 1], Bp[HPM + 1], As[HPM], Bs[HPM];
+#pragma unroll
+                for (int k = 0; k <= HPM; ++k) { Ap[k] = 0; Bp[k] = 0; }
+#pragma unroll
+                for (int k = 0; k < HPM; ++k) { As[k] = 0; Bs[k] = 0; }
+                for (int m = 0; m < nfh; ++m) {
+                    const T pa = ar[(nf + m) * nfh], pb = ai[(nf + m) * nfh];
+                    const T ma = (m > 0) ? ar[(nf - m) * nfh] : T(0), mb = (m > 0) ? ai[(nf - m) * nfh] : T(0);
+                    const T sa = pa + ma, sb = pb + mb, da = pa - ma, db = pb - mb;
+                    const T* cr = Ct + m * HPM;
+                    const T* sr = St + m * HPM;
+#pragma unroll
+                    for (int k = 0; k < HPM; ++k) {
+                        const T cv = cr[k], sv = sr[k];
+                        Ap[k] = fma(sa, cv, Ap[k]);
+                        Bp[k] = fma(sb, cv, Bp[k]);
+                        As[k] = fma(da, sv, As[k]);
+                        Bs[k] = fma(db, sv, Bs[k]);
+                    }
+                    Ap[HPM] += sa;
+                    Bp[HPM] += sb;
+                }
+#pragma unroll
+                for (int k = 0; k < HPM; ++k) {
+                    if (k < hp) {
+                        const size_t o0 = ((size_t)j1 * p + k) * pm3 + m3, o1 = ((size_t)j1 * p + p - 1 - k) * pm3 + m3;
+                        Br[o0] = Ap[k] - Bs[k];
+                        Bi[o0] = Bp[k] + As[k];
+                        Br[o1] = Ap[k] + Bs[k];
+                        Bi[o1] = Bp[k] - As[k];
+                    }
+                }
+                if (odd) {
+                    const size_t om = ((size_t)j1 * p + hp) * pm3 + m3;
+                    Br[om] = Ap[HPM];
+                    Bi[om] = Bp[HPM];
+                }
+            }
+            __syncthreads();
+            // stage C: m3 -> j3, real part with the half-spectrum weights
+            T* u = local + ((size_t)box * du + j) * p3;
+            for (int c = threadIdx.x; c < p2; c += blockDim.x) {
+                const T* br = Br + (size_t)c * pm3;
+                const T* bim = Bi + (size_t)c * pm3;
+                T X1[HPM + 1], X2[HPM];
+#pragma unroll
+                for (int k = 0; k <= HPM; ++k) X1[k] = 0;
+#pragma unroll
+                for (int k = 0; k < HPM; ++k) X2[k] = 0;
+                for (int m = 0; m < nfh; ++m) {
+                    const T wgt = (m == 0) ? T(1) : T(2);
+                    const T a = wgt * br[m], b = wgt * bim[m];
+                    const T* cr = Ct + m * HPM;
+                    const T* sr = St + m * HPM;
+#pragma unroll
+                    for (int k = 0; k < HPM; ++k) {
+                        X1[k] = fma(a, cr[k], X1[k]);
+                        X2[k] = fma(b, sr[k], X2[k]);
+                    }
+                    X1[HPM] += a;
+                }
+                T* uc = u + (size_t)c * p;
+#pragma unroll
+                for (int k = 0; k < HPM; ++k) {
+                    if (k < hp) {
+                        uc[k] += X1[k] - X2[k];
+                        uc[p - 1 - k] += X1[k] + X2[k];
+                    }
+                }
+                if (odd) uc[hp] += X1[HPM];
+            }
+        }
+    }
+}
+
+template <class T>
+inline size_t pwin4_smem(int p, int NF, int nfh, int MH) {
+    const int pm3 = nfh | 1;
+    return ((size_t)2 * MH * (kMaxPFast / 2) + (size_t)2 * p * NF * nfh + (size_t)2 * p * p * pm3) * sizeof(T);
+}
+
 }  // namespace dmk
 
 namespace dmk {
@@ -751,21 +1120,25 @@ __device__ __forceinline__ void cheb_eval(const T* cs, int p, int ng, const T (&
 // Leaf stage for p <= kMaxPFast in two launches.
 //
 // k_pair: the residual sums (Sec. 2.4 and the direct interactions of Sec. 3.1.5) as
-// independent warp tasks.  A task is a tile of m consecutive targets of one leaf: m = 32 for
-// the full tiles and, for the nt mod 32 remaining targets, one tile per set bit of that
-// remainder (m = 16, 8, 4, 2, 1), so that every lane of every task has a target.  In a tile of
-// m < 32 targets lane = s m + i holds target i and takes every S-th source pair (S = 32/m,
-// split s) of each chunk; the S partial sums are combined by a fixed xor-shuffle tree.  Warps
-// take tasks from a device counter and stage their own chunks of C sources, so no
-// barrier couples the warps of a block.  A chunk holds (x, y, z, nu^2) and (x_lo, y_lo, z_lo,
-// 1/nu) per source (source offsets from the target leaf's centre, FP32 leading and trailing
-// parts in the FP32 path).  Per chunk: support test |x_t sigma - x_s/nu| < 1 (half precision on
-// source pairs with a margin for its rounding in the FP32 path, FP64 r^2 < nu^2 in the FP64
-// path) into bit masks, in-support
-// sources appended to a per-lane byte queue, queued pairs evaluated with two-float differences
-// and the cubic residual tables (r > 0 excludes the target itself), FP32 sums folded into FP64
-// per chunk.  The result K * sum is written to the output in input order.  The kernel needs
-// only the tree, so it may run beside the far field on another stream.
+// independent warp tasks.  A task is a tile of m consecutive targets of one leaf (m = kPairTile
+// for the full tiles, and for the remainder one tile per set bit, so that every lane has a
+// target); lane = s m + i holds target i and takes every S-th source (S = 32/m, split s); the S
+// partial sums are combined by a fixed xor-shuffle tree.  Warps take tasks from a device
+// counter, so no barrier couples the warps of a block.
+//   Sources stream through the direct-list entries in order, 32 at a time (one per lane).  A
+// lane forms its source's offset from the target leaf's centre (FP32 leading and trailing
+// parts in the FP32 path) and tests it against the tile's bounding box expanded by the entry's
+// nu: only a source within nu of the box can be within nu of a target of the tile.  The
+// survivors (about 40% of the sources of a 16-target tile, against 15% inside the support of
+// one target for uniform points) are appended in order to the warp's ring of kPairList records
+// ((x, y, z, nu^2), (x_lo, y_lo, z_lo, 1/nu), strengths); each full block of 32 survivors is
+// then evaluated by every lane for its own target -- broadcast shared-memory reads, no per-lane
+// queue -- with two-float differences, the exact test 0 < r^2 < nu^2 (r = 0 is the target
+// itself, Eq. periodic_sum drops it; the target's own periodic images lie at |p| >= nu_0 and
+// are dropped by index) and the cubic residual tables.  FP32 partial sums are
+// folded into a two-float accumulator per block (FP64 in the FP64 path); the order of every
+// sum is fixed, so results are reproducible.  The result K * sum is written in input order.
+// The kernel needs only the tree, so it may run beside the far field on another stream.
 //
 // k_leafexp: thread per target.  The leaf's Chebyshev coefficients c[n1][n2][n3] (x, y, z) are
 // staged in shared memory with the n3 rows padded to a multiple of four; each thread keeps
@@ -773,23 +1146,28 @@ __device__ __forceinline__ void cheb_eval(const T* cs, int p, int ng, const T (&
 // rows as broadcast vectors (Sec. 3.1.5).  The expansion is added to the residual sums written
 // by k_pair, the self term (Sec. 2.4) subtracted, and the result written in FP64.
 constexpr int kPairWarps = 4;
+constexpr int kPairList = 64;      // survivor ring per warp (two blocks of 32)
 
-// byte offsets within one warp's shared-memory region of k_pair for chunks of C sources
-// (C <= 256: the queue holds byte indices)
-template <class T, int DR, int C>
+// byte offsets within one warp's shared-memory region of k_pair
+template <class T, int DR>
 struct PairSmem {
-    static_assert(C <= 256 && C % 32 == 0, "chunk of at most 256 sources");
-    static constexpr bool kTwo = sizeof(T) == 4;
-    static constexpr size_t a = 0;                                                    // Quad<T> [C]
-    static constexpr size_t b = a + C * sizeof(Quad<T>);                              // Quad<T> [C]
-    static constexpr size_t t = b + C * sizeof(Quad<T>);                              // Quad<half2> [C/2]
-    static constexpr size_t r = t + (kTwo ? C / 2 * sizeof(Quad<__half2>) : 0);      // T [C][DR]
-    static constexpr size_t q = (r + C * DR * sizeof(T) + 15) & ~(size_t)15;          // u8 [C][32]
-    static constexpr size_t bytes = q + C * 32;
+    static constexpr size_t a = 0;                                                    // Quad<T> [kPairList]
+    static constexpr size_t b = a + kPairList * sizeof(Quad<T>);                      // Quad<T> [kPairList]
+    static constexpr size_t r = b + kPairList * sizeof(Quad<T>);                      // T [kPairList][DR]
+    static constexpr size_t i = r + kPairList * DR * sizeof(T);                       // int [kPairList]
+    static constexpr size_t bytes = (i + kPairList * sizeof(int) + 15) & ~(size_t)15;
 };
 
-template <class T, int K, bool GRAD, int C>
-__global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? 4 : 2) k_pair(const int* __restrict__ leaves, BoxArrays B, Tab<T> tab,
+// hi + lo += v (Knuth's TwoSum on the leading part)
+__device__ __forceinline__ void two_float_acc(float& hi, float& lo, float v) {
+    const float s = hi + v;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (v - bb);
+    hi = s;
+}
+
+template <class T, int K, bool GRAD>
+__global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? (K == DMK_LAPLACE ? 6 : 4) : 2) k_pair(const int* __restrict__ leaves, BoxArrays B, Tab<T> tab,
                                                             Geo g, const double* __restrict__ xs, int64_t N,
                                                             const int* __restrict__ doffs,
                                                             const int* __restrict__ toffs, int tcap,
@@ -797,22 +1175,21 @@ __global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? 4 : 2) k_pai
                                                             const DirectEntry* __restrict__ dl, LeafOut out) {
     using Pr = Pair<T, K, GRAD>;
     using Q4 = Quad<T>;
-    constexpr int DR = Pr::DR, DU = Pr::DU;
+    constexpr int DR = Pr::DR, DU = Pr::DU, NA = DU + (GRAD ? 3 * DU : 0);
     constexpr bool kTwo = sizeof(T) == 4;
     constexpr int RQ = point_record_floats(DR) / 4;     // float4s per point record
-    using WS = PairSmem<T, DR, C>;
+    using WS = PairSmem<T, DR>;
     constexpr int NSER = (K == DMK_STRESSLET) ? (GRAD ? 6 : 3) : ((GRAD && K != DMK_LAPLACE) ? 5 : 2);
     __shared__ Quad<float> herm[kTwo ? NSER * kHermNT : 1];
     __shared__ T fits[kTwo ? 1 : 256];
     extern __shared__ __align__(16) unsigned char dsmp[];
     const int lane = threadIdx.x & 31;
-    const unsigned full = 0xffffffffu;
+    const unsigned full = 0xffffffffu, below = (1u << lane) - 1u;
     unsigned char* wsm = dsmp + (threadIdx.x >> 5) * WS::bytes;
     Q4* sA = reinterpret_cast<Q4*>(wsm + WS::a);
     Q4* sB = reinterpret_cast<Q4*>(wsm + WS::b);
-    Quad<__half2>* sT = reinterpret_cast<Quad<__half2>*>(wsm + WS::t);
     T (*sr)[DR] = reinterpret_cast<T (*)[DR]>(wsm + WS::r);
-    unsigned char (*q)[32] = reinterpret_cast<unsigned char (*)[32]>(wsm + WS::q);
+    int* sI = reinterpret_cast<int*>(wsm + WS::i);
     if constexpr (kTwo) {
         const Quad<float>* hsrc = reinterpret_cast<const Quad<float>*>(tab.herm);
         for (int e = threadIdx.x; e < NSER * kHermNT; e += blockDim.x) herm[e] = hsrc[e];
@@ -825,6 +1202,9 @@ __global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? 4 : 2) k_pai
     const int ntask = toffs[tcap] - toffs[0];
     const double inv_s = 1.0 / g.s, s2 = g.s * g.s;
     const float inv_s_f = (float)inv_s, s2_f = (float)s2;
+    // the box test passes every source within nu of the tile's box: its FP32 rounding (relative
+    // 1e-6 at most for offsets below 3 nu) is covered by the factor on nu^2
+    const T box_margin = kTwo ? T(1.0001) : T(1.0 + 1e-12);
     float Lh[3], Ll[3];
     for (int a = 0; a < 3; ++a) split_double(g.L[a], Lh[a], Ll[a]);
     while (true) {
@@ -852,150 +1232,30 @@ __global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? 4 : 2) k_pai
         } else {
             for (int a = 0; a < 3; ++a) xt[a] = (T)(xs[a * N + tg] - c[a]);
         }
-        const float inv_rT = ldexpf(inv_s_f, l);
-        __half2 xu2[3];
-        for (int a = 0; a < 3; ++a) xu2[a] = __float2half2_rn((float)(xt[a] + xtl[a]) * inv_rT);
-        double accd[DU], gaccd[3 * DU];
+        // the tile's bounding box (lanes of one split hold the m targets)
+        T blo[3], bhi[3];
+        for (int a = 0; a < 3; ++a) blo[a] = bhi[a] = xt[a] + xtl[a];
+        for (int o = 1; o < m; o <<= 1)
+            for (int a = 0; a < 3; ++a) {
+                blo[a] = min(blo[a], __shfl_xor_sync(full, blo[a], o));
+                bhi[a] = max(bhi[a], __shfl_xor_sync(full, bhi[a], o));
+            }
+        // two-float (FP32 path) or FP64 accumulators, FP32 partial sums per block of survivors
+        T acc_hi[NA], acc_lo[NA];
 #pragma unroll
-        for (int j = 0; j < DU; ++j) accd[j] = 0;
-#pragma unroll
-        for (int j = 0; j < 3 * DU; ++j) gaccd[j] = 0;
-
-        // the per-entry constants: 1/nu and nu^2 of the entry's level, the image shift minus
-        // the target leaf's centre (FP32 parts in the FP32 path), the level ratio for the
-        // half-precision test
-        struct EntryC { T nu2, tinv; float Eh[3], El[3], hs; double E[3]; };
-        auto entry_consts = [&](const DirectEntry& de, EntryC& ec) {
-            const int lev = de.code >> 6;
-            const int sb[3] = {((de.code) & 3) - 1, ((de.code >> 2) & 3) - 1, ((de.code >> 4) & 3) - 1};
-            if constexpr (kTwo) {
-                ec.tinv = ldexpf(inv_s_f, lev);
-                ec.nu2 = ldexpf(s2_f, -2 * lev);
-                for (int a = 0; a < 3; ++a)
-                    two_float_add((float)sb[a] * Lh[a], (float)sb[a] * Ll[a], ch[a], cl[a], ec.Eh[a], ec.El[a]);
-            } else {
-                ec.tinv = (T)ldexp(inv_s, lev);
-                ec.nu2 = (T)ldexp(s2, -2 * lev);
-                for (int a = 0; a < 3; ++a) ec.E[a] = (double)sb[a] * g.L[a] - c[a];
-            }
-            ec.hs = ldexpf(1.0f, lev - l);
-        };
-        // one source (sorted index si) into chunk slot `slot`
-        auto stage = [&](int64_t si, int slot, const EntryC& ec) {
-            Q4 a, b;
-            if constexpr (kTwo) {
-                const float4* rp = out.pk + si * RQ;
-                const float4 p0 = rp[0], p1 = rp[1];
-                two_float_add(p0.x, p1.x, ec.Eh[0], ec.El[0], a.x, b.x);
-                two_float_add(p0.y, p1.y, ec.Eh[1], ec.El[1], a.y, b.y);
-                two_float_add(p0.z, p1.z, ec.Eh[2], ec.El[2], a.z, b.z);
-                sr[slot][0] = p0.w;
-                if constexpr (DR > 1) {
-                    sr[slot][1] = p1.w;
-                    const float* rf = reinterpret_cast<const float*>(rp);
-                    for (int a2 = 2; a2 < DR; ++a2) sr[slot][a2] = rf[point_record_rho(a2)];
-                }
-            } else {
-                a.x = (T)(xs[si] + ec.E[0]);
-                a.y = (T)(xs[N + si] + ec.E[1]);
-                a.z = (T)(xs[2 * N + si] + ec.E[2]);
-                b.x = b.y = b.z = T(0);
-                for (int a2 = 0; a2 < DR; ++a2) sr[slot][a2] = (T)out.rs[si * DR + a2];
-            }
-            a.w = ec.nu2;
-            b.w = ec.tinv;
-            sA[slot] = a;
-            sB[slot] = b;
-            if constexpr (kTwo) {
-                __half* hp = reinterpret_cast<__half*>(&sT[slot >> 1]);
-                const int hh = slot & 1;
-                hp[0 + hh] = __float2half_rn(-(a.x + b.x) * ec.tinv);
-                hp[2 + hh] = __float2half_rn(-(a.y + b.y) * ec.tinv);
-                hp[4 + hh] = __float2half_rn(-(a.z + b.z) * ec.tinv);
-                hp[6 + hh] = __float2half_rn(ec.hs);
-            }
-        };
-        // support tests, queue and pair evaluation of one staged chunk of `filled` sources
-        auto run_chunk = [&](int filled) {
-            if constexpr (kTwo) {
-                // an odd chunk: the unused half of the last pair fails every support test
-                if ((filled & 1) && lane == 0) {
-                    __half* hp = reinterpret_cast<__half*>(&sT[filled >> 1]);
-                    hp[1] = hp[3] = hp[5] = __float2half_rn(30000.0f);
-                    hp[7] = __float2half_rn(0.0f);
-                }
-            }
+        for (int j = 0; j < NA; ++j) { acc_hi[j] = 0; acc_lo[j] = 0; }
+        int head = 0, tail = 0;
+        // evaluates the survivors head .. head + cnt - 1 of the ring for this lane's target
+        auto run_block = [&](int cnt) {
             __syncwarp();
-            // support tests into bit masks, set bits appended to the queue (column swizzled
-            // by row so that lanes with different queue lengths write to different banks)
-            int cnt = 0;
-            if constexpr (kTwo) {
-                // the half-precision test passes every pair with r^2 / nu^2 < 1: its rounding
-                // error stays below 5e-3 for |dx / nu| < 1 (operands below 2 in magnitude), so
-                // the bound 1.02 keeps every in-support pair; the exact test r^2 < nu^2 is
-                // repeated in FP32 before a pair is evaluated
-                const __half2 one2 = __float2half2_rn(1.02f);
-                const int npair = (filled + 1) >> 1;
-                const int nu = (npair - s + S - 1) / S;     // this split's pair slots s + S u
-                for (int u0 = 0; u0 < nu; u0 += 16) {
-                    const int un = min(16, nu - u0);
-                    unsigned me = 0, mo = 0;
-#pragma unroll 8
-                    for (int mm = 0; mm < 16; ++mm) {
-                        if (mm < un) {
-                            const Quad<__half2> v = sT[s + S * (u0 + mm)];
-                            const __half2 dx = __hfma2(xu2[0], v.w, v.x);
-                            const __half2 dy = __hfma2(xu2[1], v.w, v.y);
-                            const __half2 dz = __hfma2(xu2[2], v.w, v.z);
-                            const __half2 r2 = __hfma2(dx, dx, __hfma2(dy, dy, __hmul2(dz, dz)));
-                            const unsigned mk = __hlt2_mask(r2, one2);
-                            me |= (mk & 1u) << mm;
-                            mo |= ((mk >> 16) & 1u) << mm;
-                        }
-                    }
-                    while (me) {
-                        const int mm = __ffs(me) - 1;
-                        me &= me - 1;
-                        q[cnt][lane ^ ((cnt & 7) << 2)] = (unsigned char)(2 * (s + S * (u0 + mm)));
-                        ++cnt;
-                    }
-                    while (mo) {
-                        const int mm = __ffs(mo) - 1;
-                        mo &= mo - 1;
-                        q[cnt][lane ^ ((cnt & 7) << 2)] = (unsigned char)(2 * (s + S * (u0 + mm)) + 1);
-                        ++cnt;
-                    }
-                }
-            } else {
-                const int nu = (filled - s + S - 1) / S;    // this split's sources s + S u
-                for (int u0 = 0; u0 < nu; u0 += 32) {
-                    const int un = min(32, nu - u0);
-                    unsigned mask = 0;
-#pragma unroll 8
-                    for (int kk = 0; kk < 32; ++kk) {
-                        if (kk < un) {
-                            const Q4 a = sA[s + S * (u0 + kk)];
-                            const T dx = xt[0] - a.x, dy = xt[1] - a.y, dz = xt[2] - a.z;
-                            const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                            mask |= (r2 < a.w ? 1u : 0u) << kk;
-                        }
-                    }
-                    while (mask) {
-                        const int kk = __ffs(mask) - 1;
-                        mask &= mask - 1;
-                        q[cnt][lane ^ ((cnt & 7) << 2)] = (unsigned char)(s + S * (u0 + kk));
-                        ++cnt;
-                    }
-                }
-            }
             T acc[DU], gacc[3 * DU];
 #pragma unroll
             for (int j = 0; j < DU; ++j) acc[j] = 0;
 #pragma unroll
             for (int j = 0; j < 3 * DU; ++j) gacc[j] = 0;
 #pragma unroll 2
-            for (int i = 0; i < cnt; ++i) {
-                const int k = q[i][lane ^ ((i & 7) << 2)];
+            for (int i = s; i < cnt; i += S) {
+                const int k = (head + i) & (kPairList - 1);
                 const Q4 a = sA[k], b = sB[k];
                 T dx = xt[0] - a.x, dy = xt[1] - a.y, dz = xt[2] - a.z;
                 if (kTwo) {
@@ -1004,76 +1264,104 @@ __global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? 4 : 2) k_pai
                     dz += xtl[2] - b.z;
                 }
                 const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                // r = 0: the target itself (Eq. periodic_sum drops it); r >= nu: outside the
-                // residual kernel's support (the queue of the FP32 path holds a few such pairs)
-                if (r2 > T(0) && r2 < a.w) {
+                // r = 0 (the target itself at p = 0, or a coincident point) and the target's
+                // own periodic images (|p| >= nu_0 >= nu: outside the support, however r^2
+                // rounds) are dropped
+                if (r2 > T(0) && r2 < a.w && sI[k] != tg) {
                     if constexpr (kTwo)
                         Pr::eval(HermSeries(herm, r2, b.w), dx, dy, dz, r2, b.w, sr[k], acc, gacc);
                     else
                         Pr::eval(ChebSeries<T>(tab, fits, r2, b.w), dx, dy, dz, r2, b.w, sr[k], acc, gacc);
                 }
             }
+            if constexpr (kTwo) {
 #pragma unroll
-            for (int j = 0; j < DU; ++j) accd[j] += (double)acc[j];
+                for (int j = 0; j < DU; ++j) two_float_acc(acc_hi[j], acc_lo[j], acc[j]);
 #pragma unroll
-            for (int j = 0; j < 3 * DU; ++j) gaccd[j] += (double)gacc[j];
+                for (int j = 0; j < 3 * DU; ++j) two_float_acc(acc_hi[DU + j], acc_lo[DU + j], gacc[j]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < DU; ++j) acc_hi[j] += acc[j];
+#pragma unroll
+                for (int j = 0; j < 3 * DU; ++j) acc_hi[DU + j] += gacc[j];
+            }
+            head += cnt;
+            __syncwarp();
         };
-
-        const int e0 = doffs[li], e1 = doffs[li + 1], ne = e1 - e0;
-        if (ne <= 32) {
-            // Interleaved chunks: lane j holds entry e0 + j; chunk k takes positions
-            // k, k + nchunk, k + 2 nchunk, ... of every entry, so that each chunk samples the
-            // whole neighbourhood and the in-support counts of a tile's targets stay close
-            // (the warp runs to the longest queue).  With nchunk >= Ns / (C - ne) a chunk
-            // holds at most Ns / nchunk + ne <= C sources.
-            DirectEntry de = {0, 0, 0, 0};
-            EntryC ec;
-            if (lane < ne) {
-                de = dl[e0 + lane];
-                entry_consts(de, ec);
+        const int e0 = doffs[li], e1 = doffs[li + 1];
+        for (int e = e0; e < e1; ++e) {
+            const DirectEntry de = dl[e];
+            const int lev = de.code >> 6;
+            const int sb[3] = {((de.code) & 3) - 1, ((de.code >> 2) & 3) - 1, ((de.code >> 4) & 3) - 1};
+            // per-entry constants: nu^2 and 1/nu of the entry's level, image shift minus the
+            // target leaf's centre
+            T nu2, tinv;
+            float Eh[3], El[3];
+            double E[3];
+            if constexpr (kTwo) {
+                tinv = ldexpf(inv_s_f, lev);
+                nu2 = ldexpf(s2_f, -2 * lev);
+                for (int a = 0; a < 3; ++a)
+                    two_float_add((float)sb[a] * Lh[a], (float)sb[a] * Ll[a], ch[a], cl[a], Eh[a], El[a]);
+            } else {
+                tinv = (T)ldexp(inv_s, lev);
+                nu2 = (T)ldexp(s2, -2 * lev);
+                for (int a = 0; a < 3; ++a) E[a] = (double)sb[a] * g.L[a] - c[a];
             }
-            const int len = de.end - de.start;
-            const int Ns = __reduce_add_sync(full, len);
-            const int nchunk = (Ns + (C - ne) - 1) / (C - ne);
-            for (int k = 0; k < nchunk; ++k) {
-                __syncwarp();
-                const int cnt = len > k ? (len - k + nchunk - 1) / nchunk : 0;
-                int incl = cnt;
+            const T lim = nu2 * box_margin;
+            for (int base = de.start; base < de.end; base += 32) {
+                const int si = base + lane;
+                bool keep = false;
+                Q4 a, b;
+                if (si < de.end) {
+                    if constexpr (kTwo) {
+                        const float4* rp = out.pk + (int64_t)si * RQ;
+                        const float4 p0 = rp[0], p1 = rp[1];
+                        two_float_add(p0.x, p1.x, Eh[0], El[0], a.x, b.x);
+                        two_float_add(p0.y, p1.y, Eh[1], El[1], a.y, b.y);
+                        two_float_add(p0.z, p1.z, Eh[2], El[2], a.z, b.z);
+                    } else {
+                        a.x = (T)(xs[si] + E[0]);
+                        a.y = (T)(xs[N + si] + E[1]);
+                        a.z = (T)(xs[2 * N + si] + E[2]);
+                        b.x = b.y = b.z = T(0);
+                    }
+                    const T px = a.x + b.x, py = a.y + b.y, pz = a.z + b.z;
+                    const T gx = max(T(0), max(blo[0] - px, px - bhi[0]));
+                    const T gy = max(T(0), max(blo[1] - py, py - bhi[1]));
+                    const T gz = max(T(0), max(blo[2] - pz, pz - bhi[2]));
+                    keep = fma(gx, gx, fma(gy, gy, gz * gz)) < lim;
+                }
+                const unsigned bal = __ballot_sync(full, keep);
+                if (keep) {
+                    const int slot = (tail + __popc(bal & below)) & (kPairList - 1);
+                    a.w = nu2;
+                    b.w = tinv;
+                    sA[slot] = a;
+                    sB[slot] = b;
+                    sI[slot] = si;
+                    if constexpr (kTwo) {
+                        const float4* rp = out.pk + (int64_t)si * RQ;
+                        const float* rf = reinterpret_cast<const float*>(rp);
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int v = __shfl_up_sync(full, incl, o);
-                    if (lane >= o) incl += v;
+                        for (int a2 = 0; a2 < DR; ++a2) sr[slot][a2] = rf[point_record_rho(a2)];
+                    } else {
+#pragma unroll
+                        for (int a2 = 0; a2 < DR; ++a2) sr[slot][a2] = (T)out.rs[(int64_t)si * DR + a2];
+                    }
                 }
-                const int filled = __shfl_sync(full, incl, 31);
-                const int off = incl - cnt;
-                for (int i = 0; i < cnt; ++i) stage((int64_t)de.start + k + (int64_t)nchunk * i, off + i, ec);
-                run_chunk(filled);
-            }
-        } else {
-            // contiguous chunks over the entries in order
-            int e = e0, eo = 0;
-            while (e < e1) {
-                __syncwarp();
-                int filled = 0;
-                while (filled < C && e < e1) {
-                    const DirectEntry de = dl[e];
-                    const int take = min(de.end - de.start - eo, C - filled);
-                    EntryC ec;
-                    entry_consts(de, ec);
-                    for (int k = lane; k < take; k += 32) stage((int64_t)de.start + eo + k, filled + k, ec);
-                    filled += take;
-                    eo += take;
-                    if (eo == de.end - de.start) { ++e; eo = 0; }
-                }
-                run_chunk(filled);
+                tail += __popc(bal);
+                if (tail - head >= 32) run_block(32);
             }
         }
+        if (tail > head) run_block(tail - head);
         // the S splits of a target, combined in a fixed order (every lane gets the same sum)
+        double accd[NA];
+#pragma unroll
+        for (int j = 0; j < NA; ++j) accd[j] = (double)acc_hi[j] + (double)acc_lo[j];
         for (int o = m; o < 32; o <<= 1) {
 #pragma unroll
-            for (int j = 0; j < DU; ++j) accd[j] += __shfl_xor_sync(full, accd[j], o);
-#pragma unroll
-            for (int j = 0; j < 3 * DU; ++j) gaccd[j] += __shfl_xor_sync(full, gaccd[j], o);
+            for (int j = 0; j < NA; ++j) accd[j] += __shfl_xor_sync(full, accd[j], o);
         }
         if (s == 0) {
             const int oi = out.perm[tg];
@@ -1084,15 +1372,15 @@ __global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? 4 : 2) k_pai
 #pragma unroll
                 for (int i = 0; i < 3; ++i)
 #pragma unroll
-                    for (int j = 0; j < DU; ++j) out.grad[((int64_t)oi * 3 + i) * DU + j] = ks * gaccd[i * DU + j];
+                    for (int j = 0; j < DU; ++j) out.grad[((int64_t)oi * 3 + i) * DU + j] = ks * accd[DU + i * DU + j];
             }
         }
     }
 }
 
-template <class T, int DR, int C>
+template <class T, int DR>
 inline size_t pair_smem() {
-    return (size_t)kPairWarps * PairSmem<T, DR, C>::bytes;
+    return (size_t)kPairWarps * PairSmem<T, DR>::bytes;
 }
 
 constexpr int kLeafExpThreads = 128;

@@ -202,6 +202,125 @@ __global__ void __launch_bounds__((MAXP / 2 * MAXP + 31) / 32 * 32, sizeof(T) ==
     }
 }
 
+// Leaf anterpolation as a register-tiled product (FP32 path):
+//   proxy[(a, j1)][(j2, j3)] = sum_s X[s][(a, j1)] l_j2(eta_s) l_j3(zeta_s),
+//   X[s][(a, j1)] = rho_{s,a} l_j1(xi_s),
+// with M = d_rho p rows (a, j1) and p^2 columns (j2, j3).  The Lagrange rows of all sources of
+// the leaf are computed once (barycentric form) and kept in shared memory, for every strength
+// component; each thread owns a tile of 4 rows x TN consecutive j3 at one j2 (TN = p / 2 rounded
+// up to the vector width), reads per source the 4 X values, one eta value and TN zeta values,
+// and does 4 + 4 TN multiply-adds.  Tiles beyond the block's threads are taken in passes; X is
+// formed per chunk of kAntChunk sources.  Sources in super-chunks of kAntRows.
+constexpr int kAntRows = 256;      // sources whose Lagrange rows are held at once
+constexpr int kAntChunk = 32;      // sources per X chunk
+constexpr int kAntThreads = 256;
+
+template <int MAXP, int TN>
+struct AntSmem {
+    static constexpr size_t lx = 0;                                         // float [kAntRows][MAXP]
+    static constexpr size_t ly = lx + (size_t)kAntRows * MAXP * 4;
+    static constexpr size_t lz = ly + (size_t)kAntRows * MAXP * 4;
+    static constexpr size_t rho = lz + (size_t)kAntRows * MAXP * 4;       // float [kAntRows][9]
+    static constexpr size_t X = rho + (size_t)kAntRows * 9 * 4;            // float [kAntChunk][XM]
+};
+
+template <int MAXP, int TN>
+__global__ void __launch_bounds__(kAntThreads, 2)
+    k_anterp3(const int* __restrict__ nleaf_dev, const int* __restrict__ leaves, BoxArrays B,
+              const double* __restrict__ xs, int64_t N, const double* __restrict__ rs, Tab<float> tab, double s,
+              float* __restrict__ proxy, int XM) {
+    static_assert(MAXP % 4 == 0 && TN % 2 == 0, "vector reads");
+    using S = AntSmem<MAXP, TN>;
+    const int p = tab.p, p2 = p * p, p3 = p2 * p, drho = tab.d_rho;
+    const int M = drho * p, Mt = (M + 3) / 4, ng = (p + TN - 1) / TN, ntile = Mt * p * ng;
+    float* lx = reinterpret_cast<float*>(dsmem + S::lx);
+    float* ly = reinterpret_cast<float*>(dsmem + S::ly);
+    float* lz = reinterpret_cast<float*>(dsmem + S::lz);
+    float* rh = reinterpret_cast<float*>(dsmem + S::rho);
+    float* X = reinterpret_cast<float*>(dsmem + S::X);                       // [kAntChunk][XM], XM >= 4 Mt
+    const int nleaf = *nleaf_dev;
+    for (int li = blockIdx.x; li < nleaf; li += gridDim.x) {
+        const int box = leaves[li];
+        const int l = B.level[box];
+        const double r = s / (double)(1 << l), half = 0.5 * r;
+        const double c[3] = {(B.ix[3 * box] + 0.5) * r, (B.ix[3 * box + 1] + 0.5) * r, (B.ix[3 * box + 2] + 0.5) * r};
+        const int st = B.start[box], en = B.end[box];
+        float* outb = proxy + (size_t)box * drho * p3;
+        for (int s0 = st; s0 < en; s0 += kAntRows) {
+            const int ns = min(kAntRows, en - s0);
+            const bool first = s0 == st;
+            __syncthreads();
+            for (int u = threadIdx.x; u < 3 * ns; u += blockDim.x) {
+                const int ax = u / ns, pt = u - ax * ns;
+                const double xi = (xs[ax * N + s0 + pt] - c[ax]) / half;
+                float* row = (ax == 0 ? lx : (ax == 1 ? ly : lz)) + pt * MAXP;
+                lagrange_row_padded<float>((float)xi, tab.nodes, tab.bary, p, MAXP, 1.0f, row);
+            }
+            for (int u = threadIdx.x; u < ns * drho; u += blockDim.x) rh[u] = (float)rs[(int64_t)s0 * drho + u];
+            for (int pass = 0; pass * kAntThreads < ntile; ++pass) {
+                const int tile = pass * kAntThreads + threadIdx.x;
+                const bool act = tile < ntile;
+                // tile -> (row block mt, j2, column group g)
+                const int mt = act ? tile / (p * ng) : 0, rem = act ? tile % (p * ng) : 0;
+                const int j2 = rem / ng, j30 = (rem % ng) * TN;
+                float acc[4][TN];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int q = 0; q < TN; ++q) acc[i][q] = 0.f;
+                for (int k0 = 0; k0 < ns; k0 += kAntChunk) {
+                    const int nk = min(kAntChunk, ns - k0);
+                    __syncthreads();
+                    for (int u = threadIdx.x; u < nk * XM; u += blockDim.x) {
+                        const int k = u / XM, m = u - k * XM;
+                        float v = 0.f;
+                        if (m < M) {
+                            const int a = m / p, j1 = m - a * p;
+                            v = rh[(k0 + k) * drho + a] * lx[(k0 + k) * MAXP + j1];
+                        }
+                        X[u] = v;
+                    }
+                    __syncthreads();
+                    if (act) {
+                        for (int k = 0; k < nk; ++k) {
+                            const float4 xv = *reinterpret_cast<const float4*>(X + k * XM + 4 * mt);
+                            const float yv = ly[(k0 + k) * MAXP + j2];
+                            const float w[4] = {xv.x * yv, xv.y * yv, xv.z * yv, xv.w * yv};
+                            const float2* zr = reinterpret_cast<const float2*>(lz + (k0 + k) * MAXP + j30);
+#pragma unroll
+                            for (int q = 0; q < TN / 2; ++q) {
+                                const float2 zv = zr[q];
+#pragma unroll
+                                for (int i = 0; i < 4; ++i) {
+                                    acc[i][2 * q] = fmaf(w[i], zv.x, acc[i][2 * q]);
+                                    acc[i][2 * q + 1] = fmaf(w[i], zv.y, acc[i][2 * q + 1]);
+                                }
+                            }
+                        }
+                    }
+                }
+                if (act) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int m = 4 * mt + i;
+                        if (m < M) {
+                            float* o = outb + (size_t)m * p2 + j2 * p + j30;
+#pragma unroll
+                            for (int q = 0; q < TN; ++q)
+                                if (j30 + q < p) o[q] = first ? acc[i][q] : o[q] + acc[i][q];
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int MAXP, int TN>
+inline size_t anterp3_smem(int XM) {
+    return AntSmem<MAXP, TN>::X + (size_t)kAntChunk * XM * 4;
+}
+
 // ------------------------------------------------------------------------------------------
 // Upward pass child -> parent (Sec. 3.1.2): parent += sum_children (I^T x I^T x I^T) child,
 // I[o][j_child][a_parent] = l_a(child node j in parent coordinates).

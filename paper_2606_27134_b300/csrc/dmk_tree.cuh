@@ -516,14 +516,18 @@ __global__ void k_colleagues(int nb, const int* __restrict__ level, const int* _
 // Entry = {start, end, packed shifts and level, unused}.
 struct DirectEntry { int start, end, code, pad; };
 
-// Residual-sum tasks of the leaf stage: a tile of m consecutive targets of one leaf, m = 32
-// for the full tiles and one tile per set bit of nt mod 32 for the rest; as (leaf index, first
-// target offset within the leaf, m, 0).
+// Residual-sum tasks of the leaf stage: a tile of m consecutive targets of one leaf, m =
+// kPairTile for the full tiles and one tile per set bit of nt mod kPairTile for the rest; as
+// (leaf index, first target offset within the leaf, m, 0).  Consecutive targets are close in
+// key order, so a tile is spatially compact.
+constexpr int kPairTileLog = 4;
+constexpr int kPairTile = 1 << kPairTileLog;
+
 // task k of a leaf with nt targets: full tiles first, then the remainder's set bits high to low
 __device__ __forceinline__ int4 pair_task(int li, int nt, int k) {
-    const int a = nt >> 5;
-    if (k < a) return make_int4(li, 32 * k, 32, 0);
-    int rem = nt & 31, t0 = 32 * a, j = k - a;
+    const int a = nt >> kPairTileLog;
+    if (k < a) return make_int4(li, kPairTile * k, kPairTile, 0);
+    int rem = nt & (kPairTile - 1), t0 = kPairTile * a, j = k - a;
     while (true) {
         const int bit = 31 - __clz(rem);
         if (j == 0) return make_int4(li, t0, 1 << bit, 0);
@@ -534,7 +538,7 @@ __device__ __forceinline__ int4 pair_task(int li, int nt, int k) {
 }
 
 // number of such tasks
-__device__ __forceinline__ int pair_task_count(int nt) { return (nt >> 5) + __popc(nt & 31); }
+__device__ __forceinline__ int pair_task_count(int nt) { return (nt >> kPairTileLog) + __popc(nt & (kPairTile - 1)); }
 
 
 __device__ __forceinline__ int pack_code(const int sh[3], int level) {

@@ -1,4 +1,4 @@
-"""Algorithmic work per launch and the FP32 ALU peak used for the leaf-kernel roofline.
+"""Algorithmic work per launch, for the roofline of the leaf kernels.
 
 Per-unit figures (method arithmetic, not the instructions a kernel happens to issue):
   residual pair (Laplace, potential and gradient): 22 + d_q operations, where d_q is the
@@ -6,15 +6,16 @@ Per-unit figures (method arithmetic, not the instructions a kernel happens to is
       r^2, the reciprocal square root, the polynomial, the potential and force updates);
   Chebyshev evaluation of the leaf expansion with its gradient: 2 p^3 FMA = 4 p^3 FLOP
       per target (sum-factorised contraction of the p^3 coefficients).
-One launch of the residual kernel (k_pair) processes every visited pair once; one launch of
-the expansion kernel (k_leafexp) every target once.
+One launch of the residual kernel (k_pair) processes every visited pair once -- every
+(target, source) pair of the direct lists -- and one launch of the expansion kernel
+(k_leafexp) every target once.  The denominators are the pipe throughputs measured on the GPU
+(paper_2606_27134_b300.peaks); the derived FP32 figure below is for comparison.
 """
 
 # DRAM bytes (read + write) of one k_pair<float, Laplace, grad> launch at the benchmark
-# workload, from one ncu capture of the kernel as it stands
-# (profiles/k_pair_laplace_2P_N1e5_mixed.md); None whenever the kernel has changed since the
-# capture.
-PAIR_TRAFFIC_BYTES = 4.128e6 + 0.0
+# workload from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel as
+# it stands; None while the kernel has changed since its last capture.
+PAIR_TRAFFIC_BYTES = None
 
 SMS = 148
 FP32_LANES_PER_SM = 128
@@ -22,7 +23,7 @@ MAX_SM_GHZ = 2.032
 
 
 def fp32_peak_tflops():
-    """FP32 FMA pipe: SMs x lanes x 2 FLOP x maximum SM clock."""
+    """FP32 FMA pipe from unit counts: SMs x lanes x 2 FLOP x maximum SM clock."""
     return SMS * FP32_LANES_PER_SM * 2 * MAX_SM_GHZ / 1e3
 
 
