@@ -17,7 +17,7 @@ import numpy as np
 from .params import c_and_p, n_f, Geometry, root_modes
 from .pswf import PSWFWindow
 from .kernels import Kernel
-from .tree import Forest, wrap_and_quantize
+from .tree import Forest, wrap, replicate, quantize
 from . import symbols as sym
 
 _CSTEP = 1e-30
@@ -188,7 +188,12 @@ def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_p
     rho = np.asarray(strengths, dtype=np.float64).reshape(N, kern.d_rho)
     if kernel == "laplace" and D in (1, 2) and abs(rho.sum()) > 1e-12 * max(np.abs(rho).sum(), 1e-300):
         raise ValueError("Laplace with D=1,2 requires zero net charge (Sec. 5.2)")
-    w, G = wrap_and_quantize(x, geom)
+    # wrapped points, then (non-exact tilings, Sec. 4.1.2) the periodic images that fall in
+    # Omega_ext as extra sources: points N.. of w, with src mapping every point to its original
+    w, src = replicate(wrap(x, geom), geom)
+    rho_t = rho                      # the targets' strengths
+    rho = rho[src]                   # every source's strength, images included
+    G = quantize(w, geom)
     forest = Forest(geom, G, n_s)
     boxes = forest.by_id
     nb = len(boxes)
@@ -197,7 +202,7 @@ def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_p
 
     def center(b):
         r = s / 2 ** b.level
-        return np.array([(b.ix[i] + 0.5) * r for i in range(3)])
+        return np.array([geom.origin[i] + (b.ix[i] + 0.5) * r for i in range(3)])
 
     # ---- step 2: upward pass (Sec. 3.1.2, 4.2) -----------------------------------
     proxy = [None] * nb
@@ -229,12 +234,41 @@ def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_p
     Sc = [np.exp(-1j * np.outer(ax, y)) for ax in axes]            # conj(S(j, k)) [k, j]
     shp = keep.shape
     chi = np.zeros(shp + (kern.d_rho,), dtype=complex)
+
+    def chi_proxy(b):
+        """The root proxy charges entering the structure factor: only sources inside Omega count
+        (Sec. 4.3, non-exact tilings).  A cube inside Omega gives its proxy; a padding cube
+        outside Omega gives nothing; a cut cube gives its original sources (not their images),
+        anterpolated directly onto its root grid (the paper sums the proxies of its uncut
+        descendants plus the sources of its cut leaves; the grid of the cube itself represents
+        the same band-limited modes)."""
+        inside, outside = True, False
+        for i in range(3):
+            if geom.padded[i]:
+                lo = geom.origin[i] + b.ix[i] * s
+                if lo >= geom.L[i] or lo + s <= 0.0:
+                    outside = True
+                if lo < 0.0 or lo + s > geom.L[i]:
+                    inside = False
+        if outside:
+            return None
+        if inside:
+            return proxy[b.id]
+        orig = b.pts[b.pts < N]
+        if not len(orig):
+            return None
+        xi = (w[orig] - center(b)) / (s / 2)
+        Lx, Ly, Lz = (lagrange(xi[:, i], nodes) for i in range(3))
+        return np.einsum("sa,sb,sc,sd->abcd", Lx, Ly, Lz, rho[orig], optimize=True)
+
     for b in roots:
+        pr = chi_proxy(b)
+        if pr is None:
+            continue
         cb = center(b)
         ph = np.exp(-1j * (axes[0][:, None, None] * cb[0] + axes[1][None, :, None] * cb[1]
                            + axes[2][None, None, :] * cb[2]))
-        chi += ph[..., None] * np.einsum("ai,bj,ck,ijkd->abcd", Sc[0], Sc[1], Sc[2], proxy[b.id],
-                                         optimize=True)
+        chi += ph[..., None] * np.einsum("ai,bj,ck,ijkd->abcd", Sc[0], Sc[1], Sc[2], pr, optimize=True)
     uhat = np.einsum("abcud,abcd->abcu", Wk, chi)
     for b in roots:
         cb = center(b)
@@ -245,7 +279,7 @@ def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_p
     kk_count = int(keep.sum())
     if kernel == "stokeslet" and D == 0:
         # constant removed by the C^1 gauge of the truncated biharmonic kernel (symbols.B3_trunc)
-        cst = sym.stokeslet_free_space_constant(R) * rho.sum(axis=0)
+        cst = sym.stokeslet_free_space_constant(R) * rho_t.sum(axis=0)
         for b in roots:
             local[b.id] = local[b.id] + cst
 
@@ -299,7 +333,9 @@ def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_p
                 per_leaf.setdefault(T.id, []).append((S, sh, l))
     Lvec = np.array(geom.L)
     for T in forest.leaves():
-        t = T.pts if want is None else T.pts[want[T.pts]]
+        t = T.pts[T.pts < N]                       # original points only are targets
+        if want is not None:
+            t = t[want[t]]
         if not len(t):
             continue
         cT = center(T)
@@ -323,7 +359,7 @@ def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_p
                 # excluded: r = 0 (p = 0 with x_t = x_s, Eq. periodic_sum) and the target's own
                 # periodic images, which lie at |p| >= min periodic L_i = nu_0 >= nu, outside the
                 # support of K_R whatever the rounding of r^2 (Remark comp_supp)
-                ok = (r2 < nul * nul) & (r2 > 0) & (srcs[None, :] != t[:, None])
+                ok = (r2 < nul * nul) & (r2 > 0) & (src[srcs][None, :] != t[:, None])
                 ti, si = np.nonzero(ok)
                 if len(ti) == 0:
                     continue
@@ -337,20 +373,20 @@ def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_p
 
         ut = total(w[t]).real
         selfm = kern.self_matrix(s / 2 ** T.level, win)
-        u[t] = ut - rho[t] @ selfm.T
+        u[t] = ut - rho_t[t] @ selfm.T
         if grad:
             for i in range(3):
                 xc = w[t].astype(complex)
                 xc[:, i] += 1j * _CSTEP
                 gu[t, i, :] = total(xc).imag / _CSTEP
-            gu[t] -= np.einsum("ija,ta->tij", kern.self_grad(s / 2 ** T.level, win), rho[t])
+            gu[t] -= np.einsum("ija,ta->tij", kern.self_grad(s / 2 ** T.level, win), rho_t[t])
 
     # 1P Stokeslet constant (Remark stokeslet_const_corr)
     if kernel == "stokeslet" and D == 1:
         Rr = R
         corr = -np.diag([(1 + math.log(Rr)) / (2 * np.pi), (math.log(Rr) + 0.5) / (4 * np.pi),
                          (math.log(Rr) + 0.5) / (4 * np.pi)]) / geom.L[0]
-        u += (corr @ rho.sum(axis=0))[None, :]      # NaN rows (targets not evaluated) stay NaN
+        u += (corr @ rho_t.sum(axis=0))[None, :]    # NaN rows (targets not evaluated) stay NaN
     res = Result()
     res.u = u
     res.grad = gu

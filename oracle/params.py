@@ -66,7 +66,20 @@ def n_f(c):
 
 
 class Geometry:
-    """Cube tiling of the primary cell (Sec. 4.1.1, Sec. 5; exact tilings only)."""
+    """Cube tiling of the primary cell (Sec. 4.1.1-4.1.3, Sec. 5).
+
+    Cubes of side s = the shortest periodic length (the largest length for D = 0).  A periodic
+    direction whose length is an integer multiple of s is tiled exactly and stays periodic in
+    the forest.  Any other periodic direction i (Sec. 4.1.1, non-exact tiling) is covered by
+    ceil(L_i/s) cubes, the last of them cut, plus one padding cube on each side:
+    Omega_ext spans [-s, s (ceil(L_i/s) + 1)) along i, the forest is non-periodic along i, and
+    the periodic images of the sources that fall in Omega_ext are added as extra sources
+    (Sec. 4.1.2).  Free directions: lengths rounded up to multiples of s (Sec. 5).
+
+    Attributes: L (true lengths), s, M (cubes per axis, padding included), origin (lower
+    corner of Omega_ext), Lext (extent of the cube tiling per axis), periodic (the sum is
+    periodic along the axis), fperiodic (the forest wraps along the axis), padded.
+    """
 
     def __init__(self, D, L):
         L = [float(v) for v in L]
@@ -77,24 +90,38 @@ class Geometry:
         self.D = D
         self.L = L
         self.s = min(L[:D]) if D > 0 else max(L)
-        M = []
-        Lext = []
+        M, Lext, origin, fper, pad = [], [], [], [], []
         for i in range(3):
             ratio = L[i] / self.s
             if i < D:
                 m = int(round(ratio))
-                if abs(ratio - m) > 1e-12 * max(1.0, ratio):
-                    raise NotImplementedError("periodic length not an integer multiple of the cube side")
-                M.append(m)
-                Lext.append(L[i])
+                if abs(ratio - m) <= 1e-12 * max(1.0, ratio):      # exact tiling
+                    M.append(m)
+                    Lext.append(L[i])
+                    origin.append(0.0)
+                    fper.append(True)
+                    pad.append(False)
+                else:                                               # cut cubes + padding
+                    m = int(math.ceil(ratio * (1 - 1e-12))) + 2
+                    M.append(m)
+                    Lext.append(m * self.s)
+                    origin.append(-self.s)
+                    fper.append(False)
+                    pad.append(True)
             else:
                 m = int(math.ceil(ratio * (1 - 1e-12)))
                 M.append(max(m, 1))
                 Lext.append(M[-1] * self.s)
+                origin.append(0.0)
+                fper.append(False)
+                pad.append(False)
         self.M = tuple(M)
         self.Lext = Lext
+        self.origin = tuple(origin)
         self.nu0 = self.s
         self.periodic = tuple(i < D for i in range(3))
+        self.fperiodic = tuple(fper)
+        self.padded = tuple(pad)
 
 
 def root_modes(kernel, geom, c, return_axes=False):

@@ -4,7 +4,9 @@ Sec. 3.1.1: boxes split into 8 children while they hold more than n_s points; th
 tree is then made level-restricted (2:1 balanced: leaves sharing a boundary point
 differ by at most one level), with neighbour relations extended by periodic
 wrapping.  Sec. 4.1.3: one octree per cube of the tiling, neighbour lists across
-cubes, periodicity in the exactly tiled directions, balance over the whole forest.
+cubes, periodicity in the exactly tiled directions, balance over the whole forest; a direction
+that is periodic but not exactly tiled is padded and non-periodic in the forest (Sec. 4.1.1,
+4.1.2), its periodic images being extra sources (replicate()).
 
 Membership is decided on integer coordinates: a point's global integer coordinate
 on the finest grid (BITS levels below the cube) is G_i = floor((w_i / s) 2^BITS)
@@ -27,16 +29,14 @@ import numpy as np
 BITS = 18          # finest integer level below a cube; also the depth cap
 
 
-def wrap_and_quantize(points, geom):
-    """Wrap periodic coordinates into [0, L_i) and compute global integer coordinates.
+def wrap(points, geom):
+    """Wrap periodic coordinates into [0, L_i) (Eq. periodic-images).
 
     Periodic axis: w = x - L floor(x/L); w >= L -> w - L; w < 0 -> 0.
     Free axis: w = x, which must lie in [0, L_i) (else ValueError).
-    G = floor((w / s) * 2^BITS) clamped to [0, M_i 2^BITS - 1].
     """
     x = np.asarray(points, dtype=np.float64)
     w = np.empty_like(x)
-    G = np.empty(x.shape, dtype=np.int64)
     for i in range(3):
         Li = geom.L[i]
         if geom.periodic[i]:
@@ -48,9 +48,52 @@ def wrap_and_quantize(points, geom):
             if np.any(~(wi >= 0)) or np.any(~(wi < Li)):
                 raise ValueError("point outside the free extent [0, L_i)")
         w[:, i] = wi
+    return w
+
+
+def replicate(w, geom):
+    """Periodic images of the sources in the padded (non-exactly tiled) directions (Sec. 4.1.2).
+
+    Every image w + sum_i n_i L_i e_i (n_i integer, n = 0 excluded, i over the padded axes)
+    that falls inside Omega_ext = [origin_i, origin_i + M_i s) is added.  Returns (w_ext, src):
+    the original points first, then the images in order of (n, source); src[j] is the index of
+    the original point behind point j.
+    """
+    N = w.shape[0]
+    axes = [i for i in range(3) if geom.padded[i]]
+    if not axes:
+        return w, np.arange(N)
+    pts, src = [w], [np.arange(N)]
+    lo = np.array(geom.origin)
+    hi = lo + np.array(geom.M) * geom.s
+    rng = range(-3, 4)
+    for ns in itertools.product(rng, repeat=len(axes)):
+        if all(n == 0 for n in ns):
+            continue
+        img = w.copy()
+        for i, n in zip(axes, ns):
+            img[:, i] = w[:, i] + n * geom.L[i]
+        inside = np.all((img >= lo) & (img < hi), axis=1)
+        pts.append(img[inside])
+        src.append(np.nonzero(inside)[0])
+    return np.vstack(pts), np.concatenate(src)
+
+
+def quantize(w, geom):
+    """Global integer coordinates G = floor(((w - origin) / s) * 2^BITS), clamped to
+    [0, M_i 2^BITS - 1]; the origin is the lower corner of Omega_ext (0 unless padded)."""
+    G = np.empty(w.shape, dtype=np.int64)
+    for i in range(3):
+        wi = w[:, i] - geom.origin[i]
         g = np.floor((wi / geom.s) * float(2 ** BITS))
         G[:, i] = np.clip(g, 0, geom.M[i] * 2 ** BITS - 1).astype(np.int64)
-    return w, G
+    return G
+
+
+def wrap_and_quantize(points, geom):
+    """wrap() then quantize() (no images)."""
+    w = wrap(points, geom)
+    return w, quantize(w, geom)
 
 
 class Box:
@@ -128,7 +171,7 @@ class Forest:
         geom = self.geom
         ntot = np.array([geom.M[i] * 2 ** BITS for i in range(3)], dtype=np.int64)
         shifts = [s for s in itertools.product((-1, 0, 1), repeat=3)
-                  if all(s[i] == 0 or geom.periodic[i] for i in range(3))]
+                  if all(s[i] == 0 or geom.fperiodic[i] for i in range(3))]
         while True:
             leaves = self.leaves()
             lev = np.array([b.level for b in leaves])
@@ -183,7 +226,7 @@ class Forest:
         """
         geom = self.geom
         shifts = [s for s in itertools.product((-1, 0, 1), repeat=3)
-                  if all(s[i] == 0 or geom.periodic[i] for i in range(3))]
+                  if all(s[i] == 0 or geom.fperiodic[i] for i in range(3))]
         pw = [[] for _ in range(self.nlevels)]
         direct = []
 

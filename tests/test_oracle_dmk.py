@@ -36,7 +36,10 @@ def rel(a, b):
 
 
 CASES = [(3, [1, 1, 1]), (3, [2, 1, 1]), (2, [1, 1, 0.5]), (2, [1, 2, 1]), (1, [1, 1, 1]), (1, [2, 1, 1]),
-         (0, [1, 1, 1])]
+         (0, [1, 1, 1]),
+         # non-exact tilings (Sec. 4.1.1-4.1.2: cut cubes, padding, source images): Table 2's
+         # [1, 1.3, 1.7], the same with the padded axis first, and a slab with L_2 / L_1 = 1.3
+         (3, [1, 1.3, 1.7]), (3, [1.3, 1, 1.7]), (2, [1, 1.3, 0.5])]
 
 
 @pytest.mark.parametrize("D,L", CASES, ids=lambda v: str(v))
@@ -49,8 +52,9 @@ def test_laplace_vs_ewald(D, L):
     assert rel(r.grad[:, :, 0], ge) < 3e-6
 
 
-def test_laplace_vs_ewald_tight():
-    L = [1, 1, 1]
+@pytest.mark.parametrize("L", [[1, 1, 1], [1, 1.3, 1.7]])
+def test_laplace_vs_ewald_tight(L):
+    """Table 2 reports 8.5e-11 for L = [1, 1.3, 1.7] at 1e-9 (a non-exact tiling)."""
     x = workloads.uniform_points(80, L, seed=3)
     q = workloads.neutral_charges(80, seed=4)
     r = evaluate("laplace", 3, L, 1e-9, x, q, n_s=10)
@@ -139,7 +143,7 @@ def test_stokes_free_space_direct(kernel):
     assert rel(r.grad, g) < 1e-5
 
 
-@pytest.mark.parametrize("D,L", [(3, [1, 1, 1]), (2, [1, 1, 1]), (1, [1, 1, 1])])
+@pytest.mark.parametrize("D,L", [(3, [1, 1, 1]), (2, [1, 1, 1]), (1, [1, 1, 1]), (3, [1, 1.3, 1.7])])
 def test_rotlet_is_curl_of_laplace(D, L):
     """Eq. rotlet_def_deriv: Omega_jl tau_l = -1/2 eps_jlm d_m H tau_l, so the rotlet sum equals
     -1/2 curl of three Laplace potentials (one per torque component) -- to within eps."""
@@ -178,7 +182,7 @@ def test_hasimoto_smooth_part_is_inverse_transform(r):
     assert np.abs(small - np.eye(3) / (2 * np.pi ** 1.5 * nu)).max() < 1e-5 / nu
 
 
-@pytest.mark.parametrize("L", [[1, 1, 1], [1, 1, 2]])
+@pytest.mark.parametrize("L", [[1, 1, 1], [1, 1, 2], [1, 1.3, 1.7]])
 def test_stokeslet_3p_vs_ewald(L):
     """D = 3 Stokeslet: oracle vs Hasimoto's Ewald sum (two split parameters agree to roundoff),
     velocities and target gradients (complex step of the Ewald sum)."""
@@ -277,7 +281,7 @@ def test_stokeslet_1p_vs_ewald(L):
     assert rel(r.grad, g) < 1e-8
 
 
-@pytest.mark.parametrize("D,L", [(3, [1, 1, 1]), (2, [1, 1, 0.5]), (1, [1, 1, 1])])
+@pytest.mark.parametrize("D,L", [(3, [1, 1, 1]), (2, [1, 1, 0.5]), (1, [1, 1, 1]), (3, [2, 1.3, 1.7])])
 def test_stresslet_is_stokeslet_stress(D, L):
     """Stresslet (rho[s, 3l+m] = Q_lm) = sum_m [d_m u^(m)_j + d_j u^(m)_m] + sum_l d_l phi^(lj),
     u^(m) the Stokeslet velocity of the forces Q_lm (l = 0..2), phi^(lj) the Laplace potential of
