@@ -17,7 +17,7 @@ import numpy as np
 from .params import c_and_p, n_f, Geometry, root_modes
 from .pswf import PSWFWindow
 from .kernels import Kernel
-from .tree import Forest, wrap, replicate, quantize
+from .tree import BITS, Forest, wrap, replicate, quantize
 from . import symbols as sym
 
 _CSTEP = 1e-30
@@ -166,7 +166,8 @@ class Result:
     pass
 
 
-def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_parts=False, targets=None):
+def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_parts=False, targets=None,
+             owned_cubes=None, chi_reduce=None):
     """Evaluate u(x_t) = sum_s sum*_p K(x_t - x_s + p) rho_s (Eq. periodic_sum) by periodized DMK.
 
     points (N,3), strengths (N, d_rho); returns potentials (N, d_u) in input order and, if
@@ -177,6 +178,15 @@ def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_p
     are those of the whole problem -- but the leaf step (Sec. 3.1.5) runs only for the listed
     targets, so each of their values is the one the full evaluation gives; the other rows of
     the outputs are NaN.
+
+    owned_cubes, chi_reduce: the spatial split of the evaluation over several evaluators.  The
+    structure factor of Eq. structurefac is a sum over the cubes; with owned_cubes (cube indices
+    m1 + M1 (m2 + M2 m3)) only those cubes enter this evaluator's partial sum, and
+    chi_reduce(partial) -> total combines the partial sums of all evaluators (e.g. an
+    all-reduce): it receives one flat complex vector, the structure factor followed by the
+    d_rho strength sums over the own cubes (the total strength enters the Stokeslet constants).  The points given are then this evaluator's own points plus those of the
+    cubes adjacent to its own cubes (the near field of Sec. 3.1.4-3.1.5 reaches no further),
+    and targets should be its own points.
     """
     kern = Kernel(kernel)
     c, p = c_and_p(kernel, tol)
@@ -261,7 +271,23 @@ def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_p
         Lx, Ly, Lz = (lagrange(xi[:, i], nodes) for i in range(3))
         return np.einsum("sa,sb,sc,sd->abcd", Lx, Ly, Lz, rho[orig], optimize=True)
 
+    Mc = geom.M
+
+    def cube_index(b):
+        return b.ix[0] + Mc[0] * (b.ix[1] + Mc[1] * b.ix[2])
+
+    owned = None if owned_cubes is None else set(int(m) for m in owned_cubes)
+    # total strength, for the constants of Sec. 5 that multiply it (the truncated Stokeslet,
+    # Remark stokeslet_const_corr): over this evaluator's own cubes when split, then reduced
+    # with the structure factor
+    rho_sum = rho_t.sum(axis=0)
+    if owned is not None:
+        Go = G[:N] >> BITS
+        mine = np.isin(Go[:, 0] + Mc[0] * (Go[:, 1] + Mc[1] * Go[:, 2]), sorted(owned))
+        rho_sum = rho_t[mine].sum(axis=0)
     for b in roots:
+        if owned is not None and cube_index(b) not in owned:
+            continue
         pr = chi_proxy(b)
         if pr is None:
             continue
@@ -269,6 +295,10 @@ def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_p
         ph = np.exp(-1j * (axes[0][:, None, None] * cb[0] + axes[1][None, :, None] * cb[1]
                            + axes[2][None, None, :] * cb[2]))
         chi += ph[..., None] * np.einsum("ai,bj,ck,ijkd->abcd", Sc[0], Sc[1], Sc[2], pr, optimize=True)
+    if chi_reduce is not None:
+        both = chi_reduce(np.concatenate([chi.ravel(), rho_sum.astype(complex)]))
+        chi = both[:chi.size].reshape(chi.shape)
+        rho_sum = both[chi.size:].real
     uhat = np.einsum("abcud,abcd->abcu", Wk, chi)
     for b in roots:
         cb = center(b)
@@ -279,7 +309,7 @@ def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_p
     kk_count = int(keep.sum())
     if kernel == "stokeslet" and D == 0:
         # constant removed by the C^1 gauge of the truncated biharmonic kernel (symbols.B3_trunc)
-        cst = sym.stokeslet_free_space_constant(R) * rho_t.sum(axis=0)
+        cst = sym.stokeslet_free_space_constant(R) * rho_sum
         for b in roots:
             local[b.id] = local[b.id] + cst
 
@@ -386,7 +416,7 @@ def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_p
         Rr = R
         corr = -np.diag([(1 + math.log(Rr)) / (2 * np.pi), (math.log(Rr) + 0.5) / (4 * np.pi),
                          (math.log(Rr) + 0.5) / (4 * np.pi)]) / geom.L[0]
-        u += (corr @ rho_t.sum(axis=0))[None, :]    # NaN rows (targets not evaluated) stay NaN
+        u += (corr @ rho_sum)[None, :]    # NaN rows (targets not evaluated) stay NaN
     res = Result()
     res.u = u
     res.grad = gu

@@ -410,3 +410,64 @@ def test_target_subset_equals_full(kernel, D, L):
     assert rel(sub.grad[idx], full.grad[idx]) < 1e-14
     rest = np.setdiff1d(np.arange(N), idx)
     assert np.all(np.isnan(sub.u[rest])) and np.all(np.isnan(sub.grad[rest]))
+
+
+@pytest.mark.parametrize("kernel,D,L,N,parts", [
+    ("laplace", 3, [1, 1, 6], 900, [[0, 1, 2], [3, 4, 5]]),
+    # free axis: the truncated-kernel constant multiplies the total strength (Remark
+    # stokeslet_const_corr), which only the reduction supplies
+    ("stokeslet", 1, [1, 1, 4], 500, [[0, 3], [1, 2]]),
+])
+def test_split_over_cubes_equals_full(kernel, D, L, N, parts):
+    """The structure factor of Eq. structurefac is a sum over the cubes and the near field of a
+    target reaches only the adjacent cubes: two evaluators, each given its own cubes' points
+    plus those of the adjacent cubes, each summing chi (and the total strength) over its own
+    cubes, the partial sums added, reproduce the full evaluation at their own targets (to
+    rounding)."""
+    from oracle.params import Geometry
+    from oracle.tree import BITS, quantize, wrap
+    tol = 1e-6
+    d = 3 if kernel == "stokeslet" else 1
+    x = workloads.uniform_points(N, L, seed=61)
+    # Stokeslet forces with a net force, so that the constant is not zero
+    q = (workloads.neutral_charges(N, seed=62).reshape(N, 1) if d == 1
+         else np.random.default_rng(62).standard_normal((N, 3)) + 0.5)
+    full = evaluate(kernel, D, L, tol, x, q, n_s=40, grad=True)
+    geom = Geometry(D, L)
+    M = geom.M
+    Gc = quantize(wrap(x, geom), geom) >> BITS
+    cube = Gc[:, 0] + M[0] * (Gc[:, 1] + M[1] * Gc[:, 2])
+    ix = lambda m: np.array([m % M[0], (m // M[0]) % M[1], m // (M[0] * M[1])])
+
+    def near(a, b):
+        da = np.abs(ix(a) - ix(b))
+        for i in range(3):
+            if geom.periodic[i]:
+                da[i] = min(da[i], M[i] - da[i])
+        return np.all(da <= 1)
+
+    ncube = M[0] * M[1] * M[2]
+    keeps = []
+    for own in parts:
+        ghost = {m for m in range(ncube) for o in own if near(m, o)}
+        keeps.append(np.isin(cube, sorted(set(own) | ghost)))
+    partial = {}
+    for rank, own in enumerate(parts):
+        # the first pass only records this evaluator's partial sums
+        keep = keeps[rank]
+        evaluate(kernel, D, L, tol, x[keep], q[keep], n_s=40, owned_cubes=own,
+                 chi_reduce=lambda c, r=rank: partial.__setitem__(r, c.copy()) or c,
+                 targets=np.nonzero(np.isin(cube[keep], own))[0])
+    total = partial[0] + partial[1]
+    u = np.full(full.u.shape, np.nan)
+    g = np.full(full.grad.shape, np.nan)
+    for rank, own in enumerate(parts):
+        keep = keeps[rank]
+        idx = np.nonzero(keep)[0]
+        mine = np.nonzero(np.isin(cube[keep], own))[0]
+        r = evaluate(kernel, D, L, tol, x[keep], q[keep], n_s=40, grad=True, owned_cubes=own,
+                     chi_reduce=lambda c: total, targets=mine)
+        u[idx[mine]] = r.u[mine]
+        g[idx[mine]] = r.grad[mine]
+    assert rel(u, full.u) < 1e-13
+    assert rel(g, full.grad) < 1e-13

@@ -65,5 +65,10 @@ def test_geometry_tiling():
     assert g.M == (1, 1, 16)
     g = Geometry(0, [0.5, 2.0, 1.0])
     assert g.s == 2.0 and g.M == (1, 1, 1)
-    with pytest.raises(NotImplementedError):
-        Geometry(3, [1, 1.3, 1.7])
+    # non-exact tiling (Sec. 4.1.1): cubes of side min L_i, ceil(L_i / s) + 2 per padded axis
+    # (one padding cube each side, Omega_ext starting at -s), the forest non-periodic there
+    g = Geometry(3, [1, 1.3, 1.7])
+    assert g.s == 1 and g.M == (1, 4, 4) and g.origin == (0.0, -1.0, -1.0)
+    assert g.padded == (False, True, True) and g.fperiodic == (True, False, False)
+    g = Geometry(2, [1.3, 1, 0.5])
+    assert g.M == (4, 1, 1) and g.padded == (True, False, False) and g.fperiodic == (False, True, False)
