@@ -130,6 +130,39 @@ dmk_status_t dmk_eval_host(dmk_plan_t plan, int64_t N, const double* points, con
 dmk_status_t dmk_vjp(dmk_plan_t plan, int64_t N, const double* points, const double* strengths,
                      const double* grad_u, const double* g, double* d_strengths, double* d_points);
 
+/* One rank's part of an evaluation split over cubes (spatial sharding; a multi-GPU use of the
+ * method, not in the paper).  The structure factor of Sec. 4.3 (Eq. structurefac) is a sum
+ * over the cubes of the tiling, and the near field of a target (plane waves and residual sums,
+ * Sec. 3.1.4-3.1.5) reaches only the cubes adjacent to its own.  A rank that owns a set of
+ * cubes therefore evaluates its own targets from its own points plus those of the adjacent
+ * cubes ("ghosts"), once the partial structure factors of all ranks are summed.
+ *   points, strengths  device, N x 3 and N x d_rho: the n_own points of the rank's cubes first,
+ *                      then the ghost points (every point of every cube adjacent to an owned
+ *                      cube that the rank does not own, periodic neighbours included).
+ *   potentials, grad   device, n_own x d_u and n_own x 3 x d_u (grad may be NULL): the results
+ *                      for the owned points, in their order.
+ *   cube_owned         host, M1 M2 M3 ints, cube m1 + M1 (m2 + M2 m3) owned if nonzero: only
+ *                      those cubes enter this rank's partial structure factor.
+ *   reduce             called once per call with the rank's partial sums -- n doubles at chi,
+ *                      pinned HOST memory owned by the plan, valid during the call: the structure
+ *                      factor (n - 2 d_rho doubles, complex pairs), then the d_rho sums of the
+ *                      owned strengths and the d_rho sums of their absolute values (the total
+ *                      strength enters the constants of the truncated kernels, Sec. 5) -- and
+ *                      ctx; it must replace the n doubles by their sum over all ranks (an
+ *                      all-reduce over any host transport) and return 0.  Nonzero returns
+ *                      DMK_ERR_CUDA.  Every rank's call reduces the same n, a rank with N = 0
+ *                      included.
+ * Exact tilings only (DMK_ERR_UNSUPPORTED otherwise).  The sum of the strengths is not checked
+ * (no rank sees all of them).  The result for an owned point is that of dmk_eval on all points
+ * when the forest of the owned and ghost cubes is that of the whole problem there (2:1 balance
+ * of Sec. 3.1.1 propagating no further than one cube); the call returns when the results are
+ * complete. */
+typedef int (*dmk_chi_reduce_fn)(double* chi, int64_t n, void* ctx);
+
+dmk_status_t dmk_eval_shard(dmk_plan_t plan, int64_t N, int64_t n_own, const double* points, const double* strengths,
+                            double* potentials, double* grad, const int* cube_owned, dmk_chi_reduce_fn reduce,
+                            void* ctx);
+
 /* dmk_eval without any device allocation.  The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc at evaluation time -- applications whose
  * device memory is fully reserved by their own pool allocator and that must not let a

@@ -63,9 +63,12 @@ struct dmk_plan_s {
     void* d_root = nullptr;
     RootTab root{};
     double* d_self = nullptr;      // self_val then self_grad
+    int* d_cube = nullptr;         // non-exact tilings: cube classes (Mtot), then the cut-cube count and list
     // workspace
     std::vector<DevBuf> bufs;
     unsigned char* h_meta = nullptr;   // pinned host staging for the small per-evaluation readbacks
+    double* h_chi = nullptr;           // pinned host staging of a shard's structure factor
+    size_t h_chi_cap = 0;
     cudaEvent_t ev[11] = {};
     // residual sums (k_pair) run on their own stream beside the far field when pair_overlap is
     // set, at most pair_blocks resident blocks per SM (0: as many as fit).  Off by default: on
@@ -113,7 +116,7 @@ enum BufId {
     B_W, B_KEYS, B_KEYS2, B_IDX, B_IDX2, B_XS, B_RS, B_CUB, B_FLAGS, B_CNT,
     B_CELLS, B_R, B_CAND, B_BOXU64, B_BOXINT, B_LEAVES, B_DOFFS, B_DL, B_NLBOX, B_TASKS, B_BAL,
     B_PROXY, B_LOCAL, B_PW, B_SCRATCH, B_CHI, B_UHAT, B_MISC, B_DEVPTS, B_DEVRHO, B_DEVPOT, B_DEVGRAD, B_XF, B_VW, B_PART,
-    B_VJPV, B_VJPG,
+    B_VJPV, B_VJPG, B_ICNT, B_SRC, B_ORIG, B_CHIP, B_SHARDCLS,
     B_COUNT
 };
 
@@ -410,7 +413,8 @@ dmk_status_t launch_anterp(dmk_plan_s* plan, Tab<T>& tab, int nleaf_cap, const i
     size_t sm = 3 * (size_t)kAnterpChunk * MAXP * sizeof(T);
     CKS(set_smem(plan, k_anterp<T, MAXP>, sm));
     unsigned grid = (unsigned)std::max(1, std::min(nleaf_cap, plan->n_sm * 8));
-    k_anterp<T, MAXP><<<grid, threads, sm, plan->stream>>>(nleaf_dev, leaves, B, xs, N, rs, tab, plan->T.s, proxy);
+    k_anterp<T, MAXP><<<grid, threads, sm, plan->stream>>>(nleaf_dev, leaves, B, xs, N, rs, tab, plan->T.s, proxy,
+                                                           nullptr, 0);
     return DMK_OK;
 }
 
@@ -456,11 +460,21 @@ dmk_status_t launch_pair(dmk_plan_s* plan, Tab<T>& tab, const int* leaves, BoxAr
 // leaf expansions + residual sums + self terms (k_leafexp)
 template <class T, int K, bool G>
 dmk_status_t launch_leafexp(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int* leaves, BoxArrays B, const T* local,
-                            const double* xs, int64_t N, LeafOut lo) {
+                            const double* xs, int64_t N, LeafOut lo, int direct_leaf, int n_nl, const int* nl_box,
+                            int n_root) {
     const size_t se = leafexp_smem<T>(tab.p);
+    if (direct_leaf) {
+        // one item per non-leaf box with leaf children and per cube that is a leaf
+        CKS(set_smem(plan, k_leafexp_parent<T, K, G>, se));
+        const unsigned grid = (unsigned)std::max(1, std::min(n_nl + n_root, plan->n_sm * 16));
+        k_leafexp_parent<T, K, G><<<grid, kLeafExpThreads, se, plan->stream>>>(n_nl, nl_box, n_root, B, tab, plan->geo,
+                                                                               local, xs, N, lo);
+        return DMK_OK;
+    }
     CKS(set_smem(plan, k_leafexp<T, K, G>, se));
     const unsigned grid = (unsigned)std::max(1, std::min(nleaf, plan->n_sm * 16));
-    k_leafexp<T, K, G><<<grid, kLeafExpThreads, se, plan->stream>>>(nleaf, leaves, B, tab, plan->geo, local, xs, N, lo);
+    k_leafexp<T, K, G><<<grid, kLeafExpThreads, se, plan->stream>>>(nleaf, leaves, B, tab, plan->geo, local, xs, N, lo,
+                                                                    0);
     return DMK_OK;
 }
 
@@ -491,19 +505,90 @@ struct TreeInfo {
 };
 
 
+// a shard's partial structure factor (n doubles at chi, device) and its strength sums (2 d_rho
+// doubles at sums, device) summed over the ranks by the caller's reduction; nothing without a
+// shard
+dmk_status_t reduce_chi(dmk_plan_s* plan, const struct ShardArgs* sh, Cx<double>* chi, int64_t n, double* sums);
+
+// one rank of a cube-sharded evaluation (dmk_eval_shard): outputs for the first n_own points,
+// structure factor over the owned cubes, completed by the caller's reduction
+struct ShardArgs {
+    int64_t n_own;
+    const int* cube_owned;      // host, Mtot flags
+    dmk_chi_reduce_fn reduce;
+    void* ctx;
+};
+
+dmk_status_t reduce_chi(dmk_plan_s* plan, const ShardArgs* sh, Cx<double>* chi, int64_t n, double* sums) {
+    if (!sh) return DMK_OK;
+    const int ns = 2 * plan->T.d_rho;
+    const int64_t ntot = n + ns;
+    // through plan-owned pinned host memory, so that any host-side all-reduce can serve
+    if (plan->h_chi_cap < (size_t)ntot) {
+        if (plan->h_chi) cudaFreeHost(plan->h_chi);
+        plan->h_chi = nullptr;
+        plan->h_chi_cap = 0;
+        if (cudaMallocHost((void**)&plan->h_chi, (size_t)ntot * sizeof(double)) != cudaSuccess) {
+            plan->h_chi = nullptr;
+            plan->err = "pinned host allocation for the structure factor failed";
+            return DMK_ERR_OOM;
+        }
+        plan->h_chi_cap = (size_t)ntot;
+    }
+    CK(cudaMemcpyAsync(plan->h_chi, chi, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, plan->stream));
+    CK(cudaMemcpyAsync(plan->h_chi + n, sums, (size_t)ns * sizeof(double), cudaMemcpyDeviceToHost, plan->stream));
+    CK(cudaStreamSynchronize(plan->stream));
+    if (sh->reduce(plan->h_chi, ntot, sh->ctx) != 0) {
+        plan->err = "the structure-factor reduction of dmk_eval_shard failed";
+        return DMK_ERR_CUDA;
+    }
+    CK(cudaMemcpyAsync(chi, plan->h_chi, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, plan->stream));
+    CK(cudaMemcpyAsync(sums, plan->h_chi + n, (size_t)ns * sizeof(double), cudaMemcpyHostToDevice, plan->stream));
+    return DMK_OK;
+}
+
 template <class T>
-dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pts, const double* rho, double* pot,
-                      double* grad) {
+dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* pts, const double* rho, double* pot,
+                      double* grad, const ShardArgs* sh = nullptr) {
     cudaStream_t st = plan->stream;
     const PlanTables& P = plan->T;
     const int drho = P.d_rho, du = P.d_u, p = P.p, p3 = p * p * p;
     const Geo g = plan->geo;
     const int Mtot = g.M[0] * g.M[1] * g.M[2];
+    const bool padded = g.padded[0] || g.padded[1] || g.padded[2];
     int launches = 0;
     auto rec = [&](int i) { if (plan->timing) cudaEventRecord(plan->ev[i], st); };
     rec(0);
+    // ---- (0) non-exact tilings: the periodic images of the sources in Omega_ext (Sec. 4.1.2)
+    // are appended to the N0 points as extra sources; N counts both
+    int64_t N = N0;
+    void *vmisc, *vsrc = nullptr, *vicnt = nullptr;
+    CKS(ensure(plan, B_MISC, 4096, &vmisc));
+    // the previous evaluation's residual kernel (side stream) is done with the workspace
+    CK(cudaStreamWaitEvent(st, plan->ev_join, 0));
+    CK(cudaMemsetAsync(vmisc, 0, 2048, st));
+    if (padded) {
+        CKS(ensure(plan, B_ICNT, (size_t)(N0 + 1) * 2 * sizeof(int), &vicnt));
+        int* icnt = (int*)vicnt;
+        int* ioff = icnt + N0 + 1;
+        CK(cudaMemsetAsync(icnt + N0, 0, sizeof(int), st));
+        k_images<false><<<nblk(N0, 256), 256, 0, st>>>(N0, pts, g, nullptr, 0, icnt, nullptr, nullptr, nullptr,
+                                                        nullptr);
+        size_t tb = 0;
+        cub::DeviceScan::ExclusiveSum(nullptr, tb, icnt, ioff, (int)(N0 + 1), st);
+        void* vtmp;
+        CKS(ensure(plan, B_CUB, std::max<size_t>(tb, 1 << 20), &vtmp));
+        CK(cub::DeviceScan::ExclusiveSum(vtmp, tb, icnt, ioff, (int)(N0 + 1), st));
+        CK(cudaMemcpyAsync(plan->h_meta, ioff + N0, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CKS(host_wait(plan, st));
+        int nimg = 0;
+        std::memcpy(&nimg, plan->h_meta, sizeof(int));
+        N = N0 + nimg;
+        if (N > ((int64_t)1 << 30)) { plan->err = "more than 2^30 points with the periodic images"; return DMK_ERR_INVALID_ARG; }
+        launches += 3;
+    }
     // ---- (1) keys, sort, gather --------------------------------------------------------
-    void *vw, *vkeys, *vkeys2, *vidx, *vidx2, *vxs, *vrs, *vmisc;
+    void *vw, *vkeys, *vkeys2, *vidx, *vidx2, *vxs, *vrs;
     CKS(ensure(plan, B_W, 3 * N * sizeof(double), &vw));
     CKS(ensure(plan, B_KEYS, N * sizeof(uint64_t), &vkeys));
     CKS(ensure(plan, B_KEYS2, N * sizeof(uint64_t), &vkeys2));
@@ -511,21 +596,30 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     CKS(ensure(plan, B_IDX2, N * sizeof(int), &vidx2));
     CKS(ensure(plan, B_XS, 3 * N * sizeof(double), &vxs));
     CKS(ensure(plan, B_RS, N * drho * sizeof(double), &vrs));
-    CKS(ensure(plan, B_MISC, 4096, &vmisc));
     int* d_err = (int*)vmisc;
     double* d_sums = (double*)((char*)vmisc + 256);          // 2*drho doubles
     unsigned long long* d_pairs = (unsigned long long*)((char*)vmisc + 768);
-    // the previous evaluation's residual kernel (side stream) is done with the workspace
-    CK(cudaStreamWaitEvent(st, plan->ev_join, 0));
-    CK(cudaMemsetAsync(vmisc, 0, 2048, st));
     uint64_t* keys = (uint64_t*)vkeys;
     uint64_t* keys2 = (uint64_t*)vkeys2;
     int* idx = (int*)vidx;
     int* idx2 = (int*)vidx2;
     double* xs = (double*)vxs;
     double* rs = (double*)vrs;
-    k_quantize<<<nblk(N, 256), 256, 0, st>>>(N, pts, g, (double*)vw, keys, idx, d_err);
+    k_quantize<<<nblk(N0, 256), 256, 0, st>>>(N0, pts, g, (double*)vw, N, keys, idx, d_err);
     ++launches;
+    // the image of every source, its key and its original (src); orig: sorted point -> original
+    int* src = nullptr;
+    int* orig = nullptr;
+    if (padded) {
+        void* vorig;
+        CKS(ensure(plan, B_SRC, (size_t)N * sizeof(int), &vsrc));
+        CKS(ensure(plan, B_ORIG, (size_t)N * sizeof(int), &vorig));
+        src = (int*)vsrc;
+        orig = (int*)vorig;
+        const int* ioff = (const int*)vicnt + N0 + 1;
+        k_images<true><<<nblk(N0, 256), 256, 0, st>>>(N0, pts, g, (double*)vw, N, nullptr, ioff, keys, idx, src);
+        ++launches;
+    }
     int cube_bits = 0;
     while ((1 << cube_bits) < Mtot) ++cube_bits;
     const int end_bit = 3 * kBits + cube_bits;
@@ -577,8 +671,9 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         CKS(ensure(plan, B_CUB, std::max<size_t>(tmp_bytes, 1 << 20), &vcub));
         cub_cap = plan->bufs[B_CUB].cap;
         CK(cub::DeviceRadixSort::SortPairs(vcub, tmp_bytes, keys, keys2, idx, idx2, (int)N, begin_bit, end_bit, st));
-        k_gather<<<ngb, kGatherThreads, 0, st>>>(N, drho, idx2, (const double*)vw, rho, xs, rs, pk,
-                                                  (double*)vpart);
+        // strength sums over the original points (a shard: over its own points, first n_own)
+        k_gather<<<ngb, kGatherThreads, 0, st>>>(N, sh ? sh->n_own : N0, drho, idx2, src, g, (const double*)vw, rho,
+                                                  xs, rs, pk, orig, (double*)vpart);
         k_sum_partials<<<1, 1024, 0, st>>>(ngb, 2 * drho, (const double*)vpart, d_sums);
         CK(cudaMemsetAsync(d_missing, 0, (kBits + 1) * sizeof(int), st));      // missing[] and capped
         k_refine_count<<<nblkR, kRefineThreads, 0, st>>>(N, pkeys, plan->n_s, nblkR, lsort, bcnt, d_capped);
@@ -774,6 +869,8 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     lo.pot = pot;
     lo.grad = grad;
     lo.perm = idx2;
+    lo.orig = orig ? orig : idx2;
+    lo.n_orig = sh ? sh->n_own : N0;
     lo.rs = rs;
     lo.self_val = plan->d_self;
     lo.self_grad = plan->d_self + P.d_u * P.d_rho;
@@ -827,24 +924,38 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     CKS(ensure(plan, B_LOCAL, (size_t)nb * du * p3 * sizeof(T), &vloc));
     T* proxy = (T*)vpr;
     T* local = (T*)vloc;
-    CK(cudaMemsetAsync(proxy, 0, (size_t)nb * drho * p3 * sizeof(T), st));
+    // FP32 path, p <= 24: sources anterpolated onto the parent grids (k_anterp3), every proxy
+    // that is read (non-leaf boxes, cubes) written by it or by the upward pass; otherwise leaf
+    // proxies, the upward pass over all children, and a zeroed array
+    //   direct_up: the leaf sources go straight to the parent grids when the parents give enough
+    // work items for the GPU (else each leaf onto its own grid and the upward pass takes every
+    // child); direct_leaf (downward): the leaf targets evaluate their parent's expansion
+    const bool direct_leaf = sizeof(T) == 4 && p <= 24;
+    const bool direct_up = direct_leaf && n_nl + Mtot >= 2 * plan->n_sm;
+    if (!direct_up) {
+        CK(cudaMemsetAsync(proxy, 0, (size_t)nb * drho * p3 * sizeof(T), st));
+        ++launches;
+    }
     CK(cudaMemsetAsync(local, 0, (size_t)nb * du * p3 * sizeof(T), st));
-    launches += 2;
+    ++launches;
     bool anterp_done = false;
     if constexpr (sizeof(T) == 4) {
-        if (nleaf_cap > 0 && p <= 24) {
-            const int XM = 4 * ((drho * p + 3) / 4);
-            const unsigned grid = (unsigned)std::max(1, std::min(nleaf_cap, plan->n_sm * 8));
+        if (direct_leaf && nleaf_cap > 0) {
+            const int items = direct_up ? n_nl + Mtot : nleaf_cap;
+            const unsigned grid = (unsigned)std::max(1, std::min(items, plan->n_sm * 8));
+            const int TN = p <= 20 ? 20 : 24;
+            const int ntile = drho * ((p + 3) / 4) * p * ((p + TN - 1) / TN);
+            const int threads = std::min(kAntThreads, (ntile + 31) / 32 * 32);
             if (p <= 20) {
-                const size_t sm = anterp3_smem<20, 10>(XM);
-                CKS(set_smem(plan, k_anterp3<20, 10>, sm));
-                k_anterp3<20, 10><<<grid, kAntThreads, sm, st>>>(d_nleaf, leaves, B, xs, N, rs, tab, plan->T.s,
-                                                                 (float*)proxy, XM);
+                const size_t sm = anterp3_smem<20>();
+                CKS(set_smem(plan, k_anterp3<20, 20>, sm));
+                k_anterp3<20, 20><<<grid, threads, sm, st>>>(n_nl, nl_box, Mtot, B, xs, N, rs, tab, plan->T.s,
+                                                             (float*)proxy, direct_up ? nullptr : leaves, d_nleaf);
             } else {
-                const size_t sm = anterp3_smem<24, 12>(XM);
-                CKS(set_smem(plan, k_anterp3<24, 12>, sm));
-                k_anterp3<24, 12><<<grid, kAntThreads, sm, st>>>(d_nleaf, leaves, B, xs, N, rs, tab, plan->T.s,
-                                                                 (float*)proxy, XM);
+                const size_t sm = anterp3_smem<24>();
+                CKS(set_smem(plan, k_anterp3<24, 24>, sm));
+                k_anterp3<24, 24><<<grid, threads, sm, st>>>(n_nl, nl_box, Mtot, B, xs, N, rs, tab, plan->T.s,
+                                                             (float*)proxy, direct_up ? nullptr : leaves, d_nleaf);
             }
             ++launches;
             anterp_done = true;
@@ -865,6 +976,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     const size_t ch_bytes = (3 * (size_t)mp * mp + 2 * (size_t)p * p * pitch) * sizeof(T);
     const bool fast_up = p <= kMaxPFast && ch_bytes <= plan->smem_optin;
     const bool fast_shift = fast_up;
+    if (direct_leaf && !fast_up) { plan->err = "internal: the cluster upward pass does not fit"; return DMK_ERR_CUDA; }
     if (fast_up) {
         if (mp == 20) CKS(set_smem(plan, k_up_cluster<T, 20>, ch_bytes));
         else CKS(set_smem(plan, k_up_cluster<T, kMaxPFast>, ch_bytes));
@@ -874,9 +986,11 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         if (n == 0) continue;
         if (fast_up) {
             if (mp == 20)
-                k_up_cluster<T, 20><<<8 * n, up_threads, ch_bytes, st>>>(nl_box + ti.nl_off[l], B, tab, proxy);
+                k_up_cluster<T, 20><<<8 * n, up_threads, ch_bytes, st>>>(nl_box + ti.nl_off[l], B, tab, proxy,
+                                                                        direct_up ? 1 : 0);
             else
-                k_up_cluster<T, kMaxPFast><<<8 * n, up_threads, ch_bytes, st>>>(nl_box + ti.nl_off[l], B, tab, proxy);
+                k_up_cluster<T, kMaxPFast><<<8 * n, up_threads, ch_bytes, st>>>(nl_box + ti.nl_off[l], B, tab,
+                                                                               proxy, direct_up ? 1 : 0);
         } else {
             Place pl;
             unsigned char* scr;
@@ -906,8 +1020,54 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         Cx<double>* chi = (Cx<double>*)vchi;
         Cx<double>* uh = (Cx<double>*)vuh;
         auto blocks = [](int64_t n) { return (unsigned)((n + 127) / 128); };
+        // the root proxies of the structure factor: a non-exact tiling counts only the sources
+        // inside Omega (cube proxies inside, nothing for padding cubes, cut cubes from their
+        // original sources)
+        const T* rproxy = proxy;
+        if (padded || sh) {
+            void* vchip;
+            CKS(ensure(plan, B_CHIP, (size_t)Mtot * drho * p3 * sizeof(T), &vchip));
+            T* chip = (T*)vchip;
+            const int* cls = plan->d_cube;
+            if (sh) {
+                // a shard: the cubes it owns count (class 0), the others not (class 2)
+                void* vcls;
+                CKS(ensure(plan, B_SHARDCLS, (size_t)Mtot * sizeof(int), &vcls));
+                std::vector<int> hc(Mtot);
+                for (int m = 0; m < Mtot; ++m) hc[m] = sh->cube_owned[m] ? 0 : 2;
+                CK(cudaMemcpyAsync(vcls, hc.data(), Mtot * sizeof(int), cudaMemcpyHostToDevice, st));
+                CK(cudaStreamSynchronize(st));
+                cls = (const int*)vcls;
+            }
+            k_chi_proxy<T><<<nblk((int64_t)Mtot * drho * p3, 256), 256, 0, st>>>(Mtot, drho, p3, cls, proxy, chip);
+            const int ncut = sh ? 0 : (int)std::count(P.cube_class.begin(), P.cube_class.end(), 1);
+            if (ncut > 0) {
+                const int* cutlist = plan->d_cube + Mtot + 1;
+                if (p <= 20) {
+                    const int threads = (20 * 20 + 31) / 32 * 32;
+                    const size_t sm = 3 * (size_t)kAnterpChunk * 20 * sizeof(T);
+                    CKS(set_smem(plan, k_anterp<T, 20>, sm));
+                    k_anterp<T, 20><<<ncut, threads, sm, st>>>(plan->d_cube + Mtot, cutlist, B, xs, N, rs, tab, P.s,
+                                                              chip, idx2, N0);
+                } else if (p <= 24) {
+                    const int threads = (24 * 24 + 31) / 32 * 32;
+                    const size_t sm = 3 * (size_t)kAnterpChunk * 24 * sizeof(T);
+                    CKS(set_smem(plan, k_anterp<T, 24>, sm));
+                    k_anterp<T, 24><<<ncut, threads, sm, st>>>(plan->d_cube + Mtot, cutlist, B, xs, N, rs, tab, P.s,
+                                                              chip, idx2, N0);
+                } else {
+                    const size_t sm = 3 * (size_t)kAnterpChunk * 48 * sizeof(T);
+                    CKS(set_smem(plan, k_anterp<T, 48>, sm));
+                    k_anterp<T, 48><<<ncut, 512, sm, st>>>(plan->d_cube + Mtot, cutlist, B, xs, N, rs, tab, P.s, chip,
+                                                          idx2, N0);
+                }
+                ++launches;
+            }
+            rproxy = chip;
+            ++launches;
+        }
         // cubes stacked along a periodic x3: DFT over the cube index (Sec. 3.4, Case 1)
-        const bool fft_root = P.D == 3 && g.M[0] == 1 && g.M[1] == 1 && g.M[2] >= kRootFftMin &&
+        const bool fft_root = !padded && P.D == 3 && g.M[0] == 1 && g.M[1] == 1 && g.M[2] >= kRootFftMin &&
                               g.M[2] <= kRootFftMax;
         if (fft_root) {
             const int M3 = g.M[2];
@@ -921,10 +1081,11 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
             Cx<double>* B1f = q0;
             Cx<double>* B2f = B1f + (size_t)jf * f1;
             Cx<double>* Bh = B2f + (size_t)jf * f2;
-            k_root_fwd1<T><<<blocks((int64_t)jf * f1), 128, 0, st>>>(jf, p, rt, proxy, B1f);
+            k_root_fwd1<T><<<blocks((int64_t)jf * f1), 128, 0, st>>>(jf, p, rt, rproxy, B1f);
             k_root_fwd2<<<blocks((int64_t)jf * f2), 128, 0, st>>>(jf, p, rt, B1f, B2f);
             k_rootfft_dft<<<blocks((int64_t)M3 * drho * E), 128, 0, st>>>(M3, drho, (int)E, B2f, Bh);
             k_rootfft_chi<<<blocks((int64_t)drho * rt.nmode), 128, 0, st>>>(drho, p, g, rt, Bh, chi);
+            CKS(reduce_chi(plan, sh, chi, (int64_t)2 * drho * rt.nmode, d_sums));
             k_root_apply<<<nblk(rt.nmode, 128), 128, 0, st>>>(1, drho, du, rt, chi, uh);
             const int jbb = M3 * du;
             Cx<double>* C2 = q0;
@@ -937,9 +1098,10 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
                                                                                      local);
             launches += 9;
         } else {
-        k_root_fwd1<T><<<blocks((int64_t)jf * f1), 128, 0, st>>>(jf, p, rt, proxy, r0);
+        k_root_fwd1<T><<<blocks((int64_t)jf * f1), 128, 0, st>>>(jf, p, rt, rproxy, r0);
         k_root_fwd2<<<blocks((int64_t)jf * f2), 128, 0, st>>>(jf, p, rt, r0, r0 + (size_t)jf * f1);
         k_root_fwd3<<<blocks((int64_t)jf * rt.nmode), 128, 0, st>>>(jf, drho, p, g, rt, r0 + (size_t)jf * f1, chi);
+        CKS(reduce_chi(plan, sh, chi, (int64_t)2 * Mtot * drho * rt.nmode, d_sums));
         k_root_apply<<<nblk(rt.nmode, 128), 128, 0, st>>>(Mtot, drho, du, rt, chi, uh);
         Cx<double>* G = r0;
         Cx<double>* C2 = G + (size_t)jb * rt.nmode;
@@ -1041,10 +1203,11 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         if (n == 0) continue;
         if (fast_shift) {
             if (mp == 20)
-                k_shift_child<T, 20><<<8 * n, shift_threads, ch_bytes, st>>>(nl_box + ti.nl_off[l], B, tab, local);
+                k_shift_child<T, 20><<<8 * n, shift_threads, ch_bytes, st>>>(nl_box + ti.nl_off[l], B, tab, local,
+                                                                            direct_leaf ? 1 : 0);
             else
                 k_shift_child<T, kMaxPFast><<<8 * n, shift_threads, ch_bytes, st>>>(nl_box + ti.nl_off[l], B, tab,
-                                                                                   local);
+                                                                                   local, direct_leaf ? 1 : 0);
         } else {
             Place pl;
             unsigned char* scr;
@@ -1053,6 +1216,19 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
             CKS(set_smem(plan, k_shift<T>, pl.use_smem ? bytes : 0));
             k_shift<T><<<pl.grid, 256, pl.use_smem ? bytes : 0, st>>>(n, nl_box + ti.nl_off[l], B, tab, local, scr,
                                                                      bytes, pl.use_smem);
+        }
+        ++launches;
+    }
+    // direct_leaf: the non-leaf boxes with leaf children turn their grids into Chebyshev
+    // coefficients (their leaf children's targets evaluate them)
+    if (direct_leaf && n_nl > 0) {
+        const size_t cb = ((size_t)mp * mp + 2 * (size_t)p * p * pitch) * sizeof(T);
+        if (mp == 20) {
+            CKS(set_smem(plan, k_box_coef<T, 20>, cb));
+            k_box_coef<T, 20><<<n_nl, shift_threads, cb, st>>>(nl_box, B, tab, local);
+        } else {
+            CKS(set_smem(plan, k_box_coef<T, kMaxPFast>, cb));
+            k_box_coef<T, kMaxPFast><<<n_nl, shift_threads, cb, st>>>(nl_box, B, tab, local);
         }
         ++launches;
     }
@@ -1076,10 +1252,10 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
         else CKS(run_pair(st));
         if (plan->timing) cudaEventRecord(plan->ev[10], st);
         switch (P.kernel) {
-            case DMK_LAPLACE: CKS((gr ? launch_leafexp<T, DMK_LAPLACE, true> : launch_leafexp<T, DMK_LAPLACE, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo)); break;
-            case DMK_STOKESLET: CKS((gr ? launch_leafexp<T, DMK_STOKESLET, true> : launch_leafexp<T, DMK_STOKESLET, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo)); break;
-            case DMK_STRESSLET: CKS((gr ? launch_leafexp<T, DMK_STRESSLET, true> : launch_leafexp<T, DMK_STRESSLET, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo)); break;
-            default: CKS((gr ? launch_leafexp<T, DMK_ROTLET, true> : launch_leafexp<T, DMK_ROTLET, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo)); break;
+            case DMK_LAPLACE: CKS((gr ? launch_leafexp<T, DMK_LAPLACE, true> : launch_leafexp<T, DMK_LAPLACE, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo, direct_leaf ? 1 : 0, n_nl, nl_box, Mtot)); break;
+            case DMK_STOKESLET: CKS((gr ? launch_leafexp<T, DMK_STOKESLET, true> : launch_leafexp<T, DMK_STOKESLET, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo, direct_leaf ? 1 : 0, n_nl, nl_box, Mtot)); break;
+            case DMK_STRESSLET: CKS((gr ? launch_leafexp<T, DMK_STRESSLET, true> : launch_leafexp<T, DMK_STRESSLET, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo, direct_leaf ? 1 : 0, n_nl, nl_box, Mtot)); break;
+            default: CKS((gr ? launch_leafexp<T, DMK_ROTLET, true> : launch_leafexp<T, DMK_ROTLET, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo, direct_leaf ? 1 : 0, n_nl, nl_box, Mtot)); break;
         }
         ++launches;
     } else if (nleaf > 0) {
@@ -1102,7 +1278,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N, const double* pt
     std::memcpy(hs, plan->h_meta + 256, 2 * drho * sizeof(double));
     if (herr & kErrNonFinite) { plan->err = "non-finite coordinate"; return DMK_ERR_OUT_OF_DOMAIN; }
     if (herr & kErrDomain) { plan->err = "a free coordinate lies outside [0, L_i)"; return DMK_ERR_OUT_OF_DOMAIN; }
-    if (!plan->allow_charged && P.kernel == DMK_LAPLACE && (P.D == 1 || P.D == 2) &&
+    if (!plan->allow_charged && !sh && P.kernel == DMK_LAPLACE && (P.D == 1 || P.D == 2) &&
         std::fabs(hs[0]) > 1e-12 * std::max(hs[1], 1e-300)) {
         plan->err = "Laplace with D = 1, 2 requires zero net charge";
         return DMK_ERR_NOT_NEUTRAL;
@@ -1158,6 +1334,11 @@ dmk_status_t make_plan(int k, int D, const double L[3], double tol, int prec, in
     }
     plan->geo.s = plan->T.s;
     plan->geo.D = D;
+    for (int i = 0; i < 3; ++i) {
+        plan->geo.wrap[i] = plan->T.wrap[i];
+        plan->geo.origin[i] = plan->T.origin[i];
+        plan->geo.padded[i] = plan->T.padded[i];
+    }
     cudaError_t e = cudaGetDevice(&plan->device);
     if (e != cudaSuccess) { g_plan_error = std::string("no CUDA device: ") + cudaGetErrorString(e); delete plan; return DMK_ERR_CUDA; }
     int optin = 0;
@@ -1169,6 +1350,22 @@ dmk_status_t make_plan(int k, int D, const double L[3], double tol, int prec, in
         g_plan_error = plan->err;
         dmk_destroy(plan);
         return s;
+    }
+    if (plan->T.padded[0] || plan->T.padded[1] || plan->T.padded[2]) {
+        std::vector<int> cv(plan->T.cube_class);
+        std::vector<int> cut;
+        for (size_t m = 0; m < cv.size(); ++m)
+            if (cv[m] == 1) cut.push_back((int)m);
+        cv.push_back((int)cut.size());
+        cv.insert(cv.end(), cut.begin(), cut.end());
+        e = cudaMalloc((void**)&plan->d_cube, cv.size() * sizeof(int));
+        if (e != cudaSuccess) { g_plan_error = "cube table allocation failed"; dmk_destroy(plan); return DMK_ERR_OOM; }
+        ++plan->n_allocs;
+        if (cudaMemcpy(plan->d_cube, cv.data(), cv.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+            g_plan_error = "cube table upload failed";
+            dmk_destroy(plan);
+            return DMK_ERR_CUDA;
+        }
     }
     e = cudaMallocHost((void**)&plan->h_meta, 4096);
     if (e != cudaSuccess) {
@@ -1218,6 +1415,40 @@ dmk_status_t dmk_eval(dmk_plan_t plan, int64_t N, const double* points, const do
     cudaSetDevice(plan->device);
     if (plan->prec == DMK_FP64) return run_eval<double>(plan, plan->tab64, N, points, strengths, potentials, grad);
     return run_eval<float>(plan, plan->tab32, N, points, strengths, potentials, grad);
+}
+
+dmk_status_t dmk_eval_shard(dmk_plan_t plan, int64_t N, int64_t n_own, const double* points, const double* strengths,
+                            double* potentials, double* grad, const int* cube_owned, dmk_chi_reduce_fn reduce,
+                            void* ctx) {
+    if (!plan) return DMK_ERR_INVALID_ARG;
+    plan->err.clear();
+    if (N < 0 || n_own < 0 || n_own > N) { plan->err = "need 0 <= n_own <= N"; return DMK_ERR_INVALID_ARG; }
+    if (N > (int64_t)1 << 30) { plan->err = "N above 2^30"; return DMK_ERR_INVALID_ARG; }
+    if (!cube_owned || !reduce) { plan->err = "cube_owned and reduce are required"; return DMK_ERR_INVALID_ARG; }
+    if (plan->geo.padded[0] || plan->geo.padded[1] || plan->geo.padded[2]) {
+        plan->err = "dmk_eval_shard: exact tilings only";
+        return DMK_ERR_UNSUPPORTED;
+    }
+    if (N > 0 && (!points || !strengths || (n_own > 0 && !potentials))) { plan->err = "NULL array"; return DMK_ERR_INVALID_ARG; }
+    cudaSetDevice(plan->device);
+    ShardArgs sh{n_own, cube_owned, reduce, ctx};
+    if (N == 0) {
+        // nothing local, but the other ranks' reduction still needs this rank's (zero) share
+        const RootTab& rt = plan->root;
+        const bool fft = plan->T.D == 3 && plan->geo.M[0] == 1 && plan->geo.M[1] == 1 &&
+                         plan->geo.M[2] >= kRootFftMin && plan->geo.M[2] <= kRootFftMax;
+        const int Mtot = plan->geo.M[0] * plan->geo.M[1] * plan->geo.M[2];
+        const int64_t n = (int64_t)2 * (fft ? 1 : Mtot) * plan->T.d_rho * rt.nmode;
+        void* vchi;
+        CKS(ensure(plan, B_CHI, (size_t)(n + 2 * plan->T.d_rho) * sizeof(double), &vchi));
+        CK(cudaMemsetAsync(vchi, 0, (size_t)(n + 2 * plan->T.d_rho) * sizeof(double), plan->stream));
+        CKS(reduce_chi(plan, &sh, (Cx<double>*)vchi, n, (double*)vchi + n));
+        CK(cudaStreamSynchronize(plan->stream));
+        return DMK_OK;
+    }
+    if (plan->prec == DMK_FP64)
+        return run_eval<double>(plan, plan->tab64, N, points, strengths, potentials, grad, &sh);
+    return run_eval<float>(plan, plan->tab32, N, points, strengths, potentials, grad, &sh);
 }
 
 dmk_status_t dmk_eval_static(dmk_plan_t plan, int64_t N, const double* points, const double* strengths,
@@ -1338,6 +1569,7 @@ dmk_status_t dmk_destroy(dmk_plan_t plan) {
     if (plan->d_tab32) cudaFree(plan->d_tab32);
     if (plan->d_root) cudaFree(plan->d_root);
     if (plan->d_self) cudaFree(plan->d_self);
+    if (plan->d_cube) cudaFree(plan->d_cube);
     if (plan->side) {
         cudaStreamSynchronize(plan->side);
         cudaStreamDestroy(plan->side);
@@ -1348,6 +1580,7 @@ dmk_status_t dmk_destroy(dmk_plan_t plan) {
     for (int i = 0; i < 11; ++i)
         if (plan->ev[i]) cudaEventDestroy(plan->ev[i]);
     if (plan->h_meta) cudaFreeHost(plan->h_meta);
+    if (plan->h_chi) cudaFreeHost(plan->h_chi);
     delete plan;
     return DMK_OK;
 }

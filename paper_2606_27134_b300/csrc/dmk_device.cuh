@@ -42,11 +42,16 @@ __host__ __device__ __forceinline__ uint32_t compact3(uint64_t x) {
     return (uint32_t)x;
 }
 
+// Geometry of the cube tiling.  Coordinates inside the library are taken relative to the lower
+// corner of Omega_ext (origin; nonzero only on padded axes), so boxes start at 0.
 struct Geo {
-    double L[3];
-    double s;
-    int M[3];
-    int periodic[3];
+    double L[3];       // the periods (true lengths)
+    double s;          // cube side
+    int M[3];          // cubes per axis, padding included
+    int periodic[3];   // the forest wraps along the axis
+    int wrap[3];       // input coordinates are wrapped mod L along the axis (axes < D)
+    double origin[3];
+    int padded[3];
     int D;
 };
 
@@ -157,10 +162,13 @@ struct HermSeries {
     int i;
     float u;
     __device__ __forceinline__ HermSeries(const Quad<float>* tbl_, float r2, float inv_nu) : tbl(tbl_) {
-        const float x = r2 * (inv_nu * inv_nu) * (float)kHermNT;
-        const int ii = min((int)x, kHermNT - 1);
-        i = ii;
-        u = x - (float)ii;
+        const float x = r2 * (inv_nu * inv_nu) * (float)kHermNT;       // in [0, kHermNT]
+        // floor(x) without a float-to-integer conversion: with round-down, 1.5 2^23 + x keeps
+        // floor(x) in its low mantissa bits (0 <= x < 2^22); the FP32 additions are exact
+        const float big = 12582912.0f;
+        const float y = __fadd_rd(x, big);
+        i = min(__float_as_int(y) - __float_as_int(big), kHermNT - 1);
+        u = x - fminf(y - big, (float)(kHermNT - 1));
     }
     __device__ __forceinline__ float operator()(int k) const {
         const Quad<float> c = tbl[k * kHermNT + i];

@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(kLeaf2Threads) k_leaf2(int nleaf, const int* _
                         }
                         sinv[slot] = (T)inv;
                         snu2[slot] = (T)(1.0 / (inv * inv));
-                        sidx[slot] = si;
+                        sidx[slot] = out.orig[si];
                         for (int a = 0; a < DR; ++a) sr[slot][a] = (T)out.rs[(int64_t)si * DR + a];
                     }
                     filled += take;
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kLeaf2Threads) k_leaf2(int nleaf, const int* _
                         }
                         const T r2 = dx * dx + dy * dy + dz * dz;
                         // r = 0 and the target's own periodic images (|p| >= nu_0) are dropped
-                        if (r2 < snu2[k] && r2 > T(0) && sidx[k] != t0 + tt) q[cnt++][tt] = (unsigned char)k;
+                        if (r2 < snu2[k] && r2 > T(0) && sidx[k] != out.orig[t0 + tt]) q[cnt++][tt] = (unsigned char)k;
                     }
                     T acc[DU], gacc[3 * DU];
                     for (int j = 0; j < DU; ++j) acc[j] = 0;
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(kLeaf2Threads) k_leaf2(int nleaf, const int* _
             }
             __syncthreads();
             // (4) self correction and write-back (FP64)
-            if (act) {
+            if (act && out.perm[t0 + tt] < out.n_orig) {
                 const int tg = t0 + tt;
                 const int oi = out.perm[tg];
                 const double inv_nuT = 1.0 / r;
@@ -1135,7 +1135,8 @@ __device__ __forceinline__ void cheb_eval(const T* cs, int p, int ng, const T (&
 // then evaluated by every lane for its own target -- broadcast shared-memory reads, no per-lane
 // queue -- with two-float differences, the exact test 0 < r^2 < nu^2 (r = 0 is the target
 // itself, Eq. periodic_sum drops it; the target's own periodic images lie at |p| >= nu_0 and
-// are dropped by index) and the cubic residual tables.  FP32 partial sums are
+// are dropped by the index of the original point) and the cubic residual tables.  Images of a
+// non-exact tiling are sources; their own sums are not written.  FP32 partial sums are
 // folded into a two-float accumulator per block (FP64 in the FP64 path); the order of every
 // sum is fixed, so results are reproducible.  The result K * sum is written in input order.
 // The kernel needs only the tree, so it may run beside the far field on another stream.
@@ -1223,6 +1224,7 @@ __global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? (K == DMK_LA
         float ch[3], cl[3];
         for (int a = 0; a < 3; ++a) split_double(-c[a], ch[a], cl[a]);
         const int tg = B.start[box] + tk.y + ti;
+        const int tgo = out.orig[tg];                  // the original point the target is
         T xt[3], xtl[3] = {0, 0, 0};
         if constexpr (kTwo) {
             const float4 p0 = out.pk[(int64_t)tg * RQ], p1 = out.pk[(int64_t)tg * RQ + 1];
@@ -1253,25 +1255,43 @@ __global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? (K == DMK_LA
             for (int j = 0; j < DU; ++j) acc[j] = 0;
 #pragma unroll
             for (int j = 0; j < 3 * DU; ++j) gacc[j] = 0;
+            if constexpr (kTwo) {
+                // FP32: every lane evaluates the block's survivors in order (broadcast reads),
+                // predicated on its own support test
 #pragma unroll 2
-            for (int i = s; i < cnt; i += S) {
-                const int k = (head + i) & (kPairList - 1);
-                const Q4 a = sA[k], b = sB[k];
-                T dx = xt[0] - a.x, dy = xt[1] - a.y, dz = xt[2] - a.z;
-                if (kTwo) {
+                for (int i = s; i < cnt; i += S) {
+                    const int k = (head + i) & (kPairList - 1);
+                    const Q4 a = sA[k], b = sB[k];
+                    T dx = xt[0] - a.x, dy = xt[1] - a.y, dz = xt[2] - a.z;
                     dx += xtl[0] - b.x;
                     dy += xtl[1] - b.y;
                     dz += xtl[2] - b.z;
-                }
-                const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                // r = 0 (the target itself at p = 0, or a coincident point) and the target's
-                // own periodic images (|p| >= nu_0 >= nu: outside the support, however r^2
-                // rounds) are dropped
-                if (r2 > T(0) && r2 < a.w && sI[k] != tg) {
-                    if constexpr (kTwo)
+                    const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                    // r = 0 (the target itself at p = 0, or a coincident point) and the target's
+                    // own periodic images (|p| >= nu_0 >= nu: outside the support, however r^2
+                    // rounds) are dropped
+                    if (r2 > T(0) && r2 < a.w && sI[k] != tgo)
                         Pr::eval(HermSeries(herm, r2, b.w), dx, dy, dz, r2, b.w, sr[k], acc, gacc);
-                    else
-                        Pr::eval(ChebSeries<T>(tab, fits, r2, b.w), dx, dy, dz, r2, b.w, sr[k], acc, gacc);
+                }
+            } else {
+                // FP64 (a pipe 1/64 of FP32): each lane first marks its in-support survivors,
+                // then evaluates only those, so the evaluations follow the pairs in support
+                unsigned msk = 0;
+                for (int i = s, bit = 0; i < cnt; i += S, ++bit) {
+                    const int k = (head + i) & (kPairList - 1);
+                    const Q4 a = sA[k];
+                    const T dx = xt[0] - a.x, dy = xt[1] - a.y, dz = xt[2] - a.z;
+                    const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                    if (r2 > T(0) && r2 < a.w && sI[k] != tgo) msk |= 1u << bit;
+                }
+                while (msk) {
+                    const int bit = __ffs(msk) - 1;
+                    msk &= msk - 1;
+                    const int k = (head + s + bit * S) & (kPairList - 1);
+                    const Q4 a = sA[k], b = sB[k];
+                    const T dx = xt[0] - a.x, dy = xt[1] - a.y, dz = xt[2] - a.z;
+                    const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                    Pr::eval(ChebSeries<T>(tab, fits, r2, b.w), dx, dy, dz, r2, b.w, sr[k], acc, gacc);
                 }
             }
             if constexpr (kTwo) {
@@ -1339,7 +1359,7 @@ __global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? (K == DMK_LA
                     b.w = tinv;
                     sA[slot] = a;
                     sB[slot] = b;
-                    sI[slot] = si;
+                    sI[slot] = out.orig[si];
                     if constexpr (kTwo) {
                         const float4* rp = out.pk + (int64_t)si * RQ;
                         const float* rf = reinterpret_cast<const float*>(rp);
@@ -1363,8 +1383,8 @@ __global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? (K == DMK_LA
 #pragma unroll
             for (int j = 0; j < NA; ++j) accd[j] += __shfl_xor_sync(full, accd[j], o);
         }
-        if (s == 0) {
-            const int oi = out.perm[tg];
+        const int oi = out.perm[tg];
+        if (s == 0 && oi < out.n_orig) {
             const double ks = KScale<K>::v;
 #pragma unroll
             for (int j = 0; j < DU; ++j) out.pot[(int64_t)oi * DU + j] = ks * accd[j];
@@ -1388,7 +1408,8 @@ constexpr int kLeafExpThreads = 128;
 template <class T, int K, bool GRAD>
 __global__ void __launch_bounds__(kLeafExpThreads) k_leafexp(int nleaf, const int* __restrict__ leaves, BoxArrays B,
                                                             Tab<T> tab, Geo g, const T* __restrict__ coef,
-                                                            const double* __restrict__ xs, int64_t N, LeafOut out) {
+                                                            const double* __restrict__ xs, int64_t N, LeafOut out,
+                                                            int direct_leaf) {
     using Pr = Pair<T, K, GRAD>;
     constexpr int DR = Pr::DR, DU = Pr::DU, MQ = kMaxPFast / 4;
     constexpr bool kTwo = sizeof(T) == 4;
@@ -1399,8 +1420,12 @@ __global__ void __launch_bounds__(kLeafExpThreads) k_leafexp(int nleaf, const in
     for (int li = blockIdx.x; li < nleaf; li += gridDim.x) {
         const int box = leaves[li];
         const int l = B.level[box];
-        const double r = ldexp(g.s, -l), half = 0.5 * r;
-        const double c[3] = {(B.ix[3 * box] + 0.5) * r, (B.ix[3 * box + 1] + 0.5) * r, (B.ix[3 * box + 2] + 0.5) * r};
+        const double r = ldexp(g.s, -l);                 // the leaf (self term)
+        // the box whose expansion is evaluated: the leaf, or with direct_leaf its parent
+        const int eb = (direct_leaf && l > 0) ? B.parent[box] : box;
+        const int le = B.level[eb];
+        const double re = ldexp(g.s, -le), half = 0.5 * re;
+        const double c[3] = {(B.ix[3 * eb] + 0.5) * re, (B.ix[3 * eb + 1] + 0.5) * re, (B.ix[3 * eb + 2] + 0.5) * re};
         float ch[3], cl[3];
         for (int a = 0; a < 3; ++a) split_double(-c[a], ch[a], cl[a]);
         const int st = B.start[box], en = B.end[box];
@@ -1447,7 +1472,7 @@ __global__ void __launch_bounds__(kLeafExpThreads) k_leafexp(int nleaf, const in
 #pragma unroll
             for (int j = 0; j < DU; ++j) {
                 __syncthreads();
-                const T* cj = coef + ((size_t)box * DU + j) * p3;
+                const T* cj = coef + ((size_t)eb * DU + j) * p3;
                 for (int e = tt; e < p2 * PQ; e += kLeafExpThreads) {
                     const int n12 = e / PQ, n3 = e - n12 * PQ;
                     cs[e] = n3 < p ? cj[n12 * p + n3] : T(0);
@@ -1469,7 +1494,7 @@ __global__ void __launch_bounds__(kLeafExpThreads) k_leafexp(int nleaf, const in
                 eg[2 * DU + j] = Sz * sc;
             }
             // expansion + residual sums (written by k_pair), minus the self term
-            if (act) {
+            if (act && out.perm[tg] < out.n_orig) {
                 const int oi = out.perm[tg];
                 const double inv_nuT = 1.0 / r;
                 const double* rt = out.rs + (int64_t)tg * DR;
@@ -1496,6 +1521,150 @@ __global__ void __launch_bounds__(kLeafExpThreads) k_leafexp(int nleaf, const in
     }
 }
 
+// The leaf expansions with direct_leaf (Sec. 3.1.5): one work item per non-leaf box with leaf
+// children (its expansion evaluated at the targets of all those children: the same polynomial as
+// the children's shifted expansions) or per cube that is a leaf; its coefficients are staged
+// once per component for every target of the item.  Component by component, the expansion and
+// its gradient are added to the residual sums of k_pair and the self term of the target's own
+// leaf (Sec. 2.4) subtracted, in FP64.
+template <class T, int K, bool GRAD>
+__global__ void __launch_bounds__(kLeafExpThreads) k_leafexp_parent(int n_nl, const int* __restrict__ nl_box,
+                                                                   int n_root, BoxArrays B, Tab<T> tab, Geo g,
+                                                                   const T* __restrict__ coef,
+                                                                   const double* __restrict__ xs, int64_t N,
+                                                                   LeafOut out) {
+    using Pr = Pair<T, K, GRAD>;
+    constexpr int DR = Pr::DR, DU = Pr::DU, MQ = kMaxPFast / 4;
+    constexpr bool kTwo = sizeof(T) == 4;
+    constexpr int RQ = point_record_floats(DR) / 4;
+    const int p = tab.p, p2 = p * p, p3 = p2 * p, PQ = (p + 3) & ~3, ng = PQ >> 2;
+    extern __shared__ __align__(16) unsigned char dsme[];
+    T* cs = reinterpret_cast<T*>(dsme);   // one component's coefficients, rows padded to PQ
+    __shared__ int rng[8][2];
+    __shared__ int rpre[9];
+    __shared__ int nrng;
+    const int tt = threadIdx.x;
+    for (int item = blockIdx.x; item < n_nl + n_root; item += gridDim.x) {
+        int eb;
+        __syncthreads();
+        if (item < n_nl) {
+            eb = nl_box[item];
+            if (tt == 0) {
+                int k = 0;
+                const int c0 = B.child0[eb];
+                for (int o = 0; o < 8; ++o)
+                    if (B.child0[c0 + o] < 0) { rng[k][0] = B.start[c0 + o]; rng[k][1] = B.end[c0 + o]; ++k; }
+                nrng = k;
+            }
+        } else {
+            eb = item - n_nl;
+            if (tt == 0) {
+                nrng = (B.child0[eb] < 0) ? 1 : 0;
+                rng[0][0] = B.start[eb];
+                rng[0][1] = B.end[eb];
+            }
+        }
+        __syncthreads();
+        if (tt == 0) {
+            rpre[0] = 0;
+            for (int k = 0; k < nrng; ++k) rpre[k + 1] = rpre[k] + rng[k][1] - rng[k][0];
+        }
+        __syncthreads();
+        const int nr = nrng, ntot = rpre[nr];
+        if (ntot == 0) continue;                         // uniform over the block
+        const int le = B.level[eb];
+        // the targets' own leaves: the children (level le + 1), or the cube itself
+        const double rT = ldexp(g.s, -(item < n_nl ? le + 1 : le));
+        const double re = ldexp(g.s, -le), half = 0.5 * re;
+        const double c[3] = {(B.ix[3 * eb] + 0.5) * re, (B.ix[3 * eb + 1] + 0.5) * re, (B.ix[3 * eb + 2] + 0.5) * re};
+        float ch[3], cl[3];
+        for (int a = 0; a < 3; ++a) split_double(-c[a], ch[a], cl[a]);
+        const T ih = (T)(1.0 / half);
+        for (int j = 0; j < DU; ++j) {
+            __syncthreads();
+            const T* cj = coef + ((size_t)eb * DU + j) * p3;
+            for (int e = tt; e < p2 * PQ; e += kLeafExpThreads) {
+                const int n12 = e / PQ, n3 = e - n12 * PQ;
+                cs[e] = n3 < p ? cj[n12 * p + n3] : T(0);
+            }
+            __syncthreads();
+            for (int v0 = 0; v0 < ntot; v0 += kLeafExpThreads) {
+                const int v = v0 + tt;
+                const bool act = v < ntot;
+                int tg = 0;
+                if (act) {
+                    int k = 0;
+                    while (rpre[k + 1] <= v) ++k;
+                    tg = rng[k][0] + (v - rpre[k]);
+                }
+                T xi[3] = {0, 0, 0};
+                if (act) {
+                    float4 p0 = make_float4(0, 0, 0, 0), p1 = p0;
+                    if constexpr (kTwo) {
+                        p0 = out.pk[(int64_t)tg * RQ];
+                        p1 = out.pk[(int64_t)tg * RQ + 1];
+                    }
+                    const float ph[3] = {p0.x, p0.y, p0.z}, pl[3] = {p1.x, p1.y, p1.z};
+                    for (int a = 0; a < 3; ++a) {
+                        T x0, x1 = 0;
+                        if constexpr (kTwo) two_float_add(ph[a], pl[a], ch[a], cl[a], x0, x1);
+                        else x0 = (T)(xs[a * N + tg] - c[a]);
+                        const T w = (x0 + x1) * ih;
+                        xi[a] = w > T(1) ? T(1) : (w < T(-1) ? T(-1) : w);
+                    }
+                }
+                T Tz[kMaxPFast], dTz[kMaxPFast];
+                {
+                    T tm2 = 0, tm1 = 1, um2 = 0, um1 = 1;
+#pragma unroll
+                    for (int n = 0; n < kMaxPFast; ++n) {
+                        T tn, dn;
+                        if (n == 0) { tn = 1; dn = 0; }
+                        else if (n == 1) { tn = xi[2]; dn = 1; tm2 = 1; tm1 = xi[2]; um2 = 1; um1 = 2 * xi[2]; }
+                        else {
+                            tn = 2 * xi[2] * tm1 - tm2;
+                            dn = (T)n * um1;
+                            const T un = 2 * xi[2] * um1 - um2;
+                            tm2 = tm1; tm1 = tn; um2 = um1; um1 = un;
+                        }
+                        Tz[n] = n < p ? tn : T(0);
+                        dTz[n] = n < p ? dn : T(0);
+                    }
+                }
+                T S = 0, Sx = 0, Sy = 0, Sz = 0;
+                if (act) {
+                    if (ng == 5)
+                        cheb_eval<T, 5, false, GRAD>(cs, p, ng, Tz, dTz, xi, S, Sx, Sy, Sz);
+                    else if (ng == 6)
+                        cheb_eval<T, 6, false, GRAD>(cs, p, ng, Tz, dTz, xi, S, Sx, Sy, Sz);
+                    else
+                        cheb_eval<T, MQ, true, GRAD>(cs, p, ng, Tz, dTz, xi, S, Sx, Sy, Sz);
+                }
+                if (act && out.perm[tg] < out.n_orig) {
+                    const int oi = out.perm[tg];
+                    const double inv_nuT = 1.0 / rT;
+                    const double* rt = out.rs + (int64_t)tg * DR;
+                    double vv = (double)S + out.pot[(int64_t)oi * DU + j];
+                    for (int a = 0; a < DR; ++a) vv -= out.self_val[j * DR + a] * inv_nuT * rt[a];
+                    out.pot[(int64_t)oi * DU + j] = vv;
+                    if (GRAD && out.grad) {
+                        const double in3 = inv_nuT * inv_nuT * inv_nuT;
+                        const double sc = 1.0 / half;
+                        const T gs[3] = {Sx, Sy, Sz};
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            const int64_t o = ((int64_t)oi * 3 + i) * DU + j;
+                            double gv = (double)(gs[i] * (T)sc) + out.grad[o];
+                            for (int a = 0; a < DR; ++a) gv -= out.self_grad[(i * DU + j) * DR + a] * in3 * rt[a];
+                            out.grad[o] = gv;
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
 template <class T>
 inline size_t leafexp_smem(int p) {
     const int PQ = (p + 3) & ~3;
@@ -1512,14 +1681,24 @@ namespace dmk {
 // charges (three fiber contractions in shared memory), then the eight CTAs reduce the eight
 // contributions through distributed shared memory in the fixed order o = 0..7, each CTA
 // writing one eighth of the parent's tensor.
+//   With direct_leaf (the leaf sources already anterpolated onto the parent grid, k_anterp3),
+// leaf children contribute nothing here: a parent with only leaf children is skipped, and the
+// non-leaf children's sum is added to the proxy when the parent has leaf children (stored
+// otherwise).
 template <class T, int MAXP>
 __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__((MAXP * MAXP / 2 + 31) / 32 * 32, sizeof(T) == 4 ? 2 : 1)
-    k_up_cluster(const int* __restrict__ nl_box, BoxArrays B, Tab<T> tab, T* __restrict__ proxy) {
+    k_up_cluster(const int* __restrict__ nl_box, BoxArrays B, Tab<T> tab, T* __restrict__ proxy, int direct_leaf) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     const int o = (int)cl.block_rank();
     const int bi = blockIdx.x >> 3;
     const int p = tab.p, p2 = p * p, p3 = p2 * p, P = odd_pitch(p), drho = tab.d_rho;
+    const int Pb0 = nl_box[bi], c00 = B.child0[Pb0];
+    int n_leafc = 0;
+    for (int q = 0; q < 8; ++q) n_leafc += B.child0[c00 + q] < 0;
+    if (direct_leaf && n_leafc == 8) return;      // the same for every CTA of the cluster
+    const bool skip_mine = direct_leaf && B.child0[c00 + o] < 0;
+    const bool add = direct_leaf && n_leafc > 0;
     T* Mo = reinterpret_cast<T*>(dsmem);                 // 3 x MAXP x MAXP, one per axis
     T* bufA = Mo + 3 * MAXP * MAXP;
     T* bufB = bufA + p * p * P;
@@ -1537,6 +1716,20 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__((MAXP * MAXP / 2 + 3
     const int C = B.child0[Pb] + o;
     const int lo = (o * p3) >> 3, hi = ((o + 1) * p3) >> 3;
     for (int a = 0; a < drho; ++a) {
+        if (skip_mine) {
+            // a leaf child: its sources are already in the parent's proxy
+            for (int e = threadIdx.x; e < p3; e += blockDim.x) bufB[e] = T(0);
+            cl.sync();
+            T* out = proxy + ((size_t)Pb * drho + a) * p3;
+            for (int e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+                T sum = 0;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) sum += cl.map_shared_rank(bufB, r)[e];
+                out[e] = add ? out[e] + sum : sum;
+            }
+            cl.sync();
+            continue;
+        }
         __syncthreads();
         load_padded_batched<T, MAXP>(bufA, proxy + ((size_t)C * drho + a) * p3, p, P);
         __syncthreads();
@@ -1569,7 +1762,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__((MAXP * MAXP / 2 + 3
             T sum = 0;
 #pragma unroll
             for (int r = 0; r < 8; ++r) sum += cl.map_shared_rank(bufB, r)[e];
-            out[e] = sum;
+            out[e] = add ? out[e] + sum : sum;
         }
         cl.sync();
     }
@@ -1578,9 +1771,11 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__((MAXP * MAXP / 2 + 3
 // Shift to children (Sec. 3.1.4), one CTA per (parent, child octant): non-leaf child
 // local += (I_o x I_o x I_o) parent; leaf child local += (A_o x A_o x A_o) parent, A_o = C I_o,
 // the Chebyshev coefficients of the child's interpolant.
+//   With direct_leaf the leaf children are skipped: their targets evaluate the parent's
+// expansion (k_box_coef, k_leafexp), the same polynomial.
 template <class T, int MAXP>
 __global__ void __launch_bounds__((MAXP * MAXP + 31) / 32 * 32, sizeof(T) == 4 ? 2 : 1) k_shift_child(const int* __restrict__ nl_box, BoxArrays B, Tab<T> tab,
-                                                     T* __restrict__ local) {
+                                                     T* __restrict__ local, int direct_leaf) {
     const int o = blockIdx.x & 7;
     const int bi = blockIdx.x >> 3;
     const int p = tab.p, p2 = p * p, p3 = p2 * p, P = odd_pitch(p), du = tab.d_u;
@@ -1590,6 +1785,7 @@ __global__ void __launch_bounds__((MAXP * MAXP + 31) / 32 * 32, sizeof(T) == 4 ?
     const int Pb = nl_box[bi];
     const int C = B.child0[Pb] + o;
     const bool leaf_child = B.child0[C] < 0;
+    if (direct_leaf && leaf_child) return;
     const T* src = leaf_child ? tab.Aoct : tab.Ioct;
     for (int ax = 0; ax < 3; ++ax) {
         const int bit = (o >> ax) & 1;
@@ -1629,4 +1825,47 @@ __global__ void __launch_bounds__((MAXP * MAXP + 31) / 32 * 32, sizeof(T) == 4 ?
     }
 }
 
+
+// Grid values -> Chebyshev coefficients in place (c = (C x C x C) u, Sec. 3.1.5), one CTA per
+// non-leaf box that has a leaf child: those children's targets evaluate the parent's expansion.
+template <class T, int MAXP>
+__global__ void __launch_bounds__((MAXP * MAXP + 31) / 32 * 32, sizeof(T) == 4 ? 2 : 1)
+    k_box_coef(const int* __restrict__ nl_box, BoxArrays B, Tab<T> tab, T* __restrict__ local) {
+    const int p = tab.p, p2 = p * p, p3 = p2 * p, P = odd_pitch(p), du = tab.d_u;
+    const int Pb = nl_box[blockIdx.x];
+    const int c0 = B.child0[Pb];
+    bool any_leaf = false;
+    for (int q = 0; q < 8; ++q) any_leaf = any_leaf || B.child0[c0 + q] < 0;
+    if (!any_leaf) return;
+    T* Mo = reinterpret_cast<T*>(dsmem);                 // MAXP x MAXP: Mo[k][n] = C[n][k]
+    T* bufA = Mo + MAXP * MAXP;
+    T* bufB = bufA + p * p * P;
+    load_op<T, MAXP>(Mo, p, [&](int k, int j) { return tab.Cm[j * p + k]; });
+    const int f = threadIdx.x;
+    const bool own = f < p2;
+    const int fa = own ? f / p : 0, fb = own ? f % p : 0;
+    for (int j = 0; j < du; ++j) {
+        T* u = local + ((size_t)Pb * du + j) * p3;
+        __syncthreads();
+        load_padded_batched<T, MAXP>(bufA, u, p, P);
+        __syncthreads();
+        T t[MAXP];
+        if (own) {
+            fiber_contract<T, MAXP>(bufA, p, P, 2, fa, fb, Mo, t);
+            fiber_store<T, MAXP>(bufB, p, P, 2, fa, fb, t);
+        }
+        __syncthreads();
+        if (own) {
+            fiber_contract<T, MAXP>(bufB, p, P, 1, fa, fb, Mo, t);
+            fiber_store<T, MAXP>(bufA, p, P, 1, fa, fb, t);
+        }
+        __syncthreads();
+        if (own) {
+            fiber_contract<T, MAXP>(bufA, p, P, 0, fa, fb, Mo, t);
+#pragma unroll
+            for (int jj = 0; jj < MAXP; ++jj)
+                if (jj < p) u[(jj * p + fa) * p + fb] = t[jj];
+        }
+    }
+}
 }  // namespace dmk

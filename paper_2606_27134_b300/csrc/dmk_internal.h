@@ -17,8 +17,13 @@ struct PlanTables {
     int kernel = 0, D = 3, d_rho = 1, d_u = 1;
     double L[3] = {1, 1, 1};
     double s = 1;                   // cube side = nu_0 (Sec. 4.1.1; nu_0 reading)
-    int M[3] = {1, 1, 1};           // cubes per axis
-    int periodic[3] = {1, 1, 1};
+    int M[3] = {1, 1, 1};           // cubes per axis (padding included)
+    int periodic[3] = {1, 1, 1};    // the forest wraps along the axis (exactly tiled periodic axes)
+    int wrap[3] = {1, 1, 1};        // the sum is periodic along the axis (axes 0..D-1)
+    int padded[3] = {0, 0, 0};      // periodic but not exactly tiled: cut cubes + one padding cube
+                                    // each side, images of the sources added (Sec. 4.1.1-4.1.2)
+    double origin[3] = {0, 0, 0};   // lower corner of Omega_ext (-s on padded axes)
+    std::vector<int> cube_class;    // per cube: 0 inside Omega, 1 cut, 2 outside (padding)
     double c = 0;                   // PSWF band limit
     int p = 0, nf = 0, NF = 0, nfh = 0;   // Chebyshev order, n_f, N_F = 2 n_f + 1, n_f + 1
     int level_power = 1;            // difference-kernel symbol scales as 2^(level_power * l)

@@ -67,7 +67,8 @@ __global__ void __launch_bounds__(MAXP <= 24 ? (MAXP * MAXP + 31) / 32 * 32 : 51
     k_anterp(const int* __restrict__ nleaf_dev, const int* __restrict__ leaves, BoxArrays B,
                                                  const double* __restrict__ xs, int64_t N,
                                                  const double* __restrict__ rs, Tab<T> tab, double s,
-                                                 T* __restrict__ proxy) {
+                                                 T* __restrict__ proxy, const int* __restrict__ perm,
+                                                 int64_t n_orig) {
     static_assert(MAXP % 4 == 0, "rows are read as four-vectors");
     const int p = tab.p, p2 = p * p, drho = tab.d_rho;
     constexpr int PC = kAnterpChunk;
@@ -96,7 +97,9 @@ __global__ void __launch_bounds__(MAXP <= 24 ? (MAXP * MAXP + 31) / 32 * 32 : 51
                         const int ax = u / ns, pt = u - ax * ns;
                         const double xi = (xs[ax * N + s0 + pt] - c[ax]) / half;
                         T* row = (ax == 0 ? lx : (ax == 1 ? ly : lz)) + pt * MAXP;
-                        const T wgt = (ax == 0) ? (T)rs[(int64_t)(s0 + pt) * drho + a] : T(1);
+                        // with perm: only the points perm < n_orig (the sources inside Omega)
+                        const bool use = !perm || perm[s0 + pt] < n_orig;
+                        const T wgt = (ax == 0) ? (use ? (T)rs[(int64_t)(s0 + pt) * drho + a] : T(0)) : T(1);
                         lagrange_row_padded<T>((T)xi, tab.nodes, tab.bary, p, MAXP, wgt, row);
                     }
                     __syncthreads();
@@ -202,123 +205,167 @@ __global__ void __launch_bounds__((MAXP / 2 * MAXP + 31) / 32 * 32, sizeof(T) ==
     }
 }
 
-// Leaf anterpolation as a register-tiled product (FP32 path):
-//   proxy[(a, j1)][(j2, j3)] = sum_s X[s][(a, j1)] l_j2(eta_s) l_j3(zeta_s),
-//   X[s][(a, j1)] = rho_{s,a} l_j1(xi_s),
-// with M = d_rho p rows (a, j1) and p^2 columns (j2, j3).  The Lagrange rows of all sources of
-// the leaf are computed once (barycentric form) and kept in shared memory, for every strength
-// component; each thread owns a tile of 4 rows x TN consecutive j3 at one j2 (TN = p / 2 rounded
-// up to the vector width), reads per source the 4 X values, one eta value and TN zeta values,
-// and does 4 + 4 TN multiply-adds.  Tiles beyond the block's threads are taken in passes; X is
-// formed per chunk of kAntChunk sources.  Sources in super-chunks of kAntRows.
+// Anterpolation as a register-tiled product (FP32 path), onto the grid of the box that needs a
+// proxy: proxy_P[a][j1][(j2, j3)] = sum_s rho_{s,a} l_j1(xi_s) l_j2(eta_s) l_j3(zeta_s), xi the
+// coordinates relative to P.  Only non-leaf boxes (plane waves, upward pass) and the cubes
+// (structure factor) use proxies, so the sources of a leaf are anterpolated straight onto the
+// grid of its parent: by the interpolation identity sum_j l^C_j(x) l^P_a(y^C_j) = l^P_a(x)
+// (degree p - 1 reproduced at the child's p nodes) this equals the leaf proxy followed by the
+// child-to-parent interpolation of Sec. 3.1.2 and spares that interpolation.  Work item: a
+// non-leaf box with at least one leaf child (the sources of its leaf children), or a cube that
+// is a leaf (its own sources); k_up_cluster adds the non-leaf children afterwards.
+//   The Lagrange rows of up to kAntRows sources (gathered over the leaf children) are computed
+// once and kept in shared memory with the strengths, for every component; each thread owns a
+// tile of 4 consecutive j1 x every j3 (TN = MAXP, zero rows beyond p) at one (a, j2) and per
+// source forms w = rho_a l_j2 l_j1[4] (5 multiplies) and does 4 TN multiply-adds from 3 + TN/4
+// shared-memory reads.  Tiles beyond the block's threads are taken in passes over the same rows.
 constexpr int kAntRows = 256;      // sources whose Lagrange rows are held at once
-constexpr int kAntChunk = 32;      // sources per X chunk
 constexpr int kAntThreads = 256;
 
-template <int MAXP, int TN>
+template <int MAXP>
 struct AntSmem {
     static constexpr size_t lx = 0;                                         // float [kAntRows][MAXP]
     static constexpr size_t ly = lx + (size_t)kAntRows * MAXP * 4;
     static constexpr size_t lz = ly + (size_t)kAntRows * MAXP * 4;
     static constexpr size_t rho = lz + (size_t)kAntRows * MAXP * 4;       // float [kAntRows][9]
-    static constexpr size_t X = rho + (size_t)kAntRows * 9 * 4;            // float [kAntChunk][XM]
+    static constexpr size_t bytes = rho + (size_t)kAntRows * 9 * 4;
 };
 
+//   With leaf_list (few parents: too few work items for the GPU), the items are the leaves
+// themselves, each anterpolated onto its own grid, and the upward pass then takes every child.
 template <int MAXP, int TN>
 __global__ void __launch_bounds__(kAntThreads, 2)
-    k_anterp3(const int* __restrict__ nleaf_dev, const int* __restrict__ leaves, BoxArrays B,
-              const double* __restrict__ xs, int64_t N, const double* __restrict__ rs, Tab<float> tab, double s,
-              float* __restrict__ proxy, int XM) {
-    static_assert(MAXP % 4 == 0 && TN % 2 == 0, "vector reads");
-    using S = AntSmem<MAXP, TN>;
+    k_anterp3(int n_nl, const int* __restrict__ nl_box, int n_root, BoxArrays B, const double* __restrict__ xs,
+              int64_t N, const double* __restrict__ rs, Tab<float> tab, double s, float* __restrict__ proxy,
+              const int* __restrict__ leaf_list, const int* __restrict__ nleaf_dev) {
+    static_assert(MAXP % 4 == 0 && TN % 4 == 0 && TN <= MAXP, "vector reads");
+    using S = AntSmem<MAXP>;
     const int p = tab.p, p2 = p * p, p3 = p2 * p, drho = tab.d_rho;
-    const int M = drho * p, Mt = (M + 3) / 4, ng = (p + TN - 1) / TN, ntile = Mt * p * ng;
+    const int nj = (p + 3) / 4, ng = (p + TN - 1) / TN, ntile = drho * nj * p * ng;
     float* lx = reinterpret_cast<float*>(dsmem + S::lx);
     float* ly = reinterpret_cast<float*>(dsmem + S::ly);
     float* lz = reinterpret_cast<float*>(dsmem + S::lz);
     float* rh = reinterpret_cast<float*>(dsmem + S::rho);
-    float* X = reinterpret_cast<float*>(dsmem + S::X);                       // [kAntChunk][XM], XM >= 4 Mt
-    const int nleaf = *nleaf_dev;
-    for (int li = blockIdx.x; li < nleaf; li += gridDim.x) {
-        const int box = leaves[li];
+    __shared__ int rng[8][2];
+    __shared__ int nrng;
+    const int n_items = leaf_list ? *nleaf_dev : n_nl + n_root;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        int box;
+        __syncthreads();
+        if (leaf_list) {
+            box = leaf_list[item];
+            if (threadIdx.x == 0) {
+                nrng = 1;
+                rng[0][0] = B.start[box];
+                rng[0][1] = B.end[box];
+            }
+        } else if (item < n_nl) {
+            box = nl_box[item];
+            if (threadIdx.x == 0) {
+                int k = 0;
+                const int c0 = B.child0[box];
+                for (int o = 0; o < 8; ++o)
+                    if (B.child0[c0 + o] < 0) { rng[k][0] = B.start[c0 + o]; rng[k][1] = B.end[c0 + o]; ++k; }
+                nrng = k;
+            }
+        } else {
+            box = item - n_nl;                     // cube index = box index at level 0
+            if (threadIdx.x == 0) {
+                nrng = (B.child0[box] < 0) ? 1 : 0;
+                rng[0][0] = B.start[box];
+                rng[0][1] = B.end[box];
+            }
+        }
+        __syncthreads();
+        const int nr = nrng;
+        if (nr == 0) continue;                     // uniform over the block
         const int l = B.level[box];
         const double r = s / (double)(1 << l), half = 0.5 * r;
-        const double c[3] = {(B.ix[3 * box] + 0.5) * r, (B.ix[3 * box + 1] + 0.5) * r, (B.ix[3 * box + 2] + 0.5) * r};
-        const int st = B.start[box], en = B.end[box];
+        const double cx = (B.ix[3 * box] + 0.5) * r, cy = (B.ix[3 * box + 1] + 0.5) * r,
+                     cz = (B.ix[3 * box + 2] + 0.5) * r;
         float* outb = proxy + (size_t)box * drho * p3;
-        for (int s0 = st; s0 < en; s0 += kAntRows) {
-            const int ns = min(kAntRows, en - s0);
-            const bool first = s0 == st;
+        // the sources of the ranges in super-chunks of kAntRows (cursor: range ri, position pos)
+        int ri = 0, pos = rng[0][0];
+        bool first = true;
+        while (true) {
+            // gather the next super-chunk's point indices (uniform cursor logic)
+            int ns = 0;
+            int cr = ri, cp = pos;
             __syncthreads();
-            for (int u = threadIdx.x; u < 3 * ns; u += blockDim.x) {
-                const int ax = u / ns, pt = u - ax * ns;
-                const double xi = (xs[ax * N + s0 + pt] - c[ax]) / half;
-                float* row = (ax == 0 ? lx : (ax == 1 ? ly : lz)) + pt * MAXP;
-                lagrange_row_padded<float>((float)xi, tab.nodes, tab.bary, p, MAXP, 1.0f, row);
+            while (cr < nr && ns < kAntRows) {
+                const int take = min(kAntRows - ns, rng[cr][1] - cp);
+                for (int u = threadIdx.x; u < 3 * take; u += blockDim.x) {
+                    const int ax = u / take, pt = u - ax * take;
+                    const double c = ax == 0 ? cx : (ax == 1 ? cy : cz);
+                    const double xi = (xs[ax * N + cp + pt] - c) / half;
+                    float* row = (ax == 0 ? lx : (ax == 1 ? ly : lz)) + (ns + pt) * MAXP;
+                    lagrange_row_padded<float>((float)xi, tab.nodes, tab.bary, p, MAXP, 1.0f, row);
+                }
+                for (int u = threadIdx.x; u < take * drho; u += blockDim.x)
+                    rh[ns * drho + u] = (float)rs[(int64_t)cp * drho + u];
+                ns += take;
+                cp += take;
+                if (cp >= rng[cr][1]) {
+                    ++cr;
+                    if (cr < nr) cp = rng[cr][0];
+                }
             }
-            for (int u = threadIdx.x; u < ns * drho; u += blockDim.x) rh[u] = (float)rs[(int64_t)s0 * drho + u];
-            for (int pass = 0; pass * kAntThreads < ntile; ++pass) {
-                const int tile = pass * kAntThreads + threadIdx.x;
-                const bool act = tile < ntile;
-                // tile -> (row block mt, j2, column group g)
-                const int mt = act ? tile / (p * ng) : 0, rem = act ? tile % (p * ng) : 0;
-                const int j2 = rem / ng, j30 = (rem % ng) * TN;
+            ri = cr;
+            pos = cp;
+            __syncthreads();
+            for (int tile = threadIdx.x; tile < ntile; tile += blockDim.x) {
+                // tile -> (component a, row block jt, j2, column group g)
+                const int g = tile % ng, r1 = tile / ng;
+                const int j2 = r1 % p, r2 = r1 / p;
+                const int jt = r2 % nj, a = r2 / nj;
+                const int j30 = g * TN;
                 float acc[4][TN];
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
                     for (int q = 0; q < TN; ++q) acc[i][q] = 0.f;
-                for (int k0 = 0; k0 < ns; k0 += kAntChunk) {
-                    const int nk = min(kAntChunk, ns - k0);
-                    __syncthreads();
-                    for (int u = threadIdx.x; u < nk * XM; u += blockDim.x) {
-                        const int k = u / XM, m = u - k * XM;
-                        float v = 0.f;
-                        if (m < M) {
-                            const int a = m / p, j1 = m - a * p;
-                            v = rh[(k0 + k) * drho + a] * lx[(k0 + k) * MAXP + j1];
-                        }
-                        X[u] = v;
-                    }
-                    __syncthreads();
-                    if (act) {
-                        for (int k = 0; k < nk; ++k) {
-                            const float4 xv = *reinterpret_cast<const float4*>(X + k * XM + 4 * mt);
-                            const float yv = ly[(k0 + k) * MAXP + j2];
-                            const float w[4] = {xv.x * yv, xv.y * yv, xv.z * yv, xv.w * yv};
-                            const float2* zr = reinterpret_cast<const float2*>(lz + (k0 + k) * MAXP + j30);
+                const float* px = lx + 4 * jt;
+                const float* py = ly + j2;
+                const float* pz = lz + j30;
+                const float* pr = rh + a;
+#pragma unroll 1
+                for (int k = 0; k < ns; ++k) {
+                    const float4 xv = *reinterpret_cast<const float4*>(px + k * MAXP);
+                    const float f = pr[k * drho] * py[k * MAXP];
+                    const float w[4] = {xv.x * f, xv.y * f, xv.z * f, xv.w * f};
+                    const float4* zr = reinterpret_cast<const float4*>(pz + k * MAXP);
 #pragma unroll
-                            for (int q = 0; q < TN / 2; ++q) {
-                                const float2 zv = zr[q];
+                    for (int q = 0; q < TN / 4; ++q) {
+                        const float4 zv = zr[q];
 #pragma unroll
-                                for (int i = 0; i < 4; ++i) {
-                                    acc[i][2 * q] = fmaf(w[i], zv.x, acc[i][2 * q]);
-                                    acc[i][2 * q + 1] = fmaf(w[i], zv.y, acc[i][2 * q + 1]);
-                                }
-                            }
+                        for (int i = 0; i < 4; ++i) {
+                            acc[i][4 * q] = fmaf(w[i], zv.x, acc[i][4 * q]);
+                            acc[i][4 * q + 1] = fmaf(w[i], zv.y, acc[i][4 * q + 1]);
+                            acc[i][4 * q + 2] = fmaf(w[i], zv.z, acc[i][4 * q + 2]);
+                            acc[i][4 * q + 3] = fmaf(w[i], zv.w, acc[i][4 * q + 3]);
                         }
                     }
                 }
-                if (act) {
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int m = 4 * mt + i;
-                        if (m < M) {
-                            float* o = outb + (size_t)m * p2 + j2 * p + j30;
+                for (int i = 0; i < 4; ++i) {
+                    const int j1 = 4 * jt + i;
+                    if (j1 < p) {
+                        float* o = outb + ((size_t)a * p + j1) * p2 + j2 * p + j30;
 #pragma unroll
-                            for (int q = 0; q < TN; ++q)
-                                if (j30 + q < p) o[q] = first ? acc[i][q] : o[q] + acc[i][q];
-                        }
+                        for (int q = 0; q < TN; ++q)
+                            if (j30 + q < p) o[q] = first ? acc[i][q] : o[q] + acc[i][q];
                     }
                 }
             }
+            first = false;
+            if (ri >= nr) break;
         }
     }
 }
 
-template <int MAXP, int TN>
-inline size_t anterp3_smem(int XM) {
-    return AntSmem<MAXP, TN>::X + (size_t)kAntChunk * XM * 4;
+template <int MAXP>
+inline size_t anterp3_smem() {
+    return AntSmem<MAXP>::bytes;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -819,6 +866,18 @@ __global__ void k_root_bwd3(int jobs, int du, int p, RootTab rt, const Cx<double
     local[(size_t)job * p3 + e] = (T)(v + cst);
 }
 
+// Root proxies entering the structure factor of a non-exact tiling (Sec. 4.3): the cube's own
+// proxy for a cube inside Omega (class 0), nothing for a padding cube (class 2); cut cubes
+// (class 1) are filled afterwards from their original sources by k_anterp.
+template <class T>
+__global__ void k_chi_proxy(int Mtot, int drho, int p3, const int* __restrict__ cls, const T* __restrict__ proxy,
+                            T* __restrict__ chip) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)Mtot * drho * p3) return;
+    const int cube = (int)(t / ((int64_t)drho * p3));
+    chip[t] = cls[cube] == 0 ? proxy[t] : T(0);
+}
+
 // ---- root far field for cubes stacked along a periodic x3 (Sec. 3.4 "Case 1: elongated
 // cuboid", Eqs. beta_def, 1d-DFT-beta, structfac-case1-wDFTCoeffs, ufar_inverse_fft) ----------
 // With M3 cubes of side s along x3 and k3 = 2 pi n3 / (M3 s), the cube phase exp(-i k . c_m) is
@@ -1126,7 +1185,9 @@ template <int K> struct KScale { static constexpr double v = (K == DMK_LAPLACE) 
 struct LeafOut {
     double* pot;
     double* grad;      // may be null
-    const int* perm;
+    const int* perm;   // sorted point -> input point (images of a non-exact tiling: >= n_orig)
+    const int* orig;   // sorted point -> the original point it is (or is an image of)
+    int64_t n_orig;    // points with outputs: perm < n_orig
     const double* rs;  // sorted strengths (FP64)
     const double* self_val;   // du x drho at nu = 1
     const double* self_grad;  // 3 x du x drho at nu = 1

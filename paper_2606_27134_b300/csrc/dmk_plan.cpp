@@ -319,18 +319,28 @@ dmk_status_t build_plan_tables(int kernel, int D, const double Lin[3], double to
     if (D > 0) { s = Lin[0]; for (int i = 1; i < D; ++i) s = std::min(s, Lin[i]); }
     else s = std::max(Lin[0], std::max(Lin[1], Lin[2]));
     T.s = s;
+    // A periodic axis that s does not divide is tiled by ceil(L_i / s) cubes (the last one cut)
+    // plus one padding cube on each side; the forest does not wrap along it, and the images of
+    // the sources inside Omega_ext are added as sources (Sec. 4.1.1, 4.1.2).
     double Lext[3];
     for (int i = 0; i < 3; ++i) {
         double ratio = Lin[i] / s;
+        T.wrap[i] = i < D;
+        T.padded[i] = 0;
+        T.origin[i] = 0.0;
         if (i < D) {
             int m = (int)std::llround(ratio);
-            if (std::fabs(ratio - m) > 1e-12 * std::max(1.0, ratio)) {
-                err = "periodic length is not an integer multiple of the shortest periodic length";
-                return DMK_ERR_UNSUPPORTED;
+            if (std::fabs(ratio - m) <= 1e-12 * std::max(1.0, ratio)) {
+                T.M[i] = m;
+                Lext[i] = Lin[i];
+                T.periodic[i] = 1;
+            } else {
+                T.M[i] = ceil_guard(ratio) + 2;
+                Lext[i] = T.M[i] * s;
+                T.periodic[i] = 0;
+                T.padded[i] = 1;
+                T.origin[i] = -s;
             }
-            T.M[i] = m;
-            Lext[i] = Lin[i];
-            T.periodic[i] = 1;
         } else {
             T.M[i] = std::max(1, ceil_guard(ratio));
             Lext[i] = T.M[i] * s;
@@ -339,6 +349,21 @@ dmk_status_t build_plan_tables(int kernel, int D, const double Lin[3], double to
     }
     long long mtot = (long long)T.M[0] * T.M[1] * T.M[2];
     if (mtot > 1024) { err = "more than 1024 cubes in the tiling"; return DMK_ERR_UNSUPPORTED; }
+    // cubes inside Omega, cut by its boundary, or outside it (padding), along the padded axes
+    T.cube_class.assign((size_t)mtot, 0);
+    for (int m2 = 0; m2 < T.M[2]; ++m2)
+        for (int m1 = 0; m1 < T.M[1]; ++m1)
+            for (int m0 = 0; m0 < T.M[0]; ++m0) {
+                const int mi[3] = {m0, m1, m2};
+                bool inside = true, outside = false;
+                for (int i = 0; i < 3; ++i) {
+                    if (!T.padded[i]) continue;
+                    const double lo = T.origin[i] + mi[i] * s;
+                    if (lo >= Lin[i] || lo + s <= 0.0) outside = true;
+                    if (lo < 0.0 || lo + s > Lin[i]) inside = false;
+                }
+                T.cube_class[(size_t)(m2 * T.M[1] + m1) * T.M[0] + m0] = outside ? 2 : (inside ? 0 : 1);
+            }
     T.c = kRows[kernel][row].c;
     T.p = kRows[kernel][row].p;
     T.nf = ceil_guard(3.0 * T.c / kPi) - 1;        // Sec. 6.1

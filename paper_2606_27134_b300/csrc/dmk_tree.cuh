@@ -10,39 +10,125 @@ constexpr int kErrDomain = 1;
 constexpr int kErrNonFinite = 2;
 constexpr int kErrIndex = 4;
 
+// Integer coordinate of a (wrapped) coordinate v on axis a: floor(((v - origin) / s) 2^18),
+// clamped to the tiled axis, with explicitly rounded FP64 operations (the same sequence as the
+// oracle's quantisation).
+__device__ __forceinline__ int quantize_axis(const Geo& g, int a, double v) {
+    const double scale = (double)(1u << kBits);
+    const double t = floor(__dmul_rn(__ddiv_rn(__dsub_rn(v, g.origin[a]), g.s), scale));
+    long long gi = (long long)t;
+    const long long hi = ((long long)g.M[a] << kBits) - 1;
+    gi = gi < 0 ? 0 : (gi > hi ? hi : gi);
+    return (int)gi;
+}
+
 // Wrap periodic coordinates, quantise, and form the 64-bit key (cube << 54 | Morton of the
-// 18-bit in-cube coordinates).  The arithmetic uses explicitly rounded FP64 operations so
-// that the integer coordinates are exactly floor((w / s) * 2^18):
+// 18-bit in-cube coordinates):
 //   periodic: w = x - L floor(x / L); w >= L -> w - L; w < 0 -> 0.   free: w = x in [0, L).
-__global__ void k_quantize(int64_t N, const double* __restrict__ pts, Geo g, double* __restrict__ w,
+// w (SoA, stride ws) keeps the wrapped coordinate itself; the origin enters the key only.
+__device__ __forceinline__ double wrap_coord(const Geo& g, int a, double x, int* err) {
+    const double L = g.L[a];
+    double v;
+    if (!isfinite(x)) {
+        if (err) atomicOr(err, kErrNonFinite);
+        x = 0.0;
+    }
+    if (g.wrap[a]) {
+        const double f = floor(__ddiv_rn(x, L));
+        v = __dsub_rn(x, __dmul_rn(L, f));
+        if (v >= L) v = __dsub_rn(v, L);
+        if (v < 0.0) v = 0.0;
+    } else {
+        v = x;
+        if (!(v >= 0.0 && v < L)) {
+            if (err) atomicOr(err, kErrDomain);
+            v = 0.0;
+        }
+    }
+    return v;
+}
+
+__global__ void k_quantize(int64_t N, const double* __restrict__ pts, Geo g, double* __restrict__ w, int64_t ws,
                            uint64_t* __restrict__ keys, int* __restrict__ idx, int* __restrict__ err) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
     int G[3];
-    const double scale = (double)(1u << kBits);
     for (int a = 0; a < 3; ++a) {
-        double x = pts[3 * i + a];
-        double L = g.L[a];
-        double v;
-        if (!isfinite(x)) { atomicOr(err, kErrNonFinite); x = 0.0; }
-        if (g.periodic[a]) {
-            double f = floor(__ddiv_rn(x, L));
-            v = __dsub_rn(x, __dmul_rn(L, f));
-            if (v >= L) v = __dsub_rn(v, L);
-            if (v < 0.0) v = 0.0;
-        } else {
-            v = x;
-            if (!(v >= 0.0 && v < L)) { atomicOr(err, kErrDomain); v = 0.0; }
-        }
-        w[a * N + i] = v;
-        double t = floor(__dmul_rn(__ddiv_rn(v, g.s), scale));
-        long long gi = (long long)t;
-        long long hi = ((long long)g.M[a] << kBits) - 1;
-        gi = gi < 0 ? 0 : (gi > hi ? hi : gi);
-        G[a] = (int)gi;
+        const double v = wrap_coord(g, a, pts[3 * i + a], err);
+        w[a * ws + i] = v;
+        G[a] = quantize_axis(g, a, v);
     }
     keys[i] = cell_key(g, kBits, G);
     idx[i] = (int)i;
+}
+
+// Periodic images of the sources along the padded axes (Sec. 4.1.2): every w + sum_i n_i L_i e_i
+// (n_i in -3..3 over the padded axes, n = 0 excluded) inside Omega_ext = [origin, origin + M s).
+// Image enumeration: n in lexicographic order over the padded axes, the lowest axis slowest.
+__device__ __forceinline__ int image_combos(const Geo& g, int* axes) {
+    int k = 0;
+    for (int a = 0; a < 3; ++a)
+        if (g.padded[a]) axes[k++] = a;
+    return k;
+}
+__device__ __forceinline__ bool image_of(const Geo& g, const double v[3], int na, const int* axes, int combo,
+                                         double out[3]) {
+    int n[3] = {0, 0, 0};
+    int c = combo;
+    bool zero = true;
+    for (int j = na - 1; j >= 0; --j) {
+        n[j] = c % 7 - 3;
+        c /= 7;
+        zero = zero && n[j] == 0;
+    }
+    if (zero) return false;
+    for (int a = 0; a < 3; ++a) out[a] = v[a];
+    for (int j = 0; j < na; ++j) {
+        const int a = axes[j];
+        out[a] = __dadd_rn(v[a], __dmul_rn((double)n[j], g.L[a]));
+        const double lo = g.origin[a], hi = __dadd_rn(g.origin[a], (double)g.M[a] * g.s);
+        if (!(out[a] >= lo && out[a] < hi)) return false;
+    }
+    return true;
+}
+
+// images per point (cnt[i]); with FILL, the images after the N originals at off[i] in point
+// order: wrapped coordinate, key, point index N + off[i] + j and its source src[...] = i
+template <bool FILL>
+__global__ void k_images(int64_t N, const double* __restrict__ pts, Geo g, double* __restrict__ w, int64_t ws,
+                         int* __restrict__ cnt, const int* __restrict__ off, uint64_t* __restrict__ keys,
+                         int* __restrict__ idx, int* __restrict__ src) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int axes[3];
+    const int na = image_combos(g, axes);
+    int ncombo = 1;
+    for (int j = 0; j < na; ++j) ncombo *= 7;
+    double v[3];
+    if (FILL) {
+        for (int a = 0; a < 3; ++a) v[a] = w[a * ws + i];
+    } else {
+        for (int a = 0; a < 3; ++a) v[a] = wrap_coord(g, a, pts[3 * i + a], nullptr);
+    }
+    int k = 0;
+    for (int combo = 0; combo < ncombo; ++combo) {
+        double im[3];
+        if (!image_of(g, v, na, axes, combo, im)) continue;
+        if (FILL) {
+            const int64_t j = N + off[i] + k;
+            int G[3];
+            for (int a = 0; a < 3; ++a) {
+                w[a * ws + j] = im[a];
+                G[a] = quantize_axis(g, a, im[a]);
+            }
+            keys[j] = cell_key(g, kBits, G);
+            idx[j] = (int)j;
+            src[j] = (int)i;
+        }
+        ++k;
+    }
+    if (!FILL) cnt[i] = k;
+    if (FILL && i < N) src[i] = (int)i;
 }
 
 // sorted order -> sorted SoA coordinates and strengths
@@ -58,11 +144,15 @@ constexpr int kGatherThreads = 256;
 __host__ __device__ constexpr int point_record_floats(int drho) { return drho <= 1 ? 8 : 16; }
 __host__ __device__ constexpr int point_record_rho(int a) { return a == 0 ? 3 : (a == 1 ? 7 : 6 + a); }
 
-__global__ void __launch_bounds__(kGatherThreads) k_gather(int64_t N, int drho, const int* __restrict__ idx,
+// N points (originals and images), N0 originals; src maps a point to its original (NULL: the
+// identity, no images).  Coordinates leave in the frame of Omega_ext's lower corner, x - origin;
+// orig[k] = the original index of sorted point k.  The strength sums count the originals only.
+__global__ void __launch_bounds__(kGatherThreads) k_gather(int64_t N, int64_t N0, int drho, const int* __restrict__ idx,
+                                                           const int* __restrict__ src, Geo g,
                                                            const double* __restrict__ w,
                                                            const double* __restrict__ rho, double* __restrict__ xs,
                                                            double* __restrict__ rs, float* __restrict__ pk,
-                                                           double* __restrict__ partial) {
+                                                           int* __restrict__ orig, double* __restrict__ partial) {
     __shared__ double red[18][kGatherThreads / 32];
     const int64_t k = blockIdx.x * (int64_t)kGatherThreads + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -70,22 +160,26 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(int64_t N, int drho, 
     for (int a = 0; a < drho; ++a) { s[a] = 0; sa[a] = 0; }
     if (k < N) {
         const int i = idx[k];
+        const int io = src ? src[i] : i;
+        if (orig) orig[k] = io;
         float rec[16];
         const int nf = point_record_floats(drho);
         for (int f = 0; f < 16; ++f) rec[f] = 0.0f;
         for (int a = 0; a < 3; ++a) {
-            const double v = w[a * N + i];
+            const double v = __dsub_rn(w[a * N + i], g.origin[a]);
             xs[a * N + k] = v;
             const float h = (float)v;
             rec[a] = h;
             rec[4 + a] = (float)(v - (double)h);
         }
         for (int a = 0; a < drho; ++a) {
-            const double r = rho[(int64_t)i * drho + a];
+            const double r = rho[(int64_t)io * drho + a];
             rs[k * drho + a] = r;
             rec[point_record_rho(a)] = (float)r;
-            s[a] = r;
-            sa[a] = fabs(r);
+            if (i < N0) {
+                s[a] = r;
+                sa[a] = fabs(r);
+            }
         }
         if (pk) {
             float4* dst = reinterpret_cast<float4*>(pk + k * nf);

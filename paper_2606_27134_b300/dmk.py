@@ -20,6 +20,10 @@ STATUS = {0: "DMK_OK", 1: "DMK_ERR_INVALID_ARG", 2: "DMK_ERR_OUT_OF_DOMAIN", 3: 
           8: "DMK_ERR_TIMEOUT"}
 
 
+# dmk_chi_reduce_fn: int (*)(double* chi, int64_t n, void* ctx)
+CHI_REDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_void_p)
+
+
 class DmkError(RuntimeError):
     def __init__(self, status, detail):
         super().__init__(f"{STATUS.get(status, status)}: {detail}")
@@ -69,6 +73,8 @@ def load(path=None):
     lib.dmk_eval_host.argtypes = [vp, c_i64, vp, vp, vp, vp]
     lib.dmk_eval_static.argtypes = [vp, c_i64, vp, vp, vp, vp]
     lib.dmk_vjp.argtypes = [vp, c_i64, vp, vp, vp, vp, vp, vp]
+    lib.dmk_eval_shard.argtypes = [vp, c_i64, c_i64, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int), CHI_REDUCE_FN,
+                                   vp]
     lib.dmk_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.dmk_set_timing.argtypes = [vp, c_int]
     lib.dmk_destroy.argtypes = [vp]
@@ -78,7 +84,8 @@ def load(path=None):
     lib.dmk_status_string.restype = ctypes.c_char_p
     lib.dmk_last_error.argtypes = [vp]
     lib.dmk_last_error.restype = ctypes.c_char_p
-    for f in ("dmk_plan", "dmk_plan_ex", "dmk_eval", "dmk_eval_host", "dmk_eval_static", "dmk_vjp", "dmk_get_stats",
+    for f in ("dmk_plan", "dmk_plan_ex", "dmk_eval", "dmk_eval_host", "dmk_eval_static", "dmk_vjp", "dmk_eval_shard",
+              "dmk_get_stats",
               "dmk_set_timing",
               "dmk_destroy", "dmk_plan_info", "dmk_plan_table"):
         getattr(lib, f).restype = c_int

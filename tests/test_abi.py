@@ -36,8 +36,8 @@ def test_status_strings():
     (("laplace", 3, (1, 1, 1), 1e-2), 1),          # tol outside the table range
     (("laplace", 5, (1, 1, 1), 1e-6), 1),          # D out of range
     (("laplace", 3, (1, -1, 1), 1e-6), 1),         # negative length
-    (("laplace", 3, (1, 1.3, 1.7), 1e-6), 4),      # non-exact tiling (Sec. 4.1.2) unsupported
-    (("laplace", 2, (2, 3, 1), 1e-6), 4),          # 3 is not a multiple of 2
+    (("laplace", 3, (1, 1, 2000), 1e-6), 4),       # more than 1024 cubes in the tiling
+    (("laplace", 3, (1, 40, 30), 1e-6), 4),        # the same with padded axes (42 x 32 cubes)
 ])
 def test_invalid_plans_rejected_before_device(args, code):
     kernel, D, L, tol = args
@@ -45,6 +45,15 @@ def test_invalid_plans_rejected_before_device(args, code):
         dmk.Plan(kernel, D, L, tol)
     assert e.value.status == code
     assert dmk.last_plan_error()
+
+
+def test_plan_info_of_non_exact_tilings():
+    """Sec. 4.1.1: a periodic length that the cube side does not divide is tiled by
+    ceil(L_i / s) cubes plus one padding cube on each side (L = [1, 1.3, 1.7]: 1 x 4 x 4)."""
+    info = dmk.plan_info("laplace", 3, [1, 1.3, 1.7], 1e-6)
+    assert info["M"] == [1, 4, 4] and info["s"] == 1.0
+    info = dmk.plan_info("rotlet", 2, [2, 1.3, 0.7], 1e-6)
+    assert info["M"] == [4, 1, 1] and info["s"] == 1.3      # s = 1.3; axis 0 padded: ceil(2 / 1.3) + 2
 
 
 def test_bad_precision_and_leaf_size():

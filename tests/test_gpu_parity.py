@@ -35,6 +35,14 @@ CASES = [
     # the 16 cubes stacked along x3 of the stresslet/rotlet workload (cube-index DFT root)
     ("stresslet-3P-16-cubes", "stresslet", 3, [1, 1, 16], 1e-6, 1600, 50, "uniform", "stokes"),
     ("rotlet-3P-16-cubes", "rotlet", 3, [1, 1, 16], 1e-6, 1600, 50, "uniform", "stokes"),
+    # non-exact tilings (Sec. 4.1.1-4.1.2): cut cubes, one padding cube each side, source
+    # images; Table 2/6's [1, 1.3, 1.7], a slab with L2 / L1 = 1.3, two padded axes for the
+    # stresslet, the padded axis first for the Stokeslet
+    ("laplace-3P-nonexact", "laplace", 3, [1, 1.3, 1.7], 1e-6, 700, 30, "mixed", "neutral"),
+    ("laplace-2P-nonexact", "laplace", 2, [1, 1.3, 0.5], 1e-6, 700, 30, "mixed", "uniform"),
+    ("rotlet-3P-nonexact", "rotlet", 3, [1, 1.3, 1.7], 1e-6, 500, 30, "mixed", "stokes"),
+    ("stresslet-3P-nonexact", "stresslet", 3, [2, 1.3, 1.7], 1e-6, 500, 30, "mixed", "stokes"),
+    ("stokeslet-2P-nonexact", "stokeslet", 2, [1.3, 1, 0.5], 1e-6, 500, 30, "mixed", "stokes"),
 ]
 
 _oracle_cache = {}
