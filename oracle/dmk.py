@@ -430,3 +430,27 @@ def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_p
 def forest_points_below(b):
     """Indices of all points in the subtree of box b (they are exactly b.pts)."""
     return b.pts
+
+
+def evaluate_targets(kernel, D, L, tol, sources, strengths, targets, n_s=250, grad=False):
+    """Eq. periodic_sum at a target set apart from the sources:
+    u(y_t) = sum_s sum*_p K(y_t - x_s + p) rho_s, the terms with y_t - x_s + p = 0 skipped.
+
+    The forest is built on sources and targets together, the targets entering as points of
+    zero strength: they add nothing to any proxy, plane wave or residual sum, their self term
+    (their own strength times K_M(0)) is zero, and the leaf step (Sec. 3.1.5) runs for them
+    only.  Returns a Result with u (M, d_u) and, if grad, grad (M, 3, d_u).
+    """
+    kern = Kernel(kernel)
+    y = np.asarray(targets, dtype=np.float64).reshape(-1, 3)
+    x = np.asarray(sources, dtype=np.float64).reshape(-1, 3)
+    M = y.shape[0]
+    rho = np.asarray(strengths, dtype=np.float64).reshape(x.shape[0], kern.d_rho)
+    pts = np.vstack([y, x])
+    q = np.vstack([np.zeros((M, kern.d_rho)), rho])
+    r = evaluate(kernel, D, L, tol, pts, q, n_s=n_s, grad=grad, targets=np.arange(M))
+    out = Result()
+    out.u = r.u[:M]
+    if grad:
+        out.grad = r.grad[:M]
+    return out

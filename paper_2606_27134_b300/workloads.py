@@ -8,6 +8,8 @@ CUDA path's tests and the oracle's tests draw their inputs from here.
   and 6): the clustered half is Gaussian with sigma = 0.05 s around the centre of
   the first cube of side s = min periodic length (or max L for D = 0), wrapped;
 * Gaussian clusters (sigma = 0.02) for an adaptive tree;
+* the singly periodic pipe of Sec. 6 (Fig. cylinder_stokeslet): trapezoidal nodes on a cylinder
+  around the periodic x1 axis, a fixed number of points per unit length;
 * neutral +-1 charges, uniform charges minus their mean, N(0,1) vectors minus their
   mean, stresslet q (x) n with n uniform on the sphere, N(0,1) rotlet torques.
 """
@@ -49,6 +51,18 @@ def clustered_points(N, L, seed, n_centers=64, sigma=0.02):
     per[: N - per.sum()] += 1
     pts = np.vstack([c + sigma * rng.standard_normal((k, 3)) for c, k in zip(centres, per)])
     return _wrap_into(pts, L)
+
+
+def cylinder_points(L1, per_unit=10000, n_theta=100, radius=0.4, centre=(0.5, 0.5)):
+    """Trapezoidal nodes on the cylinder {(x1, c2 + r cos t, c3 + r sin t)} of the cell
+    [0, L1) x [0, 1)^2: n_theta equispaced angles times per_unit / n_theta equispaced axial
+    positions per unit of L1 (N = per_unit L1 points; the paper's pipe has 10,000 per unit
+    length, its radius is not stated: 0.4 here)."""
+    n_ax = int(round(L1 * per_unit / n_theta))
+    x1 = (np.arange(n_ax) + 0.5) * (L1 / n_ax)
+    t = 2 * np.pi * np.arange(n_theta) / n_theta
+    X1, T = np.meshgrid(x1, t, indexing="ij")
+    return np.stack([X1.ravel(), centre[0] + radius * np.cos(T.ravel()), centre[1] + radius * np.sin(T.ravel())], 1)
 
 
 def neutral_charges(N, seed):

@@ -22,7 +22,7 @@ import pytest
 from scipy.integrate import quad
 import scipy.special as sp
 
-from oracle.dmk import evaluate
+from oracle.dmk import evaluate, evaluate_targets
 from oracle import ewald
 from oracle.kernels import Kernel
 from oracle.params import Geometry
@@ -471,3 +471,32 @@ def test_split_over_cubes_equals_full(kernel, D, L, N, parts):
         g[idx[mine]] = r.grad[mine]
     assert rel(u, full.u) < 1e-13
     assert rel(g, full.grad) < 1e-13
+
+
+@pytest.mark.parametrize("D,L", [(3, [1, 1, 1]), (2, [1, 1, 0.5]), (1, [1.5, 1, 1]), (3, [1, 1.3, 1.7])])
+def test_separate_targets_laplace_vs_ewald(D, L):
+    """Targets apart from the sources (evaluate_targets) against the Ewald sum of the sources
+    at those points (an Ewald sum over sources and targets with the targets' strengths zero)."""
+    N, M = 90, 60
+    x = workloads.mixed_points(N, L, seed=401 + D)
+    q = workloads.neutral_charges(N, seed=402 + D)
+    y = workloads.uniform_points(M, L, seed=403 + D)
+
+    r = evaluate_targets("laplace", D, L, 1e-6, x, q, y, n_s=12, grad=True)
+    ue, ge = ewald.laplace_reference(D, L, np.vstack([y, x]), np.concatenate([np.zeros(M), q]), grad=True)
+    assert r.u.shape == (M, 1)
+    assert rel(r.u[:, 0], ue[:M]) < 1e-6
+    assert rel(r.grad[:, :, 0], ge[:M]) < 3e-6
+
+
+def test_separate_targets_stokeslet_3p_vs_ewald():
+    """Stokeslet, D = 3, targets apart from the sources, against Hasimoto's Ewald sum."""
+    L = [1, 1, 1]
+    x = workloads.mixed_points(50, L, seed=411)
+    f = workloads.stokes_strengths("stokeslet", 50, seed=412)
+    y = workloads.uniform_points(30, L, seed=413)
+    r = evaluate_targets("stokeslet", 3, L, 1e-9, x, f, y, n_s=12)
+    # the Ewald sum's target t is its source t: sources and targets joined, target forces zero
+    pts = np.vstack([y, x])
+    e = ewald.stokeslet_ewald_3p(pts, pts, np.vstack([np.zeros((30, 3)), f]), L, 0.25)[:30]
+    assert rel(r.u, e) < 1e-8
