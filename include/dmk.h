@@ -163,6 +163,22 @@ dmk_status_t dmk_eval_shard(dmk_plan_t plan, int64_t N, int64_t n_own, const dou
                             double* potentials, double* grad, const int* cube_owned, dmk_chi_reduce_fn reduce,
                             void* ctx);
 
+/* Separate target set: u(y_t) = sum_s sum*_p K(y_t - x_s + p) rho_s at M targets y_t that need
+ * not be sources (Eq. periodic_sum with the targets apart from the sources; terms with
+ * y_t - x_s + p = 0 are skipped).  The forest is built on sources and targets together (the
+ * targets enter as points of zero strength), so a target's value is the one dmk_eval gives a
+ * zero-strength point at y_t.
+ *   sources, strengths  device, N x 3 and N x d_rho (N >= 0; N = 0 gives zeros)
+ *   targets             device, M x 3, wrapped and checked like the sources
+ *   potentials, grad    device, M x d_u and M x 3 x d_u (grad may be NULL), target order
+ * A target on a source (or on one of its periodic images) meets a singular term: the residual
+ * sum skips the pair, and the smooth part of that term, K_M(0) rho_s, stays in the value.
+ * Workspace as dmk_eval, plus (N + M) x (3 + d_rho) doubles for the joined point set; the call
+ * is stream-ordered on the plan's stream like dmk_eval.  Errors as dmk_eval (the neutrality
+ * test of D = 1, 2 Laplace is over the sources). */
+dmk_status_t dmk_eval_targets(dmk_plan_t plan, int64_t N, const double* sources, const double* strengths,
+                              int64_t M, const double* targets, double* potentials, double* grad);
+
 /* dmk_eval without any device allocation.  The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc at evaluation time -- applications whose
  * device memory is fully reserved by their own pool allocator and that must not let a

@@ -116,7 +116,7 @@ enum BufId {
     B_W, B_KEYS, B_KEYS2, B_IDX, B_IDX2, B_XS, B_RS, B_CUB, B_FLAGS, B_CNT,
     B_CELLS, B_R, B_CAND, B_BOXU64, B_BOXINT, B_LEAVES, B_DOFFS, B_DL, B_NLBOX, B_TASKS, B_BAL,
     B_PROXY, B_LOCAL, B_PW, B_SCRATCH, B_CHI, B_UHAT, B_MISC, B_DEVPTS, B_DEVRHO, B_DEVPOT, B_DEVGRAD, B_XF, B_VW, B_PART,
-    B_VJPV, B_VJPG, B_ICNT, B_SRC, B_ORIG, B_CHIP, B_SHARDCLS,
+    B_VJPV, B_VJPG, B_ICNT, B_SRC, B_ORIG, B_CHIP, B_SHARDCLS, B_TPTS, B_TRHO, B_ITEMS,
     B_COUNT
 };
 
@@ -461,14 +461,16 @@ dmk_status_t launch_pair(dmk_plan_s* plan, Tab<T>& tab, const int* leaves, BoxAr
 template <class T, int K, bool G>
 dmk_status_t launch_leafexp(dmk_plan_s* plan, Tab<T>& tab, int nleaf, const int* leaves, BoxArrays B, const T* local,
                             const double* xs, int64_t N, LeafOut lo, int direct_leaf, int n_nl, const int* nl_box,
-                            int n_root) {
+                            int n_root, const int* woff) {
     const size_t se = leafexp_smem<T>(tab.p);
     if (direct_leaf) {
-        // one item per non-leaf box with leaf children and per cube that is a leaf
+        // chunks of targets of the non-leaf boxes with leaf children and of the cubes that are
+        // leaves; at most N / kLeafExpThreads + n_nl + n_root of them
         CKS(set_smem(plan, k_leafexp_parent<T, K, G>, se));
-        const unsigned grid = (unsigned)std::max(1, std::min(n_nl + n_root, plan->n_sm * 16));
-        k_leafexp_parent<T, K, G><<<grid, kLeafExpThreads, se, plan->stream>>>(n_nl, nl_box, n_root, B, tab, plan->geo,
-                                                                               local, xs, N, lo);
+        const int64_t most = N / kLeafExpThreads + n_nl + n_root;
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(most, (int64_t)plan->n_sm * 16));
+        k_leafexp_parent<T, K, G><<<grid, kLeafExpThreads, se, plan->stream>>>(n_nl, nl_box, n_root, woff, B, tab,
+                                                                               plan->geo, local, xs, N, lo);
         return DMK_OK;
     }
     CKS(set_smem(plan, k_leafexp<T, K, G>, se));
@@ -505,22 +507,24 @@ struct TreeInfo {
 };
 
 
-// a shard's partial structure factor (n doubles at chi, device) and its strength sums (2 d_rho
-// doubles at sums, device) summed over the ranks by the caller's reduction; nothing without a
-// shard
-dmk_status_t reduce_chi(dmk_plan_s* plan, const struct ShardArgs* sh, Cx<double>* chi, int64_t n, double* sums);
-
-// one rank of a cube-sharded evaluation (dmk_eval_shard): outputs for the first n_own points,
-// structure factor over the owned cubes, completed by the caller's reduction
-struct ShardArgs {
-    int64_t n_own;
-    const int* cube_owned;      // host, Mtot flags
-    dmk_chi_reduce_fn reduce;
+// Variants of one evaluation (nullptr: every point a target, every cube counted):
+//   separate targets (dmk_eval_targets): the targets are the first n_out points, with zero
+//       strengths; outputs for them only;
+//   one rank of a cube-sharded evaluation (dmk_eval_shard): outputs for the first n_out points
+//       (the owned ones), strength sums over them, structure factor over the owned cubes,
+//       completed by the caller's reduction.
+struct EvalOpts {
+    int64_t n_out;              // points with outputs: input index < n_out
+    int64_t n_sum;              // strength sums over input index < n_sum
+    const int* cube_owned;      // host, Mtot flags, or nullptr (every cube)
+    dmk_chi_reduce_fn reduce;   // or nullptr (no reduction)
     void* ctx;
 };
 
-dmk_status_t reduce_chi(dmk_plan_s* plan, const ShardArgs* sh, Cx<double>* chi, int64_t n, double* sums) {
-    if (!sh) return DMK_OK;
+// a shard's partial structure factor (n doubles at chi, device) and its strength sums (2 d_rho
+// doubles at sums, device) summed over the ranks by the caller's reduction; nothing without one
+dmk_status_t reduce_chi(dmk_plan_s* plan, const EvalOpts* sh, Cx<double>* chi, int64_t n, double* sums) {
+    if (!sh || !sh->reduce) return DMK_OK;
     const int ns = 2 * plan->T.d_rho;
     const int64_t ntot = n + ns;
     // through plan-owned pinned host memory, so that any host-side all-reduce can serve
@@ -549,7 +553,7 @@ dmk_status_t reduce_chi(dmk_plan_s* plan, const ShardArgs* sh, Cx<double>* chi, 
 
 template <class T>
 dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* pts, const double* rho, double* pot,
-                      double* grad, const ShardArgs* sh = nullptr) {
+                      double* grad, const EvalOpts* sh = nullptr) {
     cudaStream_t st = plan->stream;
     const PlanTables& P = plan->T;
     const int drho = P.d_rho, du = P.d_u, p = P.p, p3 = p * p * p;
@@ -672,7 +676,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* p
         cub_cap = plan->bufs[B_CUB].cap;
         CK(cub::DeviceRadixSort::SortPairs(vcub, tmp_bytes, keys, keys2, idx, idx2, (int)N, begin_bit, end_bit, st));
         // strength sums over the original points (a shard: over its own points, first n_own)
-        k_gather<<<ngb, kGatherThreads, 0, st>>>(N, sh ? sh->n_own : N0, drho, idx2, src, g, (const double*)vw, rho,
+        k_gather<<<ngb, kGatherThreads, 0, st>>>(N, sh ? sh->n_sum : N0, drho, idx2, src, g, (const double*)vw, rho,
                                                   xs, rs, pk, orig, (double*)vpart);
         k_sum_partials<<<1, 1024, 0, st>>>(ngb, 2 * drho, (const double*)vpart, d_sums);
         CK(cudaMemsetAsync(d_missing, 0, (kBits + 1) * sizeof(int), st));      // missing[] and capped
@@ -870,7 +874,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* p
     lo.grad = grad;
     lo.perm = idx2;
     lo.orig = orig ? orig : idx2;
-    lo.n_orig = sh ? sh->n_own : N0;
+    lo.n_orig = sh ? sh->n_out : N0;
     lo.rs = rs;
     lo.self_val = plan->d_self;
     lo.self_grad = plan->d_self + P.d_u * P.d_rho;
@@ -1024,12 +1028,13 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* p
         // inside Omega (cube proxies inside, nothing for padding cubes, cut cubes from their
         // original sources)
         const T* rproxy = proxy;
-        if (padded || sh) {
+        const bool owned_only = sh && sh->cube_owned;
+        if (padded || owned_only) {
             void* vchip;
             CKS(ensure(plan, B_CHIP, (size_t)Mtot * drho * p3 * sizeof(T), &vchip));
             T* chip = (T*)vchip;
             const int* cls = plan->d_cube;
-            if (sh) {
+            if (owned_only) {
                 // a shard: the cubes it owns count (class 0), the others not (class 2)
                 void* vcls;
                 CKS(ensure(plan, B_SHARDCLS, (size_t)Mtot * sizeof(int), &vcls));
@@ -1040,7 +1045,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* p
                 cls = (const int*)vcls;
             }
             k_chi_proxy<T><<<nblk((int64_t)Mtot * drho * p3, 256), 256, 0, st>>>(Mtot, drho, p3, cls, proxy, chip);
-            const int ncut = sh ? 0 : (int)std::count(P.cube_class.begin(), P.cube_class.end(), 1);
+            const int ncut = owned_only ? 0 : (int)std::count(P.cube_class.begin(), P.cube_class.end(), 1);
             if (ncut > 0) {
                 const int* cutlist = plan->d_cube + Mtot + 1;
                 if (p <= 20) {
@@ -1232,6 +1237,21 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* p
         }
         ++launches;
     }
+    // direct_leaf: chunks of targets per item for k_leafexp_parent (counts, exclusive scan)
+    int* item_off = nullptr;
+    if (direct_leaf) {
+        const int n_items = n_nl + Mtot;
+        void* vit;
+        CKS(ensure(plan, B_ITEMS, (size_t)2 * (n_items + 1) * sizeof(int), &vit));
+        int* cnt = (int*)vit;
+        item_off = cnt + n_items + 1;
+        k_item_chunks<<<nblk(n_items + 1, 256), 256, 0, st>>>(n_nl, nl_box, Mtot, B, cnt);
+        size_t tb = 0;
+        cub::DeviceScan::ExclusiveSum(nullptr, tb, cnt, item_off, n_items + 1, st);
+        if (tb > cub_cap) { CKS(ensure(plan, B_CUB, tb, &vcub)); cub_cap = plan->bufs[B_CUB].cap; }
+        CK(cub::DeviceScan::ExclusiveSum(vcub, tb, cnt, item_off, n_items + 1, st));
+        launches += 2;
+    }
     // leaf grids that did not pass through k_shift_child become Chebyshev coefficients here
     if (nleaf > 0) {
         const int root_only = fast_shift ? 1 : 0;
@@ -1252,10 +1272,10 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* p
         else CKS(run_pair(st));
         if (plan->timing) cudaEventRecord(plan->ev[10], st);
         switch (P.kernel) {
-            case DMK_LAPLACE: CKS((gr ? launch_leafexp<T, DMK_LAPLACE, true> : launch_leafexp<T, DMK_LAPLACE, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo, direct_leaf ? 1 : 0, n_nl, nl_box, Mtot)); break;
-            case DMK_STOKESLET: CKS((gr ? launch_leafexp<T, DMK_STOKESLET, true> : launch_leafexp<T, DMK_STOKESLET, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo, direct_leaf ? 1 : 0, n_nl, nl_box, Mtot)); break;
-            case DMK_STRESSLET: CKS((gr ? launch_leafexp<T, DMK_STRESSLET, true> : launch_leafexp<T, DMK_STRESSLET, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo, direct_leaf ? 1 : 0, n_nl, nl_box, Mtot)); break;
-            default: CKS((gr ? launch_leafexp<T, DMK_ROTLET, true> : launch_leafexp<T, DMK_ROTLET, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo, direct_leaf ? 1 : 0, n_nl, nl_box, Mtot)); break;
+            case DMK_LAPLACE: CKS((gr ? launch_leafexp<T, DMK_LAPLACE, true> : launch_leafexp<T, DMK_LAPLACE, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo, direct_leaf ? 1 : 0, n_nl, nl_box, Mtot, item_off)); break;
+            case DMK_STOKESLET: CKS((gr ? launch_leafexp<T, DMK_STOKESLET, true> : launch_leafexp<T, DMK_STOKESLET, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo, direct_leaf ? 1 : 0, n_nl, nl_box, Mtot, item_off)); break;
+            case DMK_STRESSLET: CKS((gr ? launch_leafexp<T, DMK_STRESSLET, true> : launch_leafexp<T, DMK_STRESSLET, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo, direct_leaf ? 1 : 0, n_nl, nl_box, Mtot, item_off)); break;
+            default: CKS((gr ? launch_leafexp<T, DMK_ROTLET, true> : launch_leafexp<T, DMK_ROTLET, false>)(plan, tab, nleaf, leaves, B, local, xs, N, lo, direct_leaf ? 1 : 0, n_nl, nl_box, Mtot, item_off)); break;
         }
         ++launches;
     } else if (nleaf > 0) {
@@ -1278,7 +1298,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* p
     std::memcpy(hs, plan->h_meta + 256, 2 * drho * sizeof(double));
     if (herr & kErrNonFinite) { plan->err = "non-finite coordinate"; return DMK_ERR_OUT_OF_DOMAIN; }
     if (herr & kErrDomain) { plan->err = "a free coordinate lies outside [0, L_i)"; return DMK_ERR_OUT_OF_DOMAIN; }
-    if (!plan->allow_charged && !sh && P.kernel == DMK_LAPLACE && (P.D == 1 || P.D == 2) &&
+    if (!plan->allow_charged && !(sh && sh->reduce) && P.kernel == DMK_LAPLACE && (P.D == 1 || P.D == 2) &&
         std::fabs(hs[0]) > 1e-12 * std::max(hs[1], 1e-300)) {
         plan->err = "Laplace with D = 1, 2 requires zero net charge";
         return DMK_ERR_NOT_NEUTRAL;
@@ -1431,7 +1451,7 @@ dmk_status_t dmk_eval_shard(dmk_plan_t plan, int64_t N, int64_t n_own, const dou
     }
     if (N > 0 && (!points || !strengths || (n_own > 0 && !potentials))) { plan->err = "NULL array"; return DMK_ERR_INVALID_ARG; }
     cudaSetDevice(plan->device);
-    ShardArgs sh{n_own, cube_owned, reduce, ctx};
+    EvalOpts sh{n_own, n_own, cube_owned, reduce, ctx};
     if (N == 0) {
         // nothing local, but the other ranks' reduction still needs this rank's (zero) share
         const RootTab& rt = plan->root;
@@ -1449,6 +1469,41 @@ dmk_status_t dmk_eval_shard(dmk_plan_t plan, int64_t N, int64_t n_own, const dou
     if (plan->prec == DMK_FP64)
         return run_eval<double>(plan, plan->tab64, N, points, strengths, potentials, grad, &sh);
     return run_eval<float>(plan, plan->tab32, N, points, strengths, potentials, grad, &sh);
+}
+
+dmk_status_t dmk_eval_targets(dmk_plan_t plan, int64_t N, const double* sources, const double* strengths,
+                              int64_t M, const double* targets, double* potentials, double* grad) {
+    if (!plan) return DMK_ERR_INVALID_ARG;
+    plan->err.clear();
+    if (N < 0 || M < 0) { plan->err = "N < 0 or M < 0"; return DMK_ERR_INVALID_ARG; }
+    if (M == 0) return DMK_OK;
+    if (N + M > (int64_t)1 << 30) { plan->err = "N + M above 2^30"; return DMK_ERR_INVALID_ARG; }
+    if ((N > 0 && (!sources || !strengths)) || !targets || !potentials) {
+        plan->err = "NULL array";
+        return DMK_ERR_INVALID_ARG;
+    }
+    cudaSetDevice(plan->device);
+    // the targets enter the forest as points of zero strength, ahead of the sources: the tree
+    // is built on both sets, the targets add nothing to any sum, and the self term of a target
+    // (its own strength) vanishes
+    const int drho = plan->T.d_rho;
+    const int64_t Nt = M + N;
+    void *vp, *vr;
+    CKS(ensure(plan, B_TPTS, (size_t)Nt * 3 * sizeof(double), &vp));
+    CKS(ensure(plan, B_TRHO, (size_t)Nt * drho * sizeof(double), &vr));
+    double* pts = (double*)vp;
+    double* rho = (double*)vr;
+    const cudaStream_t st = plan->stream;
+    CK(cudaMemcpyAsync(pts, targets, (size_t)M * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemsetAsync(rho, 0, (size_t)M * drho * sizeof(double), st));
+    if (N > 0) {
+        CK(cudaMemcpyAsync(pts + M * 3, sources, (size_t)N * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(rho + M * drho, strengths, (size_t)N * drho * sizeof(double), cudaMemcpyDeviceToDevice,
+                           st));
+    }
+    EvalOpts opt{M, Nt, nullptr, nullptr, nullptr};
+    if (plan->prec == DMK_FP64) return run_eval<double>(plan, plan->tab64, Nt, pts, rho, potentials, grad, &opt);
+    return run_eval<float>(plan, plan->tab32, Nt, pts, rho, potentials, grad, &opt);
 }
 
 dmk_status_t dmk_eval_static(dmk_plan_t plan, int64_t N, const double* points, const double* strengths,

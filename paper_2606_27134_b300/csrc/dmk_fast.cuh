@@ -1521,15 +1521,36 @@ __global__ void __launch_bounds__(kLeafExpThreads) k_leafexp(int nleaf, const in
     }
 }
 
-// The leaf expansions with direct_leaf (Sec. 3.1.5): one work item per non-leaf box with leaf
-// children (its expansion evaluated at the targets of all those children: the same polynomial as
-// the children's shifted expansions) or per cube that is a leaf; its coefficients are staged
-// once per component for every target of the item.  Component by component, the expansion and
-// its gradient are added to the residual sums of k_pair and the self term of the target's own
-// leaf (Sec. 2.4) subtracted, in FP64.
+// Work units of k_leafexp_parent: chunks of kLeafExpThreads targets of one item (a non-leaf box
+// with leaf children: the targets of those children; a cube that is a leaf: its targets).
+// cnt[item] = the item's chunk count, cnt[n_nl + n_root] = 0 (exclusive-scanned afterwards).
+__global__ void k_item_chunks(int n_nl, const int* __restrict__ nl_box, int n_root, BoxArrays B,
+                              int* __restrict__ cnt) {
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    if (item > n_nl + n_root) return;
+    int n = 0;
+    if (item < n_nl) {
+        const int eb = nl_box[item], c0 = B.child0[eb];
+        for (int o = 0; o < 8; ++o)
+            if (B.child0[c0 + o] < 0) n += B.end[c0 + o] - B.start[c0 + o];
+    } else if (item < n_nl + n_root) {
+        const int eb = item - n_nl;
+        if (B.child0[eb] < 0) n = B.end[eb] - B.start[eb];
+    }
+    cnt[item] = (n + kLeafExpThreads - 1) / kLeafExpThreads;
+}
+
+// The leaf expansions with direct_leaf (Sec. 3.1.5): the targets of the leaf children of a
+// non-leaf box evaluate that box's expansion (the same polynomial as the children's shifted
+// expansions), the targets of a cube that is a leaf its own.  Work unit = a chunk of
+// kLeafExpThreads targets of one such item (woff: exclusive prefix of the chunk counts, every
+// lane a target but in an item's last chunk); the item's coefficients are staged once per
+// component.  Component by component, the expansion and its gradient are added to the residual
+// sums of k_pair and the self term of the target's own leaf (Sec. 2.4) subtracted, in FP64.
 template <class T, int K, bool GRAD>
 __global__ void __launch_bounds__(kLeafExpThreads) k_leafexp_parent(int n_nl, const int* __restrict__ nl_box,
-                                                                   int n_root, BoxArrays B, Tab<T> tab, Geo g,
+                                                                   int n_root, const int* __restrict__ woff,
+                                                                   BoxArrays B, Tab<T> tab, Geo g,
                                                                    const T* __restrict__ coef,
                                                                    const double* __restrict__ xs, int64_t N,
                                                                    LeafOut out) {
@@ -1544,7 +1565,15 @@ __global__ void __launch_bounds__(kLeafExpThreads) k_leafexp_parent(int n_nl, co
     __shared__ int rpre[9];
     __shared__ int nrng;
     const int tt = threadIdx.x;
-    for (int item = blockIdx.x; item < n_nl + n_root; item += gridDim.x) {
+    const int n_items = n_nl + n_root, total = woff[n_items];
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+        // the item of chunk w: the last with woff[item] <= w (woff[n_items] = total > w)
+        int lo = 0, hi = n_items;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (woff[mid] <= w) lo = mid; else hi = mid;
+        }
+        const int item = lo, vbeg = (w - woff[item]) * kLeafExpThreads;
         int eb;
         __syncthreads();
         if (item < n_nl) {
@@ -1570,8 +1599,7 @@ __global__ void __launch_bounds__(kLeafExpThreads) k_leafexp_parent(int n_nl, co
             for (int k = 0; k < nrng; ++k) rpre[k + 1] = rpre[k] + rng[k][1] - rng[k][0];
         }
         __syncthreads();
-        const int nr = nrng, ntot = rpre[nr];
-        if (ntot == 0) continue;                         // uniform over the block
+        const int nr = nrng, vend = min(rpre[nr], vbeg + kLeafExpThreads);
         const int le = B.level[eb];
         // the targets' own leaves: the children (level le + 1), or the cube itself
         const double rT = ldexp(g.s, -(item < n_nl ? le + 1 : le));
@@ -1588,9 +1616,9 @@ __global__ void __launch_bounds__(kLeafExpThreads) k_leafexp_parent(int n_nl, co
                 cs[e] = n3 < p ? cj[n12 * p + n3] : T(0);
             }
             __syncthreads();
-            for (int v0 = 0; v0 < ntot; v0 += kLeafExpThreads) {
-                const int v = v0 + tt;
-                const bool act = v < ntot;
+            {
+                const int v = vbeg + tt;
+                const bool act = v < vend;
                 int tg = 0;
                 if (act) {
                     int k = 0;

@@ -75,6 +75,7 @@ def load(path=None):
     lib.dmk_vjp.argtypes = [vp, c_i64, vp, vp, vp, vp, vp, vp]
     lib.dmk_eval_shard.argtypes = [vp, c_i64, c_i64, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int), CHI_REDUCE_FN,
                                    vp]
+    lib.dmk_eval_targets.argtypes = [vp, c_i64, vp, vp, c_i64, vp, vp, vp]
     lib.dmk_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.dmk_set_timing.argtypes = [vp, c_int]
     lib.dmk_destroy.argtypes = [vp]
@@ -85,7 +86,7 @@ def load(path=None):
     lib.dmk_last_error.argtypes = [vp]
     lib.dmk_last_error.restype = ctypes.c_char_p
     for f in ("dmk_plan", "dmk_plan_ex", "dmk_eval", "dmk_eval_host", "dmk_eval_static", "dmk_vjp", "dmk_eval_shard",
-              "dmk_get_stats",
+              "dmk_eval_targets", "dmk_get_stats",
               "dmk_set_timing",
               "dmk_destroy", "dmk_plan_info", "dmk_plan_table"):
         getattr(lib, f).restype = c_int
@@ -151,6 +152,25 @@ class Plan:
         u = torch.empty((N, self.d_u), dtype=torch.float64, device=pts.device)
         g = torch.empty((N, 3, self.d_u), dtype=torch.float64, device=pts.device) if grad else None
         self.eval_ptr(N, pts.data_ptr(), rho.data_ptr(), u.data_ptr(), g.data_ptr() if grad else 0)
+        return u, g
+
+    def eval_targets(self, sources, strengths, targets, grad=False):
+        """dmk_eval_targets: the sum over the sources (N,3) with strengths (N, d_rho) at separate
+        targets (M,3); CUDA FP64 torch tensors.  Returns (u (M, d_u), grad (M, 3, d_u) or None)."""
+        import torch
+        N = sources.shape[0]
+        M = targets.shape[0]
+        src = sources.contiguous()
+        rho = strengths.reshape(N, self.d_rho).contiguous()
+        trg = targets.contiguous()
+        for t in (src, rho, trg):
+            if not (t.is_cuda and t.dtype == torch.float64):
+                raise TypeError("sources, strengths and targets must be CUDA float64 tensors")
+        u = torch.empty((M, self.d_u), dtype=torch.float64, device=trg.device)
+        g = torch.empty((M, 3, self.d_u), dtype=torch.float64, device=trg.device) if grad else None
+        vp = ctypes.c_void_p
+        _check(load().dmk_eval_targets(self._h, N, vp(src.data_ptr()), vp(rho.data_ptr()), M, vp(trg.data_ptr()),
+                                       vp(u.data_ptr()), vp(g.data_ptr()) if grad else None), self._h)
         return u, g
 
     def vjp(self, points, strengths, grad_u, g, want_strengths=True, want_points=True):

@@ -43,6 +43,11 @@ CASES = [
     ("rotlet-3P-nonexact", "rotlet", 3, [1, 1.3, 1.7], 1e-6, 500, 30, "mixed", "stokes"),
     ("stresslet-3P-nonexact", "stresslet", 3, [2, 1.3, 1.7], 1e-6, 500, 30, "mixed", "stokes"),
     ("stokeslet-2P-nonexact", "stokeslet", 2, [1.3, 1, 0.5], 1e-6, 500, 30, "mixed", "stokes"),
+    # the singly periodic pipe of Sec. 6 (trapezoidal nodes on a cylinder around x1), at the
+    # three tolerances of its figure, 1000 points per unit length
+    ("stokeslet-1P-cylinder-1e-6", "stokeslet", 1, [2, 1, 1], 1e-6, 2000, 40, "cylinder", "stokes"),
+    ("stokeslet-1P-cylinder-1e-9", "stokeslet", 1, [2, 1, 1], 1e-9, 2000, 40, "cylinder", "stokes"),
+    ("stokeslet-1P-cylinder-1e-12", "stokeslet", 1, [2, 1, 1], 1e-12, 2000, 60, "cylinder", "stokes"),
 ]
 
 _oracle_cache = {}
@@ -55,6 +60,8 @@ def make_inputs(case):
         x = W.uniform_points(N, L, seed)
     elif pg == "mixed":
         x = W.mixed_points(N, L, seed, D=D)
+    elif pg == "cylinder":
+        x = W.cylinder_points(L[0], per_unit=N // L[0], n_theta=40)
     else:
         x = W.clustered_points(N, L, seed, n_centers=8, sigma=0.03)
     if sg == "neutral":

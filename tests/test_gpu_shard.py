@@ -109,7 +109,9 @@ def test_shard_equals_whole(kernel, D, L, N, world, precision):
     assert len(set(owner.tolist())) == world
     uw, gw = whole(kernel, D, L, 1e-6, x, q, precision, 100)
     assert np.isfinite(u).all() and np.isfinite(g).all()
-    bar = 1e-12 if precision == "fp64" else 1e-6       # summation order only
+    # summation order only: FP64 rounding on the plain path; on the mixed path the FP32 sums of
+    # the two evaluations (different point orders within a leaf) each sit within the 1e-5 bar
+    bar = 1e-12 if precision == "fp64" else 1e-5
     assert rel(u, uw) < bar and rel(g, gw) < bar
 
 
