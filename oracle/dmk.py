@@ -14,7 +14,7 @@ derivatives of the computed approximation u(x_t).
 import math
 import numpy as np
 
-from .params import c_and_p, n_f, Geometry, root_modes
+from .params import c_and_p, n_f, Geometry, root_modes, original_symbol_ok, free_count
 from .pswf import PSWFWindow
 from .kernels import Kernel
 from .tree import BITS, Forest, wrap, replicate, quantize
@@ -94,6 +94,55 @@ def root_symbol(kern, geom, c, win):
     W[~keep.ravel()] = 0.0
     W = C * W * gam[:, None, None]
     return axes, keep, W.reshape(shp + (kern.d_u, kern.d_rho)), R
+
+
+def root_parts(kern, geom, c, win, tol):
+    """The root far field as one or two wavenumber rectangles, each (axes, keep, W, R) as
+    root_symbol returns them; their contributions add.
+
+    Truncated symbol for every mode (Remark alpha_switch), unless the App. E switch
+    (params.original_symbol_ok) allows the original one: then the alpha != 0 modes take the
+    original mollified symbol D-hat(k) gamma-hat(|k| nu_0)/|k|^{2,4} on the free grid of step
+    pi/L_j (the Nyquist step of the original kernel, Sec. 5.3) with the constant C^{DP} of that
+    step, and the alpha = 0 modes keep the truncated zero-mode symbols on the step-pi/R grid
+    (Eq. ewald_far_es_1P_discr_b, and its D = 2 analogue).
+    """
+    if not original_symbol_ok(kern.name, geom, tol):
+        return [root_symbol(kern, geom, c, win)]
+    D = geom.D
+    axes_t, keep_t, W_t, R = root_symbol(kern, geom, c, win)
+    # part 1: the alpha = 0 line of the truncated rectangle
+    sl = tuple(slice(int(np.argmin(np.abs(axes_t[i]))), int(np.argmin(np.abs(axes_t[i]))) + 1) if i < D
+               else slice(None) for i in range(3))
+    axes_z = [axes_t[i][sl[i]] for i in range(3)]
+    part_z = (axes_z, keep_t[sl], W_t[sl], R)
+    # part 2: alpha != 0 with the original symbol
+    K = c / geom.nu0
+    axes_o = []
+    steps = []
+    for i in range(3):
+        if i < D:
+            axes_o.append(axes_t[i])
+        else:
+            h = math.pi / geom.Lext[i]
+            n = free_count(K, h)
+            axes_o.append(h * np.arange(-n, n + 1))
+            steps.append(h)
+    kk = np.stack(np.meshgrid(*axes_o, indexing="ij"), axis=-1).reshape(-1, 3)
+    kn = np.sqrt(np.sum(kk * kk, axis=1))
+    alpha = np.sqrt(np.sum(kk[:, :D] ** 2, axis=1))
+    keep = (kn * geom.nu0 <= c * (1 + 1e-12)) & (alpha > 0)
+    kk[~keep] = 1.0              # dropped modes: a harmless point, zeroed below
+    kn = np.sqrt(np.sum(kk * kk, axis=1))
+    W = kern.op_symbol(kk) * (kern.screening(kn * geom.nu0, win) / kn ** (4 if kern.biharmonic else 2))[:, None, None]
+    W[~keep] = 0.0
+    if D == 2:
+        C = steps[0] / (geom.L[0] * geom.L[1] * 2 * math.pi)
+    else:
+        C = steps[0] * steps[1] / (geom.L[0] * (2 * math.pi) ** 2)
+    shp = tuple(len(a) for a in axes_o)
+    part_o = (axes_o, keep.reshape(shp), (C * W).reshape(shp + (kern.d_u, kern.d_rho)), R)
+    return [part_z, part_o]
 
 
 def _zero_mode_2p(kern, k3, R):
@@ -183,8 +232,8 @@ def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_p
     structure factor of Eq. structurefac is a sum over the cubes; with owned_cubes (cube indices
     m1 + M1 (m2 + M2 m3)) only those cubes enter this evaluator's partial sum, and
     chi_reduce(partial) -> total combines the partial sums of all evaluators (e.g. an
-    all-reduce): it receives one flat complex vector, the structure factor followed by the
-    d_rho strength sums over the own cubes (the total strength enters the Stokeslet constants).  The points given are then this evaluator's own points plus those of the
+    all-reduce): it receives one flat complex vector, the structure factor (of each root part
+    in turn, see root_parts) followed by the d_rho strength sums over the own cubes (the total strength enters the Stokeslet constants).  The points given are then this evaluator's own points plus those of the
     cubes adjacent to its own cubes (the near field of Sec. 3.1.4-3.1.5 reaches no further),
     and targets should be its own points.
     """
@@ -238,12 +287,10 @@ def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_p
     # Tensor-product form of Eqs. structurefac and eval_tensor on the rectangle of
     # wavenumbers enclosing the retained set; dropped modes carry weight zero.
     local = [None] * nb
-    axes, keep, Wk, R = root_symbol(kern, geom, c, win)
+    parts = root_parts(kern, geom, c, win, tol)
+    R = parts[0][3]
     roots = forest.roots
     y = (s / 2) * nodes
-    Sc = [np.exp(-1j * np.outer(ax, y)) for ax in axes]            # conj(S(j, k)) [k, j]
-    shp = keep.shape
-    chi = np.zeros(shp + (kern.d_rho,), dtype=complex)
 
     def chi_proxy(b):
         """The root proxy charges entering the structure factor: only sources inside Omega count
@@ -285,28 +332,44 @@ def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_p
         Go = G[:N] >> BITS
         mine = np.isin(Go[:, 0] + Mc[0] * (Go[:, 1] + Mc[1] * Go[:, 2]), sorted(owned))
         rho_sum = rho_t[mine].sum(axis=0)
+    proxies = {}
     for b in roots:
         if owned is not None and cube_index(b) not in owned:
             continue
         pr = chi_proxy(b)
-        if pr is None:
-            continue
-        cb = center(b)
-        ph = np.exp(-1j * (axes[0][:, None, None] * cb[0] + axes[1][None, :, None] * cb[1]
-                           + axes[2][None, None, :] * cb[2]))
-        chi += ph[..., None] * np.einsum("ai,bj,ck,ijkd->abcd", Sc[0], Sc[1], Sc[2], pr, optimize=True)
+        if pr is not None:
+            proxies[b.id] = pr
+    chis, Scs = [], []
+    for axes, keep, Wk, _ in parts:
+        Sc = [np.exp(-1j * np.outer(ax, y)) for ax in axes]            # conj(S(j, k)) [k, j]
+        chi = np.zeros(keep.shape + (kern.d_rho,), dtype=complex)
+        for b in roots:
+            if b.id not in proxies:
+                continue
+            cb = center(b)
+            ph = np.exp(-1j * (axes[0][:, None, None] * cb[0] + axes[1][None, :, None] * cb[1]
+                               + axes[2][None, None, :] * cb[2]))
+            chi += ph[..., None] * np.einsum("ai,bj,ck,ijkd->abcd", Sc[0], Sc[1], Sc[2], proxies[b.id],
+                                             optimize=True)
+        chis.append(chi)
+        Scs.append(Sc)
     if chi_reduce is not None:
-        both = chi_reduce(np.concatenate([chi.ravel(), rho_sum.astype(complex)]))
-        chi = both[:chi.size].reshape(chi.shape)
-        rho_sum = both[chi.size:].real
-    uhat = np.einsum("abcud,abcd->abcu", Wk, chi)
+        flat = chi_reduce(np.concatenate([ch.ravel() for ch in chis] + [rho_sum.astype(complex)]))
+        o = 0
+        for i, ch in enumerate(chis):
+            chis[i] = flat[o:o + ch.size].reshape(ch.shape)
+            o += ch.size
+        rho_sum = flat[o:].real
     for b in roots:
-        cb = center(b)
-        ph = np.exp(1j * (axes[0][:, None, None] * cb[0] + axes[1][None, :, None] * cb[1]
-                          + axes[2][None, None, :] * cb[2]))
-        local[b.id] = np.einsum("ai,bj,ck,abcu->ijku", Sc[0].conj(), Sc[1].conj(), Sc[2].conj(),
-                                ph[..., None] * uhat, optimize=True).real
-    kk_count = int(keep.sum())
+        local[b.id] = 0.0
+    for (axes, keep, Wk, _), chi, Sc in zip(parts, chis, Scs):
+        uhat = np.einsum("abcud,abcd->abcu", Wk, chi)
+        for b in roots:
+            cb = center(b)
+            ph = np.exp(1j * (axes[0][:, None, None] * cb[0] + axes[1][None, :, None] * cb[1]
+                              + axes[2][None, None, :] * cb[2]))
+            local[b.id] = local[b.id] + np.einsum("ai,bj,ck,abcu->ijku", Sc[0].conj(), Sc[1].conj(), Sc[2].conj(),
+                                                  ph[..., None] * uhat, optimize=True).real
     if kernel == "stokeslet" and D == 0:
         # constant removed by the C^1 gauge of the truncated biharmonic kernel (symbols.B3_trunc)
         cst = sym.stokeslet_free_space_constant(R) * rho_sum
@@ -423,7 +486,8 @@ def evaluate(kernel, D, L, tol, points, strengths, n_s=250, grad=False, return_p
     res.forest = forest
     res.local = local
     res.proxy = proxy
-    res.plan = dict(c=c, p=p, nf=nf, nmodes=kk_count, R=R, nlevels=forest.nlevels)
+    res.plan = dict(c=c, p=p, nf=nf, nmodes=sum(int(pt[1].sum()) for pt in parts), nparts=len(parts), R=R,
+                    nlevels=forest.nlevels)
     return res
 
 

@@ -18,10 +18,23 @@ the PSWF band limit c and the Chebyshev order p.  Readings taken here:
   up to a relative 1e-12.  This reproduces every N_per of Tables 1 and 5 except
   where c/(2 pi) is itself an integer (a tie whose mode carries phi-hat(c)).
 * Free directions (Sec. 5.3, Eq. k1set-1p, k1k2set-2p): step dk = pi/R (the
-  Nyquist limit for a kernel truncated at R, Sec. 5.3), N = ceil(c/(nu_0 dk)),
-  n = -N..N; R = L_3 + nu_0 (D=2), sqrt((L_2+nu_0)^2+(L_3+nu_0)^2) (D=1), with
-  the free lengths rounded up to multiples of s (Sec. 5).  The truncated symbol
-  is used for every mode (Remark alpha_switch allows "truncated for all").
+  Nyquist limit for a kernel truncated at R, Sec. 5.3), n = -N..N with N the count of Eq.
+  k1k2set-2p, (N-1) dk <= c/nu_0 <= N dk; where c/(nu_0 dk) is an integer (to a relative
+  1e-12) both N = c/(nu_0 dk) and N + 1 satisfy it, and the larger is taken (it reproduces the
+  rotlet rows of Table 5 at 1e-3, c = 2 pi); otherwise N = ceil(c/(nu_0 dk)); R = L_3 + nu_0 (D=2), sqrt((L_2+nu_0)^2+(L_3+nu_0)^2) (D=1), with
+  the free lengths rounded up to multiples of s (Sec. 5).
+* Original vs truncated symbol for the nonzero periodic modes (D = 1, 2; Sec. 5.3, App. E):
+  the trapezoidal-rule error estimates of App. E (m = 1 for the harmonic kernels, Laplace and
+  rotlet; m = 2 with C_gamma = 0 for the biharmonic ones, Stokeslet and stresslet) at
+  alpha = alpha_min, |b| = L_j (the free extent of Omega_ext) and the Nyquist step of the
+  original kernel h_j = pi/L_j, for each free direction.  If every one is at most tol (D = 1:
+  Eq. app_1P_error_estimate sums the two; the sum would exceed 1e-3 on the unit cell for the
+  harmonic kernels, 1.9e-3, and keep the truncated symbol there, whereas the D = 1 free counts
+  of Tables 1 and 5 at 1e-3 are those of the original symbol's step -- the per-direction test
+  reproduces them), the original symbol on the step-pi/L_j grid serves every mode with
+  alpha != 0 and the truncated symbol on the step-pi/R grid the alpha = 0 modes (Eq.
+  ewald_far_es_1P_discr_b and its D = 2 analogue); otherwise the truncated symbol serves every
+  mode (Remark alpha_switch).
 * D = 0: one cube of side max L_i (Sec. 3.1.1 "box of equal sides"); the root
   far field is the free-space Fourier integral of the kernel truncated at
   R = sqrt(sum (L_i+nu_0)^2) (Sec. 3.1.3), on the same trapezoidal grid rule.
@@ -148,7 +161,7 @@ def root_modes(kernel, geom, c, return_axes=False):
         R = math.sqrt(sum((Lx[i] + nu0) ** 2 for i in range(3)))
     if D < 3:
         dk = math.pi / R
-        Nfree = int(math.ceil(K / dk * (1 - 1e-12)))
+        Nfree = free_count(K, dk)
     for i in range(3):
         if i < D:
             kmax = int(math.ceil(geom.L[i] * K / (2 * math.pi) * (1 - 1e-12)))
@@ -175,16 +188,56 @@ def root_modes(kernel, geom, c, return_axes=False):
     return kk, C, R, dk
 
 
+def free_count(K, h):
+    """N of the free set n = -N..N (Eqs. k1set-1p, k1k2set-2p): the smallest N with N h > K,
+    i.e. ceil(K/h), plus one where K/h is an integer to a relative 1e-12."""
+    return int(math.floor(K / h * (1 + 1e-12))) + 1
+
+
 def mode_counts(kernel, D, L, tol):
-    """(N_per_i, N_free_i, R) in the layout of Tables 1 and 5 (Sec. 6.1)."""
+    """(N_per_i, N_free_i, R) in the layout of Tables 1 and 5 (Sec. 6.1); N_free_i counts the
+    nodes of the alpha != 0 modes (those of the original symbol's step pi/L_j where the App. E
+    switch chooses it)."""
     c, p = c_and_p(kernel, tol)
     g = Geometry(D, L)
     kk, C, R, dk = root_modes(kernel, g, c)
+    orig = original_symbol_ok(kernel, g, tol)
     counts = []
     for i in range(3):
         if i < D:       # N_per_i = number of distinct periodic integers kept
             vals = np.unique(np.round(kk[:, i] / (2 * math.pi / g.L[i])).astype(int))
             counts.append(len(vals))
         else:           # N_free_i = 2N+1 trapezoidal nodes of Eq. k1set-1p / k1k2set-2p
-            counts.append(2 * int(math.ceil(c / g.nu0 / dk * (1 - 1e-12))) + 1)
+            h = math.pi / g.Lext[i] if orig else dk
+            counts.append(2 * free_count(c / g.nu0, h) + 1)
     return counts, R
+
+
+def free_error_estimate(m, alpha, s, h, C_gamma=0.0):
+    """App. E (Eqs. app_m1_error_estimate, app_m2_error_estimate): the error of the infinite
+    trapezoidal rule with step h for the model integral I_m(alpha, b), |b| = s, from the poles
+    at kappa = +-i alpha.  With x = 2 pi alpha / h and E = e^x - 1, cosh(alpha s)/E and
+    sinh(alpha s)/E are formed as exponentials of differences (no overflow for large x)."""
+    x = 2 * math.pi * alpha / h
+    den = -math.expm1(-x)                                  # E e^{-x}
+    ch = 0.5 * (math.exp(alpha * s - x) + math.exp(-alpha * s - x)) / den      # cosh(alpha s)/E
+    if m == 1:
+        return 2 * math.pi / alpha * ch
+    sh = 0.5 * (math.exp(alpha * s - x) - math.exp(-alpha * s - x)) / den      # sinh(alpha s)/E
+    Einv = math.exp(-x) / den                                                  # 1/E
+    return math.pi / alpha ** 3 * abs(ch - alpha * (s - alpha * C_gamma) * sh + x * ch * (1 + Einv))
+
+
+def original_symbol_ok(kernel, geom, tol):
+    """The App. E switch (Sec. 5.3): True if the original symbol may serve the alpha != 0 modes."""
+    D = geom.D
+    if D not in (1, 2):
+        return False
+    L = geom.L
+    alpha = 2 * math.pi / (max(L[0], L[1]) if D == 2 else L[0])      # Eq. alphamin
+    m = 2 if kernel in ("stokeslet", "stresslet") else 1
+    err = 0.0
+    for j in range(D, 3):
+        Lj = geom.Lext[j]
+        err = max(err, free_error_estimate(m, alpha, Lj, math.pi / Lj))
+    return err <= tol

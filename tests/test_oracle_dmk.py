@@ -500,3 +500,35 @@ def test_separate_targets_stokeslet_3p_vs_ewald():
     pts = np.vstack([y, x])
     e = ewald.stokeslet_ewald_3p(pts, pts, np.vstack([np.zeros((30, 3)), f]), L, 0.25)[:30]
     assert rel(r.u, e) < 1e-8
+
+
+@pytest.mark.parametrize("D,L,tol", [(2, [1, 1, 4], 1e-6), (1, [1, 4, 4], 1e-6), (2, [1, 1, 1], 1e-3),
+                                     (1, [1, 1, 1], 1e-3)])
+def test_original_symbol_switch_vs_ewald(D, L, tol):
+    """With the App. E switch on (original symbol on the step-pi/L_j grid for alpha != 0,
+    truncated zero modes on the step-pi/R grid, Sec. 5.3) the Laplace sum stays within the
+    tolerance of the Ewald sum."""
+    from oracle.params import Geometry, original_symbol_ok
+    assert original_symbol_ok("laplace", Geometry(D, L), tol)
+    N = 80
+    x = workloads.mixed_points(N, L, seed=431 + D)
+    q = workloads.neutral_charges(N, seed=432 + D)
+    r = evaluate("laplace", D, L, tol, x, q, n_s=12, grad=True)
+    assert r.plan["nparts"] == 2
+    ue, ge = ewald.laplace_reference(D, L, x, q, grad=True)
+    assert rel(r.u[:, 0], ue) < tol
+    assert rel(r.grad[:, :, 0], ge) < 3 * tol
+
+
+@pytest.mark.parametrize("D,L", [(2, [1, 1, 3]), (1, [1, 3, 3])])
+def test_original_symbol_switch_stokeslet_vs_ewald(D, L):
+    """The same for the Stokeslet (m = 2 estimate) against Hasimoto's split, at 1e-9."""
+    from oracle.params import Geometry, original_symbol_ok
+    assert original_symbol_ok("stokeslet", Geometry(D, L), 1e-9)
+    N = 40
+    x = workloads.mixed_points(N, L, seed=441 + D, D=D)
+    f = workloads.stokes_strengths("stokeslet", N, seed=442 + D)
+    r = evaluate("stokeslet", D, L, 1e-9, x, f, n_s=12)
+    assert r.plan["nparts"] == 2
+    e = (ewald.stokeslet_ewald_2p if D == 2 else ewald.stokeslet_ewald_1p)(x, x, f, L, 0.2 * L[0])
+    assert rel(r.u, e) < 1e-8
