@@ -227,9 +227,17 @@ dmk_status_t dmk_get_stats(dmk_plan_t plan, dmk_stats_t* out);
 dmk_status_t dmk_set_timing(dmk_plan_t plan, int enable);
 
 /* Plan parameters computed on the host only (no device call): the values dmk_plan would use.
- * n_axis[i] = wavenumbers on root axis i (periodic: 2 ceil(L_i c/(2 pi nu_0)) + 1 integers,
- * Eq. kintmax; free: 2 ceil(c/(nu_0 dk)) + 1 trapezoidal nodes, Sec. 5.3); R = truncation radius
- * (0 for D = 3); fit_terms_fp64/fp32 = Chebyshev terms of the residual function q per path. */
+ * n_axis[i] = wavenumbers on root axis i of the first root part (periodic: 2 ceil(L_i c/(2 pi
+ * nu_0)) + 1 integers, Eq. kintmax; free: 2 N + 1 trapezoidal nodes of step dk = pi/R with N
+ * the smallest integer such that N dk > c/nu_0, Eqs. k1set-1p, k1k2set-2p); R = truncation radius
+ * (0 for D = 3); n_root_modes = retained modes of all root parts; fit_terms_fp64/fp32 =
+ * Chebyshev terms of the residual function q per path.
+ * Root parts (D = 1, 2; Sec. 5.3 and the error estimates of App. E): where the trapezoidal
+ * error estimate of the original kernel at the smallest nonzero periodic wavenumber, with its
+ * Nyquist step pi/L_j, is at most tol in every free direction j, the modes with a nonzero
+ * periodic wavenumber use the original symbol on that step (the second part) and the first part
+ * keeps only the zero periodic wavenumber with the truncated symbols; otherwise one part, the
+ * truncated symbol for every mode. */
 typedef struct {
     double c, s, R, dk;
     int32_t p, n_f, n_root_modes, fit_terms_fp64, fit_terms_fp32;
@@ -253,7 +261,8 @@ dmk_status_t dmk_plan_info(dmk_kernel_t k, int D, const double L[3], double tol,
  *              "precomputed polynomial approximations"): series q, f, g, dq/ds, df/ds, dg/ds of
  *              s = r^2/nu^2, with q(s) = int_0^r phi / r, f(s) = phi(r), g(s) = phi'(r)/r; 256
  *              intervals each, 4 coefficients per interval, index ((series 256 + i) 4 + c);
- *              X(s) = c0 + u (c1 + u (c2 + u c3)) with u = 256 s - i. */
+ *              X(s) = c0 + u (c1 + u (c2 + u c3)) with u = 256 s - i;
+ *   which = 5, 6: as 0 and 1 for the second root part (no doubles when there is none). */
 dmk_status_t dmk_plan_table(dmk_kernel_t k, int D, const double L[3], double tol, int which, double* out,
                             int64_t cap, int64_t* n);
 

@@ -62,6 +62,8 @@ struct dmk_plan_s {
     Tab<float> tab32{};
     void* d_root = nullptr;
     RootTab root{};
+    RootTab root2{};                // second root part (original symbol), nmode = 0 if none
+    void* d_root2 = nullptr;
     double* d_self = nullptr;      // self_val then self_grad
     int* d_cube = nullptr;         // non-exact tilings: cube classes (Mtot), then the cut-cube count and list
     // workspace
@@ -299,7 +301,9 @@ dmk_status_t upload_tab(dmk_plan_s* plan, void** mem, Tab<T>& tab, double fit_to
     return DMK_OK;
 }
 
-dmk_status_t upload_root(dmk_plan_s* plan) {
+// one root part (wavenumber axes, weights on their rectangle) as a device table
+dmk_status_t upload_root_part(dmk_plan_s* plan, const std::vector<double>* kax, const std::vector<std::complex<double>>& Wr,
+                              void** dptr, RootTab& rt) {
     const PlanTables& P = plan->T;
     const int p = P.p;
     std::vector<double> h;
@@ -307,12 +311,12 @@ dmk_status_t upload_root(dmk_plan_s* plan) {
     size_t o_k[3], o_S[3];
     for (int i = 0; i < 3; ++i) {
         o_k[i] = h.size();
-        for (double v : P.kax[i]) h.push_back(v);
+        for (double v : kax[i]) h.push_back(v);
         pad();
     }
     for (int i = 0; i < 3; ++i) {
         o_S[i] = h.size();
-        for (double k : P.kax[i])
+        for (double k : kax[i])
             for (int j = 0; j < p; ++j) {
                 double ph = -k * (P.s / 2) * P.nodes[j];
                 h.push_back(std::cos(ph));
@@ -320,7 +324,7 @@ dmk_status_t upload_root(dmk_plan_s* plan) {
             }
     }
     size_t o_W = h.size();
-    for (auto& z : P.Wroot) { h.push_back(z.real()); h.push_back(z.imag()); }
+    for (auto& z : Wr) { h.push_back(z.real()); h.push_back(z.imag()); }
     size_t o_c = h.size();
     for (double v : P.root_const) h.push_back(v);
     // n3 mod M3 per x3 wavenumber (used when x3 is periodic: k3 = 2 pi n3 / L3)
@@ -328,19 +332,18 @@ dmk_status_t upload_root(dmk_plan_s* plan) {
     {
         const int M3 = std::max(1, P.M[2]);
         const double L3 = P.L[2];
-        for (double k : P.kax[2]) {
+        for (double k : kax[2]) {
             const long long n3 = std::llround(k * L3 / (2 * 3.14159265358979323846));
             h.push_back((double)(((n3 % M3) + M3) % M3));
         }
     }
-    cudaError_t e = cudaMalloc(&plan->d_root, h.size() * sizeof(double));
+    cudaError_t e = cudaMalloc(dptr, h.size() * sizeof(double));
     if (e != cudaSuccess) { plan->err = "root table allocation failed"; return DMK_ERR_OOM; }
     ++plan->n_allocs;
-    e = cudaMemcpy(plan->d_root, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(*dptr, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { plan->err = cudaGetErrorString(e); return DMK_ERR_CUDA; }
-    double* base = (double*)plan->d_root;
-    RootTab& rt = plan->root;
-    rt.n1 = (int)P.kax[0].size(); rt.n2 = (int)P.kax[1].size(); rt.n3 = (int)P.kax[2].size();
+    double* base = (double*)*dptr;
+    rt.n1 = (int)kax[0].size(); rt.n2 = (int)kax[1].size(); rt.n3 = (int)kax[2].size();
     rt.nmode = rt.n1 * rt.n2 * rt.n3;
     for (int i = 0; i < 3; ++i) {
         rt.kax[i] = base + o_k[i];
@@ -349,6 +352,15 @@ dmk_status_t upload_root(dmk_plan_s* plan) {
     rt.W = reinterpret_cast<const Cx<double>*>(base + o_W);
     rt.rconst = base + o_c;
     rt.nmod3 = base + o_n;
+    return DMK_OK;
+}
+
+dmk_status_t upload_root(dmk_plan_s* plan) {
+    const PlanTables& P = plan->T;
+    CKS(upload_root_part(plan, P.kax, P.Wroot, &plan->d_root, plan->root));
+    plan->root2 = RootTab{};
+    if (P.original_symbol) CKS(upload_root_part(plan, P.kax2, P.Wroot2, &plan->d_root2, plan->root2));
+    cudaError_t e;
     // self tables
     std::vector<double> sv(P.self_val);
     sv.insert(sv.end(), P.self_grad.begin(), P.self_grad.end());
@@ -1011,15 +1023,23 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* p
     // ---- (6) root far field (FP64) ----------------------------------------------------------
     {
         const RootTab& rt = plan->root;
+        // the second part (original symbol for alpha != 0, App. E switch), if any
+        const RootTab& rt2 = plan->root2;
+        const int nparts = rt2.nmode > 0 ? 2 : 1;
+        const int nmode_max = std::max(rt.nmode, rt2.nmode);
         void *vchi, *vuh, *vrsc;
-        CKS(ensure(plan, B_CHI, (size_t)Mtot * drho * rt.nmode * sizeof(Cx<double>), &vchi));
-        CKS(ensure(plan, B_UHAT, (size_t)du * rt.nmode * sizeof(Cx<double>), &vuh));
+        CKS(ensure(plan, B_CHI, (size_t)Mtot * drho * (rt.nmode + rt2.nmode) * sizeof(Cx<double>), &vchi));
+        CKS(ensure(plan, B_UHAT, (size_t)du * nmode_max * sizeof(Cx<double>), &vuh));
         // scratch: forward B1 (n1 p^2) + B2 (n1 n2 p) per (cube, strength component); backward
         // G (nmode) + C2 (n1 n2 p) + C1 (n1 p^2) per (cube, potential component)
         const size_t f1 = (size_t)rt.n1 * p * p, f2 = (size_t)rt.n1 * rt.n2 * p;
         const int jf = Mtot * drho, jb = Mtot * du;
-        const size_t nfwd = (size_t)jf * (f1 + f2), nbwd = (size_t)jb * (rt.nmode + f2 + f1);
-        CKS(ensure(plan, B_SCRATCH, std::max(nfwd, nbwd) * sizeof(Cx<double>), &vrsc));
+        size_t nscr = std::max((size_t)jf * (f1 + f2), (size_t)jb * (rt.nmode + f2 + f1));
+        if (nparts == 2) {
+            const size_t g1 = (size_t)rt2.n1 * p * p, g2 = (size_t)rt2.n1 * rt2.n2 * p;
+            nscr = std::max(nscr, std::max((size_t)jf * (g1 + g2), (size_t)jb * (rt2.nmode + g2 + g1)));
+        }
+        CKS(ensure(plan, B_SCRATCH, nscr * sizeof(Cx<double>), &vrsc));
         Cx<double>* r0 = (Cx<double>*)vrsc;
         Cx<double>* chi = (Cx<double>*)vchi;
         Cx<double>* uh = (Cx<double>*)vuh;
@@ -1103,19 +1123,34 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* p
                                                                                      local);
             launches += 9;
         } else {
-        k_root_fwd1<T><<<blocks((int64_t)jf * f1), 128, 0, st>>>(jf, p, rt, rproxy, r0);
-        k_root_fwd2<<<blocks((int64_t)jf * f2), 128, 0, st>>>(jf, p, rt, r0, r0 + (size_t)jf * f1);
-        k_root_fwd3<<<blocks((int64_t)jf * rt.nmode), 128, 0, st>>>(jf, drho, p, g, rt, r0 + (size_t)jf * f1, chi);
-        CKS(reduce_chi(plan, sh, chi, (int64_t)2 * Mtot * drho * rt.nmode, d_sums));
-        k_root_apply<<<nblk(rt.nmode, 128), 128, 0, st>>>(Mtot, drho, du, rt, chi, uh);
-        Cx<double>* G = r0;
-        Cx<double>* C2 = G + (size_t)jb * rt.nmode;
-        Cx<double>* C1 = C2 + (size_t)jb * f2;
-        k_root_bwd0<<<blocks((int64_t)jb * rt.nmode), 128, 0, st>>>(jb, du, g, rt, uh, G);
-        k_root_bwd1<<<blocks((int64_t)jb * f2), 128, 0, st>>>(jb, p, rt, G, C2);
-        k_root_bwd2<<<blocks((int64_t)jb * f1), 128, 0, st>>>(jb, p, rt, C2, C1);
-        k_root_bwd3<T><<<blocks((int64_t)jb * p * p * p), 128, 0, st>>>(jb, du, p, rt, C1, d_sums, drho, local);
-        launches += 8;
+        // per part: structure factor of every cube (chi of part 1 after that of part 0), one
+        // reduction of both (sharded evaluations), then the evaluation; part 1 adds to part 0
+        const RootTab* parts[2] = {&rt, &rt2};
+        Cx<double>* chis[2] = {chi, chi + (size_t)Mtot * drho * rt.nmode};
+        for (int ip = 0; ip < nparts; ++ip) {
+            const RootTab& r = *parts[ip];
+            const size_t h1 = (size_t)r.n1 * p * p, h2 = (size_t)r.n1 * r.n2 * p;
+            k_root_fwd1<T><<<blocks((int64_t)jf * h1), 128, 0, st>>>(jf, p, r, rproxy, r0);
+            k_root_fwd2<<<blocks((int64_t)jf * h2), 128, 0, st>>>(jf, p, r, r0, r0 + (size_t)jf * h1);
+            k_root_fwd3<<<blocks((int64_t)jf * r.nmode), 128, 0, st>>>(jf, drho, p, g, r, r0 + (size_t)jf * h1,
+                                                                        chis[ip]);
+            launches += 3;
+        }
+        CKS(reduce_chi(plan, sh, chi, (int64_t)2 * Mtot * drho * (rt.nmode + rt2.nmode), d_sums));
+        for (int ip = 0; ip < nparts; ++ip) {
+            const RootTab& r = *parts[ip];
+            const size_t h1 = (size_t)r.n1 * p * p, h2 = (size_t)r.n1 * r.n2 * p;
+            k_root_apply<<<nblk(r.nmode, 128), 128, 0, st>>>(Mtot, drho, du, r, chis[ip], uh);
+            Cx<double>* G = r0;
+            Cx<double>* C2 = G + (size_t)jb * r.nmode;
+            Cx<double>* C1 = C2 + (size_t)jb * h2;
+            k_root_bwd0<<<blocks((int64_t)jb * r.nmode), 128, 0, st>>>(jb, du, g, r, uh, G);
+            k_root_bwd1<<<blocks((int64_t)jb * h2), 128, 0, st>>>(jb, p, r, G, C2);
+            k_root_bwd2<<<blocks((int64_t)jb * h1), 128, 0, st>>>(jb, p, r, C2, C1);
+            k_root_bwd3<T><<<blocks((int64_t)jb * p * p * p), 128, 0, st>>>(jb, du, p, r, C1, d_sums, drho, local,
+                                                                             ip);
+            launches += 5;
+        }
         }
     }
     rec(3);
@@ -1458,7 +1493,7 @@ dmk_status_t dmk_eval_shard(dmk_plan_t plan, int64_t N, int64_t n_own, const dou
         const bool fft = plan->T.D == 3 && plan->geo.M[0] == 1 && plan->geo.M[1] == 1 &&
                          plan->geo.M[2] >= kRootFftMin && plan->geo.M[2] <= kRootFftMax;
         const int Mtot = plan->geo.M[0] * plan->geo.M[1] * plan->geo.M[2];
-        const int64_t n = (int64_t)2 * (fft ? 1 : Mtot) * plan->T.d_rho * rt.nmode;
+        const int64_t n = (int64_t)2 * (fft ? 1 : Mtot) * plan->T.d_rho * (rt.nmode + plan->root2.nmode);
         void* vchi;
         CKS(ensure(plan, B_CHI, (size_t)(n + 2 * plan->T.d_rho) * sizeof(double), &vchi));
         CK(cudaMemsetAsync(vchi, 0, (size_t)(n + 2 * plan->T.d_rho) * sizeof(double), plan->stream));
@@ -1623,6 +1658,7 @@ dmk_status_t dmk_destroy(dmk_plan_t plan) {
     if (plan->d_tab64) cudaFree(plan->d_tab64);
     if (plan->d_tab32) cudaFree(plan->d_tab32);
     if (plan->d_root) cudaFree(plan->d_root);
+    if (plan->d_root2) cudaFree(plan->d_root2);
     if (plan->d_self) cudaFree(plan->d_self);
     if (plan->d_cube) cudaFree(plan->d_cube);
     if (plan->side) {
@@ -1681,8 +1717,12 @@ dmk_status_t dmk_plan_table(dmk_kernel_t k, int D, const double L[3], double tol
         v.insert(v.end(), T.phihat_samples.begin(), T.phihat_samples.end());
     } else if (which == 4) {
         v = herm_tables(T);
+    } else if (which == 5) {
+        for (int i = 0; i < 3; ++i) v.insert(v.end(), T.kax2[i].begin(), T.kax2[i].end());
+    } else if (which == 6) {
+        for (auto& z : T.Wroot2) { v.push_back(z.real()); v.push_back(z.imag()); }
     } else {
-        g_plan_error = "which must be 0..4";
+        g_plan_error = "which must be 0..6";
         return DMK_ERR_INVALID_ARG;
     }
     *n = (int64_t)v.size();

@@ -47,7 +47,13 @@ struct PlanTables {
     // root: rectangle axes and weights W[((i1 * n2 + i2) * n3 + i3) * du * drho + j * drho + a]
     std::vector<double> kax[3];
     std::vector<std::complex<double>> Wroot;
-    int n_root_modes = 0;
+    // second root part (the App. E switch, Sec. 5.3): when the original symbol serves the
+    // alpha != 0 modes, kax / Wroot hold the alpha = 0 line (truncated zero-mode symbols, step
+    // pi/R) and kax2 / Wroot2 the rectangle of the original symbol (step pi/L_j); else empty
+    bool original_symbol = false;
+    std::vector<double> kax2[3];
+    std::vector<std::complex<double>> Wroot2;
+    int n_root_modes = 0;           // retained modes of both parts
     double R = 0;                   // truncation radius (D < 3)
     std::vector<double> root_const; // d_u x d_rho constant added per unit summed strength
     // self correction at level 0 (scale 1/nu for the value, 1/nu^3 for the gradient)

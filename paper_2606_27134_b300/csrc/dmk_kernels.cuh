@@ -847,7 +847,7 @@ __global__ void k_root_bwd2(int jobs, int p, RootTab rt, const Cx<double>* __res
 
 template <class T>
 __global__ void k_root_bwd3(int jobs, int du, int p, RootTab rt, const Cx<double>* __restrict__ C1,
-                            const double* __restrict__ rho_sum, int drho, T* __restrict__ local) {
+                            const double* __restrict__ rho_sum, int drho, T* __restrict__ local, int add) {
     const int p2 = p * p, p3 = p2 * p;
     const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (id >= (int64_t)jobs * p3) return;
@@ -860,6 +860,11 @@ __global__ void k_root_bwd3(int jobs, int du, int p, RootTab rt, const Cx<double
         const Cx<double> f = cconj(rt.S[0][k * p + j1]);
         const Cx<double> b = c[(size_t)k * p2];
         v += f.x * b.x - f.y * b.y;
+    }
+    // add: a second root part, added to the first (whose write carried the constant)
+    if (add) {
+        local[(size_t)job * p3 + e] = (T)((double)local[(size_t)job * p3 + e] + v);
+        return;
     }
     double cst = 0;
     for (int a = 0; a < drho; ++a) cst += rt.rconst[j * drho + a] * rho_sum[a];

@@ -296,6 +296,24 @@ double B3t(double k, double R) {
 
 int ceil_guard(double x) { return (int)std::ceil(x * (1.0 - 1e-12)); }
 
+// N of the free node set n = -N..N (Eqs. k1set-1p, k1k2set-2p: (N-1) h <= K <= N h): the
+// smallest N with N h > K, i.e. ceil(K/h) and one more where K/h is an integer (relative 1e-12)
+int free_count(double K, double h) { return (int)std::floor(K / h * (1.0 + 1e-12)) + 1; }
+
+// App. E (Eqs. app_m1_error_estimate, app_m2_error_estimate): the pole estimate of the error of
+// the infinite trapezoidal rule with step h for the model integral I_m(alpha, b), |b| = s;
+// cosh(alpha s)/E and sinh(alpha s)/E (E = e^x - 1, x = 2 pi alpha / h) formed as exponentials of
+// differences.  C_gamma = 0 (the biharmonic screening; m = 1 does not use it).
+double free_error_estimate(int m, double alpha, double s, double h) {
+    const double x = 2 * kPi * alpha / h;
+    const double den = -std::expm1(-x);
+    const double ch = 0.5 * (std::exp(alpha * s - x) + std::exp(-alpha * s - x)) / den;
+    if (m == 1) return 2 * kPi / alpha * ch;
+    const double sh = 0.5 * (std::exp(alpha * s - x) - std::exp(-alpha * s - x)) / den;
+    const double einv = std::exp(-x) / den;
+    return kPi / (alpha * alpha * alpha) * std::fabs(ch - alpha * s * sh + x * ch * (1 + einv));
+}
+
 }  // namespace
 
 dmk_status_t build_plan_tables(int kernel, int D, const double Lin[3], double tol, PlanTables& T,
@@ -491,7 +509,7 @@ dmk_status_t build_plan_tables(int kernel, int D, const double Lin[3], double to
         T.R = R;
         T.dk = 0;
         int nfree = 0;
-        if (D < 3) { dk = kPi / R; nfree = ceil_guard(K / dk); T.dk = dk; }
+        if (D < 3) { dk = kPi / R; nfree = free_count(K, dk); T.dk = dk; }
         for (int i = 0; i < 3; ++i) {
             T.kax[i].clear();
             if (i < D) {
@@ -582,6 +600,73 @@ dmk_status_t build_plan_tables(int kernel, int D, const double Lin[3], double to
                     }
                     for (int e = 0; e < nm; ++e) out[e] *= C * gam;
                 }
+        // The App. E switch (Sec. 5.3): the estimate at alpha_min (Eq. alphamin), |b| = L_j and the
+        // original kernel's Nyquist step pi/L_j, for each free direction (m = 1 for the harmonic
+        // kernels, 2 for the biharmonic ones).  At most tol in every free direction: the original
+        // symbol serves alpha != 0 on that step, the truncated rectangle is cut to its alpha = 0
+        // line.
+        T.original_symbol = false;
+        for (int i = 0; i < 3; ++i) { T.kax2[i].clear(); }
+        T.Wroot2.clear();
+        if (D == 1 || D == 2) {
+            const double amin = 2 * kPi / (D == 2 ? std::max(Lin[0], Lin[1]) : Lin[0]);
+            double est = 0;
+            for (int j = D; j < 3; ++j) est = std::max(est, free_error_estimate(bih ? 2 : 1, amin, Lext[j], kPi / Lext[j]));
+            T.original_symbol = est <= tol;
+        }
+        if (T.original_symbol) {
+            // part 1: the alpha = 0 line of the truncated rectangle (periodic axes cut to k = 0)
+            const int m1 = n1 / 2, m2 = D == 2 ? n2 / 2 : 0;
+            const int z1 = 1, z2 = D == 2 ? 1 : n2;
+            std::vector<cd> Wz((size_t)z1 * z2 * n3 * nm);
+            int nz = 0;
+            for (int i2 = 0; i2 < z2; ++i2)
+                for (int i3 = 0; i3 < n3; ++i3) {
+                    const cd* src = &T.Wroot[(((size_t)m1 * n2 + (D == 2 ? m2 : i2)) * n3 + i3) * nm];
+                    cd* dst = &Wz[((size_t)i2 * n3 + i3) * nm];
+                    for (int e = 0; e < nm; ++e) dst[e] = src[e];
+                    const double k[3] = {0.0, D == 2 ? 0.0 : T.kax[1][i2], T.kax[2][i3]};
+                    const double kn = std::sqrt(k[1] * k[1] + k[2] * k[2]);
+                    if (kn * nu0 <= T.c * (1 + 1e-12)) ++nz;
+                }
+            T.kax[0] = {0.0};
+            if (D == 2) T.kax[1] = {0.0};
+            T.Wroot.swap(Wz);
+            // part 2: the original symbol D-hat(k) gamma-hat(|k| nu_0)/|k|^{2,4}, alpha != 0, on the
+            // free step pi/L_j, with C^{DP} of that step
+            double C2 = 0;
+            std::vector<double> hs;
+            for (int i = 0; i < 3; ++i) {
+                if (i < D) {
+                    int km = ceil_guard(Lin[i] * K / (2 * kPi));
+                    for (int n = -km; n <= km; ++n) T.kax2[i].push_back(2 * kPi * n / Lin[i]);
+                } else {
+                    const double h = kPi / Lext[i];
+                    const int nf2 = free_count(K, h);
+                    for (int n = -nf2; n <= nf2; ++n) T.kax2[i].push_back(h * n);
+                    hs.push_back(h);
+                }
+            }
+            C2 = D == 2 ? hs[0] / (Lin[0] * Lin[1] * 2 * kPi) : hs[0] * hs[1] / (Lin[0] * 4 * kPi * kPi);
+            const int q1 = (int)T.kax2[0].size(), q2 = (int)T.kax2[1].size(), q3 = (int)T.kax2[2].size();
+            T.Wroot2.assign((size_t)q1 * q2 * q3 * nm, cd(0));
+            int no = 0;
+            for (int i1 = 0; i1 < q1; ++i1)
+                for (int i2 = 0; i2 < q2; ++i2)
+                    for (int i3 = 0; i3 < q3; ++i3) {
+                        double k[3] = {T.kax2[0][i1], T.kax2[1][i2], T.kax2[2][i3]};
+                        const double kn = std::sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+                        const double alpha = D == 2 ? std::sqrt(k[0] * k[0] + k[1] * k[1]) : std::fabs(k[0]);
+                        if (kn * nu0 > T.c * (1 + 1e-12) || alpha == 0) continue;
+                        ++no;
+                        const double gam = bih ? W.gammaB(kn * nu0) : W.phihat(kn * nu0);
+                        op_symbol(kernel, k, op.data());
+                        const double base = C2 * gam / std::pow(kn, bih ? 4 : 2);
+                        cd* out = &T.Wroot2[(((size_t)i1 * q2 + i2) * q3 + i3) * nm];
+                        for (int e = 0; e < nm; ++e) out[e] = op[e] * base;
+                    }
+            T.n_root_modes = nz + no;
+        }
         // constants added to the root grid per unit summed strength
         T.root_const.assign(nm, 0.0);
         if (kernel == DMK_STOKESLET && D == 1) {        // Remark stokeslet_const_corr

@@ -43,6 +43,12 @@ CASES = [
     ("rotlet-3P-nonexact", "rotlet", 3, [1, 1.3, 1.7], 1e-6, 500, 30, "mixed", "stokes"),
     ("stresslet-3P-nonexact", "stresslet", 3, [2, 1.3, 1.7], 1e-6, 500, 30, "mixed", "stokes"),
     ("stokeslet-2P-nonexact", "stokeslet", 2, [1.3, 1, 0.5], 1e-6, 500, 30, "mixed", "stokes"),
+    # free extents a few periods long and the unit cell at 1e-3: the App. E switch gives the
+    # original symbol to the modes with a nonzero periodic wavenumber (two root parts)
+    ("laplace-2P-tall-original", "laplace", 2, [1, 1, 4], 1e-6, 1500, 40, "mixed", "neutral"),
+    ("stokeslet-1P-original", "stokeslet", 1, [1, 3, 3], 1e-6, 1000, 30, "mixed", "stokes"),
+    ("rotlet-2P-original", "rotlet", 2, [1, 1, 3], 1e-6, 800, 30, "mixed", "stokes"),
+    ("laplace-1P-1e-3-original", "laplace", 1, [1, 1, 1], 1e-3, 1500, 40, "uniform", "neutral"),
     # the singly periodic pipe of Sec. 6 (trapezoidal nodes on a cylinder around x1), at the
     # three tolerances of its figure, 1000 points per unit length
     ("stokeslet-1P-cylinder-1e-6", "stokeslet", 1, [2, 1, 1], 1e-6, 2000, 40, "cylinder", "stokes"),

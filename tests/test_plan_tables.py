@@ -7,14 +7,16 @@ No device is used.
 import numpy as np
 import pytest
 
-from oracle.dmk import root_symbol
+from oracle.dmk import root_parts
 from oracle.kernels import Kernel
 from oracle.params import Geometry, c_and_p, n_f, root_modes, TOL_ROWS
 from oracle.pswf import PSWFWindow
 from paper_2606_27134_b300 import dmk
 
 GEOMS = [(3, [1, 1, 1]), (3, [1, 1, 16]), (2, [1, 1, 0.25]), (2, [1, 2, 1]), (1, [8, 1, 1]), (1, [1, 1, 1]),
-         (0, [1, 1, 1]), (0, [0.5, 2, 1])]
+         (0, [1, 1, 1]), (0, [0.5, 2, 1]),
+         # free extents a few periods long: the original symbol for alpha != 0 (App. E switch)
+         (2, [1, 1, 4]), (1, [1, 4, 3]), (2, [1.5, 1, 5])]
 
 
 @pytest.mark.parametrize("kernel", ["laplace", "stokeslet", "stresslet", "rotlet"])
@@ -26,8 +28,9 @@ def test_parameters(kernel, tol):
         g = Geometry(D, L)
         assert info["c"] == pytest.approx(c, rel=1e-15) and info["p"] == p and info["n_f"] == n_f(c)
         assert info["M"] == list(g.M) and info["s"] == g.s
+        parts = root_parts(Kernel(kernel), g, c, PSWFWindow(c), tol)
+        assert info["n_root_modes"] == sum(int(pt[1].sum()) for pt in parts)
         kk, C, R, dk = root_modes(kernel, g, c)
-        assert info["n_root_modes"] == kk.shape[0]
         if D < 3:
             assert info["R"] == pytest.approx(R, rel=1e-15)
 
@@ -39,15 +42,17 @@ def test_root_weights(kernel, D, L):
     c, p = c_and_p(kernel, tol)
     g = Geometry(D, L)
     K = Kernel(kernel)
-    axes, keep, W, R = root_symbol(K, g, c, PSWFWindow(c))
-    ax = dmk.plan_table(kernel, D, L, tol, 0)
-    n = [len(a) for a in axes]
-    assert len(ax) == sum(n)
-    assert np.allclose(ax, np.concatenate(axes), rtol=1e-15, atol=1e-15)
-    w = dmk.plan_table(kernel, D, L, tol, 1)
-    w = (w[0::2] + 1j * w[1::2]).reshape(n[0], n[1], n[2], K.d_u, K.d_rho)
-    scale = np.max(np.abs(W))
-    assert np.max(np.abs(w - W)) <= 1e-12 * scale
+    parts = root_parts(K, g, c, PSWFWindow(c), tol)
+    assert len(dmk.plan_table(kernel, D, L, tol, 5)) == (0 if len(parts) == 1 else sum(len(a) for a in parts[1][0]))
+    for ip, (axes, keep, W, R) in enumerate(parts):
+        ax = dmk.plan_table(kernel, D, L, tol, 5 * ip)
+        n = [len(a) for a in axes]
+        assert len(ax) == sum(n)
+        assert np.allclose(ax, np.concatenate(axes), rtol=1e-15, atol=1e-15)
+        w = dmk.plan_table(kernel, D, L, tol, 1 + 5 * ip)
+        w = (w[0::2] + 1j * w[1::2]).reshape(n[0], n[1], n[2], K.d_u, K.d_rho)
+        scale = np.max(np.abs(W))
+        assert np.max(np.abs(w - W)) <= 1e-12 * scale
 
 
 @pytest.mark.parametrize("kernel", ["laplace", "stokeslet", "stresslet", "rotlet"])
