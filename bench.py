@@ -342,7 +342,7 @@ def main():
                              rf.MAX_SM_GHZ, rf.fp32_peak_tflops()),
             "per_unit": "%d FLOP per visited pair (22 + d_q, d_q = %d)" % (rf.pair_flops("laplace", {"n_pairs": 1,
                         "fit_terms": st["fit_terms"]}, grad=True), max(int(st["fit_terms"]) - 1, 0)),
-            "second_kernel": {"kernel": "k_leafexp<float, Laplace, grad>", "ms": exp_ms, "achieved": exp_tf,
+            "second_kernel": {"kernel": "k_leafexp_parent<float, Laplace, grad>", "ms": exp_ms, "achieved": exp_tf,
                               "frac": (exp_tf / pk) if exp_tf else None}}
     fp64_line = {"value": world * N / (fp64_ms / 1e3), "unit": "targets/s", "ms_per_step": fp64_ms}
     if "fp64" in prec_results:
@@ -375,7 +375,6 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             from oracle.dmk import evaluate
-            from threadpoolctl import threadpool_limits
             Ns = 4000
             xs = Wl.uniform_points(Ns, W["L"], 12345)
             qs = Wl.uniform_charges(Ns, 12346)
@@ -383,11 +382,18 @@ def main():
             evaluate("laplace", 2, W["L"], W["tol"], xs, qs, n_s=W["n_s"], grad=True)
             dt = time.perf_counter() - t
             # the oracle is Python loops over boxes with numpy contractions: only the BLAS calls
-            # inside numpy use more than one thread; timed again with BLAS on one thread
-            with threadpool_limits(limits=1):
-                t = time.perf_counter()
-                evaluate("laplace", 2, W["L"], W["tol"], xs, qs, n_s=W["n_s"], grad=True)
-                dt1 = time.perf_counter() - t
+            # inside numpy use more than one thread; timed again with BLAS on one thread (in a
+            # child process whose BLAS is limited before numpy loads)
+            code = ("import time, sys; sys.path.insert(0, %r); from oracle.dmk import evaluate; "
+                    "from paper_2606_27134_b300 import workloads as Wl; L = %r; "
+                    "x = Wl.uniform_points(%d, L, 12345); q = Wl.uniform_charges(%d, 12346); "
+                    "t = time.perf_counter(); evaluate('laplace', 2, L, %r, x, q, n_s=%d, grad=True); "
+                    "print(time.perf_counter() - t)" % (os.path.dirname(os.path.abspath(__file__)), list(W["L"]),
+                                                        Ns, Ns, W["tol"], W["n_s"]))
+            env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                       CUDA_VISIBLE_DEVICES="")
+            r1 = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+            dt1 = float(r1.stdout.strip().splitlines()[-1])
             line["cpu_baseline"] = {"value": Ns / dt, "unit": "targets/s", "cores": len(os.sched_getaffinity(0)),
                                     "kind": "oracle", "value_1_thread": Ns / dt1,
                                     "sample": f"oracle (FP64 numpy, single-threaded Python with numpy's BLAS "

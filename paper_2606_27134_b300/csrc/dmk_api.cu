@@ -891,6 +891,9 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* p
     lo.self_val = plan->d_self;
     lo.self_grad = plan->d_self + P.d_u * P.d_rho;
     lo.pk = reinterpret_cast<const float4*>(pk);
+    // the truncated-kernel constants, formed after the root stage (k_root_const)
+    double* d_ucst = (double*)((char*)vmisc + 1664);
+    lo.ucst = d_ucst;
     const bool gr = grad != nullptr;
     bool fast_leaf = false, overlap = false;
     auto run_pair = [&](cudaStream_t sp) -> dmk_status_t {
@@ -1119,7 +1122,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* p
             k_rootfft_bwd1<<<blocks((int64_t)jbb * f2), 128, 0, st>>>(M3, du, p, g, rt, uh, C2);
             k_root_bwd2<<<blocks((int64_t)jbb * f1), 128, 0, st>>>(jbb, p, rt, C2, C1);
             k_rootfft_bwd3<<<blocks((int64_t)jbb * p * p * p), 128, 0, st>>>(jbb, p, rt, C1, Gs);
-            k_rootfft_idft<T><<<blocks((int64_t)M3 * du * p * p * p), 128, 0, st>>>(M3, du, p, rt, Gs, d_sums, drho,
+            k_rootfft_idft<T><<<blocks((int64_t)M3 * du * p * p * p), 128, 0, st>>>(M3, du, p, rt, Gs, nullptr, drho,
                                                                                      local);
             launches += 9;
         } else {
@@ -1147,12 +1150,14 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* p
             k_root_bwd0<<<blocks((int64_t)jb * r.nmode), 128, 0, st>>>(jb, du, g, r, uh, G);
             k_root_bwd1<<<blocks((int64_t)jb * h2), 128, 0, st>>>(jb, p, r, G, C2);
             k_root_bwd2<<<blocks((int64_t)jb * h1), 128, 0, st>>>(jb, p, r, C2, C1);
-            k_root_bwd3<T><<<blocks((int64_t)jb * p * p * p), 128, 0, st>>>(jb, du, p, r, C1, d_sums, drho, local,
+            k_root_bwd3<T><<<blocks((int64_t)jb * p * p * p), 128, 0, st>>>(jb, du, p, r, C1, nullptr, drho, local,
                                                                              ip);
             launches += 5;
         }
         }
     }
+    k_root_const<<<1, 32, 0, st>>>(du, drho, plan->root.rconst, d_sums, d_ucst);
+    ++launches;
     rec(3);
     // ---- (7) plane waves: outgoing for all non-leaf boxes, then translation + incoming ------
     if (n_nl > 0) {

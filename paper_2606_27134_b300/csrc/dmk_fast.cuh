@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(kLeaf2Threads) k_leaf2(int nleaf, const int* _
                 const double ks = KScale<K>::v;
                 const double* rt = out.rs + (int64_t)tg * DR;
                 for (int j = 0; j < DU; ++j) {
-                    double v = res[tt][j] + ks * accd[j];
+                    double v = res[tt][j] + ks * accd[j] + (out.ucst ? out.ucst[j] : 0.0);
                     for (int a = 0; a < DR; ++a) v -= out.self_val[j * DR + a] * inv_nuT * rt[a];
                     out.pot[(int64_t)oi * DU + j] = v;
                 }
@@ -1500,7 +1500,7 @@ __global__ void __launch_bounds__(kLeafExpThreads) k_leafexp(int nleaf, const in
                 const double* rt = out.rs + (int64_t)tg * DR;
 #pragma unroll
                 for (int j = 0; j < DU; ++j) {
-                    double v = (double)ev[j] + out.pot[(int64_t)oi * DU + j];
+                    double v = (double)ev[j] + out.pot[(int64_t)oi * DU + j] + (out.ucst ? out.ucst[j] : 0.0);
                     for (int a = 0; a < DR; ++a) v -= out.self_val[j * DR + a] * inv_nuT * rt[a];
                     out.pot[(int64_t)oi * DU + j] = v;
                 }
@@ -1672,7 +1672,7 @@ __global__ void __launch_bounds__(kLeafExpThreads) k_leafexp_parent(int n_nl, co
                     const int oi = out.perm[tg];
                     const double inv_nuT = 1.0 / rT;
                     const double* rt = out.rs + (int64_t)tg * DR;
-                    double vv = (double)S + out.pot[(int64_t)oi * DU + j];
+                    double vv = (double)S + out.pot[(int64_t)oi * DU + j] + (out.ucst ? out.ucst[j] : 0.0);
                     for (int a = 0; a < DR; ++a) vv -= out.self_val[j * DR + a] * inv_nuT * rt[a];
                     out.pot[(int64_t)oi * DU + j] = vv;
                     if (GRAD && out.grad) {

@@ -738,7 +738,7 @@ __global__ void k_root_eval(int M, int du, int p, Geo g, RootTab rt, const Cx<do
         }
         __syncthreads();
         double cst = 0;
-        for (int a = 0; a < drho; ++a) cst += rt.rconst[j * drho + a] * rho_sum[a];
+        if (rho_sum) for (int a = 0; a < drho; ++a) cst += rt.rconst[j * drho + a] * rho_sum[a];
         T* u = local + ((size_t)m * du + j) * p3;
         for (int e = threadIdx.x; e < p3; e += blockDim.x) {                // k1 -> j1, real part
             const int j1 = e / p2, r = e % p2;
@@ -867,8 +867,21 @@ __global__ void k_root_bwd3(int jobs, int du, int p, RootTab rt, const Cx<double
         return;
     }
     double cst = 0;
-    for (int a = 0; a < drho; ++a) cst += rt.rconst[j * drho + a] * rho_sum[a];
+    if (rho_sum) for (int a = 0; a < drho; ++a) cst += rt.rconst[j * drho + a] * rho_sum[a];
     local[(size_t)job * p3 + e] = (T)(v + cst);
+}
+
+// The constants of the truncated kernels (Remark stokeslet_const_corr; the C^1 gauge of the
+// D = 0 biharmonic kernel) times the total strength: ucst[j] = sum_a rconst[j][a] rho_sum[a].
+// They are added to the potentials in FP64 at the leaf write-back rather than to the root grids,
+// so that the FP32 expansions of the mixed path do not carry them (a constant has no gradient).
+__global__ void k_root_const(int du, int drho, const double* __restrict__ rconst, const double* __restrict__ rho_sum,
+                             double* __restrict__ ucst) {
+    const int j = threadIdx.x;
+    if (j >= du) return;
+    double v = 0;
+    for (int a = 0; a < drho; ++a) v += rconst[j * drho + a] * rho_sum[a];
+    ucst[j] = v;
 }
 
 // Root proxies entering the structure factor of a non-exact tiling (Sec. 4.3): the cube's own
@@ -991,7 +1004,7 @@ __global__ void k_rootfft_idft(int M, int du, int p, RootTab rt, const Cx<double
         v += cs * gsv.x - sn * gsv.y;
     }
     double cst = 0;
-    for (int b = 0; b < drho; ++b) cst += rt.rconst[j * drho + b] * rho_sum[b];
+    if (rho_sum) for (int b = 0; b < drho; ++b) cst += rt.rconst[j * drho + b] * rho_sum[b];
     local[id] = (T)(v + cst);
 }
 
@@ -1197,6 +1210,8 @@ struct LeafOut {
     const double* self_val;   // du x drho at nu = 1
     const double* self_grad;  // 3 x du x drho at nu = 1
     const float4* pk;         // FP32 path: one record per sorted point (point_record layout)
+    const double* ucst;       // du constants added to every potential (truncated-kernel gauge
+                              // constants times the total strength), or null
 };
 
 
