@@ -943,14 +943,17 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* p
     CKS(ensure(plan, B_LOCAL, (size_t)nb * du * p3 * sizeof(T), &vloc));
     T* proxy = (T*)vpr;
     T* local = (T*)vloc;
-    // FP32 path, p <= 24: sources anterpolated onto the parent grids (k_anterp3), every proxy
-    // that is read (non-leaf boxes, cubes) written by it or by the upward pass; otherwise leaf
-    // proxies, the upward pass over all children, and a zeroed array
-    //   direct_up: the leaf sources go straight to the parent grids when the parents give enough
-    // work items for the GPU (else each leaf onto its own grid and the upward pass takes every
-    // child); direct_leaf (downward): the leaf targets evaluate their parent's expansion
+    // FP32 path, p <= 24 (direct_leaf): the leaf sources go straight onto the parent grids
+    // (k_anterp3), every proxy that is read (non-leaf boxes, cubes) written by it, by
+    // k_leaf_partials or by the upward pass over the non-leaf children; the leaf targets
+    // evaluate their parent's expansion (downward).  Otherwise leaf proxies, the upward pass
+    // over all children, and a zeroed array.
+    //   The direct upward work goes by parents (one item per parent of leaves) when they are
+    // enough work items for the GPU, else split by leaves (split_up: each leaf onto its
+    // parent's grid in its own slot, then summed per parent in child order)
     const bool direct_leaf = sizeof(T) == 4 && p <= 24;
-    const bool direct_up = direct_leaf && n_nl + Mtot >= 2 * plan->n_sm;
+    const bool direct_up = direct_leaf;
+    const bool split_up = direct_leaf && n_nl + Mtot < 2 * plan->n_sm;
     if (!direct_up) {
         CK(cudaMemsetAsync(proxy, 0, (size_t)nb * drho * p3 * sizeof(T), st));
         ++launches;
@@ -960,7 +963,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* p
     bool anterp_done = false;
     if constexpr (sizeof(T) == 4) {
         if (direct_leaf && nleaf_cap > 0) {
-            const int items = direct_up ? n_nl + Mtot : nleaf_cap;
+            const int items = split_up ? nleaf_cap : n_nl + Mtot;
             const unsigned grid = (unsigned)std::max(1, std::min(items, plan->n_sm * 8));
             const int TN = p <= 20 ? 20 : 24;
             const int ntile = drho * ((p + 3) / 4) * p * ((p + TN - 1) / TN);
@@ -969,14 +972,22 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* p
                 const size_t sm = anterp3_smem<20>();
                 CKS(set_smem(plan, k_anterp3<20, 20>, sm));
                 k_anterp3<20, 20><<<grid, threads, sm, st>>>(n_nl, nl_box, Mtot, B, xs, N, rs, tab, plan->T.s,
-                                                             (float*)proxy, direct_up ? nullptr : leaves, d_nleaf);
+                                                             (float*)proxy, split_up ? leaves : nullptr, d_nleaf,
+                                                             1);
             } else {
                 const size_t sm = anterp3_smem<24>();
                 CKS(set_smem(plan, k_anterp3<24, 24>, sm));
                 k_anterp3<24, 24><<<grid, threads, sm, st>>>(n_nl, nl_box, Mtot, B, xs, N, rs, tab, plan->T.s,
-                                                             (float*)proxy, direct_up ? nullptr : leaves, d_nleaf);
+                                                             (float*)proxy, split_up ? leaves : nullptr, d_nleaf,
+                                                             1);
             }
             ++launches;
+            if (split_up && n_nl > 0) {
+                const int per_box = drho * p3;
+                k_leaf_partials<float><<<nblk((int64_t)n_nl * per_box, 256), 256, 0, st>>>(n_nl, nl_box, B, per_box,
+                                                                                         (float*)proxy);
+                ++launches;
+            }
             anterp_done = true;
         }
     }

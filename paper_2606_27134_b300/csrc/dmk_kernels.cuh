@@ -232,12 +232,15 @@ struct AntSmem {
 };
 
 //   With leaf_list (few parents: too few work items for the GPU), the items are the leaves
-// themselves, each anterpolated onto its own grid, and the upward pass then takes every child.
+// themselves, each anterpolated onto its parent's grid (a cube that is a leaf: its own) into the
+// leaf's own proxy slot; k_leaf_partials then sums each parent's leaf children in child order.
+// With leaf_list and !to_parent every leaf is anterpolated onto its own grid (the upward pass
+// then takes every child).
 template <int MAXP, int TN>
 __global__ void __launch_bounds__(kAntThreads, 2)
     k_anterp3(int n_nl, const int* __restrict__ nl_box, int n_root, BoxArrays B, const double* __restrict__ xs,
               int64_t N, const double* __restrict__ rs, Tab<float> tab, double s, float* __restrict__ proxy,
-              const int* __restrict__ leaf_list, const int* __restrict__ nleaf_dev) {
+              const int* __restrict__ leaf_list, const int* __restrict__ nleaf_dev, int to_parent) {
     static_assert(MAXP % 4 == 0 && TN % 4 == 0 && TN <= MAXP, "vector reads");
     using S = AntSmem<MAXP>;
     const int p = tab.p, p2 = p * p, p3 = p2 * p, drho = tab.d_rho;
@@ -279,10 +282,12 @@ __global__ void __launch_bounds__(kAntThreads, 2)
         __syncthreads();
         const int nr = nrng;
         if (nr == 0) continue;                     // uniform over the block
-        const int l = B.level[box];
+        // the grid the sources go onto: the box's own, or (split leaf items) its parent's
+        const int gb = (leaf_list && to_parent && B.parent[box] >= 0) ? B.parent[box] : box;
+        const int l = B.level[gb];
         const double r = s / (double)(1 << l), half = 0.5 * r;
-        const double cx = (B.ix[3 * box] + 0.5) * r, cy = (B.ix[3 * box + 1] + 0.5) * r,
-                     cz = (B.ix[3 * box + 2] + 0.5) * r;
+        const double cx = (B.ix[3 * gb] + 0.5) * r, cy = (B.ix[3 * gb + 1] + 0.5) * r,
+                     cz = (B.ix[3 * gb + 2] + 0.5) * r;
         float* outb = proxy + (size_t)box * drho * p3;
         // the sources of the ranges in super-chunks of kAntRows (cursor: range ri, position pos)
         int ri = 0, pos = rng[0][0];
@@ -366,6 +371,28 @@ __global__ void __launch_bounds__(kAntThreads, 2)
 template <int MAXP>
 inline size_t anterp3_smem() {
     return AntSmem<MAXP>::bytes;
+}
+
+// The split form of the direct upward path: every non-leaf box with leaf children gets the sum,
+// in child order, of its non-empty leaf children's partial grids (their sources on its grid,
+// k_anterp3 with leaf_list and to_parent), stored as its proxy; per_box = d_rho p^3.  Boxes
+// without leaf children are left to k_up_cluster.
+template <class T>
+__global__ void k_leaf_partials(int n_nl, const int* __restrict__ nl_box, BoxArrays B, int per_box,
+                                T* __restrict__ proxy) {
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= (int64_t)n_nl * per_box) return;
+    const int item = (int)(id / per_box), e = (int)(id - (int64_t)item * per_box);
+    const int P = nl_box[item], c0 = B.child0[P];
+    T v = 0;
+    bool any = false;
+    for (int o = 0; o < 8; ++o) {
+        const int c = c0 + o;
+        if (B.child0[c] >= 0) continue;
+        any = true;
+        if (B.end[c] > B.start[c]) v += proxy[(size_t)c * per_box + e];
+    }
+    if (any) proxy[(size_t)P * per_box + e] = v;
 }
 
 // ------------------------------------------------------------------------------------------
