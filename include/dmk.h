@@ -125,8 +125,12 @@ dmk_status_t dmk_eval_host(dmk_plan_t plan, int64_t N, const double* points, con
  *                      change of the strengths sees).
  *   d_strengths        device, N x d_rho, or NULL to skip.
  *   d_points           device, N x 3, or NULL to skip.
- * The stresslet (d_rho = 9 != d_u) returns DMK_ERR_UNSUPPORTED.  Workspace as dmk_eval; the
- * call returns after the results are complete. */
+ * The stresslet (d_rho = 9 != d_u = 3) is not self-adjoint, but its periodized kernel
+ * T_jlm = -delta_jm P_l + d_m G_jl + d_j G_ml is fully symmetric in (j, l, m) and odd in x, so
+ *   d_strengths[s][3 l + m] = -S[g (x) e_m]_l(x_s),
+ *   d_points[a][i] = sum_j grad_u[a][i][j] g_a,j - sum_lm Q_a,lm d_i S[g (x) e_m]_l(x_a),
+ * S[Q] the stresslet sum with strengths Q: three evaluations with the strengths g (x) e_m.
+ * Workspace as dmk_eval; the call returns after the results are complete. */
 dmk_status_t dmk_vjp(dmk_plan_t plan, int64_t N, const double* points, const double* strengths,
                      const double* grad_u, const double* g, double* d_strengths, double* d_points);
 
@@ -190,9 +194,9 @@ dmk_status_t dmk_eval_targets(dmk_plan_t plan, int64_t N, const double* sources,
  *   - N must lie in [0, 16384]; a larger N returns DMK_ERR_INVALID_ARG, and a problem whose
  *     workspace does not fit in 64 MiB (large p, FP64, deep trees) returns DMK_ERR_OOM, both
  *     with a message in dmk_last_error.
- *   - The first call on a device looks up the device address of the static array (a CUDA
- *     runtime query that must not run while a stream is being captured), so make that first
- *     call on each device before any stream capture begins.
+ *   - Like dmk_eval, the call cannot be captured into a CUDA graph: it waits on the host for
+ *     small device readbacks during the tree build.  Its first call on a device also looks up
+ *     the device address of the static array (a CUDA runtime query).
  *   - Every call shares the one array, which keeps the previous call's contents; the call
  *     clears everything it needs to start at zero.  Calls that overlap on the GPU (on
  *     different streams, plans or threads) race on the array and must be serialised. */

@@ -8,14 +8,16 @@ sum is self-adjoint:
 so the backward pass is one more evaluation of the same hot path (every stage: leaf residual
 sums, plane waves, root Fourier sum) with strengths g and target gradients, followed by the
 assembly of dL/dx; dmk_vjp does all of it in the CUDA library.  The forward saves the field
-gradient of u.  The stresslet (9 strength components, 3 outputs) is not self-adjoint and is
-not covered.
+gradient of u.  The stresslet (9 strength components, 3 outputs) is not self-adjoint; its
+kernel is fully symmetric in its three indices and odd, so dmk_vjp uses three evaluations with
+the strengths g (x) e_m instead.
 """
 import torch
 
 from . import dmk
 
 SELF_ADJOINT = ("laplace", "stokeslet", "rotlet")
+DIFFERENTIABLE = SELF_ADJOINT + ("stresslet",)
 
 
 class _DMKFunction(torch.autograd.Function):
@@ -43,7 +45,7 @@ class _DMKFunction(torch.autograd.Function):
 class Potential(torch.nn.Module):
     """u = Potential(kernel, D, L, tol)(points, strengths), differentiable in both arguments.
 
-    Supported for the self-adjoint kernels (Laplace, Stokeslet, rotlet).  Points and strengths
+    Supported for every kernel (the stresslet through its symmetric form).  Points and strengths
     are CUDA float64 tensors of shapes (N, 3) and (N, d_rho).  Laplace with D = 1 or 2 needs
     neutral strengths in the forward pass (Sec. 5.2); the upstream gradient of the backward pass
     need not be neutral: dL/dpoints is exact and dL/dstrengths is exact up to an additive
@@ -52,8 +54,8 @@ class Potential(torch.nn.Module):
 
     def __init__(self, kernel, D, L, tol, precision="mixed", n_s=250, stream=None):
         super().__init__()
-        if kernel not in SELF_ADJOINT:
-            raise NotImplementedError("autograd wrapper covers the self-adjoint kernels " + str(SELF_ADJOINT))
+        if kernel not in DIFFERENTIABLE:
+            raise NotImplementedError("autograd wrapper covers the kernels " + str(DIFFERENTIABLE))
         self.plan = dmk.Plan(kernel, D, L, tol, precision=precision, n_s=n_s, stream=stream)
 
     def forward(self, points, strengths):

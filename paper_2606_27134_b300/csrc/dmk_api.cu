@@ -118,7 +118,7 @@ enum BufId {
     B_W, B_KEYS, B_KEYS2, B_IDX, B_IDX2, B_XS, B_RS, B_CUB, B_FLAGS, B_CNT,
     B_CELLS, B_R, B_CAND, B_BOXU64, B_BOXINT, B_LEAVES, B_DOFFS, B_DL, B_NLBOX, B_TASKS, B_BAL,
     B_PROXY, B_LOCAL, B_PW, B_SCRATCH, B_CHI, B_UHAT, B_MISC, B_DEVPTS, B_DEVRHO, B_DEVPOT, B_DEVGRAD, B_XF, B_VW, B_PART,
-    B_VJPV, B_VJPG, B_ICNT, B_SRC, B_ORIG, B_CHIP, B_SHARDCLS, B_TPTS, B_TRHO, B_ITEMS,
+    B_VJPV, B_VJPG, B_VJPQ, B_ICNT, B_SRC, B_ORIG, B_CHIP, B_SHARDCLS, B_TPTS, B_TRHO, B_ITEMS,
     B_COUNT
 };
 
@@ -1602,10 +1602,6 @@ dmk_status_t dmk_vjp(dmk_plan_t plan, int64_t N, const double* points, const dou
                      const double* grad_u, const double* g, double* d_strengths, double* d_points) {
     if (!plan) return DMK_ERR_INVALID_ARG;
     plan->err.clear();
-    if (plan->T.kernel == DMK_STRESSLET) {
-        plan->err = "dmk_vjp: the stresslet is not self-adjoint (d_rho = 9, d_u = 3)";
-        return DMK_ERR_UNSUPPORTED;
-    }
     if (N < 0) { plan->err = "N < 0"; return DMK_ERR_INVALID_ARG; }
     if (N == 0) return DMK_OK;
     if (N > (int64_t)1 << 30) { plan->err = "N above 2^30"; return DMK_ERR_INVALID_ARG; }
@@ -1613,6 +1609,30 @@ dmk_status_t dmk_vjp(dmk_plan_t plan, int64_t N, const double* points, const dou
     if (!d_strengths && !d_points) return DMK_OK;
     cudaSetDevice(plan->device);
     const int du = plan->T.d_u;
+    if (plan->T.kernel == DMK_STRESSLET) {
+        // three evaluations with the strengths g (x) e_m (k_vjp_stresslet_q)
+        void *vq, *vu, *vgm;
+        CKS(ensure(plan, B_VJPQ, (size_t)N * 9 * sizeof(double), &vq));
+        CKS(ensure(plan, B_VJPV, (size_t)N * 3 * sizeof(double), &vu));
+        if (d_points) CKS(ensure(plan, B_VJPG, (size_t)N * 9 * sizeof(double), &vgm));
+        const cudaStream_t st = plan->stream;
+        if (d_points)
+            k_vjp_target<<<nblk(3 * N, 256), 256, 0, st>>>(N, 3, grad_u, g, d_points);
+        for (int m = 0; m < 3; ++m) {
+            k_vjp_stresslet_q<<<nblk(9 * N, 256), 256, 0, st>>>(N, m, g, (double*)vq);
+            const dmk_status_t s = (plan->prec == DMK_FP64)
+                ? run_eval<double>(plan, plan->tab64, N, points, (const double*)vq, (double*)vu,
+                                   d_points ? (double*)vgm : nullptr)
+                : run_eval<float>(plan, plan->tab32, N, points, (const double*)vq, (double*)vu,
+                                  d_points ? (double*)vgm : nullptr);
+            if (s != DMK_OK) return s;
+            k_vjp_stresslet_acc<<<nblk(N, 256), 256, 0, st>>>(N, m, (const double*)vu, (const double*)vgm, strengths,
+                                                              d_strengths, d_points);
+        }
+        CK(cudaGetLastError());
+        CKS(host_wait(plan, st));
+        return DMK_OK;
+    }
     void *vv = d_strengths, *vg = nullptr;
     if (!vv) CKS(ensure(plan, B_VJPV, (size_t)N * du * sizeof(double), &vv));
     if (d_points) CKS(ensure(plan, B_VJPG, (size_t)N * 3 * du * sizeof(double), &vg));

@@ -1050,6 +1050,46 @@ __global__ void k_vjp_points(int64_t N, int du, const double* __restrict__ gu, c
     d[t] = v;
 }
 
+// The stresslet's vector-Jacobian product.  The periodized stresslet T_jlm is fully symmetric in
+// (j, l, m) and odd in x, so dL/dQ_s,lm = sum_t g_t,j T_jlm(x_t - x_s) = -S[g (x) e_m]_l(x_s),
+// S[Q] the stresslet sum with strengths Q: three evaluations with the strengths g (x) e_m.
+// k_vjp_stresslet_q forms those strengths (component m of q), k_vjp_stresslet_acc accumulates
+// dL/dQ[s][l][m] = -u_m[s][l] and the source part of dL/dx_s, -sum_lm Q_s,lm d_i S[g (x) e_m]_l.
+__global__ void k_vjp_stresslet_q(int64_t N, int m, const double* __restrict__ g, double* __restrict__ q) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= 9 * N) return;
+    const int64_t s = t / 9;
+    const int e = (int)(t - 9 * s), j = e / 3, k = e - 3 * j;
+    q[t] = (k == m) ? g[s * 3 + j] : 0.0;
+}
+
+__global__ void k_vjp_stresslet_acc(int64_t N, int m, const double* __restrict__ um, const double* __restrict__ gm,
+                                    const double* __restrict__ Q, double* __restrict__ dQ,
+                                    double* __restrict__ dx) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    if (dQ)
+        for (int l = 0; l < 3; ++l) dQ[s * 9 + l * 3 + m] = -um[s * 3 + l];
+    if (dx)
+        for (int i = 0; i < 3; ++i) {
+            double v = dx[s * 3 + i];
+            for (int l = 0; l < 3; ++l) v = fma(-Q[s * 9 + l * 3 + m], gm[(s * 3 + i) * 3 + l], v);
+            dx[s * 3 + i] = v;
+        }
+}
+
+// target part of dL/dx for a kernel that is not self-adjoint: d[a][i] = sum_j gu[a][i][j] g[a][j]
+__global__ void k_vjp_target(int64_t N, int du, const double* __restrict__ gu, const double* __restrict__ g,
+                             double* __restrict__ d) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= 3 * N) return;
+    const int64_t a = t / 3;
+    const int i = (int)(t - 3 * a);
+    double v = 0;
+    for (int j = 0; j < du; ++j) v = fma(gu[(a * 3 + i) * du + j], g[a * du + j], v);
+    d[t] = v;
+}
+
 __global__ void k_strength_sums(int64_t N, int drho, const double* __restrict__ rho, double* __restrict__ out) {
     // out[a] = sum rho_a, out[drho + a] = sum |rho_a|
     double s[9], sa[9];

@@ -171,3 +171,43 @@ def test_vjp_nonneutral_upstream_gradient(kernel, D, L):
         an = float(np.sum(gr * d))
         # the adjoint is one more evaluation of the eps-approximate sum: agreement to 10 tol
         assert abs(fd - an) <= 10 * tol * (np.abs(gr[3]).sum() + np.abs(gr[11]).sum()), (fd, an)
+
+
+@pytest.mark.parametrize("D,L", [(3, [1.0, 1.0, 2.0]), (2, [1.0, 1.0, 1.0]), (1, [2.0, 1.0, 1.0])])
+def test_stresslet_vjp(D, L):
+    """The stresslet through autograd (dmk_vjp with three evaluations of strengths g (x) e_m).
+    Strengths: u is linear in Q, so sum_t g_t . u[dQ]_t must equal <dL/dQ, dQ> for any dQ (the
+    discretised operator keeps the kernel's symmetry: the oracle satisfies this to 1e-15).
+    Positions: central differences of L (fixed tree, plain FP64 path)."""
+    N, tol, h = 1000, 1e-6, 1e-7
+    x = W.mixed_points(N, L, 195, D=D)
+    Q = W.stokes_strengths("stresslet", N, 196)
+    dev = torch.device("cuda", 0)
+    xt = torch.tensor(x, dtype=torch.float64, device=dev)
+    Qt = torch.tensor(Q, dtype=torch.float64, device=dev)
+    g = torch.tensor(np.random.default_rng(197).standard_normal((N, 3)), dtype=torch.float64, device=dev)
+    pot = ag.Potential("stresslet", D, L, tol, precision="fp64", n_s=40)
+
+    def loss(xx, qq):
+        return (g * pot(xx, qq)).sum()
+
+    xg = xt.clone().requires_grad_(True)
+    qg = Qt.clone().requires_grad_(True)
+    gx, gq = torch.autograd.grad(loss(xg, qg), (xg, qg))
+    with torch.no_grad():
+        for seed in (198, 199):
+            dQ = torch.tensor(np.random.default_rng(seed).standard_normal((N, 9)), dtype=torch.float64, device=dev)
+            lhs = float((g * pot(xt, dQ)).sum())
+            rhs = float((gq * dQ).sum())
+            assert abs(lhs - rhs) <= 1e-10 * (abs(lhs) + float((gq.abs() * dQ.abs()).sum())), (lhs, rhs)
+        gxn = gx.cpu().numpy()
+        frac = np.abs(x * 2 ** BITS - np.round(x * 2 ** BITS))
+        cand = np.nonzero(np.min(frac, axis=1) > 4 * h * 2 ** BITS)[0]
+        fscale = np.sqrt(np.mean(np.sum(gxn ** 2, axis=1)))
+        for a in np.random.default_rng(200).choice(cand, 4, replace=False):
+            for i in range(3):
+                xp, xm = xt.clone(), xt.clone()
+                xp[a, i] += h
+                xm[a, i] -= h
+                fd = (float(loss(xp, Qt)) - float(loss(xm, Qt))) / (2 * h)
+                assert abs(fd - gxn[a, i]) <= 10 * tol * fscale + 1e-6 * abs(fd), (a, i, fd, gxn[a, i])

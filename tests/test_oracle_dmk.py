@@ -532,3 +532,23 @@ def test_original_symbol_switch_stokeslet_vs_ewald(D, L):
     assert r.plan["nparts"] == 2
     e = (ewald.stokeslet_ewald_2p if D == 2 else ewald.stokeslet_ewald_1p)(x, x, f, L, 0.2 * L[0])
     assert rel(r.u, e) < 1e-8
+
+
+@pytest.mark.parametrize("D,L", [(3, [1, 1, 1]), (2, [1, 1, 1]), (1, [2, 1, 1])])
+def test_stresslet_adjoint_identity(D, L):
+    """The periodized stresslet T_jlm = -delta_jm P_l + d_m G_jl + d_j G_ml is fully symmetric
+    in (j, l, m) and odd, so for any Q and g: sum_t g_t . u[Q]_t = -sum_m <Q[:, :, m],
+    S[g (x) e_m]> -- the identity behind the stresslet's vector-Jacobian product.  The method's
+    discretised operator keeps it to rounding."""
+    N = 60
+    x = workloads.uniform_points(N, L, seed=5)
+    rng = np.random.default_rng(6)
+    Q = rng.standard_normal((N, 9))
+    g = rng.standard_normal((N, 3))
+    lhs = np.sum(g * evaluate("stresslet", D, L, 1e-9, x, Q, n_s=12).u)
+    rhs = 0.0
+    for m in range(3):
+        Qm = np.zeros((N, 3, 3))
+        Qm[:, :, m] = g
+        rhs -= np.sum(Q.reshape(N, 3, 3)[:, :, m] * evaluate("stresslet", D, L, 1e-9, x, Qm.reshape(N, 9), n_s=12).u)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
