@@ -319,12 +319,21 @@ def main():
     value = world * N / (step_ms / 1e3)
     st = mixed["stats"]
     # leaf kernels: timed with per-stage events in a separate pass (stage 7 = the residual
-    # kernel k_pair, on the side stream beside the far field; stage 8 = the expansion kernel
-    # k_leafexp; stage 5 = the wait for k_pair plus k_leafexp)
+    # kernel k_pair; stage 8 = the expansion kernel k_leafexp_parent; stage 5 = both)
     leaf_ms = mixed["stage"][5]
     pair_ms = mixed["stage"][7]
     pairs = st["n_pairs"]
     gpairs = pairs / (pair_ms / 1e3) / 1e9 if pair_ms > 0 else None
+    # pairs inside the support of K_R (r < nu), counted on the host with a k-d tree: every
+    # non-empty leaf of this workload sits at the deepest level, so nu = s / 2^(levels - 1) for
+    # every listed pair (periodic along x1, x2)
+    try:
+        from scipy.spatial import cKDTree
+        nu = 1.0 / 2 ** (int(st["n_levels"]) - 1)
+        tree = cKDTree(x, boxsize=[W["L"][0], W["L"][1], 1e9])
+        in_support = int(tree.count_neighbors(tree, nu)) - N
+    except Exception:       # reported when available
+        in_support = None
     # roofline of the dominant kernel, k_pair (FP32 ALU bound): algorithmic FLOPs per launch =
     # visited pairs x F_pair (roofline.pair_flops), over its CUDA-event duration; the peaks are
     # the pipe throughputs measured on this GPU in this run (paper_2606_27134_b300.peaks)
@@ -362,7 +371,9 @@ def main():
             "fp64_path": fp64_line,
             "peaks": {k: pk_meas[k] for k in ("fp32_tflops", "fp64_tflops", "mufu_rsqrt_tops", "clocks")},
             "mixed_over_fp64": fp64_ms / step_ms,
-            "p2p": {"gpairs_per_s": gpairs, "pairs_per_step": pairs, "pair_kernel_ms": pair_ms, "leaf_stage_ms": leaf_ms},
+            "p2p": {"gpairs_per_s": gpairs, "pairs_per_step": pairs, "pair_kernel_ms": pair_ms, "leaf_stage_ms": leaf_ms,
+                    "pairs_in_support": in_support,
+                    "support_fraction": (in_support / pairs) if in_support else None},
             "stage_ms": dict(zip(STAGES, mixed["stage"])),
             "tree": {k: st[k] for k in ("n_levels", "n_boxes", "n_leaves", "n_nonleaf", "n_direct_entries")},
             "roofline": roof,

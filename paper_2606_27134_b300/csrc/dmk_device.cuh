@@ -157,6 +157,14 @@ struct ChebSeries {
 // k (series order above) starts at tbl + k kHermNT.
 constexpr int kHermNT = 256;
 
+// 2^n exactly, from the exponent bits (|n| well inside the normal range): no FP64 or
+// conversion instruction
+__device__ __forceinline__ float pow2f(int n) { return __int_as_float((n + 127) << 23); }
+__device__ __forceinline__ double pow2d(int n) { return __longlong_as_double((long long)(n + 1023) << 52); }
+template <class T> __device__ __forceinline__ T pow2t(int n);
+template <> __device__ __forceinline__ float pow2t<float>(int n) { return pow2f(n); }
+template <> __device__ __forceinline__ double pow2t<double>(int n) { return pow2d(n); }
+
 struct HermSeries {
     const Quad<float>* tbl;
     int i;

@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(kTransThreads) k_pw_trans(int n, const int* __
         }
     }
     if constexpr (OP) {
-        const T gs = (T)ldexp(1.0, tab.level_power * B.level[box]) * tab.gdiff[e];
+        const T gs = pow2t<T>(tab.level_power * B.level[box]) * tab.gdiff[e];
         Cx<T> out[3];
         if constexpr (NC == 1) {
             out[0] = V[0];
@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(kTransThreads) k_pw_symbol(int n, const int* _
     for (int a = 0; a < DR; ++a) V[a] = Wb[(size_t)a * nW];
     Cx<T> out[3];
     apply_op<T>(tab.kernel, mv, V, out);
-    const T gs = (T)ldexp(1.0, tab.level_power * B.level[nl_box[bi]]) * tab.gdiff[e];
+    const T gs = pow2t<T>(tab.level_power * B.level[nl_box[bi]]) * tab.gdiff[e];
     for (int j = 0; j < du; ++j) Wb[(size_t)j * nW] = {gs * out[j].x, gs * out[j].y};
 }
 
@@ -1206,8 +1206,9 @@ __global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? (K == DMK_LA
     // the box test passes every source within nu of the tile's box: its FP32 rounding (relative
     // 1e-6 at most for offsets below 3 nu) is covered by the factor on nu^2
     const T box_margin = kTwo ? T(1.0001) : T(1.0 + 1e-12);
-    float Lh[3], Ll[3];
+    float Lh[3], Ll[3], s_hi, s_lo;
     for (int a = 0; a < 3; ++a) split_double(g.L[a], Lh[a], Ll[a]);
+    split_double(g.s, s_hi, s_lo);
     while (true) {
         int t = 0;
         if (lane == 0) t = atomicAdd(next, 1);
@@ -1219,10 +1220,22 @@ __global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? (K == DMK_LA
         const int ti = lane & (m - 1), s = lane >> lgm, S = 32 >> lgm;
         const int box = leaves[li];
         const int l = B.level[box];
-        const double r = ldexp(g.s, -l);
-        const double c[3] = {(B.ix[3 * box] + 0.5) * r, (B.ix[3 * box + 1] + 0.5) * r, (B.ix[3 * box + 2] + 0.5) * r};
+        // minus the leaf centre c = (2 ix + 1) s 2^(-l-1), as leading + trailing FP32 parts
+        // (two-product of the odd integer with s's parts: exact to 2^-48 of c, no FP64)
         float ch[3], cl[3];
-        for (int a = 0; a < 3; ++a) split_double(-c[a], ch[a], cl[a]);
+        double c[3];
+        if constexpr (kTwo) {
+            const float sc = pow2f(-l - 1);
+            for (int a = 0; a < 3; ++a) {
+                const float k = (float)(2 * B.ix[3 * box + a] + 1);
+                const float hi = k * s_hi;
+                const float lo = fmaf(k, s_hi, -hi) + k * s_lo;
+                two_float_add(-hi * sc, -lo * sc, 0.f, 0.f, ch[a], cl[a]);
+            }
+        } else {
+            const double r = ldexp(g.s, -l);
+            for (int a = 0; a < 3; ++a) c[a] = (B.ix[3 * box + a] + 0.5) * r;
+        }
         const int tg = B.start[box] + tk.y + ti;
         const int tgo = out.orig[tg];                  // the original point the target is
         T xt[3], xtl[3] = {0, 0, 0};
@@ -1247,6 +1260,10 @@ __global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? (K == DMK_LA
 #pragma unroll
         for (int j = 0; j < NA; ++j) { acc_hi[j] = 0; acc_lo[j] = 0; }
         int head = 0, tail = 0;
+        // the target's own periodic images can pass the rounded support test only in an entry of
+        // level 0 with an image shift (|p| >= nu_0 = nu there); elsewhere |p| >= 2 nu and the test
+        // alone drops them, so the index comparison runs only once such an entry was seen
+        bool chk = false;
         // evaluates the survivors head .. head + cnt - 1 of the ring for this lane's target
         auto run_block = [&](int cnt) {
             __syncwarp();
@@ -1270,8 +1287,13 @@ __global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? (K == DMK_LA
                     // r = 0 (the target itself at p = 0, or a coincident point) and the target's
                     // own periodic images (|p| >= nu_0 >= nu: outside the support, however r^2
                     // rounds) are dropped
-                    if (r2 > T(0) && r2 < a.w && sI[k] != tgo)
-                        Pr::eval(HermSeries(herm, r2, b.w), dx, dy, dz, r2, b.w, sr[k], acc, gacc);
+                    if (chk) {
+                        if (r2 > T(0) && r2 < a.w && sI[k] != tgo)
+                            Pr::eval(HermSeries(herm, r2, b.w), dx, dy, dz, r2, b.w, sr[k], acc, gacc);
+                    } else {
+                        if (r2 > T(0) && r2 < a.w)
+                            Pr::eval(HermSeries(herm, r2, b.w), dx, dy, dz, r2, b.w, sr[k], acc, gacc);
+                    }
                 }
             } else {
                 // FP64 (a pipe 1/64 of FP32): each lane first marks its in-support survivors,
@@ -1313,16 +1335,20 @@ __global__ void __launch_bounds__(kPairWarps * 32, sizeof(T) == 4 ? (K == DMK_LA
             const DirectEntry de = dl[e];
             const int lev = de.code >> 6;
             const int sb[3] = {((de.code) & 3) - 1, ((de.code >> 2) & 3) - 1, ((de.code >> 4) & 3) - 1};
+            chk |= lev == 0 && (sb[0] | sb[1] | sb[2]) != 0;
             // per-entry constants: nu^2 and 1/nu of the entry's level, image shift minus the
             // target leaf's centre
             T nu2, tinv;
             float Eh[3], El[3];
             double E[3];
             if constexpr (kTwo) {
-                tinv = ldexpf(inv_s_f, lev);
-                nu2 = ldexpf(s2_f, -2 * lev);
-                for (int a = 0; a < 3; ++a)
-                    two_float_add((float)sb[a] * Lh[a], (float)sb[a] * Ll[a], ch[a], cl[a], Eh[a], El[a]);
+                tinv = inv_s_f * pow2f(lev);
+                nu2 = s2_f * pow2f(-2 * lev);
+                for (int a = 0; a < 3; ++a) {
+                    const float sh = sb[a] == 0 ? 0.f : (sb[a] > 0 ? Lh[a] : -Lh[a]);
+                    const float sl = sb[a] == 0 ? 0.f : (sb[a] > 0 ? Ll[a] : -Ll[a]);
+                    two_float_add(sh, sl, ch[a], cl[a], Eh[a], El[a]);
+                }
             } else {
                 tinv = (T)ldexp(inv_s, lev);
                 nu2 = (T)ldexp(s2, -2 * lev);
