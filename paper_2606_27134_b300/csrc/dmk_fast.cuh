@@ -424,13 +424,22 @@ __global__ void __launch_bounds__(kTransThreads) k_pw_trans(int n, const int* __
     __shared__ int col_nl[27];
     __shared__ int col_d[27];
     const int box = nl_box[bi];
-    if (threadIdx.x == 0) {
-        int k = 0;
-        for (int d = 0; d < 27; ++d) {
-            const int C = B.coll[box * 27 + d];
-            if (C >= 0 && B.nl[C] >= 0) { col_nl[k] = B.nl[C]; col_d[k] = d; ++k; }
+    if (threadIdx.x < 32) {
+        // the non-leaf colleagues in offset order, one lane per offset (ballot compaction)
+        const int d = threadIdx.x;
+        int C = -1;
+        bool ok = false;
+        if (d < 27) {
+            C = B.coll[box * 27 + d];
+            ok = C >= 0 && B.nl[C] >= 0;
         }
-        ncol = k;
+        const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            const int k = __popc(bal & ((1u << d) - 1u));
+            col_nl[k] = B.nl[C];
+            col_d[k] = d;
+        }
+        if (d == 0) ncol = __popc(bal);
     }
     __syncthreads();
     const int e = chunk * kTransThreads + threadIdx.x;

@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kAntThreads, 2)
         // the grid the sources go onto: the box's own, or (split leaf items) its parent's
         const int gb = (leaf_list && to_parent && B.parent[box] >= 0) ? B.parent[box] : box;
         const int l = B.level[gb];
-        const double r = s / (double)(1 << l), half = 0.5 * r;
+        const double r = s / (double)(1 << l), half = 0.5 * r, ihalf = 1.0 / half;
         const double cx = (B.ix[3 * gb] + 0.5) * r, cy = (B.ix[3 * gb + 1] + 0.5) * r,
                      cz = (B.ix[3 * gb + 2] + 0.5) * r;
         float* outb = proxy + (size_t)box * drho * p3;
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(kAntThreads, 2)
                 for (int u = threadIdx.x; u < 3 * take; u += blockDim.x) {
                     const int ax = u / take, pt = u - ax * take;
                     const double c = ax == 0 ? cx : (ax == 1 ? cy : cz);
-                    const double xi = (xs[ax * N + cp + pt] - c) / half;
+                    const double xi = (xs[ax * N + cp + pt] - c) * ihalf;
                     float* row = (ax == 0 ? lx : (ax == 1 ? ly : lz)) + (ns + pt) * MAXP;
                     lagrange_row_padded<float>((float)xi, tab.nodes, tab.bary, p, MAXP, 1.0f, row);
                 }
