@@ -327,6 +327,17 @@ dmk_status_t upload_root_part(dmk_plan_s* plan, const std::vector<double>* kax, 
     for (auto& z : Wr) { h.push_back(z.real()); h.push_back(z.imag()); }
     size_t o_c = h.size();
     for (double v : P.root_const) h.push_back(v);
+    // exp(2 pi i k / M3), k = 0..M3-1, for the DFT over the cube index
+    pad();
+    size_t o_r = h.size();
+    {
+        const int M3 = std::max(1, P.M[2]);
+        for (int k = 0; k < M3; ++k) {
+            const double a = 2 * 3.14159265358979323846 * (double)k / M3;
+            h.push_back(std::cos(a));
+            h.push_back(std::sin(a));
+        }
+    }
     // n3 mod M3 per x3 wavenumber (used when x3 is periodic: k3 = 2 pi n3 / L3)
     size_t o_n = h.size();
     {
@@ -352,6 +363,7 @@ dmk_status_t upload_root_part(dmk_plan_s* plan, const std::vector<double>* kax, 
     rt.W = reinterpret_cast<const Cx<double>*>(base + o_W);
     rt.rconst = base + o_c;
     rt.nmod3 = base + o_n;
+    rt.roots = reinterpret_cast<const Cx<double>*>(base + o_r);
     return DMK_OK;
 }
 
@@ -1122,7 +1134,7 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* p
             Cx<double>* Bh = B2f + (size_t)jf * f2;
             k_root_fwd1<T><<<blocks((int64_t)jf * f1), 128, 0, st>>>(jf, p, rt, rproxy, B1f);
             k_root_fwd2<<<blocks((int64_t)jf * f2), 128, 0, st>>>(jf, p, rt, B1f, B2f);
-            k_rootfft_dft<<<blocks((int64_t)M3 * drho * E), 128, 0, st>>>(M3, drho, (int)E, B2f, Bh);
+            k_rootfft_dft<<<blocks((int64_t)M3 * drho * E), 128, 0, st>>>(M3, drho, (int)E, rt, B2f, Bh);
             k_rootfft_chi<<<blocks((int64_t)drho * rt.nmode), 128, 0, st>>>(drho, p, g, rt, Bh, chi);
             CKS(reduce_chi(plan, sh, chi, (int64_t)2 * drho * rt.nmode, d_sums));
             k_root_apply<<<nblk(rt.nmode, 128), 128, 0, st>>>(1, drho, du, rt, chi, uh);

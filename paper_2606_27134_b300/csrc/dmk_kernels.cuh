@@ -666,6 +666,7 @@ struct RootTab {
     const Cx<double>* W;         // nmode x du x drho
     const double* rconst;        // du x drho
     const double* nmod3;         // per x3 wavenumber k3 = 2 pi n3 / L3: n3 mod M3 (periodic x3)
+    const Cx<double>* roots;     // exp(2 pi i k / M3), k = 0..M3-1 (the cube-index DFT)
 };
 
 // chi_m(k) for cube m, component a (tensor form), including exp(-i k . c_m)
@@ -938,7 +939,7 @@ constexpr int kRootFftMax = 4096;
 
 // forward: beta_hat[(s drho + a) E + e] = sum_m exp(-2 pi i s m / M3) beta[(m drho + a) E + e],
 // one thread per output (direct length-M3 sum; M3 <= kRootFftMax)
-__global__ void k_rootfft_dft(int M, int drho, int E, const Cx<double>* __restrict__ beta,
+__global__ void k_rootfft_dft(int M, int drho, int E, RootTab rt, const Cx<double>* __restrict__ beta,
                               Cx<double>* __restrict__ bhat) {
     const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t per = (int64_t)drho * E;
@@ -947,9 +948,8 @@ __global__ void k_rootfft_dft(int M, int drho, int E, const Cx<double>* __restri
     const int64_t t = id % per;
     Cx<double> v = {0, 0};
     for (int m = 0; m < M; ++m) {
-        double sn, cs;
-        sincospi(-2.0 * (double)((sidx * m) % M) / M, &sn, &cs);
-        cfma(v, Cx<double>{cs, sn}, beta[(size_t)m * per + t]);
+        const Cx<double> w = rt.roots[(sidx * m) % M];
+        cfma(v, Cx<double>{w.x, -w.y}, beta[(size_t)m * per + t]);
     }
     bhat[id] = v;
 }
@@ -1025,10 +1025,9 @@ __global__ void k_rootfft_idft(int M, int du, int p, RootTab rt, const Cx<double
     const int j = (int)(t / p3);
     double v = 0;
     for (int sidx = 0; sidx < M; ++sidx) {
-        double sn, cs;
-        sincospi(2.0 * (double)((sidx * m) % M) / M, &sn, &cs);
+        const Cx<double> w = rt.roots[(sidx * m) % M];
         const Cx<double> gsv = Gs[(size_t)sidx * per + t];
-        v += cs * gsv.x - sn * gsv.y;
+        v += w.x * gsv.x - w.y * gsv.y;
     }
     double cst = 0;
     if (rho_sum) for (int b = 0; b < drho; ++b) cst += rt.rconst[j * drho + b] * rho_sum[b];
