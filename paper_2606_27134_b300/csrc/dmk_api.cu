@@ -980,18 +980,18 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* p
             const int TN = p <= 20 ? 20 : 24;
             const int ntile = drho * ((p + 3) / 4) * p * ((p + TN - 1) / TN);
             const int threads = std::min(kAntThreads, (ntile + 31) / 32 * 32);
+            auto launch = [&](auto kern, size_t sm) -> dmk_status_t {
+                CKS(set_smem(plan, kern, sm));
+                kern<<<grid, threads, sm, st>>>(n_nl, nl_box, Mtot, B, xs, N, rs, tab, plan->T.s, (float*)proxy,
+                                                split_up ? leaves : nullptr, d_nleaf, 1);
+                return DMK_OK;
+            };
             if (p <= 20) {
-                const size_t sm = anterp3_smem<20>();
-                CKS(set_smem(plan, k_anterp3<20, 20>, sm));
-                k_anterp3<20, 20><<<grid, threads, sm, st>>>(n_nl, nl_box, Mtot, B, xs, N, rs, tab, plan->T.s,
-                                                             (float*)proxy, split_up ? leaves : nullptr, d_nleaf,
-                                                             1);
+                if (split_up) CKS(launch(k_anterp3<20, 20, kAntRowsLeaf>, anterp3_smem<20>(true)));
+                else CKS(launch(k_anterp3<20, 20, kAntRows>, anterp3_smem<20>(false)));
             } else {
-                const size_t sm = anterp3_smem<24>();
-                CKS(set_smem(plan, k_anterp3<24, 24>, sm));
-                k_anterp3<24, 24><<<grid, threads, sm, st>>>(n_nl, nl_box, Mtot, B, xs, N, rs, tab, plan->T.s,
-                                                             (float*)proxy, split_up ? leaves : nullptr, d_nleaf,
-                                                             1);
+                if (split_up) CKS(launch(k_anterp3<24, 24, kAntRowsLeaf>, anterp3_smem<24>(true)));
+                else CKS(launch(k_anterp3<24, 24, kAntRows>, anterp3_smem<24>(false)));
             }
             ++launches;
             if (split_up && n_nl > 0) {

@@ -214,21 +214,23 @@ __global__ void __launch_bounds__((MAXP / 2 * MAXP + 31) / 32 * 32, sizeof(T) ==
 // child-to-parent interpolation of Sec. 3.1.2 and spares that interpolation.  Work item: a
 // non-leaf box with at least one leaf child (the sources of its leaf children), or a cube that
 // is a leaf (its own sources); k_up_cluster adds the non-leaf children afterwards.
-//   The Lagrange rows of up to kAntRows sources (gathered over the leaf children) are computed
+//   The Lagrange rows of up to ROWS sources (gathered over the leaf children) are computed
 // once and kept in shared memory with the strengths, for every component; each thread owns a
 // tile of 4 consecutive j1 x every j3 (TN = MAXP, zero rows beyond p) at one (a, j2) and per
 // source forms w = rho_a l_j2 l_j1[4] (5 multiplies) and does 4 TN multiply-adds from 3 + TN/4
 // shared-memory reads.  Tiles beyond the block's threads are taken in passes over the same rows.
-constexpr int kAntRows = 256;      // sources whose Lagrange rows are held at once
+constexpr int kAntRows = 256;      // sources whose Lagrange rows are held at once (parent items)
+constexpr int kAntRowsLeaf = 128;  // the same for leaf items (at most n_s sources, often ~100):
+                                   // half the shared memory, more resident blocks
 constexpr int kAntThreads = 256;
 
-template <int MAXP>
+template <int MAXP, int ROWS>
 struct AntSmem {
-    static constexpr size_t lx = 0;                                         // float [kAntRows][MAXP]
-    static constexpr size_t ly = lx + (size_t)kAntRows * MAXP * 4;
-    static constexpr size_t lz = ly + (size_t)kAntRows * MAXP * 4;
-    static constexpr size_t rho = lz + (size_t)kAntRows * MAXP * 4;       // float [kAntRows][9]
-    static constexpr size_t bytes = rho + (size_t)kAntRows * 9 * 4;
+    static constexpr size_t lx = 0;                                         // float [ROWS][MAXP]
+    static constexpr size_t ly = lx + (size_t)ROWS * MAXP * 4;
+    static constexpr size_t lz = ly + (size_t)ROWS * MAXP * 4;
+    static constexpr size_t rho = lz + (size_t)ROWS * MAXP * 4;            // float [ROWS][9]
+    static constexpr size_t bytes = rho + (size_t)ROWS * 9 * 4;
 };
 
 //   With leaf_list (few parents: too few work items for the GPU), the items are the leaves
@@ -236,13 +238,13 @@ struct AntSmem {
 // leaf's own proxy slot; k_leaf_partials then sums each parent's leaf children in child order.
 // With leaf_list and !to_parent every leaf is anterpolated onto its own grid (the upward pass
 // then takes every child).
-template <int MAXP, int TN>
+template <int MAXP, int TN, int ROWS>
 __global__ void __launch_bounds__(kAntThreads, 2)
     k_anterp3(int n_nl, const int* __restrict__ nl_box, int n_root, BoxArrays B, const double* __restrict__ xs,
               int64_t N, const double* __restrict__ rs, Tab<float> tab, double s, float* __restrict__ proxy,
               const int* __restrict__ leaf_list, const int* __restrict__ nleaf_dev, int to_parent) {
     static_assert(MAXP % 4 == 0 && TN % 4 == 0 && TN <= MAXP, "vector reads");
-    using S = AntSmem<MAXP>;
+    using S = AntSmem<MAXP, ROWS>;
     const int p = tab.p, p2 = p * p, p3 = p2 * p, drho = tab.d_rho;
     const int nj = (p + 3) / 4, ng = (p + TN - 1) / TN, ntile = drho * nj * p * ng;
     float* lx = reinterpret_cast<float*>(dsmem + S::lx);
@@ -289,7 +291,7 @@ __global__ void __launch_bounds__(kAntThreads, 2)
         const double cx = (B.ix[3 * gb] + 0.5) * r, cy = (B.ix[3 * gb + 1] + 0.5) * r,
                      cz = (B.ix[3 * gb + 2] + 0.5) * r;
         float* outb = proxy + (size_t)box * drho * p3;
-        // the sources of the ranges in super-chunks of kAntRows (cursor: range ri, position pos)
+        // the sources of the ranges in super-chunks of ROWS (cursor: range ri, position pos)
         int ri = 0, pos = rng[0][0];
         bool first = true;
         while (true) {
@@ -297,8 +299,8 @@ __global__ void __launch_bounds__(kAntThreads, 2)
             int ns = 0;
             int cr = ri, cp = pos;
             __syncthreads();
-            while (cr < nr && ns < kAntRows) {
-                const int take = min(kAntRows - ns, rng[cr][1] - cp);
+            while (cr < nr && ns < ROWS) {
+                const int take = min(ROWS - ns, rng[cr][1] - cp);
                 for (int u = threadIdx.x; u < 3 * take; u += blockDim.x) {
                     const int ax = u / take, pt = u - ax * take;
                     const double c = ax == 0 ? cx : (ax == 1 ? cy : cz);
@@ -369,8 +371,8 @@ __global__ void __launch_bounds__(kAntThreads, 2)
 }
 
 template <int MAXP>
-inline size_t anterp3_smem() {
-    return AntSmem<MAXP>::bytes;
+inline size_t anterp3_smem(bool leaf_items) {
+    return leaf_items ? AntSmem<MAXP, kAntRowsLeaf>::bytes : AntSmem<MAXP, kAntRows>::bytes;
 }
 
 // The split form of the direct upward path: every non-leaf box with leaf children gets the sum,
