@@ -15,7 +15,7 @@ One launch of the residual kernel (k_pair) processes every visited pair once -- 
 # DRAM bytes (read + write) of one k_pair<float, Laplace, grad> launch at the benchmark
 # workload from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel as
 # it stands; None while the kernel has changed since its last capture.
-PAIR_TRAFFIC_BYTES = None
+PAIR_TRAFFIC_BYTES = 4.160e6
 
 SMS = 148
 FP32_LANES_PER_SM = 128
