@@ -1026,6 +1026,8 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* p
     for (int l = nlev - 2; l >= 0; --l) {
         const int n = ti.nR[l];
         if (n == 0) continue;
+        // direct path: parents whose children are all leaves have their proxies already
+        if (direct_up && ti.nR[l + 1] == 0) continue;
         if (fast_up) {
             if (mp == 20)
                 k_up_cluster<T, 20><<<8 * n, up_threads, ch_bytes, st>>>(nl_box + ti.nl_off[l], B, tab, proxy,
@@ -1269,6 +1271,9 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* p
     for (int l = 0; l < nlev - 1; ++l) {
         const int n = ti.nR[l];
         if (n == 0) continue;
+        // direct path: leaf children take their parent's expansion, so a level whose children
+        // are all leaves has nothing to shift
+        if (direct_leaf && ti.nR[l + 1] == 0) continue;
         if (fast_shift) {
             if (mp == 20)
                 k_shift_child<T, 20><<<8 * n, shift_threads, ch_bytes, st>>>(nl_box + ti.nl_off[l], B, tab, local,

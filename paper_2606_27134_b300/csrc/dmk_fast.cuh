@@ -511,98 +511,6 @@ __global__ void __launch_bounds__(kTransThreads) k_pw_symbol(int n, const int* _
     for (int j = 0; j < du; ++j) Wb[(size_t)j * nW] = {gs * out[j].x, gs * out[j].y};
 }
 
-// Plane-wave outgoing expansions (Sec. 3.1.4, Eq. Dl_int_discr), register-blocked: for every
-// non-leaf box W(m) = sum_j proxy(j) exp(-i h m . y_j), m3 >= 0 only (real input).  Work item =
-// (box, half of the m2 range).  The proxy tensor is staged in shared memory; stage 1, thread per
-// (j1, j2) fiber: j3 -> m3 with the fiber in registers; stage 2, thread per (j1, m3): j2 -> m2
-// for the item's m2 half; stage 3, thread per (m2 of the half, m3, half of m1): j1 -> m1,
-// written to W[nl][a][(m1 NF + m2) nfh + m3].  The proxy buffer is reused for stage 2's output.
-template <class T, int MAXP>
-__global__ void __launch_bounds__(416, MAXP <= 20 ? 2 : 1) k_pwout2(int n, const int* __restrict__ nl_box, Tab<T> tab,
-                                                const T* __restrict__ proxy, Cx<T>* __restrict__ W) {
-    const int p = tab.p, p2 = p * p, p3 = p2 * p, P = odd_pitch(p), drho = tab.d_rho;
-    const int nf = tab.nf, NF = tab.NF, nfh = tab.nfh, nW = NF * NF * nfh;
-    const int NFP = NF + 1;                                    // row pitch of Et
-    const int pm3 = nfh | 1;
-    const int H = (NF + 1) / 2;                                // m values per half
-    constexpr int MAXH = MAXP + 2;                             // H <= MAXH, nfh <= MAXP
-    Cx<T>* Et = reinterpret_cast<Cx<T>*>(dsmem);               // p x NFP: Et[k][m] = E[m][k]
-    Cx<T>* A1 = Et + p * NFP;                                  // p^2 x pm3
-    T* X = reinterpret_cast<T*>(A1 + p2 * pm3);                // p^2 x P (stage 1 input)
-    Cx<T>* A2 = reinterpret_cast<Cx<T>*>(X);                   // p x H x nfh (stage 2 output)
-    for (int e = threadIdx.x; e < p * NFP; e += blockDim.x) {
-        const int k = e / NFP, m = e % NFP;
-        Et[e] = (m < NF) ? tab.E[m * p + k] : Cx<T>{0, 0};
-    }
-    for (int w = blockIdx.x; w < 2 * n; w += gridDim.x) {
-        const int bi = w >> 1, half = w & 1;
-        const int box = nl_box[bi];
-        const int m20 = half * H, m2c = min(H, NF - m20);
-        for (int a = 0; a < drho; ++a) {
-            __syncthreads();
-            load_padded_batched<T, MAXP>(X, proxy + ((size_t)box * drho + a) * p3, p, P);
-            __syncthreads();
-            for (int c = threadIdx.x; c < p2; c += blockDim.x) {       // j3 -> m3
-                T x[MAXP];
-#pragma unroll
-                for (int k = 0; k < MAXP; ++k) x[k] = (k < p) ? X[c * P + k] : T(0);
-                Cx<T> acc[MAXP];
-#pragma unroll
-                for (int m = 0; m < MAXP; ++m) acc[m] = {0, 0};
-#pragma unroll
-                for (int k = 0; k < MAXP; ++k) {
-                    if (k < p) {
-                        const Cx<T>* row = Et + k * NFP + nf;
-#pragma unroll
-                        for (int m = 0; m < MAXP; ++m)
-                            if (m < nfh) cfmar(acc[m], row[m], x[k]);
-                    }
-                }
-#pragma unroll
-                for (int m = 0; m < MAXP; ++m)
-                    if (m < nfh) A1[c * pm3 + m] = acc[m];
-            }
-            __syncthreads();
-            for (int c = threadIdx.x; c < p * nfh; c += blockDim.x) {   // j2 -> m2 (this half)
-                const int j1 = c / nfh, m3 = c % nfh;
-                Cx<T> acc[MAXH];
-#pragma unroll
-                for (int m = 0; m < MAXH; ++m) acc[m] = {0, 0};
-                for (int k = 0; k < p; ++k) {
-                    const Cx<T> v = A1[(j1 * p + k) * pm3 + m3];
-                    const Cx<T>* row = Et + k * NFP + m20;
-#pragma unroll
-                    for (int m = 0; m < MAXH; ++m)
-                        if (m < m2c) cfma(acc[m], row[m], v);
-                }
-#pragma unroll
-                for (int m = 0; m < MAXH; ++m)
-                    if (m < m2c) A2[(j1 * H + m) * nfh + m3] = acc[m];
-            }
-            __syncthreads();
-            Cx<T>* out = W + ((size_t)bi * drho + a) * nW;
-            for (int c = threadIdx.x; c < 2 * m2c * nfh; c += blockDim.x) {  // j1 -> m1
-                const int h1 = c / (m2c * nfh), r = c % (m2c * nfh);
-                const int mm = r / nfh, m3 = r % nfh;
-                const int m0 = h1 * H, mc = min(H, NF - m0);
-                Cx<T> acc[MAXH];
-#pragma unroll
-                for (int m = 0; m < MAXH; ++m) acc[m] = {0, 0};
-                for (int k = 0; k < p; ++k) {
-                    const Cx<T> v = A2[(k * H + mm) * nfh + m3];
-                    const Cx<T>* row = Et + k * NFP + m0;
-#pragma unroll
-                    for (int m = 0; m < MAXH; ++m)
-                        if (m < mc) cfma(acc[m], row[m], v);
-                }
-#pragma unroll
-                for (int m = 0; m < MAXH; ++m)
-                    if (m < mc) out[(size_t)(m0 + m) * NF * nfh + (m20 + mm) * nfh + m3] = acc[m];
-            }
-        }
-    }
-}
-
 // Plane-wave outgoing expansions with the symmetries of the nodes and of the modes (Sec.
 // 3.1.4, Eq. Dl_int_discr): W(m) = sum_j proxy(j) exp(-i theta m . eta_j), theta = pi / 3,
 // m3 >= 0 only (real input).  With C(m, k) = cos(theta m eta_k) and S(m, k) = sin(theta m eta_k),
@@ -777,101 +685,6 @@ inline size_t pwout3_smem(int p, int nfh, int MH, int nsplit) {
     const int hp = p / 2, pm3 = nfh | 1, P = p | 1, hcn = (nfh + nsplit - 1) / nsplit;
     const size_t r2 = (size_t)2 * p * 2 * hcn * nfh, x = (size_t)p * p * P;
     return ((size_t)2 * hp * MH + (size_t)2 * p * p * pm3 + std::max(r2, x)) * sizeof(T);
-}
-
-// shared memory of k_pwout2
-template <class T>
-inline size_t pwout2_smem(int p, int NF, int nfh) {
-    const int P = p | 1, pm3 = nfh | 1, H = (NF + 1) / 2;
-    const size_t xbytes = std::max((size_t)p * p * P * sizeof(T), (size_t)p * H * nfh * sizeof(Cx<T>));
-    return ((size_t)p * (NF + 1) + (size_t)p * p * pm3) * sizeof(Cx<T>) + xbytes;
-}
-
-// Incoming transform (Sec. 3.1.4) from the translated spectrum Vw of k_pw_trans: stage A, thread
-// per spectral column (m2, m3), m1 -> j1 with the column read from global memory in batches;
-// stages B (m2 -> j2) and C (m3 -> j3, half-spectrum weights, 1 for m3 = 0 and 2 otherwise) in
-// shared memory with an odd row pitch.
-template <class T, int MAXP>
-__global__ void __launch_bounds__(384) k_pwin3(int n, const int* __restrict__ nl_box, Tab<T> tab,
-                                               const Cx<T>* __restrict__ Vw, T* __restrict__ local) {
-    const int p = tab.p, p2 = p * p, p3 = p2 * p, du = tab.d_u;
-    const int nf = tab.nf, NF = tab.NF, nfh = tab.nfh, nW = NF * NF * nfh;
-    const int pm3 = nfh | 1;
-    Cx<T>* F = reinterpret_cast<Cx<T>*>(dsmem);                // NF x MAXP: conj(E), zero-padded
-    Cx<T>* B2 = F + NF * MAXP;                                 // p x NF x nfh
-    Cx<T>* B1 = B2 + p * NF * nfh;                             // p x p x pm3
-    for (int e = threadIdx.x; e < NF * MAXP; e += blockDim.x) {
-        const int m = e / MAXP, j = e % MAXP;
-        F[e] = (j < p) ? cconj(tab.E[m * p + j]) : Cx<T>{0, 0};
-    }
-    constexpr int KB = 9;
-    for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
-        const int box = nl_box[bi];
-        for (int j = 0; j < du; ++j) {
-            __syncthreads();
-            const Cx<T>* V = Vw + ((size_t)bi * du + j) * nW;
-            // stage A
-            for (int c = threadIdx.x; c < NF * nfh; c += blockDim.x) {
-                Cx<T> acc[MAXP];
-#pragma unroll
-                for (int q = 0; q < MAXP; ++q) acc[q] = {0, 0};
-                for (int i0 = 0; i0 < NF; i0 += KB) {
-                    Cx<T> v[KB];
-#pragma unroll
-                    for (int u = 0; u < KB; ++u)
-                        v[u] = (i0 + u < NF) ? V[(size_t)(i0 + u) * NF * nfh + c] : Cx<T>{0, 0};
-#pragma unroll
-                    for (int u = 0; u < KB; ++u) {
-                        if (i0 + u < NF) {
-                            const Cx<T>* Fr = F + (i0 + u) * MAXP;
-#pragma unroll
-                            for (int q = 0; q < MAXP; ++q) cfma(acc[q], Fr[q], v[u]);
-                        }
-                    }
-                }
-                const int i2 = c / nfh, m3 = c % nfh;
-#pragma unroll
-                for (int q = 0; q < MAXP; ++q)
-                    if (q < p) B2[(q * NF + i2) * nfh + m3] = acc[q];
-            }
-            __syncthreads();
-            // stage B
-            for (int c = threadIdx.x; c < p * nfh; c += blockDim.x) {
-                const int j1 = c / nfh, m3 = c % nfh;
-                Cx<T> acc[MAXP];
-#pragma unroll
-                for (int q = 0; q < MAXP; ++q) acc[q] = {0, 0};
-                for (int i2 = 0; i2 < NF; ++i2) {
-                    const Cx<T> b = B2[(j1 * NF + i2) * nfh + m3];
-                    const Cx<T>* Fr = F + i2 * MAXP;
-#pragma unroll
-                    for (int q = 0; q < MAXP; ++q) cfma(acc[q], Fr[q], b);
-                }
-#pragma unroll
-                for (int q = 0; q < MAXP; ++q)
-                    if (q < p) B1[(j1 * p + q) * pm3 + m3] = acc[q];
-            }
-            __syncthreads();
-            // stage C
-            T* u = local + ((size_t)box * du + j) * p3;
-            for (int c = threadIdx.x; c < p2; c += blockDim.x) {
-                T acc[MAXP];
-#pragma unroll
-                for (int q = 0; q < MAXP; ++q) acc[q] = 0;
-                for (int m3 = 0; m3 < nfh; ++m3) {
-                    const Cx<T> b = B1[c * pm3 + m3];
-                    const T wgt = (m3 == 0) ? T(1) : T(2);
-                    const Cx<T> bw = {wgt * b.x, wgt * b.y};
-                    const Cx<T>* Fr = F + (nf + m3) * MAXP;
-#pragma unroll
-                    for (int q = 0; q < MAXP; ++q) acc[q] = fma(Fr[q].x, bw.x, fma(-Fr[q].y, bw.y, acc[q]));
-                }
-#pragma unroll
-                for (int q = 0; q < MAXP; ++q)
-                    if (q < p) u[c * p + q] += acc[q];
-            }
-        }
-    }
 }
 
 // Incoming transform with the same symmetries (Sec. 3.1.4): u(j) += Re sum_m w(m3) V(m)

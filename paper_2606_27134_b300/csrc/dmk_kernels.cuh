@@ -671,47 +671,6 @@ struct RootTab {
     const Cx<double>* roots;     // exp(2 pi i k / M3), k = 0..M3-1 (the cube-index DFT)
 };
 
-// chi_m(k) for cube m, component a (tensor form), including exp(-i k . c_m)
-template <class T>
-__global__ void k_root_chi(int M, int drho, int p, Geo g, RootTab rt, const T* __restrict__ proxy,
-                           Cx<double>* __restrict__ chi_part, unsigned char* scratch, size_t per_cta) {
-    const int p2 = p * p, p3 = p2 * p;
-    const int n1 = rt.n1, n2 = rt.n2, n3 = rt.n3;
-    Cx<double>* B1 = reinterpret_cast<Cx<double>*>(scratch + (size_t)blockIdx.x * per_cta);
-    Cx<double>* B2 = B1 + (size_t)n1 * p2;
-    for (int job = blockIdx.x; job < M * drho; job += gridDim.x) {
-        const int m = job / drho, a = job % drho;   // cube m is box m (level 0, cube order)
-        const T* pr = proxy + ((size_t)m * drho + a) * p3;
-        int mc[3] = {m % g.M[0], (m / g.M[0]) % g.M[1], m / (g.M[0] * g.M[1])};
-        const double cm[3] = {(mc[0] + 0.5) * g.s, (mc[1] + 0.5) * g.s, (mc[2] + 0.5) * g.s};
-        __syncthreads();
-        for (int e = threadIdx.x; e < n1 * p2; e += blockDim.x) {
-            const int i1 = e / p2, r = e % p2;
-            Cx<double> v = {0, 0};
-            for (int k = 0; k < p; ++k) cfmar(v, rt.S[0][i1 * p + k], (double)pr[k * p2 + r]);
-            B1[e] = v;
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < n1 * n2 * p; e += blockDim.x) {
-            const int i1 = e / (n2 * p), i2 = (e / p) % n2, j3 = e % p;
-            Cx<double> v = {0, 0};
-            for (int k = 0; k < p; ++k) cfma(v, rt.S[1][i2 * p + k], B1[((size_t)i1 * p + k) * p + j3]);
-            B2[e] = v;
-        }
-        __syncthreads();
-        Cx<double>* out = chi_part + (size_t)job * rt.nmode;
-        for (int e = threadIdx.x; e < rt.nmode; e += blockDim.x) {
-            const int i1 = e / (n2 * n3), i2 = (e / n3) % n2, i3 = e % n3;
-            Cx<double> v = {0, 0};
-            for (int k = 0; k < p; ++k) cfma(v, rt.S[2][i3 * p + k], B2[((size_t)i1 * n2 + i2) * p + k]);
-            const double ph = -(rt.kax[0][i1] * cm[0] + rt.kax[1][i2] * cm[1] + rt.kax[2][i3] * cm[2]);
-            double sn, cs;
-            sincos(ph, &sn, &cs);
-            out[e] = cmul(v, Cx<double>{cs, sn});
-        }
-    }
-}
-
 // sum over cubes and apply the symbol: uhat[j][k] = sum_a W[k][j][a] sum_m chi_m,a(k)
 __global__ void k_root_apply(int M, int drho, int du, RootTab rt, const Cx<double>* __restrict__ chi_part,
                              Cx<double>* __restrict__ uhat) {
@@ -730,61 +689,8 @@ __global__ void k_root_apply(int M, int drho, int du, RootTab rt, const Cx<doubl
     }
 }
 
-// u_m(j) = Re sum_k uhat(k) exp(i k . (c_m + y_j)) + constant, written to the cube's local grid
-template <class T>
-__global__ void k_root_eval(int M, int du, int p, Geo g, RootTab rt, const Cx<double>* __restrict__ uhat,
-                            const double* __restrict__ rho_sum, int drho, T* __restrict__ local,
-                            unsigned char* scratch, size_t per_cta) {
-    const int p2 = p * p, p3 = p2 * p;
-    const int n1 = rt.n1, n2 = rt.n2, n3 = rt.n3;
-    Cx<double>* C2 = reinterpret_cast<Cx<double>*>(scratch + (size_t)blockIdx.x * per_cta);
-    Cx<double>* C1 = C2 + (size_t)n1 * n2 * p;
-    Cx<double>* G = C1 + (size_t)n1 * p2;
-    for (int job = blockIdx.x; job < M * du; job += gridDim.x) {
-        const int m = job / du, j = job % du;
-        int mc[3] = {m % g.M[0], (m / g.M[0]) % g.M[1], m / (g.M[0] * g.M[1])};
-        const double cm[3] = {(mc[0] + 0.5) * g.s, (mc[1] + 0.5) * g.s, (mc[2] + 0.5) * g.s};
-        __syncthreads();
-        for (int e = threadIdx.x; e < rt.nmode; e += blockDim.x) {
-            const int i1 = e / (n2 * n3), i2 = (e / n3) % n2, i3 = e % n3;
-            const double ph = rt.kax[0][i1] * cm[0] + rt.kax[1][i2] * cm[1] + rt.kax[2][i3] * cm[2];
-            double sn, cs;
-            sincos(ph, &sn, &cs);
-            G[e] = cmul(uhat[(size_t)j * rt.nmode + e], Cx<double>{cs, sn});
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < n1 * n2 * p; e += blockDim.x) {      // k3 -> j3
-            const int i12 = e / p, j3 = e % p;
-            Cx<double> v = {0, 0};
-            for (int k = 0; k < n3; ++k) cfma(v, cconj(rt.S[2][k * p + j3]), G[(size_t)i12 * n3 + k]);
-            C2[e] = v;
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < n1 * p2; e += blockDim.x) {          // k2 -> j2
-            const int i1 = e / p2, j2 = (e / p) % p, j3 = e % p;
-            Cx<double> v = {0, 0};
-            for (int k = 0; k < n2; ++k) cfma(v, cconj(rt.S[1][k * p + j2]), C2[((size_t)i1 * n2 + k) * p + j3]);
-            C1[e] = v;
-        }
-        __syncthreads();
-        double cst = 0;
-        if (rho_sum) for (int a = 0; a < drho; ++a) cst += rt.rconst[j * drho + a] * rho_sum[a];
-        T* u = local + ((size_t)m * du + j) * p3;
-        for (int e = threadIdx.x; e < p3; e += blockDim.x) {                // k1 -> j1, real part
-            const int j1 = e / p2, r = e % p2;
-            double v = 0;
-            for (int k = 0; k < n1; ++k) {
-                const Cx<double> f = cconj(rt.S[0][k * p + j1]);
-                const Cx<double> b = C1[(size_t)k * p2 + r];
-                v += f.x * b.x - f.y * b.y;
-            }
-            u[e] = (T)(v + cst);
-        }
-    }
-}
-
-// Root far field spread over the whole GPU: every stage of the tensor-form sums (the same
-// contractions as k_root_chi / k_root_eval) is its own launch with one thread per output
+// Root far field spread over the whole GPU: every stage of the tensor-form sums of Eqs.
+// structurefac and eval_tensor is its own launch with one thread per output
 // element of all cubes and components, so that the FP64 work is not confined to one CTA per
 // cube.  Scratch layout per job (cube m, component): B1 n1 x p^2, B2 n1 x n2 x p (forward);
 // G nmode, C2 n1 x n2 x p, C1 n1 x p^2 (backward).
@@ -1089,28 +995,6 @@ __global__ void k_vjp_target(int64_t N, int du, const double* __restrict__ gu, c
     double v = 0;
     for (int j = 0; j < du; ++j) v = fma(gu[(a * 3 + i) * du + j], g[a * du + j], v);
     d[t] = v;
-}
-
-__global__ void k_strength_sums(int64_t N, int drho, const double* __restrict__ rho, double* __restrict__ out) {
-    // out[a] = sum rho_a, out[drho + a] = sum |rho_a|
-    double s[9], sa[9];
-    for (int a = 0; a < drho; ++a) { s[a] = 0; sa[a] = 0; }
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-        for (int a = 0; a < drho; ++a) {
-            const double v = rho[i * drho + a];
-            s[a] += v;
-            sa[a] += fabs(v);
-        }
-    for (int a = 0; a < drho; ++a) {
-        for (int o = 16; o > 0; o >>= 1) {
-            s[a] += __shfl_down_sync(0xffffffffu, s[a], o);
-            sa[a] += __shfl_down_sync(0xffffffffu, sa[a], o);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(out + a, s[a]);
-            atomicAdd(out + drho + a, sa[a]);
-        }
-    }
 }
 
 // ------------------------------------------------------------------------------------------
