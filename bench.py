@@ -375,6 +375,9 @@ def main():
                     "pairs_in_support": in_support,
                     "support_fraction": (in_support / pairs) if in_support else None},
             "stage_ms": dict(zip(STAGES, mixed["stage"])),
+            # the paper's timing convention (Sec. 6): the evaluation without the octree build,
+            # from the stage-timing pass
+            "ms_excluding_tree": mixed["stage"][6] - mixed["stage"][0],
             "tree": {k: st[k] for k in ("n_levels", "n_boxes", "n_leaves", "n_nonleaf", "n_direct_entries")},
             "roofline": roof,
             "clocks": mixed["clocks"],
