@@ -190,11 +190,13 @@ def extra_configs(dmk, Wl, dev, stream, steps=3, warmup=2):
                 ms.append(a.elapsed_time(b))
             st = plan.stats()
             t = statistics.median(ms)
-            # one more pass with per-stage events
+            # one more pass with per-stage events, in order (each kernel alone on the SMs)
             plan.set_timing(True)
+            plan.set_pair_overlap(False)
             step()
             torch.cuda.synchronize()
             stage = plan.stats()["stage_ms"]
+            plan.set_pair_overlap(True)
             plan.set_timing(False)
             out.append({"workload": name, "N": N, "ms_per_step": t, "targets_per_s": N / (t / 1e3),
                         "p": st["p"], "n_boxes": st["n_boxes"], "n_levels": st["n_levels"], "pairs": st["n_pairs"],
@@ -295,8 +297,12 @@ def main():
                         stream=stream.cuda_stream)
         with Clocks(local_rank) as ck:
             ms, stats, wall, _ = timed(plan, args.steps, args.warmup)
+        # per-kernel times: the stage-timing pass runs in order (the residual kernel alone on the
+        # SMs), the timed steps above with it beside the far field (the default)
         plan.set_timing(True)
+        plan.set_pair_overlap(False)
         _, st_t, _, _ = timed(plan, 5, 1)
+        plan.set_pair_overlap(True)
         plan.set_timing(False)
         # per-stage median over the timing steps (the tree stage holds host round trips and
         # varies from step to step)

@@ -227,6 +227,15 @@ typedef struct {
 /* Statistics of the last evaluation on this plan (n_device_allocs: as of this call). */
 dmk_status_t dmk_get_stats(dmk_plan_t plan, dmk_stats_t* out);
 
+/* Residual sums beside the far field: with enable = 1 (the default) the leaf residual kernel
+ * runs on a plan-owned second stream while the upward pass, root, plane waves and shifts run on
+ * the plan's stream (they need only the tree); the leaf expansions wait for it.  At most
+ * max_blocks_per_sm resident blocks of it per SM (0: as many as fit, the default).  The results
+ * are bitwise the same either way.  enable = 0 runs everything on the plan's stream in order
+ * (per-kernel timing with dmk_set_timing then measures each kernel alone).  The environment
+ * variables DMK_PAIR_OVERLAP and DMK_PAIR_BLOCKS, read at plan creation, set the same. */
+dmk_status_t dmk_set_pair_overlap(dmk_plan_t plan, int enable, int max_blocks_per_sm);
+
 /* Enables (1) or disables (0) per-stage CUDA-event timing inside dmk_eval (stage_ms). */
 dmk_status_t dmk_set_timing(dmk_plan_t plan, int enable);
 

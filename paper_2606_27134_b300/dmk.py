@@ -78,6 +78,7 @@ def load(path=None):
     lib.dmk_eval_targets.argtypes = [vp, c_i64, vp, vp, c_i64, vp, vp, vp]
     lib.dmk_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.dmk_set_timing.argtypes = [vp, c_int]
+    lib.dmk_set_pair_overlap.argtypes = [vp, c_int, c_int]
     lib.dmk_destroy.argtypes = [vp]
     lib.dmk_plan_info.argtypes = [c_int, c_int, dp, c_double, ctypes.POINTER(PlanInfo)]
     lib.dmk_plan_table.argtypes = [c_int, c_int, dp, c_double, c_int, dp, c_i64, ctypes.POINTER(c_i64)]
@@ -86,7 +87,7 @@ def load(path=None):
     lib.dmk_last_error.argtypes = [vp]
     lib.dmk_last_error.restype = ctypes.c_char_p
     for f in ("dmk_plan", "dmk_plan_ex", "dmk_eval", "dmk_eval_host", "dmk_eval_static", "dmk_vjp", "dmk_eval_shard",
-              "dmk_eval_targets", "dmk_get_stats",
+              "dmk_eval_targets", "dmk_get_stats", "dmk_set_pair_overlap",
               "dmk_set_timing",
               "dmk_destroy", "dmk_plan_info", "dmk_plan_table"):
         getattr(lib, f).restype = c_int
@@ -126,6 +127,10 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def set_pair_overlap(self, enable=True, max_blocks_per_sm=0):
+        """dmk_set_pair_overlap: the residual sums beside the far field (default) or in order."""
+        _check(load().dmk_set_pair_overlap(self._h, 1 if enable else 0, int(max_blocks_per_sm)), self._h)
 
     def set_timing(self, on=True):
         _check(load().dmk_set_timing(self._h, 1 if on else 0), self._h)

@@ -178,3 +178,21 @@ def test_evaluation_errors(prec):
     st, _ = _status(plan, x, q)
     assert st == 0
     plan.close()
+
+
+@pytest.mark.parametrize("kernel,D,L", [("laplace", 2, [1.0, 1.0, 0.25]), ("rotlet", 3, [1.0, 1.0, 4.0])])
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_pair_overlap_is_bitwise_neutral(kernel, D, L, precision):
+    """The residual sums beside the far field (default) and in order give the same bits."""
+    N = 20000
+    x = torch.tensor(W.uniform_points(N, L, 611), device="cuda")
+    q = torch.tensor(W.stokes_strengths(kernel, N, 612), device="cuda")
+    p = dmk.Plan(kernel, D, L, 1e-6, precision=precision, n_s=100)
+    u1, g1 = p.eval(x, q, grad=True)
+    p.set_pair_overlap(False)
+    u2, g2 = p.eval(x, q, grad=True)
+    p.set_pair_overlap(True, 2)
+    u3, g3 = p.eval(x, q, grad=True)
+    assert torch.equal(u1, u2) and torch.equal(g1, g2)
+    assert torch.equal(u1, u3) and torch.equal(g1, g3)
+    p.close()
