@@ -1423,6 +1423,13 @@ dmk_status_t make_plan(int k, int D, const double L[3], double tol, int prec, in
     }
     plan->geo.s = plan->T.s;
     plan->geo.D = D;
+    // exact reciprocals of powers of two (frexp mantissa 1/2); 0 marks "divide"
+    auto inv_pow2 = [](double v) {
+        int ex = 0;
+        return std::frexp(v, &ex) == 0.5 ? 1.0 / v : 0.0;
+    };
+    plan->geo.inv_s_pow2 = inv_pow2(plan->T.s);
+    for (int i = 0; i < 3; ++i) plan->geo.inv_L_pow2[i] = inv_pow2(plan->T.L[i]);
     for (int i = 0; i < 3; ++i) {
         plan->geo.wrap[i] = plan->T.wrap[i];
         plan->geo.origin[i] = plan->T.origin[i];

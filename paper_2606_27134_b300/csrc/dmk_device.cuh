@@ -53,6 +53,10 @@ struct Geo {
     double origin[3];
     int padded[3];
     int D;
+    // 1/s and 1/L_i where they are powers of two (division by them is then exactly the
+    // multiplication, bit for bit), else 0: the quantisation and the wrap use the division
+    double inv_s_pow2;
+    double inv_L_pow2[3];
 };
 
 // global integer index of a cell -> key (valid indices only)

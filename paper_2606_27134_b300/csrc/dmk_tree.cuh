@@ -15,7 +15,9 @@ constexpr int kErrIndex = 4;
 // oracle's quantisation).
 __device__ __forceinline__ int quantize_axis(const Geo& g, int a, double v) {
     const double scale = (double)(1u << kBits);
-    const double t = floor(__dmul_rn(__ddiv_rn(__dsub_rn(v, g.origin[a]), g.s), scale));
+    const double d = __dsub_rn(v, g.origin[a]);
+    const double q = g.inv_s_pow2 != 0.0 ? __dmul_rn(d, g.inv_s_pow2) : __ddiv_rn(d, g.s);
+    const double t = floor(__dmul_rn(q, scale));
     long long gi = (long long)t;
     const long long hi = ((long long)g.M[a] << kBits) - 1;
     gi = gi < 0 ? 0 : (gi > hi ? hi : gi);
@@ -34,7 +36,7 @@ __device__ __forceinline__ double wrap_coord(const Geo& g, int a, double x, int*
         x = 0.0;
     }
     if (g.wrap[a]) {
-        const double f = floor(__ddiv_rn(x, L));
+        const double f = floor(g.inv_L_pow2[a] != 0.0 ? __dmul_rn(x, g.inv_L_pow2[a]) : __ddiv_rn(x, L));
         v = __dsub_rn(x, __dmul_rn(L, f));
         if (v >= L) v = __dsub_rn(v, L);
         if (v < 0.0) v = 0.0;
