@@ -43,6 +43,10 @@ CASES = [
     ("rotlet-3P-nonexact", "rotlet", 3, [1, 1.3, 1.7], 1e-6, 500, 30, "mixed", "stokes"),
     ("stresslet-3P-nonexact", "stresslet", 3, [2, 1.3, 1.7], 1e-6, 500, 30, "mixed", "stokes"),
     ("stokeslet-2P-nonexact", "stokeslet", 2, [1.3, 1, 0.5], 1e-6, 500, 30, "mixed", "stokes"),
+    # cells of Table 2: three cubes along the periodic x1 with a free x3 of two; the singly
+    # periodic [3, 1, 2] (one cube of side 3)
+    ("laplace-2P-[3,1,2]", "laplace", 2, [3, 1, 2], 1e-6, 1500, 40, "mixed", "neutral"),
+    ("laplace-1P-[3,1,2]", "laplace", 1, [3, 1, 2], 1e-6, 1200, 40, "mixed", "neutral"),
     # free extents a few periods long and the unit cell at 1e-3: the App. E switch gives the
     # original symbol to the modes with a nonzero periodic wavenumber (two root parts)
     ("laplace-2P-tall-original", "laplace", 2, [1, 1, 4], 1e-6, 1500, 40, "mixed", "neutral"),

@@ -39,7 +39,10 @@ CASES = [(3, [1, 1, 1]), (3, [2, 1, 1]), (2, [1, 1, 0.5]), (2, [1, 2, 1]), (1, [
          (0, [1, 1, 1]),
          # non-exact tilings (Sec. 4.1.1-4.1.2: cut cubes, padding, source images): Table 2's
          # [1, 1.3, 1.7], the same with the padded axis first, and a slab with L_2 / L_1 = 1.3
-         (3, [1, 1.3, 1.7]), (3, [1.3, 1, 1.7]), (2, [1, 1.3, 0.5])]
+         (3, [1, 1.3, 1.7]), (3, [1.3, 1, 1.7]), (2, [1, 1.3, 0.5]),
+         # the other cells of Table 2: three cubes along a periodic axis with a free x3 of two,
+         # five cubes along x2, and the singly periodic [3, 1, 2] and [1, 1, 2]
+         (2, [3, 1, 2]), (2, [1, 5, 2]), (1, [3, 1, 2]), (1, [1, 1, 2])]
 
 
 @pytest.mark.parametrize("D,L", CASES, ids=lambda v: str(v))
