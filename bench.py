@@ -205,6 +205,30 @@ def extra_configs(dmk, Wl, dev, stream, steps=3, warmup=2):
                         "steps": steps, "warmup": warmup})
             if kernel != "laplace-autograd":
                 plan.close()
+            # the plain FP64 path on the same workload (one warm-up, two steps), beside the mixed
+            try:
+                if kernel == "laplace-autograd":
+                    pot = ag.Potential("laplace", D, L, 1e-6, precision="fp64", n_s=250)
+                    plan = pot.plan
+                else:
+                    plan = dmk.Plan(kernel, D, L, 1e-6, precision="fp64", n_s=250)
+                step()
+                torch.cuda.synchronize()
+                ms64 = []
+                for _ in range(2):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(torch.cuda.current_stream())
+                    step()
+                    b.record(torch.cuda.current_stream())
+                    torch.cuda.synchronize()
+                    ms64.append(a.elapsed_time(b))
+                t64 = statistics.median(ms64)
+                out[-1]["fp64_path"] = {"ms_per_step": t64, "targets_per_s": N / (t64 / 1e3), "steps": 2, "warmup": 1,
+                                        "mixed_over_fp64": t64 / t}
+                if kernel != "laplace-autograd":
+                    plan.close()
+            except Exception as e:  # reported, never fatal
+                out[-1]["fp64_path"] = {"error": str(e)[:200]}
             del xt, rt
             torch.cuda.empty_cache()
         except Exception as e:  # reported, never fatal
