@@ -10,9 +10,9 @@
  * when x_t = x_s, by the periodized dual-space multilevel kernel-splitting method:
  * leaf residual sums over periodically wrapped neighbour lists (Sec. 2.3, Eq. u_local),
  * per-level difference-kernel plane-wave interactions (Sec. 2.3 Eq. Dl_int_discr,
- * Sec. 3.1.4) and the root-level Fourier far field (Sec. 4.3, 4.4, 5.3).  Sources and
- * targets coincide (Sec. 1).  Kernels: Laplace K = 1/(4 pi r) and the Stokeslet,
- * stresslet and rotlet of App. B.
+ * Sec. 3.1.4) and the root-level Fourier far field (Sec. 4.3, 4.4, 5.3).  In dmk_eval the
+ * sources are the targets (Sec. 1); dmk_eval_targets takes a separate target set.  Kernels:
+ * Laplace K = 1/(4 pi r) and the Stokeslet, stresslet and rotlet of App. B.
  *
  * Conventions shared by every entry point
  *   - Arrays are plain pointers, row-major, FP64, owned by the caller.  "device" pointers
@@ -22,14 +22,13 @@
  *     outputs are left unspecified and dmk_last_error() gives a one-line detail.
  *   - A plan owns its tables and a device workspace that grows on demand; calls on one
  *     plan must not overlap (the plan is not thread-safe).  Work is enqueued on the plan's
- *     CUDA stream (with DMK_PAIR_OVERLAP=1, below, the residual sums of the leaf stage go to
- *     a second stream the plan owns, ordered against the first by events).  dmk_eval
- *     returns after all of it is complete (the host waits for the small readbacks of the
- *     tree build and for the device status word).
- *   - Environment, read when a plan is created: DMK_PAIR_OVERLAP=1 runs the residual sums
- *     (p <= 24; they need only the tree) beside the far field on the second stream;
- *     DMK_PAIR_BLOCKS=n caps their resident blocks per SM while they do (default 2;
- *     0 = no cap).  The default order is serial.
+ *     CUDA stream; the residual sums of the leaf stage (p <= 24; they need only the tree)
+ *     go to a second stream the plan owns, beside the far field, ordered against the first
+ *     by events (dmk_set_pair_overlap).  dmk_eval returns after all of it is complete (the
+ *     host waits for the small readbacks of the tree build and for the device status word).
+ *   - Environment, read when a plan is created: DMK_PAIR_OVERLAP=0 runs the residual sums
+ *     in order on the plan's stream instead; DMK_PAIR_BLOCKS=n caps their resident blocks
+ *     per SM beside the far field (default 0 = no cap).
  */
 #ifndef DMK_B300_H
 #define DMK_B300_H
@@ -58,8 +57,8 @@ typedef enum {
     DMK_ERR_INVALID_ARG = 1,   /* bad kernel, D, lengths, tol, n_s or a NULL pointer             */
     DMK_ERR_OUT_OF_DOMAIN = 2, /* a free (non-periodic) coordinate outside [0, L_i), or non-finite */
     DMK_ERR_NOT_NEUTRAL = 3,   /* Laplace with D = 1, 2 needs sum rho = 0 (Sec. 5.2)               */
-    DMK_ERR_UNSUPPORTED = 4,   /* periodic length not an integer multiple of the cube side
-                                  (non-exact tilings, Sec. 4.1.2, are not implemented)            */
+    DMK_ERR_UNSUPPORTED = 4,   /* a tiling of more than 1024 cubes; dmk_eval_shard on a
+                                  non-exact tiling                                               */
     DMK_ERR_TREE_DEPTH = 5,    /* reserved, never returned: a box at the depth cap (18 levels below
                                   a cube) that holds more than n_s points (coincident or nearly
                                   coincident points) stays a leaf, the result is still the
@@ -76,7 +75,11 @@ typedef struct dmk_plan_s* dmk_plan_t;
  * paper's parameter tables (Table 1 for Laplace, Table 5 for the Stokes kernels; Sec. 6.1):
  * the PSWF band limit c, the Chebyshev order p and n_f = ceil(3c/pi) - 1; a tol between
  * rows takes the next stricter row.  The cube side is s = min of the periodic lengths
- * (max L_i for D = 0); free lengths are rounded up to multiples of s (Sec. 4.1, Sec. 5).
+ * (max L_i for D = 0); free lengths are rounded up to multiples of s (Sec. 4.1, Sec. 5).  A
+ * periodic length that s does not divide is tiled by ceil(L_i / s) cubes, the last one cut,
+ * plus one padding cube on each side; the periodic images of the sources in the padded
+ * domain are added as sources and the structure factor counts the sources inside the cell
+ * only (Sec. 4.1.1, 4.1.2, 4.3).
  * Defaults: precision DMK_MIXED, n_s = 250 (Sec. 6), the legacy default stream.
  * On success *out receives a plan to be released with dmk_destroy. */
 dmk_status_t dmk_plan(dmk_kernel_t k, int D, double L1, double L2, double L3, double tol,
