@@ -253,13 +253,20 @@ dmk_status_t dmk_set_timing(dmk_plan_t plan, int enable);
  * Nyquist step pi/L_j, is at most tol in every free direction j, the modes with a nonzero
  * periodic wavenumber use the original symbol on that step (the second part) and the first part
  * keeps only the zero periodic wavenumber with the truncated symbols; otherwise one part, the
- * truncated symbol for every mode. */
+ * truncated symbol for every mode.
+ * Sums over the cubes (Sec. 3.4 Cases 1 and 2, Sec. 5.4): root_dft_len[3 part + a] = Q_a, the
+ * length of the DFT over the cube index along axis a that replaces the direct sum of Eqs.
+ * structurefac and eval_tensor over the cubes -- M_a on an exactly tiled periodic axis, on a free
+ * axis of step h the oversampled length 2 pi / (h s) (Eq. kappaqdef; it must be an integer
+ * >= M_a), 1 on an axis of one cube.  All six are 0 where the direct sums over the cubes are used
+ * (a single cube, a non-exact tiling, or a free step without an integer length). */
 typedef struct {
     double c, s, R, dk;
     int32_t p, n_f, n_root_modes, fit_terms_fp64, fit_terms_fp32;
     int32_t M[3];
     int32_t n_axis[3];
     int32_t d_rho, d_u;
+    int32_t root_dft_len[6];
 } dmk_plan_info_t;
 
 dmk_status_t dmk_plan_info(dmk_kernel_t k, int D, const double L[3], double tol, dmk_plan_info_t* out);

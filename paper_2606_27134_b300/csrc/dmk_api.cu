@@ -302,9 +302,10 @@ dmk_status_t upload_tab(dmk_plan_s* plan, void** mem, Tab<T>& tab, double fit_to
     return DMK_OK;
 }
 
-// one root part (wavenumber axes, weights on their rectangle) as a device table
+// one root part (wavenumber axes, weights on their rectangle, cube-index DFT lengths Q or
+// nullptr) as a device table
 dmk_status_t upload_root_part(dmk_plan_s* plan, const std::vector<double>* kax, const std::vector<std::complex<double>>& Wr,
-                              void** dptr, RootTab& rt) {
+                              const int* Q, void** dptr, RootTab& rt) {
     const PlanTables& P = plan->T;
     const int p = P.p;
     std::vector<double> h;
@@ -328,25 +329,22 @@ dmk_status_t upload_root_part(dmk_plan_s* plan, const std::vector<double>* kax, 
     for (auto& z : Wr) { h.push_back(z.real()); h.push_back(z.imag()); }
     size_t o_c = h.size();
     for (double v : P.root_const) h.push_back(v);
-    // exp(2 pi i k / M3), k = 0..M3-1, for the DFT over the cube index
-    pad();
-    size_t o_r = h.size();
-    {
-        const int M3 = std::max(1, P.M[2]);
-        for (int k = 0; k < M3; ++k) {
-            const double a = 2 * 3.14159265358979323846 * (double)k / M3;
-            h.push_back(std::cos(a));
-            h.push_back(std::sin(a));
+    // per axis: exp(2 pi i t / Q), t = 0..Q-1, and n mod Q for every wavenumber k = 2 pi n / (Q s)
+    size_t o_r[3], o_n[3];
+    int Qa[3];
+    for (int a = 0; a < 3; ++a) {
+        Qa[a] = Q && Q[a] > 0 ? Q[a] : 1;
+        pad();
+        o_r[a] = h.size();
+        for (int t = 0; t < Qa[a]; ++t) {
+            const double ang = 2 * 3.14159265358979323846 * (double)t / Qa[a];
+            h.push_back(std::cos(ang));
+            h.push_back(std::sin(ang));
         }
-    }
-    // n3 mod M3 per x3 wavenumber (used when x3 is periodic: k3 = 2 pi n3 / L3)
-    size_t o_n = h.size();
-    {
-        const int M3 = std::max(1, P.M[2]);
-        const double L3 = P.L[2];
-        for (double k : kax[2]) {
-            const long long n3 = std::llround(k * L3 / (2 * 3.14159265358979323846));
-            h.push_back((double)(((n3 % M3) + M3) % M3));
+        o_n[a] = h.size();
+        for (double k : kax[a]) {
+            const long long n = std::llround(k * Qa[a] * P.s / (2 * 3.14159265358979323846));
+            h.push_back((double)(((n % Qa[a]) + Qa[a]) % Qa[a]));
         }
     }
     cudaError_t e = cudaMalloc(dptr, h.size() * sizeof(double));
@@ -363,16 +361,21 @@ dmk_status_t upload_root_part(dmk_plan_s* plan, const std::vector<double>* kax, 
     }
     rt.W = reinterpret_cast<const Cx<double>*>(base + o_W);
     rt.rconst = base + o_c;
-    rt.nmod3 = base + o_n;
-    rt.roots = reinterpret_cast<const Cx<double>*>(base + o_r);
+    for (int a = 0; a < 3; ++a) {
+        rt.Q[a] = Qa[a];
+        rt.nmod[a] = base + o_n[a];
+        rt.roots[a] = reinterpret_cast<const Cx<double>*>(base + o_r[a]);
+    }
     return DMK_OK;
 }
 
 dmk_status_t upload_root(dmk_plan_s* plan) {
     const PlanTables& P = plan->T;
-    CKS(upload_root_part(plan, P.kax, P.Wroot, &plan->d_root, plan->root));
+    CKS(upload_root_part(plan, P.kax, P.Wroot, P.root_dft ? P.root_dft_Q[0] : nullptr, &plan->d_root, plan->root));
     plan->root2 = RootTab{};
-    if (P.original_symbol) CKS(upload_root_part(plan, P.kax2, P.Wroot2, &plan->d_root2, plan->root2));
+    if (P.original_symbol)
+        CKS(upload_root_part(plan, P.kax2, P.Wroot2, P.root_dft ? P.root_dft_Q[1] : nullptr, &plan->d_root2,
+                             plan->root2));
     cudaError_t e;
     // self tables
     std::vector<double> sv(P.self_val);
@@ -1056,17 +1059,29 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* p
         const RootTab& rt2 = plan->root2;
         const int nparts = rt2.nmode > 0 ? 2 : 1;
         const int nmode_max = std::max(rt.nmode, rt2.nmode);
+        // sums over the cubes as DFTs over the cube index (Sec. 3.4, 5.4) where the plan admits them
+        const bool dft_root = P.root_dft;
         void *vchi, *vuh, *vrsc;
-        CKS(ensure(plan, B_CHI, (size_t)Mtot * drho * (rt.nmode + rt2.nmode) * sizeof(Cx<double>), &vchi));
+        CKS(ensure(plan, B_CHI, (size_t)(dft_root ? 1 : Mtot) * drho * (rt.nmode + rt2.nmode) * sizeof(Cx<double>),
+                   &vchi));
         CKS(ensure(plan, B_UHAT, (size_t)du * nmode_max * sizeof(Cx<double>), &vuh));
-        // scratch: forward B1 (n1 p^2) + B2 (n1 n2 p) per (cube, strength component); backward
-        // G (nmode) + C2 (n1 n2 p) + C1 (n1 p^2) per (cube, potential component)
-        const size_t f1 = (size_t)rt.n1 * p * p, f2 = (size_t)rt.n1 * rt.n2 * p;
         const int jf = Mtot * drho, jb = Mtot * du;
-        size_t nscr = std::max((size_t)jf * (f1 + f2), (size_t)jb * (rt.nmode + f2 + f1));
-        if (nparts == 2) {
-            const size_t g1 = (size_t)rt2.n1 * p * p, g2 = (size_t)rt2.n1 * rt2.n2 * p;
-            nscr = std::max(nscr, std::max((size_t)jf * (g1 + g2), (size_t)jb * (rt2.nmode + g2 + g1)));
+        // scratch of the direct sums: forward B1 (n1 p^2) + B2 (n1 n2 p) per (cube, strength
+        // component); backward G (nmode) + C2 (n1 n2 p) + C1 (n1 p^2) per (cube, potential
+        // component).  Of the DFTs: forward B1 and B2 per (cube, component), the sums over m1, m2
+        // (M3 n1 n2 p) and the transform (Q3 n1 n2 p) per component; backward C2 (Q3 n1 n2 p) and
+        // Dm (M3 n1 n2 p) per component, C1 per (cube, component)
+        size_t nscr = 0;
+        for (int ip = 0; ip < nparts; ++ip) {
+            const RootTab& r = ip == 0 ? rt : rt2;
+            const size_t h1 = (size_t)r.n1 * p * p, h2 = (size_t)r.n1 * r.n2 * p;
+            if (dft_root) {
+                const size_t M3 = (size_t)g.M[2], Q3 = (size_t)r.Q[2];
+                nscr = std::max(nscr, (size_t)jf * (h1 + h2) + (M3 + Q3) * drho * h2);
+                nscr = std::max(nscr, (Q3 + M3) * du * h2 + (size_t)jb * h1);
+            } else {
+                nscr = std::max(nscr, std::max((size_t)jf * (h1 + h2), (size_t)jb * (r.nmode + h2 + h1)));
+            }
         }
         CKS(ensure(plan, B_SCRATCH, nscr * sizeof(Cx<double>), &vrsc));
         Cx<double>* r0 = (Cx<double>*)vrsc;
@@ -1120,41 +1135,49 @@ dmk_status_t run_eval(dmk_plan_s* plan, Tab<T>& tab, int64_t N0, const double* p
             rproxy = chip;
             ++launches;
         }
-        // cubes stacked along a periodic x3: DFT over the cube index (Sec. 3.4, Case 1)
-        const bool fft_root = !padded && P.D == 3 && g.M[0] == 1 && g.M[1] == 1 && g.M[2] >= kRootFftMin &&
-                              g.M[2] <= kRootFftMax;
-        if (fft_root) {
-            const int M3 = g.M[2];
-            const size_t E = f2;                                   // n1 n2 p per (cube, component)
-            const size_t need = std::max((size_t)jf * (f1 + 2 * f2),
-                                         (size_t)M3 * du * (f2 + f1 + (size_t)p * p * p));
-            CKS(ensure(plan, B_SCRATCH, need * sizeof(Cx<double>), &vrsc));
-            Cx<double>* q0 = (Cx<double>*)vrsc;
-            Cx<double>* chi = (Cx<double>*)vchi;
-            Cx<double>* uh = (Cx<double>*)vuh;
-            Cx<double>* B1f = q0;
-            Cx<double>* B2f = B1f + (size_t)jf * f1;
-            Cx<double>* Bh = B2f + (size_t)jf * f2;
-            k_root_fwd1<T><<<blocks((int64_t)jf * f1), 128, 0, st>>>(jf, p, rt, rproxy, B1f);
-            k_root_fwd2<<<blocks((int64_t)jf * f2), 128, 0, st>>>(jf, p, rt, B1f, B2f);
-            k_rootfft_dft<<<blocks((int64_t)M3 * drho * E), 128, 0, st>>>(M3, drho, (int)E, rt, B2f, Bh);
-            k_rootfft_chi<<<blocks((int64_t)drho * rt.nmode), 128, 0, st>>>(drho, p, g, rt, Bh, chi);
-            CKS(reduce_chi(plan, sh, chi, (int64_t)2 * drho * rt.nmode, d_sums));
-            k_root_apply<<<nblk(rt.nmode, 128), 128, 0, st>>>(1, drho, du, rt, chi, uh);
-            const int jbb = M3 * du;
-            Cx<double>* C2 = q0;
-            Cx<double>* C1 = C2 + (size_t)jbb * f2;
-            Cx<double>* Gs = C1 + (size_t)jbb * f1;
-            k_rootfft_bwd1<<<blocks((int64_t)jbb * f2), 128, 0, st>>>(M3, du, p, g, rt, uh, C2);
-            k_root_bwd2<<<blocks((int64_t)jbb * f1), 128, 0, st>>>(jbb, p, rt, C2, C1);
-            k_rootfft_bwd3<<<blocks((int64_t)jbb * p * p * p), 128, 0, st>>>(jbb, p, rt, C1, Gs);
-            k_rootfft_idft<T><<<blocks((int64_t)M3 * du * p * p * p), 128, 0, st>>>(M3, du, p, rt, Gs, nullptr, drho,
-                                                                                     local);
-            launches += 9;
+        const RootTab* parts[2] = {&rt, &rt2};
+        if (dft_root) {
+            // per part: chi of all cubes as one (part 1 after part 0), one reduction of both
+            // (sharded evaluations), then the evaluation; part 1 adds to part 0
+            const int M1 = g.M[0], M2 = g.M[1], M3 = g.M[2];
+            Cx<double>* chis[2] = {chi, chi + (size_t)drho * rt.nmode};
+            for (int ip = 0; ip < nparts; ++ip) {
+                const RootTab& r = *parts[ip];
+                const size_t h1 = (size_t)r.n1 * p * p, h2 = (size_t)r.n1 * r.n2 * p;
+                Cx<double>* B1f = r0;
+                Cx<double>* B2f = B1f + (size_t)jf * h1;
+                Cx<double>* Af = B2f + (size_t)jf * h2;
+                Cx<double>* Bh = Af + (size_t)M3 * drho * h2;
+                k_root_fwd1<T><<<blocks((int64_t)jf * h1), 128, 0, st>>>(jf, p, r, rproxy, B1f);
+                k_root_fwd2<<<blocks((int64_t)jf * h2), 128, 0, st>>>(jf, p, r, B1f, B2f);
+                const Cx<double>* a3 = B2f;
+                if (M1 * M2 > 1) {
+                    k_rootdft_fold12<<<blocks((int64_t)M3 * drho * h2), 128, 0, st>>>(M1, M2, M3, drho, p, r, B2f,
+                                                                                        Af);
+                    a3 = Af;
+                    ++launches;
+                }
+                k_rootdft_fwd3<<<blocks((int64_t)r.Q[2] * drho * h2), 128, 0, st>>>(M3, drho, (int)h2, r, a3, Bh);
+                k_rootdft_chi<<<blocks((int64_t)drho * r.nmode), 128, 0, st>>>(drho, p, g, r, Bh, chis[ip]);
+                launches += 4;
+            }
+            CKS(reduce_chi(plan, sh, chi, (int64_t)2 * drho * (rt.nmode + rt2.nmode), d_sums));
+            for (int ip = 0; ip < nparts; ++ip) {
+                const RootTab& r = *parts[ip];
+                const size_t h1 = (size_t)r.n1 * p * p, h2 = (size_t)r.n1 * r.n2 * p;
+                k_root_apply<<<nblk(r.nmode, 128), 128, 0, st>>>(1, drho, du, r, chis[ip], uh);
+                Cx<double>* C2 = r0;
+                Cx<double>* Dm = C2 + (size_t)r.Q[2] * du * h2;
+                Cx<double>* C1 = Dm + (size_t)M3 * du * h2;
+                k_rootdft_bwd1<<<blocks((int64_t)r.Q[2] * du * h2), 128, 0, st>>>(du, p, g, r, uh, C2);
+                k_rootdft_idft3<<<blocks((int64_t)M3 * du * h2), 128, 0, st>>>(M3, du, (int)h2, r, C2, Dm);
+                k_rootdft_bwd2<<<blocks((int64_t)jb * h1), 128, 0, st>>>(Mtot, du, p, g, r, Dm, C1);
+                k_rootdft_bwd3<T><<<blocks((int64_t)jb * p * p * p), 128, 0, st>>>(Mtot, du, p, g, r, C1, local, ip);
+                launches += 5;
+            }
         } else {
         // per part: structure factor of every cube (chi of part 1 after that of part 0), one
         // reduction of both (sharded evaluations), then the evaluation; part 1 adds to part 0
-        const RootTab* parts[2] = {&rt, &rt2};
         Cx<double>* chis[2] = {chi, chi + (size_t)Mtot * drho * rt.nmode};
         for (int ip = 0; ip < nparts; ++ip) {
             const RootTab& r = *parts[ip];
@@ -1531,10 +1554,8 @@ dmk_status_t dmk_eval_shard(dmk_plan_t plan, int64_t N, int64_t n_own, const dou
     if (N == 0) {
         // nothing local, but the other ranks' reduction still needs this rank's (zero) share
         const RootTab& rt = plan->root;
-        const bool fft = plan->T.D == 3 && plan->geo.M[0] == 1 && plan->geo.M[1] == 1 &&
-                         plan->geo.M[2] >= kRootFftMin && plan->geo.M[2] <= kRootFftMax;
         const int Mtot = plan->geo.M[0] * plan->geo.M[1] * plan->geo.M[2];
-        const int64_t n = (int64_t)2 * (fft ? 1 : Mtot) * plan->T.d_rho * (rt.nmode + plan->root2.nmode);
+        const int64_t n = (int64_t)2 * (plan->T.root_dft ? 1 : Mtot) * plan->T.d_rho * (rt.nmode + plan->root2.nmode);
         void* vchi;
         CKS(ensure(plan, B_CHI, (size_t)(n + 2 * plan->T.d_rho) * sizeof(double), &vchi));
         CK(cudaMemsetAsync(vchi, 0, (size_t)(n + 2 * plan->T.d_rho) * sizeof(double), plan->stream));
@@ -1763,6 +1784,8 @@ dmk_status_t dmk_plan_info(dmk_kernel_t k, int D, const double L[3], double tol,
     out->fit_terms_fp32 = nterms(T.fit_q, 1e-9);
     for (int i = 0; i < 3; ++i) { out->M[i] = T.M[i]; out->n_axis[i] = (int)T.kax[i].size(); }
     out->d_rho = T.d_rho; out->d_u = T.d_u;
+    for (int part = 0; part < 2; ++part)
+        for (int a = 0; a < 3; ++a) out->root_dft_len[3 * part + a] = T.root_dft_Q[part][a];
     return DMK_OK;
 }
 

@@ -54,6 +54,14 @@ struct PlanTables {
     std::vector<double> kax2[3];
     std::vector<std::complex<double>> Wroot2;
     int n_root_modes = 0;           // retained modes of both parts
+    // Sums over the cubes as DFTs over the cube index (Sec. 3.4 Cases 1 and 2, Sec. 5.4): on an
+    // exact tiling of two or more cubes where every axis a of every root part has wavenumbers
+    // k = 2 pi n / (Q_a s) for an integer Q_a >= M_a (periodic axes: Q_a = M_a; free axes: the
+    // oversampled length 2 pi / (step s), e.g. 2 (M_3 + 1) for the step pi/R of D = 2), the
+    // phase of cube m is exp(-2 pi i sum_a (n_a mod Q_a) m_a / Q_a) times that of cube 0.
+    // root_dft_Q[part][a] = Q_a (1 on axes of one cube or a k = 0 line), all 0 if not used.
+    bool root_dft = false;
+    int root_dft_Q[2][3] = {{0, 0, 0}, {0, 0, 0}};
     double R = 0;                   // truncation radius (D < 3)
     std::vector<double> root_const; // d_u x d_rho constant added per unit summed strength
     // self correction at level 0 (scale 1/nu for the value, 1/nu^3 for the gradient)

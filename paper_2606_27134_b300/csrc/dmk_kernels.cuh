@@ -663,12 +663,13 @@ __global__ void k_pwin(int n, const int* __restrict__ nl_box, BoxArrays B, Tab<T
 // Root far field (Sec. 4.3 Eqs. structurefac and eval_tensor; Sec. 5.3 Eq. ewald_far_allP_discr), FP64.
 struct RootTab {
     int n1, n2, n3, nmode;
+    int Q[3];                    // cube-index DFT length per axis (1 without one)
     const double* kax[3];
     const Cx<double>* S[3];      // S_i[k * p + j] = exp(-i k (s/2) eta_j)
     const Cx<double>* W;         // nmode x du x drho
     const double* rconst;        // du x drho
-    const double* nmod3;         // per x3 wavenumber k3 = 2 pi n3 / L3: n3 mod M3 (periodic x3)
-    const Cx<double>* roots;     // exp(2 pi i k / M3), k = 0..M3-1 (the cube-index DFT)
+    const double* nmod[3];       // per wavenumber k = 2 pi n / (Q_a s) of axis a: n mod Q_a
+    const Cx<double>* roots[3];  // exp(2 pi i t / Q_a), t = 0..Q_a-1
 };
 
 // sum over cubes and apply the symbol: uhat[j][k] = sum_a W[k][j][a] sum_m chi_m,a(k)
@@ -832,45 +833,69 @@ __global__ void k_chi_proxy(int Mtot, int drho, int p3, const int* __restrict__ 
     chip[t] = cls[cube] == 0 ? proxy[t] : T(0);
 }
 
-// ---- root far field for cubes stacked along a periodic x3 (Sec. 3.4 "Case 1: elongated
-// cuboid", Eqs. beta_def, 1d-DFT-beta, structfac-case1-wDFTCoeffs, ufar_inverse_fft) ----------
-// With M3 cubes of side s along x3 and k3 = 2 pi n3 / (M3 s), the cube phase exp(-i k . c_m) is
-// exp(-i k . c_0) exp(-2 pi i (n3 mod M3) m / M3): the sum over cubes becomes a length-M3 DFT
-// over the cube index of the partial sums beta_m(j3; k1, k2) (contracted over j1, j2), taken once
-// for all modes.  The evaluation is the transpose: partial sums G_s grouped by n3 mod M3, then
-// an inverse DFT over s gives every cube's grid.  The length-M3 transforms are direct sums, one
-// thread per output (M3 <= kRootFftMax); the quadratic cost is then in M3 n1 n2 p, not in the
-// number of modes.
+// ---- root far field as DFTs over the cube index (Sec. 3.4 "Case 1: elongated cuboid" and
+// "Case 2: two long sides", Eqs. beta_def, 1d-DFT-beta, structfac-case1-wDFTCoeffs,
+// ufar_inverse_fft; Sec. 5.4 for free directions, Eqs. kappaqdef, beta_hat_oversampled,
+// structurefac_oversampled_fft) ------------------------------------------------------------
+// On an exact tiling of M1 x M2 x M3 cubes of side s whose wavenumbers are k_a = 2 pi n_a /
+// (Q_a s) on every axis (Q_a = M_a on a periodic axis, the oversampled length Q_a >= M_a on a
+// free one), the phase of cube m is exp(-i k . c_0) prod_a exp(-2 pi i (n_a mod Q_a) m_a / Q_a).
+// Forward: the partial sums beta_m(j3; k1, k2) (contracted over j1 and j2 per cube) are summed
+// over m1 and m2 at the one frequency each (k1, k2) needs, then transformed over m3 to all Q3
+// frequencies (zero padded from M3 to Q3); chi(k) contracts j3 of that transform at n3 mod Q3.
+// Evaluation, the transpose: sums over the modes grouped by n3 mod Q3, an inverse transform of
+// the groups to every m3, then per cube the k2 -> j2 and k1 -> j1 contractions with that cube's
+// phases for m2 and m1.  The transforms are direct sums, one thread per output: their cost is
+// M3 Q3 n1 n2 p per component, against M n1 n2 n3 p for the direct sums over the cubes.
 
-constexpr int kRootFftMin = 2;       // cubes along x3 from which the cube-index DFT path is used
-constexpr int kRootFftMax = 4096;
-
-// forward: beta_hat[(s drho + a) E + e] = sum_m exp(-2 pi i s m / M3) beta[(m drho + a) E + e],
-// one thread per output (direct length-M3 sum; M3 <= kRootFftMax)
-__global__ void k_rootfft_dft(int M, int drho, int E, RootTab rt, const Cx<double>* __restrict__ beta,
-                              Cx<double>* __restrict__ bhat) {
-    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// A[(m3 drho + a) E + e] = sum_{m1, m2} exp(-2 pi i (s1 m1 / Q1 + s2 m2 / Q2)) beta[(m drho + a) E + e]
+// with E = n1 n2 p, e = (i1 n2 + i2) p + j3, s_a = n_a mod Q_a of i_a, m = m1 + M1 (m2 + M2 m3)
+__global__ void k_rootdft_fold12(int M1, int M2, int M3, int drho, int p, RootTab rt,
+                                 const Cx<double>* __restrict__ beta, Cx<double>* __restrict__ A) {
+    const int n2 = rt.n2, E = rt.n1 * n2 * p;
     const int64_t per = (int64_t)drho * E;
-    if (id >= (int64_t)M * per) return;
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= (int64_t)M3 * per) return;
+    const int m3 = (int)(id / per);
+    const int64_t t = id % per;
+    const int e = (int)(t % E);
+    const int i1 = e / (n2 * p), i2 = (e / p) % n2;
+    const int s1 = (int)rt.nmod[0][i1], s2 = (int)rt.nmod[1][i2];
+    Cx<double> v = {0, 0};
+    for (int m2 = 0; m2 < M2; ++m2) {
+        const Cx<double> w2 = rt.roots[1][(int)(((int64_t)s2 * m2) % rt.Q[1])];
+        for (int m1 = 0; m1 < M1; ++m1) {
+            const Cx<double> w = cmul(rt.roots[0][(int)(((int64_t)s1 * m1) % rt.Q[0])], w2);
+            const int64_t m = m1 + (int64_t)M1 * (m2 + (int64_t)M2 * m3);
+            cfma(v, cconj(w), beta[m * per + t]);
+        }
+    }
+    A[id] = v;
+}
+
+// bhat[(s drho + a) E + e] = sum_{m3 < M3} exp(-2 pi i s m3 / Q3) A[(m3 drho + a) E + e], s < Q3
+__global__ void k_rootdft_fwd3(int M3, int drho, int E, RootTab rt, const Cx<double>* __restrict__ A,
+                               Cx<double>* __restrict__ bhat) {
+    const int Q3 = rt.Q[2];
+    const int64_t per = (int64_t)drho * E;
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= (int64_t)Q3 * per) return;
     const int sidx = (int)(id / per);
     const int64_t t = id % per;
     Cx<double> v = {0, 0};
-    for (int m = 0; m < M; ++m) {
-        const Cx<double> w = rt.roots[(sidx * m) % M];
-        cfma(v, Cx<double>{w.x, -w.y}, beta[(size_t)m * per + t]);
-    }
+    for (int m = 0; m < M3; ++m) cfma(v, cconj(rt.roots[2][(int)(((int64_t)sidx * m) % Q3)]), A[(size_t)m * per + t]);
     bhat[id] = v;
 }
 
-// chi(k) for component a (as one cube): exp(-i k . c_0) sum_j3 S3(j3, k3) beta_hat_{n3 mod M3}
-__global__ void k_rootfft_chi(int drho, int p, Geo g, RootTab rt, const Cx<double>* __restrict__ bhat,
+// chi(k) for component a (all cubes as one): exp(-i k . c_0) sum_j3 S3(j3, k3) bhat_{n3 mod Q3}
+__global__ void k_rootdft_chi(int drho, int p, Geo g, RootTab rt, const Cx<double>* __restrict__ bhat,
                               Cx<double>* __restrict__ chi) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= (int64_t)drho * rt.nmode) return;
     const int a = (int)(t / rt.nmode), e = (int)(t % rt.nmode);
     const int n2 = rt.n2, n3 = rt.n3, E = rt.n1 * n2 * p;
     const int i1 = e / (n2 * n3), i2 = (e / n3) % n2, i3 = e % n3;
-    const int sm = (int)rt.nmod3[i3];
+    const int sm = (int)rt.nmod[2][i3];
     const Cx<double>* b = bhat + ((size_t)sm * drho + a) * E + ((size_t)i1 * n2 + i2) * p;
     Cx<double> v = {0, 0};
     for (int k = 0; k < p; ++k) cfma(v, rt.S[2][i3 * p + k], b[k]);
@@ -881,21 +906,23 @@ __global__ void k_rootfft_chi(int drho, int p, Geo g, RootTab rt, const Cx<doubl
     chi[t] = cmul(v, Cx<double>{cs, sn});
 }
 
-// evaluation, k3 -> j3 grouped by s = n3 mod M3: C2[(s du + j)][i1][i2][j3] =
-//   sum_{i3 : n3 mod M3 = s} conj(S3(j3, k3)) exp(i k . c_0) uhat_j(k)
-__global__ void k_rootfft_bwd1(int M, int du, int p, Geo g, RootTab rt, const Cx<double>* __restrict__ uhat,
+// evaluation, k3 -> j3 grouped by s = n3 mod Q3: C2[(s du + j) E + e] =
+//   sum_{i3 : n3 mod Q3 = s} conj(S3(j3, k3)) exp(i k . c_0) uhat_j(k)
+__global__ void k_rootdft_bwd1(int du, int p, Geo g, RootTab rt, const Cx<double>* __restrict__ uhat,
                                Cx<double>* __restrict__ C2) {
-    const int n1 = rt.n1, n2 = rt.n2, n3 = rt.n3, per = n1 * n2 * p;
+    const int n2 = rt.n2, n3 = rt.n3, Q3 = rt.Q[2], per = rt.n1 * n2 * p;
     const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (id >= (int64_t)M * du * per) return;
+    if (id >= (int64_t)Q3 * du * per) return;
     const int job = (int)(id / per), e = (int)(id % per);
     const int sm = job / du, j = job % du;
     const int i12 = e / p, j3 = e % p;
     const int i1 = i12 / n2, i2 = i12 % n2;
     const double h = 0.5 * g.s;
+    // consecutive indices i3 are consecutive n3: the group is every Q3-th index from its first
+    const int first = ((sm - (int)rt.nmod[2][0]) % Q3 + Q3) % Q3;
     Cx<double> v = {0, 0};
-    for (int i3 = 0; i3 < n3; ++i3) {
-        if ((int)rt.nmod3[i3] != sm) continue;
+    for (int i3 = first; i3 < n3; i3 += Q3) {
+        if ((int)rt.nmod[2][i3] != sm) continue;
         const double ph = (rt.kax[0][i1] + rt.kax[1][i2] + rt.kax[2][i3]) * h;
         double sn, cs;
         sincos(ph, &sn, &cs);
@@ -905,41 +932,64 @@ __global__ void k_rootfft_bwd1(int M, int du, int p, Geo g, RootTab rt, const Cx
     C2[id] = v;
 }
 
-// k1 -> j1, complex: Gs[job][j1][j2][j3] = sum_i1 conj(S1(j1, k1)) C1[job][i1][j2][j3]
-__global__ void k_rootfft_bwd3(int jobs, int p, RootTab rt, const Cx<double>* __restrict__ C1,
-                               Cx<double>* __restrict__ Gs) {
-    const int p2 = p * p, p3 = p2 * p;
+// inverse transform to the cube index m3: Dm[(m3 du + j) E + e] = sum_{s < Q3} exp(2 pi i s m3 / Q3)
+//   C2[(s du + j) E + e]
+__global__ void k_rootdft_idft3(int M3, int du, int E, RootTab rt, const Cx<double>* __restrict__ C2,
+                                Cx<double>* __restrict__ Dm) {
+    const int Q3 = rt.Q[2];
+    const int64_t per = (int64_t)du * E;
     const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (id >= (int64_t)jobs * p3) return;
-    const int job = (int)(id / p3), e = (int)(id % p3);
-    const int j1 = e / p2, r = e % p2;
-    const Cx<double>* c = C1 + (size_t)job * rt.n1 * p2 + r;
+    if (id >= (int64_t)M3 * per) return;
+    const int m3 = (int)(id / per);
+    const int64_t t = id % per;
     Cx<double> v = {0, 0};
-    for (int k = 0; k < rt.n1; ++k) cfma(v, cconj(rt.S[0][k * p + j1]), c[(size_t)k * p2]);
-    Gs[id] = v;
+    for (int sidx = 0; sidx < Q3; ++sidx)
+        cfma(v, rt.roots[2][(int)(((int64_t)sidx * m3) % Q3)], C2[(size_t)sidx * per + t]);
+    Dm[id] = v;
 }
 
-// inverse DFT over s and the real part: local[(m du + j) p^3 + e] = Re sum_s exp(2 pi i s m / M3)
-// Gs[(s du + j) p^3 + e] + constant (cube m is box m of level 0); one thread per output
-template <class T>
-__global__ void k_rootfft_idft(int M, int du, int p, RootTab rt, const Cx<double>* __restrict__ Gs,
-                               const double* __restrict__ rho_sum, int drho, T* __restrict__ local) {
-    const int p3 = p * p * p;
-    const int64_t per = (int64_t)du * p3;
+// per cube m = m1 + M1 (m2 + M2 m3), k2 -> j2 with the cube's phase for m2:
+//   C1[(m du + j) n1 p^2 + (i1 p + j2) p + j3] =
+//     sum_i2 conj(S2(j2, k2)) exp(2 pi i s2 m2 / Q2) Dm[(m3 du + j) E + (i1 n2 + i2) p + j3]
+__global__ void k_rootdft_bwd2(int Mtot, int du, int p, Geo g, RootTab rt, const Cx<double>* __restrict__ Dm,
+                               Cx<double>* __restrict__ C1) {
+    const int p2 = p * p, n2 = rt.n2, per = rt.n1 * p2, E = rt.n1 * n2 * p;
     const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (id >= (int64_t)M * per) return;
-    const int m = (int)(id / per);
-    const int64_t t = id % per;
-    const int j = (int)(t / p3);
-    double v = 0;
-    for (int sidx = 0; sidx < M; ++sidx) {
-        const Cx<double> w = rt.roots[(sidx * m) % M];
-        const Cx<double> gsv = Gs[(size_t)sidx * per + t];
-        v += w.x * gsv.x - w.y * gsv.y;
+    if (id >= (int64_t)Mtot * du * per) return;
+    const int job = (int)(id / per), e = (int)(id % per);
+    const int m = job / du, j = job % du;
+    const int m2 = (m / g.M[0]) % g.M[1], m3 = m / (g.M[0] * g.M[1]);
+    const int i1 = e / p2, j2 = (e / p) % p, j3 = e % p;
+    const Cx<double>* c = Dm + ((size_t)m3 * du + j) * E + (size_t)i1 * n2 * p + j3;
+    Cx<double> v = {0, 0};
+    for (int k = 0; k < n2; ++k) {
+        const Cx<double> w = rt.roots[1][(int)(((int64_t)rt.nmod[1][k] * m2) % rt.Q[1])];
+        cfma(v, cmul(cconj(rt.S[1][k * p + j2]), w), c[(size_t)k * p]);
     }
-    double cst = 0;
-    if (rho_sum) for (int b = 0; b < drho; ++b) cst += rt.rconst[j * drho + b] * rho_sum[b];
-    local[id] = (T)(v + cst);
+    C1[id] = v;
+}
+
+// per cube, k1 -> j1 with the cube's phase for m1, real part: local[(m du + j) p^3 + e]
+// (= or += with add: a second root part adds to the first)
+template <class T>
+__global__ void k_rootdft_bwd3(int Mtot, int du, int p, Geo g, RootTab rt, const Cx<double>* __restrict__ C1,
+                               T* __restrict__ local, int add) {
+    const int p2 = p * p, p3 = p2 * p;
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= (int64_t)Mtot * du * p3) return;
+    const int job = (int)(id / p3), e = (int)(id % p3);
+    const int m1 = (job / du) % g.M[0];
+    const int j1 = e / p2, r = e % p2;
+    const Cx<double>* c = C1 + (size_t)job * rt.n1 * p2 + r;
+    double v = 0;
+    for (int k = 0; k < rt.n1; ++k) {
+        const Cx<double> w = rt.roots[0][(int)(((int64_t)rt.nmod[0][k] * m1) % rt.Q[0])];
+        const Cx<double> f = cmul(cconj(rt.S[0][k * p + j1]), w);
+        const Cx<double> b = c[(size_t)k * p2];
+        v += f.x * b.x - f.y * b.y;
+    }
+    const size_t o = (size_t)job * p3 + e;
+    local[o] = add ? (T)((double)local[o] + v) : (T)v;
 }
 
 // Position part of the vector-Jacobian product (reverse-mode derivative of the sums for a

@@ -300,6 +300,21 @@ int ceil_guard(double x) { return (int)std::ceil(x * (1.0 - 1e-12)); }
 // smallest N with N h > K, i.e. ceil(K/h) and one more where K/h is an integer (relative 1e-12)
 int free_count(double K, double h) { return (int)std::floor(K / h * (1.0 + 1e-12)) + 1; }
 
+// Length Q of the cube-index DFT along axis a of one root part, 0 if there is none: 1 on an
+// axis of one cube or a lone k = 0; M_a on an exactly tiled periodic axis (k = 2 pi n / L_a,
+// Sec. 3.4); on a free axis of step h, Q = 2 pi / (h s) when that is an integer >= M_a, the
+// oversampled length of Sec. 5.4 (Eq. kappaqdef with q M = Q).
+int dft_length(const std::vector<double>& ax, int Ma, bool periodic_axis, double s) {
+    if (Ma == 1 || (ax.size() == 1 && ax[0] == 0.0)) return 1;
+    if (periodic_axis) return Ma;
+    if (ax.size() < 2) return 0;
+    const double h = (ax.back() - ax.front()) / (double)(ax.size() - 1);
+    const double Qf = 2 * kPi / (h * s);
+    const long long Q = std::llround(Qf);
+    if (std::fabs(Qf - (double)Q) > 1e-9 * Qf || Q < Ma || Q > 65536) return 0;
+    return (int)Q;
+}
+
 // App. E (Eqs. app_m1_error_estimate, app_m2_error_estimate): the pole estimate of the error of
 // the infinite trapezoidal rule with step h for the model integral I_m(alpha, b), |b| = s;
 // cosh(alpha s)/E and sinh(alpha s)/E (E = e^x - 1, x = 2 pi alpha / h) formed as exponentials of
@@ -666,6 +681,22 @@ dmk_status_t build_plan_tables(int kernel, int D, const double Lin[3], double to
                         for (int e = 0; e < nm; ++e) out[e] = op[e] * base;
                     }
             T.n_root_modes = nz + no;
+        }
+        // sums over the cubes as DFTs over the cube index (Sec. 3.4, 5.4): an exact tiling of two
+        // or more cubes whose every root part admits one along every axis
+        {
+            bool ok = mtot >= 2 && !T.padded[0] && !T.padded[1] && !T.padded[2];
+            const int nparts = T.original_symbol ? 2 : 1;
+            for (int part = 0; part < nparts && ok; ++part)
+                for (int a = 0; a < 3; ++a) {
+                    const int Q = dft_length(part == 0 ? T.kax[a] : T.kax2[a], T.M[a], a < D, s);
+                    if (Q == 0) ok = false;
+                    T.root_dft_Q[part][a] = Q;
+                }
+            T.root_dft = ok;
+            if (!ok)
+                for (int part = 0; part < 2; ++part)
+                    for (int a = 0; a < 3; ++a) T.root_dft_Q[part][a] = 0;
         }
         // constants added to the root grid per unit summed strength
         T.root_const.assign(nm, 0.0);

@@ -50,7 +50,7 @@ class PlanInfo(ctypes.Structure):
                 ("p", ctypes.c_int32), ("n_f", ctypes.c_int32), ("n_root_modes", ctypes.c_int32),
                 ("fit_terms_fp64", ctypes.c_int32), ("fit_terms_fp32", ctypes.c_int32),
                 ("M", ctypes.c_int32 * 3), ("n_axis", ctypes.c_int32 * 3),
-                ("d_rho", ctypes.c_int32), ("d_u", ctypes.c_int32)]
+                ("d_rho", ctypes.c_int32), ("d_u", ctypes.c_int32), ("root_dft_len", ctypes.c_int32 * 6)]
 
 
 _lib = None
@@ -228,6 +228,7 @@ def plan_info(kernel, D, L, tol):
     d = {k: getattr(out, k) for k, _ in out._fields_}
     d["M"] = list(out.M)
     d["n_axis"] = list(out.n_axis)
+    d["root_dft_len"] = [list(out.root_dft_len)[:3], list(out.root_dft_len)[3:]]
     return d
 
 

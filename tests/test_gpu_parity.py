@@ -53,6 +53,15 @@ CASES = [
     ("stokeslet-1P-original", "stokeslet", 1, [1, 3, 3], 1e-6, 1000, 30, "mixed", "stokes"),
     ("rotlet-2P-original", "rotlet", 2, [1, 1, 3], 1e-6, 800, 30, "mixed", "stokes"),
     ("laplace-1P-1e-3-original", "laplace", 1, [1, 1, 1], 1e-3, 1500, 40, "uniform", "neutral"),
+    # sums over the cubes as DFTs over the cube index (Sec. 3.4 Case 2, Sec. 5.4 oversampled):
+    # two long periodic sides; cubes along x1 and x2 with one along x3; a long periodic x2 with a
+    # free x3 of step pi/R (length 2 R/s = 6); two free sides of R = 5 s (lengths 10), at 1e-6
+    # and at 1e-3 with the original symbol's second part (lengths 4 and 6)
+    ("laplace-3P-case2", "laplace", 3, [1, 3, 4], 1e-6, 1500, 40, "uniform", "neutral"),
+    ("rotlet-3P-2x3x1", "rotlet", 3, [2, 3, 1], 1e-6, 1200, 30, "uniform", "stokes"),
+    ("stokeslet-2P-oversampled", "stokeslet", 2, [1, 3, 2], 1e-6, 1200, 30, "mixed", "stokes"),
+    ("laplace-1P-oversampled", "laplace", 1, [1, 2, 3], 1e-6, 1200, 30, "mixed", "neutral"),
+    ("stokeslet-1P-oversampled-original", "stokeslet", 1, [1, 2, 3], 1e-3, 1000, 30, "mixed", "stokes"),
     # the singly periodic pipe of Sec. 6 (trapezoidal nodes on a cylinder around x1), at the
     # three tolerances of its figure, 1000 points per unit length
     ("stokeslet-1P-cylinder-1e-6", "stokeslet", 1, [2, 1, 1], 1e-6, 2000, 40, "cylinder", "stokes"),

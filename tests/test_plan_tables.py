@@ -123,3 +123,44 @@ def test_residual_cubic_tables(kernel, tol):
         u32 = u.astype(np.float32)
         v32 = c32[:, 0] + u32 * (c32[:, 1] + u32 * (c32[:, 2] + u32 * c32[:, 3]))
         assert np.max(np.abs(v32.astype(np.float64) - ref[k])) <= 4e-7 * scale, k
+
+
+# (D, L, the first root part's cube-index DFT lengths Q_a worked out by hand): a periodic axis of
+# M_a cubes gives M_a (Sec. 3.4); a free axis of step pi/R gives 2 R / s when that is an integer
+# (Sec. 5.4, Eq. kappaqdef): D = 2, L3 = 2 -> R = 3 s, Q3 = 6; L3 = 8 -> R = 9 s, Q3 = 18;
+# D = 1, (L2, L3) = (2, 3) -> R = |(3, 4)| s = 5 s, Q = 10 on both free axes; |(2, 4)| s is not a
+# rational multiple of s, a non-exact tiling and a single cube keep the direct sums (zeros)
+DFT_GEOMS = [(3, [1, 1, 16], [1, 1, 16]), (3, [1, 3, 4], [1, 3, 4]), (3, [2, 3, 1], [2, 3, 1]),
+             (2, [1, 3, 2], [1, 3, 6]), (2, [3, 1, 2], [3, 1, 6]), (2, [1, 1, 8], [1, 1, 18]),
+             (1, [1, 2, 3], [1, 10, 10]), (1, [1, 1, 3], [0, 0, 0]), (3, [1, 1.3, 1.7], [0, 0, 0]),
+             (2, [1, 1, 0.25], [0, 0, 0]), (0, [1, 2, 1], [0, 0, 0])]
+
+
+@pytest.mark.parametrize("kernel", ["laplace", "stokeslet", "stresslet", "rotlet"])
+@pytest.mark.parametrize("tol", [1e-3, 1e-6])
+def test_cube_index_dft_lengths(kernel, tol):
+    """Where the sums over the cubes become DFTs over the cube index, every wavenumber of every
+    root part of the oracle is k = 2 pi n / (Q_a s) with consecutive integers n along each axis
+    and Q_a >= M_a: the identity exp(-i k_a s m_a) = exp(-2 pi i (n mod Q_a) m_a / Q_a) behind
+    Eqs. 1d-DFT-beta and beta_hat_oversampled then holds on the oracle's own grids."""
+    for D, L, want in DFT_GEOMS:
+        info = dmk.plan_info(kernel, D, L, tol)
+        Q = info["root_dft_len"]
+        assert Q[0] == want, (D, L, Q)
+        c, _ = c_and_p(kernel, tol)
+        g = Geometry(D, L)
+        parts = root_parts(Kernel(kernel), g, c, PSWFWindow(c), tol)
+        if want == [0, 0, 0]:
+            assert Q[1] == [0, 0, 0]
+            continue
+        assert Q[1] == ([0, 0, 0] if len(parts) == 1 else Q[1]) and (len(parts) == 1 or min(Q[1]) >= 1)
+        for ip, (axes, *_rest) in enumerate(parts):
+            for a in range(3):
+                if g.M[a] == 1 or (len(axes[a]) == 1 and axes[a][0] == 0.0):
+                    assert Q[ip][a] == 1        # one cube, or only k = 0: every phase is 1
+                    continue
+                assert Q[ip][a] >= g.M[a]
+                n = np.asarray(axes[a]) * Q[ip][a] * g.s / (2 * np.pi)
+                assert np.max(np.abs(n - np.rint(n))) < 1e-9, (D, L, ip, a)
+                if len(n) > 1:
+                    assert np.all(np.diff(np.rint(n)) == 1)
