@@ -38,7 +38,7 @@ def test_strength_gradient_is_potential():
     u = pot(xt, qt)
     E = 0.5 * (qt * u).sum()
     (gq,) = torch.autograd.grad(E, qt)
-    assert torch.allclose(gq, u.detach(), rtol=1e-9, atol=1e-12 * float(u.abs().max()))
+    assert torch.allclose(gq, u.detach(), rtol=1e-9, atol=1e-12 * float(u.detach().abs().max()))
 
 
 def test_forces_finite_difference():
