@@ -164,3 +164,55 @@ def test_cube_index_dft_lengths(kernel, tol):
                 assert np.max(np.abs(n - np.rint(n))) < 1e-9, (D, L, ip, a)
                 if len(n) > 1:
                     assert np.all(np.diff(np.rint(n)) == 1)
+
+
+@pytest.mark.parametrize("kernel,D,L", [("laplace", 3, [1, 3, 4]), ("rotlet", 3, [2, 3, 1]), ("laplace", 2, [1, 3, 2]),
+                                        ("laplace", 2, [1, 1, 8]), ("stokeslet", 1, [1, 2, 3]),
+                                        ("rotlet", 2, [1, 1, 3])],
+                         ids=["3P-1x3x4", "3P-2x3x1", "2P-1x3x2", "2P-1x1x8", "1P-1x2x3", "2P-1x1x3"])
+def test_cube_index_dft_reproduces_direct_sums(kernel, D, L):
+    """The sums over the cubes of Eqs. structurefac and eval_tensor, written as a zero-padded FFT
+    over the cube index at the plan's lengths Q_a (Eqs. 1d-DFT-beta and beta_hat_oversampled:
+    beta-hat_s = sum_m exp(-2 pi i s . m / Q) rho~^m, chi(k) = exp(-i k . c_0) sum_j S(j, k)
+    beta-hat_{n(k) mod Q}(j); the evaluation by the inverse FFT of the sums grouped by n mod Q),
+    equal the direct sums over the cubes with the oracle's own root parts and nodes, for random
+    root proxies: the lengths of the library's plan and the reading of Sec. 3.4 and 5.4 together
+    reproduce the definition.  numpy's FFT, no device."""
+    from oracle.dmk import cheb_nodes
+    tol = 1e-3
+    K = Kernel(kernel)
+    c, p = c_and_p(kernel, tol)
+    g = Geometry(D, L)
+    Q = dmk.plan_info(kernel, D, L, tol)["root_dft_len"]
+    parts = root_parts(K, g, c, PSWFWindow(c), tol)
+    assert min(Q[0]) >= 1 and (len(parts) == 1 or min(Q[1]) >= 1)
+    M = list(g.M)
+    y = (g.s / 2) * cheb_nodes(p)
+    rng = np.random.default_rng(17)
+    prox = rng.standard_normal((M[0], M[1], M[2], p, p, p, K.d_rho))        # [m1, m2, m3, j1, j2, j3, a]
+    cen = [(np.arange(M[a]) + 0.5) * g.s for a in range(3)]
+    c0 = 0.5 * g.s
+    for ip, (axes, keep, Wk, _) in enumerate(parts):
+        S = [np.exp(-1j * np.outer(ax, y)) for ax in axes]                  # S[a][i, j] = exp(-i k y_j)
+        E = [np.exp(-1j * np.outer(cen[a], axes[a])) for a in range(3)]     # E[a][m, i] = exp(-i k c_m)
+        chi_dir = np.einsum("xa,yb,zc,ai,bj,ck,xyzijkd->abcd", E[0], E[1], E[2], S[0], S[1], S[2], prox,
+                            optimize=True)
+        u_hat = np.einsum("abcud,abcd->abcu", Wk, chi_dir)
+        u_dir = np.einsum("xa,yb,zc,ai,bj,ck,abcu->xyzijku", E[0].conj(), E[1].conj(), E[2].conj(), S[0].conj(),
+                          S[1].conj(), S[2].conj(), u_hat, optimize=True).real
+        q = Q[ip]
+        # the group of every wavenumber: n mod Q_a with k = 2 pi n / (Q_a s)
+        P = []
+        for a in range(3):
+            n = np.rint(np.asarray(axes[a]) * q[a] * g.s / (2 * np.pi)).astype(np.int64)
+            P.append((np.mod(n, q[a])[None, :] == np.arange(q[a])[:, None]).astype(float))   # [s, i]
+        bhat = np.fft.fftn(prox, s=q, axes=(0, 1, 2))                       # zero padded from M to Q
+        ph0 = np.exp(-1j * c0 * (axes[0][:, None, None] + axes[1][None, :, None] + axes[2][None, None, :]))
+        chi_dft = ph0[..., None] * np.einsum("xa,yb,zc,ai,bj,ck,xyzijkd->abcd", P[0], P[1], P[2], S[0], S[1], S[2],
+                                             bhat, optimize=True)
+        scale = np.max(np.abs(chi_dir))
+        assert np.max(np.abs(chi_dft - chi_dir)) <= 1e-12 * scale, (ip, q)
+        G = np.einsum("xa,yb,zc,ai,bj,ck,abcu->xyzijku", P[0], P[1], P[2], S[0].conj(), S[1].conj(), S[2].conj(),
+                      ph0.conj()[..., None] * u_hat, optimize=True)
+        u_dft = (np.prod(q) * np.fft.ifftn(G, axes=(0, 1, 2)))[:M[0], :M[1], :M[2]].real
+        assert np.max(np.abs(u_dft - u_dir)) <= 1e-12 * np.max(np.abs(u_dir)), (ip, q)
