@@ -10,7 +10,8 @@
  * when x_t = x_s, by the periodized dual-space multilevel kernel-splitting method:
  * leaf residual sums over periodically wrapped neighbour lists (Sec. 2.3, Eq. u_local),
  * per-level difference-kernel plane-wave interactions (Sec. 2.3 Eq. Dl_int_discr,
- * Sec. 3.1.4) and the root-level Fourier far field (Sec. 4.3, 4.4, 5.3).  In dmk_eval the
+ * Sec. 3.1.4) and the root-level Fourier far field (Sec. 4.3, 4.4, 5.3; on tilings of several
+ * cubes the sums over the cubes as DFTs over the cube index, Sec. 3.4, 5.4).  In dmk_eval the
  * sources are the targets (Sec. 1); dmk_eval_targets takes a separate target set.  Kernels:
  * Laplace K = 1/(4 pi r) and the Stokeslet, stresslet and rotlet of App. B.
  *
