@@ -306,12 +306,22 @@ int free_count(double K, double h) { return (int)std::floor(K / h * (1.0 + 1e-12
 // oversampled length of Sec. 5.4 (Eq. kappaqdef with q M = Q).
 int dft_length(const std::vector<double>& ax, int Ma, bool periodic_axis, double s) {
     if (Ma == 1 || (ax.size() == 1 && ax[0] == 0.0)) return 1;
-    if (periodic_axis) return Ma;
-    if (ax.size() < 2) return 0;
-    const double h = (ax.back() - ax.front()) / (double)(ax.size() - 1);
-    const double Qf = 2 * kPi / (h * s);
-    const long long Q = std::llround(Qf);
-    if (std::fabs(Qf - (double)Q) > 1e-9 * Qf || Q < Ma || Q > 65536) return 0;
+    long long Q = Ma;
+    if (!periodic_axis) {
+        if (ax.size() < 2) return 0;
+        const double h = (ax.back() - ax.front()) / (double)(ax.size() - 1);
+        const double Qf = 2 * kPi / (h * s);
+        Q = std::llround(Qf);
+        if (std::fabs(Qf - (double)Q) > 1e-9 * Qf || Q < Ma || Q > 65536) return 0;
+    }
+    // every wavenumber is 2 pi n / (Q s) with consecutive integers n: the evaluation reaches the
+    // modes of one residue n mod Q by stepping Q indices along the axis
+    double prev = 0;
+    for (size_t i = 0; i < ax.size(); ++i) {
+        const double n = ax[i] * (double)Q * s / (2 * kPi), nr = std::nearbyint(n);
+        if (std::fabs(n - nr) > 1e-6 || (i > 0 && nr != prev + 1)) return 0;
+        prev = nr;
+    }
     return (int)Q;
 }
 
